@@ -1,0 +1,178 @@
+/*
+ * isax.h - C ABI of the GB300 exact Euclidean k-NN engine over in-memory
+ * data-series collections, driven by an iSAX index (Peng, Fatourou, Palpanas,
+ * "Data Series Indexing Gone Parallel": ParIS / ParIS+ / MESSI).
+ *
+ * All compute runs in sm_103a CUDA kernels; these entry points only validate
+ * arguments, move buffers and launch.  Every call is stream-ordered on the
+ * given CUDA stream (a cudaStream_t passed as void*, NULL = legacy default
+ * stream) and returns after its results are in the caller's buffers.
+ *
+ * Pointers are "host" or "device" as the mem_flags bits say; device pointers
+ * must belong to the device the index lives on.  Float arrays must be 16-byte
+ * aligned (torch and cudaMalloc allocations are).  On any error a call returns
+ * a non-zero isax_status, leaves its outputs unspecified, leaks nothing, and
+ * isax_last_error() describes the failure (per calling thread).
+ */
+#ifndef ISAX_H
+#define ISAX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum isax_status {
+    ISAX_OK = 0,
+    ISAX_ERR_INVALID_ARG = 1, /* bad size, pointer, flag, or non-finite input */
+    ISAX_ERR_OOM = 2,         /* a device allocation failed */
+    ISAX_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    ISAX_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    ISAX_ERR_INTERNAL = 5     /* an internal consistency check failed */
+} isax_status;
+
+#define ISAX_W 16          /* segments per series: the paper fixes w = 16 (Section III) */
+#define ISAX_MAX_K 1024    /* largest k a query accepts */
+#define ISAX_MAX_LEN 4096  /* largest series length n */
+
+/* mem_flags bits */
+#define ISAX_MEM_INPUT_DEVICE 1u  /* input series / queries are device pointers */
+#define ISAX_MEM_OUTPUT_DEVICE 2u /* output arrays are device pointers */
+
+typedef struct isax_build_params {
+    int32_t w;           /* segments; must be ISAX_W (16) */
+    int32_t cardinality; /* symbols per segment: power of two in [2, 256] (256 = 8-bit SAX) */
+    int32_t leaf_size;   /* leaf capacity, >= 1 (runs of identical keys are cut into pieces of this size) */
+    uint32_t mem_flags;  /* ISAX_MEM_INPUT_DEVICE if `series` is a device pointer */
+} isax_build_params;
+
+typedef struct isax_query_stats {
+    int64_t leaves_total;     /* leaves in the index (each gets an envelope bound) */
+    int64_t leaves_queued;    /* leaves whose bound did not exceed the approximate BSF */
+    int64_t leaves_scanned;   /* queued leaves still unpruned when a CTA claimed them */
+    int64_t series_lb;        /* series lower bounds computed */
+    int64_t series_refined;   /* exact distances computed (approximate leaf included) */
+    int64_t candidates;       /* refined series kept for the final ordering */
+    int64_t window;           /* candidates re-ranked in FP64 */
+    int32_t approx_leaf;      /* leaf used for the approximate answer */
+    int32_t reruns;           /* reruns after a candidate-buffer overflow */
+} isax_query_stats;
+
+typedef struct isax_index_info {
+    int64_t N;             /* series */
+    int32_t n;             /* series length */
+    int32_t w;             /* segments (16) */
+    int32_t cardinality;   /* symbols per segment */
+    int32_t leaf_size;     /* leaf capacity */
+    int64_t leaves;        /* leaves */
+    int32_t max_leaf;      /* largest leaf */
+    int32_t device;        /* CUDA device ordinal */
+    int64_t device_bytes;  /* device memory held by the index */
+    float maxabs;          /* max |x| over the collection (bounds fp32 PAA error) */
+} isax_index_info;
+
+typedef struct isax_index isax_index;
+
+/*
+ * Device allocator hooks.  alloc returns NULL on failure; both are called with
+ * the stream of the calling entry point.  Default: cudaMallocAsync /
+ * cudaFreeAsync from the device's default memory pool.
+ */
+typedef void* (*isax_alloc_fn)(size_t bytes, void* cuda_stream, void* ctx);
+typedef void (*isax_free_fn)(void* ptr, void* cuda_stream, void* ctx);
+
+/* Install allocator hooks for indexes built afterwards (NULL, NULL restores
+ * the default).  Not thread-safe against concurrent builds. */
+isax_status isax_set_allocator(isax_alloc_fn alloc_fn, isax_free_fn free_fn, void* ctx);
+
+/*
+ * isax_build_index - summarise a collection and build its iSAX index
+ * (Section II, iSAX Representation and ADS+ Index; Section III, MESSI index
+ * construction, Stages 1-2).
+ *
+ *   series  [N][n] fp32, row-major; borrowed for the call only (the index keeps
+ *           its own copy, permuted into leaf order).
+ *   N       1 .. 2^32-2 series.
+ *   n       length, a multiple of 16 in [16, ISAX_MAX_LEN].
+ *   p       parameters (see isax_build_params); NULL = {16, 256, 2000, 0}.
+ *   out     receives the new index (NULL on error).
+ *
+ * Steps, all on the GPU: PAA of w segments and SAX symbols against N(0,1)
+ * breakpoints; a stable radix sort of the bit-plane-interleaved iSAX keys
+ * (first bit of every segment first: the root subtree of Section III); leaves
+ * cut top-down from the sorted keys; rows and SAX words gathered into leaf
+ * order; per-leaf min/max symbol envelopes.
+ * Errors: ISAX_ERR_INVALID_ARG (sizes, flags, null pointers, misaligned
+ * pointer, a non-finite value anywhere in `series`), ISAX_ERR_OOM, ISAX_ERR_CUDA.
+ */
+isax_status isax_build_index(const float* series, int64_t N, int32_t n, const isax_build_params* p,
+                             void* cuda_stream, isax_index** out);
+
+/*
+ * isax_query_knn - exact k nearest neighbours of one query under Euclidean
+ * distance (Section II, Similarity Search; k = 1 is the paper's NN query),
+ * answered with MESSI's strategy (Section III, MESSI Approach): approximate
+ * answer from the query's own leaf, leaf pruning by envelope lower bounds,
+ * leaves processed in lower-bound order, series lower bounds, then real
+ * distances with early abandoning, BSF updates.
+ *
+ *   q        [n] fp32 query (host or device per ISAX_MEM_INPUT_DEVICE).
+ *   k        1 .. min(N, ISAX_MAX_K).
+ *   out_idx  [k] int64: 0-based rows of the original `series`, ascending by
+ *            (distance, row); ties go to the lower row.
+ *   out_dist [k] fp32 Euclidean distances (not squared), each the FP64
+ *            distance rounded to fp32.
+ *   stats    optional per-query counters (NULL to skip).
+ * The answer equals the brute-force scan of the definition: distances are
+ * re-ranked in FP64 wherever fp32 cannot order them.  Calls on the same index
+ * are serialised internally.  Errors: ISAX_ERR_INVALID_ARG (k, pointers,
+ * non-finite query), ISAX_ERR_CUDA, ISAX_ERR_OOM.
+ */
+isax_status isax_query_knn(const isax_index* ix, const float* q, int32_t k, uint32_t mem_flags,
+                           int64_t* out_idx, float* out_dist, isax_query_stats* stats,
+                           void* cuda_stream);
+
+/*
+ * isax_query_knn_batch - B queries Q[B][n]; row b's answer, in out_idx[b][k]
+ * and out_dist[b][k], equals isax_query_knn on Q[b].  stats: NULL or [B].
+ */
+isax_status isax_query_knn_batch(const isax_index* ix, const float* Q, int32_t B, int32_t k,
+                                 uint32_t mem_flags, int64_t* out_idx, float* out_dist,
+                                 isax_query_stats* stats, void* cuda_stream);
+
+/* Release an index and its device memory (NULL is a no-op). */
+void isax_free_index(isax_index* ix);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char* isax_last_error(void);
+
+/* Sizes of an index. */
+isax_status isax_get_index_info(const isax_index* ix, isax_index_info* info);
+
+/*
+ * isax_index_export - copy the index's internal arrays to host buffers (any
+ * may be NULL): sax [N][16] symbols in leaf order, orig_id [N] original row of
+ * each leaf-order position, leaf_begin [leaves+1] first position of each leaf,
+ * envelope [leaves][32] (16 min symbols then 16 max symbols), breakpoints
+ * [cardinality-1] the fp32 N(0,1) quantiles used for the symbols.
+ */
+isax_status isax_index_export(const isax_index* ix, uint8_t* sax, uint32_t* orig_id,
+                              uint32_t* leaf_begin, uint8_t* envelope, float* breakpoints);
+
+/*
+ * isax_summarize - the build's summarisation step alone (Section II: PAA over
+ * w = 16 equal segments, then the SAX symbol of each segment mean).
+ *   series [N][n] fp32 (host or device per ISAX_MEM_INPUT_DEVICE)
+ *   out_sax [N][16] uint8 symbols, out_paa [N][16] fp32 segment means (either
+ *   may be NULL; host or device per ISAX_MEM_OUTPUT_DEVICE).
+ */
+isax_status isax_summarize(const float* series, int64_t N, int32_t n, int32_t cardinality,
+                           uint32_t mem_flags, uint8_t* out_sax, float* out_paa, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISAX_H */

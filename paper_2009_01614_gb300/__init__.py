@@ -1,0 +1,294 @@
+"""Python binding of libisaxgpu.so, the sm_103a exact k-NN engine over data
+series with an iSAX index (Peng, Fatourou, Palpanas, "Data Series Indexing Gone
+Parallel": ParIS / ParIS+ / MESSI).
+
+The C entry points are re-exported under their own names (``isax_build_index``,
+``isax_query_knn``, ...) with argument marshalling only; ``Index`` is a small
+convenience wrapper over them for numpy arrays and torch tensors.  Every step of
+the build and of the query runs in the library's CUDA kernels; there is no CPU
+fallback, and importing the binding fails loudly when the library is missing.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "ISAXError", "BuildParams", "QueryStats", "IndexInfo", "Index", "MEM_INPUT_DEVICE",
+    "MEM_OUTPUT_DEVICE", "W", "MAX_K", "lib", "build",
+    "isax_build_index", "isax_query_knn", "isax_query_knn_batch", "isax_free_index",
+    "isax_last_error", "isax_get_index_info", "isax_index_export", "isax_summarize",
+    "isax_set_allocator",
+]
+
+W = 16
+MAX_K = 1024
+MAX_LEN = 4096
+MEM_INPUT_DEVICE = 1
+MEM_OUTPUT_DEVICE = 2
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "cuda error", 4: "timeout",
+          5: "internal error"}
+
+
+class ISAXError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status, message))
+        self.status = status
+        self.message = message
+
+
+class BuildParams(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int32), ("cardinality", ctypes.c_int32),
+                ("leaf_size", ctypes.c_int32), ("mem_flags", ctypes.c_uint32)]
+
+
+class QueryStats(ctypes.Structure):
+    _fields_ = [("leaves_total", ctypes.c_int64), ("leaves_queued", ctypes.c_int64),
+                ("leaves_scanned", ctypes.c_int64), ("series_lb", ctypes.c_int64),
+                ("series_refined", ctypes.c_int64), ("candidates", ctypes.c_int64),
+                ("window", ctypes.c_int64), ("approx_leaf", ctypes.c_int32),
+                ("reruns", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class IndexInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("n", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("cardinality", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("leaves", ctypes.c_int64), ("max_leaf", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("maxabs", ctypes.c_float)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+
+def build():
+    """Compile libisaxgpu.so (sm_103a) in-tree if it is missing or stale."""
+    return _build.build()
+
+
+def lib():
+    """The loaded C library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libisaxgpu.so is not built (%s): run paper_2009_01614_gb300.build()"
+                               % _build.LIB)
+        L = ctypes.CDLL(_build.LIB)
+        vp, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+        st = ctypes.c_int
+        L.isax_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+        L.isax_set_allocator.restype = st
+        L.isax_build_index.argtypes = [vp, i64, i32, ctypes.POINTER(BuildParams), vp,
+                                       ctypes.POINTER(vp)]
+        L.isax_build_index.restype = st
+        L.isax_query_knn.argtypes = [vp, vp, i32, u32, vp, vp, ctypes.POINTER(QueryStats), vp]
+        L.isax_query_knn.restype = st
+        L.isax_query_knn_batch.argtypes = [vp, vp, i32, i32, u32, vp, vp,
+                                           ctypes.POINTER(QueryStats), vp]
+        L.isax_query_knn_batch.restype = st
+        L.isax_free_index.argtypes = [vp]
+        L.isax_free_index.restype = None
+        L.isax_last_error.argtypes = []
+        L.isax_last_error.restype = ctypes.c_char_p
+        L.isax_get_index_info.argtypes = [vp, ctypes.POINTER(IndexInfo)]
+        L.isax_get_index_info.restype = st
+        L.isax_index_export.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.isax_index_export.restype = st
+        L.isax_summarize.argtypes = [vp, i64, i32, i32, u32, vp, vp, vp]
+        L.isax_summarize.restype = st
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise ISAXError(status, lib().isax_last_error().decode())
+
+
+# ------------------------------------------------------------------ raw C ABI
+def isax_set_allocator(alloc_fn, free_fn, ctx=None):
+    _check(lib().isax_set_allocator(alloc_fn, free_fn, ctx))
+
+
+def isax_build_index(series_ptr, N, n, params=None, stream=0):
+    """Returns the index handle (int)."""
+    out = ctypes.c_void_p()
+    p = ctypes.byref(params) if params is not None else None
+    _check(lib().isax_build_index(series_ptr, N, n, p, stream, ctypes.byref(out)))
+    return out.value
+
+
+def isax_query_knn(index, q_ptr, k, mem_flags, out_idx_ptr, out_dist_ptr, stats=None, stream=0):
+    _check(lib().isax_query_knn(index, q_ptr, k, mem_flags, out_idx_ptr, out_dist_ptr,
+                                ctypes.byref(stats) if stats is not None else None, stream))
+
+
+def isax_query_knn_batch(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_ptr, stats=None,
+                         stream=0):
+    _check(lib().isax_query_knn_batch(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_ptr,
+                                      stats, stream))
+
+
+def isax_free_index(index):
+    lib().isax_free_index(index)
+
+
+def isax_last_error():
+    return lib().isax_last_error().decode()
+
+
+def isax_get_index_info(index):
+    info = IndexInfo()
+    _check(lib().isax_get_index_info(index, ctypes.byref(info)))
+    return info
+
+
+def isax_index_export(index, sax_ptr=None, orig_ptr=None, leaf_begin_ptr=None, env_ptr=None,
+                      bp_ptr=None):
+    _check(lib().isax_index_export(index, sax_ptr, orig_ptr, leaf_begin_ptr, env_ptr, bp_ptr))
+
+
+def isax_summarize(series_ptr, N, n, cardinality, mem_flags, out_sax_ptr, out_paa_ptr, stream=0):
+    _check(lib().isax_summarize(series_ptr, N, n, cardinality, mem_flags, out_sax_ptr,
+                                out_paa_ptr, stream))
+
+
+# ------------------------------------------------------------------ convenience
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _buffer(x):
+    """(pointer, on_device, keepalive, shape) of a contiguous float32 array/tensor."""
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float32:
+            raise TypeError("expected float32")
+        x = x.contiguous()
+        return x.data_ptr(), x.is_cuda, x, tuple(x.shape)
+    import numpy as np
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    return a.ctypes.data, False, a, a.shape
+
+
+def _stream_of(t, stream):
+    if stream is not None:
+        return stream
+    if _is_torch(t) and t.is_cuda:
+        import torch
+        return torch.cuda.current_stream(t.device).cuda_stream
+    return 0
+
+
+class Index:
+    """An iSAX index resident in device memory.
+
+    ``Index(series, cardinality=256, leaf_size=2000)`` builds from a float32
+    [N, n] numpy array (host) or torch tensor (host or CUDA)."""
+
+    def __init__(self, series, cardinality=256, leaf_size=2000, stream=None):
+        ptr, on_dev, keep, shape = _buffer(series)
+        if len(shape) != 2:
+            raise ValueError("series must be 2-D [N, n]")
+        N, n = shape
+        p = BuildParams(W, cardinality, leaf_size, MEM_INPUT_DEVICE if on_dev else 0)
+        self._h = None
+        self._h = isax_build_index(ptr, N, n, p, _stream_of(keep, stream))
+        self.N, self.n = N, n
+        self.cardinality, self.leaf_size = cardinality, leaf_size
+
+    def close(self):
+        if self._h:
+            isax_free_index(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        return isax_get_index_info(self._h).as_dict()
+
+    def export(self):
+        import numpy as np
+        inf = isax_get_index_info(self._h)
+        sax = np.empty((inf.N, W), np.uint8)
+        orig = np.empty(inf.N, np.uint32)
+        lb = np.empty(inf.leaves + 1, np.uint32)
+        env = np.empty((inf.leaves, 2 * W), np.uint8)
+        bp = np.empty(inf.cardinality - 1, np.float32)
+        isax_index_export(self._h, sax.ctypes.data, orig.ctypes.data, lb.ctypes.data,
+                          env.ctypes.data, bp.ctypes.data)
+        return {"sax": sax, "orig": orig, "leaf_begin": lb, "env": env, "breakpoints": bp}
+
+    def query(self, q, k=1, stats=False, stream=None):
+        """Exact k-NN of one query: (indices int64 [k], distances float32 [k]
+        [, stats dict]).  A CUDA tensor query returns CUDA tensors."""
+        return self._run(q, k, stats, stream, batch=False)
+
+    def query_batch(self, Q, k=1, stats=False, stream=None):
+        return self._run(Q, k, stats, stream, batch=True)
+
+    def _run(self, q, k, want_stats, stream, batch):
+        ptr, on_dev, keep, shape = _buffer(q)
+        B = shape[0] if batch else 1
+        if (batch and (len(shape) != 2 or shape[1] != self.n)) or (not batch and shape[-1] != self.n):
+            raise ValueError("query length must be %d" % self.n)
+        st = _stream_of(keep, stream)
+        if on_dev:
+            import torch
+            idx = torch.empty((B, k), dtype=torch.int64, device=keep.device)
+            dist = torch.empty((B, k), dtype=torch.float32, device=keep.device)
+            ip, dp, flags = idx.data_ptr(), dist.data_ptr(), MEM_INPUT_DEVICE | MEM_OUTPUT_DEVICE
+        else:
+            import numpy as np
+            idx = np.empty((B, k), np.int64)
+            dist = np.empty((B, k), np.float32)
+            ip, dp, flags = idx.ctypes.data, dist.ctypes.data, 0
+        stats = (QueryStats * B)()
+        if batch:
+            isax_query_knn_batch(self._h, ptr, B, k, flags, ip, dp, stats, st)
+        else:
+            isax_query_knn(self._h, ptr, k, flags, ip, dp, stats[0], st)
+        if not batch:
+            idx, dist = idx[0], dist[0]
+        if want_stats:
+            s = [x.as_dict() for x in stats]
+            return idx, dist, (s if batch else s[0])
+        return idx, dist
+
+
+def summarize(series, cardinality=256, stream=None):
+    """(symbols uint8 [N, 16], PAA float32 [N, 16]) from the GPU summarisation
+    kernel alone; host arrays in, host arrays out (or CUDA tensors in/out)."""
+    ptr, on_dev, keep, shape = _buffer(series)
+    N, n = shape
+    st = _stream_of(keep, stream)
+    if on_dev:
+        import torch
+        sax = torch.empty((N, W), dtype=torch.uint8, device=keep.device)
+        paa = torch.empty((N, W), dtype=torch.float32, device=keep.device)
+        isax_summarize(ptr, N, n, cardinality, MEM_INPUT_DEVICE | MEM_OUTPUT_DEVICE,
+                       sax.data_ptr(), paa.data_ptr(), st)
+    else:
+        import numpy as np
+        sax = np.empty((N, W), np.uint8)
+        paa = np.empty((N, W), np.float32)
+        isax_summarize(ptr, N, n, cardinality, 0, sax.ctypes.data, paa.ctypes.data, st)
+    return sax, paa

@@ -1,0 +1,60 @@
+"""Compile the sm_103a CUDA library libisaxgpu.so in-tree (nvcc, one gencode,
+translation units in parallel)."""
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT, "libisaxgpu.so")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+
+SOURCES = ["isax_api.cu", "isax_build.cu", "isax_query.cu"]
+HEADERS = ["isax_common.cuh", "isax_kernels_util.cuh"]
+GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
+NVCC_FLAGS = [GENCODE, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+              "-Xptxas", "-warn-spills", "--expt-relaxed-constexpr"]
+
+
+def _deps():
+    return ([os.path.join(CSRC, s) for s in SOURCES + HEADERS] +
+            [os.path.join(INCLUDE, "isax.h")])
+
+
+def stale():
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(p) > t for p in _deps())
+
+
+def build(verbose=False, extra_flags=()):
+    if not stale() and not extra_flags:
+        return LIB
+    os.makedirs(OUT, exist_ok=True)
+    procs = []
+    objs = []
+    for src in SOURCES:
+        obj = os.path.join(OUT, src.replace(".cu", ".o"))
+        objs.append(obj)
+        cmd = ["nvcc"] + NVCC_FLAGS + list(extra_flags) + ["-I", INCLUDE, "-c",
+                                                            os.path.join(CSRC, src), "-o", obj]
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    logs = []
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        logs.append(out.decode())
+        if p.returncode != 0:
+            raise RuntimeError("nvcc failed: %s\n%s" % (" ".join(cmd), out.decode()))
+    link = ["nvcc", GENCODE, "-shared", "-o", LIB] + objs + ["-lcudart"]
+    p = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    if p.returncode != 0:
+        raise RuntimeError("link failed:\n" + p.stdout.decode())
+    if verbose:
+        print("".join(logs))
+    return LIB
+
+
+if __name__ == "__main__":
+    import sys
+    build(verbose=True, extra_flags=sys.argv[1:])

@@ -1,0 +1,864 @@
+// isax_build.cu - index construction on the GPU (Section II: PAA, iSAX symbols,
+// ADS+ tree; Section III: MESSI's two-stage in-memory build).
+//
+// MESSI computes the iSAX summaries of RawData chunks and appends them to one
+// iSAX buffer per root subtree (Stage 1), then builds every root subtree
+// independently (Stage 2).  On the GPU the same result comes from:
+//   summarize  - one warp per series: PAA of 16 segments, SAX symbols, and a
+//                bit-plane-interleaved key whose top 16 bits are the root key
+//                (first bit of every segment);
+//   radix sort - a stable LSD sort of (key, row) pairs: the per-root buffers
+//                become contiguous runs, and inside a run series are ordered
+//                by their next bits, so every iSAX node is a contiguous range;
+//   leaves     - a node becomes a leaf once it holds <= leaf_size series; a
+//                node splits on the next key bit (round-robin over segments),
+//                decided for every adjacent pair from its common-prefix length
+//                and a sliding-window maximum (no pointer tree is built);
+//   permute    - rows and SAX words gathered into leaf order;
+//   envelopes  - per-leaf min/max symbol of every segment.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "isax_common.cuh"
+#include "isax_kernels_util.cuh"
+
+namespace isax {
+
+// ============================================================== breakpoints
+// Phi^{-1}(p) for p in (0, 1/2): Acklam's rational approximation
+// (P. J. Acklam, "An algorithm for computing the inverse normal cumulative
+// distribution function", 2003), then Halley steps on Phi(x) = erfc(-x/sqrt2)/2.
+__device__ double inv_norm_lower(double p) {
+    const double a1 = -3.969683028665376e+01, a2 = 2.209460984245205e+02,
+                 a3 = -2.759285104469687e+02, a4 = 1.383577518672690e+02,
+                 a5 = -3.066479806614716e+01, a6 = 2.506628277459239e+00;
+    const double b1 = -5.447609879822406e+01, b2 = 1.615858368580409e+02,
+                 b3 = -1.556989798598866e+02, b4 = 6.680131188771972e+01,
+                 b5 = -1.328068155288572e+01;
+    const double c1 = -7.784894002430293e-03, c2 = -3.223964580411365e-01,
+                 c3 = -2.400758277161838e+00, c4 = -2.549732539343734e+00,
+                 c5 = 4.374664141464968e+00, c6 = 2.938163982698783e+00;
+    const double d1 = 7.784695709041462e-03, d2 = 3.224671290700398e-01,
+                 d3 = 2.445134137142996e+00, d4 = 3.754408661907416e+00;
+    double x;
+    if (p < 0.02425) {
+        double q = sqrt(-2.0 * log(p));
+        x = (((((c1 * q + c2) * q + c3) * q + c4) * q + c5) * q + c6) /
+            ((((d1 * q + d2) * q + d3) * q + d4) * q + 1.0);
+    } else {
+        double q = p - 0.5, r = q * q;
+        x = (((((a1 * r + a2) * r + a3) * r + a4) * r + a5) * r + a6) * q /
+            (((((b1 * r + b2) * r + b3) * r + b4) * r + b5) * r + 1.0);
+    }
+    const double sqrt2pi = 2.5066282746310002;
+    for (int it = 0; it < 3; ++it) {
+        double e = 0.5 * erfc(-x * 0.70710678118654752440) - p;
+        double u = e * sqrt2pi * exp(0.5 * x * x);
+        x = x - u / (1.0 + 0.5 * x * u);
+    }
+    return x;
+}
+
+// bp[0..card] = {-inf, beta_1 .. beta_{card-1}, +inf}, beta_t = Phi^{-1}(t/card)
+// rounded to fp32; antisymmetric by construction, beta_{card/2} = 0.
+__global__ void breakpoints_kernel(int card, float* bp) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > card) return;
+    float v;
+    if (t == 0)
+        v = -INFINITY;
+    else if (t == card)
+        v = INFINITY;
+    else if (2 * t == card)
+        v = 0.0f;
+    else {
+        int tl = 2 * t < card ? t : card - t;
+        double x = inv_norm_lower((double)tl / (double)card);
+        v = __double2float_rn(2 * t < card ? x : -x);
+    }
+    bp[t] = v;
+}
+
+void launch_breakpoints(int card, float* bp, cudaStream_t st) {
+    breakpoints_kernel<<<(card + 1 + 255) / 256, 256, 0, st>>>(card, bp);
+    ISAX_CUDA_TRY(cudaGetLastError());
+}
+
+// ============================================================== summarize
+// key: bit-plane-interleaved symbols, most significant plane first, segment 0
+// at the top of each 16-bit plane; planes beyond cbits (or beyond 4) are 0.
+__device__ __forceinline__ unsigned long long planes_to_key(int sym, bool active, int cbits) {
+    unsigned long long key = 0;
+#pragma unroll
+    for (int pl = 0; pl < 4; ++pl) {
+        int b = cbits - 1 - pl;
+        unsigned m = __ballot_sync(FULL, active && b >= 0 && ((sym >> (b < 0 ? 0 : b)) & 1));
+        key = (key << 16) | (unsigned long long)(__brev(m & 0xffffu) >> 16);
+    }
+    return key;
+}
+
+// One warp per series, series length NLEN in {128, 256, 512, 1024, 2048}: each
+// lane loads NLEN/128 float4; a segment is F = NLEN/64 consecutive float4
+// held by F consecutive lanes.  Segment sum: x+y+z+w per lane, then an xor tree
+// over the F lanes.  PAA = sum * (16/NLEN) (exact scaling).
+template <int NLEN>
+__global__ void __launch_bounds__(256) summarize_vec_kernel(
+    const float4* __restrict__ x, int64_t N, int card, int cbits, const float* __restrict__ bp_g,
+    uint8_t* __restrict__ sax, unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
+    float* __restrict__ paa_out, unsigned* maxabs_bits, unsigned* nonfinite) {
+    constexpr int F = NLEN / 64;
+    constexpr int PASSES = NLEN / 128;
+    constexpr int SPP = 32 / F;
+    constexpr float INV_M = 16.0f / (float)NLEN;
+    __shared__ float bp[MAX_CARD + 1];
+    __shared__ float red_max[32];
+    __shared__ unsigned red_bad;
+    for (int i = threadIdx.x; i <= card; i += blockDim.x) bp[i] = bp_g[i];
+    if (threadIdx.x == 0) red_bad = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float amax = 0.0f;
+    bool bad = false;
+    for (int64_t row = gw; row < N; row += nw) {
+        const float4* xr = x + row * (NLEN / 4);
+        float4 v[PASSES];
+#pragma unroll
+        for (int p = 0; p < PASSES; ++p) v[p] = ld_stream(xr + p * 32 + lane);
+        int mysym = 0;
+        float mypaa = 0.0f;
+#pragma unroll
+        for (int p = 0; p < PASSES; ++p) {
+            float s = ((v[p].x + v[p].y) + v[p].z) + v[p].w;
+            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[p].x), fabsf(v[p].y)),
+                                     fmaxf(fabsf(v[p].z), fabsf(v[p].w))));
+#pragma unroll
+            for (int off = 1; off < F; off <<= 1) s += __shfl_xor_sync(FULL, s, off);
+            float paa = s * INV_M;
+            int sym = symbol_of(paa, bp, card);
+            int src = ((lane - p * SPP) & (SPP - 1)) * F;
+            int ts = __shfl_sync(FULL, sym, src);
+            float tp = __shfl_sync(FULL, paa, src);
+            if (lane >= p * SPP && lane < (p + 1) * SPP) {
+                mysym = ts;
+                mypaa = tp;
+            }
+        }
+        const bool seg = lane < W;
+        bad |= seg && !isfinite(mypaa);
+        unsigned long long key = planes_to_key(mysym, seg, cbits);
+        if (seg) {
+            sax[row * W + lane] = (uint8_t)mysym;
+            if (paa_out) paa_out[row * W + lane] = mypaa;
+        }
+        if (lane == 0) {
+            if (keys) keys[row] = key;
+            if (ids) ids[row] = (uint32_t)row;
+        }
+    }
+    // block reductions -> one atomic per block
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, off));
+    if (lane == 0) red_max[threadIdx.x >> 5] = amax;
+    if (bad) atomicOr(&red_bad, 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, red_max[i]);
+        atomicMax(maxabs_bits, __float_as_uint(m));
+        if (red_bad) atomicOr(nonfinite, 1u);
+    }
+}
+
+// Any n (multiple of 16): a half-warp per series, one lane per segment summing
+// its m values left to right; PAA = sum / m.
+__global__ void __launch_bounds__(256) summarize_generic_kernel(
+    const float* __restrict__ x, int64_t N, int n, int card, int cbits,
+    const float* __restrict__ bp_g, uint8_t* __restrict__ sax, unsigned long long* __restrict__ keys,
+    uint32_t* __restrict__ ids, float* __restrict__ paa_out, unsigned* maxabs_bits,
+    unsigned* nonfinite) {
+    __shared__ float bp[MAX_CARD + 1];
+    __shared__ float red_max[32];
+    __shared__ unsigned red_bad;
+    for (int i = threadIdx.x; i <= card; i += blockDim.x) bp[i] = bp_g[i];
+    if (threadIdx.x == 0) red_bad = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int seg = lane & 15, half = lane >> 4;
+    const int m = n / W;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float amax = 0.0f;
+    bool bad = false;
+    for (int64_t pair = gw; pair * 2 < N; pair += nw) {
+        const int64_t row = pair * 2 + half;
+        const bool valid = row < N;
+        int sym = 0;
+        float paa = 0.0f;
+        if (valid) {
+            const float* p = x + row * n + seg * m;
+            float s = 0.0f;
+            for (int j = 0; j < m; ++j) {
+                float v = p[j];
+                s += v;
+                amax = fmaxf(amax, fabsf(v));
+            }
+            paa = s / (float)m;
+            sym = symbol_of(paa, bp, card);
+            bad |= !isfinite(paa);
+        }
+        unsigned long long key = 0;
+#pragma unroll
+        for (int pl = 0; pl < 4; ++pl) {
+            int b = cbits - 1 - pl;
+            unsigned mk = __ballot_sync(FULL, valid && b >= 0 && ((sym >> (b < 0 ? 0 : b)) & 1));
+            unsigned mine = (mk >> (16 * half)) & 0xffffu;
+            key = (key << 16) | (unsigned long long)(__brev(mine) >> 16);
+        }
+        if (valid) {
+            sax[row * W + seg] = (uint8_t)sym;
+            if (paa_out) paa_out[row * W + seg] = paa;
+            if (seg == 0) {
+                if (keys) keys[row] = key;
+                if (ids) ids[row] = (uint32_t)row;
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, off));
+    if (lane == 0) red_max[threadIdx.x >> 5] = amax;
+    if (bad) atomicOr(&red_bad, 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float mm = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = fmaxf(mm, red_max[i]);
+        atomicMax(maxabs_bits, __float_as_uint(mm));
+        if (red_bad) atomicOr(nonfinite, 1u);
+    }
+}
+
+void launch_summarize(const float* x, int64_t N, int n, int card, const float* bp, uint4* sax,
+                      unsigned long long* keys, uint32_t* ids, float* paa_out,
+                      unsigned* maxabs_bits, unsigned* nonfinite, int num_sms, cudaStream_t st) {
+    int cbits = 0;
+    while ((1 << cbits) < card) ++cbits;
+    const int threads = 256;
+    int64_t want = (N + 7) / 8;  // one warp per row
+    int64_t cap = (int64_t)num_sms * 8;
+    int blocks = (int)std::max<int64_t>(1, std::min(want, cap));
+    uint8_t* s8 = reinterpret_cast<uint8_t*>(sax);
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+#define ISAX_SUM_CASE(L)                                                                       \
+    case L:                                                                                    \
+        summarize_vec_kernel<L><<<blocks, threads, 0, st>>>(x4, N, card, cbits, bp, s8, keys, \
+                                                            ids, paa_out, maxabs_bits,         \
+                                                            nonfinite);                        \
+        break;
+    switch (n) {
+        ISAX_SUM_CASE(128)
+        ISAX_SUM_CASE(256)
+        ISAX_SUM_CASE(512)
+        ISAX_SUM_CASE(1024)
+        ISAX_SUM_CASE(2048)
+        default:
+            summarize_generic_kernel<<<blocks, threads, 0, st>>>(x, N, n, card, cbits, bp, s8, keys,
+                                                                 ids, paa_out, maxabs_bits,
+                                                                 nonfinite);
+    }
+#undef ISAX_SUM_CASE
+    ISAX_CUDA_TRY(cudaGetLastError());
+}
+
+// ============================================================== exclusive scan
+constexpr int SC_THREADS = 256, SC_ITEMS = 16, SC_TILE = SC_THREADS * SC_ITEMS;
+
+__global__ void __launch_bounds__(SC_THREADS) scan_reduce_kernel(const uint32_t* __restrict__ in,
+                                                                  int64_t len,
+                                                                  uint32_t* __restrict__ sums) {
+    __shared__ uint32_t scratch[32];
+    const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j)
+        if (base + j < len) s += in[base + j];
+    uint32_t tot;
+    block_excl_scan<uint32_t>(s, 0u, OpAdd<uint32_t>(), scratch, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// single block: exclusive scan of nb block sums in place; sums[nb] = total
+__global__ void __launch_bounds__(1024) scan_sums_kernel(uint32_t* sums, int64_t nb) {
+    __shared__ uint32_t scratch[32];
+    const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
+    const int64_t b0 = (int64_t)threadIdx.x * per, b1 = std::min<int64_t>(b0 + per, nb);
+    uint32_t s = 0;
+    for (int64_t i = b0; i < b1; ++i) s += sums[i];
+    uint32_t tot;
+    uint32_t off = block_excl_scan<uint32_t>(s, 0u, OpAdd<uint32_t>(), scratch, &tot);
+    for (int64_t i = b0; i < b1; ++i) {
+        uint32_t v = sums[i];
+        sums[i] = off;
+        off += v;
+    }
+    if (threadIdx.x == 0) sums[nb] = tot;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) scan_apply_kernel(const uint32_t* in, uint32_t* out,
+                                                                 int64_t len,
+                                                                 const uint32_t* __restrict__ sums) {
+    __shared__ uint32_t scratch[32];
+    const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+    uint32_t v[SC_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        v[j] = base + j < len ? in[base + j] : 0u;
+        s += v[j];
+    }
+    uint32_t tot;
+    uint32_t off = block_excl_scan<uint32_t>(s, 0u, OpAdd<uint32_t>(), scratch, &tot) + sums[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        if (base + j < len) out[base + j] = off;
+        off += v[j];
+    }
+}
+
+// out[i] = sum_{j<i} in[i] for i < len; out may alias in.  `sums` needs
+// ceil(len / SC_TILE) + 1 entries; the total lands in sums[ceil(len/SC_TILE)].
+static void exclusive_scan(const uint32_t* in, uint32_t* out, int64_t len, uint32_t* sums,
+                           cudaStream_t st) {
+    if (len <= 0) {
+        ISAX_CUDA_TRY(cudaMemsetAsync(sums, 0, sizeof(uint32_t), st));
+        return;
+    }
+    int64_t nb = (len + SC_TILE - 1) / SC_TILE;
+    scan_reduce_kernel<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, len, sums);
+    scan_sums_kernel<<<1, 1024, 0, st>>>(sums, nb);
+    scan_apply_kernel<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, out, len, sums);
+    ISAX_CUDA_TRY(cudaGetLastError());
+}
+
+static int64_t scan_sums_len(int64_t len) { return (len + SC_TILE - 1) / SC_TILE + 1; }
+
+// ============================================================== radix sort
+// Stable LSD radix sort of (64-bit key, 32-bit row) pairs, 8-bit digits.  Per
+// pass: per-tile digit histograms, an exclusive scan over (digit, tile), then
+// a scatter in which every warp ranks its elements with ballots over the digit
+// bits (stable: element order inside a tile is warp, item, lane).
+constexpr int RS_THREADS = 256, RS_ITEMS = 16, RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+__global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(
+    const unsigned long long* __restrict__ keys, int64_t N, int shift, uint32_t* __restrict__ hist,
+    int64_t tiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
+        int64_t idx = base + i;
+        if (idx < N) atomicAdd(&h[(unsigned)(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(
+    const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
+    unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, int64_t N, int shift,
+    const uint32_t* __restrict__ offsets, int64_t tiles) {
+    __shared__ uint32_t cnt[RS_WARPS][256];
+    __shared__ uint32_t tile_off[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    tile_off[threadIdx.x] = offsets[(int64_t)threadIdx.x * tiles + blockIdx.x];
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + warp * (RS_ITEMS * 32);
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long k[RS_ITEMS];
+    uint32_t local[RS_ITEMS];
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; ++it) {
+        int64_t idx = wbase + it * 32 + lane;
+        bool valid = idx < N;
+        k[it] = valid ? kin[idx] : 0ull;
+        unsigned d = (unsigned)(k[it] >> shift) & 255u;
+        unsigned peers = __ballot_sync(FULL, valid);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            unsigned bb = __ballot_sync(FULL, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
+        int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (valid && lane == leader) {
+            old = cnt[warp][d];
+            cnt[warp][d] = old + __popc(peers);
+        }
+        old = __shfl_sync(FULL, old, leader < 0 ? 0 : leader);
+        local[it] = old + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    {   // per digit: exclusive prefix over warps
+        const int d = threadIdx.x;
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            uint32_t t = cnt[w][d];
+            cnt[w][d] = s + tile_off[d];
+            s += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; ++it) {
+        int64_t idx = wbase + it * 32 + lane;
+        if (idx < N) {
+            unsigned d = (unsigned)(k[it] >> shift) & 255u;
+            uint32_t pos = cnt[warp][d] + local[it];
+            kout[pos] = k[it];
+            vout[pos] = vin[idx];
+        }
+    }
+}
+
+// ============================================================== leaf formation
+__device__ __forceinline__ int lcp_bits(unsigned long long a, unsigned long long b, int keybits) {
+    int l = (a == b) ? 64 : __clzll((long long)(a ^ b));
+    return l < keybits ? l : keybits;
+}
+
+// c[i] = common prefix of keys i-1, i (c[0] = 0); a[j] = common prefix of keys
+// j and j+L (the whole window j..j+L shares it, the keys being sorted).
+__global__ void lf_lcp_kernel(const unsigned long long* __restrict__ keys, int64_t N, int64_t L,
+                              int keybits, uint8_t* __restrict__ c, uint8_t* __restrict__ a) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long ki = keys[i];
+        c[i] = (uint8_t)(i == 0 ? 0 : lcp_bits(keys[i - 1], ki, keybits));
+        if (i + L < N) a[i] = (uint8_t)lcp_bits(ki, keys[i + L], keybits);
+    }
+}
+
+// prefix max P and suffix max S of a[] inside consecutive blocks of L entries
+// (van Herk / Gil-Werman sliding-window maximum)
+constexpr int LF_THREADS = 256, LF_ITEMS = 8, LF_CHUNK = LF_THREADS * LF_ITEMS;
+
+__global__ void __launch_bounds__(LF_THREADS) lf_blockmax_kernel(const uint8_t* __restrict__ a,
+                                                                  int64_t NA, int64_t L,
+                                                                  uint8_t* __restrict__ P,
+                                                                  uint8_t* __restrict__ S) {
+    __shared__ uint32_t scratch[32];
+    for (int64_t blk = blockIdx.x; blk * L < NA; blk += gridDim.x) {
+        const int64_t b0 = blk * L, b1 = std::min(b0 + L, NA);
+        uint32_t carry = 0;
+        for (int64_t c0 = b0; c0 < b1; c0 += LF_CHUNK) {
+            const int64_t t0 = c0 + (int64_t)threadIdx.x * LF_ITEMS;
+            uint32_t run[LF_ITEMS];
+            uint32_t m = 0;
+#pragma unroll
+            for (int j = 0; j < LF_ITEMS; ++j) {
+                if (t0 + j < b1) m = max(m, (uint32_t)a[t0 + j]);
+                run[j] = m;
+            }
+            uint32_t tot;
+            uint32_t before = block_excl_scan<uint32_t>(m, 0u, OpMax<uint32_t>(), scratch, &tot);
+#pragma unroll
+            for (int j = 0; j < LF_ITEMS; ++j)
+                if (t0 + j < b1) P[t0 + j] = (uint8_t)max(carry, max(before, run[j]));
+            carry = max(carry, tot);
+        }
+        carry = 0;
+        for (int64_t c1 = b1; c1 > b0; c1 -= LF_CHUNK) {
+            // element e = c1 - 1 - (thread * ITEMS + j), walking right to left
+            const int64_t t1 = c1 - 1 - (int64_t)threadIdx.x * LF_ITEMS;
+            uint32_t run[LF_ITEMS];
+            uint32_t m = 0;
+#pragma unroll
+            for (int j = 0; j < LF_ITEMS; ++j) {
+                int64_t e = t1 - j;
+                if (e >= b0 && e >= c1 - LF_CHUNK) m = max(m, (uint32_t)a[e]);
+                run[j] = m;
+            }
+            uint32_t tot;
+            uint32_t before = block_excl_scan<uint32_t>(m, 0u, OpMax<uint32_t>(), scratch, &tot);
+#pragma unroll
+            for (int j = 0; j < LF_ITEMS; ++j) {
+                int64_t e = t1 - j;
+                if (e >= b0 && e >= c1 - LF_CHUNK) S[e] = (uint8_t)max(carry, max(before, run[j]));
+            }
+            carry = max(carry, tot);
+        }
+    }
+}
+
+// A boundary (new leaf) starts at position i when the node that holds both
+// i-1 and i splits: always at the root (common prefix < 16 bits); below the
+// root when that node, the run of keys sharing c[i] bits around i, holds more
+// than L series, i.e. some window of L+1 consecutive keys containing i-1 and
+// i shares c[i] bits: max(a[i-L .. i-1]) >= c[i].
+__global__ void lf_flags_kernel(const uint8_t* __restrict__ c, const uint8_t* __restrict__ P,
+                                const uint8_t* __restrict__ S, int64_t N, int64_t L, int keybits,
+                                uint32_t* __restrict__ flags) {
+    const int64_t NA = N > L ? N - L : 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t f;
+        if (i == 0) {
+            f = 1;
+        } else {
+            int ci = c[i];
+            if (ci < ROOT_BITS) {
+                f = 1;
+            } else if (ci >= keybits) {
+                f = 0;
+            } else {
+                int64_t lo = i - L > 0 ? i - L : 0;
+                int64_t hi = std::min(i - 1, NA - 1);
+                int M = 0;
+                if (NA > 0 && lo <= hi) {
+                    if (lo / L == hi / L)
+                        M = (lo % L == 0) ? P[hi] : S[lo];
+                    else
+                        M = max(S[lo], P[hi]);
+                }
+                f = M >= ci ? 1u : 0u;
+            }
+        }
+        flags[i] = f;
+    }
+}
+
+__global__ void lf_compact_kernel(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
+                                  int64_t N, uint32_t* __restrict__ starts, uint32_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flags[i]) starts[pos[i]] = (uint32_t)i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) starts[count] = (uint32_t)N;
+}
+
+// leaves over capacity (only runs of identical keys) are cut into pieces of L
+__global__ void lf_pieces_kernel(const uint32_t* __restrict__ starts, uint32_t L0, int64_t L,
+                                 uint32_t* __restrict__ pieces) {
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < L0;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        int64_t sz = (int64_t)starts[l + 1] - starts[l];
+        pieces[l] = (uint32_t)((sz + L - 1) / L);
+    }
+}
+
+__global__ void lf_expand_kernel(const uint32_t* __restrict__ starts, const uint32_t* __restrict__ poff,
+                                 uint32_t L0, int64_t L, int64_t N, uint32_t* __restrict__ leaf_begin,
+                                 uint32_t nleaves) {
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < L0;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s0 = starts[l], s1 = starts[l + 1];
+        uint32_t o = poff[l];
+        for (int64_t p = s0; p < s1; p += L) leaf_begin[o++] = (uint32_t)p;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) leaf_begin[nleaves] = (uint32_t)N;
+}
+
+// ============================================================== permute, envelopes
+// rows, SAX words and original ids gathered into leaf order; one warp per row
+__global__ void __launch_bounds__(256) permute_kernel(const float4* __restrict__ x, int n4,
+                                                      const uint32_t* __restrict__ ids, int64_t N,
+                                                      float4* __restrict__ xp,
+                                                      const uint4* __restrict__ sax_in,
+                                                      uint4* __restrict__ sax_out,
+                                                      uint32_t* __restrict__ orig) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = gw; row < N; row += nw) {
+        const uint32_t src = ids[row];
+        const float4* s = x + (int64_t)src * n4;
+        float4* d = xp + row * n4;
+        for (int j = lane; j < n4; j += 64) {
+            float4 v0 = ld_stream(s + j);
+            float4 v1;
+            bool two = j + 32 < n4;
+            if (two) v1 = ld_stream(s + j + 32);
+            st_stream(d + j, v0);
+            if (two) st_stream(d + j + 32, v1);
+        }
+        if (lane == 0) {
+            sax_out[row] = sax_in[src];
+            orig[row] = src;
+        }
+    }
+}
+
+__device__ __forceinline__ uint4 vmin4(uint4 a, uint4 b) {
+    return make_uint4(__vminu4(a.x, b.x), __vminu4(a.y, b.y), __vminu4(a.z, b.z), __vminu4(a.w, b.w));
+}
+__device__ __forceinline__ uint4 vmax4(uint4 a, uint4 b) {
+    return make_uint4(__vmaxu4(a.x, b.x), __vmaxu4(a.y, b.y), __vmaxu4(a.z, b.z), __vmaxu4(a.w, b.w));
+}
+__device__ __forceinline__ uint4 shfl_xor_u4(uint4 v, int off) {
+    return make_uint4(__shfl_xor_sync(FULL, v.x, off), __shfl_xor_sync(FULL, v.y, off),
+                      __shfl_xor_sync(FULL, v.z, off), __shfl_xor_sync(FULL, v.w, off));
+}
+
+// one warp per leaf: byte-wise min and max of the members' symbols
+__global__ void __launch_bounds__(256) envelope_kernel(const uint4* __restrict__ sax,
+                                                       const uint32_t* __restrict__ leaf_begin,
+                                                       int64_t L,
+                                                       const unsigned long long* __restrict__ keys,
+                                                       uint4* __restrict__ env,
+                                                       unsigned long long* __restrict__ leaf_key,
+                                                       uint32_t* __restrict__ max_leaf) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t l = gw; l < L; l += nw) {
+        const uint32_t b = leaf_begin[l], e = leaf_begin[l + 1];
+        uint4 mn = make_uint4(FULL, FULL, FULL, FULL), mx = make_uint4(0, 0, 0, 0);
+        for (uint32_t r = b + lane; r < e; r += 32) {
+            uint4 s = sax[r];
+            mn = vmin4(mn, s);
+            mx = vmax4(mx, s);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            mn = vmin4(mn, shfl_xor_u4(mn, off));
+            mx = vmax4(mx, shfl_xor_u4(mx, off));
+        }
+        if (lane == 0) {
+            env[2 * l] = mn;
+            env[2 * l + 1] = mx;
+            leaf_key[l] = keys[b];
+            atomicMax(max_leaf, e - b);
+        }
+    }
+}
+
+// ============================================================== orchestration
+namespace {
+
+struct TempPool {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    template <typename T>
+    T* get(size_t count) {
+        void* p = dev_alloc(std::max<size_t>(count, 1) * sizeof(T), st);
+        ptrs.push_back(p);
+        return static_cast<T*>(p);
+    }
+    void release(void* p) {
+        auto it = std::find(ptrs.begin(), ptrs.end(), p);
+        if (it != ptrs.end()) {
+            dev_free(p, st);
+            ptrs.erase(it);
+        }
+    }
+    ~TempPool() {
+        for (void* p : ptrs) dev_free(p, st);
+    }
+};
+
+inline unsigned grid_for(int64_t work, int per_block, int num_sms, int max_per_sm = 16) {
+    int64_t b = (work + per_block - 1) / per_block;
+    int64_t cap = (int64_t)num_sms * max_per_sm;
+    return (unsigned)std::max<int64_t>(1, std::min(b, cap));
+}
+
+}  // namespace
+
+void free_index_arrays(isax_index* ix, cudaStream_t st);
+void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st);
+
+isax_index* build_index_impl(const float* series, int64_t N, int n, int card, int leaf_size,
+                             uint32_t mem_flags, cudaStream_t st) {
+    int dev = 0;
+    ISAX_CUDA_TRY(cudaGetDevice(&dev));
+    int num_sms = 0;
+    ISAX_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+
+    isax_index* ix = new isax_index();
+    ix->device = dev;
+    ix->num_sms = num_sms;
+    ix->mu = new std::mutex();
+    try {
+        int cbits = 0;
+        while ((1 << cbits) < card) ++cbits;
+        const int keybits = 16 * std::min(cbits, 4);
+        TempPool tmp{st, {}};
+
+        const float* xin = series;
+        if (!(mem_flags & ISAX_MEM_INPUT_DEVICE)) {
+            float* xd = tmp.get<float>((size_t)N * n);
+            ISAX_CUDA_TRY(cudaMemcpyAsync(xd, series, (size_t)N * n * sizeof(float),
+                                          cudaMemcpyHostToDevice, st));
+            xin = xd;
+        }
+
+        // breakpoints + summaries
+        ix->bp = static_cast<float*>(dev_alloc((card + 1) * sizeof(float), st));
+        launch_breakpoints(card, ix->bp, st);
+        uint4* sax_tmp = tmp.get<uint4>(N);
+        unsigned long long* kA = tmp.get<unsigned long long>(N);
+        unsigned long long* kB = tmp.get<unsigned long long>(N);
+        uint32_t* vA = tmp.get<uint32_t>(N);
+        uint32_t* vB = tmp.get<uint32_t>(N);
+        unsigned* misc = tmp.get<unsigned>(4);  // maxabs bits, nonfinite, max_leaf
+        ISAX_CUDA_TRY(cudaMemsetAsync(misc, 0, 4 * sizeof(unsigned), st));
+        launch_summarize(xin, N, n, card, ix->bp, sax_tmp, kA, vA, nullptr, misc, misc + 1, num_sms,
+                         st);
+
+        // radix sort of (key, row): LSD over the key's meaningful bits
+        {
+            const int64_t tiles = (N + RS_TILE - 1) / RS_TILE;
+            uint32_t* hist = tmp.get<uint32_t>((size_t)256 * tiles);
+            uint32_t* sums = tmp.get<uint32_t>(scan_sums_len(256 * tiles));
+            for (int pass = 0; pass < keybits / 8; ++pass) {
+                const int shift = 64 - keybits + 8 * pass;
+                rs_hist_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(kA, N, shift, hist, tiles);
+                exclusive_scan(hist, hist, 256 * tiles, sums, st);
+                rs_scatter_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(kA, vA, kB, vB, N, shift,
+                                                                          hist, tiles);
+                ISAX_CUDA_TRY(cudaGetLastError());
+                std::swap(kA, kB);
+                std::swap(vA, vB);
+            }
+            tmp.release(hist);
+            tmp.release(sums);
+        }
+
+        // leaves
+        const int64_t Lc = leaf_size;
+        const int64_t NA = N > Lc ? N - Lc : 0;
+        uint8_t* c = tmp.get<uint8_t>(N);
+        uint8_t* a = tmp.get<uint8_t>(NA);
+        uint8_t* P = tmp.get<uint8_t>(NA);
+        uint8_t* S = tmp.get<uint8_t>(NA);
+        uint32_t* flags = tmp.get<uint32_t>(N);
+        uint32_t* pos = tmp.get<uint32_t>(N);
+        uint32_t* sums = tmp.get<uint32_t>(scan_sums_len(N));
+        lf_lcp_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(kA, N, Lc, keybits, c, a);
+        if (NA > 0) {
+            int64_t nblk = (NA + Lc - 1) / Lc;
+            lf_blockmax_kernel<<<(unsigned)std::min<int64_t>(nblk, (int64_t)num_sms * 16), LF_THREADS,
+                                 0, st>>>(a, NA, Lc, P, S);
+        }
+        lf_flags_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(c, P, S, N, Lc, keybits, flags);
+        exclusive_scan(flags, pos, N, sums, st);
+        ISAX_CUDA_TRY(cudaGetLastError());
+        uint32_t L0 = 0;
+        ISAX_CUDA_TRY(cudaMemcpyAsync(&L0, sums + (scan_sums_len(N) - 1), sizeof(uint32_t),
+                                      cudaMemcpyDeviceToHost, st));
+        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+        uint32_t* starts = tmp.get<uint32_t>((size_t)L0 + 1);
+        lf_compact_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(flags, pos, N, starts, L0);
+        uint32_t* pieces = tmp.get<uint32_t>(L0);
+        uint32_t* poff = tmp.get<uint32_t>(L0);
+        uint32_t* psums = tmp.get<uint32_t>(scan_sums_len(L0));
+        lf_pieces_kernel<<<grid_for(L0, 256, num_sms), 256, 0, st>>>(starts, L0, Lc, pieces);
+        exclusive_scan(pieces, poff, L0, psums, st);
+        uint32_t L = 0;
+        ISAX_CUDA_TRY(cudaMemcpyAsync(&L, psums + (scan_sums_len(L0) - 1), sizeof(uint32_t),
+                                      cudaMemcpyDeviceToHost, st));
+        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+        ix->leaf_begin = static_cast<uint32_t*>(dev_alloc(((size_t)L + 1) * sizeof(uint32_t), st));
+        lf_expand_kernel<<<grid_for(L0, 256, num_sms), 256, 0, st>>>(starts, poff, L0, Lc, N,
+                                                                      ix->leaf_begin, L);
+        ISAX_CUDA_TRY(cudaGetLastError());
+        for (void* p : {(void*)c, (void*)a, (void*)P, (void*)S, (void*)flags, (void*)pos,
+                        (void*)sums, (void*)starts, (void*)pieces, (void*)poff, (void*)psums})
+            tmp.release(p);
+
+        // permute rows and SAX words into leaf order
+        ix->x = static_cast<float*>(dev_alloc((size_t)N * n * sizeof(float), st));
+        ix->sax = static_cast<uint4*>(dev_alloc((size_t)N * sizeof(uint4), st));
+        ix->orig = static_cast<uint32_t*>(dev_alloc((size_t)N * sizeof(uint32_t), st));
+        permute_kernel<<<grid_for(N, 8, num_sms, 8), 256, 0, st>>>(
+            reinterpret_cast<const float4*>(xin), n / 4, vA, N, reinterpret_cast<float4*>(ix->x),
+            sax_tmp, ix->sax, ix->orig);
+        ISAX_CUDA_TRY(cudaGetLastError());
+
+        // envelopes
+        ix->env = static_cast<uint4*>(dev_alloc((size_t)L * 2 * sizeof(uint4), st));
+        ix->leaf_key = static_cast<unsigned long long*>(
+            dev_alloc((size_t)L * sizeof(unsigned long long), st));
+        envelope_kernel<<<grid_for(L, 8, num_sms, 8), 256, 0, st>>>(ix->sax, ix->leaf_begin, L, kA,
+                                                                     ix->env, ix->leaf_key, misc + 2);
+        ISAX_CUDA_TRY(cudaGetLastError());
+
+        unsigned hm[4];
+        ISAX_CUDA_TRY(cudaMemcpyAsync(hm, misc, sizeof hm, cudaMemcpyDeviceToHost, st));
+        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hm[1]) throw Error{ISAX_ERR_INVALID_ARG, "series contains a non-finite value"};
+        float maxabs;
+        memcpy(&maxabs, &hm[0], sizeof maxabs);
+
+        DevIndex& d = ix->d;
+        d.N = N;
+        d.n = n;
+        d.card = card;
+        d.cbits = cbits;
+        d.keybits = keybits;
+        d.leaf_size = leaf_size;
+        d.L = L;
+        d.x = ix->x;
+        d.sax = ix->sax;
+        d.orig = ix->orig;
+        d.leaf_begin = ix->leaf_begin;
+        d.env = ix->env;
+        d.leaf_key = ix->leaf_key;
+        d.bp = ix->bp;
+        d.maxabs = maxabs;
+        ix->max_leaf = (int32_t)hm[2];
+        ix->bytes = (int64_t)N * n * 4 + N * 16 + N * 4 + ((int64_t)L + 1) * 4 + (int64_t)L * 40 +
+                    (card + 1) * 4;
+        alloc_query_scratch(ix, (uint32_t)std::min<int64_t>(N, 1 << 20), st);
+    } catch (...) {
+        free_index_arrays(ix, st);
+        delete static_cast<std::mutex*>(ix->mu);
+        delete ix;
+        throw;
+    }
+    return ix;
+}
+
+// ---------------------------------------------------------------- summarize alone
+void summarize_impl(const float* series, int64_t N, int n, int card, uint32_t mem_flags,
+                    uint8_t* out_sax, float* out_paa, cudaStream_t st) {
+    int dev = 0, num_sms = 0;
+    ISAX_CUDA_TRY(cudaGetDevice(&dev));
+    ISAX_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+    TempPool tmp{st, {}};
+    const float* xin = series;
+    if (!(mem_flags & ISAX_MEM_INPUT_DEVICE)) {
+        float* xd = tmp.get<float>((size_t)N * n);
+        ISAX_CUDA_TRY(cudaMemcpyAsync(xd, series, (size_t)N * n * sizeof(float),
+                                      cudaMemcpyHostToDevice, st));
+        xin = xd;
+    }
+    const bool out_dev = mem_flags & ISAX_MEM_OUTPUT_DEVICE;
+    float* bp = tmp.get<float>(card + 1);
+    launch_breakpoints(card, bp, st);
+    uint4* sax = (out_dev && out_sax) ? reinterpret_cast<uint4*>(out_sax) : tmp.get<uint4>(N);
+    float* paa = nullptr;
+    if (out_paa) paa = out_dev ? out_paa : tmp.get<float>((size_t)N * W);
+    unsigned* misc = tmp.get<unsigned>(2);
+    ISAX_CUDA_TRY(cudaMemsetAsync(misc, 0, 2 * sizeof(unsigned), st));
+    launch_summarize(xin, N, n, card, bp, sax, nullptr, nullptr, paa, misc, misc + 1, num_sms, st);
+    if (!out_dev) {
+        if (out_sax)
+            ISAX_CUDA_TRY(cudaMemcpyAsync(out_sax, sax, (size_t)N * W, cudaMemcpyDeviceToHost, st));
+        if (out_paa)
+            ISAX_CUDA_TRY(cudaMemcpyAsync(out_paa, paa, (size_t)N * W * sizeof(float),
+                                          cudaMemcpyDeviceToHost, st));
+    }
+    unsigned hm[2];
+    ISAX_CUDA_TRY(cudaMemcpyAsync(hm, misc, sizeof hm, cudaMemcpyDeviceToHost, st));
+    ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hm[1]) throw Error{ISAX_ERR_INVALID_ARG, "series contains a non-finite value"};
+}
+
+}  // namespace isax

@@ -1,0 +1,139 @@
+// isax_common.cuh - shared definitions of the sm_103a iSAX k-NN library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/isax.h"
+
+namespace isax {
+
+constexpr int W = ISAX_W;          // segments (the paper fixes w = 16)
+constexpr int MAX_CARD = 256;      // 8-bit symbols
+constexpr int MAX_K = ISAX_MAX_K;
+constexpr int MAX_LEN = ISAX_MAX_LEN;
+constexpr int ROOT_BITS = W;       // root key: first bit of each of the 16 segments
+
+constexpr int NBINS = 256;         // leaf ordering bins (lower bound / threshold)
+constexpr int REFINE_CHUNK = 2048; // rows of a leaf bounded per scan round
+constexpr uint64_t EMPTY_SLOT = ~0ull;
+
+// ---------------------------------------------------------------- errors
+struct Error {
+    isax_status st;
+    std::string msg;
+};
+
+void set_error(isax_status st, const std::string& msg);
+
+#define ISAX_CUDA_TRY(expr)                                                         \
+    do {                                                                            \
+        cudaError_t e_ = (expr);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            throw ::isax::Error{ISAX_ERR_CUDA, std::string(#expr) + ": " +          \
+                                                   cudaGetErrorString(e_)};          \
+    } while (0)
+
+// ---------------------------------------------------------------- allocator
+void* dev_alloc(size_t bytes, cudaStream_t st);  // throws Error{OOM}
+void dev_free(void* p, cudaStream_t st);
+
+// ---------------------------------------------------------------- index
+// Device view of an index, passed by value to kernels.
+struct DevIndex {
+    int64_t N;
+    int32_t n, card, cbits, keybits, leaf_size;
+    int64_t L;                    // leaves
+    const float* x;               // [N][n] rows in leaf order
+    const uint4* sax;             // [N] 16 symbols per series, leaf order
+    const uint32_t* orig;         // [N] original row of each position
+    const uint32_t* leaf_begin;   // [L+1]
+    const uint4* env;             // [L][2]: min symbols, max symbols
+    const unsigned long long* leaf_key;  // [L] key of the first series of each leaf
+    const float* bp;              // [card+1] breakpoints: -inf, beta_1 .. beta_{card-1}, +inf
+    float maxabs;                 // max |x| over the collection
+};
+
+// Per-query control block (device).
+struct QCtl {
+    unsigned long long qkey;
+    int32_t descent_leaf;
+    int32_t approx_leaf;   // approximate answer: leaves [approx_leaf, approx_end)
+    int32_t approx_end;
+    uint8_t qsym[16];      // query symbols
+    uint32_t work_count;   // queued leaves
+    uint32_t work_next;    // Fetch&Inc claim counter
+    uint32_t cand_count;   // candidate appends attempted (may exceed capacity)
+    uint32_t window;       // candidates re-ranked in FP64
+    uint32_t flags;        // QF_* bits
+    double E;              // sqrt(n) * (eps_x + eps_q): PAA rounding slack
+    double delta;          // relative error bound of an fp32 squared distance
+    unsigned long long series_lb, series_refined, leaves_scanned, leaves_queued;
+};
+
+enum : uint32_t {
+    QF_NONFINITE = 1u,  // query holds NaN or Inf
+    QF_OVERFLOW = 2u,   // candidate buffer overflowed: rerun with more room
+    QF_SHORT = 4u,      // fewer than k candidates reached the end (internal error)
+};
+
+// Device scratch of one in-flight query.
+struct QueryScratch {
+    float* q;                      // [n]
+    float* table;                  // [16][card] lower-bound table
+    float* leaf_lb;                // [L]
+    uint32_t* work;                // [L] queued leaves, ordered by bin
+    uint32_t* bin_count;           // [NBINS]
+    uint32_t* bin_cursor;          // [NBINS]
+    unsigned long long* topk;      // [MAX_K] packed (fp32 d2 bits << 32 | orig)
+    unsigned long long* cand_key;  // [cap]
+    uint32_t* cand_pos;            // [cap]
+    uint32_t cand_cap;
+    QCtl* ctl;
+    int64_t* out_idx;              // [MAX_K]
+    float* out_dist;               // [MAX_K]
+};
+
+}  // namespace isax
+
+struct isax_index;
+
+namespace isax {
+
+// Host-side entry points (defined in the .cu files); they throw Error.
+isax_index* build_index_impl(const float* series, int64_t N, int n, int card, int leaf_size,
+                             uint32_t mem_flags, cudaStream_t st);
+void summarize_impl(const float* series, int64_t N, int n, int card, uint32_t mem_flags,
+                    uint8_t* out_sax, float* out_paa, cudaStream_t st);
+void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st);
+void free_index_arrays(isax_index* ix, cudaStream_t st);
+void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st);
+void launch_breakpoints(int card, float* bp, cudaStream_t st);
+void launch_summarize(const float* x, int64_t N, int n, int card, const float* bp,
+                      uint4* sax, unsigned long long* keys, uint32_t* ids, float* paa_out,
+                      unsigned int* maxabs_bits, unsigned int* nonfinite, int num_sms,
+                      cudaStream_t st);
+
+}  // namespace isax
+
+// the opaque handle of the C ABI
+struct isax_index {
+    int device;
+    int num_sms;
+    isax::DevIndex d;
+    int32_t max_leaf;
+    int64_t bytes;
+    // owned device arrays
+    float* x;
+    uint4* sax;
+    uint32_t* orig;
+    uint32_t* leaf_begin;
+    uint4* env;
+    unsigned long long* leaf_key;
+    float* bp;
+    // query scratch (one in-flight query)
+    isax::QueryScratch qs;
+    void* mu;  // std::mutex*
+};

@@ -1,0 +1,102 @@
+// isax_kernels_util.cuh - small device helpers shared by the library's kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace isax {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// streaming 16-byte load that does not allocate in L1 (data read once)
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint4 ld_stream_u4(const uint4* p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// streaming store (evict-first)
+__device__ __forceinline__ void st_stream(float4* p, float4 v) {
+    asm volatile("st.global.cs.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+    return *(volatile const unsigned long long*)p;
+}
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+    return *(volatile const uint32_t*)p;
+}
+
+// symbol of v: number of breakpoints beta_t <= v, by binary search over
+// bp[0..card] = {-inf, beta_1, ..., beta_{card-1}, +inf} (bp in shared memory)
+__device__ __forceinline__ int symbol_of(float v, const float* bp, int card) {
+    int s = 0;
+    for (int step = card >> 1; step > 0; step >>= 1)
+        if (bp[s + step] <= v) s += step;
+    return s;
+}
+
+template <typename T>
+struct OpAdd {
+    __device__ __forceinline__ T operator()(T a, T b) const { return a + b; }
+};
+template <typename T>
+struct OpMax {
+    __device__ __forceinline__ T operator()(T a, T b) const { return a > b ? a : b; }
+};
+
+// inclusive warp scan
+template <typename T, typename Op>
+__device__ __forceinline__ T warp_incl_scan(T v, Op op) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        T t = __shfl_up_sync(FULL, v, off);
+        if (lane >= off) v = op(v, t);
+    }
+    return v;
+}
+
+// exclusive block scan (blockDim.x a multiple of 32, <= 1024); `scratch` holds
+// 32 elements of shared memory; returns the exclusive prefix and the total.
+// Must be called by every thread; ends with a __syncthreads.
+template <typename T, typename Op>
+__device__ __forceinline__ T block_excl_scan(T v, T identity, Op op, T* scratch, T* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T inc = warp_incl_scan(v, op);
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nw ? scratch[lane] : identity;
+        w = warp_incl_scan(w, op);
+        scratch[lane] = w;
+    }
+    __syncthreads();
+    T before = warp > 0 ? scratch[warp - 1] : identity;
+    T excl_in_warp = __shfl_up_sync(FULL, inc, 1);
+    if (lane == 0) excl_in_warp = identity;
+    T res = op(before, excl_in_warp);
+    *total = scratch[nw - 1];
+    __syncthreads();
+    return res;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+}  // namespace isax

@@ -1,0 +1,660 @@
+// isax_query.cu - exact k-NN query answering on the GPU, following MESSI's
+// query strategy (Section III, MESSI Approach; lower-bound and real-distance
+// calculations are its two hot loops):
+//
+//   q_prep        query PAA, SAX symbols and key; the lower-bound table
+//                 T[i][s] = (n/w) dist(qpaa_i, region s)^2 in fp32; the leaf the
+//                 query's key descends to (the approximate-answer leaf).
+//   q_approx      real distances to every series of that leaf -> first BSF.
+//   q_leaf_lb     envelope lower bound of every leaf; leaves that the BSF does
+//                 not prune are counted into bins of bound / BSF.
+//   q_leaf_scatter  the unpruned leaves listed bin by bin: a work list in
+//                 ascending lower-bound order (MESSI's priority queues).
+//   q_scan_refine persistent CTAs claim leaves from the list with Fetch&Inc; a
+//                 claimed leaf whose bound now exceeds the BSF is skipped; else
+//                 16-byte SAX words are bounded against the table in shared
+//                 memory, survivors compacted with warp ballots, and refined
+//                 by one warp per row with early abandoning; the k best so far
+//                 live in a sorted array updated by an atomicMin cascade.
+//   q_finalize    candidates within fp32 error of the k-th best re-ranked in
+//                 FP64 (ties by lower row), distances rounded to fp32.
+//
+// Exactness.  Bounds are pruned only with the slack of a rigorous fp32 error
+// analysis: a series is pruned only if its bound proves its exact distance
+// exceeds (1 + 5 delta) times the current k-th best, where delta bounds the
+// relative error of an fp32 squared distance and E bounds the PAA rounding
+// error.  Every series whose fp32 distance lies within (1 + 3 delta) of the
+// final k-th best is kept as a candidate and re-ranked in FP64 with the same
+// left-to-right sum as the definition, so the indices equal the brute-force
+// answer's.
+#include <algorithm>
+#include <mutex>
+
+#include "isax_common.cuh"
+#include "isax_kernels_util.cuh"
+
+namespace isax {
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ unsigned long long pack_key(float d2, uint32_t orig) {
+    return ((unsigned long long)__float_as_uint(d2) << 32) | orig;
+}
+__device__ __forceinline__ float key_d2(unsigned long long key) {
+    return __uint_as_float((uint32_t)(key >> 32));
+}
+
+// squared lower-bound threshold: prune iff bound > this (see file comment)
+__device__ float lb_threshold(unsigned long long kth, double delta, double E) {
+    if (kth == EMPTY_SLOT) return INFINITY;
+    double t = (double)key_d2(kth);
+    double r = sqrt(t * (1.0 + 5.0 * delta)) + E;
+    double lb = r * r * (1.0 + 24.0 * 0x1p-24) * (1.0 + 1e-12);
+    return __double2float_ru(lb);
+}
+
+__device__ __forceinline__ int bin_of(float lb, float thr) {
+    if (!(thr > 0.0f) || isinf(thr)) return 0;
+    int b = (int)(sqrtf(lb / thr) * (float)NBINS);
+    return b < 0 ? 0 : (b >= NBINS ? NBINS - 1 : b);
+}
+
+// insert key into the ascending array slots[0..k): each step puts the smaller
+// value in the slot and carries the larger one down; values only decrease, so
+// after all concurrent cascades the array holds the k smallest keys, sorted.
+__device__ void topk_insert(unsigned long long* slots, int k, unsigned long long key) {
+    int j = 0;
+    while (j < k && ld_volatile_u64(&slots[j]) <= key) ++j;
+    for (; j < k; ++j) {
+        unsigned long long old = atomicMin(&slots[j], key);
+        if (old == EMPTY_SLOT) return;
+        if (old > key) key = old;
+    }
+}
+
+// one refined series (by one thread): update the k best, keep as candidate
+__device__ void consider(const QueryScratch& s, int k, unsigned long long key, uint32_t pos,
+                         double delta) {
+    unsigned long long kth = ld_volatile_u64(&s.topk[k - 1]);
+    if (key < kth) {
+        topk_insert(s.topk, k, key);
+        kth = ld_volatile_u64(&s.topk[k - 1]);
+    }
+    bool keep = kth == EMPTY_SLOT ||
+                (double)key_d2(key) <= (double)key_d2(kth) * (1.0 + 3.0 * delta);
+    if (keep) {
+        uint32_t i = atomicAdd(&s.ctl->cand_count, 1u);
+        if (i < s.cand_cap) {
+            s.cand_key[i] = key;
+            s.cand_pos[i] = pos;
+        }
+    }
+}
+
+// abandon a partial sum only above (1 + 8 delta) * k-th best: the full fp32
+// distance then exceeds the candidate window (1 + 3 delta) for sure
+__device__ __forceinline__ float abandon_limit(unsigned long long kth, double delta) {
+    if (kth == EMPTY_SLOT) return INFINITY;
+    return __double2float_ru((double)key_d2(kth) * (1.0 + 8.0 * delta));
+}
+
+// squared distance of a row to the query, one warp, fixed order: every lane
+// sums its elements left to right with fma, then a butterfly over lanes.
+// n = 128 * NV: lane holds float4 p*32+lane.  Early abandon every 256 floats.
+template <int NV>
+__device__ __forceinline__ float warp_d2_vec(const float4* __restrict__ xr, const float4 (&qv)[NV],
+                                             float abandon, bool& abandoned) {
+    const int lane = threadIdx.x & 31;
+    float acc = 0.0f;
+    abandoned = false;
+    if constexpr (NV <= 2) {
+        float4 v[NV];
+#pragma unroll
+        for (int p = 0; p < NV; ++p) v[p] = ld_stream(xr + p * 32 + lane);
+#pragma unroll
+        for (int p = 0; p < NV; ++p) {
+            float d;
+            d = v[p].x - qv[p].x; acc = fmaf(d, d, acc);
+            d = v[p].y - qv[p].y; acc = fmaf(d, d, acc);
+            d = v[p].z - qv[p].z; acc = fmaf(d, d, acc);
+            d = v[p].w - qv[p].w; acc = fmaf(d, d, acc);
+        }
+        return warp_sum_f(acc);
+    } else {
+#pragma unroll
+    for (int p = 0; p < NV; p += 2) {
+        float4 v0 = ld_stream(xr + p * 32 + lane);
+        float4 v1 = ld_stream(xr + (p + 1) * 32 + lane);
+        float d;
+        d = v0.x - qv[p].x; acc = fmaf(d, d, acc);
+        d = v0.y - qv[p].y; acc = fmaf(d, d, acc);
+        d = v0.z - qv[p].z; acc = fmaf(d, d, acc);
+        d = v0.w - qv[p].w; acc = fmaf(d, d, acc);
+        d = v1.x - qv[p + 1].x; acc = fmaf(d, d, acc);
+        d = v1.y - qv[p + 1].y; acc = fmaf(d, d, acc);
+        d = v1.z - qv[p + 1].z; acc = fmaf(d, d, acc);
+        d = v1.w - qv[p + 1].w; acc = fmaf(d, d, acc);
+        if (p + 2 < NV) {
+            float part = warp_sum_f(acc);
+            if (part > abandon) {
+                abandoned = true;
+                return part;
+            }
+        }
+    }
+    return warp_sum_f(acc);
+    }
+}
+
+// any n: lane sums elements lane, lane+32, ...; abandon check every 8 full rounds
+__device__ __forceinline__ float warp_d2_gen(const float* __restrict__ xr, const float* __restrict__ q,
+                                             int n, float abandon, bool& abandoned) {
+    const int lane = threadIdx.x & 31;
+    float acc = 0.0f;
+    abandoned = false;
+    for (int t = 0; 32 * t < n; ++t) {
+        int j = 32 * t + lane;
+        if (j < n) {
+            float d = xr[j] - __ldg(q + j);
+            acc = fmaf(d, d, acc);
+        }
+        if ((t & 7) == 7 && 32 * (t + 1) < n) {
+            float part = warp_sum_f(acc);
+            if (part > abandon) {
+                abandoned = true;
+                return part;
+            }
+        }
+    }
+    return warp_sum_f(acc);
+}
+
+template <int NV>
+__device__ __forceinline__ float warp_d2(const DevIndex& ix, int64_t r, const float4 (&qv)[NV ? NV : 1],
+                                         const float* q, float abandon, bool& abandoned) {
+    if constexpr (NV > 0) {
+        return warp_d2_vec<NV>(reinterpret_cast<const float4*>(ix.x + r * ix.n), qv, abandon,
+                               abandoned);
+    } else {
+        return warp_d2_gen(ix.x + r * ix.n, q, ix.n, abandon, abandoned);
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ void load_q(const float* q, float4 (&qv)[NV ? NV : 1]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int p = 0; p < (NV ? NV : 1); ++p)
+        qv[p] = NV ? reinterpret_cast<const float4*>(q)[p * 32 + lane] : make_float4(0, 0, 0, 0);
+}
+
+// series lower bound: 16 table lookups summed in segment order
+__device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ tab, int card) {
+    float lb = 0.0f;
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        uint32_t s = (words[i >> 2] >> (8 * (i & 3))) & 255u;
+        lb += tab[i * card + s];
+    }
+    return lb;
+}
+
+// ---------------------------------------------------------------- q_prep
+__global__ void __launch_bounds__(256) q_prep_kernel(DevIndex ix, QueryScratch s, int k) {
+    __shared__ float bp[MAX_CARD + 1];
+    __shared__ float qpaa[W];
+    __shared__ int qsym[W];
+    __shared__ float red[32];
+    __shared__ unsigned bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = ix.n, m = n / W, card = ix.card;
+    for (int i = tid; i <= card; i += blockDim.x) bp[i] = ix.bp[i];
+    if (tid == 0) bad = 0;
+    // init per-query state
+    for (int i = tid; i < k; i += blockDim.x) s.topk[i] = EMPTY_SLOT;
+    for (int i = tid; i < NBINS; i += blockDim.x) {
+        s.bin_count[i] = 0;
+        s.bin_cursor[i] = 0;
+    }
+    float amax = 0.0f;
+    for (int j = tid; j < n; j += blockDim.x) amax = fmaxf(amax, fabsf(s.q[j]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, off));
+    if (lane == 0) red[warp] = amax;
+    __syncthreads();
+    if (tid < W) {
+        float sum = 0.0f;
+        for (int j = 0; j < m; ++j) sum += s.q[tid * m + j];
+        float p = sum / (float)m;
+        qpaa[tid] = p;
+        qsym[tid] = symbol_of(p, bp, card);
+        if (!isfinite(p)) atomicOr(&bad, 1u);
+    }
+    __syncthreads();
+    // lower-bound table
+    const float mf = (float)m;
+    for (int e = tid; e < W * card; e += blockDim.x) {
+        const int i = e / card, sym = e - i * card;
+        const float lo = bp[sym], hi = bp[sym + 1], v = qpaa[i];
+        const float d = v < lo ? lo - v : (v >= hi ? v - hi : 0.0f);
+        s.table[e] = (d * d) * mf;
+    }
+    if (tid == 0) {
+        float qmax = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) qmax = fmaxf(qmax, red[i]);
+        QCtl* c = s.ctl;
+        unsigned long long key = 0;
+        for (int pl = 0; pl < 4; ++pl) {
+            int b = ix.cbits - 1 - pl;
+            unsigned plane = 0;
+            for (int i = 0; i < W; ++i)
+                plane = (plane << 1) | (b >= 0 ? ((unsigned)(qsym[i] >> b) & 1u) : 0u);
+            key = (key << 16) | plane;
+        }
+        c->qkey = key;
+        // descent: last leaf whose first key <= query key
+        int64_t lo = 0, hi = ix.L;  // find first leaf with leaf_key > key
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (ix.leaf_key[mid] <= key)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        int64_t dl = lo > 0 ? lo - 1 : 0;
+        // approximate-answer range: that leaf, widened until it holds >= k series
+        int64_t a0 = dl, a1 = dl + 1;
+        int64_t cnt = (int64_t)ix.leaf_begin[a1] - ix.leaf_begin[a0];
+        while (cnt < k) {
+            if (a1 < ix.L) {
+                cnt += (int64_t)ix.leaf_begin[a1 + 1] - ix.leaf_begin[a1];
+                ++a1;
+            } else if (a0 > 0) {
+                --a0;
+                cnt += (int64_t)ix.leaf_begin[a0 + 1] - ix.leaf_begin[a0];
+            } else {
+                break;
+            }
+        }
+        c->descent_leaf = (int32_t)dl;
+        c->approx_leaf = (int32_t)a0;
+        c->approx_end = (int32_t)a1;
+        c->work_count = 0;
+        c->work_next = 0;
+        c->cand_count = 0;
+        c->window = 0;
+        c->flags = bad ? QF_NONFINITE : 0u;
+        const double u = 0x1p-24;
+        const double eps_x = 1.01 * (m + 1) * u * (double)ix.maxabs;
+        const double eps_q = 1.01 * (m + 1) * u * (double)qmax;
+        c->E = sqrt((double)n) * (eps_x + eps_q) * (1.0 + 1e-9);
+        c->delta = (double)((n + 31) / 32 + 16) * u;
+        c->series_lb = 0;
+        c->series_refined = 0;
+        c->leaves_scanned = 0;
+        c->leaves_queued = 0;
+        for (int i = 0; i < W; ++i) c->qsym[i] = (uint8_t)qsym[i];
+    }
+}
+
+// ---------------------------------------------------------------- q_approx
+template <int NV>
+__global__ void __launch_bounds__(256) q_approx_kernel(DevIndex ix, QueryScratch s, int k) {
+    const QCtl* c = s.ctl;
+    if (c->flags & QF_NONFINITE) return;
+    const int lane = threadIdx.x & 31;
+    float4 qv[NV ? NV : 1];
+    load_q<NV>(s.q, qv);
+    const int64_t b = ix.leaf_begin[c->approx_leaf], e = ix.leaf_begin[c->approx_end];
+    const double delta = c->delta;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long refined = 0;
+    for (int64_t r = b + gw; r < e; r += nw) {
+        bool ab;
+        float d2 = warp_d2<NV>(ix, r, qv, s.q, INFINITY, ab);
+        if (lane == 0) consider(s, k, pack_key(d2, ix.orig[r]), (uint32_t)r, delta);
+        ++refined;
+    }
+    if (lane == 0 && refined) atomicAdd(&s.ctl->series_refined, refined);
+}
+
+// ---------------------------------------------------------------- q_leaf_lb
+__global__ void __launch_bounds__(256) q_leaf_lb_kernel(DevIndex ix, QueryScratch s, int k) {
+    extern __shared__ float tab[];
+    __shared__ uint32_t hist[NBINS];
+    __shared__ float thr_s;
+    const QCtl* c = s.ctl;
+    if (c->flags & QF_NONFINITE) return;
+    const int card = ix.card;
+    for (int e = threadIdx.x; e < W * card; e += blockDim.x) tab[e] = s.table[e];
+    for (int i = threadIdx.x; i < NBINS; i += blockDim.x) hist[i] = 0;
+    if (threadIdx.x == 0) thr_s = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), c->delta, c->E);
+    __syncthreads();
+    uint8_t qs[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) qs[i] = c->qsym[i];
+    const int64_t a0 = c->approx_leaf, a1 = c->approx_end;
+    const float thr = thr_s;
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < ix.L) {
+        const uint4 mn = ix.env[2 * l], mx = ix.env[2 * l + 1];
+        const uint32_t wn[4] = {mn.x, mn.y, mn.z, mn.w}, wx[4] = {mx.x, mx.y, mx.z, mx.w};
+        float lb = 0.0f;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const int lo = (wn[i >> 2] >> (8 * (i & 3))) & 255, hi = (wx[i >> 2] >> (8 * (i & 3))) & 255;
+            if (qs[i] < lo)
+                lb += tab[i * card + lo];
+            else if (qs[i] > hi)
+                lb += tab[i * card + hi];
+        }
+        s.leaf_lb[l] = lb;
+        if (!(l >= a0 && l < a1) && lb <= thr) atomicAdd(&hist[bin_of(lb, thr)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NBINS; i += blockDim.x)
+        if (hist[i]) atomicAdd(&s.bin_count[i], hist[i]);
+}
+
+// ---------------------------------------------------------------- q_leaf_scatter
+__global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, QueryScratch s, int k) {
+    __shared__ uint32_t off[NBINS];
+    __shared__ uint32_t scratch[32];
+    __shared__ float thr_s;
+    QCtl* c = s.ctl;
+    if (c->flags & QF_NONFINITE) return;
+    uint32_t tot;
+    uint32_t o = block_excl_scan<uint32_t>(s.bin_count[threadIdx.x], 0u, OpAdd<uint32_t>(), scratch, &tot);
+    off[threadIdx.x] = o;
+    if (threadIdx.x == 0) thr_s = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), c->delta, c->E);
+    __syncthreads();
+    const float thr = thr_s;
+    const int64_t a0 = c->approx_leaf, a1 = c->approx_end;
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < ix.L;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        if (l >= a0 && l < a1) continue;
+        const float lb = s.leaf_lb[l];
+        if (lb <= thr) {
+            const int b = bin_of(lb, thr);
+            const uint32_t p = off[b] + atomicAdd(&s.bin_cursor[b], 1u);
+            if (p < tot) s.work[p] = (uint32_t)l;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->work_count = tot;
+        c->leaves_queued = tot;
+    }
+}
+
+// ---------------------------------------------------------------- q_scan_refine
+constexpr int SR_THREADS = 512;
+
+template <int NV>
+__global__ void __launch_bounds__(SR_THREADS) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k) {
+    extern __shared__ float tab[];
+    __shared__ uint16_t surv[REFINE_CHUNK];
+    __shared__ int nsurv;
+    __shared__ uint32_t item_s;
+    __shared__ float thr_s;
+    QCtl* c = s.ctl;
+    if (c->flags & QF_NONFINITE) return;
+    const int card = ix.card;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = SR_THREADS / 32;
+    for (int e = tid; e < W * card; e += SR_THREADS) tab[e] = s.table[e];
+    float4 qv[NV ? NV : 1];
+    load_q<NV>(s.q, qv);
+    const double delta = c->delta, E = c->E;
+    const uint32_t work_count = c->work_count;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long n_lb = 0, n_ref = 0, n_scan = 0;
+    for (;;) {
+        if (tid == 0) {
+            item_s = atomicAdd(&c->work_next, 1u);
+            thr_s = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), delta, E);
+        }
+        __syncthreads();
+        const uint32_t item = item_s;
+        if (item >= work_count) break;
+        const uint32_t leaf = s.work[item];
+        if (s.leaf_lb[leaf] <= thr_s) {
+            if (tid == 0) ++n_scan;
+            const int64_t b = ix.leaf_begin[leaf], e = ix.leaf_begin[leaf + 1];
+            for (int64_t c0 = b; c0 < e; c0 += REFINE_CHUNK) {
+                const int64_t c1 = std::min<int64_t>(e, c0 + REFINE_CHUNK);
+                if (tid == 0) nsurv = 0;
+                __syncthreads();
+                const float thr = thr_s;
+                for (int64_t base = c0; base < c1; base += SR_THREADS) {
+                    const int64_t r = base + tid;
+                    bool keep = false;
+                    if (r < c1) {
+                        keep = series_lb(ld_stream_u4(ix.sax + r), tab, card) <= thr;
+                        ++n_lb;
+                    }
+                    const unsigned mask = __ballot_sync(FULL, keep);
+                    int wbase = 0;
+                    if (lane == 0 && mask) wbase = atomicAdd(&nsurv, __popc(mask));
+                    wbase = __shfl_sync(FULL, wbase, 0);
+                    if (keep) surv[wbase + __popc(mask & lt)] = (uint16_t)(r - c0);
+                }
+                __syncthreads();
+                const int ns = nsurv;
+                for (int t = warp; t < ns; t += nwarps) {
+                    const int64_t r = c0 + surv[t];
+                    float lim = 0.0f;
+                    if (lane == 0) lim = abandon_limit(ld_volatile_u64(&s.topk[k - 1]), delta);
+                    lim = __shfl_sync(FULL, lim, 0);
+                    bool ab;
+                    const float d2 = warp_d2<NV>(ix, r, qv, s.q, lim, ab);
+                    if (lane == 0) {
+                        ++n_ref;
+                        if (!ab) consider(s, k, pack_key(d2, ix.orig[r]), (uint32_t)r, delta);
+                    }
+                }
+                __syncthreads();
+                if (tid == 0) thr_s = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), delta, E);
+            }
+        }
+        __syncthreads();
+    }
+    if (n_lb) atomicAdd(&c->series_lb, n_lb);
+    if (lane == 0 && n_ref) atomicAdd(&c->series_refined, n_ref);
+    if (tid == 0 && n_scan) atomicAdd(&c->leaves_scanned, n_scan);
+}
+
+// ---------------------------------------------------------------- q_finalize
+constexpr int FIN_THREADS = 1024, FIN_CAP = 2 * FIN_THREADS;
+
+__device__ __forceinline__ bool key_greater(unsigned long long a, uint32_t ia, unsigned long long b,
+                                            uint32_t ib) {
+    return a > b || (a == b && ia > ib);
+}
+
+__global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, QueryScratch s, int k) {
+    __shared__ unsigned long long sk[FIN_CAP];
+    __shared__ uint32_t sid[FIN_CAP];
+    __shared__ int nst;
+    QCtl* c = s.ctl;
+    if (c->flags & QF_NONFINITE) return;
+    const int tid = threadIdx.x;
+    const unsigned long long kth = s.topk[k - 1];
+    if (kth == EMPTY_SLOT) {
+        if (tid == 0) c->flags |= QF_SHORT;
+        return;
+    }
+    const double delta = c->delta;
+    const double bound = (double)key_d2(kth) * (1.0 + 3.0 * delta);
+    const uint32_t attempted = c->cand_count;
+    const uint32_t M = attempted < s.cand_cap ? attempted : s.cand_cap;
+    const int n = ix.n;
+    int cnt = 0;
+    uint32_t window = 0;
+    for (uint32_t base = 0; base < M; base += FIN_THREADS) {
+        if (tid == 0) nst = 0;
+        __syncthreads();
+        const uint32_t i = base + tid;
+        if (i < M) {
+            const unsigned long long key = s.cand_key[i];
+            if ((double)key_d2(key) <= bound) {
+                const int p = cnt + atomicAdd(&nst, 1);
+                const uint32_t pos = s.cand_pos[i];
+                const float* xr = ix.x + (int64_t)pos * n;
+                double acc = 0.0;  // the definition: sum_j (x_j - q_j)^2, left to right
+                for (int j = 0; j < n; ++j) {
+                    const double d = __dsub_rn((double)xr[j], (double)s.q[j]);
+                    acc = __dadd_rn(acc, __dmul_rn(d, d));
+                }
+                sk[p] = (unsigned long long)__double_as_longlong(acc);
+                sid[p] = ix.orig[pos];
+            }
+        }
+        __syncthreads();
+        const int added = nst;
+        if (added == 0) continue;
+        window += added;
+        const int total = cnt + added;
+        int P = 1;
+        while (P < total) P <<= 1;
+        for (int t = total + tid; t < P; t += FIN_THREADS) {
+            sk[t] = EMPTY_SLOT;
+            sid[t] = 0xffffffffu;
+        }
+        __syncthreads();
+        for (int size = 2; size <= P; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = tid; t < P / 2; t += FIN_THREADS) {
+                    const int a = 2 * t - (t & (stride - 1));
+                    const int b = a + stride;
+                    const bool asc = (a & size) == 0;
+                    if (key_greater(sk[a], sid[a], sk[b], sid[b]) == asc) {
+                        unsigned long long tk = sk[a];
+                        sk[a] = sk[b];
+                        sk[b] = tk;
+                        uint32_t ti = sid[a];
+                        sid[a] = sid[b];
+                        sid[b] = ti;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        cnt = total < k ? total : k;
+    }
+    if (tid < cnt) {
+        s.out_idx[tid] = (int64_t)sid[tid];
+        s.out_dist[tid] = __double2float_rn(sqrt(__longlong_as_double((long long)sk[tid])));
+    }
+    if (tid == 0) {
+        c->window = window;
+        if (cnt < k) c->flags |= QF_SHORT;
+        if (attempted > s.cand_cap) c->flags |= QF_OVERFLOW;
+    }
+}
+
+// ================================================================ host side
+void free_query_scratch(isax_index* ix, cudaStream_t st) {
+    QueryScratch& q = ix->qs;
+    void* ptrs[] = {q.q, q.table, q.leaf_lb, q.work, q.bin_count, q.bin_cursor, q.topk,
+                    q.cand_key, q.cand_pos, q.ctl, q.out_idx, q.out_dist};
+    for (void* p : ptrs)
+        if (p) dev_free(p, st);
+    q = QueryScratch{};
+}
+
+void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st) {
+    free_query_scratch(ix, st);
+    QueryScratch& q = ix->qs;
+    const DevIndex& d = ix->d;
+    q.q = static_cast<float*>(dev_alloc(sizeof(float) * d.n, st));
+    q.table = static_cast<float*>(dev_alloc(sizeof(float) * W * d.card, st));
+    q.leaf_lb = static_cast<float*>(dev_alloc(sizeof(float) * d.L, st));
+    q.work = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * d.L, st));
+    q.bin_count = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * NBINS, st));
+    q.bin_cursor = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * NBINS, st));
+    q.topk = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * MAX_K, st));
+    q.cand_cap = cand_cap;
+    q.cand_key = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * cand_cap, st));
+    q.cand_pos = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * cand_cap, st));
+    q.ctl = static_cast<QCtl*>(dev_alloc(sizeof(QCtl), st));
+    q.out_idx = static_cast<int64_t*>(dev_alloc(sizeof(int64_t) * MAX_K, st));
+    q.out_dist = static_cast<float*>(dev_alloc(sizeof(float) * MAX_K, st));
+    ISAX_CUDA_TRY(cudaMemsetAsync(q.ctl, 0, sizeof(QCtl), st));
+}
+
+void free_index_arrays(isax_index* ix, cudaStream_t st) {
+    free_query_scratch(ix, st);
+    void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp};
+    for (void* p : ptrs)
+        if (p) dev_free(p, st);
+    ix->x = nullptr;
+    ix->sax = nullptr;
+    ix->orig = nullptr;
+    ix->leaf_begin = nullptr;
+    ix->env = nullptr;
+    ix->leaf_key = nullptr;
+    ix->bp = nullptr;
+}
+
+namespace {
+
+template <int NV>
+void launch_query_kernels(isax_index* ix, int k, cudaStream_t st) {
+    const DevIndex& d = ix->d;
+    const QueryScratch& s = ix->qs;
+    const size_t tab_bytes = sizeof(float) * W * d.card;
+    q_prep_kernel<<<1, 256, 0, st>>>(d, s, k);
+    const int approx_blocks = std::max(1, std::min(ix->num_sms, (d.leaf_size + 7) / 8));
+    q_approx_kernel<NV><<<approx_blocks, 256, 0, st>>>(d, s, k);
+    const unsigned lb_blocks = (unsigned)((d.L + 255) / 256);
+    q_leaf_lb_kernel<<<lb_blocks, 256, tab_bytes, st>>>(d, s, k);
+    q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
+    q_scan_refine_kernel<NV><<<ix->num_sms * 2, SR_THREADS, tab_bytes, st>>>(d, s, k);
+    q_finalize_kernel<<<1, FIN_THREADS, 0, st>>>(d, s, k);
+    ISAX_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_query(isax_index* ix, int k, cudaStream_t st) {
+    const int n = ix->d.n;
+    if (n % 128 == 0) {
+        switch (n / 128) {
+            case 1: return launch_query_kernels<1>(ix, k, st);
+            case 2: return launch_query_kernels<2>(ix, k, st);
+            case 4: return launch_query_kernels<4>(ix, k, st);
+            case 8: return launch_query_kernels<8>(ix, k, st);
+            default: break;
+        }
+    }
+    launch_query_kernels<0>(ix, k, st);
+}
+
+}  // namespace
+
+// One exact k-NN query; q is already in ix->qs.q.  Results land in
+// ix->qs.out_idx / out_dist; the control block is copied to *ctl_out.
+void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st) {
+    *reruns = 0;
+    for (int attempt = 0;; ++attempt) {
+        launch_query(ix, k, st);
+        ISAX_CUDA_TRY(cudaMemcpyAsync(ctl_out, ix->qs.ctl, sizeof(QCtl), cudaMemcpyDeviceToHost, st));
+        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+        if (ctl_out->flags & QF_NONFINITE) throw Error{ISAX_ERR_INVALID_ARG, "query contains a non-finite value"};
+        if (ctl_out->flags & QF_OVERFLOW) {
+            if (attempt >= 3) throw Error{ISAX_ERR_INTERNAL, "candidate buffer kept overflowing"};
+            uint64_t want = std::max<uint64_t>((uint64_t)ctl_out->cand_count * 2, (uint64_t)ix->qs.cand_cap * 4);
+            want = std::min<uint64_t>(want, (uint64_t)ix->d.N);
+            // keep q across the reallocation
+            float* qsave = static_cast<float*>(dev_alloc(sizeof(float) * ix->d.n, st));
+            ISAX_CUDA_TRY(cudaMemcpyAsync(qsave, ix->qs.q, sizeof(float) * ix->d.n, cudaMemcpyDeviceToDevice, st));
+            alloc_query_scratch(ix, (uint32_t)want, st);
+            ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, qsave, sizeof(float) * ix->d.n, cudaMemcpyDeviceToDevice, st));
+            dev_free(qsave, st);
+            ++*reruns;
+            continue;
+        }
+        if (ctl_out->flags & QF_SHORT) throw Error{ISAX_ERR_INTERNAL, "fewer than k candidates survived"};
+        return;
+    }
+}
+
+}  // namespace isax
