@@ -1,0 +1,428 @@
+#!/usr/bin/env python3
+"""Benchmark: exact k-NN over an in-memory data-series collection with the
+GPU iSAX index.
+
+Workload (one "step" = the whole hot path once): build the index over
+100,000,000 z-normalised random walks of length 256 fp32 (w = 16, cardinality
+256, leaf size 2000: PAA + SAX summarisation, radix bucketing, leaves, permute,
+envelopes), then answer 100 exact 1-NN queries one by one (90 fresh random
+walks + 10 collection members with N(0, 0.01^2) noise, re-normalised).  The
+collection is generated on the device by the seeded generator before timing and
+is resident in HBM when the timed region starts; it is larger than L2, and
+every build streams all of it.
+
+Printed JSON line: `value` = queries per second of the whole job (all ranks'
+queries / wall time of the timed steps, builds included); `e2e` = the same job
+through the C ABI with host buffers (the 102.4 GB collection copied from pinned
+host memory by every build, queries and answers through host memory);
+`roofline` = the dominant kernel's algorithmic bytes per launch / its mean
+CUDA-event duration; `cpu_baseline` = the CPU oracle's FP64 brute force on a
+sample of the same workload.  `--impl reference` times that oracle alone.
+
+With --gpus N > 1 (torchrun, one process per GPU) every rank runs the job on
+its own collection (seed = rank): independent problems, no collective on the
+data path; the barrier and the max over ranks only frame the timing.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact k-NN queries/s @100M x256 vs plain path; p50/p99 latency; % HBM roofline"
+UNIT = "queries/s"
+HBM_FALLBACK = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--N", type=int, default=100_000_000)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--queries", type=int, default=100)
+    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--leaf", type=int, default=2000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-rows", type=int, default=4_000_000)
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {
+        "workload": "random-walk collection %d x %d fp32 z-normalised (seed = rank), iSAX w=16 "
+                    "card=256 leaf=%d; per step: full index build + %d exact %d-NN queries "
+                    "(%d fresh walks + %d noisy members, sigma 0.01)" % (
+                        a.N, a.n, a.leaf, a.queries, a.k, a.queries - a.queries // 10,
+                        a.queries // 10),
+        "N": a.N, "n": a.n, "w": 16, "cardinality": 256, "leaf_size": a.leaf, "k": a.k,
+        "queries_per_step": a.queries,
+        "l2": "inputs larger than L2: the %.1f GB collection is streamed by every build"
+              % (a.N * a.n * 4 / 1e9),
+        "parallelism": "independent collection per GPU",
+    }
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+def make_queries(a, rank):
+    import datagen
+    nq_member = a.queries // 10
+    Q, src = datagen.queries("walk", rank, a.N, a.n, 1 + 1000 * rank, a.queries - nq_member,
+                             nq_member, 0.01)
+    return Q, src
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.p = None
+        self.path = os.path.join("/tmp", "isax_clocks_%d_%d.csv" % (os.getpid(), gpu))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu),
+                                       "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline
+def kernel_bytes(name, a, launches, acc):
+    """Algorithmic bytes of all timed launches of a kernel (None if not modelled).
+    Build kernels run once per step (rs_* once per radix pass); the scan kernel's
+    bytes come from the per-query counters: 16 B per SAX word bounded plus one
+    full row per series refined outside the approximate leaf (an upper bound:
+    early abandoning reads less)."""
+    N, n = a.N, a.n
+    row = 4 * n
+    per_launch = {
+        "permute": N * (2 * row + 2 * 16 + 4 + 4),   # rows, SAX words, ids gathered
+        "summarize": N * (row + 16 + 8 + 4),         # rows read; SAX, key, id written
+        "rs_scatter": N * (8 + 4) * 2,               # keys and ids read and written
+        "rs_hist": N * 8,
+    }
+    if name in per_launch:
+        return per_launch[name] * launches
+    if name == "q_scan_refine":
+        return 16 * acc["series_lb"] + row * (acc["series_refined"] - acc["approx_series"])
+    if name == "q_approx":
+        return row * acc["approx_series"]
+    return None
+
+
+def traffic_from_profile(kernel):
+    """dram bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (its hash is recorded next to the figure)."""
+    src = os.path.join(ROOT, "paper_2009_01614_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(src, f), "rb").read())
+    digest = h.hexdigest()[:16]
+    prof = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(prof):
+        return None
+    for line in open(prof):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == digest:
+            return float(parts[2]), parts[3]
+    return None
+
+
+# ------------------------------------------------------------------ CPU baseline
+def cpu_baseline(a, sample_rows, n_queries=10):
+    import numpy as np
+    import datagen
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    X = datagen.rows("walk", 0, 0, sample_rows, a.n)
+    Q, _ = datagen.queries("walk", 0, sample_rows, a.n, 1, n_queries, 0, 0.01)
+    t0 = time.perf_counter()
+    oracle.bruteforce_knn(X, Q, a.k, nthreads=cores)
+    t = time.perf_counter() - t0
+    qps_full = n_queries / t * (sample_rows / a.N)
+    return {"value": qps_full, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "FP64 brute-force k-NN (all host cores) of %d fresh random-walk queries over "
+                      "the first %d rows of the collection: %.2f s; scaled to N=%d by rows"
+                      % (n_queries, sample_rows, t, a.N)}
+
+
+def reference_arm(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import datagen
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    S = min(a.N, 1_000_000)
+    X = datagen.rows("walk", 0, 0, S, a.n)
+    Q, _ = datagen.queries("walk", 0, S, a.n, 1, a.queries - a.queries // 10, a.queries // 10, 0.01)
+    for _ in range(a.warmup):
+        oracle.bruteforce_knn(X, Q, a.k, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.bruteforce_knn(X, Q, a.k, nthreads=cores)
+    t = time.perf_counter() - t0
+    step_full = t / a.steps * (a.N / S)
+    value = a.queries / step_full
+    sample = ("CPU oracle (FP64 brute-force exact %d-NN, %d host cores) of the step's %d queries "
+              "over a %d-row sample of the collection, %.3f s per sample step, scaled to N=%d by rows"
+              % (a.k, cores, a.queries, S, t / a.steps, a.N))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_full * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(a),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return reference_arm(a)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import datagen
+    import paper_2009_01614_gb300 as pkg
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    N, n, k = a.N, a.n, a.k
+
+    # inputs: collection generated on the device (bit-identical to the host generator)
+    X = torch.empty((N, n), dtype=torch.float32, device="cuda")
+    datagen.rows_device("walk", rank, 0, N, n, X.data_ptr(), sp)
+    Qh, src = make_queries(a, rank)
+    Qd = torch.from_numpy(Qh).cuda()
+    torch.cuda.synchronize()
+
+    lat_ms = []
+    stats_acc = {"series_lb": 0, "series_refined": 0, "approx_series": 0}
+
+    def step(record):
+        ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp)
+        for b in range(a.queries):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            i, d, st = ix.query(Qd[b], k, stats=True, stream=sp)
+            e1.record(stream)
+            if record:
+                e1.synchronize()
+                lat_ms.append(e0.elapsed_time(e1))
+                for key in stats_acc:
+                    stats_acc[key] += st[key]
+            last = (i, d)
+        info = ix.info()
+        ix.close()
+        return info, last
+
+    for _ in range(a.warmup):
+        step(False)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = pkg.isax_launch_count()
+    pkg.isax_profile(True)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(a.steps):
+        info, last = step(True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    pkg.isax_profile(False)
+    clock_info = clocks.stop()
+    launches = pkg.isax_launch_count() - launches0
+    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end))
+    barrier()
+    prof = pkg.isax_profile_report()
+
+    total_queries = a.queries * a.steps * world
+    value = total_queries / (elapsed_ms / 1e3)
+    q_time_ms = sum(lat_ms)
+    build_ms = (elapsed_ms - q_time_ms) / a.steps
+
+    # roofline of the dominant kernel (largest share of the timed kernel time)
+    hbm, peak_kind = peaks()
+    dom_name, (dom_launches, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    algo_total = kernel_bytes(dom_name, a, dom_launches, stats_acc)
+    avg_ms = dom_ms / dom_launches
+    per_launch_bytes = algo_total / dom_launches if algo_total is not None else None
+    achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9 if per_launch_bytes else None
+    tr = traffic_from_profile(dom_name)
+    roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
+            "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None,
+            "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
+            "peak_source": "%s: MEASURED_PEAKS.json hbm_gbs (copy bandwidth)" % peak_kind
+            if peak_kind == "measured" else "fallback 6800 GB/s"}
+    kernels = {}
+    total_kernel_ms = sum(v[1] for v in prof.values())
+    for nm, (cnt, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        entry = {"launches": cnt, "total_ms": round(ms, 3), "avg_ms": round(ms / cnt, 5),
+                 "share": round(ms / total_kernel_ms, 4)}
+        b = kernel_bytes(nm, a, cnt, stats_acc)
+        if b is not None and ms > 0:
+            entry["GB_per_s"] = round(b / (ms / 1e3) / 1e9, 1)
+        kernels[nm] = entry
+
+    lat_sorted = sorted(lat_ms)
+
+    def pct(p):
+        if not lat_sorted:
+            return None
+        i = min(len(lat_sorted) - 1, int(math.ceil(p / 100.0 * len(lat_sorted))) - 1)
+        return lat_sorted[max(i, 0)]
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": elapsed_ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(a),
+        "roofline": roof,
+        "latency_ms": {"p50": pct(50), "p99": pct(99), "mean": statistics.mean(lat_ms)},
+        "query_qps": len(lat_ms) / (q_time_ms / 1e3) if q_time_ms else None,
+        "build_ms": build_ms, "build_input_GB_per_s": N * n * 4 / 1e9 / (build_ms / 1e3),
+        "index": {"leaves": info["leaves"], "max_leaf": info["max_leaf"]},
+        "pruning": {"series_lb_per_query": stats_acc["series_lb"] / max(1, len(lat_ms)),
+                    "series_refined_per_query": stats_acc["series_refined"] / max(1, len(lat_ms))},
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clock_info,
+    }
+
+    # ---------------------------------------------------------- end to end (host buffers)
+    if not a.no_e2e:
+        del Qd
+        Xh = torch.empty((N, n), dtype=torch.float32, pin_memory=True)
+        chunk = 1 << 22
+        for r0 in range(0, N, chunk):
+            c = min(chunk, N - r0)
+            Xh[r0:r0 + c].copy_(X[r0:r0 + c])
+        del X
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        Qp = torch.from_numpy(Qh).pin_memory()
+        Xh_np = Xh.numpy()
+        Qp_np = Qp.numpy()
+
+        def step_e2e():
+            ix = pkg.Index(Xh_np, cardinality=256, leaf_size=a.leaf, stream=sp)
+            for b in range(a.queries):
+                ix.query(Qp_np[b], k, stream=sp)
+            ix.close()
+
+        for _ in range(max(1, min(a.warmup, 2))):
+            step_e2e()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            step_e2e()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        out["e2e"] = {"value": total_queries / e2e_s, "unit": UNIT,
+                      "h2d_bytes_per_step": N * n * 4 + a.queries * n * 4,
+                      "d2h_bytes_per_step": a.queries * k * (8 + 4),
+                      "ms_per_step": e2e_s / a.steps * 1e3}
+        del Xh
+    else:
+        del X
+
+    if rank == 0 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(a, min(a.cpu_sample_rows, N))
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -54,6 +54,7 @@ typedef struct isax_query_stats {
     int64_t leaves_scanned;   /* queued leaves still unpruned when a CTA claimed them */
     int64_t series_lb;        /* series lower bounds computed */
     int64_t series_refined;   /* exact distances computed (approximate leaf included) */
+    int64_t approx_series;    /* series of the approximate-answer leaves (all refined) */
     int64_t candidates;       /* refined series kept for the final ordering */
     int64_t window;           /* candidates re-ranked in FP64 */
     int32_t approx_leaf;      /* leaf used for the approximate answer */
@@ -170,6 +171,27 @@ isax_status isax_index_export(const isax_index* ix, uint8_t* sax, uint32_t* orig
  */
 isax_status isax_summarize(const float* series, int64_t N, int32_t n, int32_t cardinality,
                            uint32_t mem_flags, uint8_t* out_sax, float* out_paa, void* cuda_stream);
+
+/* ------------------------------------------------------------ tracing */
+
+typedef struct isax_kernel_time {
+    char name[48];     /* kernel name */
+    int64_t launches;  /* timed launches */
+    double total_ms;   /* summed CUDA-event duration on the launching stream */
+} isax_kernel_time;
+
+/* 1: time every later kernel launch of this library with a pair of CUDA events
+ * recorded on its stream (clears earlier records); 0: stop timing.  Timing adds
+ * two event records per launch; leave it off outside measurements. */
+isax_status isax_profile(int32_t enable);
+
+/* Per-kernel totals of the timed launches (waits for their events).  Fills at
+ * most max entries of out (out may be NULL) and returns the number of distinct
+ * kernels. */
+int32_t isax_profile_report(isax_kernel_time* out, int32_t max);
+
+/* Kernels this library has launched in this process (always counted). */
+uint64_t isax_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,7 @@ __all__ = [
     "MEM_OUTPUT_DEVICE", "W", "MAX_K", "lib", "build",
     "isax_build_index", "isax_query_knn", "isax_query_knn_batch", "isax_free_index",
     "isax_last_error", "isax_get_index_info", "isax_index_export", "isax_summarize",
-    "isax_set_allocator",
+    "isax_set_allocator", "isax_profile", "isax_profile_report", "isax_launch_count",
 ]
 
 W = 16
@@ -46,7 +46,8 @@ class BuildParams(ctypes.Structure):
 class QueryStats(ctypes.Structure):
     _fields_ = [("leaves_total", ctypes.c_int64), ("leaves_queued", ctypes.c_int64),
                 ("leaves_scanned", ctypes.c_int64), ("series_lb", ctypes.c_int64),
-                ("series_refined", ctypes.c_int64), ("candidates", ctypes.c_int64),
+                ("series_refined", ctypes.c_int64), ("approx_series", ctypes.c_int64),
+                ("candidates", ctypes.c_int64),
                 ("window", ctypes.c_int64), ("approx_leaf", ctypes.c_int32),
                 ("reruns", ctypes.c_int32)]
 
@@ -63,6 +64,11 @@ class IndexInfo(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -106,6 +112,12 @@ def lib():
         L.isax_index_export.restype = st
         L.isax_summarize.argtypes = [vp, i64, i32, i32, u32, vp, vp, vp]
         L.isax_summarize.restype = st
+        L.isax_profile.argtypes = [i32]
+        L.isax_profile.restype = st
+        L.isax_profile_report.argtypes = [ctypes.POINTER(KernelTime), i32]
+        L.isax_profile_report.restype = i32
+        L.isax_launch_count.argtypes = []
+        L.isax_launch_count.restype = ctypes.c_uint64
         _lib = L
     return _lib
 
@@ -161,6 +173,23 @@ def isax_index_export(index, sax_ptr=None, orig_ptr=None, leaf_begin_ptr=None, e
 def isax_summarize(series_ptr, N, n, cardinality, mem_flags, out_sax_ptr, out_paa_ptr, stream=0):
     _check(lib().isax_summarize(series_ptr, N, n, cardinality, mem_flags, out_sax_ptr,
                                 out_paa_ptr, stream))
+
+
+def isax_profile(enable):
+    _check(lib().isax_profile(1 if enable else 0))
+
+
+def isax_profile_report():
+    """{kernel name: (timed launches, total ms)} of the launches timed since
+    isax_profile(True)."""
+    n = lib().isax_profile_report(None, 0)
+    arr = (KernelTime * max(n, 1))()
+    n = lib().isax_profile_report(arr, n)
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n)}
+
+
+def isax_launch_count():
+    return int(lib().isax_launch_count())
 
 
 # ------------------------------------------------------------------ convenience

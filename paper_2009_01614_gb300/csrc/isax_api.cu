@@ -122,6 +122,7 @@ static void fill_stats(isax_query_stats* st, const isax_index* ix, const QCtl& c
     st->leaves_scanned = (int64_t)c.leaves_scanned;
     st->series_lb = (int64_t)c.series_lb;
     st->series_refined = (int64_t)c.series_refined;
+    st->approx_series = (int64_t)c.approx_series;
     st->candidates = (int64_t)c.cand_count;
     st->window = (int64_t)c.window;
     st->approx_leaf = c.approx_leaf;

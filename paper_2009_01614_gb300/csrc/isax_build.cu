@@ -81,6 +81,7 @@ __global__ void breakpoints_kernel(int card, float* bp) {
 }
 
 void launch_breakpoints(int card, float* bp, cudaStream_t st) {
+    ISAX_LAUNCH("breakpoints", st);
     breakpoints_kernel<<<(card + 1 + 255) / 256, 256, 0, st>>>(card, bp);
     ISAX_CUDA_TRY(cudaGetLastError());
 }
@@ -251,6 +252,7 @@ void launch_summarize(const float* x, int64_t N, int n, int card, const float* b
     int blocks = (int)std::max<int64_t>(1, std::min(want, cap));
     uint8_t* s8 = reinterpret_cast<uint8_t*>(sax);
     const float4* x4 = reinterpret_cast<const float4*>(x);
+    ISAX_LAUNCH("summarize", st);
 #define ISAX_SUM_CASE(L)                                                                       \
     case L:                                                                                    \
         summarize_vec_kernel<L><<<blocks, threads, 0, st>>>(x4, N, card, cbits, bp, s8, keys, \
@@ -336,9 +338,18 @@ static void exclusive_scan(const uint32_t* in, uint32_t* out, int64_t len, uint3
         return;
     }
     int64_t nb = (len + SC_TILE - 1) / SC_TILE;
+    {
+    ISAX_LAUNCH("scan_reduce", st);
     scan_reduce_kernel<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, len, sums);
+    }
+    {
+    ISAX_LAUNCH("scan_sums", st);
     scan_sums_kernel<<<1, 1024, 0, st>>>(sums, nb);
+    }
+    {
+    ISAX_LAUNCH("scan_apply", st);
     scan_apply_kernel<<<(unsigned)nb, SC_THREADS, 0, st>>>(in, out, len, sums);
+    }
     ISAX_CUDA_TRY(cudaGetLastError());
 }
 
@@ -718,10 +729,16 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
             uint32_t* sums = tmp.get<uint32_t>(scan_sums_len(256 * tiles));
             for (int pass = 0; pass < keybits / 8; ++pass) {
                 const int shift = 64 - keybits + 8 * pass;
+                {
+                ISAX_LAUNCH("rs_hist", st);
                 rs_hist_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(kA, N, shift, hist, tiles);
+                }
                 exclusive_scan(hist, hist, 256 * tiles, sums, st);
+                {
+                ISAX_LAUNCH("rs_scatter", st);
                 rs_scatter_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(kA, vA, kB, vB, N, shift,
                                                                           hist, tiles);
+                }
                 ISAX_CUDA_TRY(cudaGetLastError());
                 std::swap(kA, kB);
                 std::swap(vA, vB);
@@ -740,13 +757,20 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         uint32_t* flags = tmp.get<uint32_t>(N);
         uint32_t* pos = tmp.get<uint32_t>(N);
         uint32_t* sums = tmp.get<uint32_t>(scan_sums_len(N));
+        {
+        ISAX_LAUNCH("lf_lcp", st);
         lf_lcp_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(kA, N, Lc, keybits, c, a);
+        }
         if (NA > 0) {
+            ISAX_LAUNCH("lf_blockmax", st);
             int64_t nblk = (NA + Lc - 1) / Lc;
             lf_blockmax_kernel<<<(unsigned)std::min<int64_t>(nblk, (int64_t)num_sms * 16), LF_THREADS,
                                  0, st>>>(a, NA, Lc, P, S);
         }
+        {
+        ISAX_LAUNCH("lf_flags", st);
         lf_flags_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(c, P, S, N, Lc, keybits, flags);
+        }
         exclusive_scan(flags, pos, N, sums, st);
         ISAX_CUDA_TRY(cudaGetLastError());
         uint32_t L0 = 0;
@@ -754,19 +778,28 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
                                       cudaMemcpyDeviceToHost, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         uint32_t* starts = tmp.get<uint32_t>((size_t)L0 + 1);
+        {
+        ISAX_LAUNCH("lf_compact", st);
         lf_compact_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(flags, pos, N, starts, L0);
+        }
         uint32_t* pieces = tmp.get<uint32_t>(L0);
         uint32_t* poff = tmp.get<uint32_t>(L0);
         uint32_t* psums = tmp.get<uint32_t>(scan_sums_len(L0));
+        {
+        ISAX_LAUNCH("lf_pieces", st);
         lf_pieces_kernel<<<grid_for(L0, 256, num_sms), 256, 0, st>>>(starts, L0, Lc, pieces);
+        }
         exclusive_scan(pieces, poff, L0, psums, st);
         uint32_t L = 0;
         ISAX_CUDA_TRY(cudaMemcpyAsync(&L, psums + (scan_sums_len(L0) - 1), sizeof(uint32_t),
                                       cudaMemcpyDeviceToHost, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         ix->leaf_begin = static_cast<uint32_t*>(dev_alloc(((size_t)L + 1) * sizeof(uint32_t), st));
+        {
+        ISAX_LAUNCH("lf_expand", st);
         lf_expand_kernel<<<grid_for(L0, 256, num_sms), 256, 0, st>>>(starts, poff, L0, Lc, N,
                                                                       ix->leaf_begin, L);
+        }
         ISAX_CUDA_TRY(cudaGetLastError());
         for (void* p : {(void*)c, (void*)a, (void*)P, (void*)S, (void*)flags, (void*)pos,
                         (void*)sums, (void*)starts, (void*)pieces, (void*)poff, (void*)psums})
@@ -776,18 +809,24 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         ix->x = static_cast<float*>(dev_alloc((size_t)N * n * sizeof(float), st));
         ix->sax = static_cast<uint4*>(dev_alloc((size_t)N * sizeof(uint4), st));
         ix->orig = static_cast<uint32_t*>(dev_alloc((size_t)N * sizeof(uint32_t), st));
+        {
+        ISAX_LAUNCH("permute", st);
         permute_kernel<<<grid_for(N, 8, num_sms, 8), 256, 0, st>>>(
             reinterpret_cast<const float4*>(xin), n / 4, vA, N, reinterpret_cast<float4*>(ix->x),
             sax_tmp, ix->sax, ix->orig);
+        }
         ISAX_CUDA_TRY(cudaGetLastError());
 
         // envelopes
         ix->env = static_cast<uint4*>(dev_alloc((size_t)L * 2 * sizeof(uint4), st));
         ix->leaf_key = static_cast<unsigned long long*>(
             dev_alloc((size_t)L * sizeof(unsigned long long), st));
+        {
+        ISAX_LAUNCH("envelope", st);
         envelope_kernel<<<grid_for(L, 8, num_sms, 8), 256, 0, st>>>(ix->sax, ix->leaf_begin, L, kA,
                                                                      ix->env, ix->leaf_key, misc + 2);
         ISAX_CUDA_TRY(cudaGetLastError());
+        }
 
         unsigned hm[4];
         ISAX_CUDA_TRY(cudaMemcpyAsync(hm, misc, sizeof hm, cudaMemcpyDeviceToHost, st));

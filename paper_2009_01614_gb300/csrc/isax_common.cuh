@@ -36,6 +36,23 @@ void set_error(isax_status st, const std::string& msg);
                                                    cudaGetErrorString(e_)};          \
     } while (0)
 
+// ---------------------------------------------------------------- tracing
+// Counts a launch; with profiling on, brackets it with CUDA events on `st`.
+class KernelScope {
+   public:
+    KernelScope(const char* name, cudaStream_t st);
+    ~KernelScope();
+    KernelScope(const KernelScope&) = delete;
+    KernelScope& operator=(const KernelScope&) = delete;
+
+   private:
+    const char* name_;
+    cudaStream_t st_;
+    void* e0_ = nullptr;
+    void* e1_ = nullptr;
+};
+#define ISAX_LAUNCH(name, st) ::isax::KernelScope isax_ks_##__LINE__(name, st)
+
 // ---------------------------------------------------------------- allocator
 void* dev_alloc(size_t bytes, cudaStream_t st);  // throws Error{OOM}
 void dev_free(void* p, cudaStream_t st);
@@ -70,7 +87,7 @@ struct QCtl {
     uint32_t flags;        // QF_* bits
     double E;              // sqrt(n) * (eps_x + eps_q): PAA rounding slack
     double delta;          // relative error bound of an fp32 squared distance
-    unsigned long long series_lb, series_refined, leaves_scanned, leaves_queued;
+    unsigned long long series_lb, series_refined, leaves_scanned, leaves_queued, approx_series;
 };
 
 enum : uint32_t {

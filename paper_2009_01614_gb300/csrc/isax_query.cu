@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(256) q_prep_kernel(DevIndex ix, QueryScratch s
                 break;
             }
         }
+        c->approx_series = (unsigned long long)cnt;
         c->descent_leaf = (int32_t)dl;
         c->approx_leaf = (int32_t)a0;
         c->approx_end = (int32_t)a1;
@@ -603,14 +604,32 @@ void launch_query_kernels(isax_index* ix, int k, cudaStream_t st) {
     const DevIndex& d = ix->d;
     const QueryScratch& s = ix->qs;
     const size_t tab_bytes = sizeof(float) * W * d.card;
+    {
+    ISAX_LAUNCH("q_prep", st);
     q_prep_kernel<<<1, 256, 0, st>>>(d, s, k);
+    }
     const int approx_blocks = std::max(1, std::min(ix->num_sms, (d.leaf_size + 7) / 8));
+    {
+    ISAX_LAUNCH("q_approx", st);
     q_approx_kernel<NV><<<approx_blocks, 256, 0, st>>>(d, s, k);
+    }
     const unsigned lb_blocks = (unsigned)((d.L + 255) / 256);
+    {
+    ISAX_LAUNCH("q_leaf_lb", st);
     q_leaf_lb_kernel<<<lb_blocks, 256, tab_bytes, st>>>(d, s, k);
+    }
+    {
+    ISAX_LAUNCH("q_leaf_scatter", st);
     q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
+    }
+    {
+    ISAX_LAUNCH("q_scan_refine", st);
     q_scan_refine_kernel<NV><<<ix->num_sms * 2, SR_THREADS, tab_bytes, st>>>(d, s, k);
+    }
+    {
+    ISAX_LAUNCH("q_finalize", st);
     q_finalize_kernel<<<1, FIN_THREADS, 0, st>>>(d, s, k);
+    }
     ISAX_CUDA_TRY(cudaGetLastError());
 }
 
