@@ -172,6 +172,39 @@ isax_status isax_index_export(const isax_index* ix, uint8_t* sax, uint32_t* orig
 isax_status isax_summarize(const float* series, int64_t N, int32_t n, int32_t cardinality,
                            uint32_t mem_flags, uint8_t* out_sax, float* out_paa, void* cuda_stream);
 
+/* ------------------------------------------------------------ allocation-free query */
+
+#define ISAX_NOALLOC_MAX_LEAVES 524288u       /* largest index (in leaves) it serves */
+#define ISAX_NOALLOC_MAX_CANDIDATES 262144u   /* fp32 near-tie candidates it can hold */
+#define ISAX_NOALLOC_SCRATCH_BYTES 7395584u   /* its fixed device scratch (about 7 MiB) */
+
+/*
+ * isax_query_knn_noalloc - the same exact k-NN query as isax_query_knn (same
+ * arguments, same answers) for callers that must not allocate device memory
+ * while they query: a runtime that owns all GPU memory through its own pool, a
+ * latency-critical serving thread for which an allocation can stall on the
+ * driver, or code being recorded into a CUDA graph, where allocation calls are
+ * not allowed.  The paper has no counterpart; it is a deployment feature.
+ *
+ * Its scratch is one device array built into the library, of
+ * ISAX_NOALLOC_SCRATCH_BYTES, held by every GPU that loads the library until
+ * the process exits.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and each clears what
+ * must start at zero; calls are serialised inside the library and return after
+ * their results are copied out, because two queries running at once on the GPU
+ * would race on the shared array.
+ * Limits and errors: ISAX_ERR_INVALID_ARG for an index with more than
+ * ISAX_NOALLOC_MAX_LEAVES leaves (and as isax_query_knn); ISAX_ERR_OOM when
+ * the query keeps more than ISAX_NOALLOC_MAX_CANDIDATES candidates for its final
+ * FP64 ordering (refined series that were within fp32 error of the k-th best
+ * when refined; isax_query_knn would rerun with a larger buffer, this entry
+ * point cannot).  It calls no allocation routine.
+ */
+isax_status isax_query_knn_noalloc(const isax_index* ix, const float* q, int32_t k,
+                                   uint32_t mem_flags, int64_t* out_idx, float* out_dist,
+                                   isax_query_stats* stats, void* cuda_stream);
+
 /* ------------------------------------------------------------ tracing */
 
 typedef struct isax_kernel_time {

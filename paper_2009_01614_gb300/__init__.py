@@ -19,6 +19,7 @@ __all__ = [
     "isax_build_index", "isax_query_knn", "isax_query_knn_batch", "isax_free_index",
     "isax_last_error", "isax_get_index_info", "isax_index_export", "isax_summarize",
     "isax_set_allocator", "isax_profile", "isax_profile_report", "isax_launch_count",
+    "isax_query_knn_noalloc",
 ]
 
 W = 16
@@ -116,6 +117,9 @@ def lib():
         L.isax_profile.restype = st
         L.isax_profile_report.argtypes = [ctypes.POINTER(KernelTime), i32]
         L.isax_profile_report.restype = i32
+        L.isax_query_knn_noalloc.argtypes = [vp, vp, i32, u32, vp, vp,
+                                             ctypes.POINTER(QueryStats), vp]
+        L.isax_query_knn_noalloc.restype = st
         L.isax_launch_count.argtypes = []
         L.isax_launch_count.restype = ctypes.c_uint64
         _lib = L
@@ -143,6 +147,15 @@ def isax_build_index(series_ptr, N, n, params=None, stream=0):
 def isax_query_knn(index, q_ptr, k, mem_flags, out_idx_ptr, out_dist_ptr, stats=None, stream=0):
     _check(lib().isax_query_knn(index, q_ptr, k, mem_flags, out_idx_ptr, out_dist_ptr,
                                 ctypes.byref(stats) if stats is not None else None, stream))
+
+
+def isax_query_knn_noalloc(index, q_ptr, k, mem_flags, out_idx_ptr, out_dist_ptr, stats=None,
+                           stream=0):
+    """The query of isax_query_knn on the library's built-in scratch: for
+    callers that must not allocate device memory (see include/isax.h)."""
+    _check(lib().isax_query_knn_noalloc(index, q_ptr, k, mem_flags, out_idx_ptr, out_dist_ptr,
+                                        ctypes.byref(stats) if stats is not None else None,
+                                        stream))
 
 
 def isax_query_knn_batch(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_ptr, stats=None,

@@ -126,6 +126,7 @@ void summarize_impl(const float* series, int64_t N, int n, int card, uint32_t me
                     uint8_t* out_sax, float* out_paa, cudaStream_t st);
 void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st);
 void free_index_arrays(isax_index* ix, cudaStream_t st);
+void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st);
 void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st);
 void launch_breakpoints(int card, float* bp, cudaStream_t st);
 void launch_summarize(const float* x, int64_t N, int n, int card, const float* bp,

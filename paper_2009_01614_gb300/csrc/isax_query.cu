@@ -649,6 +649,55 @@ void launch_query(isax_index* ix, int k, cudaStream_t st) {
 
 }  // namespace
 
+// Same launch sequence as launch_query, on caller-provided scratch (used by
+// the entry point that must not allocate; see isax_noalloc.cu).
+template <int NV>
+static void launch_query_kernels_on(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st) {
+    const DevIndex& d = ix->d;
+    const size_t tab_bytes = sizeof(float) * W * d.card;
+    {
+    ISAX_LAUNCH("q_prep", st);
+    q_prep_kernel<<<1, 256, 0, st>>>(d, s, k);
+    }
+    const int approx_blocks = std::max(1, std::min(ix->num_sms, (d.leaf_size + 7) / 8));
+    {
+    ISAX_LAUNCH("q_approx", st);
+    q_approx_kernel<NV><<<approx_blocks, 256, 0, st>>>(d, s, k);
+    }
+    const unsigned lb_blocks = (unsigned)((d.L + 255) / 256);
+    {
+    ISAX_LAUNCH("q_leaf_lb", st);
+    q_leaf_lb_kernel<<<lb_blocks, 256, tab_bytes, st>>>(d, s, k);
+    }
+    {
+    ISAX_LAUNCH("q_leaf_scatter", st);
+    q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
+    }
+    {
+    ISAX_LAUNCH("q_scan_refine", st);
+    q_scan_refine_kernel<NV><<<ix->num_sms * 2, SR_THREADS, tab_bytes, st>>>(d, s, k);
+    }
+    {
+    ISAX_LAUNCH("q_finalize", st);
+    q_finalize_kernel<<<1, FIN_THREADS, 0, st>>>(d, s, k);
+    }
+    ISAX_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st) {
+    const int n = ix->d.n;
+    if (n % 128 == 0) {
+        switch (n / 128) {
+            case 1: return launch_query_kernels_on<1>(ix, s, k, st);
+            case 2: return launch_query_kernels_on<2>(ix, s, k, st);
+            case 4: return launch_query_kernels_on<4>(ix, s, k, st);
+            case 8: return launch_query_kernels_on<8>(ix, s, k, st);
+            default: break;
+        }
+    }
+    launch_query_kernels_on<0>(ix, s, k, st);
+}
+
 // One exact k-NN query; q is already in ix->qs.q.  Results land in
 // ix->qs.out_idx / out_dist; the control block is copied to *ctl_out.
 void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st) {
