@@ -100,12 +100,41 @@ __device__ __forceinline__ unsigned long long planes_to_key(int sym, bool active
     return key;
 }
 
-// One warp per series, series length NLEN in {128, 256, 512, 1024, 2048}: each
-// lane loads NLEN/128 float4; a segment is F = NLEN/64 consecutive float4
-// held by F consecutive lanes.  Segment sum: x+y+z+w per lane, then an xor tree
-// over the F lanes.  PAA = sum * (16/NLEN) (exact scaling).
-template <int NLEN>
-__global__ void __launch_bounds__(256) summarize_vec_kernel(
+// Symbol lookup in constant time.  The breakpoints of any cardinality <= 256
+// lie in (-4, 4) and are at least 0.0098 apart, more than the 1/128 width of
+// the cells of a grid over [-4, 4); the grid stores, for each cell start g,
+// #{beta_t <= g}, so a value in the cell adds at most the next breakpoint.
+// The result is exactly #{beta_t <= v} (the definition symbol_of computes).
+constexpr int SYM_CELLS = 1024;
+
+__device__ __forceinline__ float cell_start(int c) { return -4.0f + (float)c * 0.0078125f; }
+
+__device__ __forceinline__ void build_symbol_grid(const float* bp, int card, uint8_t* grid) {
+    for (int c = threadIdx.x; c < SYM_CELLS; c += blockDim.x)
+        grid[c] = (uint8_t)symbol_of(cell_start(c), bp, card);
+}
+
+__device__ __forceinline__ int symbol_fast(float v, const float* bp, const uint8_t* grid, int card) {
+    if (!(v >= -4.0f)) return 0;  // below every breakpoint (and NaN)
+    if (v >= 4.0f) return card - 1;
+    int c = (int)floorf((v + 4.0f) * 128.0f);  // off by at most one: fixed below
+    c = c < 0 ? 0 : (c > SYM_CELLS - 1 ? SYM_CELLS - 1 : c);
+    if (c < SYM_CELLS - 1 && cell_start(c + 1) <= v) ++c;
+    if (c > 0 && cell_start(c) > v) --c;
+    int s = grid[c];
+    if (bp[s + 1] <= v) ++s;  // bp[card] = +inf
+    return s;
+}
+
+// Series length NLEN in {128, 256, 512, 1024, 2048}; a warp takes ROWS (1 or 2)
+// series per round.  Each lane loads NLEN/128 float4 of every row (all loads
+// issued before any use); a segment is F = NLEN/64 consecutive float4 held by
+// F consecutive lanes.  Segment sum: x+y+z+w per lane, then an xor tree over
+// the F lanes.  Then lane L owns (row L/16, segment L%16): its PAA = sum *
+// (16/NLEN) (exact scaling) and its symbol, computed once.
+template <int NLEN, int ROWS>
+__global__ void __launch_bounds__(256, (NLEN <= 256 ? 6 : NLEN <= 1024 ? 4 : 2))
+summarize_vec_kernel(
     const float4* __restrict__ x, int64_t N, int card, int cbits, const float* __restrict__ bp_g,
     uint8_t* __restrict__ sax, unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
     float* __restrict__ paa_out, unsigned* maxabs_bits, unsigned* nonfinite) {
@@ -114,50 +143,64 @@ __global__ void __launch_bounds__(256) summarize_vec_kernel(
     constexpr int SPP = 32 / F;
     constexpr float INV_M = 16.0f / (float)NLEN;
     __shared__ float bp[MAX_CARD + 1];
+    __shared__ uint8_t grid[SYM_CELLS];
     __shared__ float red_max[32];
     __shared__ unsigned red_bad;
     for (int i = threadIdx.x; i <= card; i += blockDim.x) bp[i] = bp_g[i];
     if (threadIdx.x == 0) red_bad = 0;
     __syncthreads();
+    build_symbol_grid(bp, card, grid);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
+    const int myrow = lane >> 4, myseg = lane & 15;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     float amax = 0.0f;
     bool bad = false;
-    for (int64_t row = gw; row < N; row += nw) {
-        const float4* xr = x + row * (NLEN / 4);
-        float4 v[PASSES];
+    for (int64_t base = gw * ROWS; base < N; base += nw * ROWS) {
+        float4 v[ROWS][PASSES];
 #pragma unroll
-        for (int p = 0; p < PASSES; ++p) v[p] = ld_stream(xr + p * 32 + lane);
-        int mysym = 0;
-        float mypaa = 0.0f;
+        for (int r = 0; r < ROWS; ++r) {
+            const float4* xr = x + (base + r) * (NLEN / 4);
+            const bool ok = base + r < N;
 #pragma unroll
-        for (int p = 0; p < PASSES; ++p) {
-            float s = ((v[p].x + v[p].y) + v[p].z) + v[p].w;
-            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[p].x), fabsf(v[p].y)),
-                                     fmaxf(fabsf(v[p].z), fabsf(v[p].w))));
+            for (int p = 0; p < PASSES; ++p)
+                v[r][p] = ok ? ld_stream(xr + p * 32 + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float mysum = 0.0f;
 #pragma unroll
-            for (int off = 1; off < F; off <<= 1) s += __shfl_xor_sync(FULL, s, off);
-            float paa = s * INV_M;
-            int sym = symbol_of(paa, bp, card);
-            int src = ((lane - p * SPP) & (SPP - 1)) * F;
-            int ts = __shfl_sync(FULL, sym, src);
-            float tp = __shfl_sync(FULL, paa, src);
-            if (lane >= p * SPP && lane < (p + 1) * SPP) {
-                mysym = ts;
-                mypaa = tp;
+        for (int r = 0; r < ROWS; ++r) {
+#pragma unroll
+            for (int p = 0; p < PASSES; ++p) {
+                float s = ((v[r][p].x + v[r][p].y) + v[r][p].z) + v[r][p].w;
+                amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[r][p].x), fabsf(v[r][p].y)),
+                                         fmaxf(fabsf(v[r][p].z), fabsf(v[r][p].w))));
+#pragma unroll
+                for (int off = 1; off < F; off <<= 1) s += __shfl_xor_sync(FULL, s, off);
+                const int src = ((myseg - p * SPP) & (SPP - 1)) * F;
+                const float t = __shfl_sync(FULL, s, src);
+                if (myrow == r && myseg / SPP == p) mysum = t;
             }
         }
-        const bool seg = lane < W;
-        bad |= seg && !isfinite(mypaa);
-        unsigned long long key = planes_to_key(mysym, seg, cbits);
-        if (seg) {
-            sax[row * W + lane] = (uint8_t)mysym;
-            if (paa_out) paa_out[row * W + lane] = mypaa;
+        const int64_t row = base + myrow;
+        const bool valid = myrow < ROWS && row < N;
+        const float paa = mysum * INV_M;
+        const int sym = symbol_fast(paa, bp, grid, card);
+        bad |= valid && !isfinite(paa);
+        unsigned long long key = 0;
+#pragma unroll
+        for (int pl = 0; pl < 4; ++pl) {
+            const int b = cbits - 1 - pl;
+            const unsigned m = __ballot_sync(FULL, valid && b >= 0 && ((sym >> (b < 0 ? 0 : b)) & 1));
+            key = (key << 16) | (unsigned long long)(__brev((m >> (16 * myrow)) & 0xffffu) >> 16);
         }
-        if (lane == 0) {
-            if (keys) keys[row] = key;
-            if (ids) ids[row] = (uint32_t)row;
+        if (valid) {
+            sax[row * W + myseg] = (uint8_t)sym;
+            if (paa_out) paa_out[row * W + myseg] = paa;
+            if (myseg == 0) {
+                if (keys) keys[row] = key;
+                if (ids) ids[row] = (uint32_t)row;
+            }
         }
     }
     // block reductions -> one atomic per block
@@ -247,26 +290,33 @@ void launch_summarize(const float* x, int64_t N, int n, int card, const float* b
     int cbits = 0;
     while ((1 << cbits) < card) ++cbits;
     const int threads = 256;
-    int64_t want = (N + 7) / 8;  // one warp per row
-    int64_t cap = (int64_t)num_sms * 8;
-    int blocks = (int)std::max<int64_t>(1, std::min(want, cap));
+    const int64_t want = (N + 15) / 16;  // up to two rows per warp
+    // persistent grid: as many blocks as are resident at once
+    auto grid_of = [&](const void* fn) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 4;
+        return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms * per_sm));
+    };
     uint8_t* s8 = reinterpret_cast<uint8_t*>(sax);
     const float4* x4 = reinterpret_cast<const float4*>(x);
     ISAX_LAUNCH("summarize", st);
-#define ISAX_SUM_CASE(L)                                                                       \
+#define ISAX_SUM_CASE(L, R)                                                                    \
     case L:                                                                                    \
-        summarize_vec_kernel<L><<<blocks, threads, 0, st>>>(x4, N, card, cbits, bp, s8, keys, \
-                                                            ids, paa_out, maxabs_bits,         \
-                                                            nonfinite);                        \
+        summarize_vec_kernel<L, R><<<grid_of((const void*)summarize_vec_kernel<L, R>),         \
+                                     threads, 0, st>>>(x4, N, card, cbits, bp, s8, keys, ids,  \
+                                                       paa_out, maxabs_bits, nonfinite);       \
         break;
     switch (n) {
-        ISAX_SUM_CASE(128)
-        ISAX_SUM_CASE(256)
-        ISAX_SUM_CASE(512)
-        ISAX_SUM_CASE(1024)
-        ISAX_SUM_CASE(2048)
+        ISAX_SUM_CASE(128, 2)
+        ISAX_SUM_CASE(256, 2)
+        ISAX_SUM_CASE(512, 2)
+        ISAX_SUM_CASE(1024, 1)
+        ISAX_SUM_CASE(2048, 1)
         default:
-            summarize_generic_kernel<<<blocks, threads, 0, st>>>(x, N, n, card, cbits, bp, s8, keys,
+            summarize_generic_kernel<<<grid_of((const void*)summarize_generic_kernel), threads, 0,
+                                       st>>>(x, N, n, card, cbits, bp, s8, keys,
                                                                  ids, paa_out, maxabs_bits,
                                                                  nonfinite);
     }

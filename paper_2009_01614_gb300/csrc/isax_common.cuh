@@ -17,7 +17,7 @@ constexpr int MAX_LEN = ISAX_MAX_LEN;
 constexpr int ROOT_BITS = W;       // root key: first bit of each of the 16 segments
 
 constexpr int NBINS = 256;         // leaf ordering bins (lower bound / threshold)
-constexpr int REFINE_CHUNK = 2048; // rows of a leaf bounded per scan round
+constexpr int SCAN_UNIT = 256;     // series of a leaf bounded by one warp per claim
 constexpr uint64_t EMPTY_SLOT = ~0ull;
 
 // ---------------------------------------------------------------- errors
@@ -85,6 +85,8 @@ struct QCtl {
     uint32_t cand_count;   // candidate appends attempted (may exceed capacity)
     uint32_t window;       // candidates re-ranked in FP64
     uint32_t flags;        // QF_* bits
+    float thr_lb0;         // bound threshold the work list was binned with
+    float qpaa[16];        // query PAA (fp32, as used by the bound table)
     double E;              // sqrt(n) * (eps_x + eps_q): PAA rounding slack
     double delta;          // relative error bound of an fp32 squared distance
     unsigned long long series_lb, series_refined, leaves_scanned, leaves_queued, approx_series;

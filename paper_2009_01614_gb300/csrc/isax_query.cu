@@ -200,83 +200,102 @@ __device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ ta
 }
 
 // ---------------------------------------------------------------- q_prep
-__global__ void __launch_bounds__(256) q_prep_kernel(DevIndex ix, QueryScratch s, int k) {
+constexpr int PREP_THREADS = 256;
+
+__global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, QueryScratch s, int k) {
     __shared__ float bp[MAX_CARD + 1];
+    __shared__ float qv[MAX_LEN];
     __shared__ float qpaa[W];
     __shared__ int qsym[W];
     __shared__ float red[32];
     __shared__ unsigned bad;
+    __shared__ unsigned cnt_s;
+    __shared__ unsigned long long key_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = ix.n, m = n / W, card = ix.card;
-    for (int i = tid; i <= card; i += blockDim.x) bp[i] = ix.bp[i];
-    if (tid == 0) bad = 0;
-    // init per-query state
-    for (int i = tid; i < k; i += blockDim.x) s.topk[i] = EMPTY_SLOT;
-    for (int i = tid; i < NBINS; i += blockDim.x) {
+    for (int i = tid; i <= card; i += PREP_THREADS) bp[i] = ix.bp[i];
+    for (int j = tid; j < n; j += PREP_THREADS) qv[j] = s.q[j];
+    if (tid == 0) {
+        bad = 0;
+        cnt_s = 0;
+    }
+    // reset the per-query state left by the previous query
+    for (int i = tid; i < k; i += PREP_THREADS) s.topk[i] = EMPTY_SLOT;
+    for (int i = tid; i < NBINS; i += PREP_THREADS) {
         s.bin_count[i] = 0;
         s.bin_cursor[i] = 0;
     }
+    __syncthreads();
     float amax = 0.0f;
-    for (int j = tid; j < n; j += blockDim.x) amax = fmaxf(amax, fabsf(s.q[j]));
+    for (int j = tid; j < n; j += PREP_THREADS) amax = fmaxf(amax, fabsf(qv[j]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, off));
     if (lane == 0) red[warp] = amax;
-    __syncthreads();
     if (tid < W) {
         float sum = 0.0f;
-        for (int j = 0; j < m; ++j) sum += s.q[tid * m + j];
-        float p = sum / (float)m;
+        for (int j = 0; j < m; ++j) sum += qv[tid * m + j];
+        const float p = sum / (float)m;
         qpaa[tid] = p;
         qsym[tid] = symbol_of(p, bp, card);
         if (!isfinite(p)) atomicOr(&bad, 1u);
     }
     __syncthreads();
-    // lower-bound table
+    // lower-bound table T[i][s] = m * dist(qpaa_i, [bp[s], bp[s+1]))^2
     const float mf = (float)m;
-    for (int e = tid; e < W * card; e += blockDim.x) {
+    for (int e = tid; e < W * card; e += PREP_THREADS) {
         const int i = e / card, sym = e - i * card;
         const float lo = bp[sym], hi = bp[sym + 1], v = qpaa[i];
         const float d = v < lo ? lo - v : (v >= hi ? v - hi : 0.0f);
         s.table[e] = (d * d) * mf;
     }
     if (tid == 0) {
-        float qmax = 0.0f;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) qmax = fmaxf(qmax, red[i]);
-        QCtl* c = s.ctl;
         unsigned long long key = 0;
         for (int pl = 0; pl < 4; ++pl) {
-            int b = ix.cbits - 1 - pl;
+            const int b = ix.cbits - 1 - pl;
             unsigned plane = 0;
             for (int i = 0; i < W; ++i)
                 plane = (plane << 1) | (b >= 0 ? ((unsigned)(qsym[i] >> b) & 1u) : 0u);
             key = (key << 16) | plane;
         }
+        key_s = key;
+    }
+    __syncthreads();
+    // descent: the last leaf whose first key <= the query key.  Keys are
+    // sorted: count the samples at stride `step` that are <= key, then count
+    // inside the one stride that holds the boundary.
+    const unsigned long long key = key_s;
+    const int64_t L = ix.L;
+    const int64_t step = (L + PREP_THREADS - 1) / PREP_THREADS;
+    const int64_t si = (int64_t)tid * step;
+    const int c1 = __syncthreads_count(si < L && ix.leaf_key[si] <= key);
+    const int64_t lo = c1 > 0 ? (int64_t)(c1 - 1) * step : 0;
+    const int64_t hi = lo + step < L ? lo + step : L;
+    unsigned cnt = 0;
+    for (int64_t j = lo + tid; j < hi; j += PREP_THREADS) cnt += ix.leaf_key[j] <= key ? 1u : 0u;
+    if (cnt) atomicAdd(&cnt_s, cnt);
+    __syncthreads();
+    if (tid == 0) {
+        float qmax = 0.0f;
+        for (int i = 0; i < PREP_THREADS / 32; ++i) qmax = fmaxf(qmax, red[i]);
+        QCtl* c = s.ctl;
         c->qkey = key;
-        // descent: last leaf whose first key <= query key
-        int64_t lo = 0, hi = ix.L;  // find first leaf with leaf_key > key
-        while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            if (ix.leaf_key[mid] <= key)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        int64_t dl = lo > 0 ? lo - 1 : 0;
+        const int64_t ub = lo + cnt_s;
+        const int64_t dl = ub > 0 ? ub - 1 : 0;
         // approximate-answer range: that leaf, widened until it holds >= k series
         int64_t a0 = dl, a1 = dl + 1;
-        int64_t cnt = (int64_t)ix.leaf_begin[a1] - ix.leaf_begin[a0];
-        while (cnt < k) {
-            if (a1 < ix.L) {
-                cnt += (int64_t)ix.leaf_begin[a1 + 1] - ix.leaf_begin[a1];
+        int64_t tot = (int64_t)ix.leaf_begin[a1] - ix.leaf_begin[a0];
+        while (tot < k) {
+            if (a1 < L) {
+                tot += (int64_t)ix.leaf_begin[a1 + 1] - ix.leaf_begin[a1];
                 ++a1;
             } else if (a0 > 0) {
                 --a0;
-                cnt += (int64_t)ix.leaf_begin[a0 + 1] - ix.leaf_begin[a0];
+                tot += (int64_t)ix.leaf_begin[a0 + 1] - ix.leaf_begin[a0];
             } else {
                 break;
             }
         }
-        c->approx_series = (unsigned long long)cnt;
+        c->approx_series = (unsigned long long)tot;
         c->descent_leaf = (int32_t)dl;
         c->approx_leaf = (int32_t)a0;
         c->approx_end = (int32_t)a1;
@@ -285,6 +304,7 @@ __global__ void __launch_bounds__(256) q_prep_kernel(DevIndex ix, QueryScratch s
         c->cand_count = 0;
         c->window = 0;
         c->flags = bad ? QF_NONFINITE : 0u;
+        c->thr_lb0 = INFINITY;
         const double u = 0x1p-24;
         const double eps_x = 1.01 * (m + 1) * u * (double)ix.maxabs;
         const double eps_q = 1.01 * (m + 1) * u * (double)qmax;
@@ -294,7 +314,10 @@ __global__ void __launch_bounds__(256) q_prep_kernel(DevIndex ix, QueryScratch s
         c->series_refined = 0;
         c->leaves_scanned = 0;
         c->leaves_queued = 0;
-        for (int i = 0; i < W; ++i) c->qsym[i] = (uint8_t)qsym[i];
+        for (int i = 0; i < W; ++i) {
+            c->qsym[i] = (uint8_t)qsym[i];
+            c->qpaa[i] = qpaa[i];
+        }
     }
 }
 
@@ -313,42 +336,57 @@ __global__ void __launch_bounds__(256) q_approx_kernel(DevIndex ix, QueryScratch
     unsigned long long refined = 0;
     for (int64_t r = b + gw; r < e; r += nw) {
         bool ab;
-        float d2 = warp_d2<NV>(ix, r, qv, s.q, INFINITY, ab);
-        if (lane == 0) consider(s, k, pack_key(d2, ix.orig[r]), (uint32_t)r, delta);
+        const float d2 = warp_d2<NV>(ix, r, qv, s.q, INFINITY, ab);
+        if (lane == 0) {
+            const unsigned long long kth = ld_volatile_u64(&s.topk[k - 1]);
+            if (kth == EMPTY_SLOT || (double)d2 <= (double)key_d2(kth) * (1.0 + 3.0 * delta))
+                consider(s, k, pack_key(d2, ix.orig[r]), (uint32_t)r, delta);
+        }
         ++refined;
     }
     if (lane == 0 && refined) atomicAdd(&s.ctl->series_refined, refined);
 }
 
 // ---------------------------------------------------------------- q_leaf_lb
+// Envelope bound of every leaf from the breakpoints and the query PAA: per
+// segment the table entry of the envelope edge nearer the query (the same
+// fp32 expression as the table), 0 when the query's symbol lies inside.
 __global__ void __launch_bounds__(256) q_leaf_lb_kernel(DevIndex ix, QueryScratch s, int k) {
-    extern __shared__ float tab[];
+    __shared__ float bp[MAX_CARD + 1];
     __shared__ uint32_t hist[NBINS];
     __shared__ float thr_s;
     const QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
     const int card = ix.card;
-    for (int e = threadIdx.x; e < W * card; e += blockDim.x) tab[e] = s.table[e];
+    for (int i = threadIdx.x; i <= card; i += blockDim.x) bp[i] = ix.bp[i];
     for (int i = threadIdx.x; i < NBINS; i += blockDim.x) hist[i] = 0;
     if (threadIdx.x == 0) thr_s = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), c->delta, c->E);
     __syncthreads();
-    uint8_t qs[W];
+    float qp[W];
+    int qs[W];
 #pragma unroll
-    for (int i = 0; i < W; ++i) qs[i] = c->qsym[i];
+    for (int i = 0; i < W; ++i) {
+        qp[i] = c->qpaa[i];
+        qs[i] = c->qsym[i];
+    }
+    const float mf = (float)(ix.n / W);
     const int64_t a0 = c->approx_leaf, a1 = c->approx_end;
     const float thr = thr_s;
-    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l < ix.L) {
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < ix.L;
+         l += (int64_t)gridDim.x * blockDim.x) {
         const uint4 mn = ix.env[2 * l], mx = ix.env[2 * l + 1];
         const uint32_t wn[4] = {mn.x, mn.y, mn.z, mn.w}, wx[4] = {mx.x, mx.y, mx.z, mx.w};
         float lb = 0.0f;
 #pragma unroll
         for (int i = 0; i < W; ++i) {
             const int lo = (wn[i >> 2] >> (8 * (i & 3))) & 255, hi = (wx[i >> 2] >> (8 * (i & 3))) & 255;
-            if (qs[i] < lo)
-                lb += tab[i * card + lo];
-            else if (qs[i] > hi)
-                lb += tab[i * card + hi];
+            if (qs[i] < lo) {
+                const float d = bp[lo] - qp[i];
+                lb += (d * d) * mf;
+            } else if (qs[i] > hi) {
+                const float d = qp[i] - bp[hi + 1];
+                lb += (d * d) * mf;
+            }
         }
         s.leaf_lb[l] = lb;
         if (!(l >= a0 && l < a1) && lb <= thr) atomicAdd(&hist[bin_of(lb, thr)], 1u);
@@ -385,100 +423,217 @@ __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, Quer
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->work_count = tot;
         c->leaves_queued = tot;
+        c->thr_lb0 = thr;
     }
 }
 
 // ---------------------------------------------------------------- q_scan_refine
-constexpr int SR_THREADS = 512;
+constexpr int SR_THREADS = NBINS;                 // one thread per bin for the offset scan
+constexpr int SR_WORDS = SCAN_UNIT / 32;          // SAX words per lane per round
 
+// squared distances of two rows (second one optional) with all loads issued first
 template <int NV>
-__global__ void __launch_bounds__(SR_THREADS) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k) {
+__device__ __forceinline__ void warp_d2_two(const DevIndex& ix, int64_t r0, int64_t r1, bool two,
+                                            const float4 (&qv)[NV], float& d0, float& d1) {
+    const int lane = threadIdx.x & 31;
+    const float4* x0 = reinterpret_cast<const float4*>(ix.x + r0 * ix.n);
+    const float4* x1 = reinterpret_cast<const float4*>(ix.x + (two ? r1 : r0) * ix.n);
+    float4 v0[NV], v1[NV];
+#pragma unroll
+    for (int p = 0; p < NV; ++p) {
+        v0[p] = ld_stream(x0 + p * 32 + lane);
+        v1[p] = two ? ld_stream(x1 + p * 32 + lane) : v0[p];
+    }
+    float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+    for (int p = 0; p < NV; ++p) {
+        float d;
+        d = v0[p].x - qv[p].x; a0 = fmaf(d, d, a0);
+        d = v0[p].y - qv[p].y; a0 = fmaf(d, d, a0);
+        d = v0[p].z - qv[p].z; a0 = fmaf(d, d, a0);
+        d = v0[p].w - qv[p].w; a0 = fmaf(d, d, a0);
+        d = v1[p].x - qv[p].x; a1 = fmaf(d, d, a1);
+        d = v1[p].y - qv[p].y; a1 = fmaf(d, d, a1);
+        d = v1[p].z - qv[p].z; a1 = fmaf(d, d, a1);
+        d = v1[p].w - qv[p].w; a1 = fmaf(d, d, a1);
+    }
+    d0 = warp_sum_f(a0);
+    d1 = warp_sum_f(a1);
+}
+
+// Persistent warps: each claims the next queued leaf (Fetch&Inc over the
+// list, which is in ascending bound-bin order), skips it if its bound now
+// exceeds the threshold, stops for good once the bin of the claimed position
+// lies wholly above the threshold, else bounds the leaf's SAX words 256 at a
+// time (all loads of a round issued first), refines the survivors two rows at
+// a time, and hands each batch of up to 32 distances to the k-best update
+// after one filter against the current k-th best.  No block barriers.
+template <int NV>
+__global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k) {
     extern __shared__ float tab[];
-    __shared__ uint16_t surv[REFINE_CHUNK];
-    __shared__ int nsurv;
-    __shared__ uint32_t item_s;
-    __shared__ float thr_s;
+    __shared__ uint32_t off[NBINS + 1];
+    __shared__ uint32_t scratch[32];
     QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
     const int card = ix.card;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = SR_THREADS / 32;
+    const int tid = threadIdx.x, lane = tid & 31;
     for (int e = tid; e < W * card; e += SR_THREADS) tab[e] = s.table[e];
-    float4 qv[NV ? NV : 1];
+    {
+        uint32_t tot;
+        const uint32_t o = block_excl_scan<uint32_t>(s.bin_count[tid], 0u, OpAdd<uint32_t>(), scratch, &tot);
+        off[tid] = o;
+        if (tid == 0) off[NBINS] = tot;
+    }
+    __syncthreads();
+    constexpr int NQ = NV ? NV : 1;
+    float4 qv[NQ];
     load_q<NV>(s.q, qv);
     const double delta = c->delta, E = c->E;
     const uint32_t work_count = c->work_count;
-    const unsigned lt = (1u << lane) - 1u;
+    const float thr0 = c->thr_lb0;
+    unsigned long long kth_seen = 0;
+    float thr = 0.0f, lim_ab = INFINITY;
+    bool have = false;
+    int wb = 0;
     unsigned long long n_lb = 0, n_ref = 0, n_scan = 0;
-    for (;;) {
-        if (tid == 0) {
-            item_s = atomicAdd(&c->work_next, 1u);
-            thr_s = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), delta, E);
+    // batch of refined distances: entry i held by lane i
+    float my_d2 = INFINITY;
+    uint32_t my_pos = 0;
+    int nb = 0;
+    auto flush = [&]() {
+        if (nb == 0) return;
+        unsigned long long kt = 0;
+        if (lane == 0) kt = ld_volatile_u64(&s.topk[k - 1]);
+        kt = __shfl_sync(FULL, kt, 0);
+        const double lim = kt == EMPTY_SLOT ? INFINITY : (double)key_d2(kt) * (1.0 + 3.0 * delta);
+        if (lane < nb && (double)my_d2 <= lim)
+            consider(s, k, pack_key(my_d2, ix.orig[my_pos]), my_pos, delta);
+        __syncwarp();
+        nb = 0;
+    };
+    auto push = [&](float d2, int64_t r) {
+        if (lane == nb) {
+            my_d2 = d2;
+            my_pos = (uint32_t)r;
         }
-        __syncthreads();
-        const uint32_t item = item_s;
+        ++nb;
+        if (nb == 32) flush();
+    };
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(&c->work_next, 1u);
+        item = __shfl_sync(FULL, item, 0);
         if (item >= work_count) break;
+        while (wb < NBINS - 1 && off[wb + 1] <= item) ++wb;
+        unsigned long long kth = 0;
+        if (lane == 0) kth = ld_volatile_u64(&s.topk[k - 1]);
+        kth = __shfl_sync(FULL, kth, 0);
+        if (!have || kth != kth_seen) {
+            thr = lb_threshold(kth, delta, E);
+            lim_ab = abandon_limit(kth, delta);
+            kth_seen = kth;
+            have = true;
+        }
+        // every later position is in bin >= wb, whose bounds are >= thr0 (wb/NBINS)^2
+        if (thr0 > 0.0f && !isinf(thr0)) {
+            const float edge = (float)wb / (float)NBINS;
+            if (thr0 * edge * edge * 0.99999f > thr) break;
+        }
         const uint32_t leaf = s.work[item];
-        if (s.leaf_lb[leaf] <= thr_s) {
-            if (tid == 0) ++n_scan;
-            const int64_t b = ix.leaf_begin[leaf], e = ix.leaf_begin[leaf + 1];
-            for (int64_t c0 = b; c0 < e; c0 += REFINE_CHUNK) {
-                const int64_t c1 = std::min<int64_t>(e, c0 + REFINE_CHUNK);
-                if (tid == 0) nsurv = 0;
-                __syncthreads();
-                const float thr = thr_s;
-                for (int64_t base = c0; base < c1; base += SR_THREADS) {
-                    const int64_t r = base + tid;
-                    bool keep = false;
-                    if (r < c1) {
-                        keep = series_lb(ld_stream_u4(ix.sax + r), tab, card) <= thr;
-                        ++n_lb;
-                    }
-                    const unsigned mask = __ballot_sync(FULL, keep);
-                    int wbase = 0;
-                    if (lane == 0 && mask) wbase = atomicAdd(&nsurv, __popc(mask));
-                    wbase = __shfl_sync(FULL, wbase, 0);
-                    if (keep) surv[wbase + __popc(mask & lt)] = (uint16_t)(r - c0);
-                }
-                __syncthreads();
-                const int ns = nsurv;
-                for (int t = warp; t < ns; t += nwarps) {
-                    const int64_t r = c0 + surv[t];
-                    float lim = 0.0f;
-                    if (lane == 0) lim = abandon_limit(ld_volatile_u64(&s.topk[k - 1]), delta);
-                    lim = __shfl_sync(FULL, lim, 0);
-                    bool ab;
-                    const float d2 = warp_d2<NV>(ix, r, qv, s.q, lim, ab);
-                    if (lane == 0) {
+        if (s.leaf_lb[leaf] > thr) continue;
+        ++n_scan;
+        const int64_t lbeg = ix.leaf_begin[leaf], lend = ix.leaf_begin[leaf + 1];
+        for (int64_t b = lbeg; b < lend; b += SCAN_UNIT) {
+            const int64_t e = b + SCAN_UNIT < lend ? b + SCAN_UNIT : lend;
+            uint4 w[SR_WORDS];
+#pragma unroll
+            for (int j = 0; j < SR_WORDS; ++j) {
+                const int64_t r = b + j * 32 + lane;
+                w[j] = r < e ? ld_stream_u4(ix.sax + r) : make_uint4(0, 0, 0, 0);
+            }
+            unsigned mk[SR_WORDS];
+#pragma unroll
+            for (int j = 0; j < SR_WORDS; ++j) {
+                const bool ok = b + j * 32 + lane < e;
+                n_lb += ok ? 1 : 0;
+                mk[j] = __ballot_sync(FULL, ok && series_lb(w[j], tab, card) <= thr);
+            }
+#pragma unroll 1
+            for (int j = 0; j < SR_WORDS; ++j) {
+                unsigned mm = mk[j];
+                while (mm) {
+                    const int l0 = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const int64_t r0 = b + j * 32 + l0;
+                    if constexpr (NV > 0 && NV <= 2) {
+                        const bool two = mm != 0;
+                        int64_t r1 = r0;
+                        if (two) {
+                            r1 = b + j * 32 + (__ffs(mm) - 1);
+                            mm &= mm - 1;
+                        }
+                        float d0, d1;
+                        warp_d2_two<NQ>(ix, r0, r1, two, qv, d0, d1);
+                        n_ref += two ? 2 : 1;
+                        push(d0, r0);
+                        if (two) push(d1, r1);
+                    } else {
+                        bool ab;
+                        const float d0 = warp_d2<NV>(ix, r0, qv, s.q, lim_ab, ab);
                         ++n_ref;
-                        if (!ab) consider(s, k, pack_key(d2, ix.orig[r]), (uint32_t)r, delta);
+                        if (!ab) push(d0, r0);
                     }
                 }
-                __syncthreads();
-                if (tid == 0) thr_s = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), delta, E);
             }
         }
-        __syncthreads();
     }
-    if (n_lb) atomicAdd(&c->series_lb, n_lb);
-    if (lane == 0 && n_ref) atomicAdd(&c->series_refined, n_ref);
-    if (tid == 0 && n_scan) atomicAdd(&c->leaves_scanned, n_scan);
+    flush();
+    if (lane == 0) {
+        if (n_ref) atomicAdd(&c->series_refined, n_ref);
+        if (n_scan) atomicAdd(&c->leaves_scanned, n_scan);
+    }
+#pragma unroll
+    for (int off2 = 16; off2 > 0; off2 >>= 1) n_lb += __shfl_xor_sync(FULL, n_lb, off2);
+    if (lane == 0 && n_lb) atomicAdd(&c->series_lb, n_lb);
 }
 
 // ---------------------------------------------------------------- q_finalize
-constexpr int FIN_THREADS = 1024, FIN_CAP = 2 * FIN_THREADS;
+constexpr int FIN_THREADS = 1024, FIN_WARPS = FIN_THREADS / 32, FIN_CAP = 2 * FIN_THREADS;
 
 __device__ __forceinline__ bool key_greater(unsigned long long a, uint32_t ia, unsigned long long b,
                                             uint32_t ib) {
     return a > b || (a == b && ia > ib);
 }
 
+// FP64 squared distance with the definition's order: sum_j (x_j - q_j)^2, j
+// ascending, no fused multiply-add.  The warp loads 32 elements at a time and
+// every lane runs the same sequential sum over shuffled values.
+__device__ __forceinline__ double warp_d2_fp64_seq(const float* __restrict__ xr,
+                                                   const float* __restrict__ q, int n) {
+    const int lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int t = 0; t < n; t += 32) {
+        const float xv = t + lane < n ? xr[t + lane] : 0.0f;
+        const float qq = t + lane < n ? q[t + lane] : 0.0f;
+        const int cnt = n - t < 32 ? n - t : 32;
+        for (int l = 0; l < cnt; ++l) {
+            const double xj = (double)__shfl_sync(FULL, xv, l);
+            const double qj = (double)__shfl_sync(FULL, qq, l);
+            const double d = __dsub_rn(xj, qj);
+            acc = __dadd_rn(acc, __dmul_rn(d, d));
+        }
+    }
+    return acc;
+}
+
 __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, QueryScratch s, int k) {
     __shared__ unsigned long long sk[FIN_CAP];
     __shared__ uint32_t sid[FIN_CAP];
+    __shared__ uint32_t stage[FIN_THREADS];
     __shared__ int nst;
     QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long kth = s.topk[k - 1];
     if (kth == EMPTY_SLOT) {
         if (tid == 0) c->flags |= QF_SHORT;
@@ -495,24 +650,18 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
         if (tid == 0) nst = 0;
         __syncthreads();
         const uint32_t i = base + tid;
-        if (i < M) {
-            const unsigned long long key = s.cand_key[i];
-            if ((double)key_d2(key) <= bound) {
-                const int p = cnt + atomicAdd(&nst, 1);
-                const uint32_t pos = s.cand_pos[i];
-                const float* xr = ix.x + (int64_t)pos * n;
-                double acc = 0.0;  // the definition: sum_j (x_j - q_j)^2, left to right
-                for (int j = 0; j < n; ++j) {
-                    const double d = __dsub_rn((double)xr[j], (double)s.q[j]);
-                    acc = __dadd_rn(acc, __dmul_rn(d, d));
-                }
-                sk[p] = (unsigned long long)__double_as_longlong(acc);
-                sid[p] = ix.orig[pos];
-            }
-        }
+        if (i < M && (double)key_d2(s.cand_key[i]) <= bound) stage[atomicAdd(&nst, 1)] = s.cand_pos[i];
         __syncthreads();
         const int added = nst;
         if (added == 0) continue;
+        for (int e = warp; e < added; e += FIN_WARPS) {
+            const uint32_t pos = stage[e];
+            const double d = warp_d2_fp64_seq(ix.x + (int64_t)pos * n, s.q, n);
+            if (lane == 0) {
+                sk[cnt + e] = (unsigned long long)__double_as_longlong(d);
+                sid[cnt + e] = ix.orig[pos];
+            }
+        }
         window += added;
         const int total = cnt + added;
         int P = 1;
@@ -529,10 +678,10 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
                     const int b = a + stride;
                     const bool asc = (a & size) == 0;
                     if (key_greater(sk[a], sid[a], sk[b], sid[b]) == asc) {
-                        unsigned long long tk = sk[a];
+                        const unsigned long long tk = sk[a];
                         sk[a] = sk[b];
                         sk[b] = tk;
-                        uint32_t ti = sid[a];
+                        const uint32_t ti = sid[a];
                         sid[a] = sid[b];
                         sid[b] = ti;
                     }
@@ -599,103 +748,67 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
 
 namespace {
 
+int occupancy_grid(const void* fn, int threads, size_t smem, int num_sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return per_sm * num_sms;
+}
+
 template <int NV>
-void launch_query_kernels(isax_index* ix, int k, cudaStream_t st) {
+void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st) {
     const DevIndex& d = ix->d;
-    const QueryScratch& s = ix->qs;
     const size_t tab_bytes = sizeof(float) * W * d.card;
     {
-    ISAX_LAUNCH("q_prep", st);
-    q_prep_kernel<<<1, 256, 0, st>>>(d, s, k);
+        ISAX_LAUNCH("q_prep", st);
+        q_prep_kernel<<<1, PREP_THREADS, 0, st>>>(d, s, k);
     }
     const int approx_blocks = std::max(1, std::min(ix->num_sms, (d.leaf_size + 7) / 8));
     {
-    ISAX_LAUNCH("q_approx", st);
-    q_approx_kernel<NV><<<approx_blocks, 256, 0, st>>>(d, s, k);
+        ISAX_LAUNCH("q_approx", st);
+        q_approx_kernel<NV><<<approx_blocks, 256, 0, st>>>(d, s, k);
     }
-    const unsigned lb_blocks = (unsigned)((d.L + 255) / 256);
+    const unsigned lb_blocks = (unsigned)std::min<int64_t>((d.L + 255) / 256, (int64_t)ix->num_sms * 8);
     {
-    ISAX_LAUNCH("q_leaf_lb", st);
-    q_leaf_lb_kernel<<<lb_blocks, 256, tab_bytes, st>>>(d, s, k);
-    }
-    {
-    ISAX_LAUNCH("q_leaf_scatter", st);
-    q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
+        ISAX_LAUNCH("q_leaf_lb", st);
+        q_leaf_lb_kernel<<<lb_blocks, 256, 0, st>>>(d, s, k);
     }
     {
-    ISAX_LAUNCH("q_scan_refine", st);
-    q_scan_refine_kernel<NV><<<ix->num_sms * 2, SR_THREADS, tab_bytes, st>>>(d, s, k);
+        ISAX_LAUNCH("q_leaf_scatter", st);
+        q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
     }
     {
-    ISAX_LAUNCH("q_finalize", st);
-    q_finalize_kernel<<<1, FIN_THREADS, 0, st>>>(d, s, k);
+        static int grid = 0;
+        if (!grid)
+            grid = occupancy_grid((const void*)q_scan_refine_kernel<NV>, SR_THREADS, tab_bytes,
+                                  ix->num_sms);
+        ISAX_LAUNCH("q_scan_refine", st);
+        q_scan_refine_kernel<NV><<<grid, SR_THREADS, tab_bytes, st>>>(d, s, k);
+    }
+    {
+        ISAX_LAUNCH("q_finalize", st);
+        q_finalize_kernel<<<1, FIN_THREADS, 0, st>>>(d, s, k);
     }
     ISAX_CUDA_TRY(cudaGetLastError());
-}
-
-void launch_query(isax_index* ix, int k, cudaStream_t st) {
-    const int n = ix->d.n;
-    if (n % 128 == 0) {
-        switch (n / 128) {
-            case 1: return launch_query_kernels<1>(ix, k, st);
-            case 2: return launch_query_kernels<2>(ix, k, st);
-            case 4: return launch_query_kernels<4>(ix, k, st);
-            case 8: return launch_query_kernels<8>(ix, k, st);
-            default: break;
-        }
-    }
-    launch_query_kernels<0>(ix, k, st);
 }
 
 }  // namespace
 
-// Same launch sequence as launch_query, on caller-provided scratch (used by
-// the entry point that must not allocate; see isax_noalloc.cu).
-template <int NV>
-static void launch_query_kernels_on(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st) {
-    const DevIndex& d = ix->d;
-    const size_t tab_bytes = sizeof(float) * W * d.card;
-    {
-    ISAX_LAUNCH("q_prep", st);
-    q_prep_kernel<<<1, 256, 0, st>>>(d, s, k);
-    }
-    const int approx_blocks = std::max(1, std::min(ix->num_sms, (d.leaf_size + 7) / 8));
-    {
-    ISAX_LAUNCH("q_approx", st);
-    q_approx_kernel<NV><<<approx_blocks, 256, 0, st>>>(d, s, k);
-    }
-    const unsigned lb_blocks = (unsigned)((d.L + 255) / 256);
-    {
-    ISAX_LAUNCH("q_leaf_lb", st);
-    q_leaf_lb_kernel<<<lb_blocks, 256, tab_bytes, st>>>(d, s, k);
-    }
-    {
-    ISAX_LAUNCH("q_leaf_scatter", st);
-    q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
-    }
-    {
-    ISAX_LAUNCH("q_scan_refine", st);
-    q_scan_refine_kernel<NV><<<ix->num_sms * 2, SR_THREADS, tab_bytes, st>>>(d, s, k);
-    }
-    {
-    ISAX_LAUNCH("q_finalize", st);
-    q_finalize_kernel<<<1, FIN_THREADS, 0, st>>>(d, s, k);
-    }
-    ISAX_CUDA_TRY(cudaGetLastError());
-}
-
+// The query's kernels on the given scratch (the index's own, or the
+// allocation-free entry point's built-in array).
 void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st) {
     const int n = ix->d.n;
     if (n % 128 == 0) {
         switch (n / 128) {
-            case 1: return launch_query_kernels_on<1>(ix, s, k, st);
-            case 2: return launch_query_kernels_on<2>(ix, s, k, st);
-            case 4: return launch_query_kernels_on<4>(ix, s, k, st);
-            case 8: return launch_query_kernels_on<8>(ix, s, k, st);
+            case 1: return launch_query_kernels<1>(ix, s, k, st);
+            case 2: return launch_query_kernels<2>(ix, s, k, st);
+            case 4: return launch_query_kernels<4>(ix, s, k, st);
+            case 8: return launch_query_kernels<8>(ix, s, k, st);
             default: break;
         }
     }
-    launch_query_kernels_on<0>(ix, s, k, st);
+    launch_query_kernels<0>(ix, s, k, st);
 }
 
 // One exact k-NN query; q is already in ix->qs.q.  Results land in
@@ -703,7 +816,7 @@ void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaS
 void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st) {
     *reruns = 0;
     for (int attempt = 0;; ++attempt) {
-        launch_query(ix, k, st);
+        launch_query_on_scratch(ix, ix->qs, k, st);
         ISAX_CUDA_TRY(cudaMemcpyAsync(ctl_out, ix->qs.ctl, sizeof(QCtl), cudaMemcpyDeviceToHost, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         if (ctl_out->flags & QF_NONFINITE) throw Error{ISAX_ERR_INVALID_ARG, "query contains a non-finite value"};
