@@ -281,7 +281,8 @@ def main():
     torch.cuda.synchronize()
 
     lat_ms = []
-    stats_acc = {"series_lb": 0, "series_refined": 0, "approx_series": 0}
+    stats_acc = {"series_lb": 0, "series_refined": 0, "approx_series": 0, "leaves_queued": 0,
+                 "leaves_scanned": 0, "candidates": 0, "window": 0}
 
     def step(record):
         ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp)
@@ -369,8 +370,7 @@ def main():
         "query_qps": len(lat_ms) / (q_time_ms / 1e3) if q_time_ms else None,
         "build_ms": build_ms, "build_input_GB_per_s": N * n * 4 / 1e9 / (build_ms / 1e3),
         "index": {"leaves": info["leaves"], "max_leaf": info["max_leaf"]},
-        "pruning": {"series_lb_per_query": stats_acc["series_lb"] / max(1, len(lat_ms)),
-                    "series_refined_per_query": stats_acc["series_refined"] / max(1, len(lat_ms))},
+        "pruning": {key + "_per_query": stats_acc[key] / max(1, len(lat_ms)) for key in stats_acc},
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": clock_info,

@@ -81,7 +81,8 @@ struct QCtl {
     int32_t approx_end;
     uint8_t qsym[16];      // query symbols
     uint32_t work_count;   // queued leaves
-    uint32_t work_next;    // Fetch&Inc claim counter
+    uint32_t work_next;    // Fetch&Inc claim counter of the first wave
+    uint32_t work_next2;   // ... and of the second
     uint32_t cand_count;   // candidate appends attempted (may exceed capacity)
     uint32_t window;       // candidates re-ranked in FP64
     uint32_t flags;        // QF_* bits

@@ -201,6 +201,7 @@ __device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ ta
 
 // ---------------------------------------------------------------- q_prep
 constexpr int PREP_THREADS = 256;
+constexpr int APPROX_NEIGHBORS = 2;
 
 __global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, QueryScratch s, int k) {
     __shared__ float bp[MAX_CARD + 1];
@@ -281,8 +282,11 @@ __global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, Query
         c->qkey = key;
         const int64_t ub = lo + cnt_s;
         const int64_t dl = ub > 0 ? ub - 1 : 0;
-        // approximate-answer range: that leaf, widened until it holds >= k series
-        int64_t a0 = dl, a1 = dl + 1;
+        // approximate-answer range: that leaf and its APPROX_NEIGHBORS neighbours on
+        // each side in key order (the nearest iSAX words), widened until it holds
+        // >= k series
+        int64_t a0 = dl - APPROX_NEIGHBORS > 0 ? dl - APPROX_NEIGHBORS : 0;
+        int64_t a1 = dl + 1 + APPROX_NEIGHBORS < L ? dl + 1 + APPROX_NEIGHBORS : L;
         int64_t tot = (int64_t)ix.leaf_begin[a1] - ix.leaf_begin[a0];
         while (tot < k) {
             if (a1 < L) {
@@ -301,6 +305,7 @@ __global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, Query
         c->approx_end = (int32_t)a1;
         c->work_count = 0;
         c->work_next = 0;
+        c->work_next2 = 0;
         c->cand_count = 0;
         c->window = 0;
         c->flags = bad ? QF_NONFINITE : 0u;
@@ -430,6 +435,8 @@ __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, Quer
 // ---------------------------------------------------------------- q_scan_refine
 constexpr int SR_THREADS = NBINS;                 // one thread per bin for the offset scan
 constexpr int SR_WORDS = SCAN_UNIT / 32;          // SAX words per lane per round
+constexpr int SR_BATCH = 8;                       // refined distances per k-best update
+constexpr uint32_t SR_WAVE0 = 256;                // leaves of the narrow first wave
 
 // squared distances of two rows (second one optional) with all loads issued first
 template <int NV>
@@ -469,7 +476,8 @@ __device__ __forceinline__ void warp_d2_two(const DevIndex& ix, int64_t r0, int6
 // a time, and hands each batch of up to 32 distances to the k-best update
 // after one filter against the current k-th best.  No block barriers.
 template <int NV>
-__global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k) {
+__global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k,
+                                                                      int wave, uint32_t wave_items) {
     extern __shared__ float tab[];
     __shared__ uint32_t off[NBINS + 1];
     __shared__ uint32_t scratch[32];
@@ -489,7 +497,11 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
     float4 qv[NQ];
     load_q<NV>(s.q, qv);
     const double delta = c->delta, E = c->E;
-    const uint32_t work_count = c->work_count;
+    // wave 0: positions [0, wave_items); wave 1: the rest, with its own counter
+    const uint32_t item0 = wave == 0 ? 0u : wave_items;
+    const uint32_t item1 = wave == 0 ? (c->work_count < wave_items ? c->work_count : wave_items)
+                                     : c->work_count;
+    uint32_t* counter = wave == 0 ? &c->work_next : &c->work_next2;
     const float thr0 = c->thr_lb0;
     unsigned long long kth_seen = 0;
     float thr = 0.0f, lim_ab = INFINITY;
@@ -517,13 +529,13 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
             my_pos = (uint32_t)r;
         }
         ++nb;
-        if (nb == 32) flush();
+        if (nb == SR_BATCH) flush();
     };
     for (;;) {
         uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(&c->work_next, 1u);
+        if (lane == 0) item = item0 + atomicAdd(counter, 1u);
         item = __shfl_sync(FULL, item, 0);
-        if (item >= work_count) break;
+        if (item >= item1) break;
         while (wb < NBINS - 1 && off[wb + 1] <= item) ++wb;
         unsigned long long kth = 0;
         if (lane == 0) kth = ld_volatile_u64(&s.topk[k - 1]);
@@ -626,6 +638,31 @@ __device__ __forceinline__ double warp_d2_fp64_seq(const float* __restrict__ xr,
     return acc;
 }
 
+__device__ __forceinline__ void bitonic_sort_smem(unsigned long long* sk, uint32_t* sid, int P) {
+    const int tid = threadIdx.x;
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = tid; t < P / 2; t += FIN_THREADS) {
+                const int a = 2 * t - (t & (stride - 1));
+                const int b = a + stride;
+                const bool asc = (a & size) == 0;
+                if (key_greater(sk[a], sid[a], sk[b], sid[b]) == asc) {
+                    const unsigned long long tk = sk[a];
+                    sk[a] = sk[b];
+                    sk[b] = tk;
+                    const uint32_t ti = sid[a];
+                    sid[a] = sid[b];
+                    sid[b] = ti;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Candidates within (1 + 3 delta) of the final k-th best (the window) are
+// re-ranked in FP64 by (d2, row).  One filter pass stages the window; a window
+// larger than the stage is processed in rounds, merging a running top-k.
 __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, QueryScratch s, int k) {
     __shared__ unsigned long long sk[FIN_CAP];
     __shared__ uint32_t sid[FIN_CAP];
@@ -644,59 +681,73 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
     const uint32_t attempted = c->cand_count;
     const uint32_t M = attempted < s.cand_cap ? attempted : s.cand_cap;
     const int n = ix.n;
+    if (tid == 0) nst = 0;
+    __syncthreads();
+    // one pass over all candidates: count the window, stage it if it fits
+    for (uint32_t i = tid; i < M; i += FIN_THREADS) {
+        if ((double)key_d2(s.cand_key[i]) <= bound) {
+            const int p = atomicAdd(&nst, 1);
+            if (p < FIN_THREADS) stage[p] = s.cand_pos[i];
+        }
+    }
+    __syncthreads();
+    const int window = nst;
     int cnt = 0;
-    uint32_t window = 0;
-    for (uint32_t base = 0; base < M; base += FIN_THREADS) {
-        if (tid == 0) nst = 0;
-        __syncthreads();
-        const uint32_t i = base + tid;
-        if (i < M && (double)key_d2(s.cand_key[i]) <= bound) stage[atomicAdd(&nst, 1)] = s.cand_pos[i];
-        __syncthreads();
-        const int added = nst;
-        if (added == 0) continue;
-        for (int e = warp; e < added; e += FIN_WARPS) {
+    if (window <= FIN_THREADS) {
+        for (int e = warp; e < window; e += FIN_WARPS) {
             const uint32_t pos = stage[e];
             const double d = warp_d2_fp64_seq(ix.x + (int64_t)pos * n, s.q, n);
             if (lane == 0) {
-                sk[cnt + e] = (unsigned long long)__double_as_longlong(d);
-                sid[cnt + e] = ix.orig[pos];
+                sk[e] = (unsigned long long)__double_as_longlong(d);
+                sid[e] = ix.orig[pos];
             }
         }
-        window += added;
-        const int total = cnt + added;
         int P = 1;
-        while (P < total) P <<= 1;
-        for (int t = total + tid; t < P; t += FIN_THREADS) {
+        while (P < window) P <<= 1;
+        for (int t = window + tid; t < P; t += FIN_THREADS) {
             sk[t] = EMPTY_SLOT;
             sid[t] = 0xffffffffu;
         }
         __syncthreads();
-        for (int size = 2; size <= P; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int t = tid; t < P / 2; t += FIN_THREADS) {
-                    const int a = 2 * t - (t & (stride - 1));
-                    const int b = a + stride;
-                    const bool asc = (a & size) == 0;
-                    if (key_greater(sk[a], sid[a], sk[b], sid[b]) == asc) {
-                        const unsigned long long tk = sk[a];
-                        sk[a] = sk[b];
-                        sk[b] = tk;
-                        const uint32_t ti = sid[a];
-                        sid[a] = sid[b];
-                        sid[b] = ti;
-                    }
+        bitonic_sort_smem(sk, sid, P);
+        cnt = window < k ? window : k;
+    } else {
+        // large window (many exact ties): rounds of FIN_THREADS candidates
+        for (uint32_t base = 0; base < M; base += FIN_THREADS) {
+            __syncthreads();
+            if (tid == 0) nst = 0;
+            __syncthreads();
+            const uint32_t i = base + tid;
+            if (i < M && (double)key_d2(s.cand_key[i]) <= bound) stage[atomicAdd(&nst, 1)] = s.cand_pos[i];
+            __syncthreads();
+            const int added = nst;
+            if (added == 0) continue;
+            for (int e = warp; e < added; e += FIN_WARPS) {
+                const uint32_t pos = stage[e];
+                const double d = warp_d2_fp64_seq(ix.x + (int64_t)pos * n, s.q, n);
+                if (lane == 0) {
+                    sk[cnt + e] = (unsigned long long)__double_as_longlong(d);
+                    sid[cnt + e] = ix.orig[pos];
                 }
-                __syncthreads();
             }
+            const int total = cnt + added;
+            int P = 1;
+            while (P < total) P <<= 1;
+            for (int t = total + tid; t < P; t += FIN_THREADS) {
+                sk[t] = EMPTY_SLOT;
+                sid[t] = 0xffffffffu;
+            }
+            __syncthreads();
+            bitonic_sort_smem(sk, sid, P);
+            cnt = total < k ? total : k;
         }
-        cnt = total < k ? total : k;
     }
     if (tid < cnt) {
         s.out_idx[tid] = (int64_t)sid[tid];
         s.out_dist[tid] = __double2float_rn(sqrt(__longlong_as_double((long long)sk[tid])));
     }
     if (tid == 0) {
-        c->window = window;
+        c->window = (uint32_t)window;
         if (cnt < k) c->flags |= QF_SHORT;
         if (attempted > s.cand_cap) c->flags |= QF_OVERFLOW;
     }
@@ -779,12 +830,19 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
         q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
     }
     {
+        // the lowest-bound leaves first, one warp each, so the k-th best tightens
+        // before the whole GPU scans with it
+        ISAX_LAUNCH("q_scan_refine", st);
+        q_scan_refine_kernel<NV><<<SR_WAVE0 / (SR_THREADS / 32), SR_THREADS, tab_bytes, st>>>(
+            d, s, k, 0, SR_WAVE0);
+    }
+    {
         static int grid = 0;
         if (!grid)
             grid = occupancy_grid((const void*)q_scan_refine_kernel<NV>, SR_THREADS, tab_bytes,
                                   ix->num_sms);
         ISAX_LAUNCH("q_scan_refine", st);
-        q_scan_refine_kernel<NV><<<grid, SR_THREADS, tab_bytes, st>>>(d, s, k);
+        q_scan_refine_kernel<NV><<<grid, SR_THREADS, tab_bytes, st>>>(d, s, k, 1, SR_WAVE0);
     }
     {
         ISAX_LAUNCH("q_finalize", st);
