@@ -66,6 +66,12 @@ isax_status isax_profile(int32_t enable) {
             g_pool.push_back(r.e1);
         }
         g_records.clear();
+        // create the events now, so no event is created while launches are timed
+        while (g_pool.size() < 16384) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) break;
+            g_pool.push_back(e);
+        }
     }
     g_on.store(enable != 0);
     return ISAX_OK;

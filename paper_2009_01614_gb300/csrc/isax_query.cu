@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, Quer
 constexpr int SR_THREADS = NBINS;                 // one thread per bin for the offset scan
 constexpr int SR_WORDS = SCAN_UNIT / 32;          // SAX words per lane per round
 constexpr int SR_BATCH = 8;                       // refined distances per k-best update
-constexpr uint32_t SR_WAVE0 = 256;                // leaves of the narrow first wave
+constexpr uint32_t SR_WAVE0 = 0;                  // leaves of an optional narrow first wave
 
 // squared distances of two rows (second one optional) with all loads issued first
 template <int NV>
@@ -468,31 +468,43 @@ __device__ __forceinline__ void warp_d2_two(const DevIndex& ix, int64_t r0, int6
     d1 = warp_sum_f(a1);
 }
 
-// Persistent warps: each claims the next queued leaf (Fetch&Inc over the
-// list, which is in ascending bound-bin order), skips it if its bound now
-// exceeds the threshold, stops for good once the bin of the claimed position
-// lies wholly above the threshold, else bounds the leaf's SAX words 256 at a
-// time (all loads of a round issued first), refines the survivors two rows at
-// a time, and hands each batch of up to 32 distances to the k-best update
-// after one filter against the current k-th best.  No block barriers.
+// Persistent CTAs claim queued leaves with Fetch&Inc (the list is in
+// ascending bound-bin order).  A claimed leaf whose bound now exceeds the
+// threshold is skipped; once the bin of the claimed position lies wholly above
+// the threshold the CTA stops (every later leaf is in a higher bin).  A leaf is
+// processed in rounds of up to 8 x 256 series: each warp bounds one 256-series
+// chunk (16-byte SAX words, all loads issued first, 16 table lookups each),
+// survivors go to a shared list, and all warps refine them two rows at a time,
+// handing each batch of distances to the k-best update after one filter
+// against the current k-th best.
+constexpr int SR_WARPS = SR_THREADS / 32;
+constexpr int SR_ROUND = SR_WARPS * SCAN_UNIT;    // series per leaf round
+
 template <int NV>
 __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k,
                                                                       int wave, uint32_t wave_items) {
     extern __shared__ float tab[];
     __shared__ uint32_t off[NBINS + 1];
     __shared__ uint32_t scratch[32];
+    __shared__ uint16_t surv[SR_ROUND];
+    __shared__ int nsurv;
+    __shared__ uint32_t item_s;
+    __shared__ float thr_s, lim_s;
+    __shared__ unsigned long long kth_s;
     QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
     const int card = ix.card;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < W * card; e += SR_THREADS) tab[e] = s.table[e];
     {
         uint32_t tot;
         const uint32_t o = block_excl_scan<uint32_t>(s.bin_count[tid], 0u, OpAdd<uint32_t>(), scratch, &tot);
         off[tid] = o;
-        if (tid == 0) off[NBINS] = tot;
+        if (tid == 0) {
+            off[NBINS] = tot;
+            kth_s = 0;
+        }
     }
-    __syncthreads();
     constexpr int NQ = NV ? NV : 1;
     float4 qv[NQ];
     load_q<NV>(s.q, qv);
@@ -503,12 +515,9 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
                                      : c->work_count;
     uint32_t* counter = wave == 0 ? &c->work_next : &c->work_next2;
     const float thr0 = c->thr_lb0;
-    unsigned long long kth_seen = 0;
-    float thr = 0.0f, lim_ab = INFINITY;
-    bool have = false;
     int wb = 0;
     unsigned long long n_lb = 0, n_ref = 0, n_scan = 0;
-    // batch of refined distances: entry i held by lane i
+    // batch of refined distances of this warp: entry i held by lane i
     float my_d2 = INFINITY;
     uint32_t my_pos = 0;
     int nb = 0;
@@ -531,59 +540,67 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
         ++nb;
         if (nb == SR_BATCH) flush();
     };
+    __syncthreads();
     for (;;) {
-        uint32_t item = 0;
-        if (lane == 0) item = item0 + atomicAdd(counter, 1u);
-        item = __shfl_sync(FULL, item, 0);
+        if (tid == 0) {
+            item_s = item0 + atomicAdd(counter, 1u);
+            const unsigned long long kth = ld_volatile_u64(&s.topk[k - 1]);
+            if (kth != kth_s || kth == 0) {
+                kth_s = kth;
+                thr_s = lb_threshold(kth, delta, E);
+                lim_s = abandon_limit(kth, delta);
+            }
+        }
+        __syncthreads();
+        const uint32_t item = item_s;
+        const float thr = thr_s;
         if (item >= item1) break;
         while (wb < NBINS - 1 && off[wb + 1] <= item) ++wb;
-        unsigned long long kth = 0;
-        if (lane == 0) kth = ld_volatile_u64(&s.topk[k - 1]);
-        kth = __shfl_sync(FULL, kth, 0);
-        if (!have || kth != kth_seen) {
-            thr = lb_threshold(kth, delta, E);
-            lim_ab = abandon_limit(kth, delta);
-            kth_seen = kth;
-            have = true;
-        }
         // every later position is in bin >= wb, whose bounds are >= thr0 (wb/NBINS)^2
         if (thr0 > 0.0f && !isinf(thr0)) {
             const float edge = (float)wb / (float)NBINS;
             if (thr0 * edge * edge * 0.99999f > thr) break;
         }
         const uint32_t leaf = s.work[item];
-        if (s.leaf_lb[leaf] > thr) continue;
-        ++n_scan;
-        const int64_t lbeg = ix.leaf_begin[leaf], lend = ix.leaf_begin[leaf + 1];
-        for (int64_t b = lbeg; b < lend; b += SCAN_UNIT) {
-            const int64_t e = b + SCAN_UNIT < lend ? b + SCAN_UNIT : lend;
-            uint4 w[SR_WORDS];
+        if (s.leaf_lb[leaf] <= thr) {
+            if (tid == 0) ++n_scan;
+            const int64_t lbeg = ix.leaf_begin[leaf], lend = ix.leaf_begin[leaf + 1];
+            for (int64_t rb = lbeg; rb < lend; rb += SR_ROUND) {
+                if (tid == 0) nsurv = 0;
+                __syncthreads();
+                const float thr_r = thr_s;
+                // bound: warp w takes series [rb + w*256, rb + (w+1)*256)
+                const int64_t b = rb + (int64_t)warp * SCAN_UNIT;
+                const int64_t e = b + SCAN_UNIT < lend ? b + SCAN_UNIT : lend;
+                if (b < lend) {
+                    uint4 w[SR_WORDS];
 #pragma unroll
-            for (int j = 0; j < SR_WORDS; ++j) {
-                const int64_t r = b + j * 32 + lane;
-                w[j] = r < e ? ld_stream_u4(ix.sax + r) : make_uint4(0, 0, 0, 0);
-            }
-            unsigned mk[SR_WORDS];
+                    for (int j = 0; j < SR_WORDS; ++j) {
+                        const int64_t r = b + j * 32 + lane;
+                        w[j] = r < e ? ld_stream_u4(ix.sax + r) : make_uint4(0, 0, 0, 0);
+                    }
 #pragma unroll
-            for (int j = 0; j < SR_WORDS; ++j) {
-                const bool ok = b + j * 32 + lane < e;
-                n_lb += ok ? 1 : 0;
-                mk[j] = __ballot_sync(FULL, ok && series_lb(w[j], tab, card) <= thr);
-            }
-#pragma unroll 1
-            for (int j = 0; j < SR_WORDS; ++j) {
-                unsigned mm = mk[j];
-                while (mm) {
-                    const int l0 = __ffs(mm) - 1;
-                    mm &= mm - 1;
-                    const int64_t r0 = b + j * 32 + l0;
+                    for (int j = 0; j < SR_WORDS; ++j) {
+                        const int64_t r = b + j * 32 + lane;
+                        const bool ok = r < e;
+                        n_lb += ok ? 1 : 0;
+                        const bool keep = ok && series_lb(w[j], tab, card) <= thr_r;
+                        const unsigned mk = __ballot_sync(FULL, keep);
+                        int base = 0;
+                        if (lane == 0 && mk) base = atomicAdd(&nsurv, __popc(mk));
+                        base = __shfl_sync(FULL, base, 0);
+                        if (keep) surv[base + __popc(mk & ((1u << lane) - 1u))] = (uint16_t)(r - rb);
+                    }
+                }
+                __syncthreads();
+                const int ns = nsurv;
+                const float lim_ab = lim_s;
+                // refine: warp w takes survivor pairs (2w, 2w+1), then the next 16, ...
+                for (int t = 2 * warp; t < ns; t += 2 * SR_WARPS) {
+                    const int64_t r0 = rb + surv[t];
+                    const bool two = t + 1 < ns;
                     if constexpr (NV > 0 && NV <= 2) {
-                        const bool two = mm != 0;
-                        int64_t r1 = r0;
-                        if (two) {
-                            r1 = b + j * 32 + (__ffs(mm) - 1);
-                            mm &= mm - 1;
-                        }
+                        const int64_t r1 = two ? rb + surv[t + 1] : r0;
                         float d0, d1;
                         warp_d2_two<NQ>(ix, r0, r1, two, qv, d0, d1);
                         n_ref += two ? 2 : 1;
@@ -594,16 +611,31 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
                         const float d0 = warp_d2<NV>(ix, r0, qv, s.q, lim_ab, ab);
                         ++n_ref;
                         if (!ab) push(d0, r0);
+                        if (two) {
+                            const int64_t r1 = rb + surv[t + 1];
+                            const float d1 = warp_d2<NV>(ix, r1, qv, s.q, lim_ab, ab);
+                            ++n_ref;
+                            if (!ab) push(d1, r1);
+                        }
+                    }
+                }
+                flush();
+                __syncthreads();
+                if (tid == 0) {
+                    const unsigned long long kth = ld_volatile_u64(&s.topk[k - 1]);
+                    if (kth != kth_s) {
+                        kth_s = kth;
+                        thr_s = lb_threshold(kth, delta, E);
+                        lim_s = abandon_limit(kth, delta);
                     }
                 }
             }
         }
+        __syncthreads();
     }
     flush();
-    if (lane == 0) {
-        if (n_ref) atomicAdd(&c->series_refined, n_ref);
-        if (n_scan) atomicAdd(&c->leaves_scanned, n_scan);
-    }
+    if (lane == 0 && n_ref) atomicAdd(&c->series_refined, n_ref);
+    if (tid == 0 && n_scan) atomicAdd(&c->leaves_scanned, n_scan);
 #pragma unroll
     for (int off2 = 16; off2 > 0; off2 >>= 1) n_lb += __shfl_xor_sync(FULL, n_lb, off2);
     if (lane == 0 && n_lb) atomicAdd(&c->series_lb, n_lb);
@@ -618,24 +650,31 @@ __device__ __forceinline__ bool key_greater(unsigned long long a, uint32_t ia, u
 }
 
 // FP64 squared distance with the definition's order: sum_j (x_j - q_j)^2, j
-// ascending, no fused multiply-add.  The warp loads 32 elements at a time and
-// every lane runs the same sequential sum over shuffled values.
+// ascending, no fused multiply-add.  Lanes form the rounded FP64 squares of 32
+// elements at a time in parallel (staged in `buf`, 32 doubles of this warp);
+// lane 0 then adds them in order, so the sum is the same sequence of FP64
+// additions as the definition.
 __device__ __forceinline__ double warp_d2_fp64_seq(const float* __restrict__ xr,
-                                                   const float* __restrict__ q, int n) {
+                                                   const float* __restrict__ q, int n,
+                                                   double* buf) {
     const int lane = threadIdx.x & 31;
     double acc = 0.0;
     for (int t = 0; t < n; t += 32) {
-        const float xv = t + lane < n ? xr[t + lane] : 0.0f;
-        const float qq = t + lane < n ? q[t + lane] : 0.0f;
-        const int cnt = n - t < 32 ? n - t : 32;
-        for (int l = 0; l < cnt; ++l) {
-            const double xj = (double)__shfl_sync(FULL, xv, l);
-            const double qj = (double)__shfl_sync(FULL, qq, l);
-            const double d = __dsub_rn(xj, qj);
-            acc = __dadd_rn(acc, __dmul_rn(d, d));
+        double sq = 0.0;
+        if (t + lane < n) {
+            const double d = __dsub_rn((double)xr[t + lane], (double)q[t + lane]);
+            sq = __dmul_rn(d, d);
         }
+        buf[lane] = sq;
+        __syncwarp();
+        if (lane == 0) {
+            const int cnt = n - t < 32 ? n - t : 32;
+#pragma unroll 8
+            for (int l = 0; l < cnt; ++l) acc = __dadd_rn(acc, buf[l]);
+        }
+        __syncwarp();
     }
-    return acc;
+    return __shfl_sync(FULL, acc, 0);
 }
 
 __device__ __forceinline__ void bitonic_sort_smem(unsigned long long* sk, uint32_t* sid, int P) {
@@ -667,6 +706,7 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
     __shared__ unsigned long long sk[FIN_CAP];
     __shared__ uint32_t sid[FIN_CAP];
     __shared__ uint32_t stage[FIN_THREADS];
+    __shared__ double sqbuf[FIN_WARPS][32];
     __shared__ int nst;
     QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
@@ -696,7 +736,7 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
     if (window <= FIN_THREADS) {
         for (int e = warp; e < window; e += FIN_WARPS) {
             const uint32_t pos = stage[e];
-            const double d = warp_d2_fp64_seq(ix.x + (int64_t)pos * n, s.q, n);
+            const double d = warp_d2_fp64_seq(ix.x + (int64_t)pos * n, s.q, n, sqbuf[warp]);
             if (lane == 0) {
                 sk[e] = (unsigned long long)__double_as_longlong(d);
                 sid[e] = ix.orig[pos];
@@ -724,7 +764,7 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
             if (added == 0) continue;
             for (int e = warp; e < added; e += FIN_WARPS) {
                 const uint32_t pos = stage[e];
-                const double d = warp_d2_fp64_seq(ix.x + (int64_t)pos * n, s.q, n);
+                const double d = warp_d2_fp64_seq(ix.x + (int64_t)pos * n, s.q, n, sqbuf[warp]);
                 if (lane == 0) {
                     sk[cnt + e] = (unsigned long long)__double_as_longlong(d);
                     sid[cnt + e] = ix.orig[pos];
@@ -829,12 +869,11 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
         ISAX_LAUNCH("q_leaf_scatter", st);
         q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
     }
-    {
-        // the lowest-bound leaves first, one warp each, so the k-th best tightens
+    if (SR_WAVE0 > 0) {
+        // the lowest-bound leaves first, one CTA each, so the k-th best tightens
         // before the whole GPU scans with it
         ISAX_LAUNCH("q_scan_refine", st);
-        q_scan_refine_kernel<NV><<<SR_WAVE0 / (SR_THREADS / 32), SR_THREADS, tab_bytes, st>>>(
-            d, s, k, 0, SR_WAVE0);
+        q_scan_refine_kernel<NV><<<SR_WAVE0, SR_THREADS, tab_bytes, st>>>(d, s, k, 0, SR_WAVE0);
     }
     {
         static int grid = 0;
