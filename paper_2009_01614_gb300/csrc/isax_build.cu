@@ -410,7 +410,7 @@ static int64_t scan_sums_len(int64_t len) { return (len + SC_TILE - 1) / SC_TILE
 // pass: per-tile digit histograms, an exclusive scan over (digit, tile), then
 // a scatter in which every warp ranks its elements with ballots over the digit
 // bits (stable: element order inside a tile is warp, item, lane).
-constexpr int RS_THREADS = 256, RS_ITEMS = 16, RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_THREADS = 256, RS_ITEMS = 8, RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_WARPS = RS_THREADS / 32;
 
 __global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(
@@ -420,41 +420,51 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(
     h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll
     for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
-        int64_t idx = base + i;
+        const int64_t idx = base + i;
         if (idx < N) atomicAdd(&h[(unsigned)(keys[idx] >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// One tile of RS_TILE pairs per block.  Ranks are computed per warp with
+// ballots over the digit bits (stable: tile order is warp, item, lane); the
+// tile is first reordered by digit in shared memory, then written out so that
+// consecutive threads write consecutive positions of each digit's run.
 __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(
     const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
     unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, int64_t N, int shift,
     const uint32_t* __restrict__ offsets, int64_t tiles) {
     __shared__ uint32_t cnt[RS_WARPS][256];
     __shared__ uint32_t tile_off[256];
+    __shared__ uint32_t dstart[256];
+    __shared__ uint32_t scratch[32];
+    __shared__ unsigned long long skey[RS_TILE];
+    __shared__ uint32_t sval[RS_TILE];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     tile_off[threadIdx.x] = offsets[(int64_t)threadIdx.x * tiles + blockIdx.x];
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
     __syncthreads();
-    const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + warp * (RS_ITEMS * 32);
+    const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
+    const int wbase = warp * (RS_ITEMS * 32);
     const unsigned lt = (1u << lane) - 1u;
     unsigned long long k[RS_ITEMS];
     uint32_t local[RS_ITEMS];
 #pragma unroll
     for (int it = 0; it < RS_ITEMS; ++it) {
-        int64_t idx = wbase + it * 32 + lane;
-        bool valid = idx < N;
+        const int64_t idx = tbase + wbase + it * 32 + lane;
+        const bool valid = idx < N;
         k[it] = valid ? kin[idx] : 0ull;
-        unsigned d = (unsigned)(k[it] >> shift) & 255u;
+        const unsigned d = (unsigned)(k[it] >> shift) & 255u;
         unsigned peers = __ballot_sync(FULL, valid);
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-            unsigned bb = __ballot_sync(FULL, (d >> b) & 1u);
+            const unsigned bb = __ballot_sync(FULL, (d >> b) & 1u);
             peers &= ((d >> b) & 1u) ? bb : ~bb;
         }
-        int leader = __ffs(peers) - 1;
+        const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (valid && lane == leader) {
             old = cnt[warp][d];
@@ -465,26 +475,38 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(
         __syncwarp();
     }
     __syncthreads();
-    {   // per digit: exclusive prefix over warps
+    {   // per digit: exclusive prefix over warps, then the tile-local start of each digit
         const int d = threadIdx.x;
-        uint32_t s = 0;
+        uint32_t sum = 0;
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) {
-            uint32_t t = cnt[w][d];
-            cnt[w][d] = s + tile_off[d];
-            s += t;
+            const uint32_t t = cnt[w][d];
+            cnt[w][d] = sum;
+            sum += t;
         }
+        uint32_t tot;
+        dstart[d] = block_excl_scan<uint32_t>(sum, 0u, OpAdd<uint32_t>(), scratch, &tot);
     }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < RS_ITEMS; ++it) {
-        int64_t idx = wbase + it * 32 + lane;
+        const int64_t idx = tbase + wbase + it * 32 + lane;
         if (idx < N) {
-            unsigned d = (unsigned)(k[it] >> shift) & 255u;
-            uint32_t pos = cnt[warp][d] + local[it];
-            kout[pos] = k[it];
-            vout[pos] = vin[idx];
+            const unsigned d = (unsigned)(k[it] >> shift) & 255u;
+            const uint32_t lp = dstart[d] + cnt[warp][d] + local[it];
+            skey[lp] = k[it];
+            sval[lp] = vin[idx];
         }
+    }
+    __syncthreads();
+    const int64_t rem = N - tbase;
+    const int valid_count = rem < RS_TILE ? (int)rem : RS_TILE;
+    for (int i = threadIdx.x; i < valid_count; i += RS_THREADS) {
+        const unsigned long long key = skey[i];
+        const unsigned d = (unsigned)(key >> shift) & 255u;
+        const uint32_t gpos = tile_off[d] + (uint32_t)(i - dstart[d]);
+        kout[gpos] = key;
+        vout[gpos] = sval[i];
     }
 }
 
@@ -626,31 +648,83 @@ __global__ void lf_expand_kernel(const uint32_t* __restrict__ starts, const uint
 }
 
 // ============================================================== permute, envelopes
-// rows, SAX words and original ids gathered into leaf order; one warp per row
-__global__ void __launch_bounds__(256) permute_kernel(const float4* __restrict__ x, int n4,
-                                                      const uint32_t* __restrict__ ids, int64_t N,
-                                                      float4* __restrict__ xp,
-                                                      const uint4* __restrict__ sax_in,
-                                                      uint4* __restrict__ sax_out,
-                                                      uint32_t* __restrict__ orig) {
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t row = gw; row < N; row += nw) {
-        const uint32_t src = ids[row];
-        const float4* s = x + (int64_t)src * n4;
-        float4* d = xp + row * n4;
-        for (int j = lane; j < n4; j += 64) {
-            float4 v0 = ld_stream(s + j);
-            float4 v1;
-            bool two = j + 32 < n4;
-            if (two) v1 = ld_stream(s + j + 32);
-            st_stream(d + j, v0);
-            if (two) st_stream(d + j + 32, v1);
+// Rows, SAX words and original ids gathered into leaf order.  Rows move through
+// the TMA engine: thread 0 of each CTA gathers a batch of rows (16 KB) into one
+// of PM_STAGES shared-memory stages with bulk copies completed on the stage's
+// mbarrier, then writes the whole batch - contiguous in the output - with one
+// bulk store, refilling the stage once that store has read it.  Up to
+// PM_STAGES batches are in flight per CTA.  The other threads copy the SAX
+// words and ids.  Waits are bounded: on a timeout the kernel flags `err`,
+// waits (bounded) for its copies in flight, and returns.
+constexpr int PM_THREADS = 128, PM_STAGES = 4, PM_STAGE_BYTES = 16384;
+constexpr uint32_t PM_MAX_TRIES = 1u << 24;
+
+__global__ void __launch_bounds__(PM_THREADS) permute_kernel(const float* __restrict__ x, int n,
+                                                             const uint32_t* __restrict__ ids,
+                                                             int64_t N, float* __restrict__ xp,
+                                                             const uint4* __restrict__ sax_in,
+                                                             uint4* __restrict__ sax_out,
+                                                             uint32_t* __restrict__ orig,
+                                                             unsigned* err) {
+    extern __shared__ __align__(1024) unsigned char pm_stage[];
+    __shared__ __align__(8) uint64_t bar[PM_STAGES];
+    const uint32_t rowbytes = (uint32_t)n * 4u;
+    const int B = (int)(PM_STAGE_BYTES / rowbytes) > 0 ? (int)(PM_STAGE_BYTES / rowbytes) : 1;
+    // contiguous output range of this CTA, in whole batches
+    const int64_t nbatch_all = (N + B - 1) / B;
+    const int64_t per = (nbatch_all + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = std::min<int64_t>((int64_t)blockIdx.x * per * B, N);
+    const int64_t r1 = std::min<int64_t>(r0 + per * B, N);
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < PM_STAGES; ++st) mbar_init(&bar[st], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int64_t nb = (r1 - r0 + B - 1) / B;
+        auto issue = [&](int64_t b) {
+            const int st = (int)(b % PM_STAGES);
+            const int64_t rb = r0 + b * B;
+            const int rows = (int)std::min<int64_t>(B, r1 - rb);
+            unsigned char* dst = pm_stage + (size_t)st * PM_STAGE_BYTES;
+            mbar_arrive_expect_tx(&bar[st], (uint32_t)rows * rowbytes);
+#pragma unroll 4
+            for (int i = 0; i < rows; ++i) {
+                const uint32_t src = ids[rb + i];
+                bulk_load(dst + (size_t)i * rowbytes, x + (int64_t)src * n, rowbytes, &bar[st]);
+            }
+        };
+        const int64_t pro = nb < PM_STAGES ? nb : PM_STAGES;
+        for (int64_t b = 0; b < pro; ++b) issue(b);
+        int64_t done = 0;
+        for (int64_t b = 0; b < nb; ++b) {
+            const int st = (int)(b % PM_STAGES);
+            const uint32_t parity = (uint32_t)((b / PM_STAGES) & 1);
+            if (!mbar_wait_bounded(&bar[st], parity, PM_MAX_TRIES)) {
+                atomicOr(err, 1u);
+                break;
+            }
+            done = b + 1;
+            fence_proxy_async_smem();
+            const int64_t rb = r0 + b * B;
+            const int rows = (int)std::min<int64_t>(B, r1 - rb);
+            bulk_store(xp + rb * n, pm_stage + (size_t)st * PM_STAGE_BYTES, (uint32_t)rows * rowbytes);
+            bulk_commit();
+            if (b + PM_STAGES < nb) {
+                bulk_wait_read_all();
+                issue(b + PM_STAGES);
+            }
         }
-        if (lane == 0) {
-            sax_out[row] = sax_in[src];
-            orig[row] = src;
+        // loads issued but not awaited (only after a timeout): bounded wait
+        const int64_t issued = nb < done + PM_STAGES ? nb : done + PM_STAGES;
+        for (int64_t b = done; b < issued; ++b)
+            mbar_wait_bounded(&bar[b % PM_STAGES], (uint32_t)((b / PM_STAGES) & 1), PM_MAX_TRIES);
+        bulk_wait_all();
+    } else {
+        for (int64_t r = r0 + threadIdx.x - 1; r < r1; r += PM_THREADS - 1) {
+            const uint32_t src = ids[r];
+            sax_out[r] = sax_in[src];
+            orig[r] = src;
         }
     }
 }
@@ -860,10 +934,16 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         ix->sax = static_cast<uint4*>(dev_alloc((size_t)N * sizeof(uint4), st));
         ix->orig = static_cast<uint32_t*>(dev_alloc((size_t)N * sizeof(uint32_t), st));
         {
+        const size_t pm_smem = (size_t)PM_STAGES * PM_STAGE_BYTES;
+        ISAX_CUDA_TRY(cudaFuncSetAttribute(permute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)pm_smem));
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, permute_kernel, PM_THREADS, pm_smem) !=
+                cudaSuccess || per_sm < 1)
+            per_sm = 1;
         ISAX_LAUNCH("permute", st);
-        permute_kernel<<<grid_for(N, 8, num_sms, 8), 256, 0, st>>>(
-            reinterpret_cast<const float4*>(xin), n / 4, vA, N, reinterpret_cast<float4*>(ix->x),
-            sax_tmp, ix->sax, ix->orig);
+        permute_kernel<<<num_sms * per_sm, PM_THREADS, pm_smem, st>>>(xin, n, vA, N, ix->x, sax_tmp,
+                                                                     ix->sax, ix->orig, misc + 3);
         }
         ISAX_CUDA_TRY(cudaGetLastError());
 
@@ -882,6 +962,7 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         ISAX_CUDA_TRY(cudaMemcpyAsync(hm, misc, sizeof hm, cudaMemcpyDeviceToHost, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         if (hm[1]) throw Error{ISAX_ERR_INVALID_ARG, "series contains a non-finite value"};
+        if (hm[3]) throw Error{ISAX_ERR_TIMEOUT, "a bulk-copy wait of the permutation gave up"};
         float maxabs;
         memcpy(&maxabs, &hm[0], sizeof maxabs);
 
