@@ -199,6 +199,25 @@ __device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ ta
     return lb;
 }
 
+// Series bound in two halves: the 8 segments of `first` (largest mean table
+// entries for this query) are summed first; the other 8 are added only if some
+// lane of the warp is still at or below the threshold.  Either way the sum is
+// a fixed order of the 16 table entries (first half, then second, each by
+// segment index); a lane whose first half already exceeds `thr` is pruned.
+__device__ __forceinline__ bool series_lb_two_phase(uint4 w, const float* __restrict__ tab, int card,
+                                                    uint32_t first, float thr) {
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+    float lb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+        if ((first >> i) & 1u) lb += tab[i * card + ((words[i >> 2] >> (8 * (i & 3))) & 255u)];
+    if (!__any_sync(FULL, lb <= thr)) return false;
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+        if (!((first >> i) & 1u)) lb += tab[i * card + ((words[i >> 2] >> (8 * (i & 3))) & 255u)];
+    return lb <= thr;
+}
+
 // ---------------------------------------------------------------- q_prep
 constexpr int PREP_THREADS = 256;
 constexpr int APPROX_NEIGHBORS = 2;
@@ -249,6 +268,20 @@ __global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, Query
         const float d = v < lo ? lo - v : (v >= hi ? v - hi : 0.0f);
         s.table[e] = (d * d) * mf;
     }
+    __syncthreads();
+    // mean table entry of each segment (symbols are equiprobable under N(0,1))
+    __shared__ float rowsum[W];
+    if (warp < W / 2) {
+        for (int h = 0; h < 2; ++h) {
+            const int i = warp * 2 + h;
+            float acc = 0.0f;
+            for (int sym = lane; sym < card; sym += 32) acc += s.table[i * card + sym];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+            if (lane == 0) rowsum[i] = acc;
+        }
+    }
+    __syncthreads();
     if (tid == 0) {
         unsigned long long key = 0;
         for (int pl = 0; pl < 4; ++pl) {
@@ -323,6 +356,15 @@ __global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, Query
             c->qsym[i] = (uint8_t)qsym[i];
             c->qpaa[i] = qpaa[i];
         }
+        // the 8 segments with the largest mean bound contribution are summed first
+        uint32_t first = 0;
+        for (int r = 0; r < W / 2; ++r) {
+            int best = -1;
+            for (int i = 0; i < W; ++i)
+                if (!((first >> i) & 1u) && (best < 0 || rowsum[i] > rowsum[best])) best = i;
+            first |= 1u << best;
+        }
+        c->first_half = first;
     }
 }
 
@@ -515,6 +557,7 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
                                      : c->work_count;
     uint32_t* counter = wave == 0 ? &c->work_next : &c->work_next2;
     const float thr0 = c->thr_lb0;
+    const uint32_t first = c->first_half;
     int wb = 0;
     unsigned long long n_lb = 0, n_ref = 0, n_scan = 0;
     // batch of refined distances of this warp: entry i held by lane i
@@ -584,7 +627,7 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
                         const int64_t r = b + j * 32 + lane;
                         const bool ok = r < e;
                         n_lb += ok ? 1 : 0;
-                        const bool keep = ok && series_lb(w[j], tab, card) <= thr_r;
+                        const bool keep = ok && series_lb_two_phase(w[j], tab, card, first, thr_r);
                         const unsigned mk = __ballot_sync(FULL, keep);
                         int base = 0;
                         if (lane == 0 && mk) base = atomicAdd(&nsurv, __popc(mk));
