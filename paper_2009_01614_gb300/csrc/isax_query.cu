@@ -204,18 +204,19 @@ __device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ ta
 // lane of the warp is still at or below the threshold.  Either way the sum is
 // a fixed order of the 16 table entries (first half, then second, each by
 // segment index); a lane whose first half already exceeds `thr` is pruned.
+// Must be called by all 32 lanes (it votes); `ok` marks lanes holding a series.
 __device__ __forceinline__ bool series_lb_two_phase(uint4 w, const float* __restrict__ tab, int card,
-                                                    uint32_t first, float thr) {
+                                                    uint32_t first, float thr, bool ok) {
     const uint32_t words[4] = {w.x, w.y, w.z, w.w};
     float lb = 0.0f;
 #pragma unroll
     for (int i = 0; i < W; ++i)
         if ((first >> i) & 1u) lb += tab[i * card + ((words[i >> 2] >> (8 * (i & 3))) & 255u)];
-    if (!__any_sync(FULL, lb <= thr)) return false;
+    if (!__any_sync(FULL, ok && lb <= thr)) return false;
 #pragma unroll
     for (int i = 0; i < W; ++i)
         if (!((first >> i) & 1u)) lb += tab[i * card + ((words[i >> 2] >> (8 * (i & 3))) & 255u)];
-    return lb <= thr;
+    return ok && lb <= thr;
 }
 
 // ---------------------------------------------------------------- q_prep
@@ -627,7 +628,7 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
                         const int64_t r = b + j * 32 + lane;
                         const bool ok = r < e;
                         n_lb += ok ? 1 : 0;
-                        const bool keep = ok && series_lb_two_phase(w[j], tab, card, first, thr_r);
+                        const bool keep = series_lb_two_phase(w[j], tab, card, first, thr_r, ok);
                         const unsigned mk = __ballot_sync(FULL, keep);
                         int base = 0;
                         if (lane == 0 && mk) base = atomicAdd(&nsurv, __popc(mk));
