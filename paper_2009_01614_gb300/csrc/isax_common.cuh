@@ -88,7 +88,6 @@ struct QCtl {
     uint32_t flags;        // QF_* bits
     float thr_lb0;         // bound threshold the work list was binned with
     float qpaa[16];        // query PAA (fp32, as used by the bound table)
-    uint32_t first_half;   // bit i: segment i is among the 8 with the largest mean table entry
     double E;              // sqrt(n) * (eps_x + eps_q): PAA rounding slack
     double delta;          // relative error bound of an fp32 squared distance
     unsigned long long series_lb, series_refined, leaves_scanned, leaves_queued, approx_series;

@@ -199,26 +199,6 @@ __device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ ta
     return lb;
 }
 
-// Series bound in two halves: the 8 segments of `first` (largest mean table
-// entries for this query) are summed first; the other 8 are added only if some
-// lane of the warp is still at or below the threshold.  Either way the sum is
-// a fixed order of the 16 table entries (first half, then second, each by
-// segment index); a lane whose first half already exceeds `thr` is pruned.
-// Must be called by all 32 lanes (it votes); `ok` marks lanes holding a series.
-__device__ __forceinline__ bool series_lb_two_phase(uint4 w, const float* __restrict__ tab, int card,
-                                                    uint32_t first, float thr, bool ok) {
-    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
-    float lb = 0.0f;
-#pragma unroll
-    for (int i = 0; i < W; ++i)
-        if ((first >> i) & 1u) lb += tab[i * card + ((words[i >> 2] >> (8 * (i & 3))) & 255u)];
-    if (!__any_sync(FULL, ok && lb <= thr)) return false;
-#pragma unroll
-    for (int i = 0; i < W; ++i)
-        if (!((first >> i) & 1u)) lb += tab[i * card + ((words[i >> 2] >> (8 * (i & 3))) & 255u)];
-    return ok && lb <= thr;
-}
-
 // ---------------------------------------------------------------- q_prep
 constexpr int PREP_THREADS = 256;
 constexpr int APPROX_NEIGHBORS = 2;
@@ -269,20 +249,6 @@ __global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, Query
         const float d = v < lo ? lo - v : (v >= hi ? v - hi : 0.0f);
         s.table[e] = (d * d) * mf;
     }
-    __syncthreads();
-    // mean table entry of each segment (symbols are equiprobable under N(0,1))
-    __shared__ float rowsum[W];
-    if (warp < W / 2) {
-        for (int h = 0; h < 2; ++h) {
-            const int i = warp * 2 + h;
-            float acc = 0.0f;
-            for (int sym = lane; sym < card; sym += 32) acc += s.table[i * card + sym];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
-            if (lane == 0) rowsum[i] = acc;
-        }
-    }
-    __syncthreads();
     if (tid == 0) {
         unsigned long long key = 0;
         for (int pl = 0; pl < 4; ++pl) {
@@ -357,15 +323,7 @@ __global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, Query
             c->qsym[i] = (uint8_t)qsym[i];
             c->qpaa[i] = qpaa[i];
         }
-        // the 8 segments with the largest mean bound contribution are summed first
-        uint32_t first = 0;
-        for (int r = 0; r < W / 2; ++r) {
-            int best = -1;
-            for (int i = 0; i < W; ++i)
-                if (!((first >> i) & 1u) && (best < 0 || rowsum[i] > rowsum[best])) best = i;
-            first |= 1u << best;
-        }
-        c->first_half = first;
+
     }
 }
 
@@ -524,15 +482,15 @@ constexpr int SR_WARPS = SR_THREADS / 32;
 constexpr int SR_ROUND = SR_WARPS * SCAN_UNIT;    // series per leaf round
 
 template <int NV>
-__global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k,
+__global__ void __launch_bounds__(SR_THREADS, 4) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k,
                                                                       int wave, uint32_t wave_items) {
     extern __shared__ float tab[];
     __shared__ uint32_t off[NBINS + 1];
     __shared__ uint32_t scratch[32];
     __shared__ uint16_t surv[SR_ROUND];
     __shared__ int nsurv;
-    __shared__ uint32_t item_s;
-    __shared__ float thr_s, lim_s;
+    __shared__ uint32_t item_s, leaf_s, beg_s, end_s;
+    __shared__ float thr_s, lim_s, lb_s;
     __shared__ unsigned long long kth_s;
     QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
@@ -558,7 +516,6 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
                                      : c->work_count;
     uint32_t* counter = wave == 0 ? &c->work_next : &c->work_next2;
     const float thr0 = c->thr_lb0;
-    const uint32_t first = c->first_half;
     int wb = 0;
     unsigned long long n_lb = 0, n_ref = 0, n_scan = 0;
     // batch of refined distances of this warp: entry i held by lane i
@@ -584,10 +541,28 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
         ++nb;
         if (nb == SR_BATCH) flush();
     };
+    // the next claimed leaf and its metadata are fetched by thread 0 while the
+    // current one is processed
+    uint32_t nx_item = 0, nx_leaf = 0, nx_beg = 0, nx_end = 0;
+    float nx_lb = 0.0f;
+    auto fetch_next = [&]() {
+        nx_item = item0 + atomicAdd(counter, 1u);
+        if (nx_item < item1) {
+            nx_leaf = s.work[nx_item];
+            nx_lb = s.leaf_lb[nx_leaf];
+            nx_beg = ix.leaf_begin[nx_leaf];
+            nx_end = ix.leaf_begin[nx_leaf + 1];
+        }
+    };
+    if (tid == 0) fetch_next();
     __syncthreads();
     for (;;) {
         if (tid == 0) {
-            item_s = item0 + atomicAdd(counter, 1u);
+            item_s = nx_item;
+            leaf_s = nx_leaf;
+            lb_s = nx_lb;
+            beg_s = nx_beg;
+            end_s = nx_end;
             const unsigned long long kth = ld_volatile_u64(&s.topk[k - 1]);
             if (kth != kth_s || kth == 0) {
                 kth_s = kth;
@@ -599,16 +574,17 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
         const uint32_t item = item_s;
         const float thr = thr_s;
         if (item >= item1) break;
+        if (tid == 0) fetch_next();
         while (wb < NBINS - 1 && off[wb + 1] <= item) ++wb;
-        // every later position is in bin >= wb, whose bounds are >= thr0 (wb/NBINS)^2
+        // every later position is in bin >= wb, whose bounds are >= thr0 (wb/NBINS)^2;
+        // the prefetched position is later, so stopping loses nothing
         if (thr0 > 0.0f && !isinf(thr0)) {
             const float edge = (float)wb / (float)NBINS;
             if (thr0 * edge * edge * 0.99999f > thr) break;
         }
-        const uint32_t leaf = s.work[item];
-        if (s.leaf_lb[leaf] <= thr) {
+        if (lb_s <= thr) {
             if (tid == 0) ++n_scan;
-            const int64_t lbeg = ix.leaf_begin[leaf], lend = ix.leaf_begin[leaf + 1];
+            const int64_t lbeg = beg_s, lend = end_s;
             for (int64_t rb = lbeg; rb < lend; rb += SR_ROUND) {
                 if (tid == 0) nsurv = 0;
                 __syncthreads();
@@ -628,7 +604,7 @@ __global__ void __launch_bounds__(SR_THREADS, 3) q_scan_refine_kernel(DevIndex i
                         const int64_t r = b + j * 32 + lane;
                         const bool ok = r < e;
                         n_lb += ok ? 1 : 0;
-                        const bool keep = series_lb_two_phase(w[j], tab, card, first, thr_r, ok);
+                        const bool keep = ok && series_lb(w[j], tab, card) <= thr_r;
                         const unsigned mk = __ballot_sync(FULL, keep);
                         int base = 0;
                         if (lane == 0 && mk) base = atomicAdd(&nsurv, __popc(mk));
