@@ -28,6 +28,9 @@ def _host_lib():
             f = getattr(lib, name)
             f.argtypes = [u64, i64, i64, c_int, fp, c_int]
             f.restype = c_int
+        lib.dg_host_rows_at.argtypes = [c_int, u64, ctypes.POINTER(ctypes.c_int64), i64, c_int, fp,
+                                        c_int]
+        lib.dg_host_rows_at.restype = c_int
         lib.dg_host_noisy.argtypes = [fp, u64, i64, i64, c_int, ctypes.POINTER(ctypes.c_double), fp]
         lib.dg_host_noisy.restype = c_int
         lib.dg_host_pick_members.argtypes = [u64, i64, i64, u64, ctypes.POINTER(ctypes.c_int64)]
@@ -78,12 +81,17 @@ def rows(kind, seed, row0, count, n, nthreads=0):
     return out
 
 
-def rows_at(kind, seed, idx, n):
-    """Arbitrary rows (by index) of a collection, regenerated one by one."""
-    idx = np.asarray(idx, dtype=np.int64).ravel()
+def rows_at(kind, seed, idx, n, nthreads=0):
+    """Arbitrary rows (by index, any order) of a collection, regenerated."""
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).ravel())
     out = np.empty((len(idx), n), dtype=np.float32)
-    for i, r in enumerate(idx):
-        out[i] = rows(kind, seed, int(r), 1, n, nthreads=1)[0]
+    if len(idx) == 0:
+        return out
+    rc = _host_lib().dg_host_rows_at(0 if kind == "walk" else 1, seed,
+                                     idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(idx),
+                                     n, _fptr(out), nthreads)
+    if rc != 0:
+        raise RuntimeError("dg_host_rows_at failed rc=%d" % rc)
     return out
 
 

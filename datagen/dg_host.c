@@ -15,6 +15,7 @@ typedef struct {
     int64_t row0, begin, end;
     int n;
     float* out;
+    const int64_t* idx; /* rows to generate (NULL: rows row0 + i) */
 } dg_job;
 
 static void* dg_worker(void* p) {
@@ -23,17 +24,26 @@ static void* dg_worker(void* p) {
     if (!buf) return (void*)1;
     for (int64_t r = j->begin; r < j->end; ++r) {
         float* o = j->out + (size_t)(r - j->row0) * (size_t)j->n;
+        const uint64_t row = j->idx ? (uint64_t)j->idx[r - j->row0] : (uint64_t)r;
         if (j->kind == 0)
-            dg_random_walk_row(j->seed, (uint64_t)r, j->n, buf, o);
+            dg_random_walk_row(j->seed, row, j->n, buf, o);
         else
-            dg_sinusoid_row(j->seed, (uint64_t)r, j->n, buf, o);
+            dg_sinusoid_row(j->seed, row, j->n, buf, o);
     }
     free(buf);
     return NULL;
 }
 
+static int dg_run_idx(int kind, uint64_t seed, int64_t row0, int64_t count, int n, float* out,
+                      int nthreads, const int64_t* idx);
+
 static int dg_run(int kind, uint64_t seed, int64_t row0, int64_t count, int n, float* out,
                   int nthreads) {
+    return dg_run_idx(kind, seed, row0, count, n, out, nthreads, NULL);
+}
+
+static int dg_run_idx(int kind, uint64_t seed, int64_t row0, int64_t count, int n, float* out,
+                      int nthreads, const int64_t* idx) {
     if (n < 1 || n > DG_MAX_N || count < 0 || !out) return 1;
     if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
     if (nthreads < 1) nthreads = 1;
@@ -50,6 +60,7 @@ static int dg_run(int kind, uint64_t seed, int64_t row0, int64_t count, int n, f
         jobs[t].end = row0 + count * (t + 1) / nthreads;
         jobs[t].n = n;
         jobs[t].out = out;
+        jobs[t].idx = idx;
     }
     for (int t = 1; t < nthreads; ++t)
         if (pthread_create(&th[t], NULL, dg_worker, &jobs[t]) != 0) return 2;
@@ -72,6 +83,12 @@ int dg_host_random_walks(uint64_t seed, int64_t row0, int64_t count, int n, floa
 int dg_host_sinusoids(uint64_t seed, int64_t row0, int64_t count, int n, float* out,
                       int nthreads) {
     return dg_run(1, seed, row0, count, n, out, nthreads);
+}
+
+/* rows idx[0..count) (any order, repeats allowed) of collection (kind, seed) */
+int dg_host_rows_at(int kind, uint64_t seed, const int64_t* idx, int64_t count, int n, float* out,
+                    int nthreads) {
+    return dg_run_idx(kind, seed, 0, count, n, out, nthreads, idx);
 }
 
 /* noisy copies: out[b] = znorm(members[b] + sigma[b] * N(0,1)), noise stream

@@ -1,0 +1,79 @@
+"""Parity at the benchmark's full size: 100,000,000 random walks x 256 fp32
+(102.4 GB in HBM), w = 16, cardinality 256, leaf size 2000, generated on the
+device by the seeded generator and queried in the benchmark's launch
+configuration.  The oracle cannot scan 10^8 rows per query here, so it checks
+what it can compute one by one, plus properties that hold at any size:
+
+- every returned distance equals the FP64 definition recomputed by the oracle
+  on the returned row, regenerated on the host (to fp32 rounding);
+- returned rows are distinct and ascending by (distance, row);
+- noisy members (sigma 0.01) return their own row as the nearest neighbour;
+- no row of a 2,000,000-row sample of the collection, regenerated on the host,
+  is closer than the returned k-th neighbour (by (distance, row)).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import datagen
+import oracle
+import paper_2009_01614_gb300 as pkg
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+N, n = 100_000_000, 256
+SAMPLE = 2_000_000
+
+
+@pytest.fixture(scope="module")
+def full_index():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    free, _ = torch.cuda.mem_get_info()
+    if free < 230e9:
+        pytest.skip("needs ~230 GB of free device memory")
+    import __graft_entry__
+    __graft_entry__.build()
+    X = torch.empty((N, n), dtype=torch.float32, device="cuda")
+    datagen.rows_device("walk", 0, 0, N, n, X.data_ptr())
+    torch.cuda.synchronize()
+    ix = pkg.Index(X, cardinality=256, leaf_size=2000)
+    del X
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    yield ix
+    ix.close()
+
+
+def _check(ix, Q, k):
+    i, d = ix.query_batch(torch.from_numpy(Q).cuda(), k)
+    i, d = i.cpu().numpy(), d.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(7)
+    sample_idx = np.sort(rng.choice(N, SAMPLE, replace=False))
+    Xs = datagen.rows_at("walk", 0, sample_idx, n)
+    si, sd2 = oracle.bruteforce_knn(Xs, Q, k)
+    for b in range(len(Q)):
+        rows = datagen.rows_at("walk", 0, i[b], n)
+        d2 = np.array([oracle.ed2(r, Q[b]) for r in rows])
+        np.testing.assert_allclose(d[b], np.sqrt(d2), rtol=1e-6, atol=0)
+        assert len(set(i[b].tolist())) == k
+        key = list(zip(d2.tolist(), i[b].tolist()))
+        assert key == sorted(key)
+        returned = set(i[b].tolist())
+        for dd, j in zip(sd2[b], si[b]):
+            g = int(sample_idx[j])
+            if g not in returned:
+                assert (float(dd), g) > key[-1], (b, g, dd, key[-1])
+    return i
+
+
+def test_fullsize_exact_1nn(full_index):
+    Q, src = datagen.queries("walk", 0, N, n, 1, 12, 8, 0.01)
+    i = _check(full_index, Q, 1)
+    np.testing.assert_array_equal(i[12:, 0], src[12:])
+
+
+def test_fullsize_exact_10nn(full_index):
+    Q, _ = datagen.queries("walk", 0, N, n, 5, 6, 2, 0.05)
+    _check(full_index, Q, 10)
