@@ -213,10 +213,12 @@ typedef struct isax_kernel_time {
     double total_ms;   /* summed CUDA-event duration on the launching stream */
 } isax_kernel_time;
 
-/* 1: time every later kernel launch of this library with a pair of CUDA events
- * recorded on its stream (clears earlier records); 0: stop timing.  Timing adds
- * two event records per launch; leave it off outside measurements. */
-isax_status isax_profile(int32_t enable);
+/* Time later kernel launches of this library with a pair of CUDA events
+ * recorded on each launch's stream (clears earlier records): mode 1 every
+ * kernel (queries then launch kernel by kernel instead of replaying their
+ * captured CUDA graph), mode 2 the index-build kernels only, 0 stop timing.
+ * Timing adds two event records per timed launch. */
+isax_status isax_profile(int32_t mode);
 
 /* Per-kernel totals of the timed launches (waits for their events).  Fills at
  * most max entries of out (out may be NULL) and returns the number of distinct

@@ -188,8 +188,9 @@ def isax_summarize(series_ptr, N, n, cardinality, mem_flags, out_sax_ptr, out_pa
                                 out_paa_ptr, stream))
 
 
-def isax_profile(enable):
-    _check(lib().isax_profile(1 if enable else 0))
+def isax_profile(mode):
+    """0 off, 1 (or True) time every kernel, 2 time the index-build kernels only."""
+    _check(lib().isax_profile(int(mode)))
 
 
 def isax_profile_report():

@@ -52,6 +52,8 @@ class KernelScope {
     void* e1_ = nullptr;
 };
 #define ISAX_LAUNCH(name, st) ::isax::KernelScope isax_ks_##__LINE__(name, st)
+bool profiling_on();               // per-kernel event timing enabled
+void count_launches(int kernels);  // launches made by replaying a captured graph
 
 // ---------------------------------------------------------------- allocator
 void* dev_alloc(size_t bytes, cudaStream_t st);  // throws Error{OOM}
@@ -156,5 +158,6 @@ struct isax_index {
     float* bp;
     // query scratch (one in-flight query)
     isax::QueryScratch qs;
-    void* mu;  // std::mutex*
+    void* mu;      // std::mutex*
+    void* graphs;  // captured query launch sequences (isax_query.cu)
 };

@@ -18,7 +18,7 @@ struct Record {
     cudaEvent_t e0, e1;
 };
 std::atomic<unsigned long long> g_launches{0};
-std::atomic<bool> g_on{false};
+std::atomic<int> g_mode{0};  // 0 off, 1 every kernel, 2 build kernels only
 std::mutex g_mu;
 std::vector<Record> g_records;
 std::vector<cudaEvent_t> g_pool;
@@ -37,7 +37,9 @@ cudaEvent_t take_event() {
 
 KernelScope::KernelScope(const char* name, cudaStream_t st) : name_(name), st_(st) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (g_on.load(std::memory_order_relaxed)) {
+    const int mode = g_mode.load(std::memory_order_relaxed);
+    // query kernels are named q_*; mode 2 leaves them untimed
+    if (mode == 1 || (mode == 2 && name[0] != 'q')) {
         std::lock_guard<std::mutex> lk(g_mu);
         e0_ = take_event();
         e1_ = take_event();
@@ -51,6 +53,10 @@ KernelScope::~KernelScope() {
     cudaEventRecord(static_cast<cudaEvent_t>(e1_), st_);
     g_records.push_back({name_, static_cast<cudaEvent_t>(e0_), static_cast<cudaEvent_t>(e1_)});
 }
+
+bool profiling_on() { return g_mode.load(std::memory_order_relaxed) == 1; }
+
+void count_launches(int kernels) { g_launches.fetch_add((unsigned long long)kernels, std::memory_order_relaxed); }
 
 }  // namespace isax
 
@@ -73,7 +79,7 @@ isax_status isax_profile(int32_t enable) {
             g_pool.push_back(e);
         }
     }
-    g_on.store(enable != 0);
+    g_mode.store(enable == 1 ? 1 : enable == 2 ? 2 : 0);
     return ISAX_OK;
 }
 

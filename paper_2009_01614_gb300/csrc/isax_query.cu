@@ -28,6 +28,7 @@
 // left-to-right sum as the definition, so the indices equal the brute-force
 // answer's.
 #include <algorithm>
+#include <map>
 #include <mutex>
 
 #include "isax_common.cuh"
@@ -823,7 +824,10 @@ void free_query_scratch(isax_index* ix, cudaStream_t st) {
     q = QueryScratch{};
 }
 
+static void drop_query_graphs(isax_index* ix);
+
 void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st) {
+    drop_query_graphs(ix);
     free_query_scratch(ix, st);
     QueryScratch& q = ix->qs;
     const DevIndex& d = ix->d;
@@ -843,7 +847,32 @@ void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st) {
     ISAX_CUDA_TRY(cudaMemsetAsync(q.ctl, 0, sizeof(QCtl), st));
 }
 
+// The query's kernel sequence, captured once per k into a CUDA graph and
+// replayed with one launch (while per-kernel tracing is off).  Graphs hold the
+// scratch pointers, so they are dropped whenever the scratch is reallocated.
+struct QueryGraphs {
+    cudaStream_t capture = nullptr;
+    std::map<int, cudaGraphExec_t> exec;
+    int kernels_per_query = 0;
+    void clear() {
+        for (auto& kv : exec) cudaGraphExecDestroy(kv.second);
+        exec.clear();
+    }
+    ~QueryGraphs() {
+        clear();
+        if (capture) cudaStreamDestroy(capture);
+    }
+};
+
+static void drop_query_graphs(isax_index* ix) {
+    if (ix->graphs) static_cast<QueryGraphs*>(ix->graphs)->clear();
+}
+
 void free_index_arrays(isax_index* ix, cudaStream_t st) {
+    if (ix->graphs) {
+        delete static_cast<QueryGraphs*>(ix->graphs);
+        ix->graphs = nullptr;
+    }
     free_query_scratch(ix, st);
     void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp};
     for (void* p : ptrs)
@@ -930,10 +959,46 @@ void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaS
 
 // One exact k-NN query; q is already in ix->qs.q.  Results land in
 // ix->qs.out_idx / out_dist; the control block is copied to *ctl_out.
+// launch the query's kernels on st: replay of a captured graph, or direct
+// launches while per-kernel tracing is on
+static void launch_query_index(isax_index* ix, int k, cudaStream_t st) {
+    if (profiling_on()) {
+        launch_query_on_scratch(ix, ix->qs, k, st);
+        return;
+    }
+    if (!ix->graphs) ix->graphs = new QueryGraphs();
+    QueryGraphs* g = static_cast<QueryGraphs*>(ix->graphs);
+    auto it = g->exec.find(k);
+    if (it == g->exec.end()) {
+        if (!g->capture) ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking));
+        ISAX_CUDA_TRY(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t graph = nullptr;
+        try {
+            launch_query_on_scratch(ix, ix->qs, k, g->capture);
+        } catch (...) {
+            cudaStreamEndCapture(g->capture, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        ISAX_CUDA_TRY(cudaStreamEndCapture(g->capture, &graph));
+        size_t nodes = 0;
+        cudaGraphGetNodes(graph, nullptr, &nodes);
+        g->kernels_per_query = (int)nodes;
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        ISAX_CUDA_TRY(e);
+        if (g->exec.size() >= 8) g->clear();
+        it = g->exec.emplace(k, exec).first;
+    }
+    ISAX_CUDA_TRY(cudaGraphLaunch(it->second, st));
+    count_launches(g->kernels_per_query);
+}
+
 void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st) {
     *reruns = 0;
     for (int attempt = 0;; ++attempt) {
-        launch_query_on_scratch(ix, ix->qs, k, st);
+        launch_query_index(ix, k, st);
         ISAX_CUDA_TRY(cudaMemcpyAsync(ctl_out, ix->qs.ctl, sizeof(QCtl), cudaMemcpyDeviceToHost, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         if (ctl_out->flags & QF_NONFINITE) throw Error{ISAX_ERR_INVALID_ARG, "query contains a non-finite value"};
