@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, Quer
 }
 
 // ---------------------------------------------------------------- q_scan_refine
-constexpr int SR_THREADS = NBINS;                 // one thread per bin for the offset scan
+constexpr int SR_THREADS = 128;                   // 4 warps: one 256-series chunk each per round
 constexpr int SR_WORDS = SCAN_UNIT / 32;          // SAX words per lane per round
 constexpr int SR_BATCH = 8;                       // refined distances per k-best update
 constexpr uint32_t SR_WAVE0 = 0;                  // leaves of an optional narrow first wave
@@ -483,7 +483,7 @@ constexpr int SR_WARPS = SR_THREADS / 32;
 constexpr int SR_ROUND = SR_WARPS * SCAN_UNIT;    // series per leaf round
 
 template <int NV>
-__global__ void __launch_bounds__(SR_THREADS, 4) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k,
+__global__ void __launch_bounds__(SR_THREADS, 8) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k,
                                                                       int wave, uint32_t wave_items) {
     extern __shared__ float tab[];
     __shared__ uint32_t off[NBINS + 1];
@@ -498,10 +498,13 @@ __global__ void __launch_bounds__(SR_THREADS, 4) q_scan_refine_kernel(DevIndex i
     const int card = ix.card;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < W * card; e += SR_THREADS) tab[e] = s.table[e];
-    {
+    {   // bin offsets: the exclusive scan the scatter kernel used (two bins per thread)
+        static_assert(NBINS == 2 * SR_THREADS, "two bins per thread");
+        const uint32_t c0 = s.bin_count[2 * tid], c1 = s.bin_count[2 * tid + 1];
         uint32_t tot;
-        const uint32_t o = block_excl_scan<uint32_t>(s.bin_count[tid], 0u, OpAdd<uint32_t>(), scratch, &tot);
-        off[tid] = o;
+        const uint32_t o = block_excl_scan<uint32_t>(c0 + c1, 0u, OpAdd<uint32_t>(), scratch, &tot);
+        off[2 * tid] = o;
+        off[2 * tid + 1] = o + c0;
         if (tid == 0) {
             off[NBINS] = tot;
             kth_s = 0;
@@ -698,6 +701,22 @@ __device__ __forceinline__ double warp_d2_fp64_seq(const float* __restrict__ xr,
     return __shfl_sync(FULL, acc, 0);
 }
 
+// FP64 squared distance summed lane-parallel (each lane left to right over its
+// elements, then a butterfly): the value returned for rows whose order is
+// already decided.
+__device__ __forceinline__ double warp_d2_fp64_tree(const float* __restrict__ xr,
+                                                    const float* __restrict__ q, int n) {
+    const int lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32) {
+        const double d = __dsub_rn((double)xr[j], (double)q[j]);
+        acc = __dadd_rn(acc, __dmul_rn(d, d));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(FULL, acc, off));
+    return acc;
+}
+
 __device__ __forceinline__ void bitonic_sort_smem(unsigned long long* sk, uint32_t* sid, int P) {
     const int tid = threadIdx.x;
     for (int size = 2; size <= P; size <<= 1) {
@@ -727,8 +746,9 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
     __shared__ unsigned long long sk[FIN_CAP];
     __shared__ uint32_t sid[FIN_CAP];
     __shared__ uint32_t stage[FIN_THREADS];
+    __shared__ unsigned long long stage_key[FIN_THREADS];
     __shared__ double sqbuf[FIN_WARPS][32];
-    __shared__ int nst;
+    __shared__ int nst, ambiguous;
     QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -746,15 +766,57 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
     __syncthreads();
     // one pass over all candidates: count the window, stage it if it fits
     for (uint32_t i = tid; i < M; i += FIN_THREADS) {
-        if ((double)key_d2(s.cand_key[i]) <= bound) {
+        const unsigned long long key = s.cand_key[i];
+        if ((double)key_d2(key) <= bound) {
             const int p = atomicAdd(&nst, 1);
-            if (p < FIN_THREADS) stage[p] = s.cand_pos[i];
+            if (p < FIN_THREADS) {
+                stage[p] = s.cand_pos[i];
+                stage_key[p] = key;
+            }
         }
     }
+    if (tid == 0) ambiguous = 0;
     __syncthreads();
     const int window = nst;
     int cnt = 0;
-    if (window <= FIN_THREADS) {
+    bool done = false;
+    if (window == k) {
+        // The window holds exactly the k best: only their order is in question.
+        // Sorted by fp32 (d2, row), it is the FP64 order as well when every
+        // two neighbours are more than 3 delta apart (each FP64 value is within
+        // delta of its fp32 value); then a warp-parallel FP64 sum gives the
+        // returned distance.  Otherwise the sequential definition decides.
+        for (int t = tid; t < window; t += FIN_THREADS) {
+            sk[t] = stage_key[t];
+            sid[t] = stage[t];
+        }
+        int P = 1;
+        while (P < window) P <<= 1;
+        for (int t = window + tid; t < P; t += FIN_THREADS) {
+            sk[t] = EMPTY_SLOT;
+            sid[t] = 0xffffffffu;
+        }
+        __syncthreads();
+        bitonic_sort_smem(sk, sid, P);
+        for (int t = tid; t + 1 < window; t += FIN_THREADS)
+            if ((double)key_d2(sk[t + 1]) <= (double)key_d2(sk[t]) * (1.0 + 3.0 * delta)) ambiguous = 1;
+        __syncthreads();
+        if (!ambiguous) {
+            for (int e = warp; e < window; e += FIN_WARPS) {
+                const uint32_t pos = sid[e];
+                const double d = warp_d2_fp64_tree(ix.x + (int64_t)pos * n, s.q, n);
+                if (lane == 0) {
+                    s.out_idx[e] = (int64_t)(uint32_t)sk[e];
+                    s.out_dist[e] = __double2float_rn(sqrt(d));
+                }
+            }
+            cnt = k;
+            done = true;
+        }
+        __syncthreads();
+    }
+    if (done) {
+    } else if (window <= FIN_THREADS) {
         for (int e = warp; e < window; e += FIN_WARPS) {
             const uint32_t pos = stage[e];
             const double d = warp_d2_fp64_seq(ix.x + (int64_t)pos * n, s.q, n, sqbuf[warp]);
@@ -803,7 +865,7 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
             cnt = total < k ? total : k;
         }
     }
-    if (tid < cnt) {
+    if (!done && tid < cnt) {
         s.out_idx[tid] = (int64_t)sid[tid];
         s.out_dist[tid] = __double2float_rn(sqrt(__longlong_as_double((long long)sk[tid])));
     }
