@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, Quer
 }
 
 // ---------------------------------------------------------------- q_scan_refine
-constexpr int SR_THREADS = 128;                   // 4 warps: one 256-series chunk each per round
+constexpr int SR_THREADS = 256;                   // 8 warps: one 256-series chunk each per round
 constexpr int SR_WORDS = SCAN_UNIT / 32;          // SAX words per lane per round
 constexpr int SR_BATCH = 8;                       // refined distances per k-best update
 constexpr uint32_t SR_WAVE0 = 0;                  // leaves of an optional narrow first wave
@@ -483,7 +483,7 @@ constexpr int SR_WARPS = SR_THREADS / 32;
 constexpr int SR_ROUND = SR_WARPS * SCAN_UNIT;    // series per leaf round
 
 template <int NV>
-__global__ void __launch_bounds__(SR_THREADS, 8) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k,
+__global__ void __launch_bounds__(SR_THREADS, 4) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k,
                                                                       int wave, uint32_t wave_items) {
     extern __shared__ float tab[];
     __shared__ uint32_t off[NBINS + 1];
@@ -499,12 +499,9 @@ __global__ void __launch_bounds__(SR_THREADS, 8) q_scan_refine_kernel(DevIndex i
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < W * card; e += SR_THREADS) tab[e] = s.table[e];
     {   // bin offsets: the exclusive scan the scatter kernel used (two bins per thread)
-        static_assert(NBINS == 2 * SR_THREADS, "two bins per thread");
-        const uint32_t c0 = s.bin_count[2 * tid], c1 = s.bin_count[2 * tid + 1];
+        static_assert(NBINS == SR_THREADS, "one bin per thread");
         uint32_t tot;
-        const uint32_t o = block_excl_scan<uint32_t>(c0 + c1, 0u, OpAdd<uint32_t>(), scratch, &tot);
-        off[2 * tid] = o;
-        off[2 * tid + 1] = o + c0;
+        off[tid] = block_excl_scan<uint32_t>(s.bin_count[tid], 0u, OpAdd<uint32_t>(), scratch, &tot);
         if (tid == 0) {
             off[NBINS] = tot;
             kth_s = 0;
