@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=4_000_000)
+    ap.add_argument("--batch", type=int, default=1024,
+                    help="also time isax_query_knn_batch on this many fresh queries (0: skip)")
     return ap.parse_args()
 
 
@@ -365,6 +367,28 @@ def main():
             entry["GB_per_s"] = round(b / (ms / 1e3) / 1e9, 1)
         kernels[nm] = entry
 
+    # batched queries (the plain FP32 path, queries run concurrently on slots)
+    batch_info = None
+    if a.batch > 0:
+        import datagen
+        Qb = torch.from_numpy(datagen.rows("walk", 4 + 1000 * rank, 0, a.batch, n)).cuda()
+        ixb = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp)
+        ixb.query_batch(Qb[:64], k, stream=sp)  # warm up the slots and their graphs
+        torch.cuda.synchronize()
+        reps = 3
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            ixb.query_batch(Qb, k, stream=sp)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        bms = t0.elapsed_time(t1) / reps
+        batch_info = {"B": a.batch, "k": k, "ms_per_batch": bms, "queries_per_s": a.batch / (bms / 1e3),
+                      "queries": "fresh random walks (seed 4), device buffers"}
+        ixb.close()
+        del Qb
+
     lat_sorted = sorted(lat_ms)
 
     def pct(p):
@@ -384,6 +408,7 @@ def main():
         "build_ms": build_ms, "build_input_GB_per_s": N * n * 4 / 1e9 / (build_ms / 1e3),
         "index": {"leaves": info["leaves"], "max_leaf": info["max_leaf"]},
         "pruning": {key + "_per_query": stats_acc[key] / max(1, len(lat_ms)) for key in stats_acc},
+        "batch": batch_info,
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": clock_info,

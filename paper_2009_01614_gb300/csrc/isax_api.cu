@@ -215,11 +215,18 @@ isax_status isax_query_knn_batch(const isax_index* cix, const float* Q, int32_t 
         const int n = ix->d.n;
         const cudaMemcpyKind kin = (mem_flags & ISAX_MEM_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice
                                                                        : cudaMemcpyHostToDevice;
-        for (int32_t b = 0; b < B; ++b) {
-            ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, Q + (size_t)b * n, sizeof(float) * n, kin, st));
-            run_one(ix, k, mem_flags, out_idx + (size_t)b * k, out_dist + (size_t)b * k,
-                    stats ? stats + b : nullptr, st);
-        }
+        if (B == 0) return;
+        (void)n;
+        (void)kin;
+        struct Ctx {
+            const isax_index* ix;
+            isax_query_stats* stats;
+        } ctx{ix, stats};
+        auto fill = [](void* p, int b, const QCtl& c, int reruns) {
+            Ctx* cx = static_cast<Ctx*>(p);
+            if (cx->stats) fill_stats(cx->stats + b, cx->ix, c, reruns);
+        };
+        query_batch_device(ix, Q, B, k, mem_flags, out_idx, out_dist, fill, &ctx, st);
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
     });
 }

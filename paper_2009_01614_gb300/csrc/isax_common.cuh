@@ -130,6 +130,10 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
 void summarize_impl(const float* series, int64_t N, int n, int card, uint32_t mem_flags,
                     uint8_t* out_sax, float* out_paa, cudaStream_t st);
 void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st);
+typedef void (*isax_query_stats_fill)(void* ctx, int b, const QCtl& c, int reruns);
+void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags,
+                        int64_t* out_idx, float* out_dist, isax_query_stats_fill fill,
+                        void* fill_ctx, cudaStream_t st);
 void free_index_arrays(isax_index* ix, cudaStream_t st);
 void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st);
 void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st);
@@ -160,4 +164,5 @@ struct isax_index {
     isax::QueryScratch qs;
     void* mu;      // std::mutex*
     void* graphs;  // captured query launch sequences (isax_query.cu)
+    void* pool;    // extra query slots for concurrent batches (isax_query.cu)
 };

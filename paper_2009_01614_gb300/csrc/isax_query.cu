@@ -27,9 +27,12 @@
 // final k-th best is kept as a candidate and re-ranked in FP64 with the same
 // left-to-right sum as the definition, so the indices equal the brute-force
 // answer's.
+#include <string.h>
+
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "isax_common.cuh"
 #include "isax_kernels_util.cuh"
@@ -498,7 +501,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) q_scan_refine_kernel(DevIndex i
     const int card = ix.card;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < W * card; e += SR_THREADS) tab[e] = s.table[e];
-    {   // bin offsets: the exclusive scan the scatter kernel used (two bins per thread)
+    {   // bin offsets: the exclusive scan the scatter kernel used (one bin per thread)
         static_assert(NBINS == SR_THREADS, "one bin per thread");
         uint32_t tot;
         off[tid] = block_excl_scan<uint32_t>(s.bin_count[tid], 0u, OpAdd<uint32_t>(), scratch, &tot);
@@ -874,8 +877,7 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
 }
 
 // ================================================================ host side
-void free_query_scratch(isax_index* ix, cudaStream_t st) {
-    QueryScratch& q = ix->qs;
+static void free_scratch(QueryScratch& q, cudaStream_t st) {
     void* ptrs[] = {q.q, q.table, q.leaf_lb, q.work, q.bin_count, q.bin_cursor, q.topk,
                     q.cand_key, q.cand_pos, q.ctl, q.out_idx, q.out_dist};
     for (void* p : ptrs)
@@ -883,13 +885,7 @@ void free_query_scratch(isax_index* ix, cudaStream_t st) {
     q = QueryScratch{};
 }
 
-static void drop_query_graphs(isax_index* ix);
-
-void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st) {
-    drop_query_graphs(ix);
-    free_query_scratch(ix, st);
-    QueryScratch& q = ix->qs;
-    const DevIndex& d = ix->d;
+static void alloc_scratch(const DevIndex& d, uint32_t cand_cap, QueryScratch& q, cudaStream_t st) {
     q.q = static_cast<float*>(dev_alloc(sizeof(float) * d.n, st));
     q.table = static_cast<float*>(dev_alloc(sizeof(float) * W * d.card, st));
     q.leaf_lb = static_cast<float*>(dev_alloc(sizeof(float) * d.L, st));
@@ -923,8 +919,52 @@ struct QueryGraphs {
     }
 };
 
+// Extra scratch sets that let the queries of a batch run concurrently, each
+// on its own stream.
+constexpr int BATCH_SLOTS = 8;
+struct QuerySlot {
+    QueryScratch qs{};
+    QueryGraphs graphs;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+struct SlotPool {
+    std::vector<QuerySlot*> slots;
+    QCtl* host_ctl = nullptr;  // pinned: one control block per query of a batch
+    size_t host_cap = 0;
+    int64_t* host_idx = nullptr;  // pinned staging for host outputs (a D2H copy into
+    float* host_dist = nullptr;   // pageable memory would serialise the streams)
+    size_t host_out_cap = 0;
+};
+
+static void free_slot_pool(isax_index* ix, cudaStream_t st) {
+    SlotPool* p = static_cast<SlotPool*>(ix->pool);
+    if (!p) return;
+    for (QuerySlot* sl : p->slots) {
+        if (sl->stream) cudaStreamSynchronize(sl->stream);
+        free_scratch(sl->qs, st);
+        sl->graphs.clear();
+        if (sl->done) cudaEventDestroy(sl->done);
+        if (sl->stream) cudaStreamDestroy(sl->stream);
+        delete sl;
+    }
+    if (p->host_ctl) cudaFreeHost(p->host_ctl);
+    if (p->host_idx) cudaFreeHost(p->host_idx);
+    if (p->host_dist) cudaFreeHost(p->host_dist);
+    delete p;
+    ix->pool = nullptr;
+}
+
+void free_query_scratch(isax_index* ix, cudaStream_t st) { free_scratch(ix->qs, st); }
+
 static void drop_query_graphs(isax_index* ix) {
     if (ix->graphs) static_cast<QueryGraphs*>(ix->graphs)->clear();
+}
+
+void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st) {
+    drop_query_graphs(ix);
+    free_query_scratch(ix, st);
+    alloc_scratch(ix->d, cand_cap, ix->qs, st);
 }
 
 void free_index_arrays(isax_index* ix, cudaStream_t st) {
@@ -932,6 +972,7 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
         delete static_cast<QueryGraphs*>(ix->graphs);
         ix->graphs = nullptr;
     }
+    free_slot_pool(ix, st);
     free_query_scratch(ix, st);
     void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp};
     for (void* p : ptrs)
@@ -1020,20 +1061,19 @@ void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaS
 // ix->qs.out_idx / out_dist; the control block is copied to *ctl_out.
 // launch the query's kernels on st: replay of a captured graph, or direct
 // launches while per-kernel tracing is on
-static void launch_query_index(isax_index* ix, int k, cudaStream_t st) {
+static void launch_query_graph(isax_index* ix, const QueryScratch& qs, QueryGraphs* g, int k,
+                               cudaStream_t st) {
     if (profiling_on()) {
-        launch_query_on_scratch(ix, ix->qs, k, st);
+        launch_query_on_scratch(ix, qs, k, st);
         return;
     }
-    if (!ix->graphs) ix->graphs = new QueryGraphs();
-    QueryGraphs* g = static_cast<QueryGraphs*>(ix->graphs);
     auto it = g->exec.find(k);
     if (it == g->exec.end()) {
         if (!g->capture) ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking));
         ISAX_CUDA_TRY(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
         cudaGraph_t graph = nullptr;
         try {
-            launch_query_on_scratch(ix, ix->qs, k, g->capture);
+            launch_query_on_scratch(ix, qs, k, g->capture);
         } catch (...) {
             cudaStreamEndCapture(g->capture, &graph);
             if (graph) cudaGraphDestroy(graph);
@@ -1052,6 +1092,11 @@ static void launch_query_index(isax_index* ix, int k, cudaStream_t st) {
     }
     ISAX_CUDA_TRY(cudaGraphLaunch(it->second, st));
     count_launches(g->kernels_per_query);
+}
+
+static void launch_query_index(isax_index* ix, int k, cudaStream_t st) {
+    if (!ix->graphs) ix->graphs = new QueryGraphs();
+    launch_query_graph(ix, ix->qs, static_cast<QueryGraphs*>(ix->graphs), k, st);
 }
 
 void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st) {
@@ -1077,6 +1122,97 @@ void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_
         if (ctl_out->flags & QF_SHORT) throw Error{ISAX_ERR_INTERNAL, "fewer than k candidates survived"};
         return;
     }
+}
+
+// B queries, up to BATCH_SLOTS at a time on their own streams (each query's
+// answer is the single-query answer: same kernels, own scratch).  Queries
+// whose candidate buffer overflowed are rerun one by one afterwards.
+void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags,
+                        int64_t* out_idx, float* out_dist, isax_query_stats_fill fill,
+                        void* fill_ctx, cudaStream_t st) {
+    const int n = ix->d.n;
+    const int S = B < BATCH_SLOTS ? B : BATCH_SLOTS;
+    if (!ix->pool) ix->pool = new SlotPool();
+    SlotPool* pool = static_cast<SlotPool*>(ix->pool);
+    while ((int)pool->slots.size() < S) {
+        QuerySlot* sl = new QuerySlot();
+        pool->slots.push_back(sl);
+        ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking));
+        ISAX_CUDA_TRY(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
+        alloc_scratch(ix->d, ix->qs.cand_cap, sl->qs, st);
+    }
+    if (pool->host_cap < (size_t)B) {
+        if (pool->host_ctl) cudaFreeHost(pool->host_ctl);
+        pool->host_ctl = nullptr;
+        pool->host_cap = 0;
+        ISAX_CUDA_TRY(cudaMallocHost((void**)&pool->host_ctl, sizeof(QCtl) * (size_t)B));
+        pool->host_cap = (size_t)B;
+    }
+    const bool host_out = !(mem_flags & ISAX_MEM_OUTPUT_DEVICE);
+    if (host_out && pool->host_out_cap < (size_t)B * k) {
+        if (pool->host_idx) cudaFreeHost(pool->host_idx);
+        if (pool->host_dist) cudaFreeHost(pool->host_dist);
+        pool->host_idx = nullptr;
+        pool->host_dist = nullptr;
+        pool->host_out_cap = 0;
+        ISAX_CUDA_TRY(cudaMallocHost((void**)&pool->host_idx, sizeof(int64_t) * (size_t)B * k));
+        ISAX_CUDA_TRY(cudaMallocHost((void**)&pool->host_dist, sizeof(float) * (size_t)B * k));
+        pool->host_out_cap = (size_t)B * k;
+    }
+    int64_t* dst_idx = host_out ? pool->host_idx : out_idx;
+    float* dst_dist = host_out ? pool->host_dist : out_dist;
+    // the slots' work starts after everything already queued on st
+    cudaEvent_t start;
+    ISAX_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    ISAX_CUDA_TRY(cudaEventRecord(start, st));
+    for (int i = 0; i < S; ++i) ISAX_CUDA_TRY(cudaStreamWaitEvent(pool->slots[i]->stream, start, 0));
+    cudaEventDestroy(start);
+    const cudaMemcpyKind kin = (mem_flags & ISAX_MEM_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                                   : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = (mem_flags & ISAX_MEM_OUTPUT_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                                     : cudaMemcpyDeviceToHost;
+    for (int b = 0; b < B; ++b) {
+        QuerySlot* sl = pool->slots[b % S];
+        const cudaStream_t ss = sl->stream;
+        ISAX_CUDA_TRY(cudaMemcpyAsync(sl->qs.q, Q + (size_t)b * n, sizeof(float) * n, kin, ss));
+        launch_query_graph(ix, sl->qs, &sl->graphs, k, ss);
+        ISAX_CUDA_TRY(cudaMemcpyAsync(&pool->host_ctl[b], sl->qs.ctl, sizeof(QCtl),
+                                      cudaMemcpyDeviceToHost, ss));
+        ISAX_CUDA_TRY(cudaMemcpyAsync(dst_idx + (size_t)b * k, sl->qs.out_idx, sizeof(int64_t) * k,
+                                      kout, ss));
+        ISAX_CUDA_TRY(cudaMemcpyAsync(dst_dist + (size_t)b * k, sl->qs.out_dist, sizeof(float) * k,
+                                      kout, ss));
+    }
+    for (int i = 0; i < S; ++i) {
+        ISAX_CUDA_TRY(cudaEventRecord(pool->slots[i]->done, pool->slots[i]->stream));
+        ISAX_CUDA_TRY(cudaStreamWaitEvent(st, pool->slots[i]->done, 0));
+    }
+    for (int i = 0; i < S; ++i) ISAX_CUDA_TRY(cudaStreamSynchronize(pool->slots[i]->stream));
+    if (host_out) {
+        memcpy(out_idx, pool->host_idx, sizeof(int64_t) * (size_t)B * k);
+        memcpy(out_dist, pool->host_dist, sizeof(float) * (size_t)B * k);
+    }
+    bool nonfinite = false;
+    for (int b = 0; b < B; ++b) {
+        QCtl c = pool->host_ctl[b];
+        int reruns = 0;
+        if (c.flags & QF_NONFINITE) {
+            nonfinite = true;
+            continue;
+        }
+        if (c.flags & (QF_OVERFLOW | QF_SHORT)) {
+            ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, Q + (size_t)b * n, sizeof(float) * n, kin, st));
+            query_device(ix, k, &c, &reruns, st);
+            ISAX_CUDA_TRY(cudaMemcpyAsync(out_idx + (size_t)b * k, ix->qs.out_idx, sizeof(int64_t) * k,
+                                          kout, st));
+            ISAX_CUDA_TRY(cudaMemcpyAsync(out_dist + (size_t)b * k, ix->qs.out_dist, sizeof(float) * k,
+                                          kout, st));
+            ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+            reruns += 1;
+        }
+        if (fill) fill(fill_ctx, b, c, reruns);
+    }
+    if (nonfinite) throw Error{ISAX_ERR_INVALID_ARG, "a query contains a non-finite value"};
 }
 
 }  // namespace isax
