@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=4_000_000)
+    ap.add_argument("--workload", choices=["walk", "hardness"], default="walk",
+                    help="hardness: the sinusoid collection, member queries by noise level and k")
     ap.add_argument("--batch", type=int, default=1024,
                     help="also time isax_query_knn_batch on this many fresh queries (0: skip)")
     return ap.parse_args()
@@ -236,11 +238,73 @@ def reference_arm(a):
     return 0
 
 
+# ------------------------------------------------------------------ query hardness
+def hardness(a):
+    """Sum-of-3-sinusoids collection (default 50M x 256): 50 member queries per
+    noise level sigma in {0.01, 0.1, 0.5, 1.0}, each answered for k in {1, 10,
+    100}; per (sigma, k): leaf and series pruning, series refined, floats read
+    by refinement, latency.  One JSON line."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import datagen
+    import paper_2009_01614_gb300 as pkg
+    N = a.N if a.N != 100_000_000 else 50_000_000
+    n = a.n
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    X = torch.empty((N, n), dtype=torch.float32, device="cuda")
+    datagen.rows_device("sine", 0, 0, N, n, X.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    del X
+    torch.cuda.empty_cache()
+    info = ix.info()
+    rows = []
+    for si, sigma in enumerate([0.01, 0.1, 0.5, 1.0]):
+        Q, _ = datagen.queries("sine", 0, N, n, 3 + si, 0, 50, sigma)
+        Qd = torch.from_numpy(Q).cuda()
+        for k in [1, 10, 100]:
+            lat, st_all = [], []
+            for b in range(len(Q)):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, _, st = ix.query(Qd[b], k, stats=True)
+                e1.record(stream)
+                e1.synchronize()
+                lat.append(e0.elapsed_time(e1))
+                st_all.append(st)
+            mean = lambda key: float(np.mean([x[key] for x in st_all]))
+            rows.append({
+                "sigma": sigma, "k": k,
+                "leaf_pruning": 1.0 - mean("leaves_scanned") / info["leaves"],
+                "series_lb_per_query": mean("series_lb"),
+                "series_pruning_by_lb": 1.0 - (mean("series_refined") - mean("approx_series"))
+                / max(1.0, mean("series_lb")),
+                "series_refined_per_query": mean("series_refined"),
+                "ed_floats_read_per_query": mean("series_refined") * n,
+                "latency_ms_p50": float(np.percentile(lat, 50)),
+                "latency_ms_p99": float(np.percentile(lat, 99)),
+            })
+    ix.close()
+    print(json.dumps({"workload": "query hardness: %d sum-of-3-sinusoid series x %d fp32, leaf %d; "
+                                  "50 member queries per noise level" % (N, n, a.leaf),
+                      "build_s": build_s, "leaves": info["leaves"], "rows": rows}), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     a = parse()
     if a.impl == "reference":
         return reference_arm(a)
+    if a.workload == "hardness":
+        return hardness(a)
 
     import numpy as np
     import torch
