@@ -205,6 +205,21 @@ isax_status isax_query_knn_noalloc(const isax_index* ix, const float* q, int32_t
                                    uint32_t mem_flags, int64_t* out_idx, float* out_dist,
                                    isax_query_stats* stats, void* cuda_stream);
 
+/* ------------------------------------------------------------ tensor-core check */
+
+/*
+ * isax_tc_selftest - one tile of the tensor-core contraction used by the
+ * BF16-filtered batch path, exposed to check the machinery on its own (the
+ * paper has no counterpart): d[i][j] = sum_t a[i][t] * b[j][t] accumulated in
+ * FP32, for i < 128, j < n_cols, t < 256.
+ *   a [128][256] and b [n_cols][256] BF16 bit patterns in device memory,
+ *   16-byte aligned, row-major; d [128][n_cols] fp32 device output.
+ *   n_cols: a multiple of 16 in [16, 256] (else ISAX_ERR_INVALID_ARG).
+ * Synchronises cuda_stream; ISAX_ERR_TIMEOUT if a bounded wait gave up.
+ */
+isax_status isax_tc_selftest(const uint16_t* a, const uint16_t* b, int32_t n_cols, float* d,
+                             void* cuda_stream);
+
 /* ------------------------------------------------------------ tracing */
 
 typedef struct isax_kernel_time {

@@ -19,7 +19,7 @@ __all__ = [
     "isax_build_index", "isax_query_knn", "isax_query_knn_batch", "isax_free_index",
     "isax_last_error", "isax_get_index_info", "isax_index_export", "isax_summarize",
     "isax_set_allocator", "isax_profile", "isax_profile_report", "isax_launch_count",
-    "isax_query_knn_noalloc",
+    "isax_query_knn_noalloc", "isax_tc_selftest",
 ]
 
 W = 16
@@ -122,6 +122,8 @@ def lib():
         L.isax_query_knn_noalloc.restype = st
         L.isax_launch_count.argtypes = []
         L.isax_launch_count.restype = ctypes.c_uint64
+        L.isax_tc_selftest.argtypes = [vp, vp, i32, vp, vp]
+        L.isax_tc_selftest.restype = st
         _lib = L
     return _lib
 
@@ -204,6 +206,12 @@ def isax_profile_report():
 
 def isax_launch_count():
     return int(lib().isax_launch_count())
+
+
+def isax_tc_selftest(a_ptr, b_ptr, n_cols, d_ptr, stream=0):
+    """d [128][n_cols] fp32 = a [128][256] bf16 . b [n_cols][256] bf16 ^T on the
+    tensor cores (device pointers)."""
+    _check(lib().isax_tc_selftest(a_ptr, b_ptr, n_cols, d_ptr, stream))
 
 
 # ------------------------------------------------------------------ convenience

@@ -9,8 +9,9 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libisaxgpu.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["isax_api.cu", "isax_build.cu", "isax_query.cu", "isax_profile.cu", "isax_noalloc.cu"]
-HEADERS = ["isax_common.cuh", "isax_kernels_util.cuh"]
+SOURCES = ["isax_api.cu", "isax_build.cu", "isax_query.cu", "isax_profile.cu", "isax_noalloc.cu",
+           "isax_tc.cu"]
+HEADERS = ["isax_common.cuh", "isax_kernels_util.cuh", "isax_tc.cuh"]
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = [GENCODE, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-Xptxas", "-warn-spills", "--expt-relaxed-constexpr"]

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "isax_common.cuh"
+#include "isax_tc.cuh"
 
 namespace isax {
 
@@ -292,6 +293,17 @@ isax_status isax_summarize(const float* series, int64_t N, int32_t n, int32_t ca
         check(!(mem_flags & ISAX_MEM_OUTPUT_DEVICE) || !out_sax || aligned16(out_sax),
               "device out_sax must be 16-byte aligned");
         summarize_impl(series, N, n, cardinality, mem_flags, out_sax, out_paa, (cudaStream_t)cuda_stream);
+    });
+}
+
+isax_status isax_tc_selftest(const uint16_t* a, const uint16_t* b, int32_t n_cols, float* d,
+                             void* cuda_stream) {
+    return guarded([&] {
+        check(a && b && d, "NULL pointer");
+        check(n_cols >= 16 && n_cols <= 256 && n_cols % 16 == 0,
+              "n_cols must be a multiple of 16 in [16, 256]");
+        check(aligned16(a) && aligned16(b), "a and b must be 16-byte aligned");
+        tc_selftest(a, b, n_cols, d, (cudaStream_t)cuda_stream);
     });
 }
 

@@ -102,3 +102,10 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.replace("Oracle", "").lower() or f.endswith(".md"), f
+
+
+def test_tc_selftest_validation(lib):
+    a = np.zeros((128, 256), np.uint16)
+    _expect(lib.isax_tc_selftest(a.ctypes.data, a.ctypes.data, 24, a.ctypes.data, None), 1,
+            "multiple of 16")
+    _expect(lib.isax_tc_selftest(None, a.ctypes.data, 32, a.ctypes.data, None), 1, "NULL")
