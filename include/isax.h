@@ -205,6 +205,39 @@ isax_status isax_query_knn_noalloc(const isax_index* ix, const float* q, int32_t
                                    uint32_t mem_flags, int64_t* out_idx, float* out_dist,
                                    isax_query_stats* stats, void* cuda_stream);
 
+/* ------------------------------------------------------------ BF16-filtered batch */
+
+/*
+ * isax_query_knn_batch_bf16 - exact k-NN of B queries, the same answers as
+ * isax_query_knn_batch (same arguments and layouts), for large batches.  The
+ * paper refines by computing real distances one series at a time (Section III,
+ * MESSI Approach); here the distances of a whole batch to the series of the
+ * leaves that the envelope bound does not prune are first computed on the
+ * tensor cores as ||x||^2 + ||q||^2 - 2 bf16(x).bf16(q) with FP32 accumulation,
+ * and used only as a filter: a series is dropped only when that value minus a
+ * rigorous bound on its rounding error (about 4.07 in squared-distance units for
+ * z-normalised series of length 256) exceeds an upper bound of the query's k-th
+ * best squared distance.  Every other series is re-checked with the exact fp32
+ * distance of the single-query path, and the k best are ordered as there (FP64
+ * where fp32 cannot separate them).  Each leaf's rows are read once per group of
+ * up to 256 queries that need them.
+ *   Requires n % 64 == 0 (else ISAX_ERR_INVALID_ARG).  The first call builds a
+ *   BF16 copy of the collection (2 N n bytes of device memory, held until the
+ *   index is freed; isax_prepare_bf16 builds it ahead of time).  Batches run in
+ *   passes of up to 4096 queries; per pass it holds about
+ *   B (4 L + 50 KB) bytes of scratch (L = leaves).  A query whose candidate
+ *   window overflows is answered again by the single-query path (stats.reruns).
+ *   ISAX_ERR_TIMEOUT if a bounded wait inside the filter gave up.
+ */
+isax_status isax_query_knn_batch_bf16(const isax_index* ix, const float* Q, int32_t B, int32_t k,
+                                      uint32_t mem_flags, int64_t* out_idx, float* out_dist,
+                                      isax_query_stats* stats, void* cuda_stream);
+
+/* Build the BF16 copy used by isax_query_knn_batch_bf16 now (synchronises
+ * cuda_stream).  ISAX_ERR_INVALID_ARG when n % 64 != 0 or values are too large
+ * for the error bound (|x| >= 1e15). */
+isax_status isax_prepare_bf16(isax_index* ix, void* cuda_stream);
+
 /* ------------------------------------------------------------ tensor-core check */
 
 /*

@@ -19,7 +19,8 @@ __all__ = [
     "isax_build_index", "isax_query_knn", "isax_query_knn_batch", "isax_free_index",
     "isax_last_error", "isax_get_index_info", "isax_index_export", "isax_summarize",
     "isax_set_allocator", "isax_profile", "isax_profile_report", "isax_launch_count",
-    "isax_query_knn_noalloc", "isax_tc_selftest",
+    "isax_query_knn_noalloc", "isax_tc_selftest", "isax_query_knn_batch_bf16",
+    "isax_prepare_bf16",
 ]
 
 W = 16
@@ -124,6 +125,11 @@ def lib():
         L.isax_launch_count.restype = ctypes.c_uint64
         L.isax_tc_selftest.argtypes = [vp, vp, i32, vp, vp]
         L.isax_tc_selftest.restype = st
+        L.isax_query_knn_batch_bf16.argtypes = [vp, vp, i32, i32, u32, vp, vp,
+                                                ctypes.POINTER(QueryStats), vp]
+        L.isax_query_knn_batch_bf16.restype = st
+        L.isax_prepare_bf16.argtypes = [vp, vp]
+        L.isax_prepare_bf16.restype = st
         _lib = L
     return _lib
 
@@ -164,6 +170,16 @@ def isax_query_knn_batch(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_pt
                          stream=0):
     _check(lib().isax_query_knn_batch(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_ptr,
                                       stats, stream))
+
+
+def isax_query_knn_batch_bf16(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_ptr, stats=None,
+                              stream=0):
+    _check(lib().isax_query_knn_batch_bf16(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_ptr,
+                                           stats, stream))
+
+
+def isax_prepare_bf16(index, stream=0):
+    _check(lib().isax_prepare_bf16(index, stream))
 
 
 def isax_free_index(index):
@@ -296,6 +312,14 @@ class Index:
     def query_batch(self, Q, k=1, stats=False, stream=None):
         return self._run(Q, k, stats, stream, batch=True)
 
+    def query_batch_bf16(self, Q, k=1, stats=False, stream=None):
+        """Same answers as query_batch, through the tensor-core (BF16) filter."""
+        return self._run(Q, k, stats, stream, batch="bf16")
+
+    def prepare_bf16(self, stream=None):
+        """Build the BF16 copy of the collection used by query_batch_bf16."""
+        isax_prepare_bf16(self._h, _stream_of(None, stream))
+
     def _run(self, q, k, want_stats, stream, batch):
         ptr, on_dev, keep, shape = _buffer(q)
         B = shape[0] if batch else 1
@@ -313,7 +337,9 @@ class Index:
             dist = np.empty((B, k), np.float32)
             ip, dp, flags = idx.ctypes.data, dist.ctypes.data, 0
         stats = (QueryStats * B)()
-        if batch:
+        if batch == "bf16":
+            isax_query_knn_batch_bf16(self._h, ptr, B, k, flags, ip, dp, stats, st)
+        elif batch:
             isax_query_knn_batch(self._h, ptr, B, k, flags, ip, dp, stats, st)
         else:
             isax_query_knn(self._h, ptr, k, flags, ip, dp, stats[0], st)

@@ -296,6 +296,48 @@ isax_status isax_summarize(const float* series, int64_t N, int32_t n, int32_t ca
     });
 }
 
+isax_status isax_prepare_bf16(isax_index* ix, void* cuda_stream) {
+    return guarded([&] {
+        check(ix != nullptr, "index is NULL");
+        DeviceGuard dg(ix->device);
+        std::lock_guard<std::mutex> lk(*static_cast<std::mutex*>(ix->mu));
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        prepare_tc(ix, st);
+        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    });
+}
+
+isax_status isax_query_knn_batch_bf16(const isax_index* cix, const float* Q, int32_t B, int32_t k,
+                                      uint32_t mem_flags, int64_t* out_idx, float* out_dist,
+                                      isax_query_stats* stats, void* cuda_stream) {
+    return guarded([&] {
+        check(cix != nullptr, "index is NULL");
+        check(B >= 0, "B must be >= 0");
+        check(B == 0 || (Q != nullptr && out_idx != nullptr && out_dist != nullptr),
+              "NULL queries or outputs");
+        check((mem_flags & ~(uint32_t)(ISAX_MEM_INPUT_DEVICE | ISAX_MEM_OUTPUT_DEVICE)) == 0,
+              "unknown mem_flags bits");
+        check(k >= 1 && k <= ISAX_MAX_K && (int64_t)k <= cix->d.N, "k must be in [1, min(N, 1024)]");
+        check(cix->d.n % 64 == 0, "the BF16 filter needs n to be a multiple of 64");
+        check(!(mem_flags & ISAX_MEM_INPUT_DEVICE) || aligned16(Q), "device queries must be 16-byte aligned");
+        isax_index* ix = const_cast<isax_index*>(cix);
+        DeviceGuard dg(ix->device);
+        std::lock_guard<std::mutex> lk(*static_cast<std::mutex*>(ix->mu));
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        if (B == 0) return;
+        struct Ctx {
+            const isax_index* ix;
+            isax_query_stats* stats;
+        } ctx{ix, stats};
+        auto fill = [](void* p, int b, const QCtl& c, int reruns) {
+            Ctx* cx = static_cast<Ctx*>(p);
+            if (cx->stats) fill_stats(cx->stats + b, cx->ix, c, reruns);
+        };
+        query_batch_tc(ix, Q, B, k, mem_flags, out_idx, out_dist, fill, &ctx, st);
+        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    });
+}
+
 isax_status isax_tc_selftest(const uint16_t* a, const uint16_t* b, int32_t n_cols, float* d,
                              void* cuda_stream) {
     return guarded([&] {

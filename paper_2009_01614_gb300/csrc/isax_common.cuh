@@ -138,6 +138,22 @@ void free_index_arrays(isax_index* ix, cudaStream_t st);
 void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st);
 void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st);
 void launch_breakpoints(int card, float* bp, cudaStream_t st);
+// batched query kernels (query b of the batch owns scratch ss[b])
+void launch_bq_prep(isax_index* ix, const QueryScratch* ss, int B, int k, int neighbors,
+                    cudaStream_t st);
+void launch_bq_approx(isax_index* ix, const QueryScratch* ss, int B, int k, int neighbors,
+                      cudaStream_t st);
+void launch_bq_pairs(isax_index* ix, const QueryScratch* ss, int B, int k, int mode,
+                     uint32_t* leaf_count, const uint32_t* leaf_off, uint32_t* leaf_cursor,
+                     uint32_t* pairs, cudaStream_t st);
+void launch_bq_recheck(isax_index* ix, const QueryScratch* ss, int k, const uint4* cand,
+                       const uint32_t* cand_count, uint32_t cap, cudaStream_t st);
+void launch_bq_finalize(isax_index* ix, const QueryScratch* ss, int B, int k, cudaStream_t st);
+// the tensor-core filtered batch (isax_tc.cu)
+void prepare_tc(isax_index* ix, cudaStream_t st);
+void query_batch_tc(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags, int64_t* out_idx,
+                    float* out_dist, isax_query_stats_fill fill, void* fill_ctx, cudaStream_t st);
+void free_tc_state(isax_index* ix, cudaStream_t st);
 void launch_summarize(const float* x, int64_t N, int n, int card, const float* bp,
                       uint4* sax, unsigned long long* keys, uint32_t* ids, float* paa_out,
                       unsigned int* maxabs_bits, unsigned int* nonfinite, int num_sms,
@@ -165,4 +181,5 @@ struct isax_index {
     void* mu;      // std::mutex*
     void* graphs;  // captured query launch sequences (isax_query.cu)
     void* pool;    // extra query slots for concurrent batches (isax_query.cu)
+    void* tc;      // BF16 copy and batch scratch of the tensor-core filter (isax_tc.cu)
 };

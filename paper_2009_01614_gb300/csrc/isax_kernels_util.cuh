@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "isax_common.cuh"
+
 namespace isax {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -37,6 +39,28 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 }
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
     return *(volatile const uint32_t*)p;
+}
+
+// packed (fp32 value bits << 32 | id): for non-negative values the integer
+// order is the (value, id) order
+__device__ __forceinline__ unsigned long long pack_key(float d2, uint32_t id) {
+    return ((unsigned long long)__float_as_uint(d2) << 32) | id;
+}
+__device__ __forceinline__ float key_d2(unsigned long long key) {
+    return __uint_as_float((uint32_t)(key >> 32));
+}
+
+// insert key into the ascending array slots[0..k): each step puts the smaller
+// value in the slot and carries the larger one down; values only decrease, so
+// after all concurrent cascades the array holds the k smallest keys, sorted.
+__device__ inline void topk_insert(unsigned long long* slots, int k, unsigned long long key) {
+    int j = 0;
+    while (j < k && ld_volatile_u64(&slots[j]) <= key) ++j;
+    for (; j < k; ++j) {
+        unsigned long long old = atomicMin(&slots[j], key);
+        if (old == EMPTY_SLOT) return;
+        if (old > key) key = old;
+    }
 }
 
 // symbol of v: number of breakpoints beta_t <= v, by binary search over

@@ -40,12 +40,6 @@
 namespace isax {
 
 // ---------------------------------------------------------------- helpers
-__device__ __forceinline__ unsigned long long pack_key(float d2, uint32_t orig) {
-    return ((unsigned long long)__float_as_uint(d2) << 32) | orig;
-}
-__device__ __forceinline__ float key_d2(unsigned long long key) {
-    return __uint_as_float((uint32_t)(key >> 32));
-}
 
 // squared lower-bound threshold: prune iff bound > this (see file comment)
 __device__ float lb_threshold(unsigned long long kth, double delta, double E) {
@@ -62,18 +56,6 @@ __device__ __forceinline__ int bin_of(float lb, float thr) {
     return b < 0 ? 0 : (b >= NBINS ? NBINS - 1 : b);
 }
 
-// insert key into the ascending array slots[0..k): each step puts the smaller
-// value in the slot and carries the larger one down; values only decrease, so
-// after all concurrent cascades the array holds the k smallest keys, sorted.
-__device__ void topk_insert(unsigned long long* slots, int k, unsigned long long key) {
-    int j = 0;
-    while (j < k && ld_volatile_u64(&slots[j]) <= key) ++j;
-    for (; j < k; ++j) {
-        unsigned long long old = atomicMin(&slots[j], key);
-        if (old == EMPTY_SLOT) return;
-        if (old > key) key = old;
-    }
-}
 
 // one refined series (by one thread): update the k best, keep as candidate
 __device__ void consider(const QueryScratch& s, int k, unsigned long long key, uint32_t pos,
@@ -207,7 +189,10 @@ __device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ ta
 constexpr int PREP_THREADS = 256;
 constexpr int APPROX_NEIGHBORS = 2;
 
-__global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, QueryScratch s, int k) {
+// One query's preparation by one CTA of PREP_THREADS threads; `neighbors`
+// leaves on each side of the descent leaf join the approximate answer.
+__device__ __forceinline__ void q_prep_body(const DevIndex& ix, const QueryScratch& s, int k,
+                                            int neighbors) {
     __shared__ float bp[MAX_CARD + 1];
     __shared__ float qv[MAX_LEN];
     __shared__ float qpaa[W];
@@ -289,8 +274,8 @@ __global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, Query
         // approximate-answer range: that leaf and its APPROX_NEIGHBORS neighbours on
         // each side in key order (the nearest iSAX words), widened until it holds
         // >= k series
-        int64_t a0 = dl - APPROX_NEIGHBORS > 0 ? dl - APPROX_NEIGHBORS : 0;
-        int64_t a1 = dl + 1 + APPROX_NEIGHBORS < L ? dl + 1 + APPROX_NEIGHBORS : L;
+        int64_t a0 = dl - neighbors > 0 ? dl - neighbors : 0;
+        int64_t a1 = dl + 1 + neighbors < L ? dl + 1 + neighbors : L;
         int64_t tot = (int64_t)ix.leaf_begin[a1] - ix.leaf_begin[a0];
         while (tot < k) {
             if (a1 < L) {
@@ -331,9 +316,18 @@ __global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, Query
     }
 }
 
+__global__ void __launch_bounds__(PREP_THREADS) q_prep_kernel(DevIndex ix, QueryScratch s, int k) {
+    q_prep_body(ix, s, k, APPROX_NEIGHBORS);
+}
+// a batch: query blockIdx.y
+__global__ void __launch_bounds__(PREP_THREADS) bq_prep_kernel(DevIndex ix, const QueryScratch* ss,
+                                                                int k, int neighbors) {
+    q_prep_body(ix, ss[blockIdx.y], k, neighbors);
+}
+
 // ---------------------------------------------------------------- q_approx
 template <int NV>
-__global__ void __launch_bounds__(256) q_approx_kernel(DevIndex ix, QueryScratch s, int k) {
+__device__ __forceinline__ void q_approx_body(const DevIndex& ix, const QueryScratch& s, int k) {
     const QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
     const int lane = threadIdx.x & 31;
@@ -355,6 +349,14 @@ __global__ void __launch_bounds__(256) q_approx_kernel(DevIndex ix, QueryScratch
         ++refined;
     }
     if (lane == 0 && refined) atomicAdd(&s.ctl->series_refined, refined);
+}
+template <int NV>
+__global__ void __launch_bounds__(256) q_approx_kernel(DevIndex ix, QueryScratch s, int k) {
+    q_approx_body<NV>(ix, s, k);
+}
+template <int NV>
+__global__ void __launch_bounds__(256) bq_approx_kernel(DevIndex ix, const QueryScratch* ss, int k) {
+    q_approx_body<NV>(ix, ss[blockIdx.y], k);
 }
 
 // ---------------------------------------------------------------- q_leaf_lb
@@ -742,7 +744,7 @@ __device__ __forceinline__ void bitonic_sort_smem(unsigned long long* sk, uint32
 // Candidates within (1 + 3 delta) of the final k-th best (the window) are
 // re-ranked in FP64 by (d2, row).  One filter pass stages the window; a window
 // larger than the stage is processed in rounds, merging a running top-k.
-__global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, QueryScratch s, int k) {
+__device__ __forceinline__ void q_finalize_body(const DevIndex& ix, const QueryScratch& s, int k) {
     __shared__ unsigned long long sk[FIN_CAP];
     __shared__ uint32_t sid[FIN_CAP];
     __shared__ uint32_t stage[FIN_THREADS];
@@ -875,6 +877,157 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
         if (attempted > s.cand_cap) c->flags |= QF_OVERFLOW;
     }
 }
+__global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, QueryScratch s, int k) {
+    q_finalize_body(ix, s, k);
+}
+__global__ void __launch_bounds__(FIN_THREADS) bq_finalize_kernel(DevIndex ix, const QueryScratch* ss,
+                                                                   int k) {
+    q_finalize_body(ix, ss[blockIdx.y], k);
+}
+
+// ================================================================ batched kernels
+// Kernels of the batched path with the tensor-core filter (the contraction
+// itself is in isax_tc.cu).  Query b of a batch owns scratch ss[b].
+
+// (leaf, query) pairs that the leaf envelope bound does not prune, against
+// each query's threshold after its approximate answer; a query's own
+// approximate-answer leaves are left out (already refined exactly).
+// Lane = query, warp = leaf: one ballot per (leaf, 32 queries).
+// mode 0 counts pairs per leaf (and leaves / series per query); mode 1 lists
+// the queries of every leaf at leaf_off[l] onwards.
+constexpr int BP_WARPS = 8;
+constexpr int BP_LEAVES = 256;  // leaves per CTA
+
+__global__ void __launch_bounds__(BP_WARPS * 32) bq_pairs_kernel(
+    DevIndex ix, const QueryScratch* ss, int B, int k, int mode, uint32_t* __restrict__ leaf_count,
+    const uint32_t* __restrict__ leaf_off, uint32_t* __restrict__ leaf_cursor,
+    uint32_t* __restrict__ pairs) {
+    __shared__ float bp[MAX_CARD + 1];
+    __shared__ unsigned long long part_l[BP_WARPS][32], part_s[BP_WARPS][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.y * 32 + lane;
+    for (int i = threadIdx.x; i <= ix.card; i += blockDim.x) bp[i] = ix.bp[i];
+    float qp[W];
+    int qs[W];
+    float thr = -1.0f;  // a negative threshold takes no leaf
+    int64_t a0 = 0, a1 = 0;
+    if (b < B) {
+        const QCtl* c = ss[b].ctl;
+        if (!(c->flags & QF_NONFINITE)) {
+            thr = lb_threshold(ld_volatile_u64(&ss[b].topk[k - 1]), c->delta, c->E);
+            a0 = c->approx_leaf;
+            a1 = c->approx_end;
+        }
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            qp[i] = c->qpaa[i];
+            qs[i] = c->qsym[i];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            qp[i] = 0.0f;
+            qs[i] = 0;
+        }
+    }
+    __syncthreads();
+    const float mf = (float)(ix.n / W);
+    const int64_t l0 = (int64_t)blockIdx.x * BP_LEAVES;
+    const int64_t l1 = l0 + BP_LEAVES < ix.L ? l0 + BP_LEAVES : ix.L;
+    unsigned long long my_leaves = 0, my_series = 0;
+    for (int64_t l = l0 + warp; l < l1; l += BP_WARPS) {
+        const uint4 mn = ix.env[2 * l], mx = ix.env[2 * l + 1];
+        const uint32_t wn[4] = {mn.x, mn.y, mn.z, mn.w}, wx[4] = {mx.x, mx.y, mx.z, mx.w};
+        float lb = 0.0f;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const int lo = (wn[i >> 2] >> (8 * (i & 3))) & 255, hi = (wx[i >> 2] >> (8 * (i & 3))) & 255;
+            if (qs[i] < lo) {
+                const float d = bp[lo] - qp[i];
+                lb += (d * d) * mf;
+            } else if (qs[i] > hi) {
+                const float d = qp[i] - bp[hi + 1];
+                lb += (d * d) * mf;
+            }
+        }
+        const bool take = lb <= thr && !(l >= a0 && l < a1);
+        const unsigned m = __ballot_sync(FULL, take);
+        if (m == 0) continue;
+        if (mode == 0) {
+            if (lane == 0) atomicAdd(&leaf_count[l], (uint32_t)__popc(m));
+            if (take) {
+                ++my_leaves;
+                my_series += ix.leaf_begin[l + 1] - ix.leaf_begin[l];
+            }
+        } else {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&leaf_cursor[l], (uint32_t)__popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (take) pairs[leaf_off[l] + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)b;
+        }
+    }
+    if (mode == 0) {
+        part_l[warp][lane] = my_leaves;
+        part_s[warp][lane] = my_series;
+        __syncthreads();
+        if (warp == 0 && b < B) {
+            unsigned long long tl = 0, ts = 0;
+            for (int w = 0; w < BP_WARPS; ++w) {
+                tl += part_l[w][lane];
+                ts += part_s[w][lane];
+            }
+            if (tl) {
+                atomicAdd(&ss[b].ctl->leaves_queued, tl);
+                atomicAdd(&ss[b].ctl->series_lb, ts);
+            }
+        }
+    }
+}
+
+// Exact fp32 check of the rows the tensor-core filter kept: one warp per
+// (row, query) record {position, query, filtered d2 bits, its error bound
+// bits}.  A record whose filtered distance minus its bound already exceeds the
+// query's current k-th best (with the fp32 slack) cannot be among the k best
+// and is skipped; the others take the single-query path's refinement (same
+// fp32 summation, same candidate window).
+template <int NV>
+__global__ void __launch_bounds__(256) bq_recheck_kernel(DevIndex ix, const QueryScratch* ss, int k,
+                                                         const uint4* __restrict__ cand,
+                                                         const uint32_t* __restrict__ cand_count,
+                                                         uint32_t cap) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t total = *cand_count;
+    const uint32_t M = total < cap ? total : cap;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = gw; i < M; i += nw) {
+        const uint4 r = cand[i];
+        const QueryScratch& s = ss[r.y];
+        const double delta = s.ctl->delta;
+        // one k-th best for the whole warp: lane 0 may still be finishing the
+        // previous record's update, and the skip and early-abandon decisions
+        // below must be warp-uniform (the distance is a warp reduction)
+        __syncwarp();
+        unsigned long long kth = 0;
+        if (lane == 0) kth = ld_volatile_u64(&s.topk[k - 1]);
+        kth = __shfl_sync(FULL, kth, 0);
+        if (kth != EMPTY_SLOT && (double)__uint_as_float(r.z) - (double)__uint_as_float(r.w) >
+                                     (double)key_d2(kth) * (1.0 + 5.0 * delta))
+            continue;
+        float4 qv[NV ? NV : 1];
+        load_q<NV>(s.q, qv);
+        bool ab;
+        const float d2 = warp_d2<NV>(ix, (int64_t)r.x, qv, s.q, abandon_limit(kth, delta), ab);
+        if (lane == 0) {
+            atomicAdd(&s.ctl->series_refined, 1ull);
+            if (!ab) {
+                const unsigned long long kk = ld_volatile_u64(&s.topk[k - 1]);
+                if (kk == EMPTY_SLOT || (double)d2 <= (double)key_d2(kk) * (1.0 + 3.0 * delta))
+                    consider(s, k, pack_key(d2, ix.orig[r.x]), r.x, delta);
+            }
+        }
+    }
+}
 
 // ================================================================ host side
 static void free_scratch(QueryScratch& q, cudaStream_t st) {
@@ -973,6 +1126,7 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
         ix->graphs = nullptr;
     }
     free_slot_pool(ix, st);
+    free_tc_state(ix, st);
     free_query_scratch(ix, st);
     void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp};
     for (void* p : ptrs)
@@ -1213,6 +1367,73 @@ void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t m
         if (fill) fill(fill_ctx, b, c, reruns);
     }
     if (nonfinite) throw Error{ISAX_ERR_INVALID_ARG, "a query contains a non-finite value"};
+}
+
+// ---------------------------------------------------------------- batched launchers
+void launch_bq_prep(isax_index* ix, const QueryScratch* ss, int B, int k, int neighbors,
+                    cudaStream_t st) {
+    ISAX_LAUNCH("bq_prep", st);
+    bq_prep_kernel<<<dim3(1, B), PREP_THREADS, 0, st>>>(ix->d, ss, k, neighbors);
+    ISAX_CUDA_TRY(cudaGetLastError());
+}
+
+template <int NV>
+static void launch_bq_approx_nv(isax_index* ix, const QueryScratch* ss, int B, int k, int blocks,
+                                cudaStream_t st) {
+    ISAX_LAUNCH("bq_approx", st);
+    bq_approx_kernel<NV><<<dim3(blocks, B), 256, 0, st>>>(ix->d, ss, k);
+}
+
+template <int NV>
+static void launch_bq_recheck_nv(isax_index* ix, const QueryScratch* ss, int k, const uint4* cand,
+                                 const uint32_t* cand_count, uint32_t cap, cudaStream_t st) {
+    ISAX_LAUNCH("bq_recheck", st);
+    bq_recheck_kernel<NV><<<ix->num_sms * 8, 256, 0, st>>>(ix->d, ss, k, cand, cand_count, cap);
+}
+
+#define ISAX_NV_DISPATCH(n, CALL)                 \
+    do {                                          \
+        switch ((n) % 128 == 0 ? (n) / 128 : 0) { \
+            case 1: CALL(1); break;               \
+            case 2: CALL(2); break;               \
+            case 4: CALL(4); break;               \
+            case 8: CALL(8); break;               \
+            default: CALL(0); break;              \
+        }                                         \
+    } while (0)
+
+void launch_bq_approx(isax_index* ix, const QueryScratch* ss, int B, int k, int neighbors,
+                      cudaStream_t st) {
+    const int per_query = (int)std::min<int64_t>(
+        16, std::max<int64_t>(1, ((int64_t)(2 * neighbors + 1) * ix->d.leaf_size + 63) / 64));
+#define ISAX_CALL(NV) launch_bq_approx_nv<NV>(ix, ss, B, k, per_query, st)
+    ISAX_NV_DISPATCH(ix->d.n, ISAX_CALL);
+#undef ISAX_CALL
+    ISAX_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_bq_pairs(isax_index* ix, const QueryScratch* ss, int B, int k, int mode,
+                     uint32_t* leaf_count, const uint32_t* leaf_off, uint32_t* leaf_cursor,
+                     uint32_t* pairs, cudaStream_t st) {
+    const dim3 grid((unsigned)((ix->d.L + BP_LEAVES - 1) / BP_LEAVES), (unsigned)((B + 31) / 32));
+    ISAX_LAUNCH(mode == 0 ? "bq_pairs_count" : "bq_pairs_fill", st);
+    bq_pairs_kernel<<<grid, BP_WARPS * 32, 0, st>>>(ix->d, ss, B, k, mode, leaf_count, leaf_off,
+                                                   leaf_cursor, pairs);
+    ISAX_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_bq_recheck(isax_index* ix, const QueryScratch* ss, int k, const uint4* cand,
+                       const uint32_t* cand_count, uint32_t cap, cudaStream_t st) {
+#define ISAX_CALL(NV) launch_bq_recheck_nv<NV>(ix, ss, k, cand, cand_count, cap, st)
+    ISAX_NV_DISPATCH(ix->d.n, ISAX_CALL);
+#undef ISAX_CALL
+    ISAX_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_bq_finalize(isax_index* ix, const QueryScratch* ss, int B, int k, cudaStream_t st) {
+    ISAX_LAUNCH("bq_finalize", st);
+    bq_finalize_kernel<<<dim3(1, B), FIN_THREADS, 0, st>>>(ix->d, ss, k);
+    ISAX_CUDA_TRY(cudaGetLastError());
 }
 
 }  // namespace isax

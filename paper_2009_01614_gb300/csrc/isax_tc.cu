@@ -8,8 +8,12 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <string.h>
+
+#include <algorithm>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "isax_common.cuh"
 #include "isax_kernels_util.cuh"
@@ -35,11 +39,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return g_encode;
 }
 
-// rows x 256 BF16 matrix (row pitch 512 B), boxes of 64 elements x box_rows rows,
+// rows x cols BF16 matrix (row-major), boxes of 64 elements x box_rows rows,
 // 128-byte swizzle, rows past the end read as zeros
-void make_tmap_bf16_rows(CUtensorMap* tm, const void* base, uint64_t rows, uint32_t box_rows) {
-    const cuuint64_t dims[2] = {(cuuint64_t)TC_K, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)TC_K * 2};
+static void make_tmap_bf16_box(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols,
+                               uint32_t box_rows) {
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
     const cuuint32_t box[2] = {(cuuint32_t)TC_KATOM, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = encode_fn()(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
@@ -48,6 +53,12 @@ void make_tmap_bf16_rows(CUtensorMap* tm, const void* base, uint64_t rows, uint3
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         throw Error{ISAX_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+}
+static void make_tmap_bf16_rows(CUtensorMap* tm, const void* base, uint64_t rows, uint32_t box_rows) {
+    make_tmap_bf16_box(tm, base, rows, TC_K, box_rows);
+}
+static void make_tmap_bf16(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols) {
+    make_tmap_bf16_box(tm, base, rows, cols, TC_M);
 }
 
 // ---------------------------------------------------------------- device: tcgen05
@@ -92,6 +103,19 @@ __device__ __forceinline__ void tc_ld_x32(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+// this warp's 32 TMEM lanes x 16 consecutive FP32 columns starting at taddr
+__device__ __forceinline__ void tc_ld_x16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* tm, int x, int y,
                                             uint64_t* bar) {
@@ -207,6 +231,699 @@ void tc_selftest(const void* A, const void* B, int N, float* D, cudaStream_t st)
     ISAX_CUDA_TRY(cudaStreamSynchronize(st));
     dev_free(err, st);
     if (h) throw Error{ISAX_ERR_TIMEOUT, "tensor-core self test: a wait gave up (" + std::to_string(h) + ")"};
+}
+
+// ================================================================ BF16 filter
+// Batched exact k-NN with the refinement's distance computation moved to the
+// tensor cores as a filter:
+//   d~2(x, q) = ||x||^2 + ||q||^2 - 2 bf16(x) . bf16(q)   (FP32 accumulate)
+// is within E(x, q) of the exact squared distance (bound below), so a row can
+// be among a query's k best only if d~2 - E <= (an upper bound of the k-th
+// best squared distance).  Those rows are re-checked with the exact fp32
+// distance of the single-query path and the k best are ordered as there
+// (FP64 only within fp32 error of each other): the answers equal the oracle's.
+//
+// Work is leaf-major: every leaf that the envelope bound leaves to a set of
+// queries is contracted once against all of them (up to TF_NQ per work item),
+// so the leaf's rows are read once per batch instead of once per query.
+//
+// Error bound.  With u = 2^-24, u_b = 2^-8 (BF16 unit roundoff), X >= ||x||,
+// Q >= ||q||: rounding x and q to BF16 moves x.q by at most (2 u_b + u_b^2) X Q;
+// the tensor-core FP32 sum of the exact BF16 products is taken to err by at
+// most n 2^-21 sum|x_i q_i| (four times the truncating-summation bound, which
+// leaves room for the hardware's internal alignment); the squared norms
+// (FP64 sums rounded to fp32), their fp32 sum and the final fma add at most
+// 4 u (X^2 + Q^2) + 2.01 u (1 + u_b)^2 X Q.  Hence
+//   E = [2 (2 u_b + u_b^2) + 2 n 2^-21 (1 + u_b)^2 + 2.01 u (1 + u_b)^2] X Q
+//       + 4 u (X^2 + Q^2),
+// evaluated in FP64 with X the largest row norm of the leaf and Q the query
+// norm, both rounded up (about 4.07 for z-normalised series of length 256).
+
+constexpr int TF_NQ = 256;           // queries per work item (MMA N, at most)
+constexpr int TF_STAGES = 5;         // A ring: one 128-row x 64-element K-atom each
+constexpr int TF_EPI_WARPS = 8;      // epilogue warps (two per TMEM lane quarter)
+constexpr int TF_THREADS = (TF_EPI_WARPS + 2) * 32;  // + TMA warp + MMA warp
+constexpr uint32_t TF_ATOM_BYTES = TC_M * TC_KATOM * 2;
+constexpr uint32_t TF_TMEM_COLS = 512;  // two accumulators of up to TF_NQ columns
+constexpr uint32_t TF_WAIT = 1u << 22;  // bounded mbarrier waits
+constexpr int TF_QCAP = 4096;        // per-query candidate window entries
+constexpr int TF_MAX_B = 4096;       // queries per pass
+constexpr int TC_APPROX_NEIGHBORS = 2;  // approximate answer: descent leaf +- 2 leaves
+
+static size_t smem_max_tf() { return 1024 + (size_t)65536 * 2 + (size_t)TF_STAGES * TF_ATOM_BYTES; }
+
+// queries per work item for series length n: the B tile (nq x n BF16) fits 128 KB
+static int tf_nq_max(int n) {
+    int q = 65536 / n;
+    q = q > TF_NQ ? TF_NQ : q;
+    return q & ~15;
+}
+
+__device__ __forceinline__ int tf_nq_max_dev(int n) {
+    int q = 65536 / n;
+    q = q > TF_NQ ? TF_NQ : q;
+    return q & ~15;
+}
+
+struct TcView {
+    const uint32_t* leaf_begin;
+    const float* xn;           // [N] squared row norms (fp32), leaf order
+    const float* leaf_xnorm;   // [L] largest row norm of the leaf, rounded up
+    const uint4* items;        // work items {leaf, first pair, queries, 0}
+    const uint32_t* n_items;
+    uint32_t* claim;
+    const uint32_t* pairs;     // query of each pair, grouped by leaf
+    const uint16_t* qb;        // [B][n] BF16 queries
+    const float* qn;           // [B] squared query norms (fp32)
+    const float* qnorm;        // [B] query norms, rounded up
+    const QueryScratch* ss;    // [B]
+    unsigned long long* utop;  // [B][MAX_K] k smallest upper bounds d~2 + E (packed with the position)
+    uint4* cand;               // kept rows {position, query, d~2 bits, E bits}
+    uint32_t* cand_count;
+    uint32_t cand_cap;
+    uint32_t* err;
+    int n, k;
+    double c_xq, c_sq;
+};
+
+__device__ __forceinline__ void tf_fail(volatile int* abort_flag, uint32_t* err, uint32_t code) {
+    *abort_flag = 1;
+    atomicOr(err, code);
+}
+
+__global__ void __launch_bounds__(TF_THREADS, 1)
+    tc_filter_kernel(const __grid_constant__ CUtensorMap tmX, TcView v) {
+    extern __shared__ unsigned char sm_raw[];
+    __shared__ __align__(8) uint64_t full[TF_STAGES], empty[TF_STAGES], accf[2], acce[2], fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ uint4 item_s;
+    __shared__ int item_ok;
+    __shared__ volatile int abort_s;
+    __shared__ float lim_s[TF_NQ], eu_s[TF_NQ], qn_s[TF_NQ];
+    __shared__ unsigned int ku_s[TF_NQ];
+    __shared__ uint32_t qid_s[TF_NQ];
+    unsigned char* sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+    const int n = v.n, k = v.k;
+    const int katoms = n / TC_KATOM;
+    unsigned char* Bs = sm;
+    unsigned char* As = sm + (size_t)tf_nq_max_dev(n) * n * 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) tmem_alloc(&tmem_base, TF_TMEM_COLS);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < TF_STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], TF_EPI_WARPS);
+        }
+        mbar_init(&fin, 1);
+        abort_s = 0;
+        mbar_fence_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    uint32_t p_it = 0, m_it = 0, m_t = 0, e_t = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t i = atomicAdd(v.claim, 1u);
+            item_ok = i < *v.n_items;
+            if (item_ok) item_s = v.items[i];
+        }
+        __syncthreads();
+        if (!item_ok || abort_s) break;
+        const uint4 it = item_s;
+        const uint32_t leaf = it.x, q0 = it.y, nq = it.z;
+        const int n16 = (int)((nq + 15u) & ~15u);
+        const int64_t lb = v.leaf_begin[leaf], le = v.leaf_begin[leaf + 1];
+        const int tiles = (int)((le - lb + TC_M - 1) / TC_M);
+        if (warp < TF_EPI_WARPS) {
+            // B tile: the item's queries, 128-byte swizzled K-major; rows past nq are zero
+            const int tid = threadIdx.x, cpr = n / 8;
+            for (int c = tid; c < n16 * cpr; c += TF_EPI_WARPS * 32) {
+                const int j = c / cpr, ch = c - j * cpr;
+                uint4 val = make_uint4(0u, 0u, 0u, 0u);
+                if (j < (int)nq)
+                    val = reinterpret_cast<const uint4*>(v.qb + (size_t)v.pairs[q0 + j] * n)[ch];
+                *reinterpret_cast<uint4*>(Bs + sw128_offset(j, ch, n16)) = val;
+            }
+            if (tid < (int)nq) {
+                const uint32_t b = v.pairs[q0 + tid];
+                const QueryScratch& s = v.ss[b];
+                const double delta = s.ctl->delta;
+                const unsigned long long kth = ld_volatile_u64(&s.topk[k - 1]);
+                double ub = kth == EMPTY_SLOT ? INFINITY : (double)key_d2(kth) * (1.0 + 5.0 * delta);
+                const unsigned long long ku = ld_volatile_u64(&v.utop[(size_t)b * MAX_K + k - 1]);
+                if (ku != EMPTY_SLOT) ub = fmin(ub, (double)key_d2(ku));
+                const double X = (double)v.leaf_xnorm[leaf], Q = (double)v.qnorm[b];
+                const double E = (v.c_xq * X * Q + v.c_sq * (X * X + Q * Q)) * (1.0 + 1e-9);
+                qid_s[tid] = b;
+                qn_s[tid] = v.qn[b];
+                lim_s[tid] = __double2float_ru(ub + E);
+                eu_s[tid] = __double2float_ru(E);
+                ku_s[tid] = ku == EMPTY_SLOT ? 0x7f800000u : (unsigned)(ku >> 32);
+            }
+            fence_proxy_async_smem();
+        }
+        __syncthreads();
+        if (warp == TF_EPI_WARPS) {
+            // TMA producer: the leaf's rows, one K-atom of one 128-row tile per stage
+            if (lane == 0) {
+                for (int t = 0; t < tiles && !abort_s; ++t) {
+                    for (int ka = 0; ka < katoms; ++ka, ++p_it) {
+                        const uint32_t st = p_it % TF_STAGES, ph = (p_it / TF_STAGES) & 1u;
+                        if (!mbar_wait_bounded(&empty[st], ph ^ 1u, TF_WAIT)) {
+                            tf_fail(&abort_s, v.err, 1u);
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full[st], TF_ATOM_BYTES);
+                        tma_load_2d(As + st * TF_ATOM_BYTES, &tmX, ka * TC_KATOM, (int)(lb + (int64_t)t * TC_M),
+                                    &full[st]);
+                    }
+                }
+            }
+        } else if (warp == TF_EPI_WARPS + 1) {
+            // MMA issuer: D[a] = A_tile . B^T over the K-atoms, a alternating per tile
+            if (lane == 0) {
+                const uint32_t idesc = tc_idesc_bf16(TC_M, n16);
+                for (int t = 0; t < tiles && !abort_s; ++t, ++m_t) {
+                    const uint32_t a = m_t & 1u, aph = (m_t >> 1) & 1u;
+                    if (!mbar_wait_bounded(&acce[a], aph ^ 1u, TF_WAIT)) {
+                        tf_fail(&abort_s, v.err, 2u);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dcol = tmem + a * (uint32_t)TF_NQ;
+                    bool ok = true;
+                    for (int ka = 0; ka < katoms; ++ka, ++m_it) {
+                        const uint32_t st = m_it % TF_STAGES, ph = (m_it / TF_STAGES) & 1u;
+                        if (!mbar_wait_bounded(&full[st], ph, TF_WAIT)) {
+                            tf_fail(&abort_s, v.err, 4u);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t abase = smem_u32(As + st * TF_ATOM_BYTES);
+                        const uint32_t bbase = smem_u32(Bs) + (uint32_t)(ka * n16 * 128);
+#pragma unroll
+                        for (int kk = 0; kk < TC_KATOM / 16; ++kk)
+                            tc_mma_f16(dcol, sdesc_sw128(abase + kk * 32), sdesc_sw128(bbase + kk * 32), idesc,
+                                       (ka | kk) ? 1u : 0u);
+                        tc_commit(&empty[st]);
+                    }
+                    if (!ok) break;
+                    tc_commit(&accf[a]);
+                }
+            }
+        } else {
+            // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows), column
+            // groups of 16 alternating between the two warps of a quarter
+            const int qd = warp & 3, half = warp >> 2;
+            const int groups = n16 / 16;
+            for (int t = 0; t < tiles; ++t, ++e_t) {
+                const uint32_t a = e_t & 1u, aph = (e_t >> 1) & 1u;
+                // warp-uniform outcome: the TMEM loads below need all 32 lanes
+                const bool ready = __all_sync(FULL, mbar_wait_bounded(&accf[a], aph, TF_WAIT));
+                if (!ready) {
+                    if (lane == 0) tf_fail(&abort_s, v.err, 8u);
+                    break;
+                }
+                tc_fence_after();
+                const int row = qd * 32 + lane;
+                const int64_t pos = lb + (int64_t)t * TC_M + row;
+                const bool valid = pos < le;
+                const float xr = valid ? v.xn[pos] : 0.0f;
+                for (int g = half; g < groups; g += 2) {
+                    float acc[16];
+                    __syncwarp();  // converge after the divergent updates below
+                    tc_ld_x16(tmem + a * (uint32_t)TF_NQ + (uint32_t)(g * 16) + ((uint32_t)(qd * 32) << 16), acc);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int j = g * 16 + i;
+                        if (j >= (int)nq) break;
+                        const float dt = fmaf(-2.0f, acc[i], xr + qn_s[j]);
+                        const bool pass = valid && dt <= lim_s[j];
+                        const unsigned m = __ballot_sync(FULL, pass);
+                        if (m == 0) continue;
+                        const int leader = __ffs(m) - 1;
+                        uint32_t base = 0;
+                        if (lane == leader) base = atomicAdd(v.cand_count, (uint32_t)__popc(m));
+                        base = __shfl_sync(FULL, base, leader);
+                        if (pass) {
+                            const uint32_t slot = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+                            const float eu = eu_s[j];
+                            if (slot < v.cand_cap)
+                                v.cand[slot] = make_uint4((uint32_t)pos, qid_s[j], __float_as_uint(dt),
+                                                          __float_as_uint(eu));
+                            const float up = __fadd_ru(dt, eu);
+                            if (__float_as_uint(up) < ku_s[j]) {
+                                unsigned long long* slots = v.utop + (size_t)qid_s[j] * MAX_K;
+                                topk_insert(slots, k, pack_key(up, (uint32_t)pos));
+                                const unsigned long long kk = ld_volatile_u64(&slots[k - 1]);
+                                if (kk != EMPTY_SLOT) atomicMin(&ku_s[j], (unsigned)(kk >> 32));
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[a]);
+            }
+        }
+        __syncthreads();
+    }
+    // teardown: after an abort, let copies and MMAs in flight finish first
+    if (abort_s) {
+        if (warp == TF_EPI_WARPS && lane == 0) {
+            for (uint32_t i = p_it > TF_STAGES ? p_it - TF_STAGES : 0; i < p_it; ++i)
+                mbar_wait_bounded(&full[i % TF_STAGES], (i / TF_STAGES) & 1u, TF_WAIT);
+        }
+        if (warp == TF_EPI_WARPS + 1 && lane == 0) {
+            tc_commit(&fin);
+            mbar_wait_bounded(&fin, 0, TF_WAIT);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, TF_TMEM_COLS);
+}
+
+// BF16 copy of the collection (leaf order), fp32 squared row norms, and the
+// largest row norm of every leaf (rounded up).  One CTA per leaf, one warp per row.
+__global__ void __launch_bounds__(256) tc_prepare_kernel(const float* __restrict__ x,
+                                                         const uint32_t* __restrict__ leaf_begin, int n,
+                                                         uint16_t* __restrict__ xb, float* __restrict__ xn,
+                                                         float* __restrict__ leaf_xnorm, unsigned* bad) {
+    __shared__ double wmax[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t l = blockIdx.x;
+    const int64_t lb = leaf_begin[l], le = leaf_begin[l + 1];
+    double mymax = 0.0;
+    for (int64_t r = lb + warp; r < le; r += 8) {
+        const float4* xr = reinterpret_cast<const float4*>(x + r * n);
+        uint2* dst = reinterpret_cast<uint2*>(xb + r * n);
+        double acc = 0.0;
+        for (int i = lane; i < n / 4; i += 32) {
+            const float4 f = ld_stream(xr + i);
+            acc += (double)f.x * f.x + (double)f.y * f.y + (double)f.z * f.z + (double)f.w * f.w;
+            const __nv_bfloat162 h0 = __floats2bfloat162_rn(f.x, f.y), h1 = __floats2bfloat162_rn(f.z, f.w);
+            dst[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+        if (lane == 0) xn[r] = __double2float_rn(acc);
+        mymax = fmax(mymax, acc);
+    }
+    if (lane == 0) wmax[warp] = mymax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < 8; ++i) m = fmax(m, wmax[i]);
+        const float X = __double2float_ru(sqrt(m) * (1.0 + 1e-12));
+        leaf_xnorm[l] = X;
+        if (!(X < 1e18f)) atomicOr(bad, 1u);
+    }
+}
+
+// per query of the batch: BF16 copy, squared norm (fp32) and norm (rounded up)
+__global__ void __launch_bounds__(256) tc_qprep_kernel(const float* __restrict__ q, int B, int n,
+                                                       uint16_t* __restrict__ qb, float* __restrict__ qn,
+                                                       float* __restrict__ qnorm) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + warp;
+    if (b >= B) return;
+    const float4* qr = reinterpret_cast<const float4*>(q + (size_t)b * n);
+    uint2* dst = reinterpret_cast<uint2*>(qb + (size_t)b * n);
+    double acc = 0.0;
+    for (int i = lane; i < n / 4; i += 32) {
+        const float4 f = qr[i];
+        acc += (double)f.x * f.x + (double)f.y * f.y + (double)f.z * f.z + (double)f.w * f.w;
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(f.x, f.y), h1 = __floats2bfloat162_rn(f.z, f.w);
+        dst[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+    if (lane == 0) {
+        qn[b] = __double2float_rn(acc);
+        qnorm[b] = __double2float_ru(sqrt(acc) * (1.0 + 1e-12));
+    }
+}
+
+// one CTA: exclusive scan of the per-leaf pair counts (pair offsets) and of the
+// per-leaf work items (ceil(count / nq_max), the leaf's queries split evenly),
+// writing the items.  misc[0] = items, misc[1] = pairs.
+__global__ void __launch_bounds__(1024) bq_items_kernel(const uint32_t* __restrict__ leaf_count, int64_t L,
+                                                        int nq_max, uint32_t* __restrict__ leaf_off,
+                                                        uint4* __restrict__ items, uint32_t items_cap,
+                                                        uint32_t* misc) {
+    __shared__ uint32_t scr0[32], scr1[32];
+    const int64_t per = (L + blockDim.x - 1) / blockDim.x;
+    const int64_t l0 = (int64_t)threadIdx.x * per, l1 = l0 + per < L ? l0 + per : L;
+    uint32_t sc = 0, sch = 0;
+    for (int64_t l = l0; l < l1; ++l) {
+        const uint32_t c = leaf_count[l];
+        sc += c;
+        sch += (c + nq_max - 1) / nq_max;
+    }
+    uint32_t tot_c, tot_ch;
+    uint32_t oc = block_excl_scan<uint32_t>(sc, 0u, OpAdd<uint32_t>(), scr0, &tot_c);
+    uint32_t och = block_excl_scan<uint32_t>(sch, 0u, OpAdd<uint32_t>(), scr1, &tot_ch);
+    for (int64_t l = l0; l < l1; ++l) {
+        const uint32_t c = leaf_count[l];
+        leaf_off[l] = oc;
+        const uint32_t nch = (c + nq_max - 1) / nq_max;
+        for (uint32_t ch = 0; ch < nch; ++ch, ++och) {
+            const uint32_t a = (uint32_t)((uint64_t)c * ch / nch), e = (uint32_t)((uint64_t)c * (ch + 1) / nch);
+            if (och < items_cap) items[och] = make_uint4((uint32_t)l, oc + a, e - a, 0u);
+        }
+        oc += c;
+    }
+    if (threadIdx.x == 0) {
+        misc[0] = tot_ch < items_cap ? tot_ch : items_cap;
+        misc[1] = tot_c;
+        leaf_off[L] = tot_c;
+    }
+}
+
+// ================================================================ host side
+struct TcState {
+    // per index: BF16 copy of the collection
+    uint16_t* xb = nullptr;        // [N][n]
+    float* xn = nullptr;           // [N]
+    float* leaf_xnorm = nullptr;   // [L]
+    CUtensorMap tmap;
+    uint32_t* leaf_count = nullptr;   // [L]
+    uint32_t* leaf_off = nullptr;     // [L+1]
+    uint32_t* leaf_cursor = nullptr;  // [L]
+    uint32_t* misc = nullptr;         // [0] items [1] pairs [2] claim [3] kept rows [4] error bits
+    uint32_t* host_misc = nullptr;    // pinned copy of misc
+    uint4* cand = nullptr;            // kept rows
+    uint32_t cand_cap = 0;
+    // per batch (grown on demand)
+    int Bcap = 0;
+    float* q = nullptr;
+    float* table = nullptr;
+    uint32_t* bins = nullptr;
+    unsigned long long* topk = nullptr;
+    unsigned long long* cand_key = nullptr;
+    uint32_t* cand_pos = nullptr;
+    QCtl* ctl = nullptr;
+    int64_t* out_idx = nullptr;
+    float* out_dist = nullptr;
+    QueryScratch* ss = nullptr;
+    uint16_t* qb = nullptr;
+    float* qn = nullptr;
+    float* qnorm = nullptr;
+    unsigned long long* utop = nullptr;
+    uint32_t* pairs = nullptr;
+    uint4* items = nullptr;
+    uint32_t items_cap = 0;
+    QCtl* host_ctl = nullptr;      // pinned
+    int64_t* host_idx = nullptr;   // pinned [Bcap][MAX_K]
+    float* host_dist = nullptr;
+};
+
+static void free_batch(TcState* t, cudaStream_t st) {
+    void* ptrs[] = {t->q, t->table, t->bins, t->topk, t->cand_key, t->cand_pos, t->ctl, t->out_idx,
+                    t->out_dist, t->ss, t->qb, t->qn, t->qnorm, t->utop, t->pairs, t->items};
+    for (void* p : ptrs)
+        if (p) dev_free(p, st);
+    if (t->host_ctl) cudaFreeHost(t->host_ctl);
+    if (t->host_idx) cudaFreeHost(t->host_idx);
+    if (t->host_dist) cudaFreeHost(t->host_dist);
+    t->q = t->table = nullptr;
+    t->bins = t->cand_pos = t->pairs = nullptr;
+    t->topk = t->cand_key = t->utop = nullptr;
+    t->ctl = nullptr;
+    t->out_idx = nullptr;
+    t->out_dist = t->qn = t->qnorm = nullptr;
+    t->ss = nullptr;
+    t->qb = nullptr;
+    t->items = nullptr;
+    t->items_cap = 0;
+    t->host_ctl = nullptr;
+    t->host_idx = nullptr;
+    t->host_dist = nullptr;
+    t->Bcap = 0;
+}
+
+void free_tc_state(isax_index* ix, cudaStream_t st) {
+    TcState* t = static_cast<TcState*>(ix->tc);
+    if (!t) return;
+    free_batch(t, st);
+    void* ptrs[] = {t->xb, t->xn, t->leaf_xnorm, t->leaf_count, t->leaf_off, t->leaf_cursor, t->misc, t->cand};
+    for (void* p : ptrs)
+        if (p) dev_free(p, st);
+    if (t->host_misc) cudaFreeHost(t->host_misc);
+    delete t;
+    ix->tc = nullptr;
+}
+
+template <typename T>
+static T* dalloc(size_t count, cudaStream_t st) {
+    return static_cast<T*>(dev_alloc(sizeof(T) * (count ? count : 1), st));
+}
+
+// the BF16 copy of the collection, built once per index
+static TcState* ensure_tc(isax_index* ix, cudaStream_t st) {
+    if (ix->tc) return static_cast<TcState*>(ix->tc);
+    const DevIndex& d = ix->d;
+    if (d.n % TC_KATOM != 0)
+        throw Error{ISAX_ERR_INVALID_ARG, "the BF16 filter needs a series length that is a multiple of 64"};
+    if (!(d.maxabs < 1e15f))
+        throw Error{ISAX_ERR_INVALID_ARG, "values too large for the BF16 filter's error bound"};
+    TcState* t = new TcState();
+    ix->tc = t;
+    try {
+        t->xb = dalloc<uint16_t>((size_t)d.N * d.n, st);
+        t->xn = dalloc<float>((size_t)d.N, st);
+        t->leaf_xnorm = dalloc<float>((size_t)d.L, st);
+        t->leaf_count = dalloc<uint32_t>((size_t)d.L, st);
+        t->leaf_off = dalloc<uint32_t>((size_t)d.L + 1, st);
+        t->leaf_cursor = dalloc<uint32_t>((size_t)d.L, st);
+        t->misc = dalloc<uint32_t>(8, st);
+        ISAX_CUDA_TRY(cudaMallocHost((void**)&t->host_misc, sizeof(uint32_t) * 8));
+        ISAX_CUDA_TRY(cudaMemsetAsync(t->misc, 0, sizeof(uint32_t) * 8, st));
+        {
+            ISAX_LAUNCH("tc_prepare", st);
+            tc_prepare_kernel<<<(unsigned)d.L, 256, 0, st>>>(ix->x, ix->leaf_begin, d.n, t->xb, t->xn,
+                                                             t->leaf_xnorm, t->misc + 4);
+            ISAX_CUDA_TRY(cudaGetLastError());
+        }
+        ISAX_CUDA_TRY(cudaMemcpyAsync(t->host_misc, t->misc, sizeof(uint32_t) * 8, cudaMemcpyDeviceToHost, st));
+        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+        if (t->host_misc[4])
+            throw Error{ISAX_ERR_INVALID_ARG, "row norms too large for the BF16 filter's error bound"};
+        make_tmap_bf16(&t->tmap, t->xb, (uint64_t)d.N, (uint64_t)d.n);
+    } catch (...) {
+        free_tc_state(ix, st);
+        throw;
+    }
+    return t;
+}
+
+static void ensure_batch(TcState* t, const isax_index* ix, int B, cudaStream_t st) {
+    if (t->Bcap >= B) return;
+    free_batch(t, st);
+    const DevIndex& d = ix->d;
+    const size_t Bs = (size_t)B;
+    t->q = dalloc<float>(Bs * d.n, st);
+    t->table = dalloc<float>(Bs * W * d.card, st);
+    t->bins = dalloc<uint32_t>(Bs * 2 * NBINS, st);
+    t->topk = dalloc<unsigned long long>(Bs * MAX_K, st);
+    t->cand_key = dalloc<unsigned long long>(Bs * TF_QCAP, st);
+    t->cand_pos = dalloc<uint32_t>(Bs * TF_QCAP, st);
+    t->ctl = dalloc<QCtl>(Bs, st);
+    t->out_idx = dalloc<int64_t>(Bs * MAX_K, st);
+    t->out_dist = dalloc<float>(Bs * MAX_K, st);
+    t->ss = dalloc<QueryScratch>(Bs, st);
+    t->qb = dalloc<uint16_t>(Bs * d.n, st);
+    t->qn = dalloc<float>(Bs, st);
+    t->qnorm = dalloc<float>(Bs, st);
+    t->utop = dalloc<unsigned long long>(Bs * MAX_K, st);
+    t->pairs = dalloc<uint32_t>(Bs * (size_t)d.L, st);
+    const int nq = tf_nq_max(d.n);
+    t->items_cap = (uint32_t)std::min<uint64_t>((uint64_t)d.L * (1 + (Bs + nq - 1) / nq), 0xffffffffull);
+    t->items = dalloc<uint4>(t->items_cap, st);
+    ISAX_CUDA_TRY(cudaMallocHost((void**)&t->host_ctl, sizeof(QCtl) * Bs));
+    ISAX_CUDA_TRY(cudaMallocHost((void**)&t->host_idx, sizeof(int64_t) * Bs * MAX_K));
+    ISAX_CUDA_TRY(cudaMallocHost((void**)&t->host_dist, sizeof(float) * Bs * MAX_K));
+    std::vector<QueryScratch> hs(Bs);
+    for (size_t b = 0; b < Bs; ++b) {
+        QueryScratch& q = hs[b];
+        q.q = t->q + b * d.n;
+        q.table = t->table + b * W * d.card;
+        q.leaf_lb = nullptr;
+        q.work = nullptr;
+        q.bin_count = t->bins + b * 2 * NBINS;
+        q.bin_cursor = q.bin_count + NBINS;
+        q.topk = t->topk + b * MAX_K;
+        q.cand_key = t->cand_key + b * TF_QCAP;
+        q.cand_pos = t->cand_pos + b * TF_QCAP;
+        q.cand_cap = TF_QCAP;
+        q.ctl = t->ctl + b;
+        q.out_idx = t->out_idx + b * MAX_K;
+        q.out_dist = t->out_dist + b * MAX_K;
+    }
+    ISAX_CUDA_TRY(cudaMemcpyAsync(t->ss, hs.data(), sizeof(QueryScratch) * Bs, cudaMemcpyHostToDevice, st));
+    ISAX_CUDA_TRY(cudaMemsetAsync(t->ctl, 0, sizeof(QCtl) * Bs, st));
+    ISAX_CUDA_TRY(cudaStreamSynchronize(st));  // hs goes out of scope
+    t->Bcap = B;
+}
+
+static void ensure_cand(TcState* t, uint32_t cap, cudaStream_t st) {
+    if (t->cand_cap >= cap) return;
+    if (t->cand) dev_free(t->cand, st);
+    t->cand = nullptr;
+    t->cand_cap = 0;
+    t->cand = dalloc<uint4>(cap, st);
+    t->cand_cap = cap;
+}
+
+// E = c_xq X Q + c_sq (X^2 + Q^2)  (see the error bound at the top of this part)
+static void tc_bound_constants(int n, double* c_xq, double* c_sq) {
+    const double u = 0x1p-24, ub = 0x1p-8;
+    const double g = (1.0 + ub) * (1.0 + ub);
+    *c_xq = 2.0 * (2.0 * ub + ub * ub) + 2.0 * n * 0x1p-21 * g + 2.01 * u * g;
+    *c_sq = 4.0 * u;
+}
+
+// one pass of at most TF_MAX_B queries, already in t->q; false if the kept-row
+// buffer overflowed (nothing is valid then)
+static bool run_pass(isax_index* ix, TcState* t, int B, int k, cudaStream_t st) {
+    const DevIndex& d = ix->d;
+    const int nq = tf_nq_max(d.n);
+    {
+        ISAX_LAUNCH("tc_qprep", st);
+        tc_qprep_kernel<<<(B + 7) / 8, 256, 0, st>>>(t->q, B, d.n, t->qb, t->qn, t->qnorm);
+        ISAX_CUDA_TRY(cudaGetLastError());
+    }
+    launch_bq_prep(ix, t->ss, B, k, TC_APPROX_NEIGHBORS, st);
+    launch_bq_approx(ix, t->ss, B, k, TC_APPROX_NEIGHBORS, st);
+    ISAX_CUDA_TRY(cudaMemsetAsync(t->utop, 0xff, sizeof(unsigned long long) * (size_t)B * MAX_K, st));
+    ISAX_CUDA_TRY(cudaMemsetAsync(t->leaf_count, 0, sizeof(uint32_t) * d.L, st));
+    ISAX_CUDA_TRY(cudaMemsetAsync(t->leaf_cursor, 0, sizeof(uint32_t) * d.L, st));
+    ISAX_CUDA_TRY(cudaMemsetAsync(t->misc, 0, sizeof(uint32_t) * 8, st));
+    launch_bq_pairs(ix, t->ss, B, k, 0, t->leaf_count, nullptr, nullptr, nullptr, st);
+    {
+        ISAX_LAUNCH("bq_items", st);
+        bq_items_kernel<<<1, 1024, 0, st>>>(t->leaf_count, d.L, nq, t->leaf_off, t->items, t->items_cap,
+                                            t->misc);
+        ISAX_CUDA_TRY(cudaGetLastError());
+    }
+    launch_bq_pairs(ix, t->ss, B, k, 1, nullptr, t->leaf_off, t->leaf_cursor, t->pairs, st);
+    TcView v;
+    v.leaf_begin = ix->leaf_begin;
+    v.xn = t->xn;
+    v.leaf_xnorm = t->leaf_xnorm;
+    v.items = t->items;
+    v.n_items = t->misc + 0;
+    v.claim = t->misc + 2;
+    v.pairs = t->pairs;
+    v.qb = t->qb;
+    v.qn = t->qn;
+    v.qnorm = t->qnorm;
+    v.ss = t->ss;
+    v.utop = t->utop;
+    v.cand = t->cand;
+    v.cand_count = t->misc + 3;
+    v.cand_cap = t->cand_cap;
+    v.err = t->misc + 4;
+    v.n = d.n;
+    v.k = k;
+    tc_bound_constants(d.n, &v.c_xq, &v.c_sq);
+    const size_t smem = 1024 + (size_t)nq * d.n * 2 + (size_t)TF_STAGES * TF_ATOM_BYTES;
+    {
+        static bool attr[64] = {};
+        if (ix->device < 0 || ix->device >= 64 || !attr[ix->device]) {
+            ISAX_CUDA_TRY(cudaFuncSetAttribute(tc_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem_max_tf()));
+            if (ix->device >= 0 && ix->device < 64) attr[ix->device] = true;
+        }
+        ISAX_LAUNCH("tc_filter", st);
+        tc_filter_kernel<<<ix->num_sms, TF_THREADS, smem, st>>>(t->tmap, v);
+        ISAX_CUDA_TRY(cudaGetLastError());
+    }
+    launch_bq_recheck(ix, t->ss, k, t->cand, t->misc + 3, t->cand_cap, st);
+    launch_bq_finalize(ix, t->ss, B, k, st);
+    ISAX_CUDA_TRY(cudaMemcpyAsync(t->host_misc, t->misc, sizeof(uint32_t) * 8, cudaMemcpyDeviceToHost, st));
+    ISAX_CUDA_TRY(cudaMemcpyAsync(t->host_ctl, t->ctl, sizeof(QCtl) * B, cudaMemcpyDeviceToHost, st));
+    ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    if (t->host_misc[4])
+        throw Error{ISAX_ERR_TIMEOUT, "tensor-core filter: a bounded wait gave up (" +
+                                          std::to_string(t->host_misc[4]) + ")"};
+    return t->host_misc[3] <= t->cand_cap;
+}
+
+void prepare_tc(isax_index* ix, cudaStream_t st) { ensure_tc(ix, st); }
+
+void query_batch_tc(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags, int64_t* out_idx,
+                    float* out_dist, isax_query_stats_fill fill, void* fill_ctx, cudaStream_t st) {
+    TcState* t = ensure_tc(ix, st);
+    const int n = ix->d.n;
+    const int P = std::max(1, std::min<int>(TF_MAX_B, (int)std::min<int64_t>(B, (1ll << 29) / std::max<int64_t>(ix->d.L, 1))));
+    ensure_batch(t, ix, std::min(B, P), st);
+    if (!t->cand) ensure_cand(t, 1u << 22, st);
+    const cudaMemcpyKind kin = (mem_flags & ISAX_MEM_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                                   : cudaMemcpyHostToDevice;
+    const bool dev_out = (mem_flags & ISAX_MEM_OUTPUT_DEVICE) != 0;
+    bool nonfinite = false;
+    for (int b0 = 0; b0 < B; b0 += P) {
+        const int Bp = std::min(P, B - b0);
+        for (int attempt = 0;; ++attempt) {
+            ISAX_CUDA_TRY(cudaMemcpyAsync(t->q, Q + (size_t)b0 * n, sizeof(float) * (size_t)Bp * n, kin, st));
+            if (run_pass(ix, t, Bp, k, st)) break;
+            if (attempt >= 3) throw Error{ISAX_ERR_INTERNAL, "tensor-core filter kept too many rows"};
+            const uint64_t want = std::min<uint64_t>((uint64_t)t->host_misc[3] * 2, 0xffffffffull);
+            ensure_cand(t, (uint32_t)want, st);
+        }
+        // outputs: row b of the [Bp][MAX_K] result arrays holds query b0 + b
+        if (dev_out) {
+            ISAX_CUDA_TRY(cudaMemcpy2DAsync(out_idx + (size_t)b0 * k, sizeof(int64_t) * k, t->out_idx,
+                                            sizeof(int64_t) * MAX_K, sizeof(int64_t) * k, Bp,
+                                            cudaMemcpyDeviceToDevice, st));
+            ISAX_CUDA_TRY(cudaMemcpy2DAsync(out_dist + (size_t)b0 * k, sizeof(float) * k, t->out_dist,
+                                            sizeof(float) * MAX_K, sizeof(float) * k, Bp,
+                                            cudaMemcpyDeviceToDevice, st));
+        } else {
+            ISAX_CUDA_TRY(cudaMemcpy2DAsync(t->host_idx, sizeof(int64_t) * k, t->out_idx,
+                                            sizeof(int64_t) * MAX_K, sizeof(int64_t) * k, Bp,
+                                            cudaMemcpyDeviceToHost, st));
+            ISAX_CUDA_TRY(cudaMemcpy2DAsync(t->host_dist, sizeof(float) * k, t->out_dist,
+                                            sizeof(float) * MAX_K, sizeof(float) * k, Bp,
+                                            cudaMemcpyDeviceToHost, st));
+            ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+            memcpy(out_idx + (size_t)b0 * k, t->host_idx, sizeof(int64_t) * (size_t)Bp * k);
+            memcpy(out_dist + (size_t)b0 * k, t->host_dist, sizeof(float) * (size_t)Bp * k);
+        }
+        const cudaMemcpyKind kout = dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        for (int b = 0; b < Bp; ++b) {
+            QCtl c = t->host_ctl[b];
+            int reruns = 0;
+            if (c.flags & QF_NONFINITE) {
+                nonfinite = true;
+                continue;
+            }
+            c.leaves_scanned = c.leaves_queued;
+            if (c.flags & (QF_OVERFLOW | QF_SHORT)) {
+                // this query's candidate window overflowed: answer it alone
+                ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, Q + (size_t)(b0 + b) * n, sizeof(float) * n, kin, st));
+                query_device(ix, k, &c, &reruns, st);
+                ISAX_CUDA_TRY(cudaMemcpyAsync(out_idx + (size_t)(b0 + b) * k, ix->qs.out_idx,
+                                              sizeof(int64_t) * k, kout, st));
+                ISAX_CUDA_TRY(cudaMemcpyAsync(out_dist + (size_t)(b0 + b) * k, ix->qs.out_dist,
+                                              sizeof(float) * k, kout, st));
+                ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+                reruns += 1;
+            }
+            if (fill) fill(fill_ctx, b0 + b, c, reruns);
+        }
+    }
+    if (nonfinite) throw Error{ISAX_ERR_INVALID_ARG, "a query contains a non-finite value"};
 }
 
 }  // namespace isax
