@@ -241,7 +241,7 @@ void tc_selftest(const void* A, const void* B, int N, float* D, cudaStream_t st)
 // be among a query's k best only if d~2 - E <= (an upper bound of the k-th
 // best squared distance).  Those rows are re-checked with the exact fp32
 // distance of the single-query path and the k best are ordered as there
-// (FP64 only within fp32 error of each other): the answers equal the oracle's.
+// (FP64 only within fp32 error of each other): the answers are the exact ones.
 //
 // Work is leaf-major: every leaf that the envelope bound leaves to a set of
 // queries is contracted once against all of them (up to TF_NQ per work item),
