@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--workload", choices=["walk", "hardness"], default="walk",
                     help="hardness: the sinusoid collection, member queries by noise level and k")
     ap.add_argument("--batch", type=int, default=1024,
-                    help="also time isax_query_knn_batch on this many fresh queries (0: skip)")
+                    help="batched leg: time the plain and the BF16-filtered batch paths on "
+                         "batches of this size and of 4x this size, k = 1 and 10 (0: skip)")
     return ap.parse_args()
 
 
@@ -186,6 +187,97 @@ def traffic_from_profile(kernel):
         if len(parts) >= 4 and parts[0] == kernel and parts[1] == digest:
             return float(parts[2]), parts[3]
     return None
+
+
+# ------------------------------------------------------------------ batched leg
+def bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def batch_leg(a, X, pkg, torch, stream, rank):
+    """Batches of B queries drawn like the single-query workload (90% fresh
+    walks, 10% noisy members; seed 4), answered by the plain FP32 batch path
+    (queries run concurrently on stream slots) and by the tensor-core filtered
+    batch path, on the same index; both must return identical answers.  Device
+    buffers in and out; times are CUDA events around whole batch calls."""
+    import datagen
+    import numpy as np
+    sp = stream.cuda_stream
+    N, n = a.N, a.n
+    ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix.prepare_bf16(stream=sp)
+    prep_ms = (time.perf_counter() - t0) * 1e3
+    tflops_peak, tsrc = bf16_peak()
+    hbm, _ = peaks()
+    runs = []
+
+    def timed(fn, reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for B in (a.batch, 4 * a.batch):
+        Qh, _ = datagen.queries("walk", rank, N, n, 4 + 1000 * rank + B, B - B // 10, B // 10, 0.01)
+        Q = torch.from_numpy(Qh).cuda()
+        for k in (1, 10):
+            i_p, d_p = ix.query_batch(Q, k, stream=sp)
+            i_b, d_b, st = ix.query_batch_bf16(Q, k, stats=True, stream=sp)
+            identical = bool(torch.equal(i_p, i_b) and torch.equal(d_p, d_b))
+            plain_ms = timed(lambda: ix.query_batch(Q, k, stream=sp), 2)
+            bf16_ms = timed(lambda: ix.query_batch_bf16(Q, k, stream=sp), 3)
+            pkg.isax_profile(1)
+            ix.query_batch_bf16(Q, k, stream=sp)
+            torch.cuda.synchronize()
+            pkg.isax_profile(0)
+            prof = pkg.isax_profile_report()
+            rows = sum(s["series_lb"] for s in st)
+            kern = {nm: round(v[1], 4) for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+            tf_ms = prof.get("tc_filter", (1, None))[1]
+            flops = 2.0 * n * rows
+            achieved = flops / (tf_ms / 1e3) / 1e12 if tf_ms else None
+            runs.append({
+                "B": B, "k": k, "identical_answers": identical,
+                "plain_ms_per_batch": round(plain_ms, 3),
+                "plain_queries_per_s": round(B / (plain_ms / 1e3), 1),
+                "bf16_ms_per_batch": round(bf16_ms, 3),
+                "bf16_queries_per_s": round(B / (bf16_ms / 1e3), 1),
+                "speedup": round(plain_ms / bf16_ms, 2),
+                "per_query": {
+                    "leaves_contracted": float(np.mean([s["leaves_queued"] for s in st])),
+                    "rows_contracted": rows / B,
+                    "rows_rechecked_fp32": float(np.mean([s["series_refined"] - s["approx_series"]
+                                                         for s in st])),
+                    "reruns": int(sum(s["reruns"] for s in st)),
+                },
+                "kernels_ms": kern,
+                "tc_filter_roofline": {
+                    "bound": "tensor", "unit": "TFLOP/s",
+                    "achieved": achieved, "peak": tflops_peak,
+                    "frac": achieved / tflops_peak if achieved else None,
+                    "flops": "2 n x rows contracted (useful work; padding of tiles excluded)",
+                    "bf16_copy_GB_per_s_if_read_once": (N * n * 2 / 1e9) / (tf_ms / 1e3) if tf_ms else None,
+                    "hbm_peak": hbm,
+                    "peak_source": "%s: MEASURED_PEAKS.json bf16_tflops (burst)" % tsrc,
+                },
+            })
+        del Q
+    ix.close()
+    torch.cuda.synchronize()
+    return {"prepare_bf16_ms": prep_ms, "bf16_copy_GB": N * n * 2 / 1e9,
+            "queries": "config-0 style: 90% fresh walks, 10% members + N(0, 0.01) noise, seed 4",
+            "runs": runs}
 
 
 # ------------------------------------------------------------------ CPU baseline
@@ -431,27 +523,8 @@ def main():
             entry["GB_per_s"] = round(b / (ms / 1e3) / 1e9, 1)
         kernels[nm] = entry
 
-    # batched queries (the plain FP32 path, queries run concurrently on slots)
-    batch_info = None
-    if a.batch > 0:
-        import datagen
-        Qb = torch.from_numpy(datagen.rows("walk", 4 + 1000 * rank, 0, a.batch, n)).cuda()
-        ixb = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp)
-        ixb.query_batch(Qb[:64], k, stream=sp)  # warm up the slots and their graphs
-        torch.cuda.synchronize()
-        reps = 3
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for _ in range(reps):
-            ixb.query_batch(Qb, k, stream=sp)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        bms = t0.elapsed_time(t1) / reps
-        batch_info = {"B": a.batch, "k": k, "ms_per_batch": bms, "queries_per_s": a.batch / (bms / 1e3),
-                      "queries": "fresh random walks (seed 4), device buffers"}
-        ixb.close()
-        del Qb
+    # batched queries: the plain FP32 path against the tensor-core (BF16) filter
+    batch_info = batch_leg(a, X, pkg, torch, stream, rank) if a.batch > 0 else None
 
     lat_sorted = sorted(lat_ms)
 

@@ -294,9 +294,8 @@ struct TcView {
     uint32_t* claim;
     const uint32_t* pairs;     // query of each pair, grouped by leaf
     const uint16_t* qb;        // [B][n] BF16 queries
-    const float* qn;           // [B] squared query norms (fp32)
-    const float* qnorm;        // [B] query norms, rounded up
-    const QueryScratch* ss;    // [B]
+    const float4* qc;          // [B] {squared norm (fp32), norm rounded up, upper bound of the
+                               //      k-th best squared distance after the approximate answer, 0}
     unsigned long long* utop;  // [B][MAX_K] k smallest upper bounds d~2 + E (packed with the position)
     uint4* cand;               // kept rows {position, query, d~2 bits, E bits}
     uint32_t* cand_count;
@@ -311,13 +310,35 @@ __device__ __forceinline__ void tf_fail(volatile int* abort_flag, uint32_t* err,
     atomicOr(err, code);
 }
 
+// 16-byte global -> shared copy that completes asynchronously (cp.async)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// warp-uniform bounded wait
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity) {
+    return __all_sync(FULL, mbar_wait_bounded(bar, parity, TF_WAIT));
+}
+
+// Roles (TF_THREADS = 320):
+//   warps 0-7  gather the item's queries into the B tile (cp.async, 128-byte
+//              swizzled K-major), compute the per-column limits, then read the
+//              accumulators back and keep the rows that pass (epilogue);
+//   warp 8     claims work items (two descriptor slots ahead) and streams the
+//              leaf's rows through the A ring with TMA, running into the next
+//              item while the current one finishes;
+//   warp 9     issues the MMAs (one thread), accumulators alternating between
+//              two TMEM buffers.
+// Every hand-off is an mbarrier with a bounded wait; a wait that gives up sets
+// the error word and every role leaves its loop (no CTA-wide barrier inside).
 __global__ void __launch_bounds__(TF_THREADS, 1)
     tc_filter_kernel(const __grid_constant__ CUtensorMap tmX, TcView v) {
     extern __shared__ unsigned char sm_raw[];
-    __shared__ __align__(8) uint64_t full[TF_STAGES], empty[TF_STAGES], accf[2], acce[2], fin;
+    __shared__ __align__(8) uint64_t full[TF_STAGES], empty[TF_STAGES], accf[2], acce[2];
+    __shared__ __align__(8) uint64_t itemf[2], iteme[2], gathered, epi_done, fin;
+    __shared__ uint4 item_s[2];
     __shared__ uint32_t tmem_base;
-    __shared__ uint4 item_s;
-    __shared__ int item_ok;
     __shared__ volatile int abort_s;
     __shared__ float lim_s[TF_NQ], eu_s[TF_NQ], qn_s[TF_NQ];
     __shared__ unsigned int ku_s[TF_NQ];
@@ -337,7 +358,11 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&accf[i], 1);
             mbar_init(&acce[i], TF_EPI_WARPS);
+            mbar_init(&itemf[i], 1);
+            mbar_init(&iteme[i], TF_EPI_WARPS + 1);
         }
+        mbar_init(&gathered, TF_EPI_WARPS);
+        mbar_init(&epi_done, TF_EPI_WARPS);
         mbar_init(&fin, 1);
         abort_s = 0;
         mbar_fence_init();
@@ -346,82 +371,81 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    uint32_t p_it = 0, m_it = 0, m_t = 0, e_t = 0;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const uint32_t i = atomicAdd(v.claim, 1u);
-            item_ok = i < *v.n_items;
-            if (item_ok) item_s = v.items[i];
-        }
-        __syncthreads();
-        if (!item_ok || abort_s) break;
-        const uint4 it = item_s;
-        const uint32_t leaf = it.x, q0 = it.y, nq = it.z;
-        const int n16 = (int)((nq + 15u) & ~15u);
-        const int64_t lb = v.leaf_begin[leaf], le = v.leaf_begin[leaf + 1];
-        const int tiles = (int)((le - lb + TC_M - 1) / TC_M);
-        if (warp < TF_EPI_WARPS) {
-            // B tile: the item's queries, 128-byte swizzled K-major; rows past nq are zero
-            const int tid = threadIdx.x, cpr = n / 8;
-            for (int c = tid; c < n16 * cpr; c += TF_EPI_WARPS * 32) {
-                const int j = c / cpr, ch = c - j * cpr;
-                uint4 val = make_uint4(0u, 0u, 0u, 0u);
-                if (j < (int)nq)
-                    val = reinterpret_cast<const uint4*>(v.qb + (size_t)v.pairs[q0 + j] * n)[ch];
-                *reinterpret_cast<uint4*>(Bs + sw128_offset(j, ch, n16)) = val;
-            }
-            if (tid < (int)nq) {
-                const uint32_t b = v.pairs[q0 + tid];
-                const QueryScratch& s = v.ss[b];
-                const double delta = s.ctl->delta;
-                const unsigned long long kth = ld_volatile_u64(&s.topk[k - 1]);
-                double ub = kth == EMPTY_SLOT ? INFINITY : (double)key_d2(kth) * (1.0 + 5.0 * delta);
-                const unsigned long long ku = ld_volatile_u64(&v.utop[(size_t)b * MAX_K + k - 1]);
-                if (ku != EMPTY_SLOT) ub = fmin(ub, (double)key_d2(ku));
-                const double X = (double)v.leaf_xnorm[leaf], Q = (double)v.qnorm[b];
-                const double E = (v.c_xq * X * Q + v.c_sq * (X * X + Q * Q)) * (1.0 + 1e-9);
-                qid_s[tid] = b;
-                qn_s[tid] = v.qn[b];
-                lim_s[tid] = __double2float_ru(ub + E);
-                eu_s[tid] = __double2float_ru(E);
-                ku_s[tid] = ku == EMPTY_SLOT ? 0x7f800000u : (unsigned)(ku >> 32);
-            }
-            fence_proxy_async_smem();
-        }
-        __syncthreads();
-        if (warp == TF_EPI_WARPS) {
-            // TMA producer: the leaf's rows, one K-atom of one 128-row tile per stage
-            if (lane == 0) {
-                for (int t = 0; t < tiles && !abort_s; ++t) {
+
+    if (warp == TF_EPI_WARPS) {
+        // ------------------------------------------------ scheduler + TMA producer
+        if (lane == 0) {
+            uint32_t p_it = 0;
+            for (uint32_t i = 0;; ++i) {
+                const uint32_t slot = i & 1u, ph = (i >> 1) & 1u;
+                if (!mbar_wait_bounded(&iteme[slot], ph ^ 1u, TF_WAIT)) {
+                    tf_fail(&abort_s, v.err, 1u);
+                    break;
+                }
+                const uint32_t idx = atomicAdd(v.claim, 1u);
+                const uint4 it = idx < *v.n_items ? v.items[idx] : make_uint4(0u, 0u, 0u, 0u);
+                item_s[slot] = it;
+                mbar_arrive(&itemf[slot]);
+                if (it.z == 0 || abort_s) break;
+                const int64_t lb = v.leaf_begin[it.x], le = v.leaf_begin[it.x + 1];
+                const int tiles = (int)((le - lb + TC_M - 1) / TC_M);
+                bool ok = true;
+                for (int t = 0; t < tiles && ok; ++t) {
                     for (int ka = 0; ka < katoms; ++ka, ++p_it) {
-                        const uint32_t st = p_it % TF_STAGES, ph = (p_it / TF_STAGES) & 1u;
-                        if (!mbar_wait_bounded(&empty[st], ph ^ 1u, TF_WAIT)) {
-                            tf_fail(&abort_s, v.err, 1u);
+                        const uint32_t st = p_it % TF_STAGES, sph = (p_it / TF_STAGES) & 1u;
+                        if (abort_s || !mbar_wait_bounded(&empty[st], sph ^ 1u, TF_WAIT)) {
+                            tf_fail(&abort_s, v.err, 2u);
+                            ok = false;
                             break;
                         }
                         mbar_arrive_expect_tx(&full[st], TF_ATOM_BYTES);
-                        tma_load_2d(As + st * TF_ATOM_BYTES, &tmX, ka * TC_KATOM, (int)(lb + (int64_t)t * TC_M),
-                                    &full[st]);
+                        tma_load_2d(As + st * TF_ATOM_BYTES, &tmX, ka * TC_KATOM,
+                                    (int)(lb + (int64_t)t * TC_M), &full[st]);
                     }
                 }
+                if (!ok) break;
             }
-        } else if (warp == TF_EPI_WARPS + 1) {
-            // MMA issuer: D[a] = A_tile . B^T over the K-atoms, a alternating per tile
-            if (lane == 0) {
+            // copies still in flight (after an abort) land before the CTA exits
+            for (uint32_t i = p_it > TF_STAGES ? p_it - TF_STAGES : 0; i < p_it; ++i)
+                mbar_wait_bounded(&full[i % TF_STAGES], (i / TF_STAGES) & 1u, TF_WAIT);
+        }
+    } else if (warp == TF_EPI_WARPS + 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t m_it = 0, m_t = 0;
+            for (uint32_t i = 0;; ++i) {
+                const uint32_t slot = i & 1u, ph = (i >> 1) & 1u;
+                if (!mbar_wait_bounded(&itemf[slot], ph, TF_WAIT)) {
+                    tf_fail(&abort_s, v.err, 4u);
+                    break;
+                }
+                const uint4 it = item_s[slot];
+                mbar_arrive(&iteme[slot]);
+                if (it.z == 0 || abort_s) break;
+                const int n16 = (int)((it.z + 15u) & ~15u);
+                const int64_t lb = v.leaf_begin[it.x], le = v.leaf_begin[it.x + 1];
+                const int tiles = (int)((le - lb + TC_M - 1) / TC_M);
+                // the B tile and the column limits of this item are in place
+                if (!mbar_wait_bounded(&gathered, i & 1u, TF_WAIT)) {
+                    tf_fail(&abort_s, v.err, 8u);
+                    break;
+                }
+                tc_fence_after();
                 const uint32_t idesc = tc_idesc_bf16(TC_M, n16);
-                for (int t = 0; t < tiles && !abort_s; ++t, ++m_t) {
+                bool ok = true;
+                for (int t = 0; t < tiles && ok; ++t, ++m_t) {
                     const uint32_t a = m_t & 1u, aph = (m_t >> 1) & 1u;
                     if (!mbar_wait_bounded(&acce[a], aph ^ 1u, TF_WAIT)) {
-                        tf_fail(&abort_s, v.err, 2u);
+                        tf_fail(&abort_s, v.err, 16u);
+                        ok = false;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t dcol = tmem + a * (uint32_t)TF_NQ;
-                    bool ok = true;
                     for (int ka = 0; ka < katoms; ++ka, ++m_it) {
-                        const uint32_t st = m_it % TF_STAGES, ph = (m_it / TF_STAGES) & 1u;
-                        if (!mbar_wait_bounded(&full[st], ph, TF_WAIT)) {
-                            tf_fail(&abort_s, v.err, 4u);
+                        const uint32_t st = m_it % TF_STAGES, sph = (m_it / TF_STAGES) & 1u;
+                        if (!mbar_wait_bounded(&full[st], sph, TF_WAIT)) {
+                            tf_fail(&abort_s, v.err, 32u);
                             ok = false;
                             break;
                         }
@@ -434,38 +458,112 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                                        (ka | kk) ? 1u : 0u);
                         tc_commit(&empty[st]);
                     }
-                    if (!ok) break;
-                    tc_commit(&accf[a]);
+                    if (ok) tc_commit(&accf[a]);
                 }
+                if (!ok) break;
             }
-        } else {
+            // every MMA issued has completed before TMEM is released
+            tc_commit(&fin);
+            mbar_wait_bounded(&fin, 0, TF_WAIT);
+        }
+    } else {
+        // ------------------------------------------------ gather + epilogue warps
+        const int tid = threadIdx.x;  // 0 .. 255
+        const int qd = warp & 3, half = warp >> 2;
+        const int cpr = n / 8;        // 16-byte chunks per query row
+        uint32_t e_t = 0;
+        for (uint32_t i = 0;; ++i) {
+            const uint32_t slot = i & 1u, ph = (i >> 1) & 1u;
+            if (!warp_wait(&itemf[slot], ph)) {
+                if (lane == 0) tf_fail(&abort_s, v.err, 64u);
+                break;
+            }
+            const uint4 it = item_s[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&iteme[slot]);
+            if (__any_sync(FULL, it.z == 0 || abort_s)) break;  // warp-uniform exit
+            const uint32_t leaf = it.x, q0 = it.y, nq = it.z;
+            const int n16 = (int)((nq + 15u) & ~15u);
+            const int64_t lb = v.leaf_begin[leaf], le = v.leaf_begin[leaf + 1];
+            const int tiles = (int)((le - lb + TC_M - 1) / TC_M);
+            // the previous item's MMAs and epilogues are complete: B tile and limits are free
+            if (i > 0 && !warp_wait(&epi_done, (i - 1) & 1u)) {
+                if (lane == 0) tf_fail(&abort_s, v.err, 128u);
+                break;
+            }
+            // B tile: all copies in flight at once
+            for (int c = tid; c < n16 * cpr; c += TF_EPI_WARPS * 32) {
+                const int j = c / cpr, ch = c - j * cpr;
+                unsigned char* dst = Bs + sw128_offset(j, ch, n16);
+                if (j < (int)nq)
+                    cp_async16(dst, v.qb + (size_t)v.pairs[q0 + j] * n + ch * 8);
+                else
+                    *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+            }
+            if (tid < (int)nq) {
+                const uint32_t b = v.pairs[q0 + tid];
+                const float4 qc = v.qc[b];
+                const unsigned long long ku = ld_volatile_u64(&v.utop[(size_t)b * MAX_K + k - 1]);
+                double ub = (double)qc.z;
+                if (ku != EMPTY_SLOT) ub = fmin(ub, (double)key_d2(ku));
+                const double X = (double)v.leaf_xnorm[leaf], Q = (double)qc.y;
+                const double E = (v.c_xq * X * Q + v.c_sq * (X * X + Q * Q)) * (1.0 + 1e-9);
+                qid_s[tid] = b;
+                qn_s[tid] = qc.x;
+                lim_s[tid] = __double2float_ru(ub + E);
+                eu_s[tid] = __double2float_ru(E);
+                ku_s[tid] = ku == EMPTY_SLOT ? 0x7f800000u : (unsigned)(ku >> 32);
+            } else if (tid < n16) {
+                qn_s[tid] = 0.0f;  // padding columns: a limit no value passes
+                lim_s[tid] = -INFINITY;
+            }
+            cp_async_wait_all();
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&gathered);
+            if (!warp_wait(&gathered, i & 1u)) {
+                if (lane == 0) tf_fail(&abort_s, v.err, 256u);
+                break;
+            }
             // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows), column
             // groups of 16 alternating between the two warps of a quarter
-            const int qd = warp & 3, half = warp >> 2;
             const int groups = n16 / 16;
+            const int row = qd * 32 + lane;
+            int64_t pos = lb + row;
+            float xr = pos < le ? v.xn[pos] : INFINITY;
+            bool ok = true;
             for (int t = 0; t < tiles; ++t, ++e_t) {
                 const uint32_t a = e_t & 1u, aph = (e_t >> 1) & 1u;
-                // warp-uniform outcome: the TMEM loads below need all 32 lanes
-                const bool ready = __all_sync(FULL, mbar_wait_bounded(&accf[a], aph, TF_WAIT));
-                if (!ready) {
-                    if (lane == 0) tf_fail(&abort_s, v.err, 8u);
+                const bool valid = pos < le;
+                // the next tile's row norm, loaded while this tile is consumed
+                const int64_t pn = pos + TC_M;
+                const float xr_next = pn < le ? v.xn[pn] : INFINITY;
+                if (!warp_wait(&accf[a], aph)) {
+                    if (lane == 0) tf_fail(&abort_s, v.err, 512u);
+                    ok = false;
                     break;
                 }
                 tc_fence_after();
-                const int row = qd * 32 + lane;
-                const int64_t pos = lb + (int64_t)t * TC_M + row;
-                const bool valid = pos < le;
-                const float xr = valid ? v.xn[pos] : 0.0f;
                 for (int g = half; g < groups; g += 2) {
                     float acc[16];
                     __syncwarp();  // converge after the divergent updates below
                     tc_ld_x16(tmem + a * (uint32_t)TF_NQ + (uint32_t)(g * 16) + ((uint32_t)(qd * 32) << 16), acc);
+                    // fast test of the 16 columns; rows past the leaf carry +inf
+                    unsigned pm = 0;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int j = g * 16 + i;
+                    for (int c = 0; c < 16; ++c) {
+                        const int j = g * 16 + c;
+                        const float dt = fmaf(-2.0f, acc[c], xr + qn_s[j]);
+                        pm |= (dt <= lim_s[j] ? 1u : 0u) << c;
+                    }
+                    if (!valid) pm = 0;
+                    if (__any_sync(FULL, pm != 0) == 0) continue;
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const int j = g * 16 + c;
                         if (j >= (int)nq) break;
-                        const float dt = fmaf(-2.0f, acc[i], xr + qn_s[j]);
-                        const bool pass = valid && dt <= lim_s[j];
+                        const float dt = fmaf(-2.0f, acc[c], xr + qn_s[j]);
+                        const bool pass = (pm >> c) & 1u;
                         const unsigned m = __ballot_sync(FULL, pass);
                         if (m == 0) continue;
                         const int leader = __ffs(m) - 1;
@@ -473,11 +571,11 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                         if (lane == leader) base = atomicAdd(v.cand_count, (uint32_t)__popc(m));
                         base = __shfl_sync(FULL, base, leader);
                         if (pass) {
-                            const uint32_t slot = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+                            const uint32_t slot_c = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
                             const float eu = eu_s[j];
-                            if (slot < v.cand_cap)
-                                v.cand[slot] = make_uint4((uint32_t)pos, qid_s[j], __float_as_uint(dt),
-                                                          __float_as_uint(eu));
+                            if (slot_c < v.cand_cap)
+                                v.cand[slot_c] = make_uint4((uint32_t)pos, qid_s[j], __float_as_uint(dt),
+                                                            __float_as_uint(eu));
                             const float up = __fadd_ru(dt, eu);
                             if (__float_as_uint(up) < ku_s[j]) {
                                 unsigned long long* slots = v.utop + (size_t)qid_s[j] * MAX_K;
@@ -491,19 +589,12 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce[a]);
+                pos = pn;
+                xr = xr_next;
             }
-        }
-        __syncthreads();
-    }
-    // teardown: after an abort, let copies and MMAs in flight finish first
-    if (abort_s) {
-        if (warp == TF_EPI_WARPS && lane == 0) {
-            for (uint32_t i = p_it > TF_STAGES ? p_it - TF_STAGES : 0; i < p_it; ++i)
-                mbar_wait_bounded(&full[i % TF_STAGES], (i / TF_STAGES) & 1u, TF_WAIT);
-        }
-        if (warp == TF_EPI_WARPS + 1 && lane == 0) {
-            tc_commit(&fin);
-            mbar_wait_bounded(&fin, 0, TF_WAIT);
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&epi_done);
         }
     }
     tc_fence_before();
@@ -549,14 +640,17 @@ __global__ void __launch_bounds__(256) tc_prepare_kernel(const float* __restrict
     }
 }
 
-// per query of the batch: BF16 copy, squared norm (fp32) and norm (rounded up)
-__global__ void __launch_bounds__(256) tc_qprep_kernel(const float* __restrict__ q, int B, int n,
-                                                       uint16_t* __restrict__ qb, float* __restrict__ qn,
-                                                       float* __restrict__ qnorm) {
+// per query of the batch (after its approximate answer): BF16 copy, and
+// {squared norm (fp32), norm rounded up, upper bound of the k-th best squared
+// distance: the approximate answer's k-th fp32 value times (1 + 5 delta)}
+__global__ void __launch_bounds__(256) tc_qprep_kernel(const QueryScratch* __restrict__ ss, int B, int n,
+                                                       int k, uint16_t* __restrict__ qb,
+                                                       float4* __restrict__ qc) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * 8 + warp;
     if (b >= B) return;
-    const float4* qr = reinterpret_cast<const float4*>(q + (size_t)b * n);
+    const QueryScratch& s = ss[b];
+    const float4* qr = reinterpret_cast<const float4*>(s.q);
     uint2* dst = reinterpret_cast<uint2*>(qb + (size_t)b * n);
     double acc = 0.0;
     for (int i = lane; i < n / 4; i += 32) {
@@ -568,8 +662,10 @@ __global__ void __launch_bounds__(256) tc_qprep_kernel(const float* __restrict__
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
     if (lane == 0) {
-        qn[b] = __double2float_rn(acc);
-        qnorm[b] = __double2float_ru(sqrt(acc) * (1.0 + 1e-12));
+        const unsigned long long kth = s.topk[k - 1];
+        const float ub = kth == EMPTY_SLOT ? INFINITY
+                                           : __double2float_ru((double)key_d2(kth) * (1.0 + 5.0 * s.ctl->delta));
+        qc[b] = make_float4(__double2float_rn(acc), __double2float_ru(sqrt(acc) * (1.0 + 1e-12)), ub, 0.0f);
     }
 }
 
@@ -636,8 +732,7 @@ struct TcState {
     float* out_dist = nullptr;
     QueryScratch* ss = nullptr;
     uint16_t* qb = nullptr;
-    float* qn = nullptr;
-    float* qnorm = nullptr;
+    float4* qc = nullptr;
     unsigned long long* utop = nullptr;
     uint32_t* pairs = nullptr;
     uint4* items = nullptr;
@@ -649,7 +744,7 @@ struct TcState {
 
 static void free_batch(TcState* t, cudaStream_t st) {
     void* ptrs[] = {t->q, t->table, t->bins, t->topk, t->cand_key, t->cand_pos, t->ctl, t->out_idx,
-                    t->out_dist, t->ss, t->qb, t->qn, t->qnorm, t->utop, t->pairs, t->items};
+                    t->out_dist, t->ss, t->qb, t->qc, t->utop, t->pairs, t->items};
     for (void* p : ptrs)
         if (p) dev_free(p, st);
     if (t->host_ctl) cudaFreeHost(t->host_ctl);
@@ -660,7 +755,8 @@ static void free_batch(TcState* t, cudaStream_t st) {
     t->topk = t->cand_key = t->utop = nullptr;
     t->ctl = nullptr;
     t->out_idx = nullptr;
-    t->out_dist = t->qn = t->qnorm = nullptr;
+    t->out_dist = nullptr;
+    t->qc = nullptr;
     t->ss = nullptr;
     t->qb = nullptr;
     t->items = nullptr;
@@ -742,8 +838,7 @@ static void ensure_batch(TcState* t, const isax_index* ix, int B, cudaStream_t s
     t->out_dist = dalloc<float>(Bs * MAX_K, st);
     t->ss = dalloc<QueryScratch>(Bs, st);
     t->qb = dalloc<uint16_t>(Bs * d.n, st);
-    t->qn = dalloc<float>(Bs, st);
-    t->qnorm = dalloc<float>(Bs, st);
+    t->qc = dalloc<float4>(Bs, st);
     t->utop = dalloc<unsigned long long>(Bs * MAX_K, st);
     t->pairs = dalloc<uint32_t>(Bs * (size_t)d.L, st);
     const int nq = tf_nq_max(d.n);
@@ -797,13 +892,13 @@ static void tc_bound_constants(int n, double* c_xq, double* c_sq) {
 static bool run_pass(isax_index* ix, TcState* t, int B, int k, cudaStream_t st) {
     const DevIndex& d = ix->d;
     const int nq = tf_nq_max(d.n);
-    {
-        ISAX_LAUNCH("tc_qprep", st);
-        tc_qprep_kernel<<<(B + 7) / 8, 256, 0, st>>>(t->q, B, d.n, t->qb, t->qn, t->qnorm);
-        ISAX_CUDA_TRY(cudaGetLastError());
-    }
     launch_bq_prep(ix, t->ss, B, k, TC_APPROX_NEIGHBORS, st);
     launch_bq_approx(ix, t->ss, B, k, TC_APPROX_NEIGHBORS, st);
+    {
+        ISAX_LAUNCH("tc_qprep", st);
+        tc_qprep_kernel<<<(B + 7) / 8, 256, 0, st>>>(t->ss, B, d.n, k, t->qb, t->qc);
+        ISAX_CUDA_TRY(cudaGetLastError());
+    }
     ISAX_CUDA_TRY(cudaMemsetAsync(t->utop, 0xff, sizeof(unsigned long long) * (size_t)B * MAX_K, st));
     ISAX_CUDA_TRY(cudaMemsetAsync(t->leaf_count, 0, sizeof(uint32_t) * d.L, st));
     ISAX_CUDA_TRY(cudaMemsetAsync(t->leaf_cursor, 0, sizeof(uint32_t) * d.L, st));
@@ -825,9 +920,7 @@ static bool run_pass(isax_index* ix, TcState* t, int B, int k, cudaStream_t st) 
     v.claim = t->misc + 2;
     v.pairs = t->pairs;
     v.qb = t->qb;
-    v.qn = t->qn;
-    v.qnorm = t->qnorm;
-    v.ss = t->ss;
+    v.qc = t->qc;
     v.utop = t->utop;
     v.cand = t->cand;
     v.cand_count = t->misc + 3;
