@@ -143,9 +143,10 @@ void launch_bq_prep(isax_index* ix, const QueryScratch* ss, int B, int k, int ne
                     cudaStream_t st);
 void launch_bq_approx(isax_index* ix, const QueryScratch* ss, int B, int k, int neighbors,
                       cudaStream_t st);
-void launch_bq_pairs(isax_index* ix, const QueryScratch* ss, int B, int k, int mode,
-                     uint32_t* leaf_count, const uint32_t* leaf_off, uint32_t* leaf_cursor,
-                     uint32_t* pairs, cudaStream_t st);
+void launch_bq_pairs(isax_index* ix, const QueryScratch* ss, int B, int k, uint32_t* leaf_count,
+                     uint32_t* mask, cudaStream_t st);
+void launch_bq_fill(isax_index* ix, int B, const uint32_t* mask, const uint32_t* leaf_off,
+                    uint32_t* pairs, cudaStream_t st);
 void launch_bq_recheck(isax_index* ix, const QueryScratch* ss, int k, const uint4* cand,
                        const uint32_t* cand_count, uint32_t cap, cudaStream_t st);
 void launch_bq_finalize(isax_index* ix, const QueryScratch* ss, int B, int k, cudaStream_t st);

@@ -892,23 +892,25 @@ __global__ void __launch_bounds__(FIN_THREADS) bq_finalize_kernel(DevIndex ix, c
 // (leaf, query) pairs that the leaf envelope bound does not prune, against
 // each query's threshold after its approximate answer; a query's own
 // approximate-answer leaves are left out (already refined exactly).
-// Lane = query, warp = leaf: one ballot per (leaf, 32 queries).
-// mode 0 counts pairs per leaf (and leaves / series per query); mode 1 lists
-// the queries of every leaf at leaf_off[l] onwards.
+// Lane = query, warp = leaf: one ballot per (leaf, 32 queries), stored in
+// mask[l * G + g] (G = ceil(B / 32) query groups); the pairs of every leaf are
+// counted, and per query the leaves and series it keeps.  The bound is the
+// single-query path's fp32 expression without branches: per segment at most
+// one of (beta_lo - paa) and (paa - beta_hi+1) is positive, and the other
+// clamps to +0, so the sum takes the same values in the same order.
 constexpr int BP_WARPS = 8;
 constexpr int BP_LEAVES = 256;  // leaves per CTA
 
 __global__ void __launch_bounds__(BP_WARPS * 32) bq_pairs_kernel(
-    DevIndex ix, const QueryScratch* ss, int B, int k, int mode, uint32_t* __restrict__ leaf_count,
-    const uint32_t* __restrict__ leaf_off, uint32_t* __restrict__ leaf_cursor,
-    uint32_t* __restrict__ pairs) {
+    DevIndex ix, const QueryScratch* ss, int B, int k, uint32_t* __restrict__ leaf_count,
+    uint32_t* __restrict__ mask) {
     __shared__ float bp[MAX_CARD + 1];
     __shared__ unsigned long long part_l[BP_WARPS][32], part_s[BP_WARPS][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int G = gridDim.y;
     const int b = blockIdx.y * 32 + lane;
     for (int i = threadIdx.x; i <= ix.card; i += blockDim.x) bp[i] = ix.bp[i];
     float qp[W];
-    int qs[W];
     float thr = -1.0f;  // a negative threshold takes no leaf
     int64_t a0 = 0, a1 = 0;
     if (b < B) {
@@ -919,16 +921,10 @@ __global__ void __launch_bounds__(BP_WARPS * 32) bq_pairs_kernel(
             a1 = c->approx_end;
         }
 #pragma unroll
-        for (int i = 0; i < W; ++i) {
-            qp[i] = c->qpaa[i];
-            qs[i] = c->qsym[i];
-        }
+        for (int i = 0; i < W; ++i) qp[i] = c->qpaa[i];
     } else {
 #pragma unroll
-        for (int i = 0; i < W; ++i) {
-            qp[i] = 0.0f;
-            qs[i] = 0;
-        }
+        for (int i = 0; i < W; ++i) qp[i] = 0.0f;
     }
     __syncthreads();
     const float mf = (float)(ix.n / W);
@@ -942,45 +938,62 @@ __global__ void __launch_bounds__(BP_WARPS * 32) bq_pairs_kernel(
 #pragma unroll
         for (int i = 0; i < W; ++i) {
             const int lo = (wn[i >> 2] >> (8 * (i & 3))) & 255, hi = (wx[i >> 2] >> (8 * (i & 3))) & 255;
-            if (qs[i] < lo) {
-                const float d = bp[lo] - qp[i];
-                lb += (d * d) * mf;
-            } else if (qs[i] > hi) {
-                const float d = qp[i] - bp[hi + 1];
-                lb += (d * d) * mf;
-            }
+            const float d = fmaxf(bp[lo] - qp[i], 0.0f) + fmaxf(qp[i] - bp[hi + 1], 0.0f);
+            lb += (d * d) * mf;
         }
         const bool take = lb <= thr && !(l >= a0 && l < a1);
         const unsigned m = __ballot_sync(FULL, take);
-        if (m == 0) continue;
-        if (mode == 0) {
-            if (lane == 0) atomicAdd(&leaf_count[l], (uint32_t)__popc(m));
-            if (take) {
-                ++my_leaves;
-                my_series += ix.leaf_begin[l + 1] - ix.leaf_begin[l];
-            }
-        } else {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&leaf_cursor[l], (uint32_t)__popc(m));
-            base = __shfl_sync(FULL, base, 0);
-            if (take) pairs[leaf_off[l] + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)b;
+        if (lane == 0) {
+            mask[l * G + blockIdx.y] = m;
+            if (m) atomicAdd(&leaf_count[l], (uint32_t)__popc(m));
+        }
+        if (take) {
+            ++my_leaves;
+            my_series += ix.leaf_begin[l + 1] - ix.leaf_begin[l];
         }
     }
-    if (mode == 0) {
-        part_l[warp][lane] = my_leaves;
-        part_s[warp][lane] = my_series;
-        __syncthreads();
-        if (warp == 0 && b < B) {
-            unsigned long long tl = 0, ts = 0;
-            for (int w = 0; w < BP_WARPS; ++w) {
-                tl += part_l[w][lane];
-                ts += part_s[w][lane];
-            }
-            if (tl) {
-                atomicAdd(&ss[b].ctl->leaves_queued, tl);
-                atomicAdd(&ss[b].ctl->series_lb, ts);
-            }
+    part_l[warp][lane] = my_leaves;
+    part_s[warp][lane] = my_series;
+    __syncthreads();
+    if (warp == 0 && b < B) {
+        unsigned long long tl = 0, ts = 0;
+        for (int w = 0; w < BP_WARPS; ++w) {
+            tl += part_l[w][lane];
+            ts += part_s[w][lane];
         }
+        if (tl) {
+            atomicAdd(&ss[b].ctl->leaves_queued, tl);
+            atomicAdd(&ss[b].ctl->series_lb, ts);
+        }
+    }
+}
+
+// the queries of every leaf, ascending, at leaf_off[l] onwards: one warp per
+// leaf, lanes over query groups, offsets by a warp scan of the group counts
+__global__ void __launch_bounds__(256) bq_fill_kernel(int64_t L, int G, const uint32_t* __restrict__ mask,
+                                                      const uint32_t* __restrict__ leaf_off,
+                                                      uint32_t* __restrict__ pairs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (l >= L) return;
+    uint32_t base = leaf_off[l];
+    for (int g0 = 0; g0 < G; g0 += 32) {
+        const int g = g0 + lane;
+        uint32_t m = g < G ? mask[l * G + g] : 0u;
+        const uint32_t c = (uint32_t)__popc(m);
+        uint32_t incl = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += v;
+        }
+        uint32_t o = base + incl - c;
+        while (m) {
+            const int bit = __ffs(m) - 1;
+            m &= m - 1;
+            pairs[o++] = (uint32_t)(g * 32 + bit);
+        }
+        base += __shfl_sync(FULL, incl, 31);
     }
 }
 
@@ -1412,13 +1425,19 @@ void launch_bq_approx(isax_index* ix, const QueryScratch* ss, int B, int k, int 
     ISAX_CUDA_TRY(cudaGetLastError());
 }
 
-void launch_bq_pairs(isax_index* ix, const QueryScratch* ss, int B, int k, int mode,
-                     uint32_t* leaf_count, const uint32_t* leaf_off, uint32_t* leaf_cursor,
-                     uint32_t* pairs, cudaStream_t st) {
+void launch_bq_pairs(isax_index* ix, const QueryScratch* ss, int B, int k, uint32_t* leaf_count,
+                     uint32_t* mask, cudaStream_t st) {
     const dim3 grid((unsigned)((ix->d.L + BP_LEAVES - 1) / BP_LEAVES), (unsigned)((B + 31) / 32));
-    ISAX_LAUNCH(mode == 0 ? "bq_pairs_count" : "bq_pairs_fill", st);
-    bq_pairs_kernel<<<grid, BP_WARPS * 32, 0, st>>>(ix->d, ss, B, k, mode, leaf_count, leaf_off,
-                                                   leaf_cursor, pairs);
+    ISAX_LAUNCH("bq_pairs", st);
+    bq_pairs_kernel<<<grid, BP_WARPS * 32, 0, st>>>(ix->d, ss, B, k, leaf_count, mask);
+    ISAX_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_bq_fill(isax_index* ix, int B, const uint32_t* mask, const uint32_t* leaf_off,
+                    uint32_t* pairs, cudaStream_t st) {
+    const int64_t L = ix->d.L;
+    ISAX_LAUNCH("bq_fill", st);
+    bq_fill_kernel<<<(unsigned)((L * 32 + 255) / 256), 256, 0, st>>>(L, (B + 31) / 32, mask, leaf_off, pairs);
     ISAX_CUDA_TRY(cudaGetLastError());
 }
 

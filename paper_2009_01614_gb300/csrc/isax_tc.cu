@@ -714,7 +714,7 @@ struct TcState {
     CUtensorMap tmap;
     uint32_t* leaf_count = nullptr;   // [L]
     uint32_t* leaf_off = nullptr;     // [L+1]
-    uint32_t* leaf_cursor = nullptr;  // [L]
+    uint32_t* mask = nullptr;         // [L][ceil(Bcap / 32)] pair ballots
     uint32_t* misc = nullptr;         // [0] items [1] pairs [2] claim [3] kept rows [4] error bits
     uint32_t* host_misc = nullptr;    // pinned copy of misc
     uint4* cand = nullptr;            // kept rows
@@ -744,7 +744,7 @@ struct TcState {
 
 static void free_batch(TcState* t, cudaStream_t st) {
     void* ptrs[] = {t->q, t->table, t->bins, t->topk, t->cand_key, t->cand_pos, t->ctl, t->out_idx,
-                    t->out_dist, t->ss, t->qb, t->qc, t->utop, t->pairs, t->items};
+                    t->out_dist, t->ss, t->qb, t->qc, t->utop, t->pairs, t->items, t->mask};
     for (void* p : ptrs)
         if (p) dev_free(p, st);
     if (t->host_ctl) cudaFreeHost(t->host_ctl);
@@ -760,6 +760,7 @@ static void free_batch(TcState* t, cudaStream_t st) {
     t->ss = nullptr;
     t->qb = nullptr;
     t->items = nullptr;
+    t->mask = nullptr;
     t->items_cap = 0;
     t->host_ctl = nullptr;
     t->host_idx = nullptr;
@@ -771,7 +772,7 @@ void free_tc_state(isax_index* ix, cudaStream_t st) {
     TcState* t = static_cast<TcState*>(ix->tc);
     if (!t) return;
     free_batch(t, st);
-    void* ptrs[] = {t->xb, t->xn, t->leaf_xnorm, t->leaf_count, t->leaf_off, t->leaf_cursor, t->misc, t->cand};
+    void* ptrs[] = {t->xb, t->xn, t->leaf_xnorm, t->leaf_count, t->leaf_off, t->misc, t->cand};
     for (void* p : ptrs)
         if (p) dev_free(p, st);
     if (t->host_misc) cudaFreeHost(t->host_misc);
@@ -800,7 +801,6 @@ static TcState* ensure_tc(isax_index* ix, cudaStream_t st) {
         t->leaf_xnorm = dalloc<float>((size_t)d.L, st);
         t->leaf_count = dalloc<uint32_t>((size_t)d.L, st);
         t->leaf_off = dalloc<uint32_t>((size_t)d.L + 1, st);
-        t->leaf_cursor = dalloc<uint32_t>((size_t)d.L, st);
         t->misc = dalloc<uint32_t>(8, st);
         ISAX_CUDA_TRY(cudaMallocHost((void**)&t->host_misc, sizeof(uint32_t) * 8));
         ISAX_CUDA_TRY(cudaMemsetAsync(t->misc, 0, sizeof(uint32_t) * 8, st));
@@ -841,6 +841,7 @@ static void ensure_batch(TcState* t, const isax_index* ix, int B, cudaStream_t s
     t->qc = dalloc<float4>(Bs, st);
     t->utop = dalloc<unsigned long long>(Bs * MAX_K, st);
     t->pairs = dalloc<uint32_t>(Bs * (size_t)d.L, st);
+    t->mask = dalloc<uint32_t>((size_t)d.L * ((Bs + 31) / 32), st);
     const int nq = tf_nq_max(d.n);
     t->items_cap = (uint32_t)std::min<uint64_t>((uint64_t)d.L * (1 + (Bs + nq - 1) / nq), 0xffffffffull);
     t->items = dalloc<uint4>(t->items_cap, st);
@@ -901,16 +902,15 @@ static bool run_pass(isax_index* ix, TcState* t, int B, int k, cudaStream_t st) 
     }
     ISAX_CUDA_TRY(cudaMemsetAsync(t->utop, 0xff, sizeof(unsigned long long) * (size_t)B * MAX_K, st));
     ISAX_CUDA_TRY(cudaMemsetAsync(t->leaf_count, 0, sizeof(uint32_t) * d.L, st));
-    ISAX_CUDA_TRY(cudaMemsetAsync(t->leaf_cursor, 0, sizeof(uint32_t) * d.L, st));
     ISAX_CUDA_TRY(cudaMemsetAsync(t->misc, 0, sizeof(uint32_t) * 8, st));
-    launch_bq_pairs(ix, t->ss, B, k, 0, t->leaf_count, nullptr, nullptr, nullptr, st);
+    launch_bq_pairs(ix, t->ss, B, k, t->leaf_count, t->mask, st);
     {
         ISAX_LAUNCH("bq_items", st);
         bq_items_kernel<<<1, 1024, 0, st>>>(t->leaf_count, d.L, nq, t->leaf_off, t->items, t->items_cap,
                                             t->misc);
         ISAX_CUDA_TRY(cudaGetLastError());
     }
-    launch_bq_pairs(ix, t->ss, B, k, 1, nullptr, t->leaf_off, t->leaf_cursor, t->pairs, st);
+    launch_bq_fill(ix, B, t->mask, t->leaf_off, t->pairs, st);
     TcView v;
     v.leaf_begin = ix->leaf_begin;
     v.xn = t->xn;
