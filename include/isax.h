@@ -220,8 +220,8 @@ isax_status isax_query_knn_noalloc(const isax_index* ix, const float* q, int32_t
  * best squared distance.  Every other series is re-checked with the exact fp32
  * distance of the single-query path, and the k best are ordered as there (FP64
  * where fp32 cannot separate them).  Each leaf's rows are read once per group of
- * up to 256 queries that need them.
- *   Requires n % 64 == 0 (else ISAX_ERR_INVALID_ARG).  The first call builds a
+ * up to 128 queries that need them (up to 65536 / (2 n) for n > 256).
+ *   Requires n % 64 == 0 and n <= 2048 (else ISAX_ERR_INVALID_ARG).  The first call builds a
  *   BF16 copy of the collection (2 N n bytes of device memory, held until the
  *   index is freed; isax_prepare_bf16 builds it ahead of time).  Batches run in
  *   passes of up to 4096 queries; per pass it holds about
@@ -234,8 +234,8 @@ isax_status isax_query_knn_batch_bf16(const isax_index* ix, const float* Q, int3
                                       isax_query_stats* stats, void* cuda_stream);
 
 /* Build the BF16 copy used by isax_query_knn_batch_bf16 now (synchronises
- * cuda_stream).  ISAX_ERR_INVALID_ARG when n % 64 != 0 or values are too large
- * for the error bound (|x| >= 1e15). */
+ * cuda_stream).  ISAX_ERR_INVALID_ARG when n % 64 != 0, n > 2048, or values are
+ * too large for the error bound (|x| >= 1e15). */
 isax_status isax_prepare_bf16(isax_index* ix, void* cuda_stream);
 
 /* ------------------------------------------------------------ tensor-core check */

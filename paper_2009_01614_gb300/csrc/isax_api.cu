@@ -318,7 +318,8 @@ isax_status isax_query_knn_batch_bf16(const isax_index* cix, const float* Q, int
         check((mem_flags & ~(uint32_t)(ISAX_MEM_INPUT_DEVICE | ISAX_MEM_OUTPUT_DEVICE)) == 0,
               "unknown mem_flags bits");
         check(k >= 1 && k <= ISAX_MAX_K && (int64_t)k <= cix->d.N, "k must be in [1, min(N, 1024)]");
-        check(cix->d.n % 64 == 0, "the BF16 filter needs n to be a multiple of 64");
+        check(cix->d.n % 64 == 0 && cix->d.n <= 2048,
+              "the BF16 filter needs n to be a multiple of 64 and at most 2048");
         check(!(mem_flags & ISAX_MEM_INPUT_DEVICE) || aligned16(Q), "device queries must be 16-byte aligned");
         isax_index* ix = const_cast<isax_index*>(cix);
         DeviceGuard dg(ix->device);

@@ -117,6 +117,12 @@ __device__ __forceinline__ void tc_ld_x16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// bring a tile of the tensor into L2 ahead of its load (no shared memory, no completion)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* tm, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)tm), "r"(x),
+                 "r"(y)
+                 : "memory");
+}
 __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* tm, int x, int y,
                                             uint64_t* bar) {
     asm volatile(
@@ -266,6 +272,7 @@ constexpr int TF_THREADS = (TF_EPI_WARPS + 2) * 32;  // + TMA warp + MMA warp
 constexpr uint32_t TF_ATOM_BYTES = TC_M * TC_KATOM * 2;
 constexpr uint32_t TF_TMEM_COLS = 512;  // two accumulators of up to TF_NQ columns
 constexpr uint32_t TF_WAIT = 1u << 22;  // bounded mbarrier waits
+constexpr int TF_PREFETCH = 4;          // tiles brought into L2 ahead of their load
 constexpr int TF_QCAP = 4096;        // per-query candidate window entries
 constexpr int TF_MAX_B = 4096;       // queries per pass
 constexpr int TC_APPROX_NEIGHBORS = 2;  // approximate answer: descent leaf +- 2 leaves
@@ -337,7 +344,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
     extern __shared__ unsigned char sm_raw[];
     __shared__ __align__(8) uint64_t full[TF_STAGES], empty[TF_STAGES], accf[2], acce[2];
     __shared__ __align__(8) uint64_t itemf[2], iteme[2], gathered, epi_done, fin;
-    __shared__ uint4 item_s[2];
+    __shared__ uint4 item_s[2];     // {leaf, first pair, queries, first row}
+    __shared__ uint32_t item_le[2];  // one past the leaf's last row
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_s;
     __shared__ float lim_s[TF_NQ], eu_s[TF_NQ], qn_s[TF_NQ];
@@ -383,14 +391,27 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                     break;
                 }
                 const uint32_t idx = atomicAdd(v.claim, 1u);
-                const uint4 it = idx < *v.n_items ? v.items[idx] : make_uint4(0u, 0u, 0u, 0u);
+                uint4 it = idx < *v.n_items ? v.items[idx] : make_uint4(0u, 0u, 0u, 0u);
+                uint32_t it_le = 0;
+                if (it.z != 0) {
+                    it.w = v.leaf_begin[it.x];
+                    it_le = v.leaf_begin[it.x + 1];
+                }
                 item_s[slot] = it;
+                item_le[slot] = it_le;
                 mbar_arrive(&itemf[slot]);
                 if (it.z == 0 || abort_s) break;
-                const int64_t lb = v.leaf_begin[it.x], le = v.leaf_begin[it.x + 1];
+                const int64_t lb = it.w, le = it_le;
                 const int tiles = (int)((le - lb + TC_M - 1) / TC_M);
+                // the first tiles go to L2 now; later ones TF_PREFETCH tiles ahead of their load
+                for (int t = 0; t < tiles && t < TF_PREFETCH; ++t)
+                    for (int ka = 0; ka < katoms; ++ka)
+                        tma_prefetch_2d(&tmX, ka * TC_KATOM, (int)(lb + (int64_t)t * TC_M));
                 bool ok = true;
                 for (int t = 0; t < tiles && ok; ++t) {
+                    if (t + TF_PREFETCH < tiles)
+                        for (int ka = 0; ka < katoms; ++ka)
+                            tma_prefetch_2d(&tmX, ka * TC_KATOM, (int)(lb + (int64_t)(t + TF_PREFETCH) * TC_M));
                     for (int ka = 0; ka < katoms; ++ka, ++p_it) {
                         const uint32_t st = p_it % TF_STAGES, sph = (p_it / TF_STAGES) & 1u;
                         if (abort_s || !mbar_wait_bounded(&empty[st], sph ^ 1u, TF_WAIT)) {
@@ -420,10 +441,11 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                     break;
                 }
                 const uint4 it = item_s[slot];
+                const uint32_t it_le = item_le[slot];
                 mbar_arrive(&iteme[slot]);
                 if (it.z == 0 || abort_s) break;
                 const int n16 = (int)((it.z + 15u) & ~15u);
-                const int64_t lb = v.leaf_begin[it.x], le = v.leaf_begin[it.x + 1];
+                const int64_t lb = it.w, le = it_le;
                 const int tiles = (int)((le - lb + TC_M - 1) / TC_M);
                 // the B tile and the column limits of this item are in place
                 if (!mbar_wait_bounded(&gathered, i & 1u, TF_WAIT)) {
@@ -479,26 +501,36 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                 break;
             }
             const uint4 it = item_s[slot];
+            const uint32_t it_le = item_le[slot];
             __syncwarp();
             if (lane == 0) mbar_arrive(&iteme[slot]);
             if (__any_sync(FULL, it.z == 0 || abort_s)) break;  // warp-uniform exit
             const uint32_t leaf = it.x, q0 = it.y, nq = it.z;
             const int n16 = (int)((nq + 15u) & ~15u);
-            const int64_t lb = v.leaf_begin[leaf], le = v.leaf_begin[leaf + 1];
+            const int64_t lb = it.w, le = it_le;
             const int tiles = (int)((le - lb + TC_M - 1) / TC_M);
             // the previous item's MMAs and epilogues are complete: B tile and limits are free
             if (i > 0 && !warp_wait(&epi_done, (i - 1) & 1u)) {
                 if (lane == 0) tf_fail(&abort_s, v.err, 128u);
                 break;
             }
-            // B tile: all copies in flight at once
-            for (int c = tid; c < n16 * cpr; c += TF_EPI_WARPS * 32) {
-                const int j = c / cpr, ch = c - j * cpr;
-                unsigned char* dst = Bs + sw128_offset(j, ch, n16);
-                if (j < (int)nq)
-                    cp_async16(dst, v.qb + (size_t)v.pairs[q0 + j] * n + ch * 8);
-                else
-                    *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+            // B tile: warp w fills rows w, w + 8, ...; lane r fetches the query id of
+            // row w + 8 r up front, so every copy is issued without waiting
+            {
+                const int jr = warp + TF_EPI_WARPS * lane;
+                const uint32_t myq = jr < (int)nq ? v.pairs[q0 + jr] : 0u;
+                for (int r = 0; r < 32; ++r) {
+                    const int j = warp + TF_EPI_WARPS * r;
+                    if (j >= n16) break;
+                    const uint32_t b = __shfl_sync(FULL, myq, r);
+                    for (int ch = lane; ch < cpr; ch += 32) {
+                        unsigned char* dst = Bs + sw128_offset(j, ch, n16);
+                        if (j < (int)nq)
+                            cp_async16(dst, v.qb + (size_t)b * n + ch * 8);
+                        else
+                            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
             }
             if (tid < (int)nq) {
                 const uint32_t b = v.pairs[q0 + tid];
@@ -789,8 +821,9 @@ static T* dalloc(size_t count, cudaStream_t st) {
 static TcState* ensure_tc(isax_index* ix, cudaStream_t st) {
     if (ix->tc) return static_cast<TcState*>(ix->tc);
     const DevIndex& d = ix->d;
-    if (d.n % TC_KATOM != 0)
-        throw Error{ISAX_ERR_INVALID_ARG, "the BF16 filter needs a series length that is a multiple of 64"};
+    if (d.n % TC_KATOM != 0 || d.n > 2048)
+        throw Error{ISAX_ERR_INVALID_ARG,
+                    "the BF16 filter needs a series length that is a multiple of 64 and at most 2048"};
     if (!(d.maxabs < 1e15f))
         throw Error{ISAX_ERR_INVALID_ARG, "values too large for the BF16 filter's error bound"};
     TcState* t = new TcState();

@@ -71,7 +71,7 @@ def test_many_queries_per_leaf_and_ragged_tiles():
     check_knn(i, d, X, Q, 5)
 
 
-@pytest.mark.parametrize("n,N", [(64, 20000), (128, 20000), (192, 12000), (512, 8000)])
+@pytest.mark.parametrize("n,N", [(64, 20000), (128, 20000), (192, 12000), (512, 8000), (2048, 3000)])
 def test_lengths(n, N):
     X = datagen.rows("walk", 23, 0, N, n)
     Q, _ = datagen.queries("walk", 23, N, n, 24, 40, 20, 0.1)
@@ -137,6 +137,10 @@ def test_invalid_inputs():
     with pytest.raises(pkg.ISAXError) as e:
         ix.query_batch_bf16(X[:4], 1)
     assert e.value.status == 1 and "multiple of 64" in e.value.message
+    X4 = datagen.rows("walk", 29, 0, 500, 4096)
+    with pytest.raises(pkg.ISAXError) as e:
+        pkg.Index(torch.from_numpy(X4).cuda(), leaf_size=100).query_batch_bf16(X4[:2], 1)
+    assert "at most 2048" in e.value.message
     X = datagen.rows("walk", 29, 0, 2000, 64)
     ix = pkg.Index(torch.from_numpy(X).cuda(), leaf_size=100)
     q = X[:3].copy()
