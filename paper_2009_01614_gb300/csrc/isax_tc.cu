@@ -268,26 +268,22 @@ void tc_selftest(const void* A, const void* B, int N, float* D, cudaStream_t st)
 constexpr int TF_NQ = 256;           // queries per work item (MMA N, at most)
 constexpr int TF_STAGES = 5;         // A ring: one 128-row x 64-element K-atom each
 constexpr int TF_EPI_WARPS = 8;      // epilogue warps (two per TMEM lane quarter)
-constexpr int TF_THREADS = (TF_EPI_WARPS + 2) * 32;  // + TMA warp + MMA warp
+constexpr int TF_GATHER_WARPS = 4;   // warps that fill the B tile
+constexpr int TF_THREADS = (TF_EPI_WARPS + TF_GATHER_WARPS + 2) * 32;  // + TMA warp + MMA warp
+constexpr int TF_SLOTS = 4;          // work-item descriptors in flight
 constexpr uint32_t TF_ATOM_BYTES = TC_M * TC_KATOM * 2;
-constexpr uint32_t TF_TMEM_COLS = 512;  // two accumulators of up to TF_NQ columns
+constexpr uint32_t TF_B_BYTES = 131072;  // the B tile: up to TF_NQ queries x n BF16 (<= 128 KB)
+constexpr uint32_t TF_TMEM_COLS = 2 * TF_NQ;  // two accumulators
 constexpr uint32_t TF_WAIT = 1u << 22;  // bounded mbarrier waits
-constexpr int TF_PREFETCH = 4;          // tiles brought into L2 ahead of their load
 constexpr int TF_QCAP = 4096;        // per-query candidate window entries
 constexpr int TF_MAX_B = 4096;       // queries per pass
 constexpr int TC_APPROX_NEIGHBORS = 2;  // approximate answer: descent leaf +- 2 leaves
 
-static size_t smem_max_tf() { return 1024 + (size_t)65536 * 2 + (size_t)TF_STAGES * TF_ATOM_BYTES; }
+static size_t smem_tf() { return 1024 + (size_t)TF_B_BYTES + (size_t)TF_STAGES * TF_ATOM_BYTES; }
 
 // queries per work item for series length n: the B tile (nq x n BF16) fits 128 KB
 static int tf_nq_max(int n) {
-    int q = 65536 / n;
-    q = q > TF_NQ ? TF_NQ : q;
-    return q & ~15;
-}
-
-__device__ __forceinline__ int tf_nq_max_dev(int n) {
-    int q = 65536 / n;
+    int q = (int)TF_B_BYTES / (2 * n);
     q = q > TF_NQ ? TF_NQ : q;
     return q & ~15;
 }
@@ -328,34 +324,34 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity) {
     return __all_sync(FULL, mbar_wait_bounded(bar, parity, TF_WAIT));
 }
 
-// Roles (TF_THREADS = 320):
-//   warps 0-7  gather the item's queries into the B tile (cp.async, 128-byte
-//              swizzled K-major), compute the per-column limits, then read the
-//              accumulators back and keep the rows that pass (epilogue);
-//   warp 8     claims work items (two descriptor slots ahead) and streams the
-//              leaf's rows through the A ring with TMA, running into the next
-//              item while the current one finishes;
-//   warp 9     issues the MMAs (one thread), accumulators alternating between
-//              two TMEM buffers.
+// Roles (TF_THREADS = 448):
+//   warps 0-7   epilogue: read the accumulators back and keep the rows that pass;
+//   warps 8-11  gather: the item's queries into the B tile (cp.async, 128-byte
+//               swizzled K-major) as soon as the previous item's MMAs retire,
+//               and its per-column limits into one of two limit buffers;
+//   warp 12     claims work items (TF_SLOTS descriptor slots ahead) and streams
+//               the leaf's rows through the A ring with TMA, across items;
+//   warp 13     issues the MMAs (one thread), accumulators alternating between
+//               two TMEM buffers, and releases the B tile when its MMAs complete.
 // Every hand-off is an mbarrier with a bounded wait; a wait that gives up sets
 // the error word and every role leaves its loop (no CTA-wide barrier inside).
 __global__ void __launch_bounds__(TF_THREADS, 1)
     tc_filter_kernel(const __grid_constant__ CUtensorMap tmX, TcView v) {
     extern __shared__ unsigned char sm_raw[];
     __shared__ __align__(8) uint64_t full[TF_STAGES], empty[TF_STAGES], accf[2], acce[2];
-    __shared__ __align__(8) uint64_t itemf[2], iteme[2], gathered, epi_done, fin;
-    __shared__ uint4 item_s[2];     // {leaf, first pair, queries, first row}
-    __shared__ uint32_t item_le[2];  // one past the leaf's last row
+    __shared__ __align__(8) uint64_t itemf[TF_SLOTS], iteme[TF_SLOTS], bfull, bempty, cfull[2], cempty[2], fin;
+    __shared__ uint4 item_s[TF_SLOTS];     // {leaf, first pair, queries, first row}
+    __shared__ uint32_t item_le[TF_SLOTS];  // one past the leaf's last row
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_s;
-    __shared__ float lim_s[TF_NQ], eu_s[TF_NQ], qn_s[TF_NQ];
-    __shared__ unsigned int ku_s[TF_NQ];
-    __shared__ uint32_t qid_s[TF_NQ];
+    __shared__ float lim_s[2][TF_NQ], eu_s[2][TF_NQ], qn_s[2][TF_NQ];
+    __shared__ unsigned int ku_s[2][TF_NQ];
+    __shared__ uint32_t qid_s[2][TF_NQ];
     unsigned char* sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
     const int n = v.n, k = v.k;
     const int katoms = n / TC_KATOM;
     unsigned char* Bs = sm;
-    unsigned char* As = sm + (size_t)tf_nq_max_dev(n) * n * 2;
+    unsigned char* As = sm + TF_B_BYTES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) tmem_alloc(&tmem_base, TF_TMEM_COLS);
     if (threadIdx.x == 0) {
@@ -366,11 +362,15 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&accf[i], 1);
             mbar_init(&acce[i], TF_EPI_WARPS);
-            mbar_init(&itemf[i], 1);
-            mbar_init(&iteme[i], TF_EPI_WARPS + 1);
+            mbar_init(&cfull[i], TF_GATHER_WARPS);
+            mbar_init(&cempty[i], TF_EPI_WARPS);
         }
-        mbar_init(&gathered, TF_EPI_WARPS);
-        mbar_init(&epi_done, TF_EPI_WARPS);
+        mbar_init(&bfull, TF_GATHER_WARPS);
+        mbar_init(&bempty, 1);
+        for (int i = 0; i < TF_SLOTS; ++i) {
+            mbar_init(&itemf[i], 1);
+            mbar_init(&iteme[i], TF_EPI_WARPS + TF_GATHER_WARPS + 1);
+        }
         mbar_init(&fin, 1);
         abort_s = 0;
         mbar_fence_init();
@@ -379,13 +379,14 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
+    constexpr int W_GATHER = TF_EPI_WARPS, W_PROD = TF_EPI_WARPS + TF_GATHER_WARPS, W_MMA = W_PROD + 1;
 
-    if (warp == TF_EPI_WARPS) {
+    if (warp == W_PROD) {
         // ------------------------------------------------ scheduler + TMA producer
         if (lane == 0) {
             uint32_t p_it = 0;
             for (uint32_t i = 0;; ++i) {
-                const uint32_t slot = i & 1u, ph = (i >> 1) & 1u;
+                const uint32_t slot = i % TF_SLOTS, ph = (i / TF_SLOTS) & 1u;
                 if (!mbar_wait_bounded(&iteme[slot], ph ^ 1u, TF_WAIT)) {
                     tf_fail(&abort_s, v.err, 1u);
                     break;
@@ -403,15 +404,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                 if (it.z == 0 || abort_s) break;
                 const int64_t lb = it.w, le = it_le;
                 const int tiles = (int)((le - lb + TC_M - 1) / TC_M);
-                // the first tiles go to L2 now; later ones TF_PREFETCH tiles ahead of their load
-                for (int t = 0; t < tiles && t < TF_PREFETCH; ++t)
-                    for (int ka = 0; ka < katoms; ++ka)
-                        tma_prefetch_2d(&tmX, ka * TC_KATOM, (int)(lb + (int64_t)t * TC_M));
                 bool ok = true;
                 for (int t = 0; t < tiles && ok; ++t) {
-                    if (t + TF_PREFETCH < tiles)
-                        for (int ka = 0; ka < katoms; ++ka)
-                            tma_prefetch_2d(&tmX, ka * TC_KATOM, (int)(lb + (int64_t)(t + TF_PREFETCH) * TC_M));
                     for (int ka = 0; ka < katoms; ++ka, ++p_it) {
                         const uint32_t st = p_it % TF_STAGES, sph = (p_it / TF_STAGES) & 1u;
                         if (abort_s || !mbar_wait_bounded(&empty[st], sph ^ 1u, TF_WAIT)) {
@@ -430,12 +424,12 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
             for (uint32_t i = p_it > TF_STAGES ? p_it - TF_STAGES : 0; i < p_it; ++i)
                 mbar_wait_bounded(&full[i % TF_STAGES], (i / TF_STAGES) & 1u, TF_WAIT);
         }
-    } else if (warp == TF_EPI_WARPS + 1) {
+    } else if (warp == W_MMA) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             uint32_t m_it = 0, m_t = 0;
             for (uint32_t i = 0;; ++i) {
-                const uint32_t slot = i & 1u, ph = (i >> 1) & 1u;
+                const uint32_t slot = i % TF_SLOTS, ph = (i / TF_SLOTS) & 1u;
                 if (!mbar_wait_bounded(&itemf[slot], ph, TF_WAIT)) {
                     tf_fail(&abort_s, v.err, 4u);
                     break;
@@ -447,13 +441,13 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                 const int n16 = (int)((it.z + 15u) & ~15u);
                 const int64_t lb = it.w, le = it_le;
                 const int tiles = (int)((le - lb + TC_M - 1) / TC_M);
-                // the B tile and the column limits of this item are in place
-                if (!mbar_wait_bounded(&gathered, i & 1u, TF_WAIT)) {
+                if (!mbar_wait_bounded(&bfull, i & 1u, TF_WAIT)) {
                     tf_fail(&abort_s, v.err, 8u);
                     break;
                 }
                 tc_fence_after();
                 const uint32_t idesc = tc_idesc_bf16(TC_M, n16);
+                const uint32_t bs = smem_u32(Bs);
                 bool ok = true;
                 for (int t = 0; t < tiles && ok; ++t, ++m_t) {
                     const uint32_t a = m_t & 1u, aph = (m_t >> 1) & 1u;
@@ -473,7 +467,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                         }
                         tc_fence_after();
                         const uint32_t abase = smem_u32(As + st * TF_ATOM_BYTES);
-                        const uint32_t bbase = smem_u32(Bs) + (uint32_t)(ka * n16 * 128);
+                        const uint32_t bbase = bs + (uint32_t)(ka * n16 * 128);
 #pragma unroll
                         for (int kk = 0; kk < TC_KATOM / 16; ++kk)
                             tc_mma_f16(dcol, sdesc_sw128(abase + kk * 32), sdesc_sw128(bbase + kk * 32), idesc,
@@ -483,21 +477,98 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                     if (ok) tc_commit(&accf[a]);
                 }
                 if (!ok) break;
+                tc_commit(&bempty);  // the B tile is free once these MMAs complete
             }
             // every MMA issued has completed before TMEM is released
             tc_commit(&fin);
             mbar_wait_bounded(&fin, 0, TF_WAIT);
         }
-    } else {
-        // ------------------------------------------------ gather + epilogue warps
-        const int tid = threadIdx.x;  // 0 .. 255
-        const int qd = warp & 3, half = warp >> 2;
-        const int cpr = n / 8;        // 16-byte chunks per query row
-        uint32_t e_t = 0;
+    } else if (warp >= W_GATHER) {
+        // ------------------------------------------------ gather warps
+        const int gt = threadIdx.x - W_GATHER * 32;  // 0 .. 127
+        const int cpr = n / 8;                        // 16-byte chunks per query row
         for (uint32_t i = 0;; ++i) {
-            const uint32_t slot = i & 1u, ph = (i >> 1) & 1u;
+            const uint32_t slot = i % TF_SLOTS, ph = (i / TF_SLOTS) & 1u;
             if (!warp_wait(&itemf[slot], ph)) {
                 if (lane == 0) tf_fail(&abort_s, v.err, 64u);
+                break;
+            }
+            const uint4 it = item_s[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&iteme[slot]);
+            if (__any_sync(FULL, it.z == 0 || abort_s)) break;  // warp-uniform exit
+            const uint32_t s = i & 1u, u = i >> 1;
+            const uint32_t leaf = it.x, q0 = it.y, nq = it.z;
+            const int n16 = (int)((nq + 15u) & ~15u);
+            // the limit buffer s is free once the epilogue of the item two back is done,
+            // and the B tile once the previous item's MMAs have completed
+            if (!warp_wait(&cempty[s], (u & 1u) ^ 1u) || (i > 0 && !warp_wait(&bempty, (i - 1) & 1u))) {
+                if (lane == 0) tf_fail(&abort_s, v.err, 128u);
+                break;
+            }
+            // gather warp g fills rows g, g + 4, ...; lanes fetch those rows' query
+            // ids up front, so every copy is issued without waiting
+            {
+                const int gw = warp - W_GATHER;
+                uint32_t myq[TF_NQ / (TF_GATHER_WARPS * 32)];
+#pragma unroll
+                for (int h = 0; h < TF_NQ / (TF_GATHER_WARPS * 32); ++h) {
+                    const int jr = gw + TF_GATHER_WARPS * (lane + 32 * h);
+                    myq[h] = jr < (int)nq ? v.pairs[q0 + jr] : 0u;
+                }
+#pragma unroll
+                for (int h = 0; h < TF_NQ / (TF_GATHER_WARPS * 32); ++h) {
+                    for (int r = 0; r < 32; ++r) {
+                        const int j = gw + TF_GATHER_WARPS * (r + 32 * h);
+                        if (j >= n16) break;
+                        const uint32_t b = __shfl_sync(FULL, myq[h], r);
+                        for (int ch = lane; ch < cpr; ch += 32) {
+                            unsigned char* dst = Bs + sw128_offset(j, ch, n16);
+                            if (j < (int)nq)
+                                cp_async16(dst, v.qb + (size_t)b * n + ch * 8);
+                            else
+                                *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+                        }
+                    }
+                }
+            }
+            for (int j = gt; j < n16; j += TF_GATHER_WARPS * 32) {
+                if (j < (int)nq) {
+                    const uint32_t b = v.pairs[q0 + j];
+                    const float4 qc = v.qc[b];
+                    const unsigned long long ku = ld_volatile_u64(&v.utop[(size_t)b * MAX_K + k - 1]);
+                    double ub = (double)qc.z;
+                    if (ku != EMPTY_SLOT) ub = fmin(ub, (double)key_d2(ku));
+                    const double X = (double)v.leaf_xnorm[leaf], Q = (double)qc.y;
+                    const double E = (v.c_xq * X * Q + v.c_sq * (X * X + Q * Q)) * (1.0 + 1e-9);
+                    qid_s[s][j] = b;
+                    qn_s[s][j] = qc.x;
+                    lim_s[s][j] = __double2float_ru(ub + E);
+                    eu_s[s][j] = __double2float_ru(E);
+                    ku_s[s][j] = ku == EMPTY_SLOT ? 0x7f800000u : (unsigned)(ku >> 32);
+                } else {
+                    qn_s[s][j] = 0.0f;  // padding columns: a limit no value passes
+                    lim_s[s][j] = -INFINITY;
+                }
+            }
+            cp_async_wait_all();
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&cfull[s]);
+                mbar_arrive(&bfull);
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue warps
+        // warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows), column groups of
+        // 16 alternating between the two warps of a quarter
+        const int qd = warp & 3, half = warp >> 2;
+        uint32_t e_t = 0;
+        for (uint32_t i = 0;; ++i) {
+            const uint32_t slot = i % TF_SLOTS, ph = (i / TF_SLOTS) & 1u;
+            if (!warp_wait(&itemf[slot], ph)) {
+                if (lane == 0) tf_fail(&abort_s, v.err, 256u);
                 break;
             }
             const uint4 it = item_s[slot];
@@ -505,60 +576,17 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&iteme[slot]);
             if (__any_sync(FULL, it.z == 0 || abort_s)) break;  // warp-uniform exit
-            const uint32_t leaf = it.x, q0 = it.y, nq = it.z;
+            const uint32_t s = i & 1u, u = i >> 1;
+            const uint32_t nq = it.z;
             const int n16 = (int)((nq + 15u) & ~15u);
             const int64_t lb = it.w, le = it_le;
             const int tiles = (int)((le - lb + TC_M - 1) / TC_M);
-            // the previous item's MMAs and epilogues are complete: B tile and limits are free
-            if (i > 0 && !warp_wait(&epi_done, (i - 1) & 1u)) {
-                if (lane == 0) tf_fail(&abort_s, v.err, 128u);
+            if (!warp_wait(&cfull[s], u & 1u)) {  // this item's limits are in place
+                if (lane == 0) tf_fail(&abort_s, v.err, 512u);
                 break;
             }
-            // B tile: warp w fills rows w, w + 8, ...; lane r fetches the query id of
-            // row w + 8 r up front, so every copy is issued without waiting
-            {
-                const int jr = warp + TF_EPI_WARPS * lane;
-                const uint32_t myq = jr < (int)nq ? v.pairs[q0 + jr] : 0u;
-                for (int r = 0; r < 32; ++r) {
-                    const int j = warp + TF_EPI_WARPS * r;
-                    if (j >= n16) break;
-                    const uint32_t b = __shfl_sync(FULL, myq, r);
-                    for (int ch = lane; ch < cpr; ch += 32) {
-                        unsigned char* dst = Bs + sw128_offset(j, ch, n16);
-                        if (j < (int)nq)
-                            cp_async16(dst, v.qb + (size_t)b * n + ch * 8);
-                        else
-                            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
-                    }
-                }
-            }
-            if (tid < (int)nq) {
-                const uint32_t b = v.pairs[q0 + tid];
-                const float4 qc = v.qc[b];
-                const unsigned long long ku = ld_volatile_u64(&v.utop[(size_t)b * MAX_K + k - 1]);
-                double ub = (double)qc.z;
-                if (ku != EMPTY_SLOT) ub = fmin(ub, (double)key_d2(ku));
-                const double X = (double)v.leaf_xnorm[leaf], Q = (double)qc.y;
-                const double E = (v.c_xq * X * Q + v.c_sq * (X * X + Q * Q)) * (1.0 + 1e-9);
-                qid_s[tid] = b;
-                qn_s[tid] = qc.x;
-                lim_s[tid] = __double2float_ru(ub + E);
-                eu_s[tid] = __double2float_ru(E);
-                ku_s[tid] = ku == EMPTY_SLOT ? 0x7f800000u : (unsigned)(ku >> 32);
-            } else if (tid < n16) {
-                qn_s[tid] = 0.0f;  // padding columns: a limit no value passes
-                lim_s[tid] = -INFINITY;
-            }
-            cp_async_wait_all();
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&gathered);
-            if (!warp_wait(&gathered, i & 1u)) {
-                if (lane == 0) tf_fail(&abort_s, v.err, 256u);
-                break;
-            }
-            // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows), column
-            // groups of 16 alternating between the two warps of a quarter
+            const float* lim = lim_s[s];
+            const float* qn = qn_s[s];
             const int groups = n16 / 16;
             const int row = qd * 32 + lane;
             int64_t pos = lb + row;
@@ -571,7 +599,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                 const int64_t pn = pos + TC_M;
                 const float xr_next = pn < le ? v.xn[pn] : INFINITY;
                 if (!warp_wait(&accf[a], aph)) {
-                    if (lane == 0) tf_fail(&abort_s, v.err, 512u);
+                    if (lane == 0) tf_fail(&abort_s, v.err, 1024u);
                     ok = false;
                     break;
                 }
@@ -585,8 +613,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
                         const int j = g * 16 + c;
-                        const float dt = fmaf(-2.0f, acc[c], xr + qn_s[j]);
-                        pm |= (dt <= lim_s[j] ? 1u : 0u) << c;
+                        const float dt = fmaf(-2.0f, acc[c], xr + qn[j]);
+                        pm |= (dt <= lim[j] ? 1u : 0u) << c;
                     }
                     if (!valid) pm = 0;
                     if (__any_sync(FULL, pm != 0) == 0) continue;
@@ -594,7 +622,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                     for (int c = 0; c < 16; ++c) {
                         const int j = g * 16 + c;
                         if (j >= (int)nq) break;
-                        const float dt = fmaf(-2.0f, acc[c], xr + qn_s[j]);
+                        const float dt = fmaf(-2.0f, acc[c], xr + qn[j]);
                         const bool pass = (pm >> c) & 1u;
                         const unsigned m = __ballot_sync(FULL, pass);
                         if (m == 0) continue;
@@ -604,16 +632,17 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                         base = __shfl_sync(FULL, base, leader);
                         if (pass) {
                             const uint32_t slot_c = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
-                            const float eu = eu_s[j];
+                            const float eu = eu_s[s][j];
+                            const uint32_t qb_id = qid_s[s][j];
                             if (slot_c < v.cand_cap)
-                                v.cand[slot_c] = make_uint4((uint32_t)pos, qid_s[j], __float_as_uint(dt),
+                                v.cand[slot_c] = make_uint4((uint32_t)pos, qb_id, __float_as_uint(dt),
                                                             __float_as_uint(eu));
                             const float up = __fadd_ru(dt, eu);
-                            if (__float_as_uint(up) < ku_s[j]) {
-                                unsigned long long* slots = v.utop + (size_t)qid_s[j] * MAX_K;
+                            if (__float_as_uint(up) < ku_s[s][j]) {
+                                unsigned long long* slots = v.utop + (size_t)qb_id * MAX_K;
                                 topk_insert(slots, k, pack_key(up, (uint32_t)pos));
                                 const unsigned long long kk = ld_volatile_u64(&slots[k - 1]);
-                                if (kk != EMPTY_SLOT) atomicMin(&ku_s[j], (unsigned)(kk >> 32));
+                                if (kk != EMPTY_SLOT) atomicMin(&ku_s[s][j], (unsigned)(kk >> 32));
                             }
                         }
                     }
@@ -626,7 +655,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
             }
             if (!ok) break;
             __syncwarp();
-            if (lane == 0) mbar_arrive(&epi_done);
+            if (lane == 0) mbar_arrive(&cempty[s]);  // this item's limits are no longer read
         }
     }
     tc_fence_before();
@@ -962,12 +991,12 @@ static bool run_pass(isax_index* ix, TcState* t, int B, int k, cudaStream_t st) 
     v.n = d.n;
     v.k = k;
     tc_bound_constants(d.n, &v.c_xq, &v.c_sq);
-    const size_t smem = 1024 + (size_t)nq * d.n * 2 + (size_t)TF_STAGES * TF_ATOM_BYTES;
+    const size_t smem = smem_tf();
     {
         static bool attr[64] = {};
         if (ix->device < 0 || ix->device >= 64 || !attr[ix->device]) {
             ISAX_CUDA_TRY(cudaFuncSetAttribute(tc_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem_max_tf()));
+                                               (int)smem_tf()));
             if (ix->device >= 0 && ix->device < 64) attr[ix->device] = true;
         }
         ISAX_LAUNCH("tc_filter", st);
