@@ -500,37 +500,19 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
             const uint32_t s = i & 1u, u = i >> 1;
             const uint32_t leaf = it.x, q0 = it.y, nq = it.z;
             const int n16 = (int)((nq + 15u) & ~15u);
-            // the limit buffer s is free once the epilogue of the item two back is done,
-            // and the B tile once the previous item's MMAs have completed
-            if (!warp_wait(&cempty[s], (u & 1u) ^ 1u) || (i > 0 && !warp_wait(&bempty, (i - 1) & 1u))) {
+            // the limit buffer s is free once the epilogue of the item two back is done
+            if (!warp_wait(&cempty[s], (u & 1u) ^ 1u)) {
                 if (lane == 0) tf_fail(&abort_s, v.err, 128u);
                 break;
             }
-            // gather warp g fills rows g, g + 4, ...; lanes fetch those rows' query
-            // ids up front, so every copy is issued without waiting
-            {
-                const int gw = warp - W_GATHER;
-                uint32_t myq[TF_NQ / (TF_GATHER_WARPS * 32)];
+            // query ids of this warp's rows (g, g + 4, ...; lane r holds row g + 4 r) and
+            // the per-column limits, before the B tile is free
+            const int gw = warp - W_GATHER;
+            uint32_t myq[TF_NQ / (TF_GATHER_WARPS * 32)];
 #pragma unroll
-                for (int h = 0; h < TF_NQ / (TF_GATHER_WARPS * 32); ++h) {
-                    const int jr = gw + TF_GATHER_WARPS * (lane + 32 * h);
-                    myq[h] = jr < (int)nq ? v.pairs[q0 + jr] : 0u;
-                }
-#pragma unroll
-                for (int h = 0; h < TF_NQ / (TF_GATHER_WARPS * 32); ++h) {
-                    for (int r = 0; r < 32; ++r) {
-                        const int j = gw + TF_GATHER_WARPS * (r + 32 * h);
-                        if (j >= n16) break;
-                        const uint32_t b = __shfl_sync(FULL, myq[h], r);
-                        for (int ch = lane; ch < cpr; ch += 32) {
-                            unsigned char* dst = Bs + sw128_offset(j, ch, n16);
-                            if (j < (int)nq)
-                                cp_async16(dst, v.qb + (size_t)b * n + ch * 8);
-                            else
-                                *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
-                        }
-                    }
-                }
+            for (int h = 0; h < TF_NQ / (TF_GATHER_WARPS * 32); ++h) {
+                const int jr = gw + TF_GATHER_WARPS * (lane + 32 * h);
+                myq[h] = jr < (int)nq ? v.pairs[q0 + jr] : 0u;
             }
             for (int j = gt; j < n16; j += TF_GATHER_WARPS * 32) {
                 if (j < (int)nq) {
@@ -549,6 +531,27 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
                 } else {
                     qn_s[s][j] = 0.0f;  // padding columns: a limit no value passes
                     lim_s[s][j] = -INFINITY;
+                }
+            }
+            // the B tile is free once the previous item's MMAs have completed; every
+            // copy is then issued without waiting
+            if (i > 0 && !warp_wait(&bempty, (i - 1) & 1u)) {
+                if (lane == 0) tf_fail(&abort_s, v.err, 128u);
+                break;
+            }
+#pragma unroll
+            for (int h = 0; h < TF_NQ / (TF_GATHER_WARPS * 32); ++h) {
+                for (int r = 0; r < 32; ++r) {
+                    const int j = gw + TF_GATHER_WARPS * (r + 32 * h);
+                    if (j >= n16) break;
+                    const uint32_t b = __shfl_sync(FULL, myq[h], r);
+                    for (int ch = lane; ch < cpr; ch += 32) {
+                        unsigned char* dst = Bs + sw128_offset(j, ch, n16);
+                        if (j < (int)nq)
+                            cp_async16(dst, v.qb + (size_t)b * n + ch * 8);
+                        else
+                            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+                    }
                 }
             }
             cp_async_wait_all();
