@@ -170,15 +170,23 @@ def kernel_bytes(name, a, launches, acc):
     return None
 
 
+def kernel_source_hash(kernel):
+    """Hash of the sources a kernel is built from: the file that defines it (q_*
+    kernels: isax_query.cu, tc_*: isax_tc.cu, the rest: isax_build.cu) and the
+    two shared device headers."""
+    src = os.path.join(ROOT, "paper_2009_01614_gb300", "csrc")
+    own = ("isax_query.cu" if kernel.startswith(("q_", "bq_")) else
+           "isax_tc.cu" if kernel.startswith("tc_") else "isax_build.cu")
+    h = hashlib.sha256()
+    for f in (own, "isax_common.cuh", "isax_kernels_util.cuh"):
+        h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profile(kernel):
     """dram bytes per launch from a committed ncu summary, if it was taken on
     the current kernel source (its hash is recorded next to the figure)."""
-    src = os.path.join(ROOT, "paper_2009_01614_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(src, f), "rb").read())
-    digest = h.hexdigest()[:16]
+    digest = kernel_source_hash(kernel)
     prof = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(prof):
         return None
