@@ -77,3 +77,17 @@ def test_fullsize_exact_1nn(full_index):
 def test_fullsize_exact_10nn(full_index):
     Q, _ = datagen.queries("walk", 0, N, n, 5, 6, 2, 0.05)
     _check(full_index, Q, 10)
+
+
+def test_fullsize_bf16_batch_equals_plain_and_oracle(full_index):
+    """The tensor-core filtered batch at full size, in the benchmark's batch
+    shape (queries drawn like the single-query workload), equals the plain
+    batch path exactly; sampled queries are checked against the oracle."""
+    Q, src = datagen.queries("walk", 0, N, n, 9, 460, 52, 0.01)
+    Qt = torch.from_numpy(Q).cuda()
+    i1, d1 = full_index.query_batch(Qt, 10)
+    i2, d2 = full_index.query_batch_bf16(Qt, 10)
+    assert torch.equal(i2, i1) and torch.equal(d2, d1)
+    np.testing.assert_array_equal(i2[460:, 0].cpu().numpy(), src[460:])
+    sel = np.arange(0, 512, 64)
+    _check(full_index, Q[sel], 10)
