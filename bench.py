@@ -55,7 +55,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=4_000_000)
-    ap.add_argument("--workload", choices=["walk", "hardness"], default="walk",
+    ap.add_argument("--serve-scale", type=float, default=1.0,
+                    help="serving workload: scale the three collections' sizes (1.0: 40M x 256, "
+                         "80M x 128, 10M x 1024)")
+    ap.add_argument("--serve-requests", type=int, default=3000,
+                    help="serving workload: requests per arrival rate")
+    ap.add_argument("--workload", choices=["walk", "hardness", "serving"], default="walk",
                     help="hardness: the sinusoid collection, member queries by noise level and k")
     ap.add_argument("--batch", type=int, default=1024,
                     help="batched leg: time the plain and the BF16-filtered batch paths on "
@@ -288,6 +293,118 @@ def batch_leg(a, X, pkg, torch, stream, rank):
             "runs": runs}
 
 
+# ------------------------------------------------------------------ serving workload
+def serving(a):
+    """Three resident collections (40M x 256, 80M x 128, 10M x 1024 z-normalised
+    random walks, seeds 10-12, w 16, leaf 2000) behind one query server (16
+    slots, 256 MiB candidate budget).  Requests arrive as a Poisson process
+    (seed 20) at 200, 1000 and 5000 per second, each routed uniformly to a
+    collection with k uniform in {1, 10, 100}, half fresh walks and half members
+    with noise sigma ~ U[0.01, 0.5].  Latency = answer back on the host minus the
+    scheduled arrival (queueing included).  One JSON line."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import datagen
+    import paper_2009_01614_gb300 as pkg
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream().cuda_stream
+    specs = [(10, int(40_000_000 * a.serve_scale), 256), (11, int(80_000_000 * a.serve_scale), 128),
+             (12, int(10_000_000 * a.serve_scale), 1024)]
+    indexes = []
+    build_ms = []
+    for seed, N, n in specs:
+        X = torch.empty((N, n), dtype=torch.float32, device="cuda")
+        datagen.rows_device("walk", seed, 0, N, n, X.data_ptr(), st)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        indexes.append(pkg.Index(X, leaf_size=a.leaf))
+        torch.cuda.synchronize()
+        build_ms.append((time.perf_counter() - t0) * 1e3)
+        del X
+        torch.cuda.empty_cache()
+    rng = np.random.default_rng(20)
+    R = a.serve_requests
+
+    def requests(count, salt):
+        out = []
+        for t in range(count):
+            c = int(rng.integers(3))
+            seed, N, n = specs[c]
+            k = int(rng.choice([1, 10, 100]))
+            if rng.random() < 0.5:
+                q = datagen.rows("walk", 100 + seed + salt, t, 1, n)[0]
+            else:
+                q = datagen.queries("walk", seed, N, n, 200 + seed + 1000 * salt + t, 0, 1,
+                                    float(rng.uniform(0.01, 0.5)))[0][0]
+            out.append((c, k, q))
+        return out
+
+    def run_rate(rate, reqs, srv):
+        gaps = rng.exponential(1.0 / rate, size=len(reqs))
+        sched = np.cumsum(gaps)
+        got = {}
+        t0 = srv.clock() + 0.05
+        arrival = t0 + sched
+        for i, (c, k, q) in enumerate(reqs):
+            while srv.clock() < arrival[i]:
+                for r in srv.poll(64, 0):
+                    got[r["tag"]] = r
+            srv.submit(c, q, k, i)
+        while len(got) < len(reqs):
+            for r in srv.poll(256, 20):
+                got[r["tag"]] = r
+        lat = np.array([got[i]["done_s"] - arrival[i] for i in range(len(reqs))]) * 1e3
+        svc = np.array([got[i]["done_s"] - got[i]["start_s"] for i in range(len(reqs))]) * 1e3
+        wall = max(r["done_s"] for r in got.values()) - arrival[0]
+        assert all(r["status"] == 0 for r in got.values())
+        return got, {"offered_per_s": rate, "requests": len(reqs),
+                     "queries_per_s": len(reqs) / wall,
+                     "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                    "mean": float(lat.mean())},
+                     "in_slot_ms": {"p50": float(np.percentile(svc, 50)), "p99": float(np.percentile(svc, 99))},
+                     "max_in_flight": srv.info()["max_in_flight"],
+                     "reruns": int(sum(r["reruns"] for r in got.values()))}
+
+    results = []
+    identical = None
+    for rate in (200, 1000, 5000):
+        srv = pkg.Server(slots=16, candidate_budget=256 << 20)
+        for ix in indexes:
+            srv.add(ix)
+        reqs = requests(min(R, int(rate * 4) + 200), rate)
+        run_rate(rate, reqs[:64], srv)  # warm up: graphs captured per (slot, collection, k)
+        got, res = run_rate(rate, reqs, srv)
+        results.append(res)
+        if rate == 5000:
+            # the same requests one at a time give the same answers
+            alone = pkg.Server(slots=16, candidate_budget=256 << 20)
+            for ix in indexes:
+                alone.add(ix)
+            same = True
+            for i, (c, k, q) in enumerate(reqs[:200]):
+                alone.submit(c, q, k, i)
+                r = alone.poll(1, 10_000)[0]
+                same &= bool(np.array_equal(r["idx"], got[i]["idx"]) and
+                             np.array_equal(r["dist"], got[i]["dist"]))
+            identical = same
+            alone.close()
+        srv.close()
+    out = {"metric": "exact k-NN queries/s served (continuous batching) + p50/p99 latency",
+           "workload": "3 resident collections %s (w 16, leaf %d); Poisson arrivals, collection uniform, "
+                       "k in {1,10,100}, 50%% fresh / 50%% noisy members sigma U[0.01,0.5]" % (
+                           ", ".join("%dx%d" % (N, n) for _, N, n in specs), a.leaf),
+           "unit": "queries/s", "server": {"slots": 16, "candidate_budget_bytes": 256 << 20},
+           "build_ms": build_ms, "rates": results,
+           "mixed_equals_alone_first_200_at_5000_per_s": identical,
+           "dtype": "f32", "data": "synthetic"}
+    for ix in indexes:
+        ix.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ CPU baseline
 def cpu_baseline(a, sample_rows, n_queries=10):
     import numpy as np
@@ -405,6 +522,8 @@ def main():
         return reference_arm(a)
     if a.workload == "hardness":
         return hardness(a)
+    if a.workload == "serving":
+        return serving(a)
 
     import numpy as np
     import torch

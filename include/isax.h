@@ -238,6 +238,79 @@ isax_status isax_query_knn_batch_bf16(const isax_index* ix, const float* Q, int3
  * too large for the error bound (|x| >= 1e15). */
 isax_status isax_prepare_bf16(isax_index* ix, void* cuda_stream);
 
+/* ------------------------------------------------------------ resident query server */
+
+/*
+ * A resident query server (the paper has no counterpart; it serves the
+ * single-query path of Section III to many clients).  Several indexes stay in
+ * device memory; requests for any of them are admitted, as they arrive, into a
+ * fixed set of in-flight slots (continuous batching: no batch has to form or
+ * drain).  A request is admitted, in arrival order, when a slot is free and its
+ * candidate buffer (12 bytes x (4096 + 256 k) entries) fits the memory budget
+ * beside those of the requests in flight; a query whose buffer overflows is
+ * rerun with four times the room once the budget allows.  Each request runs
+ * the single-query kernels on its slot's own stream, scratch and captured
+ * graphs, so its answer is the one isax_query_knn returns for it alone.  A host
+ * thread inside the library runs the loop; the calls below are thread-safe.
+ */
+typedef struct isax_server isax_server;
+
+typedef struct isax_server_params {
+    int32_t slots;             /* requests in flight at most (1..256; 0: 16) */
+    int64_t candidate_budget;  /* bytes of candidate buffers in flight (0: 256 MiB) */
+} isax_server_params;
+
+typedef struct isax_server_result {
+    uint64_t tag;              /* the caller's tag from isax_server_submit */
+    int32_t collection;        /* id from isax_server_add_collection */
+    int32_t k;
+    int32_t status;            /* ISAX_OK, or the error of this request */
+    int32_t reruns;            /* reruns after a candidate overflow */
+    double submit_s;           /* times on isax_server_clock(): submitted, */
+    double start_s;            /* admitted into a slot, */
+    double done_s;             /* answer copied back */
+    isax_query_stats stats;
+} isax_server_result;
+
+typedef struct isax_server_info {
+    int32_t collections, slots;
+    int64_t queued;            /* submitted, not yet admitted */
+    int32_t in_flight, max_in_flight;
+    int64_t reserved_bytes, budget_bytes;
+    int64_t submitted, completed;
+} isax_server_info;
+
+/* A server on the current device (params may be NULL for the defaults). */
+isax_status isax_server_create(const isax_server_params* params, isax_server** out);
+
+/* Add a collection before the first submit (the slots are sized for the
+ * collections added by then).  The index stays owned by the caller and must
+ * outlive the server; it must live on the server's device.  *id = 0, 1, ... */
+isax_status isax_server_add_collection(isax_server* s, isax_index* ix, int32_t* id);
+
+/* Queue one exact k-NN request: q is a HOST array of the collection's series
+ * length n (copied before the call returns), 1 <= k <= min(N, 1024).  Returns
+ * at once; the result is collected with isax_server_poll. */
+isax_status isax_server_submit(isax_server* s, int32_t collection, const float* q, int32_t k,
+                               uint64_t tag);
+
+/* Up to max finished results, oldest first, waiting up to wait_ms for the
+ * first one.  Result i's answer goes to idx[i * stride .. + k) and
+ * dist[i * stride .. + k) (host arrays; either may be NULL; a result with
+ * k > stride stays queued).  Returns the number of results, -1 on bad
+ * arguments. */
+int32_t isax_server_poll(isax_server* s, isax_server_result* out, int64_t* idx, float* dist,
+                         int32_t max, int32_t stride, int32_t wait_ms);
+
+/* Queue lengths, slots in use, budget in use. */
+isax_status isax_server_get_info(isax_server* s, isax_server_info* info);
+
+/* Seconds on the server's (monotonic) clock, for request timestamps. */
+double isax_server_clock(void);
+
+/* Finish every queued and in-flight request, then release the server. */
+void isax_server_destroy(isax_server* s);
+
 /* ------------------------------------------------------------ tensor-core check */
 
 /*

@@ -20,7 +20,9 @@ __all__ = [
     "isax_last_error", "isax_get_index_info", "isax_index_export", "isax_summarize",
     "isax_set_allocator", "isax_profile", "isax_profile_report", "isax_launch_count",
     "isax_query_knn_noalloc", "isax_tc_selftest", "isax_query_knn_batch_bf16",
-    "isax_prepare_bf16",
+    "isax_prepare_bf16", "Server", "ServerParams", "ServerResult", "ServerInfo",
+    "isax_server_create", "isax_server_add_collection", "isax_server_submit", "isax_server_poll",
+    "isax_server_get_info", "isax_server_clock", "isax_server_destroy",
 ]
 
 W = 16
@@ -52,6 +54,28 @@ class QueryStats(ctypes.Structure):
                 ("candidates", ctypes.c_int64),
                 ("window", ctypes.c_int64), ("approx_leaf", ctypes.c_int32),
                 ("reruns", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("candidate_budget", ctypes.c_int64)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("collection", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("reruns", ctypes.c_int32),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("stats", QueryStats)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("collections", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int32),
+                ("max_in_flight", ctypes.c_int32), ("reserved_bytes", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64), ("submitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -130,6 +154,20 @@ def lib():
         L.isax_query_knn_batch_bf16.restype = st
         L.isax_prepare_bf16.argtypes = [vp, vp]
         L.isax_prepare_bf16.restype = st
+        L.isax_server_create.argtypes = [ctypes.POINTER(ServerParams), ctypes.POINTER(vp)]
+        L.isax_server_create.restype = st
+        L.isax_server_add_collection.argtypes = [vp, vp, ctypes.POINTER(i32)]
+        L.isax_server_add_collection.restype = st
+        L.isax_server_submit.argtypes = [vp, i32, vp, i32, ctypes.c_uint64]
+        L.isax_server_submit.restype = st
+        L.isax_server_poll.argtypes = [vp, ctypes.POINTER(ServerResult), vp, vp, i32, i32, i32]
+        L.isax_server_poll.restype = i32
+        L.isax_server_get_info.argtypes = [vp, ctypes.POINTER(ServerInfo)]
+        L.isax_server_get_info.restype = st
+        L.isax_server_clock.argtypes = []
+        L.isax_server_clock.restype = ctypes.c_double
+        L.isax_server_destroy.argtypes = [vp]
+        L.isax_server_destroy.restype = None
         _lib = L
     return _lib
 
@@ -184,6 +222,41 @@ def isax_prepare_bf16(index, stream=0):
 
 def isax_free_index(index):
     lib().isax_free_index(index)
+
+
+def isax_server_create(slots=0, candidate_budget=0):
+    p = ServerParams(int(slots), int(candidate_budget))
+    h = ctypes.c_void_p()
+    _check(lib().isax_server_create(ctypes.byref(p), ctypes.byref(h)))
+    return h.value
+
+
+def isax_server_add_collection(server, index):
+    cid = ctypes.c_int32()
+    _check(lib().isax_server_add_collection(server, index, ctypes.byref(cid)))
+    return cid.value
+
+
+def isax_server_submit(server, collection, q_ptr, k, tag):
+    _check(lib().isax_server_submit(server, collection, q_ptr, k, tag))
+
+
+def isax_server_poll(server, out, idx_ptr, dist_ptr, max_results, stride, wait_ms):
+    return int(lib().isax_server_poll(server, out, idx_ptr, dist_ptr, max_results, stride, wait_ms))
+
+
+def isax_server_get_info(server):
+    info = ServerInfo()
+    _check(lib().isax_server_get_info(server, ctypes.byref(info)))
+    return info
+
+
+def isax_server_clock():
+    return float(lib().isax_server_clock())
+
+
+def isax_server_destroy(server):
+    lib().isax_server_destroy(server)
 
 
 def isax_last_error():
@@ -369,3 +442,71 @@ def summarize(series, cardinality=256, stream=None):
         paa = np.empty((N, W), np.float32)
         isax_summarize(ptr, N, n, cardinality, 0, sax.ctypes.data, paa.ctypes.data, st)
     return sax, paa
+
+
+class Server:
+    """A resident query server over several indexes (isax_server_*): requests
+    are admitted into in-flight slots as they arrive (continuous batching) and
+    each returns the same answer as the single query.
+
+    ``Server(slots=16, candidate_budget=256 << 20)``; ``add(index)`` -> id
+    (before the first submit; the index must outlive the server);
+    ``submit(collection, q, k, tag)`` with a host array q; ``poll(max, wait_ms)``
+    -> list of dicts (tag, collection, k, status, reruns, submit_s, start_s,
+    done_s, stats, idx, dist)."""
+
+    def __init__(self, slots=16, candidate_budget=256 << 20):
+        self._h = None
+        self._h = isax_server_create(slots, candidate_budget)
+        self._indexes = []
+        self._stride = 0
+        self._bufs = None
+
+    def add(self, index):
+        cid = isax_server_add_collection(self._h, index._h)
+        self._indexes.append(index)
+        return cid
+
+    def submit(self, collection, q, k=1, tag=0):
+        import numpy as np
+        q = np.ascontiguousarray(q, dtype=np.float32)
+        isax_server_submit(self._h, collection, q.ctypes.data, int(k), int(tag))
+        self._stride = max(self._stride, int(k))
+
+    def poll(self, max_results=256, wait_ms=0):
+        import numpy as np
+        stride = max(self._stride, 1)
+        if self._bufs is None or self._bufs[0] < max_results or self._bufs[1] < stride:
+            self._bufs = (max_results, stride, (ServerResult * max_results)(),
+                          np.empty((max_results, stride), np.int64),
+                          np.empty((max_results, stride), np.float32))
+        _, st, out, idx, dist = self._bufs
+        m = isax_server_poll(self._h, out, idx.ctypes.data, dist.ctypes.data, max_results, st,
+                             int(wait_ms))
+        res = []
+        for i in range(m):
+            r = out[i]
+            res.append({"tag": int(r.tag), "collection": int(r.collection), "k": int(r.k),
+                        "status": int(r.status), "reruns": int(r.reruns),
+                        "submit_s": r.submit_s, "start_s": r.start_s, "done_s": r.done_s,
+                        "stats": r.stats.as_dict(),
+                        "idx": idx[i, :r.k].copy(), "dist": dist[i, :r.k].copy()})
+        return res
+
+    def info(self):
+        return isax_server_get_info(self._h).as_dict()
+
+    @staticmethod
+    def clock():
+        return isax_server_clock()
+
+    def close(self):
+        if self._h is not None:
+            isax_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -150,6 +150,15 @@ void launch_bq_fill(isax_index* ix, int B, const uint32_t* mask, const uint32_t*
 void launch_bq_recheck(isax_index* ix, const QueryScratch* ss, int k, const uint4* cand,
                        const uint32_t* cand_count, uint32_t cap, cudaStream_t st);
 void launch_bq_finalize(isax_index* ix, const QueryScratch* ss, int B, int k, cudaStream_t st);
+// scratch and captured graphs for the resident query server (isax_serve.cu)
+void alloc_query_scratch_for(int64_t L, int n, int card, uint32_t cand_cap, QueryScratch& q,
+                             cudaStream_t st);
+void grow_query_candidates(QueryScratch& q, uint32_t cand_cap, cudaStream_t st);
+void free_query_scratch_struct(QueryScratch& q, cudaStream_t st);
+void* query_graphs_new();
+void query_graphs_delete(void* g);
+void query_graphs_clear(void* g);
+void launch_query_graph_ext(isax_index* ix, const QueryScratch& qs, void* g, int k, cudaStream_t st);
 // the tensor-core filtered batch (isax_tc.cu)
 void prepare_tc(isax_index* ix, cudaStream_t st);
 void query_batch_tc(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags, int64_t* out_idx,

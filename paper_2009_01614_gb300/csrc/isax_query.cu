@@ -1043,7 +1043,9 @@ __global__ void __launch_bounds__(256) bq_recheck_kernel(DevIndex ix, const Quer
 }
 
 // ================================================================ host side
-static void free_scratch(QueryScratch& q, cudaStream_t st) {
+void free_query_scratch_struct(QueryScratch& q, cudaStream_t st);
+static void free_scratch(QueryScratch& q, cudaStream_t st) { free_query_scratch_struct(q, st); }
+void free_query_scratch_struct(QueryScratch& q, cudaStream_t st) {
     void* ptrs[] = {q.q, q.table, q.leaf_lb, q.work, q.bin_count, q.bin_cursor, q.topk,
                     q.cand_key, q.cand_pos, q.ctl, q.out_idx, q.out_dist};
     for (void* p : ptrs)
@@ -1051,11 +1053,14 @@ static void free_scratch(QueryScratch& q, cudaStream_t st) {
     q = QueryScratch{};
 }
 
-static void alloc_scratch(const DevIndex& d, uint32_t cand_cap, QueryScratch& q, cudaStream_t st) {
-    q.q = static_cast<float*>(dev_alloc(sizeof(float) * d.n, st));
-    q.table = static_cast<float*>(dev_alloc(sizeof(float) * W * d.card, st));
-    q.leaf_lb = static_cast<float*>(dev_alloc(sizeof(float) * d.L, st));
-    q.work = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * d.L, st));
+// scratch for queries on any index with at most L leaves, series length n and
+// cardinality card
+void alloc_query_scratch_for(int64_t L, int n, int card, uint32_t cand_cap, QueryScratch& q,
+                             cudaStream_t st) {
+    q.q = static_cast<float*>(dev_alloc(sizeof(float) * n, st));
+    q.table = static_cast<float*>(dev_alloc(sizeof(float) * W * card, st));
+    q.leaf_lb = static_cast<float*>(dev_alloc(sizeof(float) * L, st));
+    q.work = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * L, st));
     q.bin_count = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * NBINS, st));
     q.bin_cursor = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * NBINS, st));
     q.topk = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * MAX_K, st));
@@ -1066,6 +1071,22 @@ static void alloc_scratch(const DevIndex& d, uint32_t cand_cap, QueryScratch& q,
     q.out_idx = static_cast<int64_t*>(dev_alloc(sizeof(int64_t) * MAX_K, st));
     q.out_dist = static_cast<float*>(dev_alloc(sizeof(float) * MAX_K, st));
     ISAX_CUDA_TRY(cudaMemsetAsync(q.ctl, 0, sizeof(QCtl), st));
+}
+
+static void alloc_scratch(const DevIndex& d, uint32_t cand_cap, QueryScratch& q, cudaStream_t st) {
+    alloc_query_scratch_for(d.L, d.n, d.card, cand_cap, q, st);
+}
+
+// a larger candidate buffer (the old contents are dropped)
+void grow_query_candidates(QueryScratch& q, uint32_t cand_cap, cudaStream_t st) {
+    if (q.cand_key) dev_free(q.cand_key, st);
+    if (q.cand_pos) dev_free(q.cand_pos, st);
+    q.cand_key = nullptr;
+    q.cand_pos = nullptr;
+    q.cand_cap = 0;
+    q.cand_key = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * cand_cap, st));
+    q.cand_pos = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * cand_cap, st));
+    q.cand_cap = cand_cap;
 }
 
 // The query's kernel sequence, captured once per k into a CUDA graph and
@@ -1259,6 +1280,14 @@ static void launch_query_graph(isax_index* ix, const QueryScratch& qs, QueryGrap
     }
     ISAX_CUDA_TRY(cudaGraphLaunch(it->second, st));
     count_launches(g->kernels_per_query);
+}
+
+// captured query graphs for callers outside this file (one cache per index and scratch)
+void* query_graphs_new() { return new QueryGraphs(); }
+void query_graphs_delete(void* g) { delete static_cast<QueryGraphs*>(g); }
+void query_graphs_clear(void* g) { static_cast<QueryGraphs*>(g)->clear(); }
+void launch_query_graph_ext(isax_index* ix, const QueryScratch& qs, void* g, int k, cudaStream_t st) {
+    launch_query_graph(ix, qs, static_cast<QueryGraphs*>(g), k, st);
 }
 
 static void launch_query_index(isax_index* ix, int k, cudaStream_t st) {

@@ -109,3 +109,18 @@ def test_tc_selftest_validation(lib):
     _expect(lib.isax_tc_selftest(a.ctypes.data, a.ctypes.data, 24, a.ctypes.data, None), 1,
             "multiple of 16")
     _expect(lib.isax_tc_selftest(None, a.ctypes.data, 32, a.ctypes.data, None), 1, "NULL")
+
+
+def test_server_argument_validation(lib):
+    assert lib.isax_server_create(None, None) == 1
+    p = pkg.ServerParams(-1, 0)
+    h = ctypes.c_void_p()
+    assert lib.isax_server_create(ctypes.byref(p), ctypes.byref(h)) == 1
+    p = pkg.ServerParams(300, 0)
+    assert lib.isax_server_create(ctypes.byref(p), ctypes.byref(h)) == 1
+    assert lib.isax_server_submit(None, 0, None, 1, 0) == 1
+    assert lib.isax_server_add_collection(None, None, None) == 1
+    assert lib.isax_server_poll(None, None, None, None, 1, 1, 0) == -1
+    assert lib.isax_server_get_info(None, None) == 1
+    lib.isax_server_destroy(None)  # no-op
+    assert lib.isax_server_clock() > 0
