@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=4_000_000)
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving leg (three resident collections, Poisson arrivals)")
     ap.add_argument("--serve-scale", type=float, default=1.0,
                     help="serving workload: scale the three collections' sizes (1.0: 40M x 256, "
                          "80M x 128, 10M x 1024)")
@@ -295,20 +297,29 @@ def batch_leg(a, X, pkg, torch, stream, rank):
 
 # ------------------------------------------------------------------ serving workload
 def serving(a):
+    """The serving workload alone (see serving_leg).  One JSON line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2009_01614_gb300 as pkg
+    torch.cuda.set_device(0)
+    out = serving_leg(a, pkg, torch)
+    out.update({"metric": "exact k-NN queries/s served (continuous batching) + p50/p99 latency",
+                "unit": "queries/s", "dtype": "f32", "data": "synthetic"})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def serving_leg(a, pkg, torch):
     """Three resident collections (40M x 256, 80M x 128, 10M x 1024 z-normalised
     random walks, seeds 10-12, w 16, leaf 2000) behind one query server (16
     slots, 256 MiB candidate budget).  Requests arrive as a Poisson process
     (seed 20) at 200, 1000 and 5000 per second, each routed uniformly to a
     collection with k uniform in {1, 10, 100}, half fresh walks and half members
     with noise sigma ~ U[0.01, 0.5].  Latency = answer back on the host minus the
-    scheduled arrival (queueing included).  One JSON line."""
+    scheduled arrival (queueing included)."""
     import numpy as np
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
     import datagen
-    import paper_2009_01614_gb300 as pkg
-    torch.cuda.set_device(0)
     st = torch.cuda.current_stream().cuda_stream
     specs = [(10, int(40_000_000 * a.serve_scale), 256), (11, int(80_000_000 * a.serve_scale), 128),
              (12, int(10_000_000 * a.serve_scale), 1024)]
@@ -391,18 +402,16 @@ def serving(a):
             identical = same
             alone.close()
         srv.close()
-    out = {"metric": "exact k-NN queries/s served (continuous batching) + p50/p99 latency",
-           "workload": "3 resident collections %s (w 16, leaf %d); Poisson arrivals, collection uniform, "
+    out = {"workload": "3 resident collections %s (w 16, leaf %d); Poisson arrivals, collection uniform, "
                        "k in {1,10,100}, 50%% fresh / 50%% noisy members sigma U[0.01,0.5]" % (
                            ", ".join("%dx%d" % (N, n) for _, N, n in specs), a.leaf),
-           "unit": "queries/s", "server": {"slots": 16, "candidate_budget_bytes": 256 << 20},
+           "server": {"slots": 16, "candidate_budget_bytes": 256 << 20},
            "build_ms": build_ms, "rates": results,
-           "mixed_equals_alone_first_200_at_5000_per_s": identical,
-           "dtype": "f32", "data": "synthetic"}
+           "mixed_equals_alone_first_200_at_5000_per_s": identical}
     for ix in indexes:
         ix.close()
-    print(json.dumps(out), flush=True)
-    return 0
+    torch.cuda.synchronize()
+    return out
 
 
 # ------------------------------------------------------------------ CPU baseline
@@ -714,6 +723,11 @@ def main():
         del Xh
     else:
         del X
+
+    if rank == 0 and not a.no_serving and world == 1:
+        # the served path (config 4): its own collections, after the main job's are freed
+        torch.cuda.empty_cache()
+        out["serving"] = serving_leg(a, pkg, torch)
 
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, min(a.cpu_sample_rows, N))
