@@ -178,14 +178,14 @@ def kernel_bytes(name, a, launches, acc):
 
 
 def kernel_source_hash(kernel):
-    """Hash of the sources a kernel is built from: the file that defines it (q_*
-    kernels: isax_query.cu, tc_*: isax_tc.cu, the rest: isax_build.cu) and the
-    two shared device headers."""
+    """Hash of the sources a kernel is compiled from: the file that defines it
+    (q_* kernels: isax_query.cu, tc_*: isax_tc.cu, the rest: isax_build.cu) and
+    the shared device-helper header (the host declarations header is left out)."""
     src = os.path.join(ROOT, "paper_2009_01614_gb300", "csrc")
     own = ("isax_query.cu" if kernel.startswith(("q_", "bq_")) else
            "isax_tc.cu" if kernel.startswith("tc_") else "isax_build.cu")
     h = hashlib.sha256()
-    for f in (own, "isax_common.cuh", "isax_kernels_util.cuh"):
+    for f in (own, "isax_kernels_util.cuh"):
         h.update(open(os.path.join(src, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -202,6 +202,46 @@ def traffic_from_profile(kernel):
         if len(parts) >= 4 and parts[0] == kernel and parts[1] == digest:
             return float(parts[2]), parts[3]
     return None
+
+
+# ------------------------------------------------------------------ ablation
+def ablation_leg(a, X, Qd, pkg, torch, stream):
+    """The step's queries answered twice on one index: MESSI (leaf envelopes
+    prune leaves, leaves visited in bound order) and the ParIS flat scan (every
+    series of the SAX array bounded in storage order).  Answers must agree.
+    Per-query CUDA-event latency and pruning counters."""
+    import numpy as np
+    sp = stream.cuda_stream
+    ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp)
+    out = {}
+    answers = {}
+    for mode in ("messi", "flat"):
+        fn = ix.query if mode == "messi" else ix.query_flat
+        fn(Qd[0], a.k, stream=sp)  # capture its graph
+        lat, st_all, ans = [], [], []
+        for b in range(len(Qd)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            i, d, st = fn(Qd[b], a.k, stats=True, stream=sp)
+            e1.record(stream)
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1))
+            st_all.append(st)
+            ans.append((i.cpu().numpy(), d.cpu().numpy()))
+        answers[mode] = ans
+        out[mode] = {
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "queries_per_s": len(lat) / (sum(lat) / 1e3),
+            "series_bounded_per_query": float(np.mean([s["series_lb"] for s in st_all])),
+            "series_refined_per_query": float(np.mean([s["series_refined"] for s in st_all])),
+            "leaves_scanned_per_query": float(np.mean([s["leaves_scanned"] for s in st_all])),
+        }
+    out["same_answers"] = all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+                              for x, y in zip(answers["messi"], answers["flat"]))
+    out["messi_speedup"] = out["flat"]["latency_ms"]["p50"] / out["messi"]["latency_ms"]["p50"]
+    ix.close()
+    return out
 
 
 # ------------------------------------------------------------------ batched leg
@@ -659,6 +699,9 @@ def main():
             entry["GB_per_s"] = round(b / (ms / 1e3) / 1e9, 1)
         kernels[nm] = entry
 
+    # the ParIS flat scan against MESSI's pruned, ordered search, same queries and index
+    ablation = ablation_leg(a, X, Qd, pkg, torch, stream)
+
     # batched queries: the plain FP32 path against the tensor-core (BF16) filter
     batch_info = batch_leg(a, X, pkg, torch, stream, rank) if a.batch > 0 else None
 
@@ -682,6 +725,7 @@ def main():
         "index": {"leaves": info["leaves"], "max_leaf": info["max_leaf"]},
         "pruning": {key + "_per_query": stats_acc[key] / max(1, len(lat_ms)) for key in stats_acc},
         "batch": batch_info,
+        "ablation_flat_scan": ablation,
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": clock_info,

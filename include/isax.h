@@ -205,6 +205,18 @@ isax_status isax_query_knn_noalloc(const isax_index* ix, const float* q, int32_t
                                    uint32_t mem_flags, int64_t* out_idx, float* out_dist,
                                    isax_query_stats* stats, void* cuda_stream);
 
+/*
+ * isax_query_knn_flat - the same exact k-NN query (same arguments, same
+ * answers) answered the ParIS way instead of MESSI's (Section III, ParIS+ query
+ * answering): after the approximate answer, the lower bound of EVERY series in
+ * the SAX array is computed, in storage order, and the series it does not prune
+ * are refined; no leaf is pruned by its envelope and leaves are not visited in
+ * bound order.  Kept to measure what MESSI's leaf pruning and ordering buy.
+ */
+isax_status isax_query_knn_flat(const isax_index* ix, const float* q, int32_t k, uint32_t mem_flags,
+                                int64_t* out_idx, float* out_dist, isax_query_stats* stats,
+                                void* cuda_stream);
+
 /* ------------------------------------------------------------ BF16-filtered batch */
 
 /*

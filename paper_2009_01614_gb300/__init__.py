@@ -20,7 +20,7 @@ __all__ = [
     "isax_last_error", "isax_get_index_info", "isax_index_export", "isax_summarize",
     "isax_set_allocator", "isax_profile", "isax_profile_report", "isax_launch_count",
     "isax_query_knn_noalloc", "isax_tc_selftest", "isax_query_knn_batch_bf16",
-    "isax_prepare_bf16", "Server", "ServerParams", "ServerResult", "ServerInfo",
+    "isax_prepare_bf16", "isax_query_knn_flat", "Server", "ServerParams", "ServerResult", "ServerInfo",
     "isax_server_create", "isax_server_add_collection", "isax_server_submit", "isax_server_poll",
     "isax_server_get_info", "isax_server_clock", "isax_server_destroy",
 ]
@@ -149,6 +149,8 @@ def lib():
         L.isax_launch_count.restype = ctypes.c_uint64
         L.isax_tc_selftest.argtypes = [vp, vp, i32, vp, vp]
         L.isax_tc_selftest.restype = st
+        L.isax_query_knn_flat.argtypes = [vp, vp, i32, u32, vp, vp, ctypes.POINTER(QueryStats), vp]
+        L.isax_query_knn_flat.restype = st
         L.isax_query_knn_batch_bf16.argtypes = [vp, vp, i32, i32, u32, vp, vp,
                                                 ctypes.POINTER(QueryStats), vp]
         L.isax_query_knn_batch_bf16.restype = st
@@ -208,6 +210,11 @@ def isax_query_knn_batch(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_pt
                          stream=0):
     _check(lib().isax_query_knn_batch(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_ptr,
                                       stats, stream))
+
+
+def isax_query_knn_flat(index, q_ptr, k, mem_flags, out_idx_ptr, out_dist_ptr, stats=None, stream=0):
+    _check(lib().isax_query_knn_flat(index, q_ptr, k, mem_flags, out_idx_ptr, out_dist_ptr, stats,
+                                     stream))
 
 
 def isax_query_knn_batch_bf16(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_ptr, stats=None,
@@ -385,6 +392,10 @@ class Index:
     def query_batch(self, Q, k=1, stats=False, stream=None):
         return self._run(Q, k, stats, stream, batch=True)
 
+    def query_flat(self, q, k=1, stats=False, stream=None):
+        """Same answer as query, by the ParIS flat scan (every series bounded)."""
+        return self._run(q, k, stats, stream, batch=False, flat=True)
+
     def query_batch_bf16(self, Q, k=1, stats=False, stream=None):
         """Same answers as query_batch, through the tensor-core (BF16) filter."""
         return self._run(Q, k, stats, stream, batch="bf16")
@@ -393,7 +404,7 @@ class Index:
         """Build the BF16 copy of the collection used by query_batch_bf16."""
         isax_prepare_bf16(self._h, _stream_of(None, stream))
 
-    def _run(self, q, k, want_stats, stream, batch):
+    def _run(self, q, k, want_stats, stream, batch, flat=False):
         ptr, on_dev, keep, shape = _buffer(q)
         B = shape[0] if batch else 1
         if (batch and (len(shape) != 2 or shape[1] != self.n)) or (not batch and shape[-1] != self.n):
@@ -410,7 +421,9 @@ class Index:
             dist = np.empty((B, k), np.float32)
             ip, dp, flags = idx.ctypes.data, dist.ctypes.data, 0
         stats = (QueryStats * B)()
-        if batch == "bf16":
+        if flat:
+            isax_query_knn_flat(self._h, ptr, k, flags, ip, dp, stats[0], st)
+        elif batch == "bf16":
             isax_query_knn_batch_bf16(self._h, ptr, B, k, flags, ip, dp, stats, st)
         elif batch:
             isax_query_knn_batch(self._h, ptr, B, k, flags, ip, dp, stats, st)

@@ -132,10 +132,10 @@ static void fill_stats(isax_query_stats* st, const isax_index* ix, const QCtl& c
 
 // one query whose input already sits in ix->qs.q; copies the results out
 static void run_one(isax_index* ix, int32_t k, uint32_t mem_flags, int64_t* out_idx,
-                    float* out_dist, isax_query_stats* stats, cudaStream_t st) {
+                    float* out_dist, isax_query_stats* stats, cudaStream_t st, int mode = QUERY_MESSI) {
     QCtl c;
     int reruns = 0;
-    query_device(ix, k, &c, &reruns, st);
+    query_device(ix, k, &c, &reruns, st, mode);
     const cudaMemcpyKind kind = (mem_flags & ISAX_MEM_OUTPUT_DEVICE) ? cudaMemcpyDeviceToDevice
                                                                      : cudaMemcpyDeviceToHost;
     ISAX_CUDA_TRY(cudaMemcpyAsync(out_idx, ix->qs.out_idx, sizeof(int64_t) * k, kind, st));
@@ -147,6 +147,26 @@ static void run_one(isax_index* ix, int32_t k, uint32_t mem_flags, int64_t* out_
 }  // namespace isax
 
 using namespace isax;
+
+static isax_status query_knn_mode(const isax_index* cix, const float* q, int32_t k, uint32_t mem_flags,
+                           int64_t* out_idx, float* out_dist, isax_query_stats* stats,
+                           void* cuda_stream, int mode) {
+    return guarded([&] {
+        check(cix != nullptr, "index is NULL");
+        check(q != nullptr && out_idx != nullptr && out_dist != nullptr, "NULL query or output");
+        check((mem_flags & ~(uint32_t)(ISAX_MEM_INPUT_DEVICE | ISAX_MEM_OUTPUT_DEVICE)) == 0,
+              "unknown mem_flags bits");
+        check(k >= 1 && k <= ISAX_MAX_K && (int64_t)k <= cix->d.N, "k must be in [1, min(N, 1024)]");
+        isax_index* ix = const_cast<isax_index*>(cix);
+        DeviceGuard dg(ix->device);
+        std::lock_guard<std::mutex> lk(*static_cast<std::mutex*>(ix->mu));
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        const cudaMemcpyKind kin = (mem_flags & ISAX_MEM_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                                       : cudaMemcpyHostToDevice;
+        ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, q, sizeof(float) * ix->d.n, kin, st));
+        run_one(ix, k, mem_flags, out_idx, out_dist, stats, st, mode);
+    });
+}
 
 extern "C" {
 
@@ -181,21 +201,13 @@ isax_status isax_build_index(const float* series, int64_t N, int32_t n, const is
 isax_status isax_query_knn(const isax_index* cix, const float* q, int32_t k, uint32_t mem_flags,
                            int64_t* out_idx, float* out_dist, isax_query_stats* stats,
                            void* cuda_stream) {
-    return guarded([&] {
-        check(cix != nullptr, "index is NULL");
-        check(q != nullptr && out_idx != nullptr && out_dist != nullptr, "NULL query or output");
-        check((mem_flags & ~(uint32_t)(ISAX_MEM_INPUT_DEVICE | ISAX_MEM_OUTPUT_DEVICE)) == 0,
-              "unknown mem_flags bits");
-        check(k >= 1 && k <= ISAX_MAX_K && (int64_t)k <= cix->d.N, "k must be in [1, min(N, 1024)]");
-        isax_index* ix = const_cast<isax_index*>(cix);
-        DeviceGuard dg(ix->device);
-        std::lock_guard<std::mutex> lk(*static_cast<std::mutex*>(ix->mu));
-        cudaStream_t st = (cudaStream_t)cuda_stream;
-        const cudaMemcpyKind kin = (mem_flags & ISAX_MEM_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice
-                                                                       : cudaMemcpyHostToDevice;
-        ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, q, sizeof(float) * ix->d.n, kin, st));
-        run_one(ix, k, mem_flags, out_idx, out_dist, stats, st);
-    });
+    return query_knn_mode(cix, q, k, mem_flags, out_idx, out_dist, stats, cuda_stream, QUERY_MESSI);
+}
+
+isax_status isax_query_knn_flat(const isax_index* cix, const float* q, int32_t k, uint32_t mem_flags,
+                                int64_t* out_idx, float* out_dist, isax_query_stats* stats,
+                                void* cuda_stream) {
+    return query_knn_mode(cix, q, k, mem_flags, out_idx, out_dist, stats, cuda_stream, QUERY_FLAT);
 }
 
 isax_status isax_query_knn_batch(const isax_index* cix, const float* Q, int32_t B, int32_t k,

@@ -129,13 +129,18 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
                              uint32_t mem_flags, cudaStream_t st);
 void summarize_impl(const float* series, int64_t N, int n, int card, uint32_t mem_flags,
                     uint8_t* out_sax, float* out_paa, cudaStream_t st);
-void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st);
+// query strategies: MESSI (leaf pruning, leaves in bound order) and the ParIS
+// flat scan (every series of the SAX array bounded, storage order)
+enum : int { QUERY_MESSI = 0, QUERY_FLAT = 1 };
+void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st,
+                  int mode = QUERY_MESSI);
 typedef void (*isax_query_stats_fill)(void* ctx, int b, const QCtl& c, int reruns);
 void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags,
                         int64_t* out_idx, float* out_dist, isax_query_stats_fill fill,
                         void* fill_ctx, cudaStream_t st);
 void free_index_arrays(isax_index* ix, cudaStream_t st);
-void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st);
+void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st,
+                             int mode = QUERY_MESSI);
 void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st);
 void launch_breakpoints(int card, float* bp, cudaStream_t st);
 // batched query kernels (query b of the batch owns scratch ss[b])

@@ -439,6 +439,33 @@ __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, Quer
     }
 }
 
+// ---------------------------------------------------------------- q_flat_list
+// The ParIS way of answering (Section III, ParIS+ query answering: the lower
+// bound of every series in the SAX array, then the real distance of those it
+// does not prune): every leaf goes on the work list, in storage order, with
+// bound 0 and all in the first bin, so the scan bounds every series and never
+// stops early nor skips a leaf.  The approximate-answer leaves stay out.
+__global__ void __launch_bounds__(256) q_flat_list_kernel(DevIndex ix, QueryScratch s) {
+    QCtl* c = s.ctl;
+    if (c->flags & QF_NONFINITE) return;
+    const int64_t a0 = c->approx_leaf, a1 = c->approx_end;
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < ix.L;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        s.leaf_lb[l] = 0.0f;
+        if (l < a0)
+            s.work[l] = (uint32_t)l;
+        else if (l >= a1)
+            s.work[l - (a1 - a0)] = (uint32_t)l;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t cnt = (uint32_t)(ix.L - (a1 - a0));
+        s.bin_count[0] = cnt;
+        c->work_count = cnt;
+        c->leaves_queued = cnt;
+        c->thr_lb0 = 0.0f;  // no bin-order stop
+    }
+}
+
 // ---------------------------------------------------------------- q_scan_refine
 constexpr int SR_THREADS = 256;                   // 8 warps: one 256-series chunk each per round
 constexpr int SR_WORDS = SCAN_UNIT / 32;          // SAX words per lane per round
@@ -1185,7 +1212,7 @@ int occupancy_grid(const void* fn, int threads, size_t smem, int num_sms) {
 }
 
 template <int NV>
-void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st) {
+void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st, int mode) {
     const DevIndex& d = ix->d;
     const size_t tab_bytes = sizeof(float) * W * d.card;
     {
@@ -1198,13 +1225,18 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
         q_approx_kernel<NV><<<approx_blocks, 256, 0, st>>>(d, s, k);
     }
     const unsigned lb_blocks = (unsigned)std::min<int64_t>((d.L + 255) / 256, (int64_t)ix->num_sms * 8);
-    {
-        ISAX_LAUNCH("q_leaf_lb", st);
-        q_leaf_lb_kernel<<<lb_blocks, 256, 0, st>>>(d, s, k);
-    }
-    {
-        ISAX_LAUNCH("q_leaf_scatter", st);
-        q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
+    if (mode == QUERY_FLAT) {
+        ISAX_LAUNCH("q_flat_list", st);
+        q_flat_list_kernel<<<lb_blocks, 256, 0, st>>>(d, s);
+    } else {
+        {
+            ISAX_LAUNCH("q_leaf_lb", st);
+            q_leaf_lb_kernel<<<lb_blocks, 256, 0, st>>>(d, s, k);
+        }
+        {
+            ISAX_LAUNCH("q_leaf_scatter", st);
+            q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
+        }
     }
     if (SR_WAVE0 > 0) {
         // the lowest-bound leaves first, one CTA each, so the k-th best tightens
@@ -1231,18 +1263,18 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
 
 // The query's kernels on the given scratch (the index's own, or the
 // allocation-free entry point's built-in array).
-void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st) {
+void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st, int mode) {
     const int n = ix->d.n;
     if (n % 128 == 0) {
         switch (n / 128) {
-            case 1: return launch_query_kernels<1>(ix, s, k, st);
-            case 2: return launch_query_kernels<2>(ix, s, k, st);
-            case 4: return launch_query_kernels<4>(ix, s, k, st);
-            case 8: return launch_query_kernels<8>(ix, s, k, st);
+            case 1: return launch_query_kernels<1>(ix, s, k, st, mode);
+            case 2: return launch_query_kernels<2>(ix, s, k, st, mode);
+            case 4: return launch_query_kernels<4>(ix, s, k, st, mode);
+            case 8: return launch_query_kernels<8>(ix, s, k, st, mode);
             default: break;
         }
     }
-    launch_query_kernels<0>(ix, s, k, st);
+    launch_query_kernels<0>(ix, s, k, st, mode);
 }
 
 // One exact k-NN query; q is already in ix->qs.q.  Results land in
@@ -1250,18 +1282,19 @@ void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaS
 // launch the query's kernels on st: replay of a captured graph, or direct
 // launches while per-kernel tracing is on
 static void launch_query_graph(isax_index* ix, const QueryScratch& qs, QueryGraphs* g, int k,
-                               cudaStream_t st) {
+                               cudaStream_t st, int mode = QUERY_MESSI) {
     if (profiling_on()) {
-        launch_query_on_scratch(ix, qs, k, st);
+        launch_query_on_scratch(ix, qs, k, st, mode);
         return;
     }
-    auto it = g->exec.find(k);
+    const int key = k | (mode << 16);
+    auto it = g->exec.find(key);
     if (it == g->exec.end()) {
         if (!g->capture) ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking));
         ISAX_CUDA_TRY(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
         cudaGraph_t graph = nullptr;
         try {
-            launch_query_on_scratch(ix, qs, k, g->capture);
+            launch_query_on_scratch(ix, qs, k, g->capture, mode);
         } catch (...) {
             cudaStreamEndCapture(g->capture, &graph);
             if (graph) cudaGraphDestroy(graph);
@@ -1276,7 +1309,7 @@ static void launch_query_graph(isax_index* ix, const QueryScratch& qs, QueryGrap
         cudaGraphDestroy(graph);
         ISAX_CUDA_TRY(e);
         if (g->exec.size() >= 8) g->clear();
-        it = g->exec.emplace(k, exec).first;
+        it = g->exec.emplace(key, exec).first;
     }
     ISAX_CUDA_TRY(cudaGraphLaunch(it->second, st));
     count_launches(g->kernels_per_query);
@@ -1290,15 +1323,15 @@ void launch_query_graph_ext(isax_index* ix, const QueryScratch& qs, void* g, int
     launch_query_graph(ix, qs, static_cast<QueryGraphs*>(g), k, st);
 }
 
-static void launch_query_index(isax_index* ix, int k, cudaStream_t st) {
+static void launch_query_index(isax_index* ix, int k, cudaStream_t st, int mode) {
     if (!ix->graphs) ix->graphs = new QueryGraphs();
-    launch_query_graph(ix, ix->qs, static_cast<QueryGraphs*>(ix->graphs), k, st);
+    launch_query_graph(ix, ix->qs, static_cast<QueryGraphs*>(ix->graphs), k, st, mode);
 }
 
-void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st) {
+void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st, int mode) {
     *reruns = 0;
     for (int attempt = 0;; ++attempt) {
-        launch_query_index(ix, k, st);
+        launch_query_index(ix, k, st, mode);
         ISAX_CUDA_TRY(cudaMemcpyAsync(ctl_out, ix->qs.ctl, sizeof(QCtl), cudaMemcpyDeviceToHost, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         if (ctl_out->flags & QF_NONFINITE) throw Error{ISAX_ERR_INVALID_ARG, "query contains a non-finite value"};

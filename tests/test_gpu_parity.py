@@ -314,3 +314,26 @@ def test_candidate_overflow_rerun():
     i, d, st = ix.query(torch.zeros(n, device="cuda"), 3, stats=True)
     assert i.cpu().tolist() == [0, 1, 2] and d.cpu().tolist() == [0.0, 0.0, 0.0]
     assert st["reruns"] >= 1
+
+
+@pytest.mark.parametrize("kind,k", [("walk", 1), ("walk", 10), ("sine", 5)])
+def test_flat_scan_equals_messi_and_oracle(kind, k):
+    """The ParIS-style flat scan bounds every series outside the approximate
+    answer and returns the same answer as MESSI's pruned, ordered search."""
+    N, n = 60_000, 256
+    X = datagen.rows(kind, 31, 0, N, n)
+    Q, _ = datagen.queries(kind, 31, N, n, 32, 12, 8, 0.1)
+    ix = pkg.Index(torch.from_numpy(X).cuda(), leaf_size=500)
+    L = ix.info()["leaves"]
+    got_i, got_d = [], []
+    for q in Q:
+        i1, d1, s1 = ix.query(q, k, stats=True)
+        i2, d2, s2 = ix.query_flat(q, k, stats=True)
+        np.testing.assert_array_equal(i2, i1)
+        np.testing.assert_array_equal(d2, d1)
+        assert s2["series_lb"] == N - s2["approx_series"]
+        assert s2["leaves_queued"] == s2["leaves_scanned"] <= L
+        assert s2["series_lb"] >= s1["series_lb"]
+        got_i.append(i2)
+        got_d.append(d2)
+    check_knn(np.array(got_i), np.array(got_d), X, Q, k)
