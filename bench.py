@@ -62,6 +62,8 @@ def parse():
                          "80M x 128, 10M x 1024)")
     ap.add_argument("--serve-requests", type=int, default=3000,
                     help="serving workload: requests per arrival rate")
+    ap.add_argument("--no-host-rows", action="store_true",
+                    help="skip the leg with the index's rows in host memory")
     ap.add_argument("--workload", choices=["walk", "hardness", "serving"], default="walk",
                     help="hardness: the sinusoid collection, member queries by noise level and k")
     ap.add_argument("--batch", type=int, default=1024,
@@ -242,6 +244,43 @@ def ablation_leg(a, X, Qd, pkg, torch, stream):
     out["messi_speedup"] = out["flat"]["latency_ms"]["p50"] / out["messi"]["latency_ms"]["p50"]
     ix.close()
     return out
+
+
+# ------------------------------------------------------------------ rows in host memory
+def host_rows_leg(a, X, Qd, pkg, torch, stream):
+    """The step's queries on an index whose leaf-ordered rows live in pinned
+    host memory (ISAX_BUILD_ROWS_HOST): bounds from the SAX words in HBM, rows
+    refined over the CPU-GPU link.  Same answers as with the rows in HBM."""
+    import numpy as np
+    sp = stream.cuda_stream
+    ref = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp)
+    want = [ref.query(Qd[b], a.k, stream=sp) for b in range(len(Qd))]
+    ref.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp, rows_on_host=True)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    ix.query(Qd[0], a.k, stream=sp)
+    lat, rows_read, same = [], [], True
+    for b in range(len(Qd)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        i, d, st = ix.query(Qd[b], a.k, stats=True, stream=sp)
+        e1.record(stream)
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+        rows_read.append(st["series_refined"])
+        same &= bool(torch.equal(i, want[b][0]) and torch.equal(d, want[b][1]))
+    info = ix.info()
+    ix.close()
+    return {"build_s_incl_pinning": build_s, "device_bytes": info["device_bytes"],
+            "host_bytes": a.N * a.n * 4,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "queries_per_s": len(lat) / (sum(lat) / 1e3),
+            "rows_refined_per_query": float(np.mean(rows_read)),
+            "same_answers_as_rows_in_hbm": same}
 
 
 # ------------------------------------------------------------------ batched leg
@@ -702,6 +741,9 @@ def main():
     # the ParIS flat scan against MESSI's pruned, ordered search, same queries and index
     ablation = ablation_leg(a, X, Qd, pkg, torch, stream)
 
+    # rows in host memory, read over the CPU-GPU link by the refinement
+    host_rows = None if a.no_host_rows else host_rows_leg(a, X, Qd, pkg, torch, stream)
+
     # batched queries: the plain FP32 path against the tensor-core (BF16) filter
     batch_info = batch_leg(a, X, pkg, torch, stream, rank) if a.batch > 0 else None
 
@@ -726,6 +768,7 @@ def main():
         "pruning": {key + "_per_query": stats_acc[key] / max(1, len(lat_ms)) for key in stats_acc},
         "batch": batch_info,
         "ablation_flat_scan": ablation,
+        "rows_in_host_memory": host_rows,
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": clock_info,

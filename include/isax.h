@@ -40,12 +40,20 @@ typedef enum isax_status {
 /* mem_flags bits */
 #define ISAX_MEM_INPUT_DEVICE 1u  /* input series / queries are device pointers */
 #define ISAX_MEM_OUTPUT_DEVICE 2u /* output arrays are device pointers */
+/* build only: after the build, keep the leaf-ordered series in pinned HOST memory
+ * and free their device copy; the SAX words, ids, leaf boundaries and envelopes
+ * stay in device memory.  Queries then compute every lower bound on the GPU and
+ * read the rows they refine over the CPU-GPU link (the paper's sketch of a GPU
+ * design with the raw data in host memory, Section V).  The build itself still
+ * stages the rows in device memory. */
+#define ISAX_BUILD_ROWS_HOST 4u
 
 typedef struct isax_build_params {
     int32_t w;           /* segments; must be ISAX_W (16) */
     int32_t cardinality; /* symbols per segment: power of two in [2, 256] (256 = 8-bit SAX) */
     int32_t leaf_size;   /* leaf capacity, >= 1 (runs of identical keys are cut into pieces of this size) */
-    uint32_t mem_flags;  /* ISAX_MEM_INPUT_DEVICE if `series` is a device pointer */
+    uint32_t mem_flags;  /* ISAX_MEM_INPUT_DEVICE if `series` is a device pointer;
+                            ISAX_BUILD_ROWS_HOST to keep the rows in host memory */
 } isax_build_params;
 
 typedef struct isax_query_stats {

@@ -26,6 +26,7 @@ __all__ = [
 ]
 
 W = 16
+BUILD_ROWS_HOST = 4
 MAX_K = 1024
 MAX_LEN = 4096
 MEM_INPUT_DEVICE = 1
@@ -341,14 +342,17 @@ class Index:
     """An iSAX index resident in device memory.
 
     ``Index(series, cardinality=256, leaf_size=2000)`` builds from a float32
-    [N, n] numpy array (host) or torch tensor (host or CUDA)."""
+    [N, n] numpy array (host) or torch tensor (host or CUDA).  With
+    ``rows_on_host=True`` the leaf-ordered rows live in pinned host memory after
+    the build (ISAX_BUILD_ROWS_HOST)."""
 
-    def __init__(self, series, cardinality=256, leaf_size=2000, stream=None):
+    def __init__(self, series, cardinality=256, leaf_size=2000, stream=None, rows_on_host=False):
         ptr, on_dev, keep, shape = _buffer(series)
         if len(shape) != 2:
             raise ValueError("series must be 2-D [N, n]")
         N, n = shape
-        p = BuildParams(W, cardinality, leaf_size, MEM_INPUT_DEVICE if on_dev else 0)
+        flags = (MEM_INPUT_DEVICE if on_dev else 0) | (BUILD_ROWS_HOST if rows_on_host else 0)
+        p = BuildParams(W, cardinality, leaf_size, flags)
         self._h = None
         self._h = isax_build_index(ptr, N, n, p, _stream_of(keep, stream))
         self.N, self.n = N, n

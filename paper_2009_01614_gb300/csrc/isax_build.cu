@@ -985,6 +985,23 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         ix->max_leaf = (int32_t)hm[2];
         ix->bytes = (int64_t)N * n * 4 + N * 16 + N * 4 + ((int64_t)L + 1) * 4 + (int64_t)L * 40 +
                     (card + 1) * 4;
+        if (mem_flags & ISAX_BUILD_ROWS_HOST) {
+            // the rows move to pinned host memory, read by the query kernels over the
+            // CPU-GPU link (unified addressing: the host pointer is valid on the device)
+            float* xh = nullptr;
+            ISAX_CUDA_TRY(cudaMallocHost((void**)&xh, (size_t)N * n * sizeof(float)));
+            cudaError_t e = cudaMemcpyAsync(xh, ix->x, (size_t)N * n * sizeof(float), cudaMemcpyDefault, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                cudaFreeHost(xh);
+                ISAX_CUDA_TRY(e);
+            }
+            dev_free(ix->x, st);
+            ix->x = xh;
+            ix->rows_host = true;
+            d.x = xh;
+            ix->bytes -= (int64_t)N * n * 4;
+        }
         alloc_query_scratch(ix, (uint32_t)std::min<int64_t>(N, 1 << 20), st);
     } catch (...) {
         free_index_arrays(ix, st);

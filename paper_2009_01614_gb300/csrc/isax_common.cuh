@@ -197,4 +197,5 @@ struct isax_index {
     void* graphs;  // captured query launch sequences (isax_query.cu)
     void* pool;    // extra query slots for concurrent batches (isax_query.cu)
     void* tc;      // BF16 copy and batch scratch of the tensor-core filter (isax_tc.cu)
+    bool rows_host;  // x is pinned host memory (ISAX_BUILD_ROWS_HOST)
 };

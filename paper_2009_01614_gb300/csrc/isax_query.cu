@@ -1189,6 +1189,11 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
     free_slot_pool(ix, st);
     free_tc_state(ix, st);
     free_query_scratch(ix, st);
+    if (ix->rows_host && ix->x) {
+        cudaStreamSynchronize(st);
+        cudaFreeHost(ix->x);
+        ix->x = nullptr;
+    }
     void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp};
     for (void* p : ptrs)
         if (p) dev_free(p, st);

@@ -337,3 +337,27 @@ def test_flat_scan_equals_messi_and_oracle(kind, k):
         got_i.append(i2)
         got_d.append(d2)
     check_knn(np.array(got_i), np.array(got_d), X, Q, k)
+
+
+def test_rows_on_host_give_the_same_answers():
+    """Rows kept in pinned host memory (read over the CPU-GPU link) give the
+    same answers on every query path as rows in device memory."""
+    N, n = 40_000, 256
+    X = datagen.rows("walk", 33, 0, N, n)
+    Q, _ = datagen.queries("walk", 33, N, n, 34, 10, 6, 0.05)
+    a = pkg.Index(torch.from_numpy(X).cuda(), leaf_size=400)
+    b = pkg.Index(torch.from_numpy(X).cuda(), leaf_size=400, rows_on_host=True)
+    assert b.info()["device_bytes"] < a.info()["device_bytes"] - N * n * 4 + 1
+    for k in (1, 10):
+        i1, d1 = a.query_batch(Q, k)
+        i2, d2 = b.query_batch(Q, k)
+        np.testing.assert_array_equal(i2, i1)
+        np.testing.assert_array_equal(d2, d1)
+        i3, d3 = b.query_batch_bf16(Q, k)
+        np.testing.assert_array_equal(i3, i1)
+        np.testing.assert_array_equal(d3, d1)
+        i4, d4 = b.query_flat(Q[0], k)
+        np.testing.assert_array_equal(i4, i1[0])
+        check_knn(i2, d2, X, Q, k)
+    b.close()
+    a.close()
