@@ -180,15 +180,27 @@ def kernel_bytes(name, a, launches, acc):
 
 
 def kernel_source_hash(kernel):
-    """Hash of the sources a kernel is compiled from: the file that defines it
-    (q_* kernels: isax_query.cu, tc_*: isax_tc.cu, the rest: isax_build.cu) and
-    the shared device-helper header (the host declarations header is left out)."""
+    """Hash of what a kernel is compiled from: the text of its __global__
+    definition (`<kernel>_kernel` in the file that defines it: q_* and bq_* in
+    isax_query.cu, tc_* in isax_tc.cu, the rest in isax_build.cu) and the shared
+    device-helper header."""
+    import re
     src = os.path.join(ROOT, "paper_2009_01614_gb300", "csrc")
     own = ("isax_query.cu" if kernel.startswith(("q_", "bq_")) else
            "isax_tc.cu" if kernel.startswith("tc_") else "isax_build.cu")
-    h = hashlib.sha256()
-    for f in (own, "isax_kernels_util.cuh"):
-        h.update(open(os.path.join(src, f), "rb").read())
+    text = open(os.path.join(src, own)).read()
+    m = re.search(r"__global__[^;{]*?\b%s_kernel\s*\(" % re.escape(kernel), text)
+    body = ""
+    if m:
+        i = text.index("{", m.end())
+        depth = 0
+        for j in range(i, len(text)):
+            depth += {"{": 1, "}": -1}.get(text[j], 0)
+            if depth == 0:
+                body = text[m.start():j + 1]
+                break
+    h = hashlib.sha256(body.encode())
+    h.update(open(os.path.join(src, "isax_kernels_util.cuh"), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -729,6 +729,32 @@ __global__ void __launch_bounds__(PM_THREADS) permute_kernel(const float* __rest
     }
 }
 
+// The same gather with plain 16-byte loads and stores, one warp per row, for
+// an index whose rows live in host memory: the output (and the input, when it
+// is host memory) is reached over the CPU-GPU link, where many independent
+// small requests in flight keep the link busy.
+__global__ void __launch_bounds__(256) permute_plain_kernel(const float* __restrict__ x, int n,
+                                                           const uint32_t* __restrict__ ids, int64_t N,
+                                                           float* __restrict__ xp,
+                                                           const uint4* __restrict__ sax_in,
+                                                           uint4* __restrict__ sax_out,
+                                                           uint32_t* __restrict__ orig) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nv = n / 4;
+    for (int64_t r = gw; r < N; r += nw) {
+        const uint32_t src = ids[r];
+        const float4* s4 = reinterpret_cast<const float4*>(x + (int64_t)src * n);
+        float4* d4 = reinterpret_cast<float4*>(xp + r * n);
+        for (int i = lane; i < nv; i += 32) d4[i] = s4[i];
+        if (lane == 0) {
+            sax_out[r] = sax_in[src];
+            orig[r] = src;
+        }
+    }
+}
+
 __device__ __forceinline__ uint4 vmin4(uint4 a, uint4 b) {
     return make_uint4(__vminu4(a.x, b.x), __vminu4(a.y, b.y), __vminu4(a.z, b.z), __vminu4(a.w, b.w));
 }
@@ -819,6 +845,18 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
     ix->device = dev;
     ix->num_sms = num_sms;
     ix->mu = new std::mutex();
+    // a host buffer this build page-locked, unlocked again when the build ends
+    struct HostReg {
+        void* p = nullptr;
+        cudaStream_t st = nullptr;
+        ~HostReg() {
+            if (p) {
+                cudaStreamSynchronize(st);
+                cudaHostUnregister(p);
+            }
+        }
+    } host_reg;
+    host_reg.st = st;
     try {
         int cbits = 0;
         while ((1 << cbits) < card) ++cbits;
@@ -826,11 +864,28 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         TempPool tmp{st, {}};
 
         const float* xin = series;
+        const bool rows_host = (mem_flags & ISAX_BUILD_ROWS_HOST) != 0;
         if (!(mem_flags & ISAX_MEM_INPUT_DEVICE)) {
-            float* xd = tmp.get<float>((size_t)N * n);
-            ISAX_CUDA_TRY(cudaMemcpyAsync(xd, series, (size_t)N * n * sizeof(float),
-                                          cudaMemcpyHostToDevice, st));
-            xin = xd;
+            if (rows_host) {
+                // read in place over the CPU-GPU link: page-lock it for the build if the
+                // caller has not (nothing of the collection is staged in device memory)
+                cudaPointerAttributes at{};
+                cudaError_t e = cudaPointerGetAttributes(&at, series);
+                if (e != cudaSuccess) cudaGetLastError();
+                if (e != cudaSuccess || at.type == cudaMemoryTypeUnregistered) {
+                    ISAX_CUDA_TRY(cudaHostRegister(const_cast<float*>(series), (size_t)N * n * sizeof(float),
+                                                   cudaHostRegisterDefault));
+                    host_reg.p = const_cast<float*>(series);
+                }
+                void* dp = nullptr;
+                ISAX_CUDA_TRY(cudaHostGetDevicePointer(&dp, const_cast<float*>(series), 0));
+                xin = static_cast<const float*>(dp);
+            } else {
+                float* xd = tmp.get<float>((size_t)N * n);
+                ISAX_CUDA_TRY(cudaMemcpyAsync(xd, series, (size_t)N * n * sizeof(float),
+                                              cudaMemcpyHostToDevice, st));
+                xin = xd;
+            }
         }
 
         // breakpoints + summaries
@@ -930,20 +985,30 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
             tmp.release(p);
 
         // permute rows and SAX words into leaf order
-        ix->x = static_cast<float*>(dev_alloc((size_t)N * n * sizeof(float), st));
         ix->sax = static_cast<uint4*>(dev_alloc((size_t)N * sizeof(uint4), st));
         ix->orig = static_cast<uint32_t*>(dev_alloc((size_t)N * sizeof(uint32_t), st));
-        {
-        const size_t pm_smem = (size_t)PM_STAGES * PM_STAGE_BYTES;
-        ISAX_CUDA_TRY(cudaFuncSetAttribute(permute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)pm_smem));
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, permute_kernel, PM_THREADS, pm_smem) !=
-                cudaSuccess || per_sm < 1)
-            per_sm = 1;
-        ISAX_LAUNCH("permute", st);
-        permute_kernel<<<num_sms * per_sm, PM_THREADS, pm_smem, st>>>(xin, n, vA, N, ix->x, sax_tmp,
-                                                                     ix->sax, ix->orig, misc + 3);
+        if (rows_host) {
+            // leaf-ordered rows in pinned host memory (unified addressing: the host
+            // pointer is valid on the device)
+            float* xh = nullptr;
+            ISAX_CUDA_TRY(cudaMallocHost((void**)&xh, (size_t)N * n * sizeof(float)));
+            ix->x = xh;
+            ix->rows_host = true;
+            ISAX_LAUNCH("permute_plain", st);
+            permute_plain_kernel<<<num_sms * 8, 256, 0, st>>>(xin, n, vA, N, ix->x, sax_tmp, ix->sax,
+                                                              ix->orig);
+        } else {
+            ix->x = static_cast<float*>(dev_alloc((size_t)N * n * sizeof(float), st));
+            const size_t pm_smem = (size_t)PM_STAGES * PM_STAGE_BYTES;
+            ISAX_CUDA_TRY(cudaFuncSetAttribute(permute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)pm_smem));
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, permute_kernel, PM_THREADS, pm_smem) !=
+                    cudaSuccess || per_sm < 1)
+                per_sm = 1;
+            ISAX_LAUNCH("permute", st);
+            permute_kernel<<<num_sms * per_sm, PM_THREADS, pm_smem, st>>>(xin, n, vA, N, ix->x, sax_tmp,
+                                                                         ix->sax, ix->orig, misc + 3);
         }
         ISAX_CUDA_TRY(cudaGetLastError());
 
@@ -985,23 +1050,7 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         ix->max_leaf = (int32_t)hm[2];
         ix->bytes = (int64_t)N * n * 4 + N * 16 + N * 4 + ((int64_t)L + 1) * 4 + (int64_t)L * 40 +
                     (card + 1) * 4;
-        if (mem_flags & ISAX_BUILD_ROWS_HOST) {
-            // the rows move to pinned host memory, read by the query kernels over the
-            // CPU-GPU link (unified addressing: the host pointer is valid on the device)
-            float* xh = nullptr;
-            ISAX_CUDA_TRY(cudaMallocHost((void**)&xh, (size_t)N * n * sizeof(float)));
-            cudaError_t e = cudaMemcpyAsync(xh, ix->x, (size_t)N * n * sizeof(float), cudaMemcpyDefault, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) {
-                cudaFreeHost(xh);
-                ISAX_CUDA_TRY(e);
-            }
-            dev_free(ix->x, st);
-            ix->x = xh;
-            ix->rows_host = true;
-            d.x = xh;
-            ix->bytes -= (int64_t)N * n * 4;
-        }
+        if (rows_host) ix->bytes -= (int64_t)N * n * 4;
         alloc_query_scratch(ix, (uint32_t)std::min<int64_t>(N, 1 << 20), st);
     } catch (...) {
         free_index_arrays(ix, st);

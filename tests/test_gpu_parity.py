@@ -348,6 +348,12 @@ def test_rows_on_host_give_the_same_answers():
     a = pkg.Index(torch.from_numpy(X).cuda(), leaf_size=400)
     b = pkg.Index(torch.from_numpy(X).cuda(), leaf_size=400, rows_on_host=True)
     assert b.info()["device_bytes"] < a.info()["device_bytes"] - N * n * 4 + 1
+    # built from host memory read in place (page-locked by the build), rows to host
+    c = pkg.Index(X, leaf_size=400, rows_on_host=True)
+    ea, eb = np.empty((a.info()["N"], 16), np.uint8), np.empty((a.info()["N"], 16), np.uint8)
+    pkg.isax_index_export(a._h, ea.ctypes.data)
+    pkg.isax_index_export(c._h, eb.ctypes.data)
+    np.testing.assert_array_equal(ea, eb)
     for k in (1, 10):
         i1, d1 = a.query_batch(Q, k)
         i2, d2 = b.query_batch(Q, k)
@@ -358,6 +364,10 @@ def test_rows_on_host_give_the_same_answers():
         np.testing.assert_array_equal(d3, d1)
         i4, d4 = b.query_flat(Q[0], k)
         np.testing.assert_array_equal(i4, i1[0])
+        i5, d5 = c.query_batch(Q, k)
+        np.testing.assert_array_equal(i5, i1)
+        np.testing.assert_array_equal(d5, d1)
         check_knn(i2, d2, X, Q, k)
+    c.close()
     b.close()
     a.close()
