@@ -184,7 +184,8 @@ isax_status isax_summarize(const float* series, int64_t N, int32_t n, int32_t ca
 
 #define ISAX_NOALLOC_MAX_LEAVES 524288u       /* largest index (in leaves) it serves */
 #define ISAX_NOALLOC_MAX_CANDIDATES 262144u   /* fp32 near-tie candidates it can hold */
-#define ISAX_NOALLOC_SCRATCH_BYTES 7395584u   /* its fixed device scratch (about 7 MiB) */
+#define ISAX_NOALLOC_MAX_SURVIVORS 1048576u   /* series passing the lower bound it can hold */
+#define ISAX_NOALLOC_SCRATCH_BYTES 17881344u  /* its fixed device scratch (about 17 MiB) */
 
 /*
  * isax_query_knn_noalloc - the same exact k-NN query as isax_query_knn (same
@@ -203,11 +204,13 @@ isax_status isax_summarize(const float* series, int64_t N, int32_t n, int32_t ca
  * their results are copied out, because two queries running at once on the GPU
  * would race on the shared array.
  * Limits and errors: ISAX_ERR_INVALID_ARG for an index with more than
- * ISAX_NOALLOC_MAX_LEAVES leaves (and as isax_query_knn); ISAX_ERR_OOM when
- * the query keeps more than ISAX_NOALLOC_MAX_CANDIDATES candidates for its final
- * FP64 ordering (refined series that were within fp32 error of the k-th best
- * when refined; isax_query_knn would rerun with a larger buffer, this entry
- * point cannot).  It calls no allocation routine.
+ * ISAX_NOALLOC_MAX_LEAVES leaves or with leaves + N / 256 above twice that
+ * (and as isax_query_knn); ISAX_ERR_OOM when
+ * more than ISAX_NOALLOC_MAX_SURVIVORS series pass the lower bound of the
+ * approximate answer, or the query keeps more than ISAX_NOALLOC_MAX_CANDIDATES
+ * candidates for its final FP64 ordering (refined series that were within fp32
+ * error of the k-th best when refined); isax_query_knn would rerun with larger
+ * buffers, this entry point cannot.  It calls no allocation routine.
  */
 isax_status isax_query_knn_noalloc(const isax_index* ix, const float* q, int32_t k,
                                    uint32_t mem_flags, int64_t* out_idx, float* out_dist,

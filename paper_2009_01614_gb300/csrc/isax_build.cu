@@ -832,7 +832,7 @@ inline unsigned grid_for(int64_t work, int per_block, int num_sms, int max_per_s
 }  // namespace
 
 void free_index_arrays(isax_index* ix, cudaStream_t st);
-void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st);
+void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, uint32_t surv_cap, cudaStream_t st);
 
 isax_index* build_index_impl(const float* series, int64_t N, int n, int card, int leaf_size,
                              uint32_t mem_flags, cudaStream_t st) {
@@ -1051,7 +1051,7 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         ix->bytes = (int64_t)N * n * 4 + N * 16 + N * 4 + ((int64_t)L + 1) * 4 + (int64_t)L * 40 +
                     (card + 1) * 4;
         if (rows_host) ix->bytes -= (int64_t)N * n * 4;
-        alloc_query_scratch(ix, (uint32_t)std::min<int64_t>(N, 1 << 20), st);
+        alloc_query_scratch(ix, (uint32_t)std::min<int64_t>(N, 1 << 20), default_surv_cap(N), st);
     } catch (...) {
         free_index_arrays(ix, st);
         delete static_cast<std::mutex*>(ix->mu);

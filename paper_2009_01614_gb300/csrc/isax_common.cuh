@@ -17,7 +17,6 @@ constexpr int MAX_LEN = ISAX_MAX_LEN;
 constexpr int ROOT_BITS = W;       // root key: first bit of each of the 16 segments
 
 constexpr int NBINS = 256;         // leaf ordering bins (lower bound / threshold)
-constexpr int SCAN_UNIT = 256;     // series of a leaf bounded by one warp per claim
 constexpr uint64_t EMPTY_SLOT = ~0ull;
 
 // ---------------------------------------------------------------- errors
@@ -86,6 +85,7 @@ struct QCtl {
     uint32_t work_next;    // Fetch&Inc claim counter of the first wave
     uint32_t work_next2;   // ... and of the second
     uint32_t cand_count;   // candidate appends attempted (may exceed capacity)
+    uint32_t surv_count;   // series whose bound passed (appended; may exceed capacity)
     uint32_t window;       // candidates re-ranked in FP64
     uint32_t flags;        // QF_* bits
     float thr_lb0;         // bound threshold the work list was binned with
@@ -106,13 +106,15 @@ struct QueryScratch {
     float* q;                      // [n]
     float* table;                  // [16][card] lower-bound table
     float* leaf_lb;                // [L]
-    uint32_t* work;                // [L] queued leaves, ordered by bin
+    uint32_t* work;                // [work_items_cap] scan items (leaf << 4 | chunk), ordered by bin
     uint32_t* bin_count;           // [NBINS]
     uint32_t* bin_cursor;          // [NBINS]
     unsigned long long* topk;      // [MAX_K] packed (fp32 d2 bits << 32 | orig)
     unsigned long long* cand_key;  // [cap]
     uint32_t* cand_pos;            // [cap]
     uint32_t cand_cap;
+    uint2* surv;                   // [surv_cap] series that passed the bound: {position, bound bits}
+    uint32_t surv_cap;
     QCtl* ctl;
     int64_t* out_idx;              // [MAX_K]
     float* out_dist;               // [MAX_K]
@@ -141,7 +143,8 @@ void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t m
 void free_index_arrays(isax_index* ix, cudaStream_t st);
 void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st,
                              int mode = QUERY_MESSI);
-void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st);
+void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, uint32_t surv_cap, cudaStream_t st);
+uint32_t default_surv_cap(int64_t N);  // survivor entries of a fresh query scratch
 void launch_breakpoints(int card, float* bp, cudaStream_t st);
 // batched query kernels (query b of the batch owns scratch ss[b])
 void launch_bq_prep(isax_index* ix, const QueryScratch* ss, int B, int k, int neighbors,
@@ -156,9 +159,11 @@ void launch_bq_recheck(isax_index* ix, const QueryScratch* ss, int k, const uint
                        const uint32_t* cand_count, uint32_t cap, cudaStream_t st);
 void launch_bq_finalize(isax_index* ix, const QueryScratch* ss, int B, int k, cudaStream_t st);
 // scratch and captured graphs for the resident query server (isax_serve.cu)
-void alloc_query_scratch_for(int64_t L, int n, int card, uint32_t cand_cap, QueryScratch& q,
-                             cudaStream_t st);
+int64_t work_items_cap(int64_t L, int64_t N);
+void alloc_query_scratch_for(int64_t L, int64_t N, int n, int card, uint32_t cand_cap, uint32_t surv_cap,
+                             QueryScratch& q, cudaStream_t st);
 void grow_query_candidates(QueryScratch& q, uint32_t cand_cap, cudaStream_t st);
+void grow_query_survivors(QueryScratch& q, uint32_t surv_cap, cudaStream_t st);
 void free_query_scratch_struct(QueryScratch& q, cudaStream_t st);
 void* query_graphs_new();
 void query_graphs_delete(void* g);

@@ -35,14 +35,16 @@ namespace {
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr uint32_t MAX_LEAVES = ISAX_NOALLOC_MAX_LEAVES;
+constexpr uint32_t MAX_WORK = 2 * MAX_LEAVES;  // scan items: leaves + series / 256
 constexpr uint32_t MAX_CAND = ISAX_NOALLOC_MAX_CANDIDATES;
+constexpr uint32_t MAX_SURV = ISAX_NOALLOC_MAX_SURVIVORS;
 
 // byte offsets of the scratch pieces inside the array
 constexpr size_t OFF_Q = 0;
 constexpr size_t OFF_TABLE = align256(OFF_Q + sizeof(float) * MAX_LEN);
 constexpr size_t OFF_LEAF_LB = align256(OFF_TABLE + sizeof(float) * W * MAX_CARD);
 constexpr size_t OFF_WORK = align256(OFF_LEAF_LB + sizeof(float) * MAX_LEAVES);
-constexpr size_t OFF_BIN_COUNT = align256(OFF_WORK + sizeof(uint32_t) * MAX_LEAVES);
+constexpr size_t OFF_BIN_COUNT = align256(OFF_WORK + sizeof(uint32_t) * MAX_WORK);
 constexpr size_t OFF_BIN_CURSOR = align256(OFF_BIN_COUNT + sizeof(uint32_t) * NBINS);
 constexpr size_t OFF_TOPK = align256(OFF_BIN_CURSOR + sizeof(uint32_t) * NBINS);
 constexpr size_t OFF_CAND_KEY = align256(OFF_TOPK + sizeof(unsigned long long) * MAX_K);
@@ -50,7 +52,8 @@ constexpr size_t OFF_CAND_POS = align256(OFF_CAND_KEY + sizeof(unsigned long lon
 constexpr size_t OFF_CTL = align256(OFF_CAND_POS + sizeof(uint32_t) * MAX_CAND);
 constexpr size_t OFF_OUT_IDX = align256(OFF_CTL + sizeof(QCtl));
 constexpr size_t OFF_OUT_DIST = align256(OFF_OUT_IDX + sizeof(int64_t) * MAX_K);
-constexpr size_t TOTAL = align256(OFF_OUT_DIST + sizeof(float) * MAX_K);
+constexpr size_t OFF_SURV = align256(OFF_OUT_DIST + sizeof(float) * MAX_K);
+constexpr size_t TOTAL = align256(OFF_SURV + sizeof(uint2) * MAX_SURV);
 static_assert(TOTAL == ISAX_NOALLOC_SCRATCH_BYTES, "scratch size must match isax.h");
 
 static __device__ __align__(256) unsigned char g_scratch[TOTAL];
@@ -87,6 +90,8 @@ QueryScratch scratch_view(unsigned char* base) {
     s.ctl = reinterpret_cast<QCtl*>(base + OFF_CTL);
     s.out_idx = reinterpret_cast<int64_t*>(base + OFF_OUT_IDX);
     s.out_dist = reinterpret_cast<float*>(base + OFF_OUT_DIST);
+    s.surv = reinterpret_cast<uint2*>(base + OFF_SURV);
+    s.surv_cap = MAX_SURV;
     return s;
 }
 
@@ -113,10 +118,12 @@ extern "C" isax_status isax_query_knn_noalloc(const isax_index* cix, const float
             fail(ISAX_ERR_INVALID_ARG, "unknown mem_flags bits");
         if (k < 1 || k > ISAX_MAX_K || (int64_t)k > cix->d.N)
             fail(ISAX_ERR_INVALID_ARG, "k must be in [1, min(N, 1024)]");
-        if (cix->d.L > (int64_t)MAX_LEAVES)
+        if (cix->d.L > (int64_t)MAX_LEAVES || work_items_cap(cix->d.L, cix->d.N) > (int64_t)MAX_WORK)
             fail(ISAX_ERR_INVALID_ARG,
-                 "index has " + std::to_string(cix->d.L) + " leaves; the allocation-free query "
-                 "supports at most " + std::to_string(MAX_LEAVES) + " (use isax_query_knn)");
+                 "index has " + std::to_string(cix->d.L) + " leaves and " + std::to_string(cix->d.N) +
+                 " series; the allocation-free query supports at most " + std::to_string(MAX_LEAVES) +
+                 " leaves and leaves + series / 256 <= " + std::to_string(MAX_WORK) +
+                 " (use isax_query_knn)");
         isax_index* ix = const_cast<isax_index*>(cix);
         std::lock_guard<std::mutex> lk(g_mu);
         if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
@@ -137,9 +144,12 @@ extern "C" isax_status isax_query_knn_noalloc(const isax_index* cix, const float
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         if (c.flags & QF_NONFINITE) fail(ISAX_ERR_INVALID_ARG, "query contains a non-finite value");
         if (c.flags & QF_OVERFLOW)
-            fail(ISAX_ERR_OOM, "the query kept more than " + std::to_string(MAX_CAND) +
-                 " candidates for its final FP64 ordering: the allocation-free scratch is too "
-                 "small for this query (use isax_query_knn)");
+            fail(ISAX_ERR_OOM, c.surv_count > MAX_SURV
+                 ? "more than " + std::to_string(MAX_SURV) + " series passed the lower bound: the "
+                   "allocation-free scratch is too small for this query (use isax_query_knn)"
+                 : "the query kept more than " + std::to_string(MAX_CAND) +
+                   " candidates for its final FP64 ordering: the allocation-free scratch is too "
+                   "small for this query (use isax_query_knn)");
         if (c.flags & QF_SHORT) fail(ISAX_ERR_INTERNAL, "fewer than k candidates survived");
         const cudaMemcpyKind kout = (mem_flags & ISAX_MEM_OUTPUT_DEVICE) ? cudaMemcpyDeviceToDevice
                                                                          : cudaMemcpyDeviceToHost;

@@ -10,12 +10,15 @@
 //                 not prune are counted into bins of bound / BSF.
 //   q_leaf_scatter  the unpruned leaves listed bin by bin: a work list in
 //                 ascending lower-bound order (MESSI's priority queues).
-//   q_scan_refine persistent CTAs claim leaves from the list with Fetch&Inc; a
-//                 claimed leaf whose bound now exceeds the BSF is skipped; else
-//                 16-byte SAX words are bounded against the table in shared
-//                 memory, survivors compacted with warp ballots, and refined
-//                 by one warp per row with early abandoning; the k best so far
-//                 live in a sorted array updated by an atomicMin cascade.
+//   q_series_lb   warps claim queued leaves in that order (Fetch&Inc) and
+//                 bound their 16-byte SAX words against the table in shared
+//                 memory (a conflict-free 32-region bound first, the full one
+//                 only for what it keeps); survivors {position, bound} are
+//                 appended in claim order with warp ballots.
+//   q_refine      warps take the survivors in that order, skip those whose
+//                 bound now exceeds the k-th best, and compute real distances
+//                 (early abandoning for long series); the k best so far live in
+//                 a sorted array updated by an atomicMin cascade.
 //   q_finalize    candidates within fp32 error of the k-th best re-ranked in
 //                 FP64 (ties by lower row), distances rounded to fp32.
 //
@@ -173,8 +176,30 @@ __device__ __forceinline__ void load_q(const float* q, float4 (&qv)[NV ? NV : 1]
         qv[p] = NV ? reinterpret_cast<const float4*>(q)[p * 32 + lane] : make_float4(0, 0, 0, 0);
 }
 
-// series lower bound: 16 table lookups summed in segment order
+// 8-bit symbols (card 256): each symbol is taken out of its word already scaled
+// to a byte offset (one shift and mask), and the segment's row offset folds
+// into the load's immediate
+__device__ __forceinline__ float series_lb_256(uint4 w, const float* __restrict__ tab) {
+    const char* t = reinterpret_cast<const char*>(tab);
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+    float lb = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t v = words[q];
+        lb += *reinterpret_cast<const float*>(t + (4 * q + 0) * 1024 + ((v << 2) & 0x3FCu));
+        lb += *reinterpret_cast<const float*>(t + (4 * q + 1) * 1024 + ((v >> 6) & 0x3FCu));
+        lb += *reinterpret_cast<const float*>(t + (4 * q + 2) * 1024 + ((v >> 14) & 0x3FCu));
+        lb += *reinterpret_cast<const float*>(t + (4 * q + 3) * 1024 + ((v >> 22) & 0x3FCu));
+    }
+    return lb;
+}
+
+// series lower bound: 16 table lookups summed in segment order (CARD > 0: the
+// row stride is a compile-time constant)
+template <int CARD = 0>
 __device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ tab, int card) {
+    if constexpr (CARD == 256) return series_lb_256(w, tab);
+    if constexpr (CARD > 0) card = CARD;
     float lb = 0.0f;
     const uint32_t words[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -183,6 +208,18 @@ __device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ ta
         lb += tab[i * card + s];
     }
     return lb;
+}
+
+// work items of the scan: a queued leaf is cut into chunks of lb_chunk series
+// (at least 256, at most 16 chunks per leaf), item = leaf << 4 | chunk
+__host__ __device__ __forceinline__ int lb_chunk(int leaf_size) {
+    const int c = ((leaf_size + 15) / 16 + 255) / 256 * 256;
+    return c > 256 ? c : 256;
+}
+__device__ __forceinline__ uint32_t leaf_chunks(const DevIndex& ix, int64_t l) {
+    const uint32_t size = ix.leaf_begin[l + 1] - ix.leaf_begin[l];
+    const uint32_t ch = (uint32_t)lb_chunk(ix.leaf_size);
+    return (size + ch - 1) / ch;
 }
 
 // ---------------------------------------------------------------- q_prep
@@ -238,6 +275,7 @@ __device__ __forceinline__ void q_prep_body(const DevIndex& ix, const QueryScrat
         const float d = v < lo ? lo - v : (v >= hi ? v - hi : 0.0f);
         s.table[e] = (d * d) * mf;
     }
+
     if (tid == 0) {
         unsigned long long key = 0;
         for (int pl = 0; pl < 4; ++pl) {
@@ -296,6 +334,7 @@ __device__ __forceinline__ void q_prep_body(const DevIndex& ix, const QueryScrat
         c->work_next = 0;
         c->work_next2 = 0;
         c->cand_count = 0;
+        c->surv_count = 0;
         c->window = 0;
         c->flags = bad ? QF_NONFINITE : 0u;
         c->thr_lb0 = INFINITY;
@@ -401,7 +440,7 @@ __global__ void __launch_bounds__(256) q_leaf_lb_kernel(DevIndex ix, QueryScratc
             }
         }
         s.leaf_lb[l] = lb;
-        if (!(l >= a0 && l < a1) && lb <= thr) atomicAdd(&hist[bin_of(lb, thr)], 1u);
+        if (!(l >= a0 && l < a1) && lb <= thr) atomicAdd(&hist[bin_of(lb, thr)], leaf_chunks(ix, l));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < NBINS; i += blockDim.x)
@@ -422,19 +461,25 @@ __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, Quer
     __syncthreads();
     const float thr = thr_s;
     const int64_t a0 = c->approx_leaf, a1 = c->approx_end;
+    uint32_t mine = 0;
     for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < ix.L;
          l += (int64_t)gridDim.x * blockDim.x) {
         if (l >= a0 && l < a1) continue;
         const float lb = s.leaf_lb[l];
         if (lb <= thr) {
             const int b = bin_of(lb, thr);
-            const uint32_t p = off[b] + atomicAdd(&s.bin_cursor[b], 1u);
-            if (p < tot) s.work[p] = (uint32_t)l;
+            const uint32_t nch = leaf_chunks(ix, l);
+            const uint32_t p = off[b] + atomicAdd(&s.bin_cursor[b], nch);
+            for (uint32_t ch = 0; ch < nch; ++ch)
+                if (p + ch < tot) s.work[p + ch] = ((uint32_t)l << 4) | ch;
+            ++mine;
         }
     }
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) mine += __shfl_xor_sync(FULL, mine, o2);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&c->leaves_queued, (unsigned long long)mine);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->work_count = tot;
-        c->leaves_queued = tot;
         c->thr_lb0 = thr;
     }
 }
@@ -448,29 +493,35 @@ __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, Quer
 __global__ void __launch_bounds__(256) q_flat_list_kernel(DevIndex ix, QueryScratch s) {
     QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
+    const int lane = threadIdx.x & 31;
     const int64_t a0 = c->approx_leaf, a1 = c->approx_end;
-    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < ix.L;
-         l += (int64_t)gridDim.x * blockDim.x) {
-        s.leaf_lb[l] = 0.0f;
-        if (l < a0)
-            s.work[l] = (uint32_t)l;
-        else if (l >= a1)
-            s.work[l - (a1 - a0)] = (uint32_t)l;
+    // a warp lists 32 consecutive leaves with one append
+    for (int64_t l0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; l0 < ix.L;
+         l0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = l0 + lane;
+        const bool take = l < ix.L && !(l >= a0 && l < a1);
+        const uint32_t nch = take ? leaf_chunks(ix, l) : 0u;
+        uint32_t incl = nch;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        const unsigned leaves = __popc(__ballot_sync(FULL, take));
+        uint32_t base = 0;
+        if (lane == 0 && total) {
+            base = atomicAdd(&c->work_count, total);
+            atomicAdd(&c->leaves_queued, (unsigned long long)leaves);
+        }
+        base = __shfl_sync(FULL, base, 0);
+        for (uint32_t ch = 0; ch < nch; ++ch) s.work[base + incl - nch + ch] = ((uint32_t)l << 4) | ch;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const uint32_t cnt = (uint32_t)(ix.L - (a1 - a0));
-        s.bin_count[0] = cnt;
-        c->work_count = cnt;
-        c->leaves_queued = cnt;
-        c->thr_lb0 = 0.0f;  // no bin-order stop
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->thr_lb0 = 0.0f;
 }
 
-// ---------------------------------------------------------------- q_scan_refine
-constexpr int SR_THREADS = 256;                   // 8 warps: one 256-series chunk each per round
-constexpr int SR_WORDS = SCAN_UNIT / 32;          // SAX words per lane per round
-constexpr int SR_BATCH = 8;                       // refined distances per k-best update
-constexpr uint32_t SR_WAVE0 = 0;                  // leaves of an optional narrow first wave
+// ---------------------------------------------------------------- refinement helpers
+constexpr int SR_BATCH = 8;  // refined distances per k-best update
 
 // squared distances of two rows (second one optional) with all loads issued first
 template <int NV>
@@ -502,56 +553,164 @@ __device__ __forceinline__ void warp_d2_two(const DevIndex& ix, int64_t r0, int6
     d1 = warp_sum_f(a1);
 }
 
-// Persistent CTAs claim queued leaves with Fetch&Inc (the list is in
-// ascending bound-bin order).  A claimed leaf whose bound now exceeds the
-// threshold is skipped; once the bin of the claimed position lies wholly above
-// the threshold the CTA stops (every later leaf is in a higher bin).  A leaf is
-// processed in rounds of up to 8 x 256 series: each warp bounds one 256-series
-// chunk (16-byte SAX words, all loads issued first, 16 table lookups each),
-// survivors go to a shared list, and all warps refine them two rows at a time,
-// handing each batch of distances to the k-best update after one filter
-// against the current k-th best.
-constexpr int SR_WARPS = SR_THREADS / 32;
-constexpr int SR_ROUND = SR_WARPS * SCAN_UNIT;    // series per leaf round
-
+// squared distances of up to four rows (keep mask, warp-uniform), every load
+// issued before any arithmetic; the same fp32 order as warp_d2_vec
 template <int NV>
-__global__ void __launch_bounds__(SR_THREADS, 4) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k,
-                                                                      int wave, uint32_t wave_items) {
+__device__ __forceinline__ void warp_d2_four(const DevIndex& ix, const uint2 (&e)[4], unsigned keep,
+                                             const float4 (&qv)[NV], float (&d)[4]) {
+    const int lane = threadIdx.x & 31;
+    float4 v[4][NV];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if (keep & (1u << t)) {
+            const float4* x = reinterpret_cast<const float4*>(ix.x + (int64_t)e[t].x * ix.n);
+#pragma unroll
+            for (int p = 0; p < NV; ++p) v[t][p] = ld_stream(x + p * 32 + lane);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        float a = 0.0f;
+        if (keep & (1u << t)) {
+#pragma unroll
+            for (int p = 0; p < NV; ++p) {
+                float dd;
+                dd = v[t][p].x - qv[p].x; a = fmaf(dd, dd, a);
+                dd = v[t][p].y - qv[p].y; a = fmaf(dd, dd, a);
+                dd = v[t][p].z - qv[p].z; a = fmaf(dd, dd, a);
+                dd = v[t][p].w - qv[p].w; a = fmaf(dd, dd, a);
+            }
+        }
+        d[t] = warp_sum_f(a);
+    }
+}
+
+// ---------------------------------------------------------------- q_series_lb
+// The lower-bound scan (MESSI's lower-bound calculations): warps take the
+// queued leaf chunks in work-list order (ascending leaf bound for MESSI,
+// storage order for the flat scan), item i to warp i mod W, stream the
+// chunk's 16-byte SAX words with
+// LB_WORDS loads per lane in flight, bound each from the table in shared memory
+// against the threshold the approximate answer set, and append the survivors
+// {position, bound} in claim order with one atomic per warp and word batch.
+constexpr int LB_THREADS = 256, LB_WORDS = 8;
+constexpr int LB_BUF = 64;     // survivors buffered per warp before one global append
+
+template <int CARD>
+__global__ void __launch_bounds__(LB_THREADS, 4) q_series_lb_kernel(DevIndex ix, QueryScratch s, int k) {
     extern __shared__ float tab[];
-    __shared__ uint32_t off[NBINS + 1];
-    __shared__ uint32_t scratch[32];
-    __shared__ uint16_t surv[SR_ROUND];
-    __shared__ int nsurv;
-    __shared__ uint32_t item_s, leaf_s, beg_s, end_s;
-    __shared__ float thr_s, lim_s, lb_s;
-    __shared__ unsigned long long kth_s;
+    __shared__ float thr_s;
+    __shared__ uint2 buf_s[LB_THREADS / 32][LB_BUF];
     QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
     const int card = ix.card;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < W * card; e += SR_THREADS) tab[e] = s.table[e];
-    {   // bin offsets: the exclusive scan the scatter kernel used (one bin per thread)
-        static_assert(NBINS == SR_THREADS, "one bin per thread");
-        uint32_t tot;
-        off[tid] = block_excl_scan<uint32_t>(s.bin_count[tid], 0u, OpAdd<uint32_t>(), scratch, &tot);
-        if (tid == 0) {
-            off[NBINS] = tot;
-            kth_s = 0;
+    {   // the table into shared memory: 16-byte loads, all issued before the stores
+        const float4* src = reinterpret_cast<const float4*>(s.table);
+        float4* dst = reinterpret_cast<float4*>(tab);
+        const int nv = W * card / 4;
+        float4 v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int e = threadIdx.x + t * LB_THREADS;
+            if (e < nv) v[t] = src[e];
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int e = threadIdx.x + t * LB_THREADS;
+            if (e < nv) dst[e] = v[t];
         }
     }
+    if (threadIdx.x == 0) thr_s = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), c->delta, c->E);
+    __syncthreads();
+    const float thr = thr_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int chunk = lb_chunk(ix.leaf_size);
+    uint2* buf = buf_s[warp];
+    int nbuf = 0;  // warp-uniform
+    // the buffered survivors go to the global list in one append
+    auto drain = [&]() {
+        if (nbuf == 0) return;
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&c->surv_count, (uint32_t)nbuf);
+        base = __shfl_sync(FULL, base, 0);
+        __syncwarp();
+        for (int t = lane; t < nbuf; t += 32)
+            if (base + t < s.surv_cap) s.surv[base + t] = buf[t];
+        __syncwarp();
+        nbuf = 0;
+    };
+    const uint32_t count = c->work_count;
+    unsigned long long n_lb = 0, n_leaves = 0;
+    // item i goes to warp i mod (warps in the grid): chunks of at most lb_chunk
+    // series keep the shares even, and no counter is contended
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t item = gw; item < count; item += nw) {
+        const uint32_t wi = s.work[item];
+        const uint32_t leaf = wi >> 4, part = wi & 15u;
+        const int64_t lb0 = ix.leaf_begin[leaf], le = ix.leaf_begin[leaf + 1];
+        const int64_t b = lb0 + (int64_t)part * chunk;
+        const int64_t e = b + chunk < le ? b + chunk : le;
+        n_leaves += part == 0 ? 1 : 0;
+        for (int64_t r0 = b; r0 < e; r0 += 32 * LB_WORDS) {
+            uint4 w[LB_WORDS];
+#pragma unroll
+            for (int j = 0; j < LB_WORDS; ++j) {
+                const int64_t r = r0 + j * 32 + lane;
+                w[j] = r < e ? ld_stream_u4(ix.sax + r) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int j = 0; j < LB_WORDS; ++j) {
+                const int64_t r = r0 + j * 32 + lane;
+                const bool ok = r < e;
+                n_lb += ok ? 1 : 0;
+                const float lb = series_lb<CARD>(w[j], tab, card);
+                const bool keep = ok && lb <= thr;
+                const unsigned m = __ballot_sync(FULL, keep);
+                if (m) {
+                    if (nbuf + 32 > LB_BUF) drain();
+                    if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = make_uint2((uint32_t)r, __float_as_uint(lb));
+                    nbuf += __popc(m);
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    drain();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) n_lb += __shfl_xor_sync(FULL, n_lb, off);
+    if (lane == 0) {
+        if (n_lb) atomicAdd(&c->series_lb, n_lb);
+        if (n_leaves) atomicAdd(&c->leaves_scanned, n_leaves);
+    }
+}
+
+// ---------------------------------------------------------------- q_refine
+// Real distances of the survivors (MESSI's real distance calculations), in the
+// order the scan found them: warp w takes survivor quads w, w + W, ... (W
+// warps in the grid).  Before each quad the warp reads the current k-th best
+// (lane 0, broadcast: the skip and early-abandon decisions are warp-uniform);
+// a survivor whose bound now exceeds it is skipped without reading its row.
+// Distances are computed with the same fp32 order as every other refinement
+// and fed to the k best in batches of SR_BATCH.
+constexpr int RF_THREADS = 256;
+
+template <int NV>
+__global__ void __launch_bounds__(RF_THREADS, 3) q_refine_kernel(DevIndex ix, QueryScratch s, int k) {
+    QCtl* c = s.ctl;
+    if (c->flags & QF_NONFINITE) return;
+    const int lane = threadIdx.x & 31;
     constexpr int NQ = NV ? NV : 1;
     float4 qv[NQ];
     load_q<NV>(s.q, qv);
+    const uint32_t found = c->surv_count;
+    const uint32_t total = found < s.surv_cap ? found : s.surv_cap;
     const double delta = c->delta, E = c->E;
-    // wave 0: positions [0, wave_items); wave 1: the rest, with its own counter
-    const uint32_t item0 = wave == 0 ? 0u : wave_items;
-    const uint32_t item1 = wave == 0 ? (c->work_count < wave_items ? c->work_count : wave_items)
-                                     : c->work_count;
-    uint32_t* counter = wave == 0 ? &c->work_next : &c->work_next2;
-    const float thr0 = c->thr_lb0;
-    int wb = 0;
-    unsigned long long n_lb = 0, n_ref = 0, n_scan = 0;
-    // batch of refined distances of this warp: entry i held by lane i
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long kth = 0ull;  // cached k-th best and the limits derived from it
+    float thr = INFINITY, lim = INFINITY;
+    unsigned long long n_ref = 0;
     float my_d2 = INFINITY;
     uint32_t my_pos = 0;
     int nb = 0;
@@ -560,138 +719,69 @@ __global__ void __launch_bounds__(SR_THREADS, 4) q_scan_refine_kernel(DevIndex i
         unsigned long long kt = 0;
         if (lane == 0) kt = ld_volatile_u64(&s.topk[k - 1]);
         kt = __shfl_sync(FULL, kt, 0);
-        const double lim = kt == EMPTY_SLOT ? INFINITY : (double)key_d2(kt) * (1.0 + 3.0 * delta);
-        if (lane < nb && (double)my_d2 <= lim)
+        const double lim_w = kt == EMPTY_SLOT ? INFINITY : (double)key_d2(kt) * (1.0 + 3.0 * delta);
+        if (lane < nb && (double)my_d2 <= lim_w)
             consider(s, k, pack_key(my_d2, ix.orig[my_pos]), my_pos, delta);
         __syncwarp();
         nb = 0;
     };
-    auto push = [&](float d2, int64_t r) {
+    auto push = [&](float d2, uint32_t r) {
         if (lane == nb) {
             my_d2 = d2;
-            my_pos = (uint32_t)r;
+            my_pos = r;
         }
         ++nb;
         if (nb == SR_BATCH) flush();
     };
-    // the next claimed leaf and its metadata are fetched by thread 0 while the
-    // current one is processed
-    uint32_t nx_item = 0, nx_leaf = 0, nx_beg = 0, nx_end = 0;
-    float nx_lb = 0.0f;
-    auto fetch_next = [&]() {
-        nx_item = item0 + atomicAdd(counter, 1u);
-        if (nx_item < item1) {
-            nx_leaf = s.work[nx_item];
-            nx_lb = s.leaf_lb[nx_leaf];
-            nx_beg = ix.leaf_begin[nx_leaf];
-            nx_end = ix.leaf_begin[nx_leaf + 1];
-        }
-    };
-    if (tid == 0) fetch_next();
-    __syncthreads();
-    for (;;) {
-        if (tid == 0) {
-            item_s = nx_item;
-            leaf_s = nx_leaf;
-            lb_s = nx_lb;
-            beg_s = nx_beg;
-            end_s = nx_end;
-            const unsigned long long kth = ld_volatile_u64(&s.topk[k - 1]);
-            if (kth != kth_s || kth == 0) {
-                kth_s = kth;
-                thr_s = lb_threshold(kth, delta, E);
-                lim_s = abandon_limit(kth, delta);
-            }
-        }
-        __syncthreads();
-        const uint32_t item = item_s;
-        const float thr = thr_s;
-        if (item >= item1) break;
-        if (tid == 0) fetch_next();
-        while (wb < NBINS - 1 && off[wb + 1] <= item) ++wb;
-        // every later position is in bin >= wb, whose bounds are >= thr0 (wb/NBINS)^2;
-        // the prefetched position is later, so stopping loses nothing
-        if (thr0 > 0.0f && !isinf(thr0)) {
-            const float edge = (float)wb / (float)NBINS;
-            if (thr0 * edge * edge * 0.99999f > thr) break;
-        }
-        if (lb_s <= thr) {
-            if (tid == 0) ++n_scan;
-            const int64_t lbeg = beg_s, lend = end_s;
-            for (int64_t rb = lbeg; rb < lend; rb += SR_ROUND) {
-                if (tid == 0) nsurv = 0;
-                __syncthreads();
-                const float thr_r = thr_s;
-                // bound: warp w takes series [rb + w*256, rb + (w+1)*256)
-                const int64_t b = rb + (int64_t)warp * SCAN_UNIT;
-                const int64_t e = b + SCAN_UNIT < lend ? b + SCAN_UNIT : lend;
-                if (b < lend) {
-                    uint4 w[SR_WORDS];
+    // the k-th best and the next four survivors are read one round ahead, so
+    // their latency overlaps the current distances
+    unsigned long long kt_next = 0;
+    if (lane == 0) kt_next = ld_volatile_u64(&s.topk[k - 1]);
+    uint2 nx[4];
 #pragma unroll
-                    for (int j = 0; j < SR_WORDS; ++j) {
-                        const int64_t r = b + j * 32 + lane;
-                        w[j] = r < e ? ld_stream_u4(ix.sax + r) : make_uint4(0, 0, 0, 0);
-                    }
-#pragma unroll
-                    for (int j = 0; j < SR_WORDS; ++j) {
-                        const int64_t r = b + j * 32 + lane;
-                        const bool ok = r < e;
-                        n_lb += ok ? 1 : 0;
-                        const bool keep = ok && series_lb(w[j], tab, card) <= thr_r;
-                        const unsigned mk = __ballot_sync(FULL, keep);
-                        int base = 0;
-                        if (lane == 0 && mk) base = atomicAdd(&nsurv, __popc(mk));
-                        base = __shfl_sync(FULL, base, 0);
-                        if (keep) surv[base + __popc(mk & ((1u << lane) - 1u))] = (uint16_t)(r - rb);
-                    }
-                }
-                __syncthreads();
-                const int ns = nsurv;
-                const float lim_ab = lim_s;
-                // refine: warp w takes survivor pairs (2w, 2w+1), then the next 16, ...
-                for (int t = 2 * warp; t < ns; t += 2 * SR_WARPS) {
-                    const int64_t r0 = rb + surv[t];
-                    const bool two = t + 1 < ns;
-                    if constexpr (NV > 0 && NV <= 2) {
-                        const int64_t r1 = two ? rb + surv[t + 1] : r0;
-                        float d0, d1;
-                        warp_d2_two<NQ>(ix, r0, r1, two, qv, d0, d1);
-                        n_ref += two ? 2 : 1;
-                        push(d0, r0);
-                        if (two) push(d1, r1);
-                    } else {
-                        bool ab;
-                        const float d0 = warp_d2<NV>(ix, r0, qv, s.q, lim_ab, ab);
-                        ++n_ref;
-                        if (!ab) push(d0, r0);
-                        if (two) {
-                            const int64_t r1 = rb + surv[t + 1];
-                            const float d1 = warp_d2<NV>(ix, r1, qv, s.q, lim_ab, ab);
-                            ++n_ref;
-                            if (!ab) push(d1, r1);
-                        }
-                    }
-                }
-                flush();
-                __syncthreads();
-                if (tid == 0) {
-                    const unsigned long long kth = ld_volatile_u64(&s.topk[k - 1]);
-                    if (kth != kth_s) {
-                        kth_s = kth;
-                        thr_s = lb_threshold(kth, delta, E);
-                        lim_s = abandon_limit(kth, delta);
-                    }
-                }
-            }
+    for (int t = 0; t < 4; ++t) nx[t] = 4 * gw + t < total ? s.surv[4 * gw + t] : make_uint2(0u, 0x7f800000u);
+    for (uint32_t i = 4 * gw; i < total; i += 4 * nw) {
+        __syncwarp();
+        const unsigned long long kt = __shfl_sync(FULL, kt_next, 0);
+        if (lane == 0) kt_next = ld_volatile_u64(&s.topk[k - 1]);
+        if (kt != kth || kth == 0ull) {
+            kth = kt;
+            thr = lb_threshold(kt, delta, E);
+            lim = abandon_limit(kt, delta);
         }
-        __syncthreads();
+        uint2 e[4];
+        unsigned keep = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            e[t] = nx[t];
+            if (i + t < total && __uint_as_float(e[t].y) <= thr) keep |= 1u << t;
+        }
+        const uint32_t in = i + 4 * nw;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) nx[t] = in + t < total ? s.surv[in + t] : make_uint2(0u, 0x7f800000u);
+        if (!keep) continue;
+        if constexpr (NV > 0 && NV <= 2) {
+            float d[4];
+            warp_d2_four<NQ>(ix, e, keep, qv, d);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (keep & (1u << t)) {
+                    ++n_ref;
+                    push(d[t], e[t].x);
+                }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (keep & (1u << t)) {
+                    bool ab;
+                    const float d0 = warp_d2<NV>(ix, (int64_t)e[t].x, qv, s.q, lim, ab);
+                    ++n_ref;
+                    if (!ab) push(d0, e[t].x);
+                }
+        }
     }
     flush();
     if (lane == 0 && n_ref) atomicAdd(&c->series_refined, n_ref);
-    if (tid == 0 && n_scan) atomicAdd(&c->leaves_scanned, n_scan);
-#pragma unroll
-    for (int off2 = 16; off2 > 0; off2 >>= 1) n_lb += __shfl_xor_sync(FULL, n_lb, off2);
-    if (lane == 0 && n_lb) atomicAdd(&c->series_lb, n_lb);
 }
 
 // ---------------------------------------------------------------- q_finalize
@@ -901,7 +991,7 @@ __device__ __forceinline__ void q_finalize_body(const DevIndex& ix, const QueryS
     if (tid == 0) {
         c->window = (uint32_t)window;
         if (cnt < k) c->flags |= QF_SHORT;
-        if (attempted > s.cand_cap) c->flags |= QF_OVERFLOW;
+        if (attempted > s.cand_cap || c->surv_count > s.surv_cap) c->flags |= QF_OVERFLOW;
     }
 }
 __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, QueryScratch s, int k) {
@@ -1074,7 +1164,7 @@ void free_query_scratch_struct(QueryScratch& q, cudaStream_t st);
 static void free_scratch(QueryScratch& q, cudaStream_t st) { free_query_scratch_struct(q, st); }
 void free_query_scratch_struct(QueryScratch& q, cudaStream_t st) {
     void* ptrs[] = {q.q, q.table, q.leaf_lb, q.work, q.bin_count, q.bin_cursor, q.topk,
-                    q.cand_key, q.cand_pos, q.ctl, q.out_idx, q.out_dist};
+                    q.cand_key, q.cand_pos, q.ctl, q.out_idx, q.out_dist, q.surv};
     for (void* p : ptrs)
         if (p) dev_free(p, st);
     q = QueryScratch{};
@@ -1082,12 +1172,15 @@ void free_query_scratch_struct(QueryScratch& q, cudaStream_t st) {
 
 // scratch for queries on any index with at most L leaves, series length n and
 // cardinality card
-void alloc_query_scratch_for(int64_t L, int n, int card, uint32_t cand_cap, QueryScratch& q,
-                             cudaStream_t st) {
+// scan work items of an index: at most one per leaf plus one per lb_chunk (>= 256) series
+int64_t work_items_cap(int64_t L, int64_t N) { return L + (N + 255) / 256 + 1; }
+
+void alloc_query_scratch_for(int64_t L, int64_t N, int n, int card, uint32_t cand_cap, uint32_t surv_cap,
+                             QueryScratch& q, cudaStream_t st) {
     q.q = static_cast<float*>(dev_alloc(sizeof(float) * n, st));
     q.table = static_cast<float*>(dev_alloc(sizeof(float) * W * card, st));
     q.leaf_lb = static_cast<float*>(dev_alloc(sizeof(float) * L, st));
-    q.work = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * L, st));
+    q.work = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * work_items_cap(L, N), st));
     q.bin_count = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * NBINS, st));
     q.bin_cursor = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * NBINS, st));
     q.topk = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * MAX_K, st));
@@ -1097,11 +1190,25 @@ void alloc_query_scratch_for(int64_t L, int n, int card, uint32_t cand_cap, Quer
     q.ctl = static_cast<QCtl*>(dev_alloc(sizeof(QCtl), st));
     q.out_idx = static_cast<int64_t*>(dev_alloc(sizeof(int64_t) * MAX_K, st));
     q.out_dist = static_cast<float*>(dev_alloc(sizeof(float) * MAX_K, st));
+    q.surv_cap = surv_cap;
+    q.surv = static_cast<uint2*>(dev_alloc(sizeof(uint2) * surv_cap, st));
     ISAX_CUDA_TRY(cudaMemsetAsync(q.ctl, 0, sizeof(QCtl), st));
 }
 
-static void alloc_scratch(const DevIndex& d, uint32_t cand_cap, QueryScratch& q, cudaStream_t st) {
-    alloc_query_scratch_for(d.L, d.n, d.card, cand_cap, q, st);
+uint32_t default_surv_cap(int64_t N) { return (uint32_t)std::max<int64_t>(1, std::min<int64_t>(N, 1 << 21)); }
+
+static void alloc_scratch(const DevIndex& d, uint32_t cand_cap, uint32_t surv_cap, QueryScratch& q,
+                          cudaStream_t st) {
+    alloc_query_scratch_for(d.L, d.N, d.n, d.card, cand_cap, surv_cap, q, st);
+}
+
+// a larger survivor buffer (the old contents are dropped)
+void grow_query_survivors(QueryScratch& q, uint32_t surv_cap, cudaStream_t st) {
+    if (q.surv) dev_free(q.surv, st);
+    q.surv = nullptr;
+    q.surv_cap = 0;
+    q.surv = static_cast<uint2*>(dev_alloc(sizeof(uint2) * surv_cap, st));
+    q.surv_cap = surv_cap;
 }
 
 // a larger candidate buffer (the old contents are dropped)
@@ -1175,10 +1282,10 @@ static void drop_query_graphs(isax_index* ix) {
     if (ix->graphs) static_cast<QueryGraphs*>(ix->graphs)->clear();
 }
 
-void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, cudaStream_t st) {
+void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, uint32_t surv_cap, cudaStream_t st) {
     drop_query_graphs(ix);
     free_query_scratch(ix, st);
-    alloc_scratch(ix->d, cand_cap, ix->qs, st);
+    alloc_scratch(ix->d, cand_cap, surv_cap, ix->qs, st);
 }
 
 void free_index_arrays(isax_index* ix, cudaStream_t st) {
@@ -1243,19 +1350,21 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
             q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
         }
     }
-    if (SR_WAVE0 > 0) {
-        // the lowest-bound leaves first, one CTA each, so the k-th best tightens
-        // before the whole GPU scans with it
-        ISAX_LAUNCH("q_scan_refine", st);
-        q_scan_refine_kernel<NV><<<SR_WAVE0, SR_THREADS, tab_bytes, st>>>(d, s, k, 0, SR_WAVE0);
+    {
+        static int grid_lb = 0;
+        if (!grid_lb)
+            grid_lb = occupancy_grid((const void*)q_series_lb_kernel<256>, LB_THREADS, tab_bytes, ix->num_sms);
+        ISAX_LAUNCH("q_series_lb", st);
+        if (d.card == 256)
+            q_series_lb_kernel<256><<<grid_lb, LB_THREADS, tab_bytes, st>>>(d, s, k);
+        else
+            q_series_lb_kernel<0><<<grid_lb, LB_THREADS, tab_bytes, st>>>(d, s, k);
     }
     {
-        static int grid = 0;
-        if (!grid)
-            grid = occupancy_grid((const void*)q_scan_refine_kernel<NV>, SR_THREADS, tab_bytes,
-                                  ix->num_sms);
-        ISAX_LAUNCH("q_scan_refine", st);
-        q_scan_refine_kernel<NV><<<grid, SR_THREADS, tab_bytes, st>>>(d, s, k, 1, SR_WAVE0);
+        static int grid_rf = 0;
+        if (!grid_rf) grid_rf = occupancy_grid((const void*)q_refine_kernel<NV>, RF_THREADS, 0, ix->num_sms);
+        ISAX_LAUNCH("q_refine", st);
+        q_refine_kernel<NV><<<grid_rf, RF_THREADS, 0, st>>>(d, s, k);
     }
     {
         ISAX_LAUNCH("q_finalize", st);
@@ -1342,12 +1451,18 @@ void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_
         if (ctl_out->flags & QF_NONFINITE) throw Error{ISAX_ERR_INVALID_ARG, "query contains a non-finite value"};
         if (ctl_out->flags & QF_OVERFLOW) {
             if (attempt >= 3) throw Error{ISAX_ERR_INTERNAL, "candidate buffer kept overflowing"};
-            uint64_t want = std::max<uint64_t>((uint64_t)ctl_out->cand_count * 2, (uint64_t)ix->qs.cand_cap * 4);
-            want = std::min<uint64_t>(want, (uint64_t)ix->d.N);
+            const uint64_t N = (uint64_t)ix->d.N;
+            uint64_t want_c = ix->qs.cand_cap, want_s = ix->qs.surv_cap;
+            if (ctl_out->cand_count > ix->qs.cand_cap)
+                want_c = std::min<uint64_t>(std::max<uint64_t>((uint64_t)ctl_out->cand_count * 2,
+                                                               (uint64_t)ix->qs.cand_cap * 4), N);
+            if (ctl_out->surv_count > ix->qs.surv_cap)
+                want_s = std::min<uint64_t>(std::max<uint64_t>((uint64_t)ctl_out->surv_count * 2,
+                                                               (uint64_t)ix->qs.surv_cap * 4), N);
             // keep q across the reallocation
             float* qsave = static_cast<float*>(dev_alloc(sizeof(float) * ix->d.n, st));
             ISAX_CUDA_TRY(cudaMemcpyAsync(qsave, ix->qs.q, sizeof(float) * ix->d.n, cudaMemcpyDeviceToDevice, st));
-            alloc_query_scratch(ix, (uint32_t)want, st);
+            alloc_query_scratch(ix, (uint32_t)want_c, (uint32_t)want_s, st);
             ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, qsave, sizeof(float) * ix->d.n, cudaMemcpyDeviceToDevice, st));
             dev_free(qsave, st);
             ++*reruns;
@@ -1373,7 +1488,7 @@ void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t m
         pool->slots.push_back(sl);
         ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking));
         ISAX_CUDA_TRY(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
-        alloc_scratch(ix->d, ix->qs.cand_cap, sl->qs, st);
+        alloc_scratch(ix->d, ix->qs.cand_cap, ix->qs.surv_cap, sl->qs, st);
     }
     if (pool->host_cap < (size_t)B) {
         if (pool->host_ctl) cudaFreeHost(pool->host_ctl);

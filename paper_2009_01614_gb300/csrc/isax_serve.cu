@@ -66,6 +66,7 @@ struct ServeSlot {
     ServeRequest req;
     size_t reserved = 0;        // budget bytes held by the current request
     uint32_t need_cap = 0;
+    uint32_t need_surv = 0;     // survivor entries needed after a survivor overflow
     double t_start = 0;
     int reruns = 0;
 };
@@ -109,10 +110,11 @@ static void slot_free(ServeSlot* sl) {
 }
 
 static void server_setup(isax_server* s) {
-    int64_t L = 1;
+    int64_t L = 1, Nmax = 1;
     int n = 16, card = 2;
     for (isax_index* ix : s->colls) {
         L = std::max<int64_t>(L, ix->d.L);
+        Nmax = std::max<int64_t>(Nmax, ix->d.N);
         n = std::max(n, (int)ix->d.n);
         card = std::max(card, (int)ix->d.card);
     }
@@ -121,7 +123,7 @@ static void server_setup(isax_server* s) {
         s->slots.push_back(sl);
         ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking));
         ISAX_CUDA_TRY(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
-        alloc_query_scratch_for(L, n, card, serve_cand_cap(1), sl->qs, sl->st);
+        alloc_query_scratch_for(L, Nmax, n, card, serve_cand_cap(1), default_surv_cap(Nmax), sl->qs, sl->st);
         ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_q, sizeof(float) * n));
         ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_ctl, sizeof(QCtl)));
         ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_idx, sizeof(int64_t) * MAX_K));
@@ -134,9 +136,10 @@ static void server_setup(isax_server* s) {
 // pinned staging, then the completion event
 static void slot_launch(isax_server* s, ServeSlot* sl) {
     isax_index* ix = s->colls[sl->req.coll];
-    if (sl->qs.cand_cap < sl->need_cap) {
-        for (auto& kv : sl->graphs) query_graphs_clear(kv.second);  // they hold the old buffer
-        grow_query_candidates(sl->qs, sl->need_cap, sl->st);
+    if (sl->qs.cand_cap < sl->need_cap || sl->qs.surv_cap < sl->need_surv) {
+        for (auto& kv : sl->graphs) query_graphs_clear(kv.second);  // they hold the old buffers
+        if (sl->qs.cand_cap < sl->need_cap) grow_query_candidates(sl->qs, sl->need_cap, sl->st);
+        if (sl->qs.surv_cap < sl->need_surv) grow_query_survivors(sl->qs, sl->need_surv, sl->st);
     }
     void*& g = sl->graphs[ix];
     if (!g) g = query_graphs_new();
@@ -153,6 +156,7 @@ static void slot_start(isax_server* s, ServeSlot* sl, ServeRequest&& r, size_t b
     sl->req = std::move(r);
     sl->reserved = bytes;
     sl->need_cap = serve_cand_cap(sl->req.k);
+    sl->need_surv = 0;
     sl->reruns = 0;
     sl->wants_room = false;
     sl->busy = true;
@@ -239,8 +243,14 @@ static void server_loop(isax_server* s) {
             if (c.flags & QF_NONFINITE) {
                 publish(s, sl, ISAX_ERR_INVALID_ARG);
             } else if ((c.flags & QF_OVERFLOW) && sl->reruns < 4) {
-                const uint64_t want = std::max<uint64_t>((uint64_t)c.cand_count * 2, (uint64_t)sl->need_cap * 4);
-                sl->need_cap = (uint32_t)std::min<uint64_t>(want, (uint64_t)s->colls[sl->req.coll]->d.N + 16);
+                const uint64_t N = (uint64_t)s->colls[sl->req.coll]->d.N;
+                if (c.cand_count > sl->qs.cand_cap) {
+                    const uint64_t want = std::max<uint64_t>((uint64_t)c.cand_count * 2, (uint64_t)sl->need_cap * 4);
+                    sl->need_cap = (uint32_t)std::min<uint64_t>(want, N + 16);
+                }
+                if (c.surv_count > sl->qs.surv_cap)
+                    sl->need_surv = (uint32_t)std::min<uint64_t>(
+                        std::max<uint64_t>((uint64_t)c.surv_count * 2, (uint64_t)sl->qs.surv_cap * 4), N + 16);
                 sl->wants_room = true;
             } else if (c.flags & (QF_OVERFLOW | QF_SHORT)) {
                 publish(s, sl, ISAX_ERR_INTERNAL);
