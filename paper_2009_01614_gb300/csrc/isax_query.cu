@@ -645,12 +645,23 @@ __global__ void __launch_bounds__(LB_THREADS, 4) q_series_lb_kernel(DevIndex ix,
     // series keep the shares even, and no counter is contended
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t item = gw; item < count; item += nw) {
+    // an item's row range (work entry, then the leaf's bounds: two dependent
+    // loads) is fetched one item ahead, while the current one is bounded
+    auto range_of = [&](uint32_t item, int64_t& b, int64_t& e, uint32_t& part) {
         const uint32_t wi = s.work[item];
-        const uint32_t leaf = wi >> 4, part = wi & 15u;
+        const uint32_t leaf = wi >> 4;
+        part = wi & 15u;
         const int64_t lb0 = ix.leaf_begin[leaf], le = ix.leaf_begin[leaf + 1];
-        const int64_t b = lb0 + (int64_t)part * chunk;
-        const int64_t e = b + chunk < le ? b + chunk : le;
+        b = lb0 + (int64_t)part * chunk;
+        e = b + chunk < le ? b + chunk : le;
+    };
+    int64_t nb_ = 0, ne_ = 0;
+    uint32_t npart = 0;
+    if (gw < count) range_of(gw, nb_, ne_, npart);
+    for (uint32_t item = gw; item < count; item += nw) {
+        const int64_t b = nb_, e = ne_;
+        const uint32_t part = npart;
+        if (item + nw < count) range_of(item + nw, nb_, ne_, npart);
         n_leaves += part == 0 ? 1 : 0;
         for (int64_t r0 = b; r0 < e; r0 += 32 * LB_WORDS) {
             uint4 w[LB_WORDS];
