@@ -185,7 +185,7 @@ isax_status isax_summarize(const float* series, int64_t N, int32_t n, int32_t ca
 #define ISAX_NOALLOC_MAX_LEAVES 524288u       /* largest index (in leaves) it serves */
 #define ISAX_NOALLOC_MAX_CANDIDATES 262144u   /* fp32 near-tie candidates it can hold */
 #define ISAX_NOALLOC_MAX_SURVIVORS 1048576u   /* series passing the lower bound it can hold */
-#define ISAX_NOALLOC_SCRATCH_BYTES 17881344u  /* its fixed device scratch (about 17 MiB) */
+#define ISAX_NOALLOC_SCRATCH_BYTES 22075648u  /* its fixed device scratch (about 21 MiB) */
 
 /*
  * isax_query_knn_noalloc - the same exact k-NN query as isax_query_knn (same

@@ -99,6 +99,7 @@ enum : uint32_t {
     QF_NONFINITE = 1u,  // query holds NaN or Inf
     QF_OVERFLOW = 2u,   // candidate buffer overflowed: rerun with more room
     QF_SHORT = 4u,      // fewer than k candidates reached the end (internal error)
+    QF_STALLED = 8u,    // a bounded wait on a bulk copy gave up (internal error)
 };
 
 // Device scratch of one in-flight query.
@@ -106,7 +107,8 @@ struct QueryScratch {
     float* q;                      // [n]
     float* table;                  // [16][card] lower-bound table
     float* leaf_lb;                // [L]
-    uint32_t* work;                // [work_items_cap] scan items (leaf << 4 | chunk), ordered by bin
+    uint2* work;                   // [work_items_cap] scan items {first row, rows | leaf-start bit 31},
+                                   // ordered by bin
     uint32_t* bin_count;           // [NBINS]
     uint32_t* bin_cursor;          // [NBINS]
     unsigned long long* topk;      // [MAX_K] packed (fp32 d2 bits << 32 | orig)

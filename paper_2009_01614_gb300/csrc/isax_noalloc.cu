@@ -44,7 +44,7 @@ constexpr size_t OFF_Q = 0;
 constexpr size_t OFF_TABLE = align256(OFF_Q + sizeof(float) * MAX_LEN);
 constexpr size_t OFF_LEAF_LB = align256(OFF_TABLE + sizeof(float) * W * MAX_CARD);
 constexpr size_t OFF_WORK = align256(OFF_LEAF_LB + sizeof(float) * MAX_LEAVES);
-constexpr size_t OFF_BIN_COUNT = align256(OFF_WORK + sizeof(uint32_t) * MAX_WORK);
+constexpr size_t OFF_BIN_COUNT = align256(OFF_WORK + sizeof(uint2) * MAX_WORK);
 constexpr size_t OFF_BIN_CURSOR = align256(OFF_BIN_COUNT + sizeof(uint32_t) * NBINS);
 constexpr size_t OFF_TOPK = align256(OFF_BIN_CURSOR + sizeof(uint32_t) * NBINS);
 constexpr size_t OFF_CAND_KEY = align256(OFF_TOPK + sizeof(unsigned long long) * MAX_K);
@@ -80,7 +80,7 @@ QueryScratch scratch_view(unsigned char* base) {
     s.q = reinterpret_cast<float*>(base + OFF_Q);
     s.table = reinterpret_cast<float*>(base + OFF_TABLE);
     s.leaf_lb = reinterpret_cast<float*>(base + OFF_LEAF_LB);
-    s.work = reinterpret_cast<uint32_t*>(base + OFF_WORK);
+    s.work = reinterpret_cast<uint2*>(base + OFF_WORK);
     s.bin_count = reinterpret_cast<uint32_t*>(base + OFF_BIN_COUNT);
     s.bin_cursor = reinterpret_cast<uint32_t*>(base + OFF_BIN_CURSOR);
     s.topk = reinterpret_cast<unsigned long long*>(base + OFF_TOPK);
@@ -143,6 +143,7 @@ extern "C" isax_status isax_query_knn_noalloc(const isax_index* cix, const float
         ISAX_CUDA_TRY(cudaMemcpyAsync(&c, s.ctl, sizeof(QCtl), cudaMemcpyDeviceToHost, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         if (c.flags & QF_NONFINITE) fail(ISAX_ERR_INVALID_ARG, "query contains a non-finite value");
+        if (c.flags & QF_STALLED) fail(ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed");
         if (c.flags & QF_OVERFLOW)
             fail(ISAX_ERR_OOM, c.surv_count > MAX_SURV
                  ? "more than " + std::to_string(MAX_SURV) + " series passed the lower bound: the "

@@ -10,11 +10,12 @@
 //                 not prune are counted into bins of bound / BSF.
 //   q_leaf_scatter  the unpruned leaves listed bin by bin: a work list in
 //                 ascending lower-bound order (MESSI's priority queues).
-//   q_series_lb   warps claim queued leaves in that order (Fetch&Inc) and
-//                 bound their 16-byte SAX words against the table in shared
-//                 memory (a conflict-free 32-region bound first, the full one
-//                 only for what it keeps); survivors {position, bound} are
-//                 appended in claim order with warp ballots.
+//   q_series_lb   the queued leaves' pieces (at most 256 rows) dealt to the
+//                 warps in that order; each warp streams its pieces' 16-byte
+//                 SAX words through a ring of shared-memory stages filled by
+//                 bulk copies and bounds them against the table in shared
+//                 memory; survivors {position, bound} are appended with warp
+//                 ballots.
 //   q_refine      warps take the survivors in that order, skip those whose
 //                 bound now exceeds the k-th best, and compute real distances
 //                 (early abandoning for long series); the k best so far live in
@@ -210,16 +211,21 @@ __device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ ta
     return lb;
 }
 
-// work items of the scan: a queued leaf is cut into chunks of lb_chunk series
-// (at least 256, at most 16 chunks per leaf), item = leaf << 4 | chunk
-__host__ __device__ __forceinline__ int lb_chunk(int leaf_size) {
-    const int c = ((leaf_size + 15) / 16 + 255) / 256 * 256;
-    return c > 256 ? c : 256;
-}
-__device__ __forceinline__ uint32_t leaf_chunks(const DevIndex& ix, int64_t l) {
+// work items of the scan: a queued leaf is cut into pieces of at most LB_PIECE
+// rows, item = {first row, rows | 1 << 31 on the leaf's first piece}
+constexpr int LB_PIECE = 256;
+__device__ __forceinline__ uint32_t leaf_pieces(const DevIndex& ix, int64_t l) {
     const uint32_t size = ix.leaf_begin[l + 1] - ix.leaf_begin[l];
-    const uint32_t ch = (uint32_t)lb_chunk(ix.leaf_size);
-    return (size + ch - 1) / ch;
+    return (size + LB_PIECE - 1) / LB_PIECE;
+}
+__device__ __forceinline__ void put_pieces(const DevIndex& ix, const QueryScratch& s, int64_t l, uint32_t at,
+                                           uint32_t n_pieces, uint32_t cap) {
+    const uint32_t b = (uint32_t)ix.leaf_begin[l], e = (uint32_t)ix.leaf_begin[l + 1];
+    for (uint32_t ch = 0; ch < n_pieces && at + ch < cap; ++ch) {
+        const uint32_t r = b + ch * LB_PIECE;
+        const uint32_t rows = e - r < (uint32_t)LB_PIECE ? e - r : (uint32_t)LB_PIECE;
+        s.work[at + ch] = make_uint2(r, rows | (ch == 0 ? 0x80000000u : 0u));
+    }
 }
 
 // ---------------------------------------------------------------- q_prep
@@ -440,7 +446,7 @@ __global__ void __launch_bounds__(256) q_leaf_lb_kernel(DevIndex ix, QueryScratc
             }
         }
         s.leaf_lb[l] = lb;
-        if (!(l >= a0 && l < a1) && lb <= thr) atomicAdd(&hist[bin_of(lb, thr)], leaf_chunks(ix, l));
+        if (!(l >= a0 && l < a1) && lb <= thr) atomicAdd(&hist[bin_of(lb, thr)], leaf_pieces(ix, l));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < NBINS; i += blockDim.x)
@@ -468,10 +474,9 @@ __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, Quer
         const float lb = s.leaf_lb[l];
         if (lb <= thr) {
             const int b = bin_of(lb, thr);
-            const uint32_t nch = leaf_chunks(ix, l);
+            const uint32_t nch = leaf_pieces(ix, l);
             const uint32_t p = off[b] + atomicAdd(&s.bin_cursor[b], nch);
-            for (uint32_t ch = 0; ch < nch; ++ch)
-                if (p + ch < tot) s.work[p + ch] = ((uint32_t)l << 4) | ch;
+            put_pieces(ix, s, l, p, nch, tot);
             ++mine;
         }
     }
@@ -500,7 +505,7 @@ __global__ void __launch_bounds__(256) q_flat_list_kernel(DevIndex ix, QueryScra
          l0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t l = l0 + lane;
         const bool take = l < ix.L && !(l >= a0 && l < a1);
-        const uint32_t nch = take ? leaf_chunks(ix, l) : 0u;
+        const uint32_t nch = take ? leaf_pieces(ix, l) : 0u;
         uint32_t incl = nch;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -515,7 +520,7 @@ __global__ void __launch_bounds__(256) q_flat_list_kernel(DevIndex ix, QueryScra
             atomicAdd(&c->leaves_queued, (unsigned long long)leaves);
         }
         base = __shfl_sync(FULL, base, 0);
-        for (uint32_t ch = 0; ch < nch; ++ch) s.work[base + incl - nch + ch] = ((uint32_t)l << 4) | ch;
+        if (nch) put_pieces(ix, s, l, base + incl - nch, nch, 0xFFFFFFFFu);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) c->thr_lb0 = 0.0f;
 }
@@ -586,46 +591,88 @@ __device__ __forceinline__ void warp_d2_four(const DevIndex& ix, const uint2 (&e
 }
 
 // ---------------------------------------------------------------- q_series_lb
-// The lower-bound scan (MESSI's lower-bound calculations): warps take the
-// queued leaf chunks in work-list order (ascending leaf bound for MESSI,
-// storage order for the flat scan), item i to warp i mod W, stream the
-// chunk's 16-byte SAX words with
-// LB_WORDS loads per lane in flight, bound each from the table in shared memory
-// against the threshold the approximate answer set, and append the survivors
-// {position, bound} in claim order with one atomic per warp and word batch.
-constexpr int LB_THREADS = 256, LB_WORDS = 8;
+// The lower-bound scan (MESSI's lower-bound calculations).  Work item i of the
+// list (a piece of at most LB_PIECE rows of a queued leaf, in ascending leaf
+// bound for MESSI, storage order for the flat scan) belongs to warp i mod W of
+// the grid.  Each warp streams its pieces' 16-byte SAX words through a private
+// ring of LB_STAGES shared-memory stages filled by bulk copies (the TMA engine,
+// completion counted on one mbarrier per stage), LB_STAGES - 1 pieces ahead of
+// the one it bounds, so HBM sees many copies in flight while the warp works
+// from shared memory.  A series is bounded from the table (in shared memory,
+// 1 KB-aligned rows) against the threshold the approximate answer set: the
+// first 8 segments first, the other 8 only when some lane of the warp is still
+// under the threshold (the sum runs in segment order either way, so the bound
+// is the same).  Survivors {position, bound} are buffered per warp and
+// appended with one atomic per batch.
+constexpr int LB_THREADS = 512;
+constexpr int LB_WARPS = LB_THREADS / 32;
+constexpr int LB_STAGES = 3;
+constexpr int LB_PER_LANE = LB_PIECE / 32;
 constexpr int LB_BUF = 64;     // survivors buffered per warp before one global append
+constexpr uint32_t LB_WAIT = 1u << 22;  // bounded wait on a stage's copy
+constexpr size_t LB_TAB_BYTES = sizeof(float) * W * MAX_CARD;
+constexpr size_t LB_RING_BYTES = (size_t)LB_WARPS * LB_STAGES * LB_PIECE * sizeof(uint4);
+constexpr size_t LB_SMEM = 1024 + LB_TAB_BYTES + LB_RING_BYTES + sizeof(uint64_t) * LB_WARPS * LB_STAGES +
+                           sizeof(uint2) * LB_WARPS * LB_BUF + 16;
+
+template <int OFF>
+__device__ __forceinline__ float lds_f32(uint32_t addr) {
+    float x;
+    asm("ld.shared.f32 %0, [%1+%2];" : "=f"(x) : "r"(addr), "n"(OFF));
+    return x;
+}
+// 4 segments (word Q of the SAX word, 8-bit symbols) added to lb in segment
+// order; tab_sa is the table's shared address, 1024-aligned, so the symbol's
+// byte offset ORs into it and the row offset is the load's immediate
+template <int Q>
+__device__ __forceinline__ float lb_word256(float lb, uint32_t v, uint32_t tab_sa) {
+    lb += lds_f32<(4 * Q + 0) * 1024>(((v << 2) & 0x3FCu) | tab_sa);
+    lb += lds_f32<(4 * Q + 1) * 1024>(((v >> 6) & 0x3FCu) | tab_sa);
+    lb += lds_f32<(4 * Q + 2) * 1024>(((v >> 14) & 0x3FCu) | tab_sa);
+    lb += lds_f32<(4 * Q + 3) * 1024>(((v >> 22) & 0x3FCu) | tab_sa);
+    return lb;
+}
 
 template <int CARD>
-__global__ void __launch_bounds__(LB_THREADS, 4) q_series_lb_kernel(DevIndex ix, QueryScratch s, int k) {
-    extern __shared__ float tab[];
-    __shared__ float thr_s;
-    __shared__ uint2 buf_s[LB_THREADS / 32][LB_BUF];
+__global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix, QueryScratch s, int k) {
+    extern __shared__ unsigned char lb_smem_raw[];
     QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
+    unsigned char* sm = lb_smem_raw + ((1024u - (smem_u32(lb_smem_raw) & 1023u)) & 1023u);
+    float* tab = reinterpret_cast<float*>(sm);
+    uint4* ring = reinterpret_cast<uint4*>(sm + LB_TAB_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + LB_TAB_BYTES + LB_RING_BYTES);
+    uint2* bufs = reinterpret_cast<uint2*>(bars + LB_WARPS * LB_STAGES);
+    float* thr_p = reinterpret_cast<float*>(bufs + LB_WARPS * LB_BUF);
     const int card = ix.card;
     {   // the table into shared memory: 16-byte loads, all issued before the stores
         const float4* src = reinterpret_cast<const float4*>(s.table);
         float4* dst = reinterpret_cast<float4*>(tab);
         const int nv = W * card / 4;
-        float4 v[4];
+        float4 v[2];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < 2; ++t) {
             const int e = threadIdx.x + t * LB_THREADS;
             if (e < nv) v[t] = src[e];
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < 2; ++t) {
             const int e = threadIdx.x + t * LB_THREADS;
             if (e < nv) dst[e] = v[t];
         }
     }
-    if (threadIdx.x == 0) thr_s = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), c->delta, c->E);
+    if (threadIdx.x < LB_WARPS * LB_STAGES) mbar_init(&bars[threadIdx.x], 1);
+    if (threadIdx.x == 0) {
+        *thr_p = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), c->delta, c->E);
+        mbar_fence_init();
+    }
     __syncthreads();
-    const float thr = thr_s;
+    const float thr = *thr_p;
+    const uint32_t tab_sa = smem_u32(tab);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int chunk = lb_chunk(ix.leaf_size);
-    uint2* buf = buf_s[warp];
+    uint4* wring = ring + (size_t)warp * LB_STAGES * LB_PIECE;
+    uint64_t* wbar = bars + warp * LB_STAGES;
+    uint2* buf = bufs + warp * LB_BUF;
     int nbuf = 0;  // warp-uniform
     // the buffered survivors go to the global list in one append
     auto drain = [&]() {
@@ -640,52 +687,92 @@ __global__ void __launch_bounds__(LB_THREADS, 4) q_series_lb_kernel(DevIndex ix,
         nbuf = 0;
     };
     const uint32_t count = c->work_count;
-    unsigned long long n_lb = 0, n_leaves = 0;
-    // item i goes to warp i mod (warps in the grid): chunks of at most lb_chunk
-    // series keep the shares even, and no counter is contended
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    // an item's row range (work entry, then the leaf's bounds: two dependent
-    // loads) is fetched one item ahead, while the current one is bounded
-    auto range_of = [&](uint32_t item, int64_t& b, int64_t& e, uint32_t& part) {
-        const uint32_t wi = s.work[item];
-        const uint32_t leaf = wi >> 4;
-        part = wi & 15u;
-        const int64_t lb0 = ix.leaf_begin[leaf], le = ix.leaf_begin[leaf + 1];
-        b = lb0 + (int64_t)part * chunk;
-        e = b + chunk < le ? b + chunk : le;
+    const uint32_t gw = blockIdx.x * LB_WARPS + warp;
+    const uint32_t nw = gridDim.x * LB_WARPS;
+    const uint32_t mine = gw < count ? (count - gw + nw - 1) / nw : 0u;  // this warp's pieces
+    // piece t of this warp is work[gw + t * nw]; lane j holds piece 32 b + j of
+    // the current block b and of the next one, loaded a block ahead
+    auto piece_of = [&](uint32_t t) -> uint2 {
+        return t < mine ? s.work[gw + (size_t)t * nw] : make_uint2(0u, 0u);
     };
-    int64_t nb_ = 0, ne_ = 0;
-    uint32_t npart = 0;
-    if (gw < count) range_of(gw, nb_, ne_, npart);
-    for (uint32_t item = gw; item < count; item += nw) {
-        const int64_t b = nb_, e = ne_;
-        const uint32_t part = npart;
-        if (item + nw < count) range_of(item + nw, nb_, ne_, npart);
-        n_leaves += part == 0 ? 1 : 0;
-        for (int64_t r0 = b; r0 < e; r0 += 32 * LB_WORDS) {
-            uint4 w[LB_WORDS];
+    uint2 cur = piece_of(lane), nxt = piece_of(32 + lane);
+    auto piece = [&](uint32_t t, uint32_t t_block0) -> uint2 {  // warp-wide, t warp-uniform
+        if (t - t_block0 < 32)
+            return make_uint2(__shfl_sync(FULL, cur.x, t & 31), __shfl_sync(FULL, cur.y, t & 31));
+        return make_uint2(__shfl_sync(FULL, nxt.x, t & 31), __shfl_sync(FULL, nxt.y, t & 31));
+    };
+    // lane 0 starts the copy of piece t into stage t % LB_STAGES
+    auto issue = [&](uint32_t t, uint2 p) {
+        if (lane == 0) {
+            const uint32_t rows = p.y & 0x7FFFFFFFu;
+            uint64_t* bar = &wbar[t % LB_STAGES];
+            mbar_arrive_expect_tx(bar, rows * (uint32_t)sizeof(uint4));
+            if (rows)
+                bulk_load(wring + (t % LB_STAGES) * LB_PIECE, ix.sax + p.x, rows * (uint32_t)sizeof(uint4), bar);
+        }
+    };
+    unsigned long long n_lb = 0, n_leaves = 0;
+    for (uint32_t t = 0; t + 1 < LB_STAGES && t < mine; ++t) issue(t, piece(t, 0));
+    bool stalled = false;
+    uint32_t it = 0;
+    for (; it < mine; ++it) {
+        const uint32_t block0 = it & ~31u;
+        if (it && (it & 31u) == 0) {
+            cur = nxt;
+            nxt = piece_of(it + 32 + lane);
+        }
+        const uint2 p = piece(it, block0);
+        if (it + LB_STAGES - 1 < mine) issue(it + LB_STAGES - 1, piece(it + LB_STAGES - 1, block0));
+        if (!__all_sync(FULL, mbar_wait_bounded(&wbar[it % LB_STAGES], (it / LB_STAGES) & 1u, LB_WAIT))) {
+            stalled = true;
+            break;
+        }
+        const uint32_t rows = p.y & 0x7FFFFFFFu, pos0 = p.x;
+        if (lane == 0) {
+            n_lb += rows;
+            n_leaves += p.y >> 31;
+        }
+        const uint4* src = wring + (it % LB_STAGES) * LB_PIECE;
+        uint4 w[LB_PER_LANE];
 #pragma unroll
-            for (int j = 0; j < LB_WORDS; ++j) {
-                const int64_t r = r0 + j * 32 + lane;
-                w[j] = r < e ? ld_stream_u4(ix.sax + r) : make_uint4(0u, 0u, 0u, 0u);
+        for (int j = 0; j < LB_PER_LANE; ++j) {
+            const uint32_t r = j * 32 + lane;
+            w[j] = r < rows ? src[r] : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int j = 0; j < LB_PER_LANE; ++j) {
+            const uint32_t r = j * 32 + lane;
+            const bool ok = r < rows;
+            float lb;
+            if constexpr (CARD == 256) {
+                lb = lb_word256<0>(0.0f, w[j].x, tab_sa);
+                lb = lb_word256<1>(lb, w[j].y, tab_sa);
+                if (!__any_sync(FULL, ok && lb <= thr)) continue;
+                lb = lb_word256<2>(lb, w[j].z, tab_sa);
+                lb = lb_word256<3>(lb, w[j].w, tab_sa);
+            } else {
+                lb = series_lb<CARD>(w[j], tab, card);
             }
-#pragma unroll
-            for (int j = 0; j < LB_WORDS; ++j) {
-                const int64_t r = r0 + j * 32 + lane;
-                const bool ok = r < e;
-                n_lb += ok ? 1 : 0;
-                const float lb = series_lb<CARD>(w[j], tab, card);
-                const bool keep = ok && lb <= thr;
-                const unsigned m = __ballot_sync(FULL, keep);
-                if (m) {
-                    if (nbuf + 32 > LB_BUF) drain();
-                    if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = make_uint2((uint32_t)r, __float_as_uint(lb));
-                    nbuf += __popc(m);
-                    __syncwarp();
-                }
+            const bool keep = ok && lb <= thr;
+            const unsigned m = __ballot_sync(FULL, keep);
+            if (m) {
+                if (nbuf + 32 > LB_BUF) drain();
+                if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = make_uint2(pos0 + r, __float_as_uint(lb));
+                nbuf += __popc(m);
+                __syncwarp();
             }
         }
+        __syncwarp();  // every lane is done with the stage before it is refilled
+    }
+    if (stalled) {
+        // a copy never completed: flag the query and wait (bounded) for the
+        // copies still in flight into this warp's stages before leaving
+        if (lane == 0) {
+            atomicOr(&c->flags, QF_STALLED);
+            for (uint32_t t = it; t < mine && t < it + LB_STAGES; ++t)
+                mbar_wait_bounded(&wbar[t % LB_STAGES], (t / LB_STAGES) & 1u, LB_WAIT);
+        }
+        __syncwarp();
     }
     drain();
 #pragma unroll
@@ -694,6 +781,19 @@ __global__ void __launch_bounds__(LB_THREADS, 4) q_series_lb_kernel(DevIndex ix,
         if (n_lb) atomicAdd(&c->series_lb, n_lb);
         if (n_leaves) atomicAdd(&c->leaves_scanned, n_leaves);
     }
+}
+
+// the scan kernels' shared-memory limit, raised once per device (before any
+// capture: scratch allocation calls this too)
+void prepare_scan_kernel(int device) {
+    if (device < 0 && cudaGetDevice(&device) != cudaSuccess) device = -1;
+    static bool done[64] = {};
+    if (device >= 0 && device < 64 && done[device]) return;
+    ISAX_CUDA_TRY(cudaFuncSetAttribute(q_series_lb_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)LB_SMEM));
+    ISAX_CUDA_TRY(cudaFuncSetAttribute(q_series_lb_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)LB_SMEM));
+    if (device >= 0 && device < 64) done[device] = true;
 }
 
 // ---------------------------------------------------------------- q_refine
@@ -1183,15 +1283,16 @@ void free_query_scratch_struct(QueryScratch& q, cudaStream_t st) {
 
 // scratch for queries on any index with at most L leaves, series length n and
 // cardinality card
-// scan work items of an index: at most one per leaf plus one per lb_chunk (>= 256) series
+// scan work items of an index: at most one per leaf plus one per LB_PIECE series
 int64_t work_items_cap(int64_t L, int64_t N) { return L + (N + 255) / 256 + 1; }
 
 void alloc_query_scratch_for(int64_t L, int64_t N, int n, int card, uint32_t cand_cap, uint32_t surv_cap,
                              QueryScratch& q, cudaStream_t st) {
+    prepare_scan_kernel(-1);
     q.q = static_cast<float*>(dev_alloc(sizeof(float) * n, st));
     q.table = static_cast<float*>(dev_alloc(sizeof(float) * W * card, st));
     q.leaf_lb = static_cast<float*>(dev_alloc(sizeof(float) * L, st));
-    q.work = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * work_items_cap(L, N), st));
+    q.work = static_cast<uint2*>(dev_alloc(sizeof(uint2) * work_items_cap(L, N), st));
     q.bin_count = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * NBINS, st));
     q.bin_cursor = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * NBINS, st));
     q.topk = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * MAX_K, st));
@@ -1337,7 +1438,6 @@ int occupancy_grid(const void* fn, int threads, size_t smem, int num_sms) {
 template <int NV>
 void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st, int mode) {
     const DevIndex& d = ix->d;
-    const size_t tab_bytes = sizeof(float) * W * d.card;
     {
         ISAX_LAUNCH("q_prep", st);
         q_prep_kernel<<<1, PREP_THREADS, 0, st>>>(d, s, k);
@@ -1362,14 +1462,13 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
         }
     }
     {
-        static int grid_lb = 0;
-        if (!grid_lb)
-            grid_lb = occupancy_grid((const void*)q_series_lb_kernel<256>, LB_THREADS, tab_bytes, ix->num_sms);
+        // one CTA per SM: its warps' copy rings take most of the SM's shared memory
+        prepare_scan_kernel(ix->device);
         ISAX_LAUNCH("q_series_lb", st);
         if (d.card == 256)
-            q_series_lb_kernel<256><<<grid_lb, LB_THREADS, tab_bytes, st>>>(d, s, k);
+            q_series_lb_kernel<256><<<ix->num_sms, LB_THREADS, LB_SMEM, st>>>(d, s, k);
         else
-            q_series_lb_kernel<0><<<grid_lb, LB_THREADS, tab_bytes, st>>>(d, s, k);
+            q_series_lb_kernel<0><<<ix->num_sms, LB_THREADS, LB_SMEM, st>>>(d, s, k);
     }
     {
         static int grid_rf = 0;
@@ -1460,6 +1559,7 @@ void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_
         ISAX_CUDA_TRY(cudaMemcpyAsync(ctl_out, ix->qs.ctl, sizeof(QCtl), cudaMemcpyDeviceToHost, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         if (ctl_out->flags & QF_NONFINITE) throw Error{ISAX_ERR_INVALID_ARG, "query contains a non-finite value"};
+        if (ctl_out->flags & QF_STALLED) throw Error{ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed"};
         if (ctl_out->flags & QF_OVERFLOW) {
             if (attempt >= 3) throw Error{ISAX_ERR_INTERNAL, "candidate buffer kept overflowing"};
             const uint64_t N = (uint64_t)ix->d.N;
@@ -1560,6 +1660,7 @@ void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t m
             nonfinite = true;
             continue;
         }
+        if (c.flags & QF_STALLED) throw Error{ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed"};
         if (c.flags & (QF_OVERFLOW | QF_SHORT)) {
             ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, Q + (size_t)b * n, sizeof(float) * n, kin, st));
             query_device(ix, k, &c, &reruns, st);

@@ -242,6 +242,8 @@ static void server_loop(isax_server* s) {
             const QCtl& c = *sl->h_ctl;
             if (c.flags & QF_NONFINITE) {
                 publish(s, sl, ISAX_ERR_INVALID_ARG);
+            } else if (c.flags & QF_STALLED) {
+                publish(s, sl, ISAX_ERR_TIMEOUT);
             } else if ((c.flags & QF_OVERFLOW) && sl->reruns < 4) {
                 const uint64_t N = (uint64_t)s->colls[sl->req.coll]->d.N;
                 if (c.cand_count > sl->qs.cand_cap) {
