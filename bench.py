@@ -16,7 +16,9 @@ queries / wall time of the timed steps, builds included); `e2e` = the same job
 through the C ABI with host buffers (the 102.4 GB collection copied from pinned
 host memory by every build, queries and answers through host memory);
 `roofline` = the dominant kernel's algorithmic bytes per launch / its mean
-CUDA-event duration; `cpu_baseline` = the CPU oracle's FP64 brute force on a
+CUDA-event duration; `scan_roofline` = the same for the lower-bound scan
+(16 B per series bounded; MESSI queries here, the ParIS flat scan under
+`ablation_flat_scan`); `cpu_baseline` = the CPU oracle's FP64 brute force on a
 sample of the same workload.  `--impl reference` times that oracle alone.
 
 With --gpus N > 1 (torchrun, one process per GPU) every rank runs the job on
@@ -158,10 +160,11 @@ class ClockSampler:
 # ------------------------------------------------------------------ roofline
 def kernel_bytes(name, a, launches, acc):
     """Algorithmic bytes of all timed launches of a kernel (None if not modelled).
-    Build kernels run once per step (rs_* once per radix pass); the scan kernel's
-    bytes come from the per-query counters: 16 B per SAX word bounded plus one
-    full row per series refined outside the approximate leaf (an upper bound:
-    early abandoning reads less)."""
+    Build kernels run once per step (rs_* once per radix pass); the query
+    kernels' bytes come from the per-query counters: 16 B per SAX word bounded
+    (q_series_lb), one full row per series refined outside the approximate leaf
+    (q_refine; an upper bound: early abandoning reads less), one row per series
+    of the approximate leaf (q_approx)."""
     N, n = a.N, a.n
     row = 4 * n
     per_launch = {
@@ -172,8 +175,10 @@ def kernel_bytes(name, a, launches, acc):
     }
     if name in per_launch:
         return per_launch[name] * launches
-    if name == "q_scan_refine":
-        return 16 * acc["series_lb"] + row * (acc["series_refined"] - acc["approx_series"])
+    if name == "q_series_lb":
+        return 16 * acc["series_lb"]
+    if name == "q_refine":
+        return row * (acc["series_refined"] - acc["approx_series"])
     if name == "q_approx":
         return row * acc["approx_series"]
     return None
@@ -218,12 +223,27 @@ def traffic_from_profile(kernel):
     return None
 
 
+def scan_roofline(prof, series_lb_total, hbm):
+    """The lower-bound scan's HBM fraction: 16 B per series bounded over the
+    traced launches / their summed CUDA-event time (events around each launch:
+    a little above the kernel's own duration)."""
+    if "q_series_lb" not in prof:
+        return None
+    cnt, ms = prof["q_series_lb"]
+    per_launch = 16 * series_lb_total / cnt
+    achieved = per_launch / (ms / cnt / 1e3) / 1e9
+    return {"kernel": "q_series_lb", "launches": cnt, "avg_launch_ms": ms / cnt,
+            "algorithmic_bytes_per_launch": per_launch, "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm}
+
+
 # ------------------------------------------------------------------ ablation
 def ablation_leg(a, X, Qd, pkg, torch, stream):
     """The step's queries answered twice on one index: MESSI (leaf envelopes
     prune leaves, leaves visited in bound order) and the ParIS flat scan (every
     series of the SAX array bounded in storage order).  Answers must agree.
-    Per-query CUDA-event latency and pruning counters."""
+    Per-query CUDA-event latency and pruning counters, then one more pass with
+    every kernel traced for the lower-bound scan's HBM fraction."""
     import numpy as np
     sp = stream.cuda_stream
     ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp)
@@ -251,6 +271,13 @@ def ablation_leg(a, X, Qd, pkg, torch, stream):
             "series_refined_per_query": float(np.mean([s["series_refined"] for s in st_all])),
             "leaves_scanned_per_query": float(np.mean([s["leaves_scanned"] for s in st_all])),
         }
+        pkg.isax_profile(1)
+        for b in range(len(Qd)):
+            fn(Qd[b], a.k, stream=sp)
+        torch.cuda.synchronize()
+        pkg.isax_profile(0)
+        out[mode]["scan_roofline"] = scan_roofline(
+            pkg.isax_profile_report(), sum(s["series_lb"] for s in st_all), peaks()[0])
     out["same_answers"] = all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
                               for x, y in zip(answers["messi"], answers["flat"]))
     out["messi_speedup"] = out["flat"]["latency_ms"]["p50"] / out["messi"]["latency_ms"]["p50"]
@@ -782,6 +809,7 @@ def main():
         "ablation_flat_scan": ablation,
         "rows_in_host_memory": host_rows,
         "kernels": kernels,
+        "scan_roofline": scan_roofline(qprof, stats_acc["series_lb"] / a.steps, hbm),
         "gpu_launches": launches,
         "clocks": clock_info,
     }

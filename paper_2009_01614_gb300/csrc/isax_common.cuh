@@ -107,8 +107,9 @@ struct QueryScratch {
     float* q;                      // [n]
     float* table;                  // [16][card] lower-bound table
     float* leaf_lb;                // [L]
-    uint2* work;                   // [work_items_cap] scan items {first row, rows | leaf-start bit 31},
+    uint2* work;                   // [work_cap] scan items {first row, rows | leaf-start bit 31},
                                    // ordered by bin
+    uint32_t work_cap;
     uint32_t* bin_count;           // [NBINS]
     uint32_t* bin_cursor;          // [NBINS]
     unsigned long long* topk;      // [MAX_K] packed (fp32 d2 bits << 32 | orig)

@@ -81,6 +81,7 @@ QueryScratch scratch_view(unsigned char* base) {
     s.table = reinterpret_cast<float*>(base + OFF_TABLE);
     s.leaf_lb = reinterpret_cast<float*>(base + OFF_LEAF_LB);
     s.work = reinterpret_cast<uint2*>(base + OFF_WORK);
+    s.work_cap = MAX_WORK;
     s.bin_count = reinterpret_cast<uint32_t*>(base + OFF_BIN_COUNT);
     s.bin_cursor = reinterpret_cast<uint32_t*>(base + OFF_BIN_CURSOR);
     s.topk = reinterpret_cast<unsigned long long*>(base + OFF_TOPK);

@@ -593,17 +593,19 @@ __device__ __forceinline__ void warp_d2_four(const DevIndex& ix, const uint2 (&e
 // ---------------------------------------------------------------- q_series_lb
 // The lower-bound scan (MESSI's lower-bound calculations).  Work item i of the
 // list (a piece of at most LB_PIECE rows of a queued leaf, in ascending leaf
-// bound for MESSI, storage order for the flat scan) belongs to warp i mod W of
-// the grid.  Each warp streams its pieces' 16-byte SAX words through a private
-// ring of LB_STAGES shared-memory stages filled by bulk copies (the TMA engine,
+// bound for MESSI, storage order for the flat scan) belongs to CTA i mod G,
+// whose warps take its items in list order from a shared-memory counter.  Each
+// warp streams its pieces' 16-byte SAX words through a private ring of
+// LB_STAGES shared-memory stages filled by bulk copies (the TMA engine,
 // completion counted on one mbarrier per stage), LB_STAGES - 1 pieces ahead of
 // the one it bounds, so HBM sees many copies in flight while the warp works
-// from shared memory.  A series is bounded from the table (in shared memory,
-// 1 KB-aligned rows) against the threshold the approximate answer set: the
-// first 8 segments first, the other 8 only when some lane of the warp is still
-// under the threshold (the sum runs in segment order either way, so the bound
-// is the same).  Survivors {position, bound} are buffered per warp and
-// appended with one atomic per batch.
+// from shared memory; the first copies start before the table is staged.  A
+// series is bounded from the table (in shared memory, 1 KB-aligned rows)
+// against the threshold the approximate answer set: the first 8 segments
+// first, then 4 more and the last 4, each step only while some lane of the
+// warp is still under the threshold (the sum runs in segment order either way,
+// so the bound is the same).  Survivors {position, bound} are buffered per warp and appended with
+// one atomic per batch.
 constexpr int LB_THREADS = 512;
 constexpr int LB_WARPS = LB_THREADS / 32;
 constexpr int LB_STAGES = 3;
@@ -613,7 +615,7 @@ constexpr uint32_t LB_WAIT = 1u << 22;  // bounded wait on a stage's copy
 constexpr size_t LB_TAB_BYTES = sizeof(float) * W * MAX_CARD;
 constexpr size_t LB_RING_BYTES = (size_t)LB_WARPS * LB_STAGES * LB_PIECE * sizeof(uint4);
 constexpr size_t LB_SMEM = 1024 + LB_TAB_BYTES + LB_RING_BYTES + sizeof(uint64_t) * LB_WARPS * LB_STAGES +
-                           sizeof(uint2) * LB_WARPS * LB_BUF + 16;
+                           sizeof(uint2) * LB_WARPS * (LB_STAGES + LB_BUF) + 16;
 
 template <int OFF>
 __device__ __forceinline__ float lds_f32(uint32_t addr) {
@@ -637,41 +639,79 @@ template <int CARD>
 __global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix, QueryScratch s, int k) {
     extern __shared__ unsigned char lb_smem_raw[];
     QCtl* c = s.ctl;
-    if (c->flags & QF_NONFINITE) return;
     unsigned char* sm = lb_smem_raw + ((1024u - (smem_u32(lb_smem_raw) & 1023u)) & 1023u);
     float* tab = reinterpret_cast<float*>(sm);
     uint4* ring = reinterpret_cast<uint4*>(sm + LB_TAB_BYTES);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + LB_TAB_BYTES + LB_RING_BYTES);
-    uint2* bufs = reinterpret_cast<uint2*>(bars + LB_WARPS * LB_STAGES);
+    uint2* metas = reinterpret_cast<uint2*>(bars + LB_WARPS * LB_STAGES);
+    uint2* bufs = metas + LB_WARPS * LB_STAGES;
     float* thr_p = reinterpret_cast<float*>(bufs + LB_WARPS * LB_BUF);
+    uint32_t* next_p = reinterpret_cast<uint32_t*>(thr_p + 1);
     const int card = ix.card;
-    {   // the table into shared memory: 16-byte loads, all issued before the stores
-        const float4* src = reinterpret_cast<const float4*>(s.table);
-        float4* dst = reinterpret_cast<float4*>(tab);
-        const int nv = W * card / 4;
-        float4 v[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4* wring = ring + (size_t)warp * LB_STAGES * LB_PIECE;
+    uint64_t* wbar = bars + warp * LB_STAGES;
+    uint2* wmeta = metas + warp * LB_STAGES;
+    const uint32_t G = gridDim.x;
+    // everything the start needs is loaded at once: the flags, the item count,
+    // this warp's first LB_STAGES items of the CTA (items warp * LB_STAGES + t,
+    // read within the list's capacity and used only if below the count), the
+    // threshold and the table
+    const uint32_t flags = c->flags;
+    const uint32_t count = c->work_count;
+    uint2 e[LB_STAGES];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int e = threadIdx.x + t * LB_THREADS;
-            if (e < nv) v[t] = src[e];
-        }
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int e = threadIdx.x + t * LB_THREADS;
-            if (e < nv) dst[e] = v[t];
-        }
+    for (int t = 0; t < LB_STAGES; ++t) {
+        const size_t i = blockIdx.x + (size_t)(warp * LB_STAGES + t) * G;
+        e[t] = lane == 0 && i < s.work_cap ? s.work[i] : make_uint2(0u, 0u);
     }
-    if (threadIdx.x < LB_WARPS * LB_STAGES) mbar_init(&bars[threadIdx.x], 1);
-    if (threadIdx.x == 0) {
-        *thr_p = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), c->delta, c->E);
+    const float4* tsrc = reinterpret_cast<const float4*>(s.table);
+    const int nv = W * card / 4;
+    constexpr int TV = (W * MAX_CARD / 4 + LB_THREADS - 1) / LB_THREADS;
+    float4 tv[TV];
+#pragma unroll
+    for (int t = 0; t < TV; ++t) {
+        const int i = threadIdx.x + t * LB_THREADS;
+        if (i < nv) tv[t] = tsrc[i];
+    }
+    if (flags & QF_NONFINITE) return;
+    const uint32_t mine = count > blockIdx.x ? (count - blockIdx.x + G - 1) / G : 0u;  // this CTA's items
+    // lane 0 starts the copy of a piece into stage st
+    auto issue = [&](uint32_t st, uint2 p) {
+        const uint32_t rows = p.y & 0x7FFFFFFFu;
+        wmeta[st] = p;
+        mbar_arrive_expect_tx(&wbar[st], rows * (uint32_t)sizeof(uint4));
+        if (rows) bulk_load(wring + st * LB_PIECE, ix.sax + p.x, rows * (uint32_t)sizeof(uint4), &wbar[st]);
+    };
+    // the warp's own stage barriers, then its first LB_STAGES - 1 pieces; the
+    // last of its first LB_STAGES is held until a stage frees up
+    uint32_t issued = 0;
+    const uint32_t j0 = warp * LB_STAGES;
+    if (lane == 0) {
+#pragma unroll
+        for (int t = 0; t < LB_STAGES; ++t) mbar_init(&wbar[t], 1);
         mbar_fence_init();
+#pragma unroll
+        for (int t = 0; t + 1 < LB_STAGES; ++t)
+            if (j0 + t < mine) issue(t, e[t]);
+    }
+#pragma unroll
+    for (int t = 0; t + 1 < LB_STAGES; ++t) issued += j0 + t < mine ? 1u : 0u;
+    uint2 pend = e[LB_STAGES - 1];
+    bool pend_ok = j0 + LB_STAGES - 1 < mine;
+    float4* tdst = reinterpret_cast<float4*>(tab);
+#pragma unroll
+    for (int t = 0; t < TV; ++t) {
+        const int i = threadIdx.x + t * LB_THREADS;
+        if (i < nv) tdst[i] = tv[t];
+    }
+    if (threadIdx.x == 0) {
+        *next_p = LB_WARPS * LB_STAGES;  // the items after the warps' first ones go by claim
+        *thr_p = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), c->delta, c->E);
     }
     __syncthreads();
     const float thr = *thr_p;
     const uint32_t tab_sa = smem_u32(tab);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint4* wring = ring + (size_t)warp * LB_STAGES * LB_PIECE;
-    uint64_t* wbar = bars + warp * LB_STAGES;
     uint2* buf = bufs + warp * LB_BUF;
     int nbuf = 0;  // warp-uniform
     // the buffered survivors go to the global list in one append
@@ -686,69 +726,56 @@ __global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix,
         __syncwarp();
         nbuf = 0;
     };
-    const uint32_t count = c->work_count;
-    const uint32_t gw = blockIdx.x * LB_WARPS + warp;
-    const uint32_t nw = gridDim.x * LB_WARPS;
-    const uint32_t mine = gw < count ? (count - gw + nw - 1) / nw : 0u;  // this warp's pieces
-    // piece t of this warp is work[gw + t * nw]; lane j holds piece 32 b + j of
-    // the current block b and of the next one, loaded a block ahead
-    auto piece_of = [&](uint32_t t) -> uint2 {
-        return t < mine ? s.work[gw + (size_t)t * nw] : make_uint2(0u, 0u);
-    };
-    uint2 cur = piece_of(lane), nxt = piece_of(32 + lane);
-    auto piece = [&](uint32_t t, uint32_t t_block0) -> uint2 {  // warp-wide, t warp-uniform
-        if (t - t_block0 < 32)
-            return make_uint2(__shfl_sync(FULL, cur.x, t & 31), __shfl_sync(FULL, cur.y, t & 31));
-        return make_uint2(__shfl_sync(FULL, nxt.x, t & 31), __shfl_sync(FULL, nxt.y, t & 31));
-    };
-    // lane 0 starts the copy of piece t into stage t % LB_STAGES
-    auto issue = [&](uint32_t t, uint2 p) {
-        if (lane == 0) {
-            const uint32_t rows = p.y & 0x7FFFFFFFu;
-            uint64_t* bar = &wbar[t % LB_STAGES];
-            mbar_arrive_expect_tx(bar, rows * (uint32_t)sizeof(uint4));
-            if (rows)
-                bulk_load(wring + (t % LB_STAGES) * LB_PIECE, ix.sax + p.x, rows * (uint32_t)sizeof(uint4), bar);
-        }
-    };
     unsigned long long n_lb = 0, n_leaves = 0;
-    for (uint32_t t = 0; t + 1 < LB_STAGES && t < mine; ++t) issue(t, piece(t, 0));
     bool stalled = false;
-    uint32_t it = 0;
-    for (; it < mine; ++it) {
-        const uint32_t block0 = it & ~31u;
-        if (it && (it & 31u) == 0) {
-            cur = nxt;
-            nxt = piece_of(it + 32 + lane);
+    uint32_t done = 0;  // warp-uniform, like issued and pend_ok
+    for (;;) {
+        if (pend_ok) {
+            // the stage of piece `issued` held piece issued - LB_STAGES, already bounded
+            if (lane == 0) issue(issued % LB_STAGES, pend);
+            ++issued;
+            uint32_t j = 0;
+            if (lane == 0) j = atomicAdd(next_p, 1u);
+            j = __shfl_sync(FULL, j, 0);
+            pend_ok = j < mine;
+            if (lane == 0 && pend_ok) pend = s.work[blockIdx.x + (size_t)j * G];
         }
-        const uint2 p = piece(it, block0);
-        if (it + LB_STAGES - 1 < mine) issue(it + LB_STAGES - 1, piece(it + LB_STAGES - 1, block0));
-        if (!__all_sync(FULL, mbar_wait_bounded(&wbar[it % LB_STAGES], (it / LB_STAGES) & 1u, LB_WAIT))) {
+        if (done == issued) break;
+        const uint32_t st = done % LB_STAGES;
+        if (!__all_sync(FULL, mbar_wait_bounded(&wbar[st], (done / LB_STAGES) & 1u, LB_WAIT))) {
             stalled = true;
             break;
         }
+        const uint2 p = wmeta[st];
         const uint32_t rows = p.y & 0x7FFFFFFFu, pos0 = p.x;
         if (lane == 0) {
             n_lb += rows;
             n_leaves += p.y >> 31;
         }
-        const uint4* src = wring + (it % LB_STAGES) * LB_PIECE;
+        const uint4* src = wring + st * LB_PIECE;
         uint4 w[LB_PER_LANE];
 #pragma unroll
         for (int j = 0; j < LB_PER_LANE; ++j) {
             const uint32_t r = j * 32 + lane;
             w[j] = r < rows ? src[r] : make_uint4(0u, 0u, 0u, 0u);
         }
+        // the first 8 segments of every row of the lane at once (independent
+        // chains), then per row the rest, 4 segments at a time, while some lane
+        // of the warp is still under the threshold
+        float part[LB_PER_LANE];
+#pragma unroll
+        for (int j = 0; j < LB_PER_LANE; ++j)
+            part[j] = CARD == 256 ? lb_word256<1>(lb_word256<0>(0.0f, w[j].x, tab_sa), w[j].y, tab_sa) : 0.0f;
 #pragma unroll
         for (int j = 0; j < LB_PER_LANE; ++j) {
             const uint32_t r = j * 32 + lane;
             const bool ok = r < rows;
             float lb;
             if constexpr (CARD == 256) {
-                lb = lb_word256<0>(0.0f, w[j].x, tab_sa);
-                lb = lb_word256<1>(lb, w[j].y, tab_sa);
+                lb = part[j];
                 if (!__any_sync(FULL, ok && lb <= thr)) continue;
                 lb = lb_word256<2>(lb, w[j].z, tab_sa);
+                if (!__any_sync(FULL, ok && lb <= thr)) continue;
                 lb = lb_word256<3>(lb, w[j].w, tab_sa);
             } else {
                 lb = series_lb<CARD>(w[j], tab, card);
@@ -762,14 +789,15 @@ __global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix,
                 __syncwarp();
             }
         }
+        ++done;
         __syncwarp();  // every lane is done with the stage before it is refilled
     }
     if (stalled) {
         // a copy never completed: flag the query and wait (bounded) for the
-        // copies still in flight into this warp's stages before leaving
+        // other copies still in flight into this warp's stages before leaving
         if (lane == 0) {
             atomicOr(&c->flags, QF_STALLED);
-            for (uint32_t t = it; t < mine && t < it + LB_STAGES; ++t)
+            for (uint32_t t = done + 1; t < issued; ++t)
                 mbar_wait_bounded(&wbar[t % LB_STAGES], (t / LB_STAGES) & 1u, LB_WAIT);
         }
         __syncwarp();
@@ -1292,7 +1320,8 @@ void alloc_query_scratch_for(int64_t L, int64_t N, int n, int card, uint32_t can
     q.q = static_cast<float*>(dev_alloc(sizeof(float) * n, st));
     q.table = static_cast<float*>(dev_alloc(sizeof(float) * W * card, st));
     q.leaf_lb = static_cast<float*>(dev_alloc(sizeof(float) * L, st));
-    q.work = static_cast<uint2*>(dev_alloc(sizeof(uint2) * work_items_cap(L, N), st));
+    q.work_cap = (uint32_t)work_items_cap(L, N);
+    q.work = static_cast<uint2*>(dev_alloc(sizeof(uint2) * q.work_cap, st));
     q.bin_count = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * NBINS, st));
     q.bin_cursor = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * NBINS, st));
     q.topk = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long) * MAX_K, st));
