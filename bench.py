@@ -209,21 +209,23 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel):
+def traffic_from_profile(kernel, label=None):
     """dram bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (its hash is recorded next to the figure)."""
+    the current kernel source (its hash is recorded next to the figure); label
+    picks one of several workloads of the same kernel."""
     digest = kernel_source_hash(kernel)
+    label = label or kernel
     prof = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(prof):
         return None
     for line in open(prof):
         parts = line.split()
-        if len(parts) >= 4 and parts[0] == kernel and parts[1] == digest:
+        if len(parts) >= 4 and parts[0] == label and parts[1] == digest:
             return float(parts[2]), parts[3]
     return None
 
 
-def scan_roofline(prof, series_lb_total, hbm):
+def scan_roofline(prof, series_lb_total, hbm, workload):
     """The lower-bound scan's HBM fraction: 16 B per series bounded over the
     traced launches / their summed CUDA-event time (events around each launch:
     a little above the kernel's own duration)."""
@@ -232,9 +234,11 @@ def scan_roofline(prof, series_lb_total, hbm):
     cnt, ms = prof["q_series_lb"]
     per_launch = 16 * series_lb_total / cnt
     achieved = per_launch / (ms / cnt / 1e3) / 1e9
-    return {"kernel": "q_series_lb", "launches": cnt, "avg_launch_ms": ms / cnt,
+    tr = traffic_from_profile("q_series_lb", "q_series_lb:" + workload)
+    return {"kernel": "q_series_lb", "bound": "hbm", "launches": cnt, "avg_launch_ms": ms / cnt,
             "algorithmic_bytes_per_launch": per_launch, "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm}
+            "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None}
 
 
 # ------------------------------------------------------------------ ablation
@@ -277,7 +281,8 @@ def ablation_leg(a, X, Qd, pkg, torch, stream):
         torch.cuda.synchronize()
         pkg.isax_profile(0)
         out[mode]["scan_roofline"] = scan_roofline(
-            pkg.isax_profile_report(), sum(s["series_lb"] for s in st_all), peaks()[0])
+            pkg.isax_profile_report(), sum(s["series_lb"] for s in st_all), peaks()[0],
+            "%s_%dMx%d" % (mode, a.N // 1000000, a.n))
     out["same_answers"] = all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
                               for x, y in zip(answers["messi"], answers["flat"]))
     out["messi_speedup"] = out["flat"]["latency_ms"]["p50"] / out["messi"]["latency_ms"]["p50"]
@@ -809,7 +814,8 @@ def main():
         "ablation_flat_scan": ablation,
         "rows_in_host_memory": host_rows,
         "kernels": kernels,
-        "scan_roofline": scan_roofline(qprof, stats_acc["series_lb"] / a.steps, hbm),
+        "scan_roofline": scan_roofline(qprof, stats_acc["series_lb"] / a.steps, hbm,
+                                       "messi_%dMx%d" % (a.N // 1000000, a.n)),
         "gpu_launches": launches,
         "clocks": clock_info,
     }
