@@ -4,12 +4,16 @@ GPU iSAX index.
 
 Workload (one "step" = the whole hot path once): build the index over
 100,000,000 z-normalised random walks of length 256 fp32 (w = 16, cardinality
-256, leaf size 2000: PAA + SAX summarisation, radix bucketing, leaves, permute,
-envelopes), then answer 100 exact 1-NN queries one by one (90 fresh random
-walks + 10 collection members with N(0, 0.01^2) noise, re-normalised).  The
-collection is generated on the device by the seeded generator before timing and
-is resident in HBM when the timed region starts; it is larger than L2, and
-every build streams all of it.
+256, leaf size 2000: PAA + SAX summarisation, radix bucketing, leaves, SAX
+words and ids into leaf order, envelopes), then answer 100 exact 1-NN queries
+one by one (90 fresh random walks + 10 collection members with N(0, 0.01^2)
+noise, re-normalised).  The collection is generated on the device by the seeded
+generator before timing and is resident in HBM when the timed region starts;
+it is larger than L2, and every build streams all of it.  By default the index
+reads the rows in the collection array itself (`--rows in-place`: the paper's
+in-memory layout, leaves hold iSAX words and row ids); `--rows copy` makes
+every build also copy the rows into leaf order, and the JSON line reports that
+variant too (`rows_copied`).
 
 Printed JSON line: `value` = queries per second of the whole job (all ranks'
 queries / wall time of the timed steps, builds included); `e2e` = the same job
@@ -68,6 +72,9 @@ def parse():
                     help="skip the leg with the index's rows in host memory")
     ap.add_argument("--workload", choices=["walk", "hardness", "serving"], default="walk",
                     help="hardness: the sinusoid collection, member queries by noise level and k")
+    ap.add_argument("--rows", choices=["in-place", "copy"], default="in-place",
+                    help="in-place: the index reads the rows in the collection array by row id "
+                         "(nothing copied); copy: each build also copies the rows into leaf order")
     ap.add_argument("--batch", type=int, default=1024,
                     help="batched leg: time the plain and the BF16-filtered batch paths on "
                          "batches of this size and of 4x this size, k = 1 and 10 (0: skip)")
@@ -82,6 +89,8 @@ def workload_config(a):
                         a.N, a.n, a.leaf, a.queries, a.k, a.queries - a.queries // 10,
                         a.queries // 10),
         "N": a.N, "n": a.n, "w": 16, "cardinality": 256, "leaf_size": a.leaf, "k": a.k,
+        "rows": ("read in place in the collection array by row id (leaves hold iSAX words and "
+                 "row ids)" if a.rows == "in-place" else "copied into leaf order by every build"),
         "queries_per_step": a.queries,
         "l2": "inputs larger than L2: the %.1f GB collection is streamed by every build"
               % (a.N * a.n * 4 / 1e9),
@@ -172,6 +181,7 @@ def kernel_bytes(name, a, launches, acc):
         "summarize": N * (row + 16 + 8 + 4),         # rows read; SAX, key, id written
         "rs_scatter": N * (8 + 4) * 2,               # keys and ids read and written
         "rs_hist": N * 8,
+        "permute_sax": N * (4 + 2 * 16 + 4),         # ids read, SAX words gathered, ids written
     }
     if name in per_launch:
         return per_launch[name] * launches
@@ -190,11 +200,14 @@ def kernel_source_hash(kernel):
     isax_query.cu, tc_* in isax_tc.cu, the rest in isax_build.cu) and the shared
     device-helper header."""
     import re
+    kernel = {"summarize": "summarize_vec"}.get(kernel, kernel)  # launch name -> kernel name
     src = os.path.join(ROOT, "paper_2009_01614_gb300", "csrc")
     own = ("isax_query.cu" if kernel.startswith(("q_", "bq_")) else
            "isax_tc.cu" if kernel.startswith("tc_") else "isax_build.cu")
     text = open(os.path.join(src, own)).read()
     m = re.search(r"__global__[^;{]*?\b%s_kernel\s*\(" % re.escape(kernel), text)
+    if m is None:
+        raise KeyError("no __global__ definition of %s_kernel in %s" % (kernel, own))
     body = ""
     if m:
         i = text.index("{", m.end())
@@ -213,7 +226,10 @@ def traffic_from_profile(kernel, label=None):
     """dram bytes per launch from a committed ncu summary, if it was taken on
     the current kernel source (its hash is recorded next to the figure); label
     picks one of several workloads of the same kernel."""
-    digest = kernel_source_hash(kernel)
+    try:
+        digest = kernel_source_hash(kernel)
+    except KeyError:
+        return None
     label = label or kernel
     prof = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(prof):
@@ -250,7 +266,7 @@ def ablation_leg(a, X, Qd, pkg, torch, stream):
     every kernel traced for the lower-bound scan's HBM fraction."""
     import numpy as np
     sp = stream.cuda_stream
-    ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp)
+    ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp, rows_in_place=a.rows == "in-place")
     out = {}
     answers = {}
     for mode in ("messi", "flat"):
@@ -288,6 +304,34 @@ def ablation_leg(a, X, Qd, pkg, torch, stream):
     out["messi_speedup"] = out["flat"]["latency_ms"]["p50"] / out["messi"]["latency_ms"]["p50"]
     ix.close()
     return out
+
+
+# ------------------------------------------------------------------ rows copied by the build
+def copy_leg(a, X, Qd, pkg, torch, stream):
+    """The step with the other rows mode (by default: every build also copies
+    the rows into leaf order), timed the same way: one warm-up step, then
+    `steps` steps, CUDA events around the build and around the whole step, a
+    host synchronisation after every query as in the main loop."""
+    sp = stream.cuda_stream
+    other = "copy" if a.rows == "in-place" else "in-place"
+    build, total = [], []
+    for it in range(a.steps + 1):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp, rows_in_place=other == "in-place")
+        e1.record(stream)
+        for b in range(len(Qd)):
+            ix.query(Qd[b], a.k, stream=sp)
+            stream.synchronize()
+        e2.record(stream)
+        e2.synchronize()
+        ix.close()
+        if it > 0:
+            build.append(e0.elapsed_time(e1))
+            total.append(e0.elapsed_time(e2))
+    ms = sum(total) / len(total)
+    return {"rows": other, "ms_per_step": ms, "value": len(Qd) / (ms / 1e3), "unit": "queries/s",
+            "build_ms": sum(build) / len(build), "steps": a.steps, "warmup": 1}
 
 
 # ------------------------------------------------------------------ rows in host memory
@@ -347,7 +391,7 @@ def batch_leg(a, X, pkg, torch, stream, rank):
     import numpy as np
     sp = stream.cuda_stream
     N, n = a.N, a.n
-    ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp)
+    ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp, rows_in_place=a.rows == "in-place")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ix.prepare_bf16(stream=sp)
@@ -701,8 +745,8 @@ def main():
     stats_acc = {"series_lb": 0, "series_refined": 0, "approx_series": 0, "leaves_queued": 0,
                  "leaves_scanned": 0, "candidates": 0, "window": 0}
 
-    def step(record):
-        ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp)
+    def step(record, rows=a.rows):
+        ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp, rows_in_place=rows == "in-place")
         for b in range(a.queries):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -782,6 +826,9 @@ def main():
             entry["GB_per_s"] = round(b / (ms / 1e3) / 1e9, 1)
         kernels[nm] = entry
 
+    # the same step with the other rows mode
+    rows_other = copy_leg(a, X, Qd, pkg, torch, stream)
+
     # the ParIS flat scan against MESSI's pruned, ordered search, same queries and index
     ablation = ablation_leg(a, X, Qd, pkg, torch, stream)
 
@@ -811,6 +858,7 @@ def main():
         "index": {"leaves": info["leaves"], "max_leaf": info["max_leaf"]},
         "pruning": {key + "_per_query": stats_acc[key] / max(1, len(lat_ms)) for key in stats_acc},
         "batch": batch_info,
+        "rows_copied" if a.rows == "in-place" else "rows_in_place": rows_other,
         "ablation_flat_scan": ablation,
         "rows_in_host_memory": host_rows,
         "kernels": kernels,

@@ -47,13 +47,24 @@ typedef enum isax_status {
  * design with the raw data in host memory, Section V).  The build itself still
  * stages the rows in device memory. */
 #define ISAX_BUILD_ROWS_HOST 4u
+/* build only, with ISAX_MEM_INPUT_DEVICE: the index keeps a pointer to the
+ * caller's device array `series` and reads the rows there, by original row
+ * index, for the rest of its life; it copies none of them.  This is the paper's
+ * in-memory layout (Section III: the raw series stay in the RawData array and
+ * each leaf holds the series' iSAX words and pointers into it, Section II).
+ * The array must stay allocated and unchanged until isax_free_index; the index
+ * owns only its SAX words, ids, leaf boundaries and envelopes.  Without this
+ * flag the build copies the rows into leaf order and the caller may free
+ * `series` when the call returns.  Not combinable with ISAX_BUILD_ROWS_HOST. */
+#define ISAX_BUILD_ROWS_IN_PLACE 8u
 
 typedef struct isax_build_params {
     int32_t w;           /* segments; must be ISAX_W (16) */
     int32_t cardinality; /* symbols per segment: power of two in [2, 256] (256 = 8-bit SAX) */
     int32_t leaf_size;   /* leaf capacity, >= 1 (runs of identical keys are cut into pieces of this size) */
     uint32_t mem_flags;  /* ISAX_MEM_INPUT_DEVICE if `series` is a device pointer;
-                            ISAX_BUILD_ROWS_HOST to keep the rows in host memory */
+                            ISAX_BUILD_ROWS_HOST to keep the rows in host memory;
+                            ISAX_BUILD_ROWS_IN_PLACE to read them in the caller's array */
 } isax_build_params;
 
 typedef struct isax_query_stats {

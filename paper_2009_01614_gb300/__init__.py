@@ -27,6 +27,7 @@ __all__ = [
 
 W = 16
 BUILD_ROWS_HOST = 4
+BUILD_ROWS_IN_PLACE = 8
 MAX_K = 1024
 MAX_LEN = 4096
 MEM_INPUT_DEVICE = 1
@@ -344,16 +345,24 @@ class Index:
     ``Index(series, cardinality=256, leaf_size=2000)`` builds from a float32
     [N, n] numpy array (host) or torch tensor (host or CUDA).  With
     ``rows_on_host=True`` the leaf-ordered rows live in pinned host memory after
-    the build (ISAX_BUILD_ROWS_HOST)."""
+    the build (ISAX_BUILD_ROWS_HOST).  With ``rows_in_place=True`` (a contiguous
+    CUDA tensor) the index reads the rows in ``series`` itself and copies none
+    (ISAX_BUILD_ROWS_IN_PLACE); it keeps a reference to the tensor, which must not
+    be modified while the index lives."""
 
-    def __init__(self, series, cardinality=256, leaf_size=2000, stream=None, rows_on_host=False):
+    def __init__(self, series, cardinality=256, leaf_size=2000, stream=None, rows_on_host=False,
+                 rows_in_place=False):
         ptr, on_dev, keep, shape = _buffer(series)
         if len(shape) != 2:
             raise ValueError("series must be 2-D [N, n]")
+        if rows_in_place and (not on_dev or keep is not series):
+            raise ValueError("rows_in_place needs a contiguous float32 CUDA tensor")
         N, n = shape
-        flags = (MEM_INPUT_DEVICE if on_dev else 0) | (BUILD_ROWS_HOST if rows_on_host else 0)
+        flags = ((MEM_INPUT_DEVICE if on_dev else 0) | (BUILD_ROWS_HOST if rows_on_host else 0) |
+                 (BUILD_ROWS_IN_PLACE if rows_in_place else 0))
         p = BuildParams(W, cardinality, leaf_size, flags)
         self._h = None
+        self._rows = keep if rows_in_place else None
         self._h = isax_build_index(ptr, N, n, p, _stream_of(keep, stream))
         self.N, self.n = N, n
         self.cardinality, self.leaf_size = cardinality, leaf_size
@@ -362,6 +371,7 @@ class Index:
         if self._h:
             isax_free_index(self._h)
             self._h = None
+        self._rows = None
 
     def __del__(self):
         try:

@@ -191,8 +191,13 @@ isax_status isax_build_index(const float* series, int64_t N, int32_t n, const is
         check(prm.w == ISAX_W, "w must be 16");
         check_card(prm.cardinality);
         check(prm.leaf_size >= 1, "leaf_size must be >= 1");
-        check((prm.mem_flags & ~(uint32_t)(ISAX_MEM_INPUT_DEVICE | ISAX_BUILD_ROWS_HOST)) == 0,
+        check((prm.mem_flags & ~(uint32_t)(ISAX_MEM_INPUT_DEVICE | ISAX_BUILD_ROWS_HOST |
+                                           ISAX_BUILD_ROWS_IN_PLACE)) == 0,
               "unknown mem_flags bits");
+        check(!(prm.mem_flags & ISAX_BUILD_ROWS_IN_PLACE) || (prm.mem_flags & ISAX_MEM_INPUT_DEVICE),
+              "ISAX_BUILD_ROWS_IN_PLACE needs device-resident series (ISAX_MEM_INPUT_DEVICE)");
+        check(!((prm.mem_flags & ISAX_BUILD_ROWS_IN_PLACE) && (prm.mem_flags & ISAX_BUILD_ROWS_HOST)),
+              "ISAX_BUILD_ROWS_IN_PLACE and ISAX_BUILD_ROWS_HOST exclude each other");
         check(aligned16(series), "series must be 16-byte aligned");
         cudaStream_t st = (cudaStream_t)cuda_stream;
         *out = build_index_impl(series, N, n, prm.cardinality, prm.leaf_size, prm.mem_flags, st);

@@ -729,6 +729,20 @@ __global__ void __launch_bounds__(PM_THREADS) permute_kernel(const float* __rest
     }
 }
 
+// SAX words and original ids alone into leaf order, for an index that reads
+// the caller's rows in place: thread per position.
+__global__ void __launch_bounds__(256) permute_sax_kernel(const uint32_t* __restrict__ ids, int64_t N,
+                                                         const uint4* __restrict__ sax_in,
+                                                         uint4* __restrict__ sax_out,
+                                                         uint32_t* __restrict__ orig) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t src = ids[r];
+        sax_out[r] = sax_in[src];
+        orig[r] = src;
+    }
+}
+
 // The same gather with plain 16-byte loads and stores, one warp per row, for
 // an index whose rows live in host memory: the output (and the input, when it
 // is host memory) is reached over the CPU-GPU link, where many independent
@@ -865,6 +879,7 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
 
         const float* xin = series;
         const bool rows_host = (mem_flags & ISAX_BUILD_ROWS_HOST) != 0;
+        const bool in_place = (mem_flags & ISAX_BUILD_ROWS_IN_PLACE) != 0;
         if (!(mem_flags & ISAX_MEM_INPUT_DEVICE)) {
             if (rows_host) {
                 // read in place over the CPU-GPU link: page-lock it for the build if the
@@ -987,7 +1002,13 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         // permute rows and SAX words into leaf order
         ix->sax = static_cast<uint4*>(dev_alloc((size_t)N * sizeof(uint4), st));
         ix->orig = static_cast<uint32_t*>(dev_alloc((size_t)N * sizeof(uint32_t), st));
-        if (rows_host) {
+        if (in_place) {
+            // the caller's rows stay where they are, read by original id
+            ix->x = const_cast<float*>(series);
+            ix->rows_in_place = true;
+            ISAX_LAUNCH("permute_sax", st);
+            permute_sax_kernel<<<num_sms * 8, 256, 0, st>>>(vA, N, sax_tmp, ix->sax, ix->orig);
+        } else if (rows_host) {
             // leaf-ordered rows in pinned host memory (unified addressing: the host
             // pointer is valid on the device)
             float* xh = nullptr;
@@ -1047,10 +1068,11 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         d.leaf_key = ix->leaf_key;
         d.bp = ix->bp;
         d.maxabs = maxabs;
+        d.rows_in_place = in_place ? 1 : 0;
         ix->max_leaf = (int32_t)hm[2];
         ix->bytes = (int64_t)N * n * 4 + N * 16 + N * 4 + ((int64_t)L + 1) * 4 + (int64_t)L * 40 +
                     (card + 1) * 4;
-        if (rows_host) ix->bytes -= (int64_t)N * n * 4;
+        if (rows_host || in_place) ix->bytes -= (int64_t)N * n * 4;
         alloc_query_scratch(ix, (uint32_t)std::min<int64_t>(N, 1 << 20), default_surv_cap(N), st);
     } catch (...) {
         free_index_arrays(ix, st);

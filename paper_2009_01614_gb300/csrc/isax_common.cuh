@@ -64,7 +64,8 @@ struct DevIndex {
     int64_t N;
     int32_t n, card, cbits, keybits, leaf_size;
     int64_t L;                    // leaves
-    const float* x;               // [N][n] rows in leaf order
+    const float* x;               // [N][n] rows: in leaf order, or the caller's rows in their
+                                  // original order when rows_in_place
     const uint4* sax;             // [N] 16 symbols per series, leaf order
     const uint32_t* orig;         // [N] original row of each position
     const uint32_t* leaf_begin;   // [L+1]
@@ -72,7 +73,17 @@ struct DevIndex {
     const unsigned long long* leaf_key;  // [L] key of the first series of each leaf
     const float* bp;              // [card+1] breakpoints: -inf, beta_1 .. beta_{card-1}, +inf
     float maxabs;                 // max |x| over the collection
+    int32_t rows_in_place;        // x is the caller's array, indexed by original id
 };
+
+// row of x that holds the series at leaf-order position pos
+__device__ __forceinline__ uint32_t row_at(const DevIndex& ix, int64_t pos) {
+    return ix.rows_in_place ? ix.orig[pos] : (uint32_t)pos;
+}
+// original id of the series in row r of x
+__device__ __forceinline__ uint32_t id_of_row(const DevIndex& ix, uint32_t r) {
+    return ix.rows_in_place ? r : ix.orig[r];
+}
 
 // Per-query control block (device).
 struct QCtl {
@@ -116,7 +127,7 @@ struct QueryScratch {
     unsigned long long* cand_key;  // [cap]
     uint32_t* cand_pos;            // [cap]
     uint32_t cand_cap;
-    uint2* surv;                   // [surv_cap] series that passed the bound: {position, bound bits}
+    uint2* surv;                   // [surv_cap] series that passed the bound: {row of x, bound bits}
     uint32_t surv_cap;
     QCtl* ctl;
     int64_t* out_idx;              // [MAX_K]
@@ -206,4 +217,5 @@ struct isax_index {
     void* pool;    // extra query slots for concurrent batches (isax_query.cu)
     void* tc;      // BF16 copy and batch scratch of the tensor-core filter (isax_tc.cu)
     bool rows_host;  // x is pinned host memory (ISAX_BUILD_ROWS_HOST)
+    bool rows_in_place;  // x is the caller's device array, not owned (ISAX_BUILD_ROWS_IN_PLACE)
 };

@@ -14,7 +14,7 @@
 //                 warps in that order; each warp streams its pieces' 16-byte
 //                 SAX words through a ring of shared-memory stages filled by
 //                 bulk copies and bounds them against the table in shared
-//                 memory; survivors {position, bound} are appended with warp
+//                 memory; survivors {row of x, bound} are appended with warp
 //                 ballots.
 //   q_refine      warps take the survivors in that order, skip those whose
 //                 bound now exceeds the k-th best, and compute real distances
@@ -22,6 +22,12 @@
 //                 a sorted array updated by an atomicMin cascade.
 //   q_finalize    candidates within fp32 error of the k-th best re-ranked in
 //                 FP64 (ties by lower row), distances rounded to fp32.
+//
+// Rows.  The rows are either copied into leaf order by the build (row of x =
+// leaf-order position) or read in the caller's array, where each leaf refers
+// to its series by original row (the paper's leaves hold pointers into the raw
+// data array): row_at() maps a position to its row of x, id_of_row() a row of
+// x to the original id.  Survivors and candidates carry rows of x.
 //
 // Exactness.  Bounds are pruned only with the slack of a rigorous fp32 error
 // analysis: a series is pruned only if its bound proves its exact distance
@@ -383,13 +389,14 @@ __device__ __forceinline__ void q_approx_body(const DevIndex& ix, const QueryScr
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long refined = 0;
-    for (int64_t r = b + gw; r < e; r += nw) {
+    for (int64_t p = b + gw; p < e; p += nw) {
         bool ab;
+        const uint32_t r = row_at(ix, p);
         const float d2 = warp_d2<NV>(ix, r, qv, s.q, INFINITY, ab);
         if (lane == 0) {
             const unsigned long long kth = ld_volatile_u64(&s.topk[k - 1]);
             if (kth == EMPTY_SLOT || (double)d2 <= (double)key_d2(kth) * (1.0 + 3.0 * delta))
-                consider(s, k, pack_key(d2, ix.orig[r]), (uint32_t)r, delta);
+                consider(s, k, pack_key(d2, ix.orig[p]), r, delta);
         }
         ++refined;
     }
@@ -604,8 +611,8 @@ __device__ __forceinline__ void warp_d2_four(const DevIndex& ix, const uint2 (&e
 // against the threshold the approximate answer set: the first 8 segments
 // first, then 4 more and the last 4, each step only while some lane of the
 // warp is still under the threshold (the sum runs in segment order either way,
-// so the bound is the same).  Survivors {position, bound} are buffered per warp and appended with
-// one atomic per batch.
+// so the bound is the same).  Survivors {row of x, bound} are buffered per warp
+// and appended with one atomic per batch.
 constexpr int LB_THREADS = 512;
 constexpr int LB_WARPS = LB_THREADS / 32;
 constexpr int LB_STAGES = 3;
@@ -714,7 +721,8 @@ __global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix,
     const uint32_t tab_sa = smem_u32(tab);
     uint2* buf = bufs + warp * LB_BUF;
     int nbuf = 0;  // warp-uniform
-    // the buffered survivors go to the global list in one append
+    // the buffered survivors go to the global list in one append, each as
+    // {row of x, bound} (the position is translated here, once per batch)
     auto drain = [&]() {
         if (nbuf == 0) return;
         uint32_t base = 0;
@@ -722,7 +730,7 @@ __global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix,
         base = __shfl_sync(FULL, base, 0);
         __syncwarp();
         for (int t = lane; t < nbuf; t += 32)
-            if (base + t < s.surv_cap) s.surv[base + t] = buf[t];
+            if (base + t < s.surv_cap) s.surv[base + t] = make_uint2(row_at(ix, buf[t].x), buf[t].y);
         __syncwarp();
         nbuf = 0;
     };
@@ -860,7 +868,7 @@ __global__ void __launch_bounds__(RF_THREADS, 3) q_refine_kernel(DevIndex ix, Qu
         kt = __shfl_sync(FULL, kt, 0);
         const double lim_w = kt == EMPTY_SLOT ? INFINITY : (double)key_d2(kt) * (1.0 + 3.0 * delta);
         if (lane < nb && (double)my_d2 <= lim_w)
-            consider(s, k, pack_key(my_d2, ix.orig[my_pos]), my_pos, delta);
+            consider(s, k, pack_key(my_d2, id_of_row(ix, my_pos)), my_pos, delta);
         __syncwarp();
         nb = 0;
     };
@@ -1080,7 +1088,7 @@ __device__ __forceinline__ void q_finalize_body(const DevIndex& ix, const QueryS
             const double d = warp_d2_fp64_seq(ix.x + (int64_t)pos * n, s.q, n, sqbuf[warp]);
             if (lane == 0) {
                 sk[e] = (unsigned long long)__double_as_longlong(d);
-                sid[e] = ix.orig[pos];
+                sid[e] = id_of_row(ix, pos);
             }
         }
         int P = 1;
@@ -1108,7 +1116,7 @@ __device__ __forceinline__ void q_finalize_body(const DevIndex& ix, const QueryS
                 const double d = warp_d2_fp64_seq(ix.x + (int64_t)pos * n, s.q, n, sqbuf[warp]);
                 if (lane == 0) {
                     sk[cnt + e] = (unsigned long long)__double_as_longlong(d);
-                    sid[cnt + e] = ix.orig[pos];
+                    sid[cnt + e] = id_of_row(ix, pos);
                 }
             }
             const int total = cnt + added;
@@ -1286,13 +1294,14 @@ __global__ void __launch_bounds__(256) bq_recheck_kernel(DevIndex ix, const Quer
         float4 qv[NV ? NV : 1];
         load_q<NV>(s.q, qv);
         bool ab;
-        const float d2 = warp_d2<NV>(ix, (int64_t)r.x, qv, s.q, abandon_limit(kth, delta), ab);
+        const uint32_t row = row_at(ix, r.x);
+        const float d2 = warp_d2<NV>(ix, (int64_t)row, qv, s.q, abandon_limit(kth, delta), ab);
         if (lane == 0) {
             atomicAdd(&s.ctl->series_refined, 1ull);
             if (!ab) {
                 const unsigned long long kk = ld_volatile_u64(&s.topk[k - 1]);
                 if (kk == EMPTY_SLOT || (double)d2 <= (double)key_d2(kk) * (1.0 + 3.0 * delta))
-                    consider(s, k, pack_key(d2, ix.orig[r.x]), r.x, delta);
+                    consider(s, k, pack_key(d2, ix.orig[r.x]), row, delta);
             }
         }
     }
@@ -1442,6 +1451,7 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
         cudaFreeHost(ix->x);
         ix->x = nullptr;
     }
+    if (ix->rows_in_place) ix->x = nullptr;  // the caller's array
     void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp};
     for (void* p : ptrs)
         if (p) dev_free(p, st);

@@ -670,6 +670,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
 // BF16 copy of the collection (leaf order), fp32 squared row norms, and the
 // largest row norm of every leaf (rounded up).  One CTA per leaf, one warp per row.
 __global__ void __launch_bounds__(256) tc_prepare_kernel(const float* __restrict__ x,
+                                                         const uint32_t* __restrict__ row_of,
                                                          const uint32_t* __restrict__ leaf_begin, int n,
                                                          uint16_t* __restrict__ xb, float* __restrict__ xn,
                                                          float* __restrict__ leaf_xnorm, unsigned* bad) {
@@ -679,7 +680,8 @@ __global__ void __launch_bounds__(256) tc_prepare_kernel(const float* __restrict
     const int64_t lb = leaf_begin[l], le = leaf_begin[l + 1];
     double mymax = 0.0;
     for (int64_t r = lb + warp; r < le; r += 8) {
-        const float4* xr = reinterpret_cast<const float4*>(x + r * n);
+        // rows in leaf order, or the caller's rows gathered by original id
+        const float4* xr = reinterpret_cast<const float4*>(x + (int64_t)(row_of ? row_of[r] : (uint32_t)r) * n);
         uint2* dst = reinterpret_cast<uint2*>(xb + r * n);
         double acc = 0.0;
         for (int i = lane; i < n / 4; i += 32) {
@@ -871,7 +873,8 @@ static TcState* ensure_tc(isax_index* ix, cudaStream_t st) {
         ISAX_CUDA_TRY(cudaMemsetAsync(t->misc, 0, sizeof(uint32_t) * 8, st));
         {
             ISAX_LAUNCH("tc_prepare", st);
-            tc_prepare_kernel<<<(unsigned)d.L, 256, 0, st>>>(ix->x, ix->leaf_begin, d.n, t->xb, t->xn,
+            tc_prepare_kernel<<<(unsigned)d.L, 256, 0, st>>>(ix->x, d.rows_in_place ? d.orig : nullptr,
+                                                             ix->leaf_begin, d.n, t->xb, t->xn,
                                                              t->leaf_xnorm, t->misc + 4);
             ISAX_CUDA_TRY(cudaGetLastError());
         }

@@ -67,8 +67,15 @@ def test_build_rejects_bad_arguments(lib):
     _expect(lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out)), 1, "w must be 16")
     q = pkg.BuildParams(16, 256, 0, 0)
     _expect(lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out)), 1, "leaf_size")
-    q = pkg.BuildParams(16, 256, 10, 8)
+    q = pkg.BuildParams(16, 256, 10, 16)
     _expect(lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out)), 1, "mem_flags")
+    # rows read in place need device-resident series, and exclude rows in host memory
+    q = pkg.BuildParams(16, 256, 10, pkg.BUILD_ROWS_IN_PLACE)
+    _expect(lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out)), 1,
+            "ISAX_MEM_INPUT_DEVICE")
+    q = pkg.BuildParams(16, 256, 10, pkg.BUILD_ROWS_IN_PLACE | pkg.BUILD_ROWS_HOST | pkg.MEM_INPUT_DEVICE)
+    _expect(lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out)), 1,
+            "exclude each other")
     _expect(lib.isax_build_index(ptr + 4, 4, 32, bp, None, ctypes.byref(out)), 1, "aligned")
     assert out.value is None
 

@@ -371,3 +371,47 @@ def test_rows_on_host_give_the_same_answers():
     c.close()
     b.close()
     a.close()
+
+
+@pytest.mark.parametrize("n,card", [(256, 256), (192, 16), (64, 256)])
+def test_rows_in_place_give_the_same_answers(n, card):
+    """An index that reads the caller's rows in place (by original row index,
+    nothing copied) answers every query path exactly like the index that copies
+    the rows into leaf order, and like the oracle; it holds no row bytes."""
+    N = 30_000
+    X = datagen.rows("walk", 41, 0, N, n)
+    Q, _ = datagen.queries("walk", 41, N, n, 42, 12, 6, 0.05)
+    Xd = torch.from_numpy(X).cuda()
+    a = pkg.Index(Xd, cardinality=card, leaf_size=300)
+    b = pkg.Index(Xd, cardinality=card, leaf_size=300, rows_in_place=True)
+    assert b.info()["device_bytes"] <= a.info()["device_bytes"] - N * n * 4
+    ea, eb = np.empty((N, 16), np.uint8), np.empty((N, 16), np.uint8)
+    oa, ob = np.empty(N, np.uint32), np.empty(N, np.uint32)
+    pkg.isax_index_export(a._h, ea.ctypes.data, oa.ctypes.data)
+    pkg.isax_index_export(b._h, eb.ctypes.data, ob.ctypes.data)
+    np.testing.assert_array_equal(ea, eb)
+    np.testing.assert_array_equal(oa, ob)
+    for k in (1, 7):
+        i1, d1 = a.query_batch(Q, k)
+        i2, d2 = b.query_batch(Q, k)
+        np.testing.assert_array_equal(i2, i1)
+        np.testing.assert_array_equal(d2, d1)
+        check_knn(i2, d2, X, Q, k)
+        for qi in (0, len(Q) - 1):
+            i3, d3 = b.query(Q[qi], k)
+            np.testing.assert_array_equal(i3, i1[qi])
+            np.testing.assert_array_equal(d3, d1[qi])
+            i4, d4 = b.query_flat(Q[qi], k)
+            np.testing.assert_array_equal(i4, i1[qi])
+            np.testing.assert_array_equal(d4, d1[qi])
+        if n % 64 == 0:
+            i5, d5 = b.query_batch_bf16(Q, k)
+            np.testing.assert_array_equal(i5, i1)
+            np.testing.assert_array_equal(d5, d1)
+    b.close()
+    a.close()
+    # the index keeps the tensor alive on its own
+    c = pkg.Index(torch.from_numpy(X).cuda(), cardinality=card, leaf_size=300, rows_in_place=True)
+    i6, d6 = c.query_batch(Q, 1)
+    check_knn(i6, d6, X, Q, 1)
+    c.close()
