@@ -24,9 +24,10 @@ def collections():
     import __graft_entry__
     __graft_entry__.build()
     out = []
-    for kind, seed, N, n, leaf in COLLS:
+    for c, (kind, seed, N, n, leaf) in enumerate(COLLS):
         X = datagen.rows(kind, seed, 0, N, n)
-        out.append((X, pkg.Index(torch.from_numpy(X).cuda(), leaf_size=leaf)))
+        # the server holds indexes of both kinds: rows copied, rows read in place
+        out.append((X, pkg.Index(torch.from_numpy(X).cuda(), leaf_size=leaf, rows_in_place=c % 2 == 1)))
     yield out
     for _, ix in out:
         ix.close()
