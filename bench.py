@@ -384,9 +384,11 @@ def bf16_peak():
 def batch_leg(a, X, pkg, torch, stream, rank):
     """Batches of B queries drawn like the single-query workload (90% fresh
     walks, 10% noisy members; seed 4), answered by the plain FP32 batch path
-    (queries run concurrently on stream slots) and by the tensor-core filtered
-    batch path, on the same index; both must return identical answers.  Device
-    buffers in and out; times are CUDA events around whole batch calls."""
+    (the single-query kernels launched once per chunk of queries, grid.y =
+    query) and by the tensor-core filtered batch path, on the same index; both
+    must return identical answers.  Device buffers in and out; times are CUDA
+    events around whole batch calls; one more traced call of each gives the
+    per-kernel times and the batched lower-bound scan's HBM fraction."""
     import datagen
     import numpy as np
     sp = stream.cuda_stream
@@ -414,11 +416,25 @@ def batch_leg(a, X, pkg, torch, stream, rank):
         Qh, _ = datagen.queries("walk", rank, N, n, 4 + 1000 * rank + B, B - B // 10, B // 10, 0.01)
         Q = torch.from_numpy(Qh).cuda()
         for k in (1, 10):
-            i_p, d_p = ix.query_batch(Q, k, stream=sp)
+            i_p, d_p, st_p = ix.query_batch(Q, k, stats=True, stream=sp)
             i_b, d_b, st = ix.query_batch_bf16(Q, k, stats=True, stream=sp)
             identical = bool(torch.equal(i_p, i_b) and torch.equal(d_p, d_b))
             plain_ms = timed(lambda: ix.query_batch(Q, k, stream=sp), 2)
             bf16_ms = timed(lambda: ix.query_batch_bf16(Q, k, stream=sp), 3)
+            pkg.isax_profile(1)
+            ix.query_batch(Q, k, stream=sp)
+            torch.cuda.synchronize()
+            pkg.isax_profile(0)
+            pprof = pkg.isax_profile_report()
+            pkern = {nm: round(v[1], 4) for nm, v in sorted(pprof.items(), key=lambda kv: -kv[1][1])}
+            scan = None
+            if "bq_series_lb" in pprof:
+                lb_ms = pprof["bq_series_lb"][1]
+                lb_bytes = 16.0 * sum(s["series_lb"] for s in st_p)
+                scan = {"kernel": "bq_series_lb", "bound": "hbm", "launches": pprof["bq_series_lb"][0],
+                        "algorithmic_bytes": lb_bytes, "ms": lb_ms,
+                        "achieved": lb_bytes / (lb_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": lb_bytes / (lb_ms / 1e3) / 1e9 / hbm}
             pkg.isax_profile(1)
             ix.query_batch_bf16(Q, k, stream=sp)
             torch.cuda.synchronize()
@@ -443,6 +459,9 @@ def batch_leg(a, X, pkg, torch, stream, rank):
                                                          for s in st])),
                     "reruns": int(sum(s["reruns"] for s in st)),
                 },
+                "plain_reruns": int(sum(s["reruns"] for s in st_p)),
+                "plain_kernels_ms": pkern,
+                "plain_scan_roofline": scan,
                 "kernels_ms": kern,
                 "tc_filter_roofline": {
                     "bound": "tensor", "unit": "TFLOP/s",

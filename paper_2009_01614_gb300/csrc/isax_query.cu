@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(256) bq_approx_kernel(DevIndex ix, const Query
 // Envelope bound of every leaf from the breakpoints and the query PAA: per
 // segment the table entry of the envelope edge nearer the query (the same
 // fp32 expression as the table), 0 when the query's symbol lies inside.
-__global__ void __launch_bounds__(256) q_leaf_lb_kernel(DevIndex ix, QueryScratch s, int k) {
+__device__ __forceinline__ void q_leaf_lb_body(const DevIndex& ix, const QueryScratch& s, int k) {
     __shared__ float bp[MAX_CARD + 1];
     __shared__ uint32_t hist[NBINS];
     __shared__ float thr_s;
@@ -459,9 +459,16 @@ __global__ void __launch_bounds__(256) q_leaf_lb_kernel(DevIndex ix, QueryScratc
     for (int i = threadIdx.x; i < NBINS; i += blockDim.x)
         if (hist[i]) atomicAdd(&s.bin_count[i], hist[i]);
 }
+__global__ void __launch_bounds__(256) q_leaf_lb_kernel(DevIndex ix, QueryScratch s, int k) {
+    q_leaf_lb_body(ix, s, k);
+}
+// the same for a batch of queries, grid.y = query
+__global__ void __launch_bounds__(256) bq_leaf_lb_kernel(DevIndex ix, const QueryScratch* ss, int k) {
+    q_leaf_lb_body(ix, ss[blockIdx.y], k);
+}
 
 // ---------------------------------------------------------------- q_leaf_scatter
-__global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, QueryScratch s, int k) {
+__device__ __forceinline__ void q_leaf_scatter_body(const DevIndex& ix, const QueryScratch& s, int k) {
     __shared__ uint32_t off[NBINS];
     __shared__ uint32_t scratch[32];
     __shared__ float thr_s;
@@ -483,7 +490,7 @@ __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, Quer
             const int b = bin_of(lb, thr);
             const uint32_t nch = leaf_pieces(ix, l);
             const uint32_t p = off[b] + atomicAdd(&s.bin_cursor[b], nch);
-            put_pieces(ix, s, l, p, nch, tot);
+            put_pieces(ix, s, l, p, nch, tot < s.work_cap ? tot : s.work_cap);
             ++mine;
         }
     }
@@ -491,9 +498,16 @@ __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, Quer
     for (int o2 = 16; o2 > 0; o2 >>= 1) mine += __shfl_xor_sync(FULL, mine, o2);
     if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&c->leaves_queued, (unsigned long long)mine);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        c->work_count = tot;
+        c->work_count = tot < s.work_cap ? tot : s.work_cap;
+        if (tot > s.work_cap) atomicOr(&c->flags, QF_OVERFLOW);
         c->thr_lb0 = thr;
     }
+}
+__global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, QueryScratch s, int k) {
+    q_leaf_scatter_body(ix, s, k);
+}
+__global__ void __launch_bounds__(NBINS) bq_leaf_scatter_kernel(DevIndex ix, const QueryScratch* ss, int k) {
+    q_leaf_scatter_body(ix, ss[blockIdx.y], k);
 }
 
 // ---------------------------------------------------------------- q_flat_list
@@ -642,8 +656,11 @@ __device__ __forceinline__ float lb_word256(float lb, uint32_t v, uint32_t tab_s
     return lb;
 }
 
+// One query's scan by G CTAs, this one being number cta (item i belongs to CTA
+// i mod G).
 template <int CARD>
-__global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix, QueryScratch s, int k) {
+__device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const QueryScratch& s, int k, uint32_t cta,
+                                                 uint32_t G) {
     extern __shared__ unsigned char lb_smem_raw[];
     QCtl* c = s.ctl;
     unsigned char* sm = lb_smem_raw + ((1024u - (smem_u32(lb_smem_raw) & 1023u)) & 1023u);
@@ -659,7 +676,6 @@ __global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix,
     uint4* wring = ring + (size_t)warp * LB_STAGES * LB_PIECE;
     uint64_t* wbar = bars + warp * LB_STAGES;
     uint2* wmeta = metas + warp * LB_STAGES;
-    const uint32_t G = gridDim.x;
     // everything the start needs is loaded at once: the flags, the item count,
     // this warp's first LB_STAGES items of the CTA (items warp * LB_STAGES + t,
     // read within the list's capacity and used only if below the count), the
@@ -669,7 +685,7 @@ __global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix,
     uint2 e[LB_STAGES];
 #pragma unroll
     for (int t = 0; t < LB_STAGES; ++t) {
-        const size_t i = blockIdx.x + (size_t)(warp * LB_STAGES + t) * G;
+        const size_t i = cta + (size_t)(warp * LB_STAGES + t) * G;
         e[t] = lane == 0 && i < s.work_cap ? s.work[i] : make_uint2(0u, 0u);
     }
     const float4* tsrc = reinterpret_cast<const float4*>(s.table);
@@ -682,7 +698,7 @@ __global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix,
         if (i < nv) tv[t] = tsrc[i];
     }
     if (flags & QF_NONFINITE) return;
-    const uint32_t mine = count > blockIdx.x ? (count - blockIdx.x + G - 1) / G : 0u;  // this CTA's items
+    const uint32_t mine = count > cta ? (count - cta + G - 1) / G : 0u;  // this CTA's items
     // lane 0 starts the copy of a piece into stage st
     auto issue = [&](uint32_t st, uint2 p) {
         const uint32_t rows = p.y & 0x7FFFFFFFu;
@@ -746,7 +762,7 @@ __global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix,
             if (lane == 0) j = atomicAdd(next_p, 1u);
             j = __shfl_sync(FULL, j, 0);
             pend_ok = j < mine;
-            if (lane == 0 && pend_ok) pend = s.work[blockIdx.x + (size_t)j * G];
+            if (lane == 0 && pend_ok) pend = s.work[cta + (size_t)j * G];
         }
         if (done == issued) break;
         const uint32_t st = done % LB_STAGES;
@@ -818,6 +834,18 @@ __global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix,
         if (n_leaves) atomicAdd(&c->leaves_scanned, n_leaves);
     }
 }
+template <int CARD>
+__global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix, QueryScratch s, int k) {
+    q_series_lb_body<CARD>(ix, s, k, blockIdx.x, gridDim.x);
+}
+// a batch of queries: CTA j runs task j = {query, part | parts << 16}, the
+// parts of a query sized to its number of work items
+template <int CARD>
+__global__ void __launch_bounds__(LB_THREADS, 1) bq_series_lb_kernel(DevIndex ix, const QueryScratch* ss,
+                                                                     const uint2* __restrict__ tasks, int k) {
+    const uint2 t = tasks[blockIdx.x];
+    q_series_lb_body<CARD>(ix, ss[t.x], k, t.y & 0xFFFFu, t.y >> 16);
+}
 
 // the scan kernels' shared-memory limit, raised once per device (before any
 // capture: scratch allocation calls this too)
@@ -828,6 +856,10 @@ void prepare_scan_kernel(int device) {
     ISAX_CUDA_TRY(cudaFuncSetAttribute(q_series_lb_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)LB_SMEM));
     ISAX_CUDA_TRY(cudaFuncSetAttribute(q_series_lb_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)LB_SMEM));
+    ISAX_CUDA_TRY(cudaFuncSetAttribute(bq_series_lb_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)LB_SMEM));
+    ISAX_CUDA_TRY(cudaFuncSetAttribute(bq_series_lb_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)LB_SMEM));
     if (device >= 0 && device < 64) done[device] = true;
 }
@@ -842,8 +874,10 @@ void prepare_scan_kernel(int device) {
 // and fed to the k best in batches of SR_BATCH.
 constexpr int RF_THREADS = 256;
 
+// gw / nw: this warp and the warps that share the query's survivors
 template <int NV>
-__global__ void __launch_bounds__(RF_THREADS, 3) q_refine_kernel(DevIndex ix, QueryScratch s, int k) {
+__device__ __forceinline__ void q_refine_body(const DevIndex& ix, const QueryScratch& s, int k, uint32_t gw,
+                                              uint32_t nw) {
     QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
     const int lane = threadIdx.x & 31;
@@ -853,8 +887,6 @@ __global__ void __launch_bounds__(RF_THREADS, 3) q_refine_kernel(DevIndex ix, Qu
     const uint32_t found = c->surv_count;
     const uint32_t total = found < s.surv_cap ? found : s.surv_cap;
     const double delta = c->delta, E = c->E;
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     unsigned long long kth = 0ull;  // cached k-th best and the limits derived from it
     float thr = INFINITY, lim = INFINITY;
     unsigned long long n_ref = 0;
@@ -929,6 +961,19 @@ __global__ void __launch_bounds__(RF_THREADS, 3) q_refine_kernel(DevIndex ix, Qu
     }
     flush();
     if (lane == 0 && n_ref) atomicAdd(&c->series_refined, n_ref);
+}
+template <int NV>
+__global__ void __launch_bounds__(RF_THREADS, 3) q_refine_kernel(DevIndex ix, QueryScratch s, int k) {
+    q_refine_body<NV>(ix, s, k, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+}
+// a batch of queries: CTA j runs task j = {query, part | parts << 16}, the
+// parts of a query sharing its survivors
+template <int NV>
+__global__ void __launch_bounds__(RF_THREADS, 3) bq_refine_kernel(DevIndex ix, const QueryScratch* ss,
+                                                                  const uint2* __restrict__ tasks, int k) {
+    const uint2 t = tasks[blockIdx.x];
+    constexpr uint32_t WPB = RF_THREADS / 32;
+    q_refine_body<NV>(ix, ss[t.x], k, (t.y & 0xFFFFu) * WPB + (threadIdx.x >> 5), (t.y >> 16) * WPB);
 }
 
 // ---------------------------------------------------------------- q_finalize
@@ -1399,7 +1444,10 @@ struct QuerySlot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
 };
+struct PlainBatch;
+static void free_plain_batch(PlainBatch* pb, cudaStream_t st);
 struct SlotPool {
+    PlainBatch* plain = nullptr;  // scratch of the batched path (query_batch_device)
     std::vector<QuerySlot*> slots;
     QCtl* host_ctl = nullptr;  // pinned: one control block per query of a batch
     size_t host_cap = 0;
@@ -1411,6 +1459,7 @@ struct SlotPool {
 static void free_slot_pool(isax_index* ix, cudaStream_t st) {
     SlotPool* p = static_cast<SlotPool*>(ix->pool);
     if (!p) return;
+    if (p->plain) free_plain_batch(p->plain, st);
     for (QuerySlot* sl : p->slots) {
         if (sl->stream) cudaStreamSynchronize(sl->stream);
         free_scratch(sl->qs, st);
@@ -1626,9 +1675,9 @@ void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_
 // B queries, up to BATCH_SLOTS at a time on their own streams (each query's
 // answer is the single-query answer: same kernels, own scratch).  Queries
 // whose candidate buffer overflowed are rerun one by one afterwards.
-void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags,
-                        int64_t* out_idx, float* out_dist, isax_query_stats_fill fill,
-                        void* fill_ctx, cudaStream_t st) {
+static void query_batch_slots(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags,
+                              int64_t* out_idx, float* out_dist, isax_query_stats_fill fill,
+                              void* fill_ctx, cudaStream_t st) {
     const int n = ix->d.n;
     const int S = B < BATCH_SLOTS ? B : BATCH_SLOTS;
     if (!ix->pool) ix->pool = new SlotPool();
@@ -1715,6 +1764,255 @@ void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t m
     if (nonfinite) throw Error{ISAX_ERR_INVALID_ARG, "a query contains a non-finite value"};
 }
 
+// a launcher instantiated for the row length: NV float4 per lane (n / 128), 0 = generic
+#define ISAX_NV_DISPATCH(n, CALL)                 \
+    do {                                          \
+        switch ((n) % 128 == 0 ? (n) / 128 : 0) { \
+            case 1: CALL(1); break;               \
+            case 2: CALL(2); break;               \
+            case 4: CALL(4); break;               \
+            case 8: CALL(8); break;               \
+            default: CALL(0); break;              \
+        }                                         \
+    } while (0)
+
+// ---------------------------------------------------------------- batched plain path
+// A batch answered chunk by chunk with one launch per step for the whole chunk:
+// the same per-query kernels as isax_query_knn, on per-query scratch carved
+// from one allocation.  Preparation, approximate answer and leaf bounds run
+// with grid.y = query.  The scan and the refinement run as task lists built on
+// the host from the queries' counts: a query gets one scan CTA per PB_SCAN_ITEMS
+// work items (item i to its part i mod P) and one refinement CTA per
+// PB_REFINE_SURV survivors, so the chunk's scans stream the SAX words of all
+// its queries in one long launch, balanced however skewed the queries are.
+// Each query has the single
+// query's worst-case room for work items, and room for PB_SURV survivors and
+// PB_CAND candidates; a query that overflows one is answered again alone.  The
+// chunk holds as many queries as fit in PB_BYTES (at most PB_MAX_CHUNK).
+constexpr int PB_MAX_CHUNK = 1024;
+constexpr size_t PB_BYTES = (size_t)12 << 30;
+constexpr uint32_t PB_SURV = 1u << 21;        // survivors per query
+constexpr uint32_t PB_CAND = 1u << 18;        // candidates per query
+constexpr uint32_t PB_SCAN_ITEMS = 1024;       // work items per scan task
+constexpr uint32_t PB_REFINE_SURV = 4096;      // survivors per refinement task
+constexpr uint32_t PB_MAX_PARTS = 1024;        // tasks per query and step
+
+struct PlainBatch {
+    int cap = 0, n = 0, card = 0;
+    int64_t L = 0, N = 0;
+    float* q = nullptr;                   // [cap][n]
+    float* table = nullptr;               // [cap][16][card]
+    float* leaf_lb = nullptr;             // [cap][L]
+    uint2* work = nullptr;                // [cap][PB_WORK]
+    uint32_t* bins = nullptr;             // [cap][2][NBINS]
+    unsigned long long* topk = nullptr;   // [cap][MAX_K]
+    unsigned long long* cand_key = nullptr;  // [cap][PB_CAND]
+    uint32_t* cand_pos = nullptr;         // [cap][PB_CAND]
+    uint2* surv = nullptr;                // [cap][PB_SURV]
+    QCtl* ctl = nullptr;                  // [cap]
+    int64_t* out_idx = nullptr;           // [cap][MAX_K]
+    float* out_dist = nullptr;            // [cap][MAX_K]
+    QueryScratch* ss = nullptr;           // [cap] device copy of the per-query views
+    uint2* tasks_scan = nullptr;          // [cap * PB_MAX_PARTS] {query, part | parts << 16}
+    uint2* tasks_refine = nullptr;        // [cap * PB_MAX_PARTS]
+    QCtl* h_ctl = nullptr;                // pinned [cap]
+    uint2* h_tasks_scan = nullptr;        // pinned staging of the task lists
+    uint2* h_tasks_refine = nullptr;
+};
+
+static void free_plain_batch(PlainBatch* pb, cudaStream_t st) {
+    if (!pb) return;
+    cudaStreamSynchronize(st);
+    void* ptrs[] = {pb->q, pb->table, pb->leaf_lb, pb->work, pb->bins, pb->topk, pb->cand_key, pb->cand_pos,
+                    pb->surv, pb->ctl, pb->out_idx, pb->out_dist, pb->ss, pb->tasks_scan, pb->tasks_refine};
+    for (void* p : ptrs)
+        if (p) dev_free(p, st);
+    if (pb->h_ctl) cudaFreeHost(pb->h_ctl);
+    if (pb->h_tasks_scan) cudaFreeHost(pb->h_tasks_scan);
+    if (pb->h_tasks_refine) cudaFreeHost(pb->h_tasks_refine);
+    delete pb;
+}
+
+static PlainBatch* ensure_plain_batch(isax_index* ix, cudaStream_t st) {
+    SlotPool* pool = static_cast<SlotPool*>(ix->pool);
+    const DevIndex& d = ix->d;
+    if (pool->plain && pool->plain->n == d.n && pool->plain->card == d.card && pool->plain->L == d.L &&
+        pool->plain->N == d.N)
+        return pool->plain;
+    if (pool->plain) free_plain_batch(pool->plain, st);
+    pool->plain = nullptr;
+    PlainBatch* pb = new PlainBatch();
+    const uint32_t work_cap = (uint32_t)work_items_cap(d.L, d.N);
+    const uint32_t surv_cap = (uint32_t)std::min<int64_t>(PB_SURV, d.N);
+    const uint32_t cand_cap = (uint32_t)std::min<int64_t>(PB_CAND, d.N + 16);
+    const size_t per_query = sizeof(uint2) * (work_cap + (size_t)surv_cap) + sizeof(float) * (size_t)d.L +
+                             12 * (size_t)cand_cap + sizeof(float) * (d.n + W * d.card) + 16 * MAX_K + 4096;
+    const size_t C = (size_t)std::max<int64_t>(8, std::min<int64_t>(PB_MAX_CHUNK, (int64_t)(PB_BYTES / per_query)));
+    try {
+        pb->cap = (int)C;
+        pb->n = d.n;
+        pb->card = d.card;
+        pb->L = d.L;
+        pb->N = d.N;
+        auto alloc = [&](size_t bytes) { return dev_alloc(bytes, st); };
+        pb->q = static_cast<float*>(alloc(sizeof(float) * C * d.n));
+        pb->table = static_cast<float*>(alloc(sizeof(float) * C * W * d.card));
+        pb->leaf_lb = static_cast<float*>(alloc(sizeof(float) * C * (size_t)d.L));
+        pb->work = static_cast<uint2*>(alloc(sizeof(uint2) * C * work_cap));
+        pb->bins = static_cast<uint32_t*>(alloc(sizeof(uint32_t) * C * 2 * NBINS));
+        pb->topk = static_cast<unsigned long long*>(alloc(sizeof(unsigned long long) * C * MAX_K));
+        pb->cand_key = static_cast<unsigned long long*>(alloc(sizeof(unsigned long long) * C * cand_cap));
+        pb->cand_pos = static_cast<uint32_t*>(alloc(sizeof(uint32_t) * C * cand_cap));
+        pb->surv = static_cast<uint2*>(alloc(sizeof(uint2) * C * surv_cap));
+        pb->ctl = static_cast<QCtl*>(alloc(sizeof(QCtl) * C));
+        pb->out_idx = static_cast<int64_t*>(alloc(sizeof(int64_t) * C * MAX_K));
+        pb->out_dist = static_cast<float*>(alloc(sizeof(float) * C * MAX_K));
+        pb->ss = static_cast<QueryScratch*>(alloc(sizeof(QueryScratch) * C));
+        pb->tasks_scan = static_cast<uint2*>(alloc(sizeof(uint2) * C * PB_MAX_PARTS));
+        pb->tasks_refine = static_cast<uint2*>(alloc(sizeof(uint2) * C * PB_MAX_PARTS));
+        ISAX_CUDA_TRY(cudaMallocHost((void**)&pb->h_ctl, sizeof(QCtl) * C));
+        ISAX_CUDA_TRY(cudaMallocHost((void**)&pb->h_tasks_scan, sizeof(uint2) * C * PB_MAX_PARTS));
+        ISAX_CUDA_TRY(cudaMallocHost((void**)&pb->h_tasks_refine, sizeof(uint2) * C * PB_MAX_PARTS));
+        std::vector<QueryScratch> hs(C);
+        for (size_t b = 0; b < C; ++b) {
+            QueryScratch& v = hs[b];
+            v.q = pb->q + b * d.n;
+            v.table = pb->table + b * W * d.card;
+            v.leaf_lb = pb->leaf_lb + b * (size_t)d.L;
+            v.work = pb->work + b * work_cap;
+            v.work_cap = work_cap;
+            v.bin_count = pb->bins + b * 2 * NBINS;
+            v.bin_cursor = v.bin_count + NBINS;
+            v.topk = pb->topk + b * MAX_K;
+            v.cand_key = pb->cand_key + b * cand_cap;
+            v.cand_pos = pb->cand_pos + b * cand_cap;
+            v.cand_cap = cand_cap;
+            v.surv = pb->surv + b * surv_cap;
+            v.surv_cap = surv_cap;
+            v.ctl = pb->ctl + b;
+            v.out_idx = pb->out_idx + b * MAX_K;
+            v.out_dist = pb->out_dist + b * MAX_K;
+        }
+        ISAX_CUDA_TRY(cudaMemcpyAsync(pb->ss, hs.data(), sizeof(QueryScratch) * C, cudaMemcpyHostToDevice, st));
+        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    } catch (...) {
+        free_plain_batch(pb, st);
+        throw;
+    }
+    pool->plain = pb;
+    return pb;
+}
+
+// the task list of one step: each query's parts, from its count of units
+static uint32_t make_tasks(const QCtl* ctl, int C, uint2* tasks, bool scan, uint32_t surv_cap) {
+    uint32_t T = 0;
+    for (int b = 0; b < C; ++b) {
+        const QCtl& c = ctl[b];
+        if (c.flags & (QF_NONFINITE | QF_OVERFLOW | QF_STALLED)) continue;  // answered again alone
+        if (!scan && c.surv_count > surv_cap) continue;                      // likewise
+        const uint64_t units = scan ? c.work_count : c.surv_count;
+        if (units == 0) continue;
+        const uint64_t per = scan ? PB_SCAN_ITEMS : PB_REFINE_SURV;
+        const uint32_t P = (uint32_t)std::min<uint64_t>(PB_MAX_PARTS, (units + per - 1) / per);
+        for (uint32_t p = 0; p < P; ++p) tasks[T++] = make_uint2((uint32_t)b, p | (P << 16));
+    }
+    return T;
+}
+
+template <int NV>
+static void launch_plain_chunk(isax_index* ix, PlainBatch* pb, int C, int k, cudaStream_t st) {
+    const DevIndex& d = ix->d;
+    const QueryScratch* ss = pb->ss;
+    launch_bq_prep(ix, ss, C, k, APPROX_NEIGHBORS, st);
+    launch_bq_approx(ix, ss, C, k, APPROX_NEIGHBORS, st);
+    const unsigned lb_blocks = (unsigned)std::min<int64_t>((d.L + 255) / 256, (int64_t)ix->num_sms * 8);
+    {
+        ISAX_LAUNCH("bq_leaf_lb", st);
+        bq_leaf_lb_kernel<<<dim3(lb_blocks, C), 256, 0, st>>>(d, ss, k);
+    }
+    {
+        ISAX_LAUNCH("bq_leaf_scatter", st);
+        bq_leaf_scatter_kernel<<<dim3(lb_blocks, C), NBINS, 0, st>>>(d, ss, k);
+    }
+    ISAX_CUDA_TRY(cudaMemcpyAsync(pb->h_ctl, pb->ctl, sizeof(QCtl) * (size_t)C, cudaMemcpyDeviceToHost, st));
+    ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    const uint32_t Ts = make_tasks(pb->h_ctl, C, pb->h_tasks_scan, true, 0);
+    if (Ts) {
+        ISAX_CUDA_TRY(cudaMemcpyAsync(pb->tasks_scan, pb->h_tasks_scan, sizeof(uint2) * Ts, cudaMemcpyHostToDevice, st));
+        prepare_scan_kernel(ix->device);
+        ISAX_LAUNCH("bq_series_lb", st);
+        if (d.card == 256)
+            bq_series_lb_kernel<256><<<Ts, LB_THREADS, LB_SMEM, st>>>(d, ss, pb->tasks_scan, k);
+        else
+            bq_series_lb_kernel<0><<<Ts, LB_THREADS, LB_SMEM, st>>>(d, ss, pb->tasks_scan, k);
+    }
+    ISAX_CUDA_TRY(cudaMemcpyAsync(pb->h_ctl, pb->ctl, sizeof(QCtl) * (size_t)C, cudaMemcpyDeviceToHost, st));
+    ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    const uint32_t surv_cap = (uint32_t)std::min<int64_t>(PB_SURV, d.N);
+    const uint32_t Tr = make_tasks(pb->h_ctl, C, pb->h_tasks_refine, false, surv_cap);
+    if (Tr) {
+        ISAX_CUDA_TRY(cudaMemcpyAsync(pb->tasks_refine, pb->h_tasks_refine, sizeof(uint2) * Tr,
+                                      cudaMemcpyHostToDevice, st));
+        ISAX_LAUNCH("bq_refine", st);
+        bq_refine_kernel<NV><<<Tr, RF_THREADS, 0, st>>>(d, ss, pb->tasks_refine, k);
+    }
+    launch_bq_finalize(ix, ss, C, k, st);
+    ISAX_CUDA_TRY(cudaGetLastError());
+}
+
+// Batches of at least PLAIN_BATCH_MIN queries take the chunked path; smaller
+// ones run their single-query graphs concurrently on stream slots.
+constexpr int PLAIN_BATCH_MIN = 8;
+
+void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags,
+                        int64_t* out_idx, float* out_dist, isax_query_stats_fill fill,
+                        void* fill_ctx, cudaStream_t st) {
+    if (B < PLAIN_BATCH_MIN)
+        return query_batch_slots(ix, Q, B, k, mem_flags, out_idx, out_dist, fill, fill_ctx, st);
+    if (!ix->pool) ix->pool = new SlotPool();
+    PlainBatch* pb = ensure_plain_batch(ix, st);
+    const int n = ix->d.n;
+    const cudaMemcpyKind kin = (mem_flags & ISAX_MEM_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                                   : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = (mem_flags & ISAX_MEM_OUTPUT_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                                     : cudaMemcpyDeviceToHost;
+    bool nonfinite = false;
+    for (int b0 = 0; b0 < B; b0 += pb->cap) {
+        const int C = std::min(pb->cap, B - b0);
+        ISAX_CUDA_TRY(cudaMemcpyAsync(pb->q, Q + (size_t)b0 * n, sizeof(float) * (size_t)C * n, kin, st));
+#define ISAX_CALL(NV) launch_plain_chunk<NV>(ix, pb, C, k, st)
+        ISAX_NV_DISPATCH(n, ISAX_CALL);
+#undef ISAX_CALL
+        ISAX_CUDA_TRY(cudaMemcpyAsync(pb->h_ctl, pb->ctl, sizeof(QCtl) * (size_t)C, cudaMemcpyDeviceToHost, st));
+        ISAX_CUDA_TRY(cudaMemcpy2DAsync(out_idx + (size_t)b0 * k, sizeof(int64_t) * k, pb->out_idx,
+                                        sizeof(int64_t) * MAX_K, sizeof(int64_t) * k, C, kout, st));
+        ISAX_CUDA_TRY(cudaMemcpy2DAsync(out_dist + (size_t)b0 * k, sizeof(float) * k, pb->out_dist,
+                                        sizeof(float) * MAX_K, sizeof(float) * k, C, kout, st));
+        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int b = 0; b < C; ++b) {
+            QCtl c = pb->h_ctl[b];
+            int reruns = 0;
+            if (c.flags & QF_NONFINITE) {
+                nonfinite = true;
+                continue;
+            }
+            if (c.flags & QF_STALLED) throw Error{ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed"};
+            if (c.flags & (QF_OVERFLOW | QF_SHORT)) {
+                // a per-query capacity of the chunk was too small: answer it alone
+                const size_t g = (size_t)b0 + b;
+                ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, Q + g * n, sizeof(float) * n, kin, st));
+                query_device(ix, k, &c, &reruns, st);
+                ISAX_CUDA_TRY(cudaMemcpyAsync(out_idx + g * k, ix->qs.out_idx, sizeof(int64_t) * k, kout, st));
+                ISAX_CUDA_TRY(cudaMemcpyAsync(out_dist + g * k, ix->qs.out_dist, sizeof(float) * k, kout, st));
+                ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+                reruns += 1;
+            }
+            if (fill) fill(fill_ctx, b0 + b, c, reruns);
+        }
+    }
+    if (nonfinite) throw Error{ISAX_ERR_INVALID_ARG, "a query contains a non-finite value"};
+}
+
 // ---------------------------------------------------------------- batched launchers
 void launch_bq_prep(isax_index* ix, const QueryScratch* ss, int B, int k, int neighbors,
                     cudaStream_t st) {
@@ -1736,17 +2034,6 @@ static void launch_bq_recheck_nv(isax_index* ix, const QueryScratch* ss, int k, 
     ISAX_LAUNCH("bq_recheck", st);
     bq_recheck_kernel<NV><<<ix->num_sms * 8, 256, 0, st>>>(ix->d, ss, k, cand, cand_count, cap);
 }
-
-#define ISAX_NV_DISPATCH(n, CALL)                 \
-    do {                                          \
-        switch ((n) % 128 == 0 ? (n) / 128 : 0) { \
-            case 1: CALL(1); break;               \
-            case 2: CALL(2); break;               \
-            case 4: CALL(4); break;               \
-            case 8: CALL(8); break;               \
-            default: CALL(0); break;              \
-        }                                         \
-    } while (0)
 
 void launch_bq_approx(isax_index* ix, const QueryScratch* ss, int B, int k, int neighbors,
                       cudaStream_t st) {
