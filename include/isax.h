@@ -157,6 +157,12 @@ isax_status isax_query_knn(const isax_index* ix, const float* q, int32_t k, uint
 /*
  * isax_query_knn_batch - B queries Q[B][n]; row b's answer, in out_idx[b][k]
  * and out_dist[b][k], equals isax_query_knn on Q[b].  stats: NULL or [B].
+ * Fewer than 8 queries run concurrently on per-query stream slots; larger
+ * batches run in chunks, each step of the query launched once for the whole
+ * chunk (Section III's query strategy, per query).  The chunk's device scratch
+ * (up to 12 GB, sized to fit) is allocated on the first such call and kept until
+ * isax_free_index.  Errors as isax_query_knn, plus ISAX_ERR_TIMEOUT if a
+ * bounded wait of the scan gave up.
  */
 isax_status isax_query_knn_batch(const isax_index* ix, const float* Q, int32_t B, int32_t k,
                                  uint32_t mem_flags, int64_t* out_idx, float* out_dist,
