@@ -155,8 +155,10 @@ void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t m
                         int64_t* out_idx, float* out_dist, isax_query_stats_fill fill,
                         void* fill_ctx, cudaStream_t st);
 void free_index_arrays(isax_index* ix, cudaStream_t st);
+// scan_share: the query's scan runs on num_sms / scan_share CTAs (1: every SM;
+// more leaves room for the scans of concurrent queries)
 void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st,
-                             int mode = QUERY_MESSI);
+                             int mode = QUERY_MESSI, int scan_share = 1);
 void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, uint32_t surv_cap, cudaStream_t st);
 uint32_t default_surv_cap(int64_t N);  // survivor entries of a fresh query scratch
 void launch_breakpoints(int card, float* bp, cudaStream_t st);
@@ -182,7 +184,8 @@ void free_query_scratch_struct(QueryScratch& q, cudaStream_t st);
 void* query_graphs_new();
 void query_graphs_delete(void* g);
 void query_graphs_clear(void* g);
-void launch_query_graph_ext(isax_index* ix, const QueryScratch& qs, void* g, int k, cudaStream_t st);
+void launch_query_graph_ext(isax_index* ix, const QueryScratch& qs, void* g, int k, cudaStream_t st,
+                            int scan_share = 1);
 // the tensor-core filtered batch (isax_tc.cu)
 void prepare_tc(isax_index* ix, cudaStream_t st);
 void query_batch_tc(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags, int64_t* out_idx,

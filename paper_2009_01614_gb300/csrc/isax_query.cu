@@ -1524,7 +1524,8 @@ int occupancy_grid(const void* fn, int threads, size_t smem, int num_sms) {
 }
 
 template <int NV>
-void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st, int mode) {
+void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st, int mode,
+                          int scan_share) {
     const DevIndex& d = ix->d;
     {
         ISAX_LAUNCH("q_prep", st);
@@ -1552,11 +1553,12 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
     {
         // one CTA per SM: its warps' copy rings take most of the SM's shared memory
         prepare_scan_kernel(ix->device);
+        const unsigned grid = (unsigned)std::max(1, ix->num_sms / std::max(1, scan_share));
         ISAX_LAUNCH("q_series_lb", st);
         if (d.card == 256)
-            q_series_lb_kernel<256><<<ix->num_sms, LB_THREADS, LB_SMEM, st>>>(d, s, k);
+            q_series_lb_kernel<256><<<grid, LB_THREADS, LB_SMEM, st>>>(d, s, k);
         else
-            q_series_lb_kernel<0><<<ix->num_sms, LB_THREADS, LB_SMEM, st>>>(d, s, k);
+            q_series_lb_kernel<0><<<grid, LB_THREADS, LB_SMEM, st>>>(d, s, k);
     }
     {
         static int grid_rf = 0;
@@ -1575,18 +1577,19 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
 
 // The query's kernels on the given scratch (the index's own, or the
 // allocation-free entry point's built-in array).
-void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st, int mode) {
+void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st, int mode,
+                             int scan_share) {
     const int n = ix->d.n;
     if (n % 128 == 0) {
         switch (n / 128) {
-            case 1: return launch_query_kernels<1>(ix, s, k, st, mode);
-            case 2: return launch_query_kernels<2>(ix, s, k, st, mode);
-            case 4: return launch_query_kernels<4>(ix, s, k, st, mode);
-            case 8: return launch_query_kernels<8>(ix, s, k, st, mode);
+            case 1: return launch_query_kernels<1>(ix, s, k, st, mode, scan_share);
+            case 2: return launch_query_kernels<2>(ix, s, k, st, mode, scan_share);
+            case 4: return launch_query_kernels<4>(ix, s, k, st, mode, scan_share);
+            case 8: return launch_query_kernels<8>(ix, s, k, st, mode, scan_share);
             default: break;
         }
     }
-    launch_query_kernels<0>(ix, s, k, st, mode);
+    launch_query_kernels<0>(ix, s, k, st, mode, scan_share);
 }
 
 // One exact k-NN query; q is already in ix->qs.q.  Results land in
@@ -1594,19 +1597,19 @@ void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaS
 // launch the query's kernels on st: replay of a captured graph, or direct
 // launches while per-kernel tracing is on
 static void launch_query_graph(isax_index* ix, const QueryScratch& qs, QueryGraphs* g, int k,
-                               cudaStream_t st, int mode = QUERY_MESSI) {
+                               cudaStream_t st, int mode = QUERY_MESSI, int scan_share = 1) {
     if (profiling_on()) {
-        launch_query_on_scratch(ix, qs, k, st, mode);
+        launch_query_on_scratch(ix, qs, k, st, mode, scan_share);
         return;
     }
-    const int key = k | (mode << 16);
+    const int key = k | (mode << 16) | (scan_share << 20);
     auto it = g->exec.find(key);
     if (it == g->exec.end()) {
         if (!g->capture) ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking));
         ISAX_CUDA_TRY(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
         cudaGraph_t graph = nullptr;
         try {
-            launch_query_on_scratch(ix, qs, k, g->capture, mode);
+            launch_query_on_scratch(ix, qs, k, g->capture, mode, scan_share);
         } catch (...) {
             cudaStreamEndCapture(g->capture, &graph);
             if (graph) cudaGraphDestroy(graph);
@@ -1631,8 +1634,9 @@ static void launch_query_graph(isax_index* ix, const QueryScratch& qs, QueryGrap
 void* query_graphs_new() { return new QueryGraphs(); }
 void query_graphs_delete(void* g) { delete static_cast<QueryGraphs*>(g); }
 void query_graphs_clear(void* g) { static_cast<QueryGraphs*>(g)->clear(); }
-void launch_query_graph_ext(isax_index* ix, const QueryScratch& qs, void* g, int k, cudaStream_t st) {
-    launch_query_graph(ix, qs, static_cast<QueryGraphs*>(g), k, st);
+void launch_query_graph_ext(isax_index* ix, const QueryScratch& qs, void* g, int k, cudaStream_t st,
+                            int scan_share) {
+    launch_query_graph(ix, qs, static_cast<QueryGraphs*>(g), k, st, QUERY_MESSI, scan_share);
 }
 
 static void launch_query_index(isax_index* ix, int k, cudaStream_t st, int mode) {

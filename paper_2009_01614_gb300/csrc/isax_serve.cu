@@ -132,6 +132,10 @@ static void server_setup(isax_server* s) {
     }
 }
 
+// The scan of a served query runs on num_sms / SERVE_SCAN_SHARE CTAs, so the
+// scans of requests in flight on other slots can run beside it.
+constexpr int SERVE_SCAN_SHARE = 2;
+
 // the query's kernels, then its control block and answer copied to the slot's
 // pinned staging, then the completion event
 static void slot_launch(isax_server* s, ServeSlot* sl) {
@@ -143,7 +147,7 @@ static void slot_launch(isax_server* s, ServeSlot* sl) {
     }
     void*& g = sl->graphs[ix];
     if (!g) g = query_graphs_new();
-    launch_query_graph_ext(ix, sl->qs, g, sl->req.k, sl->st);
+    launch_query_graph_ext(ix, sl->qs, g, sl->req.k, sl->st, SERVE_SCAN_SHARE);
     ISAX_CUDA_TRY(cudaMemcpyAsync(sl->h_ctl, sl->qs.ctl, sizeof(QCtl), cudaMemcpyDeviceToHost, sl->st));
     ISAX_CUDA_TRY(cudaMemcpyAsync(sl->h_idx, sl->qs.out_idx, sizeof(int64_t) * sl->req.k,
                                   cudaMemcpyDeviceToHost, sl->st));
