@@ -898,6 +898,9 @@ def main():
         del X
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
+        # the earlier legs' freed indexes and scratch stay cached in the library's pool;
+        # hand them back so the collection's device copy is mapped in one piece
+        pkg.isax_trim_memory(local)
         Qp = torch.from_numpy(Qh).pin_memory()
         Xh_np = Xh.numpy()
         Qp_np = Qp.numpy()

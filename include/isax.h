@@ -107,13 +107,23 @@ typedef void (*isax_free_fn)(void* ptr, void* cuda_stream, void* ctx);
  * the default).  Not thread-safe against concurrent builds. */
 isax_status isax_set_allocator(isax_alloc_fn alloc_fn, isax_free_fn free_fn, void* ctx);
 
+/* The default pool keeps the memory of freed indexes and scratch for reuse.
+ * isax_trim_memory synchronises `device` and hands that cached memory back to
+ * the driver (the memory of live indexes stays).  Useful before a large build
+ * whose allocation the cached pieces cannot serve.  No effect on memory from
+ * allocator hooks.  Errors: ISAX_ERR_INVALID_ARG (device), ISAX_ERR_CUDA. */
+isax_status isax_trim_memory(int32_t device);
+
 /*
  * isax_build_index - summarise a collection and build its iSAX index
  * (Section II, iSAX Representation and ADS+ Index; Section III, MESSI index
  * construction, Stages 1-2).
  *
- *   series  [N][n] fp32, row-major; borrowed for the call only (the index keeps
- *           its own copy, permuted into leaf order).
+ *   series  [N][n] fp32, row-major; borrowed for the call only unless
+ *           ISAX_BUILD_ROWS_IN_PLACE.  A device input is copied into leaf
+ *           order; a host input is copied to the device in chunks, each
+ *           summarised as soon as it lands, and the copy (in the input's
+ *           order, read by row) is the index's row store.
  *   N       1 .. 2^32-2 series.
  *   n       length, a multiple of 16 in [16, ISAX_MAX_LEN].
  *   p       parameters (see isax_build_params); NULL = {16, 256, 2000, 0}.

@@ -18,7 +18,7 @@ __all__ = [
     "MEM_OUTPUT_DEVICE", "W", "MAX_K", "lib", "build",
     "isax_build_index", "isax_query_knn", "isax_query_knn_batch", "isax_free_index",
     "isax_last_error", "isax_get_index_info", "isax_index_export", "isax_summarize",
-    "isax_set_allocator", "isax_profile", "isax_profile_report", "isax_launch_count",
+    "isax_set_allocator", "isax_trim_memory", "isax_profile", "isax_profile_report", "isax_launch_count",
     "isax_query_knn_noalloc", "isax_tc_selftest", "isax_query_knn_batch_bf16",
     "isax_prepare_bf16", "isax_query_knn_flat", "Server", "ServerParams", "ServerResult", "ServerInfo",
     "isax_server_create", "isax_server_add_collection", "isax_server_submit", "isax_server_poll",
@@ -122,6 +122,8 @@ def lib():
         st = ctypes.c_int
         L.isax_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
         L.isax_set_allocator.restype = st
+        L.isax_trim_memory.argtypes = [i32]
+        L.isax_trim_memory.restype = st
         L.isax_build_index.argtypes = [vp, i64, i32, ctypes.POINTER(BuildParams), vp,
                                        ctypes.POINTER(vp)]
         L.isax_build_index.restype = st
@@ -182,6 +184,11 @@ def _check(status):
 
 
 # ------------------------------------------------------------------ raw C ABI
+def isax_trim_memory(device=0):
+    """Hand the device memory cached by the library's pool back to the driver."""
+    _check(lib().isax_trim_memory(int(device)))
+
+
 def isax_set_allocator(alloc_fn, free_fn, ctx=None):
     _check(lib().isax_set_allocator(alloc_fn, free_fn, ctx))
 

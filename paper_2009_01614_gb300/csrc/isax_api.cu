@@ -58,6 +58,12 @@ void* dev_alloc(size_t bytes, cudaStream_t st) {
     return p;
 }
 
+void trim_pool(int dev) {
+    cudaMemPool_t pool;
+    ISAX_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    ISAX_CUDA_TRY(cudaMemPoolTrimTo(pool, 0));
+}
+
 void dev_free(void* p, cudaStream_t st) {
     if (!p) return;
     if (g_free) {
@@ -278,6 +284,17 @@ isax_status isax_get_index_info(const isax_index* ix, isax_index_info* info) {
         info->device = ix->device;
         info->device_bytes = ix->bytes;
         info->maxabs = ix->d.maxabs;
+    });
+}
+
+isax_status isax_trim_memory(int32_t device) {
+    return guarded([&] {
+        int count = 0;
+        ISAX_CUDA_TRY(cudaGetDeviceCount(&count));
+        check(device >= 0 && device < count, "device ordinal out of range");
+        DeviceGuard dg(device);
+        ISAX_CUDA_TRY(cudaDeviceSynchronize());
+        trim_pool(device);
     });
 }
 

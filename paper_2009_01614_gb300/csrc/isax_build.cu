@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256, (NLEN <= 256 ? 6 : NLEN <= 1024 ? 4 : 2))
 summarize_vec_kernel(
     const float4* __restrict__ x, int64_t N, int card, int cbits, const float* __restrict__ bp_g,
     uint8_t* __restrict__ sax, unsigned long long* __restrict__ keys, uint32_t* __restrict__ ids,
-    float* __restrict__ paa_out, unsigned* maxabs_bits, unsigned* nonfinite) {
+    float* __restrict__ paa_out, unsigned* maxabs_bits, unsigned* nonfinite, uint32_t id_base) {
     constexpr int F = NLEN / 64;
     constexpr int PASSES = NLEN / 128;
     constexpr int SPP = 32 / F;
@@ -199,7 +199,7 @@ summarize_vec_kernel(
             if (paa_out) paa_out[row * W + myseg] = paa;
             if (myseg == 0) {
                 if (keys) keys[row] = key;
-                if (ids) ids[row] = (uint32_t)row;
+                if (ids) ids[row] = id_base + (uint32_t)row;
             }
         }
     }
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) summarize_generic_kernel(
     const float* __restrict__ x, int64_t N, int n, int card, int cbits,
     const float* __restrict__ bp_g, uint8_t* __restrict__ sax, unsigned long long* __restrict__ keys,
     uint32_t* __restrict__ ids, float* __restrict__ paa_out, unsigned* maxabs_bits,
-    unsigned* nonfinite) {
+    unsigned* nonfinite, uint32_t id_base) {
     __shared__ float bp[MAX_CARD + 1];
     __shared__ float red_max[32];
     __shared__ unsigned red_bad;
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256) summarize_generic_kernel(
             if (paa_out) paa_out[row * W + seg] = paa;
             if (seg == 0) {
                 if (keys) keys[row] = key;
-                if (ids) ids[row] = (uint32_t)row;
+                if (ids) ids[row] = id_base + (uint32_t)row;
             }
         }
     }
@@ -286,7 +286,8 @@ __global__ void __launch_bounds__(256) summarize_generic_kernel(
 
 void launch_summarize(const float* x, int64_t N, int n, int card, const float* bp, uint4* sax,
                       unsigned long long* keys, uint32_t* ids, float* paa_out,
-                      unsigned* maxabs_bits, unsigned* nonfinite, int num_sms, cudaStream_t st) {
+                      unsigned* maxabs_bits, unsigned* nonfinite, int num_sms, cudaStream_t st,
+                      uint32_t id_base) {
     int cbits = 0;
     while ((1 << cbits) < card) ++cbits;
     const int threads = 256;
@@ -306,7 +307,7 @@ void launch_summarize(const float* x, int64_t N, int n, int card, const float* b
     case L:                                                                                    \
         summarize_vec_kernel<L, R><<<grid_of((const void*)summarize_vec_kernel<L, R>),         \
                                      threads, 0, st>>>(x4, N, card, cbits, bp, s8, keys, ids,  \
-                                                       paa_out, maxabs_bits, nonfinite);       \
+                                                       paa_out, maxabs_bits, nonfinite, id_base); \
         break;
     switch (n) {
         ISAX_SUM_CASE(128, 2)
@@ -318,7 +319,7 @@ void launch_summarize(const float* x, int64_t N, int n, int card, const float* b
             summarize_generic_kernel<<<grid_of((const void*)summarize_generic_kernel), threads, 0,
                                        st>>>(x, N, n, card, cbits, bp, s8, keys,
                                                                  ids, paa_out, maxabs_bits,
-                                                                 nonfinite);
+                                                                 nonfinite, id_base);
     }
 #undef ISAX_SUM_CASE
     ISAX_CUDA_TRY(cudaGetLastError());
@@ -816,6 +817,37 @@ __global__ void __launch_bounds__(256) envelope_kernel(const uint4* __restrict__
 // ============================================================== orchestration
 namespace {
 
+// Host-to-device copies on a stream of their own, each followed by an event
+// that the build's stream waits for, so summarising one chunk overlaps the copy
+// of the next.  The destructor waits for every copy issued: the host source is
+// the caller's and is only borrowed for the call.
+struct ChunkCopier {
+    cudaStream_t main;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    explicit ChunkCopier(cudaStream_t st) : main(st) {
+        ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        ISAX_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        // the copies start after what the build has queued (the destination's allocation)
+        ISAX_CUDA_TRY(cudaEventRecord(ev, main));
+        ISAX_CUDA_TRY(cudaStreamWaitEvent(cs, ev, 0));
+    }
+    void copy(void* dst, const void* src, size_t bytes) {
+        ISAX_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, cs));
+        ISAX_CUDA_TRY(cudaEventRecord(ev, cs));
+        ISAX_CUDA_TRY(cudaStreamWaitEvent(main, ev, 0));
+    }
+    ~ChunkCopier() {
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
+        if (ev) cudaEventDestroy(ev);
+    }
+    ChunkCopier(const ChunkCopier&) = delete;
+    ChunkCopier& operator=(const ChunkCopier&) = delete;
+};
+
 struct TempPool {
     cudaStream_t st;
     std::vector<void*> ptrs;
@@ -880,7 +912,14 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         const float* xin = series;
         const bool rows_host = (mem_flags & ISAX_BUILD_ROWS_HOST) != 0;
         const bool in_place = (mem_flags & ISAX_BUILD_ROWS_IN_PLACE) != 0;
-        if (!(mem_flags & ISAX_MEM_INPUT_DEVICE)) {
+        // host input copied to the device in chunks, each summarised as soon as it has
+        // landed; that copy, in the input's order, is the index's row store (read by row)
+        const bool chunked_host = !(mem_flags & ISAX_MEM_INPUT_DEVICE) && !rows_host;
+        if (chunked_host) {
+            ix->x = static_cast<float*>(dev_alloc((size_t)N * n * sizeof(float), st));
+            ix->rows_in_place = true;
+            xin = ix->x;
+        } else if (!(mem_flags & ISAX_MEM_INPUT_DEVICE)) {
             if (rows_host) {
                 // read in place over the CPU-GPU link: page-lock it for the build if the
                 // caller has not (nothing of the collection is staged in device memory)
@@ -895,11 +934,6 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
                 void* dp = nullptr;
                 ISAX_CUDA_TRY(cudaHostGetDevicePointer(&dp, const_cast<float*>(series), 0));
                 xin = static_cast<const float*>(dp);
-            } else {
-                float* xd = tmp.get<float>((size_t)N * n);
-                ISAX_CUDA_TRY(cudaMemcpyAsync(xd, series, (size_t)N * n * sizeof(float),
-                                              cudaMemcpyHostToDevice, st));
-                xin = xd;
             }
         }
 
@@ -913,8 +947,20 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         uint32_t* vB = tmp.get<uint32_t>(N);
         unsigned* misc = tmp.get<unsigned>(4);  // maxabs bits, nonfinite, max_leaf
         ISAX_CUDA_TRY(cudaMemsetAsync(misc, 0, 4 * sizeof(unsigned), st));
-        launch_summarize(xin, N, n, card, ix->bp, sax_tmp, kA, vA, nullptr, misc, misc + 1, num_sms,
-                         st);
+        if (chunked_host) {
+            ChunkCopier cp(st);
+            float* xd = ix->x;
+            const int64_t R = std::max<int64_t>(1, ((int64_t)1 << 30) / ((int64_t)n * 4));  // ~1 GB chunks
+            for (int64_t r0 = 0; r0 < N; r0 += R) {
+                const int64_t rows = std::min<int64_t>(R, N - r0);
+                cp.copy(xd + r0 * n, series + r0 * n, (size_t)rows * n * sizeof(float));
+                launch_summarize(xd + r0 * n, rows, n, card, ix->bp, sax_tmp + r0, kA + r0, vA + r0, nullptr,
+                                 misc, misc + 1, num_sms, st, (uint32_t)r0);
+            }
+        } else {
+            launch_summarize(xin, N, n, card, ix->bp, sax_tmp, kA, vA, nullptr, misc, misc + 1, num_sms,
+                             st);
+        }
 
         // radix sort of (key, row): LSD over the key's meaningful bits
         {
@@ -1002,10 +1048,14 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         // permute rows and SAX words into leaf order
         ix->sax = static_cast<uint4*>(dev_alloc((size_t)N * sizeof(uint4), st));
         ix->orig = static_cast<uint32_t*>(dev_alloc((size_t)N * sizeof(uint32_t), st));
-        if (in_place) {
-            // the caller's rows stay where they are, read by original id
-            ix->x = const_cast<float*>(series);
-            ix->rows_in_place = true;
+        if (in_place || chunked_host) {
+            // the rows stay in the input's order (the caller's array, or the device copy
+            // of a host input), read by original id
+            if (in_place) {
+                ix->x = const_cast<float*>(series);
+                ix->rows_in_place = true;
+                ix->rows_borrowed = true;
+            }
             ISAX_LAUNCH("permute_sax", st);
             permute_sax_kernel<<<num_sms * 8, 256, 0, st>>>(vA, N, sax_tmp, ix->sax, ix->orig);
         } else if (rows_host) {
@@ -1068,7 +1118,7 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         d.leaf_key = ix->leaf_key;
         d.bp = ix->bp;
         d.maxabs = maxabs;
-        d.rows_in_place = in_place ? 1 : 0;
+        d.rows_in_place = ix->rows_in_place ? 1 : 0;
         ix->max_leaf = (int32_t)hm[2];
         ix->bytes = (int64_t)N * n * 4 + N * 16 + N * 4 + ((int64_t)L + 1) * 4 + (int64_t)L * 40 +
                     (card + 1) * 4;

@@ -194,7 +194,7 @@ void free_tc_state(isax_index* ix, cudaStream_t st);
 void launch_summarize(const float* x, int64_t N, int n, int card, const float* bp,
                       uint4* sax, unsigned long long* keys, uint32_t* ids, float* paa_out,
                       unsigned int* maxabs_bits, unsigned int* nonfinite, int num_sms,
-                      cudaStream_t st);
+                      cudaStream_t st, uint32_t id_base = 0);
 
 }  // namespace isax
 
@@ -220,5 +220,6 @@ struct isax_index {
     void* pool;    // extra query slots for concurrent batches (isax_query.cu)
     void* tc;      // BF16 copy and batch scratch of the tensor-core filter (isax_tc.cu)
     bool rows_host;  // x is pinned host memory (ISAX_BUILD_ROWS_HOST)
-    bool rows_in_place;  // x is the caller's device array, not owned (ISAX_BUILD_ROWS_IN_PLACE)
+    bool rows_in_place;  // x holds the rows in the input's order, read by original row
+    bool rows_borrowed;  // ... and is the caller's device array (ISAX_BUILD_ROWS_IN_PLACE), not owned
 };

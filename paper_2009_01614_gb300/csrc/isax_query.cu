@@ -1500,7 +1500,7 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
         cudaFreeHost(ix->x);
         ix->x = nullptr;
     }
-    if (ix->rows_in_place) ix->x = nullptr;  // the caller's array
+    if (ix->rows_borrowed) ix->x = nullptr;  // the caller's array
     void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp};
     for (void* p : ptrs)
         if (p) dev_free(p, st);

@@ -415,3 +415,24 @@ def test_rows_in_place_give_the_same_answers(n, card):
     i6, d6 = c.query_batch(Q, 1)
     check_knn(i6, d6, X, Q, 1)
     c.close()
+
+
+def test_trim_memory_between_builds():
+    """Cached pool memory handed back to the driver between two builds of the
+    same collection from host memory: same answers, and a bad device ordinal is
+    rejected."""
+    N, n = 20_000, 128
+    X = datagen.rows("walk", 51, 0, N, n)
+    Q, _ = datagen.queries("walk", 51, N, n, 52, 8, 4, 0.05)
+    a = pkg.Index(X, leaf_size=200)
+    i1, d1 = a.query_batch(Q, 3)
+    a.close()
+    pkg.isax_trim_memory(0)
+    b = pkg.Index(X, leaf_size=200)
+    i2, d2 = b.query_batch(Q, 3)
+    np.testing.assert_array_equal(i2, i1)
+    np.testing.assert_array_equal(d2, d1)
+    check_knn(i2, d2, X, Q, 3)
+    b.close()
+    with pytest.raises(pkg.ISAXError):
+        pkg.isax_trim_memory(4096)
