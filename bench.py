@@ -759,6 +759,16 @@ def main():
     Qh, src = make_queries(a, rank)
     Qd = torch.from_numpy(Qh).cuda()
     torch.cuda.synchronize()
+    # the end-to-end leg's page-locked host copy of the collection, taken now while
+    # host memory is fresh (page-locked later, after other large host allocations,
+    # it copied to the device measurably slower)
+    Xh = None
+    if not a.no_e2e:
+        Xh = torch.empty((N, n), dtype=torch.float32, pin_memory=True)
+        for r0 in range(0, N, 1 << 22):
+            c = min(1 << 22, N - r0)
+            Xh[r0:r0 + c].copy_(X[r0:r0 + c])
+        torch.cuda.synchronize()
 
     lat_ms = []
     stats_acc = {"series_lb": 0, "series_refined": 0, "approx_series": 0, "leaves_queued": 0,
@@ -851,8 +861,6 @@ def main():
     # the ParIS flat scan against MESSI's pruned, ordered search, same queries and index
     ablation = ablation_leg(a, X, Qd, pkg, torch, stream)
 
-    # rows in host memory, read over the CPU-GPU link by the refinement
-    host_rows = None if a.no_host_rows else host_rows_leg(a, X, Qd, pkg, torch, stream)
 
     # batched queries: the plain FP32 path against the tensor-core (BF16) filter
     batch_info = batch_leg(a, X, pkg, torch, stream, rank) if a.batch > 0 else None
@@ -879,7 +887,7 @@ def main():
         "batch": batch_info,
         "rows_copied" if a.rows == "in-place" else "rows_in_place": rows_other,
         "ablation_flat_scan": ablation,
-        "rows_in_host_memory": host_rows,
+        "rows_in_host_memory": None,
         "kernels": kernels,
         "scan_roofline": scan_roofline(qprof, stats_acc["series_lb"] / a.steps, hbm,
                                        "messi_%dMx%d" % (a.N // 1000000, a.n)),
@@ -890,11 +898,6 @@ def main():
     # ---------------------------------------------------------- end to end (host buffers)
     if not a.no_e2e:
         del Qd
-        Xh = torch.empty((N, n), dtype=torch.float32, pin_memory=True)
-        chunk = 1 << 22
-        for r0 in range(0, N, chunk):
-            c = min(chunk, N - r0)
-            Xh[r0:r0 + c].copy_(X[r0:r0 + c])
         del X
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
@@ -915,17 +918,57 @@ def main():
             step_e2e()
         barrier()
         t0 = time.perf_counter()
+        marks = []
         for _ in range(a.steps):
             step_e2e()
+            marks.append(time.perf_counter())
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0)
+        step_ms = [round((b - a_) * 1e3, 1) for a_, b in zip([t0] + marks[:-1], marks)]
         out["e2e"] = {"value": total_queries / e2e_s, "unit": UNIT,
                       "h2d_bytes_per_step": N * n * 4 + a.queries * n * 4,
                       "d2h_bytes_per_step": a.queries * k * (8 + 4),
-                      "ms_per_step": e2e_s / a.steps * 1e3}
-        del Xh
+                      "ms_per_step": e2e_s / a.steps * 1e3, "step_ms": step_ms}
+        del Xh, Qp, Qp_np, Xh_np
     else:
-        del X
+        del X, Qd
+    # torch keeps freed page-locked blocks cached; hand them back to the system before
+    # the host-rows leg page-locks 102 GB of its own (host memory holds one such copy)
+    empty_host = getattr(torch._C, "_host_emptyCache", None)
+    if empty_host is not None:
+        torch.cuda.synchronize()
+        empty_host()
+
+    # rows in host memory, read over the CPU-GPU link by the refinement.  Run after
+    # the end-to-end leg: run before it, its 102 GB of page-locked rows, once freed,
+    # left the end-to-end leg's page-locked input slower to copy (a step took ~680
+    # instead of ~520 ms).  The collection is generated on the device again.
+    def host_available_bytes():
+        try:
+            for line in open("/proc/meminfo"):
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+        except OSError:
+            pass
+        return None
+
+    need = N * n * 4 * 1.1
+    avail = host_available_bytes()
+    if not a.no_host_rows and avail is not None and avail < need:
+        out["rows_in_host_memory"] = {"skipped": "host memory available %.0f GB < %.0f GB needed"
+                                                 % (avail / 1e9, need / 1e9)}
+    elif not a.no_host_rows and (a.no_e2e or empty_host is not None):
+        torch.cuda.synchronize()
+        X = torch.empty((N, n), dtype=torch.float32, device="cuda")
+        datagen.rows_device("walk", rank, 0, N, n, X.data_ptr(), sp)
+        Qd = torch.from_numpy(Qh).cuda()
+        out["rows_in_host_memory"] = host_rows_leg(a, X, Qd, pkg, torch, stream)
+        del X, Qd
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    elif not a.no_host_rows:
+        out["rows_in_host_memory"] = {"skipped": "this PyTorch cannot release its cached page-locked "
+                                                 "memory, and host memory holds one 102 GB copy"}
 
     if rank == 0 and not a.no_serving and world == 1:
         # the served path (config 4): its own collections, after the main job's are freed
