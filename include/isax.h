@@ -70,7 +70,7 @@ typedef struct isax_build_params {
 typedef struct isax_query_stats {
     int64_t leaves_total;     /* leaves in the index (each gets an envelope bound) */
     int64_t leaves_queued;    /* leaves whose bound did not exceed the approximate BSF */
-    int64_t leaves_scanned;   /* queued leaves still unpruned when a CTA claimed them */
+    int64_t leaves_scanned;   /* queued leaves whose series were bounded (all queued ones) */
     int64_t series_lb;        /* series lower bounds computed */
     int64_t series_refined;   /* exact distances computed (approximate leaf included) */
     int64_t approx_series;    /* series of the approximate-answer leaves (all refined) */

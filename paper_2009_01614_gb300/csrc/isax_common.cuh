@@ -92,9 +92,7 @@ struct QCtl {
     int32_t approx_leaf;   // approximate answer: leaves [approx_leaf, approx_end)
     int32_t approx_end;
     uint8_t qsym[16];      // query symbols
-    uint32_t work_count;   // queued leaves
-    uint32_t work_next;    // Fetch&Inc claim counter of the first wave
-    uint32_t work_next2;   // ... and of the second
+    uint32_t work_count;   // scan work items (pieces of the queued leaves)
     uint32_t cand_count;   // candidate appends attempted (may exceed capacity)
     uint32_t surv_count;   // series whose bound passed (appended; may exceed capacity)
     uint32_t window;       // candidates re-ranked in FP64

@@ -183,30 +183,9 @@ __device__ __forceinline__ void load_q(const float* q, float4 (&qv)[NV ? NV : 1]
         qv[p] = NV ? reinterpret_cast<const float4*>(q)[p * 32 + lane] : make_float4(0, 0, 0, 0);
 }
 
-// 8-bit symbols (card 256): each symbol is taken out of its word already scaled
-// to a byte offset (one shift and mask), and the segment's row offset folds
-// into the load's immediate
-__device__ __forceinline__ float series_lb_256(uint4 w, const float* __restrict__ tab) {
-    const char* t = reinterpret_cast<const char*>(tab);
-    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
-    float lb = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint32_t v = words[q];
-        lb += *reinterpret_cast<const float*>(t + (4 * q + 0) * 1024 + ((v << 2) & 0x3FCu));
-        lb += *reinterpret_cast<const float*>(t + (4 * q + 1) * 1024 + ((v >> 6) & 0x3FCu));
-        lb += *reinterpret_cast<const float*>(t + (4 * q + 2) * 1024 + ((v >> 14) & 0x3FCu));
-        lb += *reinterpret_cast<const float*>(t + (4 * q + 3) * 1024 + ((v >> 22) & 0x3FCu));
-    }
-    return lb;
-}
-
-// series lower bound: 16 table lookups summed in segment order (CARD > 0: the
-// row stride is a compile-time constant)
-template <int CARD = 0>
+// series lower bound for any cardinality: 16 table lookups (row stride card)
+// summed in segment order; the 256-symbol scan has its own form (lb_word256)
 __device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ tab, int card) {
-    if constexpr (CARD == 256) return series_lb_256(w, tab);
-    if constexpr (CARD > 0) card = CARD;
     float lb = 0.0f;
     const uint32_t words[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -343,8 +322,6 @@ __device__ __forceinline__ void q_prep_body(const DevIndex& ix, const QueryScrat
         c->approx_leaf = (int32_t)a0;
         c->approx_end = (int32_t)a1;
         c->work_count = 0;
-        c->work_next = 0;
-        c->work_next2 = 0;
         c->cand_count = 0;
         c->surv_count = 0;
         c->window = 0;
@@ -802,7 +779,7 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
                 if (!__any_sync(FULL, ok && lb <= thr)) continue;
                 lb = lb_word256<3>(lb, w[j].w, tab_sa);
             } else {
-                lb = series_lb<CARD>(w[j], tab, card);
+                lb = series_lb(w[j], tab, card);
             }
             const bool keep = ok && lb <= thr;
             const unsigned m = __ballot_sync(FULL, keep);

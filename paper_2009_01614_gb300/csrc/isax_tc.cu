@@ -117,12 +117,6 @@ __device__ __forceinline__ void tc_ld_x16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// bring a tile of the tensor into L2 ahead of its load (no shared memory, no completion)
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* tm, int x, int y) {
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)tm), "r"(x),
-                 "r"(y)
-                 : "memory");
-}
 __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* tm, int x, int y,
                                             uint64_t* bar) {
     asm volatile(
