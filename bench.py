@@ -197,27 +197,33 @@ def kernel_bytes(name, a, launches, acc):
 def kernel_source_hash(kernel):
     """Hash of what a kernel is compiled from: the text of its __global__
     definition (`<kernel>_kernel` in the file that defines it: q_* and bq_* in
-    isax_query.cu, tc_* in isax_tc.cu, the rest in isax_build.cu) and the shared
-    device-helper header."""
+    isax_query.cu, tc_* in isax_tc.cu, the rest in isax_build.cu), of the device
+    body it wraps (`<kernel>_body`, if any) and of the shared device-helper
+    header."""
     import re
     kernel = {"summarize": "summarize_vec"}.get(kernel, kernel)  # launch name -> kernel name
     src = os.path.join(ROOT, "paper_2009_01614_gb300", "csrc")
     own = ("isax_query.cu" if kernel.startswith(("q_", "bq_")) else
            "isax_tc.cu" if kernel.startswith("tc_") else "isax_build.cu")
     text = open(os.path.join(src, own)).read()
-    m = re.search(r"__global__[^;{]*?\b%s_kernel\s*\(" % re.escape(kernel), text)
-    if m is None:
-        raise KeyError("no __global__ definition of %s_kernel in %s" % (kernel, own))
-    body = ""
-    if m:
+    def definition(pattern):
+        m = re.search(pattern, text)
+        if m is None:
+            return None
         i = text.index("{", m.end())
         depth = 0
         for j in range(i, len(text)):
             depth += {"{": 1, "}": -1}.get(text[j], 0)
             if depth == 0:
-                body = text[m.start():j + 1]
-                break
-    h = hashlib.sha256(body.encode())
+                return text[m.start():j + 1]
+        return None
+
+    body = definition(r"__global__[^;{]*?\b%s_kernel\s*\(" % re.escape(kernel))
+    if body is None:
+        raise KeyError("no __global__ definition of %s_kernel in %s" % (kernel, own))
+    # a kernel that wraps a device body (shared with its batched form) is hashed with it
+    inner = definition(r"__device__[^;{]*?\b%s_body\s*\(" % re.escape(kernel))
+    h = hashlib.sha256(body.encode() + (inner or "").encode())
     h.update(open(os.path.join(src, "isax_kernels_util.cuh"), "rb").read())
     return h.hexdigest()[:16]
 
