@@ -1424,7 +1424,7 @@ struct QuerySlot {
 struct PlainBatch;
 static void free_plain_batch(PlainBatch* pb, cudaStream_t st);
 struct SlotPool {
-    PlainBatch* plain = nullptr;  // scratch of the batched path (query_batch_device)
+    PlainBatch* plain[2] = {nullptr, nullptr};  // scratch of the batched path: normal and large tier
     std::vector<QuerySlot*> slots;
     QCtl* host_ctl = nullptr;  // pinned: one control block per query of a batch
     size_t host_cap = 0;
@@ -1436,7 +1436,8 @@ struct SlotPool {
 static void free_slot_pool(isax_index* ix, cudaStream_t st) {
     SlotPool* p = static_cast<SlotPool*>(ix->pool);
     if (!p) return;
-    if (p->plain) free_plain_batch(p->plain, st);
+    for (PlainBatch*& pb : p->plain)
+        if (pb) free_plain_batch(pb, st);
     for (QuerySlot* sl : p->slots) {
         if (sl->stream) cudaStreamSynchronize(sl->stream);
         free_scratch(sl->qs, st);
@@ -1768,18 +1769,22 @@ static void query_batch_slots(isax_index* ix, const float* Q, int B, int k, uint
 // its queries in one long launch, balanced however skewed the queries are.
 // Each query has the single
 // query's worst-case room for work items, and room for PB_SURV survivors and
-// PB_CAND candidates; a query that overflows one is answered again alone.  The
-// chunk holds as many queries as fit in PB_BYTES (at most PB_MAX_CHUNK).
+// PB_CAND candidates (tier 0).  The queries that overflow one are answered again
+// together, in a second pass with 8x and 4x the room (tier 1); one that overflows
+// that too is answered alone.  A chunk holds as many queries as fit in the
+// tier's byte budget (at most PB_MAX_CHUNK).
 constexpr int PB_MAX_CHUNK = 1024;
-constexpr size_t PB_BYTES = (size_t)12 << 30;
-constexpr uint32_t PB_SURV = 1u << 21;        // survivors per query
-constexpr uint32_t PB_CAND = 1u << 18;        // candidates per query
+constexpr size_t PB_BYTES[2] = {(size_t)12 << 30, (size_t)6 << 30};
+constexpr uint32_t PB_SURV = 1u << 21;        // survivors per query (tier 0)
+constexpr uint32_t PB_CAND = 1u << 18;        // candidates per query (tier 0)
+constexpr uint32_t PB_SURV_MULT[2] = {1, 8}, PB_CAND_MULT[2] = {1, 4};
 constexpr uint32_t PB_SCAN_ITEMS = 1024;       // work items per scan task
 constexpr uint32_t PB_REFINE_SURV = 4096;      // survivors per refinement task
 constexpr uint32_t PB_MAX_PARTS = 1024;        // tasks per query and step
 
 struct PlainBatch {
     int cap = 0, n = 0, card = 0;
+    uint32_t surv_cap = 0;
     int64_t L = 0, N = 0;
     float* q = nullptr;                   // [cap][n]
     float* table = nullptr;               // [cap][16][card]
@@ -1814,27 +1819,28 @@ static void free_plain_batch(PlainBatch* pb, cudaStream_t st) {
     delete pb;
 }
 
-static PlainBatch* ensure_plain_batch(isax_index* ix, cudaStream_t st) {
+static PlainBatch* ensure_plain_batch(isax_index* ix, cudaStream_t st, int tier) {
     SlotPool* pool = static_cast<SlotPool*>(ix->pool);
     const DevIndex& d = ix->d;
-    if (pool->plain && pool->plain->n == d.n && pool->plain->card == d.card && pool->plain->L == d.L &&
-        pool->plain->N == d.N)
-        return pool->plain;
-    if (pool->plain) free_plain_batch(pool->plain, st);
-    pool->plain = nullptr;
+    PlainBatch*& slot = pool->plain[tier];
+    if (slot && slot->n == d.n && slot->card == d.card && slot->L == d.L && slot->N == d.N) return slot;
+    if (slot) free_plain_batch(slot, st);
+    slot = nullptr;
     PlainBatch* pb = new PlainBatch();
     const uint32_t work_cap = (uint32_t)work_items_cap(d.L, d.N);
-    const uint32_t surv_cap = (uint32_t)std::min<int64_t>(PB_SURV, d.N);
-    const uint32_t cand_cap = (uint32_t)std::min<int64_t>(PB_CAND, d.N + 16);
+    const uint32_t surv_cap = (uint32_t)std::min<int64_t>((int64_t)PB_SURV * PB_SURV_MULT[tier], d.N);
+    const uint32_t cand_cap = (uint32_t)std::min<int64_t>((int64_t)PB_CAND * PB_CAND_MULT[tier], d.N + 16);
     const size_t per_query = sizeof(uint2) * (work_cap + (size_t)surv_cap) + sizeof(float) * (size_t)d.L +
                              12 * (size_t)cand_cap + sizeof(float) * (d.n + W * d.card) + 16 * MAX_K + 4096;
-    const size_t C = (size_t)std::max<int64_t>(8, std::min<int64_t>(PB_MAX_CHUNK, (int64_t)(PB_BYTES / per_query)));
+    const size_t C = (size_t)std::max<int64_t>(
+        8, std::min<int64_t>(PB_MAX_CHUNK, (int64_t)(PB_BYTES[tier] / per_query)));
     try {
         pb->cap = (int)C;
         pb->n = d.n;
         pb->card = d.card;
         pb->L = d.L;
         pb->N = d.N;
+        pb->surv_cap = surv_cap;
         auto alloc = [&](size_t bytes) { return dev_alloc(bytes, st); };
         pb->q = static_cast<float*>(alloc(sizeof(float) * C * d.n));
         pb->table = static_cast<float*>(alloc(sizeof(float) * C * W * d.card));
@@ -1880,7 +1886,7 @@ static PlainBatch* ensure_plain_batch(isax_index* ix, cudaStream_t st) {
         free_plain_batch(pb, st);
         throw;
     }
-    pool->plain = pb;
+    slot = pb;
     return pb;
 }
 
@@ -1929,8 +1935,7 @@ static void launch_plain_chunk(isax_index* ix, PlainBatch* pb, int C, int k, cud
     }
     ISAX_CUDA_TRY(cudaMemcpyAsync(pb->h_ctl, pb->ctl, sizeof(QCtl) * (size_t)C, cudaMemcpyDeviceToHost, st));
     ISAX_CUDA_TRY(cudaStreamSynchronize(st));
-    const uint32_t surv_cap = (uint32_t)std::min<int64_t>(PB_SURV, d.N);
-    const uint32_t Tr = make_tasks(pb->h_ctl, C, pb->h_tasks_refine, false, surv_cap);
+    const uint32_t Tr = make_tasks(pb->h_ctl, C, pb->h_tasks_refine, false, pb->surv_cap);
     if (Tr) {
         ISAX_CUDA_TRY(cudaMemcpyAsync(pb->tasks_refine, pb->h_tasks_refine, sizeof(uint2) * Tr,
                                       cudaMemcpyHostToDevice, st));
@@ -1951,45 +1956,77 @@ void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t m
     if (B < PLAIN_BATCH_MIN)
         return query_batch_slots(ix, Q, B, k, mem_flags, out_idx, out_dist, fill, fill_ctx, st);
     if (!ix->pool) ix->pool = new SlotPool();
-    PlainBatch* pb = ensure_plain_batch(ix, st);
     const int n = ix->d.n;
     const cudaMemcpyKind kin = (mem_flags & ISAX_MEM_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice
                                                                    : cudaMemcpyHostToDevice;
     const cudaMemcpyKind kout = (mem_flags & ISAX_MEM_OUTPUT_DEVICE) ? cudaMemcpyDeviceToDevice
                                                                      : cudaMemcpyDeviceToHost;
     bool nonfinite = false;
-    for (int b0 = 0; b0 < B; b0 += pb->cap) {
-        const int C = std::min(pb->cap, B - b0);
-        ISAX_CUDA_TRY(cudaMemcpyAsync(pb->q, Q + (size_t)b0 * n, sizeof(float) * (size_t)C * n, kin, st));
+    // tier 0 takes every query in order; tier 1 the ones that overflowed tier 0
+    std::vector<int> todo(B), next;
+    for (int b = 0; b < B; ++b) todo[b] = b;
+    for (int tier = 0; tier < 2 && !todo.empty(); ++tier) {
+        PlainBatch* pb = ensure_plain_batch(ix, st, tier);
+        const int T = (int)todo.size();
+        for (int c0 = 0; c0 < T; c0 += pb->cap) {
+            const int C = std::min(pb->cap, T - c0);
+            const bool contiguous = todo[c0 + C - 1] - todo[c0] == C - 1;
+            if (contiguous) {
+                ISAX_CUDA_TRY(cudaMemcpyAsync(pb->q, Q + (size_t)todo[c0] * n, sizeof(float) * (size_t)C * n, kin, st));
+            } else {
+                for (int i = 0; i < C; ++i)
+                    ISAX_CUDA_TRY(cudaMemcpyAsync(pb->q + (size_t)i * n, Q + (size_t)todo[c0 + i] * n,
+                                                  sizeof(float) * n, kin, st));
+            }
 #define ISAX_CALL(NV) launch_plain_chunk<NV>(ix, pb, C, k, st)
-        ISAX_NV_DISPATCH(n, ISAX_CALL);
+            ISAX_NV_DISPATCH(n, ISAX_CALL);
 #undef ISAX_CALL
-        ISAX_CUDA_TRY(cudaMemcpyAsync(pb->h_ctl, pb->ctl, sizeof(QCtl) * (size_t)C, cudaMemcpyDeviceToHost, st));
-        ISAX_CUDA_TRY(cudaMemcpy2DAsync(out_idx + (size_t)b0 * k, sizeof(int64_t) * k, pb->out_idx,
-                                        sizeof(int64_t) * MAX_K, sizeof(int64_t) * k, C, kout, st));
-        ISAX_CUDA_TRY(cudaMemcpy2DAsync(out_dist + (size_t)b0 * k, sizeof(float) * k, pb->out_dist,
-                                        sizeof(float) * MAX_K, sizeof(float) * k, C, kout, st));
-        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
-        for (int b = 0; b < C; ++b) {
-            QCtl c = pb->h_ctl[b];
-            int reruns = 0;
-            if (c.flags & QF_NONFINITE) {
-                nonfinite = true;
-                continue;
+            ISAX_CUDA_TRY(cudaMemcpyAsync(pb->h_ctl, pb->ctl, sizeof(QCtl) * (size_t)C, cudaMemcpyDeviceToHost, st));
+            if (contiguous) {
+                const size_t g0 = (size_t)todo[c0];
+                ISAX_CUDA_TRY(cudaMemcpy2DAsync(out_idx + g0 * k, sizeof(int64_t) * k, pb->out_idx,
+                                                sizeof(int64_t) * MAX_K, sizeof(int64_t) * k, C, kout, st));
+                ISAX_CUDA_TRY(cudaMemcpy2DAsync(out_dist + g0 * k, sizeof(float) * k, pb->out_dist,
+                                                sizeof(float) * MAX_K, sizeof(float) * k, C, kout, st));
+            } else {
+                for (int i = 0; i < C; ++i) {
+                    const size_t g = (size_t)todo[c0 + i];
+                    ISAX_CUDA_TRY(cudaMemcpyAsync(out_idx + g * k, pb->out_idx + (size_t)i * MAX_K,
+                                                  sizeof(int64_t) * k, kout, st));
+                    ISAX_CUDA_TRY(cudaMemcpyAsync(out_dist + g * k, pb->out_dist + (size_t)i * MAX_K,
+                                                  sizeof(float) * k, kout, st));
+                }
             }
-            if (c.flags & QF_STALLED) throw Error{ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed"};
-            if (c.flags & (QF_OVERFLOW | QF_SHORT)) {
-                // a per-query capacity of the chunk was too small: answer it alone
-                const size_t g = (size_t)b0 + b;
-                ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, Q + g * n, sizeof(float) * n, kin, st));
-                query_device(ix, k, &c, &reruns, st);
-                ISAX_CUDA_TRY(cudaMemcpyAsync(out_idx + g * k, ix->qs.out_idx, sizeof(int64_t) * k, kout, st));
-                ISAX_CUDA_TRY(cudaMemcpyAsync(out_dist + g * k, ix->qs.out_dist, sizeof(float) * k, kout, st));
-                ISAX_CUDA_TRY(cudaStreamSynchronize(st));
-                reruns += 1;
+            ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+            for (int i = 0; i < C; ++i) {
+                const int b = todo[c0 + i];
+                QCtl c = pb->h_ctl[i];
+                int reruns = tier;
+                if (c.flags & QF_NONFINITE) {
+                    nonfinite = true;
+                    continue;
+                }
+                if (c.flags & QF_STALLED) throw Error{ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed"};
+                if (c.flags & (QF_OVERFLOW | QF_SHORT)) {
+                    if (tier == 0) {
+                        next.push_back(b);  // answered again with more room
+                        continue;
+                    }
+                    // even the larger room was too small: answer it alone
+                    const size_t g = (size_t)b;
+                    ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, Q + g * n, sizeof(float) * n, kin, st));
+                    int more = 0;
+                    query_device(ix, k, &c, &more, st);
+                    ISAX_CUDA_TRY(cudaMemcpyAsync(out_idx + g * k, ix->qs.out_idx, sizeof(int64_t) * k, kout, st));
+                    ISAX_CUDA_TRY(cudaMemcpyAsync(out_dist + g * k, ix->qs.out_dist, sizeof(float) * k, kout, st));
+                    ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+                    reruns += 1 + more;
+                }
+                if (fill) fill(fill_ctx, b, c, reruns);
             }
-            if (fill) fill(fill_ctx, b0 + b, c, reruns);
         }
+        todo.swap(next);
+        next.clear();
     }
     if (nonfinite) throw Error{ISAX_ERR_INVALID_ARG, "a query contains a non-finite value"};
 }
