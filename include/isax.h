@@ -169,9 +169,10 @@ isax_status isax_query_knn(const isax_index* ix, const float* q, int32_t k, uint
  * and out_dist[b][k], equals isax_query_knn on Q[b].  stats: NULL or [B].
  * Fewer than 8 queries run concurrently on per-query stream slots; larger
  * batches run in chunks, each step of the query launched once for the whole
- * chunk (Section III's query strategy, per query).  The chunk's device scratch
- * (up to 12 GB, sized to fit) is allocated on the first such call and kept until
- * isax_free_index.  Errors as isax_query_knn, plus ISAX_ERR_TIMEOUT if a
+ * chunk (Section III's query strategy, per query); queries whose survivors or
+ * candidates overflow their room run again in a second pass with more room.  The
+ * device scratch (up to 12 GB, and 6 GB for the second pass when one is needed,
+ * sized to fit) is allocated on first use and kept until isax_free_index.  Errors as isax_query_knn, plus ISAX_ERR_TIMEOUT if a
  * bounded wait of the scan gave up.
  */
 isax_status isax_query_knn_batch(const isax_index* ix, const float* Q, int32_t B, int32_t k,
