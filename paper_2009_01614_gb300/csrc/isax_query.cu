@@ -1343,7 +1343,7 @@ void free_query_scratch_struct(QueryScratch& q, cudaStream_t st) {
 // scratch for queries on any index with at most L leaves, series length n and
 // cardinality card
 // scan work items of an index: at most one per leaf plus one per LB_PIECE series
-int64_t work_items_cap(int64_t L, int64_t N) { return L + (N + 255) / 256 + 1; }
+int64_t work_items_cap(int64_t L, int64_t N) { return L + (N + LB_PIECE - 1) / LB_PIECE + 1; }
 
 void alloc_query_scratch_for(int64_t L, int64_t N, int n, int card, uint32_t cand_cap, uint32_t surv_cap,
                              QueryScratch& q, cudaStream_t st) {
