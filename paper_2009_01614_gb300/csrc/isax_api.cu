@@ -141,12 +141,8 @@ static void run_one(isax_index* ix, int32_t k, uint32_t mem_flags, int64_t* out_
                     float* out_dist, isax_query_stats* stats, cudaStream_t st, int mode = QUERY_MESSI) {
     QCtl c;
     int reruns = 0;
-    query_device(ix, k, &c, &reruns, st, mode);
-    const cudaMemcpyKind kind = (mem_flags & ISAX_MEM_OUTPUT_DEVICE) ? cudaMemcpyDeviceToDevice
-                                                                     : cudaMemcpyDeviceToHost;
-    ISAX_CUDA_TRY(cudaMemcpyAsync(out_idx, ix->qs.out_idx, sizeof(int64_t) * k, kind, st));
-    ISAX_CUDA_TRY(cudaMemcpyAsync(out_dist, ix->qs.out_dist, sizeof(float) * k, kind, st));
-    if (kind == cudaMemcpyDeviceToHost) ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    // the answer is copied out with the control block, under the same wait
+    query_device(ix, k, &c, &reruns, st, mode, out_idx, out_dist, (mem_flags & ISAX_MEM_OUTPUT_DEVICE) != 0);
     fill_stats(stats, ix, c, reruns);
 }
 

@@ -146,8 +146,12 @@ void summarize_impl(const float* series, int64_t N, int n, int card, uint32_t me
 // query strategies: MESSI (leaf pruning, leaves in bound order) and the ParIS
 // flat scan (every series of the SAX array bounded, storage order)
 enum : int { QUERY_MESSI = 0, QUERY_FLAT = 1 };
+// One query on the index's own scratch (q already there); the control block is
+// copied to *ctl_out and, when given, the answer to out_idx / out_dist (device
+// pointers if out_device), all under one wait.
 void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st,
-                  int mode = QUERY_MESSI);
+                  int mode = QUERY_MESSI, int64_t* out_idx = nullptr, float* out_dist = nullptr,
+                  bool out_device = false);
 typedef void (*isax_query_stats_fill)(void* ctx, int b, const QCtl& c, int reruns);
 void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags,
                         int64_t* out_idx, float* out_dist, isax_query_stats_fill fill,
@@ -220,4 +224,5 @@ struct isax_index {
     bool rows_host;  // x is pinned host memory (ISAX_BUILD_ROWS_HOST)
     bool rows_in_place;  // x holds the rows in the input's order, read by original row
     bool rows_borrowed;  // ... and is the caller's device array (ISAX_BUILD_ROWS_IN_PLACE), not owned
+    isax::QCtl* h_ctl;   // page-locked copy of the single query's control block
 };

@@ -1479,6 +1479,10 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
         ix->x = nullptr;
     }
     if (ix->rows_borrowed) ix->x = nullptr;  // the caller's array
+    if (ix->h_ctl) {
+        cudaFreeHost(ix->h_ctl);
+        ix->h_ctl = nullptr;
+    }
     void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp};
     for (void* p : ptrs)
         if (p) dev_free(p, st);
@@ -1622,12 +1626,20 @@ static void launch_query_index(isax_index* ix, int k, cudaStream_t st, int mode)
     launch_query_graph(ix, ix->qs, static_cast<QueryGraphs*>(ix->graphs), k, st, mode);
 }
 
-void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st, int mode) {
+void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st, int mode,
+                  int64_t* out_idx, float* out_dist, bool out_device) {
     *reruns = 0;
+    if (!ix->h_ctl) ISAX_CUDA_TRY(cudaMallocHost((void**)&ix->h_ctl, sizeof(QCtl)));
+    const cudaMemcpyKind kout = out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     for (int attempt = 0;; ++attempt) {
         launch_query_index(ix, k, st, mode);
-        ISAX_CUDA_TRY(cudaMemcpyAsync(ctl_out, ix->qs.ctl, sizeof(QCtl), cudaMemcpyDeviceToHost, st));
+        // the control block into page-locked memory and, if asked, the answer too:
+        // one wait covers both (an overflow below answers again and copies again)
+        ISAX_CUDA_TRY(cudaMemcpyAsync(ix->h_ctl, ix->qs.ctl, sizeof(QCtl), cudaMemcpyDeviceToHost, st));
+        if (out_idx) ISAX_CUDA_TRY(cudaMemcpyAsync(out_idx, ix->qs.out_idx, sizeof(int64_t) * k, kout, st));
+        if (out_dist) ISAX_CUDA_TRY(cudaMemcpyAsync(out_dist, ix->qs.out_dist, sizeof(float) * k, kout, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+        *ctl_out = *ix->h_ctl;
         if (ctl_out->flags & QF_NONFINITE) throw Error{ISAX_ERR_INVALID_ARG, "query contains a non-finite value"};
         if (ctl_out->flags & QF_STALLED) throw Error{ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed"};
         if (ctl_out->flags & QF_OVERFLOW) {
