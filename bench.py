@@ -166,6 +166,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def host_available_bytes():
+    """MemAvailable of this host, in bytes (None if unknown)."""
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
 # ------------------------------------------------------------------ roofline
 def kernel_bytes(name, a, launches, acc):
     """Algorithmic bytes of all timed launches of a kernel (None if not modelled).
@@ -767,9 +778,22 @@ def main():
     torch.cuda.synchronize()
     # the end-to-end leg's page-locked host copy of the collection, taken now while
     # host memory is fresh (page-locked later, after other large host allocations,
-    # it copied to the device measurably slower)
+    # it copied to the device measurably slower).  Every rank on this host holds one:
+    # the leg runs only if they all fit, decided alike on every rank.
     Xh = None
+    e2e_skip = None
     if not a.no_e2e:
+        local_world = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
+        avail = host_available_bytes()
+        fits = avail is None or avail >= local_world * N * n * 4 * 1.15
+        if dist is not None:
+            t = torch.tensor([1.0 if fits else 0.0], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MIN)
+            fits = bool(t.item() > 0)
+        if not fits:
+            e2e_skip = ("host memory available %.0f GB < %d ranks x %.0f GB of page-locked collection"
+                        % ((avail or 0) / 1e9, local_world, N * n * 4 * 1.15 / 1e9))
+    if not a.no_e2e and e2e_skip is None:
         Xh = torch.empty((N, n), dtype=torch.float32, pin_memory=True)
         for r0 in range(0, N, 1 << 22):
             c = min(1 << 22, N - r0)
@@ -902,7 +926,9 @@ def main():
     }
 
     # ---------------------------------------------------------- end to end (host buffers)
-    if not a.no_e2e:
+    if e2e_skip is not None:
+        out["e2e"] = {"skipped": e2e_skip}
+    if not a.no_e2e and e2e_skip is None:
         del Qd
         del X
         torch.cuda.synchronize()
@@ -949,21 +975,14 @@ def main():
     # the end-to-end leg: run before it, its 102 GB of page-locked rows, once freed,
     # left the end-to-end leg's page-locked input slower to copy (a step took ~680
     # instead of ~520 ms).  The collection is generated on the device again.
-    def host_available_bytes():
-        try:
-            for line in open("/proc/meminfo"):
-                if line.startswith("MemAvailable:"):
-                    return int(line.split()[1]) * 1024
-        except OSError:
-            pass
-        return None
-
     need = N * n * 4 * 1.1
     avail = host_available_bytes()
-    if not a.no_host_rows and avail is not None and avail < need:
+    if world > 1 and not a.no_host_rows:
+        out["rows_in_host_memory"] = {"skipped": "one rank only (102 GB of page-locked rows per process)"}
+    elif not a.no_host_rows and avail is not None and avail < need:
         out["rows_in_host_memory"] = {"skipped": "host memory available %.0f GB < %.0f GB needed"
                                                  % (avail / 1e9, need / 1e9)}
-    elif not a.no_host_rows and (a.no_e2e or empty_host is not None):
+    elif not a.no_host_rows and (a.no_e2e or e2e_skip is not None or empty_host is not None):
         torch.cuda.synchronize()
         X = torch.empty((N, n), dtype=torch.float32, device="cuda")
         datagen.rows_device("walk", rank, 0, N, n, X.data_ptr(), sp)
