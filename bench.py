@@ -276,18 +276,21 @@ def scan_roofline(prof, series_lb_total, hbm, workload):
 
 # ------------------------------------------------------------------ ablation
 def ablation_leg(a, X, Qd, pkg, torch, stream):
-    """The step's queries answered twice on one index: MESSI (leaf envelopes
-    prune leaves, leaves visited in bound order) and the ParIS flat scan (every
-    series of the SAX array bounded in storage order).  Answers must agree.
-    Per-query CUDA-event latency and pruning counters, then one more pass with
-    every kernel traced for the lower-bound scan's HBM fraction."""
+    """The step's queries answered three ways: MESSI (leaf envelopes prune
+    leaves, leaves visited in bound order) and the ParIS flat scan (every series
+    of the SAX array bounded in storage order) on one index, then MESSI on an
+    index whose leaves come from ADS+ node splitting (the split on the most
+    balanced segment) instead of the round-robin split.  Answers must agree.
+    Per-query CUDA-event latency and pruning counters; for the first two, one
+    more pass with every kernel traced for the lower-bound scan's HBM fraction."""
     import numpy as np
     sp = stream.cuda_stream
-    ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp, rows_in_place=a.rows == "in-place")
+    in_place = a.rows == "in-place"
+    ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp, rows_in_place=in_place)
     out = {}
     answers = {}
-    for mode in ("messi", "flat"):
-        fn = ix.query if mode == "messi" else ix.query_flat
+
+    def measure(fn):
         fn(Qd[0], a.k, stream=sp)  # capture its graph
         lat, st_all, ans = [], [], []
         for b in range(len(Qd)):
@@ -300,14 +303,19 @@ def ablation_leg(a, X, Qd, pkg, torch, stream):
             lat.append(e0.elapsed_time(e1))
             st_all.append(st)
             ans.append((i.cpu().numpy(), d.cpu().numpy()))
-        answers[mode] = ans
-        out[mode] = {
+        res = {
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "queries_per_s": len(lat) / (sum(lat) / 1e3),
             "series_bounded_per_query": float(np.mean([s["series_lb"] for s in st_all])),
             "series_refined_per_query": float(np.mean([s["series_refined"] for s in st_all])),
             "leaves_scanned_per_query": float(np.mean([s["leaves_scanned"] for s in st_all])),
+            "approx_series_per_query": float(np.mean([s["approx_series"] for s in st_all])),
         }
+        return res, st_all, ans
+
+    for mode in ("messi", "flat"):
+        fn = ix.query if mode == "messi" else ix.query_flat
+        out[mode], st_all, answers[mode] = measure(fn)
         pkg.isax_profile(1)
         for b in range(len(Qd)):
             fn(Qd[b], a.k, stream=sp)
@@ -319,7 +327,22 @@ def ablation_leg(a, X, Qd, pkg, torch, stream):
     out["same_answers"] = all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
                               for x, y in zip(answers["messi"], answers["flat"]))
     out["messi_speedup"] = out["flat"]["latency_ms"]["p50"] / out["messi"]["latency_ms"]["p50"]
+    info = ix.info()
+    out["messi"]["leaves"], out["messi"]["max_leaf"] = info["leaves"], info["max_leaf"]
     ix.close()
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ib = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp, rows_in_place=in_place, split="balanced")
+    e1.record(stream)
+    e1.synchronize()
+    res, _, ans = measure(ib.query)
+    info = ib.info()
+    res.update({"build_ms": e0.elapsed_time(e1), "leaves": info["leaves"], "max_leaf": info["max_leaf"]})
+    res["same_answers"] = all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+                              for x, y in zip(answers["messi"], ans))
+    out["messi_balanced_split"] = res
+    ib.close()
     return out
 
 

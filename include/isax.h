@@ -57,6 +57,19 @@ typedef enum isax_status {
  * flag the build copies the rows into leaf order and the caller may free
  * `series` when the call returns.  Not combinable with ISAX_BUILD_ROWS_HOST. */
 #define ISAX_BUILD_ROWS_IN_PLACE 8u
+/* build only: form the leaves by ADS+ node splitting (Section II, ADS+ Index)
+ * instead of the default round-robin split.  The root has one child per 16-bit
+ * key (the first bit of every segment); a node holding more than leaf_size
+ * series splits on the segment whose next bit divides its first leaf_size + 1
+ * series (in row order, i.e. as if the series were inserted one by one) most
+ * evenly, the lowest segment on a tie; children take the node's series in row
+ * order, child 0 (bit 0) first.  A node whose 16 segments are all at full
+ * cardinality is not split (a leaf of identical words may exceed leaf_size).
+ * The leaves are those of that tree in depth-first order, empty ones dropped; a
+ * query's approximate-answer leaf is the one its word descends to.  Slower to
+ * build (one pass over the collection per tree level); combinable with every
+ * other build flag. */
+#define ISAX_BUILD_SPLIT_BALANCED 16u
 
 typedef struct isax_build_params {
     int32_t w;           /* segments; must be ISAX_W (16) */
@@ -64,7 +77,8 @@ typedef struct isax_build_params {
     int32_t leaf_size;   /* leaf capacity, >= 1 (runs of identical keys are cut into pieces of this size) */
     uint32_t mem_flags;  /* ISAX_MEM_INPUT_DEVICE if `series` is a device pointer;
                             ISAX_BUILD_ROWS_HOST to keep the rows in host memory;
-                            ISAX_BUILD_ROWS_IN_PLACE to read them in the caller's array */
+                            ISAX_BUILD_ROWS_IN_PLACE to read them in the caller's array;
+                            ISAX_BUILD_SPLIT_BALANCED for ADS+ node splitting */
 } isax_build_params;
 
 typedef struct isax_query_stats {

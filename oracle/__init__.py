@@ -71,6 +71,8 @@ def lib():
         L.or_index_leaves.restype = i64
         L.or_index_leaf_sizes.argtypes = [ctypes.c_void_p, i64p]
         L.or_index_leaf_sizes.restype = i64
+        L.or_index_leaf_ids.argtypes = [ctypes.c_void_p, i64p]
+        L.or_index_leaf_ids.restype = i64
         L.or_index_query.argtypes = [ctypes.c_void_p, fp, c_int, i64p, dp, ctypes.POINTER(Stats)]
         L.or_index_query.restype = c_int
         _lib = L
@@ -191,6 +193,15 @@ class ISAXIndex:
         m = int(lib().or_index_leaf_sizes(self._h, None))
         out = np.empty(m, dtype=np.int64)
         lib().or_index_leaf_sizes(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+        return out
+
+    def leaf_ids(self):
+        """Member ids of every leaf, leaf after leaf in depth-first order (root
+        children by key, child 0 first), ids inside a leaf in insertion order;
+        split with np.cumsum(leaf_sizes())."""
+        out = np.empty(self.X.shape[0], dtype=np.int64)
+        m = int(lib().or_index_leaf_ids(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        assert m == len(out)
         return out
 
     def query(self, q, k=1):

@@ -426,6 +426,25 @@ int64_t or_index_leaf_sizes(const void* p, int64_t* out) {
     return pos;
 }
 
+/* member ids of every leaf, leaf after leaf in the depth-first order above,
+ * each leaf's ids in insertion (row) order; returns N */
+static void or_collect_ids(const or_node* nd, int64_t* out, int64_t* pos) {
+    if (!nd) return;
+    if (nd->leaf) {
+        for (int64_t i = 0; i < nd->cnt; ++i) out[(*pos)++] = nd->ids[i];
+        return;
+    }
+    or_collect_ids(nd->child[0], out, pos);
+    or_collect_ids(nd->child[1], out, pos);
+}
+
+int64_t or_index_leaf_ids(const void* p, int64_t* out) {
+    const or_index* ix = (const or_index*)p;
+    int64_t pos = 0;
+    for (int64_t k = 0; k < ((int64_t)1 << ix->w); ++k) or_collect_ids(ix->root[k], out, &pos);
+    return pos;
+}
+
 /* ---- priority queue of (lower bound, leaf) ordered by bound, then insertion */
 typedef struct {
     double lb;

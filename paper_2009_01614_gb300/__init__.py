@@ -28,6 +28,7 @@ __all__ = [
 W = 16
 BUILD_ROWS_HOST = 4
 BUILD_ROWS_IN_PLACE = 8
+BUILD_SPLIT_BALANCED = 16
 MAX_K = 1024
 MAX_LEN = 4096
 MEM_INPUT_DEVICE = 1
@@ -355,10 +356,14 @@ class Index:
     the build (ISAX_BUILD_ROWS_HOST).  With ``rows_in_place=True`` (a contiguous
     CUDA tensor) the index reads the rows in ``series`` itself and copies none
     (ISAX_BUILD_ROWS_IN_PLACE); it keeps a reference to the tensor, which must not
-    be modified while the index lives."""
+    be modified while the index lives.  ``split="balanced"`` forms the leaves by
+    ADS+ node splitting (ISAX_BUILD_SPLIT_BALANCED) instead of the default
+    round-robin split of the sorted keys."""
 
     def __init__(self, series, cardinality=256, leaf_size=2000, stream=None, rows_on_host=False,
-                 rows_in_place=False):
+                 rows_in_place=False, split="round-robin"):
+        if split not in ("round-robin", "balanced"):
+            raise ValueError("split must be 'round-robin' or 'balanced'")
         ptr, on_dev, keep, shape = _buffer(series)
         if len(shape) != 2:
             raise ValueError("series must be 2-D [N, n]")
@@ -366,13 +371,14 @@ class Index:
             raise ValueError("rows_in_place needs a contiguous float32 CUDA tensor")
         N, n = shape
         flags = ((MEM_INPUT_DEVICE if on_dev else 0) | (BUILD_ROWS_HOST if rows_on_host else 0) |
-                 (BUILD_ROWS_IN_PLACE if rows_in_place else 0))
+                 (BUILD_ROWS_IN_PLACE if rows_in_place else 0) |
+                 (BUILD_SPLIT_BALANCED if split == "balanced" else 0))
         p = BuildParams(W, cardinality, leaf_size, flags)
         self._h = None
         self._rows = keep if rows_in_place else None
         self._h = isax_build_index(ptr, N, n, p, _stream_of(keep, stream))
         self.N, self.n = N, n
-        self.cardinality, self.leaf_size = cardinality, leaf_size
+        self.cardinality, self.leaf_size, self.split = cardinality, leaf_size, split
 
     def close(self):
         if self._h:

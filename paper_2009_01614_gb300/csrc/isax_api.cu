@@ -194,7 +194,7 @@ isax_status isax_build_index(const float* series, int64_t N, int32_t n, const is
         check_card(prm.cardinality);
         check(prm.leaf_size >= 1, "leaf_size must be >= 1");
         check((prm.mem_flags & ~(uint32_t)(ISAX_MEM_INPUT_DEVICE | ISAX_BUILD_ROWS_HOST |
-                                           ISAX_BUILD_ROWS_IN_PLACE)) == 0,
+                                           ISAX_BUILD_ROWS_IN_PLACE | ISAX_BUILD_SPLIT_BALANCED)) == 0,
               "unknown mem_flags bits");
         check(!(prm.mem_flags & ISAX_BUILD_ROWS_IN_PLACE) || (prm.mem_flags & ISAX_MEM_INPUT_DEVICE),
               "ISAX_BUILD_ROWS_IN_PLACE needs device-resident series (ISAX_MEM_INPUT_DEVICE)");

@@ -788,6 +788,7 @@ __global__ void __launch_bounds__(256) envelope_kernel(const uint4* __restrict__
                                                        const unsigned long long* __restrict__ keys,
                                                        uint4* __restrict__ env,
                                                        unsigned long long* __restrict__ leaf_key,
+                                                       unsigned long long key_mask,
                                                        uint32_t* __restrict__ max_leaf) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -808,10 +809,223 @@ __global__ void __launch_bounds__(256) envelope_kernel(const uint4* __restrict__
         if (lane == 0) {
             env[2 * l] = mn;
             env[2 * l + 1] = mx;
-            leaf_key[l] = keys[b];
+            leaf_key[l] = keys[b] & key_mask;
             atomicMax(max_leaf, e - b);
         }
     }
+}
+
+
+// ============================================================== balanced-split leaves
+// ADS+ node splitting (Section II, ADS+ Index), built one tree level at a time
+// over the whole collection.  Positions are grouped by node, each node's
+// series in row order.  A level decides, for every node holding more than
+// leaf_size series, the segment whose next bit divides its first leaf_size + 1
+// series most evenly (what a node filled one series at a time sees when it
+// first overflows), then partitions every such node stably by that bit, child
+// 0 first.  Node state: first position, size, bits taken on each segment
+// (4-bit fields), tree node id.
+constexpr unsigned long long BL_BITS1 = 0x1111111111111111ull;  // one bit on every segment
+
+__device__ __forceinline__ int bl_nib(unsigned long long bits, int g) {
+    return (int)(bits >> (4 * g)) & 15;
+}
+
+// flags[i] = 1 where a run of equal root keys (the key's top 16 bits) starts
+__global__ void bl_root_flags_kernel(const unsigned long long* __restrict__ keys, int64_t N,
+                                     uint32_t* __restrict__ flags) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flags[i] = (i == 0 || (keys[i] >> 48) != (keys[i - 1] >> 48)) ? 1u : 0u;
+}
+
+// level 0: node j is run j of the root-key order
+__global__ void bl_root_nodes_kernel(const unsigned long long* __restrict__ keys,
+                                     const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
+                                     int64_t N, uint32_t* __restrict__ elem_node,
+                                     uint32_t* __restrict__ nstart, int32_t* __restrict__ root) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = pos[i] + flags[i] - 1u;
+        elem_node[i] = j;
+        if (flags[i]) {
+            nstart[j] = (uint32_t)i;
+            root[keys[i] >> 48] = (int32_t)j;
+        }
+    }
+}
+
+__global__ void bl_root_fill_kernel(const uint32_t* __restrict__ nstart, int64_t nodes, int64_t N,
+                                    uint32_t* __restrict__ ncnt, unsigned long long* __restrict__ nbits,
+                                    uint32_t* __restrict__ ngid) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nodes;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t e = j + 1 < nodes ? nstart[j + 1] : (uint32_t)N;
+        ncnt[j] = e - nstart[j];
+        nbits[j] = BL_BITS1;
+        ngid[j] = (uint32_t)j;
+    }
+}
+
+// warp per node: the split segment of every node over capacity (-1: no split,
+// also when all 16 segments are at full cardinality)
+__global__ void __launch_bounds__(256) bl_decide_kernel(const uint4* __restrict__ sax,
+                                                        const uint32_t* __restrict__ nstart,
+                                                        const uint32_t* __restrict__ ncnt,
+                                                        const unsigned long long* __restrict__ nbits,
+                                                        int64_t nodes, uint32_t cap, int cbits,
+                                                        int32_t* __restrict__ seg,
+                                                        uint32_t* __restrict__ split) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = gw; j < nodes; j += nw) {
+        int best = -1;
+        if (ncnt[j] > cap) {
+            const unsigned long long bits = nbits[j];
+            const uint32_t b = nstart[j], m = cap + 1u;
+            int sh[16];
+            uint32_t ones[16];
+#pragma unroll
+            for (int g = 0; g < 16; ++g) {
+                const int nb = bl_nib(bits, g);
+                sh[g] = nb < cbits ? cbits - 1 - nb : -1;
+                ones[g] = 0;
+            }
+            for (uint32_t p = lane; p < m; p += 32) {
+                const uint4 v = sax[b + p];
+                const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int g = 0; g < 16; ++g) {
+                    const uint32_t sym = (wd[g >> 2] >> (8 * (g & 3))) & 255u;
+                    ones[g] += sh[g] >= 0 ? (sym >> sh[g]) & 1u : 0u;
+                }
+            }
+            long long best_bal = 0;
+#pragma unroll
+            for (int g = 0; g < 16; ++g) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) ones[g] += __shfl_xor_sync(FULL, ones[g], off);
+                const long long bal = llabs(2LL * (long long)ones[g] - (long long)m);
+                if (sh[g] >= 0 && (best < 0 || bal < best_bal)) {
+                    best = g;
+                    best_bal = bal;
+                }
+            }
+        }
+        if (lane == 0) {
+            seg[j] = best;
+            split[j] = best >= 0 ? 1u : 0u;
+        }
+    }
+}
+
+// zf[i] = 1 unless position i is in a splitting node and its next bit there is 1
+__global__ void bl_bit_kernel(const uint4* __restrict__ sax, const uint32_t* __restrict__ elem_node,
+                              const int32_t* __restrict__ seg, const unsigned long long* __restrict__ nbits,
+                              int64_t N, int cbits, uint32_t* __restrict__ zf) {
+    const uint8_t* s8 = reinterpret_cast<const uint8_t*>(sax);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = elem_node[i];
+        const int s = seg[j];
+        uint32_t f = 1u;
+        if (s >= 0) {
+            const uint32_t sym = s8[i * 16 + s];
+            f = ((sym >> (cbits - 1 - bl_nib(nbits[j], s))) & 1u) ^ 1u;
+        }
+        zf[i] = f;
+    }
+}
+
+// the next level's nodes: a splitting node j becomes its children at j + spos[j]
+// (bit 0) and the one after (bit 1); the tree records the split
+__global__ void bl_nodes_kernel(int64_t nodes, const uint32_t* __restrict__ nstart,
+                                const uint32_t* __restrict__ ncnt, const unsigned long long* __restrict__ nbits,
+                                const uint32_t* __restrict__ ngid, const int32_t* __restrict__ seg,
+                                const uint32_t* __restrict__ spos, const uint32_t* __restrict__ Z,
+                                const uint32_t* __restrict__ ztot, int64_t N, uint32_t next_gid,
+                                uint32_t* __restrict__ nstart2, uint32_t* __restrict__ ncnt2,
+                                unsigned long long* __restrict__ nbits2, uint32_t* __restrict__ ngid2,
+                                int2* __restrict__ tree) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nodes;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t o = (uint32_t)j + spos[j];
+        const int s = seg[j];
+        if (s < 0) {
+            nstart2[o] = nstart[j];
+            ncnt2[o] = ncnt[j];
+            nbits2[o] = nbits[j];
+            ngid2[o] = ngid[j];
+            continue;
+        }
+        const uint32_t st = nstart[j], c = ncnt[j], e = st + c;
+        const uint32_t zeros = (e < N ? Z[e] : *ztot) - Z[st];
+        const unsigned long long nb = nbits[j] + (1ull << (4 * s));
+        const uint32_t g0 = next_gid + 2u * spos[j];
+        tree[ngid[j]] = make_int2((int)g0, s);
+        nstart2[o] = st;
+        ncnt2[o] = zeros;
+        nbits2[o] = nb;
+        ngid2[o] = g0;
+        nstart2[o + 1] = st + zeros;
+        ncnt2[o + 1] = c - zeros;
+        nbits2[o + 1] = nb;
+        ngid2[o + 1] = g0 + 1u;
+    }
+}
+
+// stable partition of every splitting node by its bit; the rest stay in place
+__global__ void bl_scatter_kernel(int64_t N, const uint4* __restrict__ sax_a, const uint32_t* __restrict__ id_a,
+                                  const uint32_t* __restrict__ en_a, const int32_t* __restrict__ seg,
+                                  const uint32_t* __restrict__ nstart, const uint32_t* __restrict__ ncnt,
+                                  const uint32_t* __restrict__ spos, const uint32_t* __restrict__ zf,
+                                  const uint32_t* __restrict__ Z, const uint32_t* __restrict__ ztot,
+                                  uint4* __restrict__ sax_b, uint32_t* __restrict__ id_b,
+                                  uint32_t* __restrict__ en_b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = en_a[i];
+        const int s = seg[j];
+        const uint32_t o = j + spos[j];
+        int64_t dst = i;
+        uint32_t nn = o;
+        if (s >= 0) {
+            const uint32_t st = nstart[j], e = st + ncnt[j];
+            const uint32_t zs = Z[st], zeros = (e < N ? Z[e] : *ztot) - zs, zb = Z[i] - zs;
+            if (zf[i]) {
+                dst = (int64_t)st + zb;
+            } else {
+                dst = (int64_t)st + zeros + ((uint32_t)i - st - zb);
+                nn = o + 1u;
+            }
+        }
+        sax_b[dst] = sax_a[i];
+        id_b[dst] = id_a[i];
+        en_b[dst] = nn;
+    }
+}
+
+__global__ void bl_leaf_flags_kernel(const uint32_t* __restrict__ ncnt, int64_t nodes,
+                                     uint32_t* __restrict__ nonempty) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nodes;
+         j += (int64_t)gridDim.x * blockDim.x)
+        nonempty[j] = ncnt[j] > 0 ? 1u : 0u;
+}
+
+// the final nodes are the leaves in depth-first order; the empty ones are
+// dropped and a descent that ends in one continues to the next leaf kept
+__global__ void bl_leaves_kernel(int64_t nodes, const uint32_t* __restrict__ nstart,
+                                 const uint32_t* __restrict__ ncnt, const uint32_t* __restrict__ ngid,
+                                 const uint32_t* __restrict__ li, uint32_t L, int64_t N,
+                                 uint32_t* __restrict__ leaf_begin, int2* __restrict__ tree) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nodes;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t l = li[j];
+        if (ncnt[j] > 0) leaf_begin[l] = nstart[j];
+        tree[ngid[j]] = make_int2(-1 - (int)(l < L ? l : L - 1u), -1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) leaf_begin[L] = (uint32_t)N;
 }
 
 // ============================================================== orchestration
@@ -873,6 +1087,228 @@ inline unsigned grid_for(int64_t work, int per_block, int num_sms, int max_per_s
     int64_t b = (work + per_block - 1) / per_block;
     int64_t cap = (int64_t)num_sms * max_per_sm;
     return (unsigned)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// Stable LSD radix sort of (key, row) pairs on `passes` 8-bit digits, the
+// lowest at bit `shift0`; the sorted pairs end in kA / vA.
+void radix_sort(unsigned long long*& kA, uint32_t*& vA, unsigned long long*& kB, uint32_t*& vB, int64_t N,
+                int shift0, int passes, TempPool& tmp, cudaStream_t st) {
+    const int64_t tiles = (N + RS_TILE - 1) / RS_TILE;
+    uint32_t* hist = tmp.get<uint32_t>((size_t)256 * tiles);
+    uint32_t* sums = tmp.get<uint32_t>(scan_sums_len(256 * tiles));
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = shift0 + 8 * pass;
+        {
+        ISAX_LAUNCH("rs_hist", st);
+        rs_hist_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(kA, N, shift, hist, tiles);
+        }
+        exclusive_scan(hist, hist, 256 * tiles, sums, st);
+        {
+        ISAX_LAUNCH("rs_scatter", st);
+        rs_scatter_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(kA, vA, kB, vB, N, shift, hist, tiles);
+        }
+        ISAX_CUDA_TRY(cudaGetLastError());
+        std::swap(kA, kB);
+        std::swap(vA, vB);
+    }
+    tmp.release(hist);
+    tmp.release(sums);
+}
+
+uint32_t read_u32(const uint32_t* p, cudaStream_t st) {
+    uint32_t v = 0;
+    ISAX_CUDA_TRY(cudaMemcpyAsync(&v, p, sizeof v, cudaMemcpyDeviceToHost, st));
+    ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    return v;
+}
+
+// Leaves of the round-robin split, cut top-down from the sorted keys kA; fills
+// ix->leaf_begin and returns the number of leaves.
+uint32_t round_robin_leaves(isax_index* ix, TempPool& tmp, const unsigned long long* kA, int64_t N,
+                            int leaf_size, int keybits, int num_sms, cudaStream_t st) {
+    const int64_t Lc = leaf_size;
+    const int64_t NA = N > Lc ? N - Lc : 0;
+    uint8_t* c = tmp.get<uint8_t>(N);
+    uint8_t* a = tmp.get<uint8_t>(NA);
+    uint8_t* P = tmp.get<uint8_t>(NA);
+    uint8_t* S = tmp.get<uint8_t>(NA);
+    uint32_t* flags = tmp.get<uint32_t>(N);
+    uint32_t* pos = tmp.get<uint32_t>(N);
+    uint32_t* sums = tmp.get<uint32_t>(scan_sums_len(N));
+    {
+    ISAX_LAUNCH("lf_lcp", st);
+    lf_lcp_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(kA, N, Lc, keybits, c, a);
+    }
+    if (NA > 0) {
+        ISAX_LAUNCH("lf_blockmax", st);
+        int64_t nblk = (NA + Lc - 1) / Lc;
+        lf_blockmax_kernel<<<(unsigned)std::min<int64_t>(nblk, (int64_t)num_sms * 16), LF_THREADS,
+                             0, st>>>(a, NA, Lc, P, S);
+    }
+    {
+    ISAX_LAUNCH("lf_flags", st);
+    lf_flags_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(c, P, S, N, Lc, keybits, flags);
+    }
+    exclusive_scan(flags, pos, N, sums, st);
+    ISAX_CUDA_TRY(cudaGetLastError());
+    uint32_t L0 = 0;
+    ISAX_CUDA_TRY(cudaMemcpyAsync(&L0, sums + (scan_sums_len(N) - 1), sizeof(uint32_t),
+                                  cudaMemcpyDeviceToHost, st));
+    ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    uint32_t* starts = tmp.get<uint32_t>((size_t)L0 + 1);
+    {
+    ISAX_LAUNCH("lf_compact", st);
+    lf_compact_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(flags, pos, N, starts, L0);
+    }
+    uint32_t* pieces = tmp.get<uint32_t>(L0);
+    uint32_t* poff = tmp.get<uint32_t>(L0);
+    uint32_t* psums = tmp.get<uint32_t>(scan_sums_len(L0));
+    {
+    ISAX_LAUNCH("lf_pieces", st);
+    lf_pieces_kernel<<<grid_for(L0, 256, num_sms), 256, 0, st>>>(starts, L0, Lc, pieces);
+    }
+    exclusive_scan(pieces, poff, L0, psums, st);
+    uint32_t L = 0;
+    ISAX_CUDA_TRY(cudaMemcpyAsync(&L, psums + (scan_sums_len(L0) - 1), sizeof(uint32_t),
+                                  cudaMemcpyDeviceToHost, st));
+    ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    ix->leaf_begin = static_cast<uint32_t*>(dev_alloc(((size_t)L + 1) * sizeof(uint32_t), st));
+    {
+    ISAX_LAUNCH("lf_expand", st);
+    lf_expand_kernel<<<grid_for(L0, 256, num_sms), 256, 0, st>>>(starts, poff, L0, Lc, N,
+                                                                  ix->leaf_begin, L);
+    }
+    ISAX_CUDA_TRY(cudaGetLastError());
+    for (void* p : {(void*)c, (void*)a, (void*)P, (void*)S, (void*)flags, (void*)pos,
+                    (void*)sums, (void*)starts, (void*)pieces, (void*)poff, (void*)psums})
+        tmp.release(p);
+    return L;
+}
+
+// Leaves of ADS+ node splitting: sorts (kA, vA) by root key, then splits level
+// by level; vA ends holding the rows in leaf order.  Fills ix->leaf_begin,
+// ix->tree, ix->tree_root, ix->tree_nodes and returns the number of leaves.
+uint32_t balanced_leaves(isax_index* ix, TempPool& tmp, const uint4* sax_tmp, unsigned long long*& kA,
+                         unsigned long long*& kB, uint32_t*& vA, uint32_t*& vB, int64_t N, int cbits,
+                         int leaf_size, int num_sms, cudaStream_t st) {
+    radix_sort(kA, vA, kB, vB, N, 48, 2, tmp, st);  // the root key: top 16 bits
+
+    const unsigned g_n = grid_for(N, 256, num_sms);
+    uint32_t* zf = tmp.get<uint32_t>(N);
+    uint32_t* Z = tmp.get<uint32_t>(N);
+    uint32_t* zsums = tmp.get<uint32_t>(scan_sums_len(N));
+    const uint32_t* ztot = zsums + (scan_sums_len(N) - 1);
+    {
+    ISAX_LAUNCH("bl_root", st);
+    bl_root_flags_kernel<<<g_n, 256, 0, st>>>(kA, N, zf);
+    }
+    exclusive_scan(zf, Z, N, zsums, st);
+    const int64_t n0 = read_u32(ztot, st);
+
+    uint4* sax_a = tmp.get<uint4>(N);
+    uint4* sax_b = tmp.get<uint4>(N);
+    uint32_t* en_a = tmp.get<uint32_t>(N);
+    uint32_t* en_b = tmp.get<uint32_t>(N);
+    uint32_t* nstart = tmp.get<uint32_t>(n0);
+    uint32_t* ncnt = tmp.get<uint32_t>(n0);
+    unsigned long long* nbits = tmp.get<unsigned long long>(n0);
+    uint32_t* ngid = tmp.get<uint32_t>(n0);
+    ix->tree_root = static_cast<int32_t*>(dev_alloc(((size_t)1 << 16) * sizeof(int32_t), st));
+    ISAX_CUDA_TRY(cudaMemsetAsync(ix->tree_root, 0xFF, ((size_t)1 << 16) * sizeof(int32_t), st));
+    int64_t tcap = n0 + 2 * (N / ((int64_t)leaf_size + 1) + 1) + 1024;
+    ix->tree = static_cast<int2*>(dev_alloc((size_t)tcap * sizeof(int2), st));
+    {
+    ISAX_LAUNCH("bl_root", st);
+    permute_sax_kernel<<<num_sms * 8, 256, 0, st>>>(vA, N, sax_tmp, sax_a, vB);
+    bl_root_nodes_kernel<<<g_n, 256, 0, st>>>(kA, zf, Z, N, en_a, nstart, ix->tree_root);
+    bl_root_fill_kernel<<<grid_for(n0, 256, num_sms), 256, 0, st>>>(nstart, n0, N, ncnt, nbits, ngid);
+    }
+    ISAX_CUDA_TRY(cudaGetLastError());
+
+    int64_t nodes = n0;
+    int64_t next_gid = n0;
+    // a path adds one bit to one segment per level: at most 16 (cbits - 1) levels split
+    for (int level = 0;; ++level) {
+        if (level > 16 * cbits) throw Error{ISAX_ERR_CUDA, "balanced split: too many tree levels"};
+        int32_t* seg = tmp.get<int32_t>(nodes);
+        uint32_t* split = tmp.get<uint32_t>(nodes);
+        uint32_t* spos = tmp.get<uint32_t>(nodes);
+        uint32_t* ssums = tmp.get<uint32_t>(scan_sums_len(nodes));
+        {
+        ISAX_LAUNCH("bl_decide", st);
+        bl_decide_kernel<<<grid_for(nodes, 8, num_sms), 256, 0, st>>>(sax_a, nstart, ncnt, nbits, nodes,
+                                                                    (uint32_t)leaf_size, cbits, seg, split);
+        }
+        exclusive_scan(split, spos, nodes, ssums, st);
+        const int64_t S = read_u32(ssums + (scan_sums_len(nodes) - 1), st);
+        if (S == 0) {
+            for (void* p : {(void*)seg, (void*)split, (void*)spos, (void*)ssums}) tmp.release(p);
+            break;
+        }
+        if (next_gid + 2 * S > tcap) {
+            const int64_t nc = std::max(next_gid + 2 * S, 2 * tcap);
+            int2* t = static_cast<int2*>(dev_alloc((size_t)nc * sizeof(int2), st));
+            ISAX_CUDA_TRY(cudaMemcpyAsync(t, ix->tree, (size_t)next_gid * sizeof(int2), cudaMemcpyDeviceToDevice, st));
+            dev_free(ix->tree, st);
+            ix->tree = t;
+            tcap = nc;
+        }
+        {
+        ISAX_LAUNCH("bl_split", st);
+        bl_bit_kernel<<<g_n, 256, 0, st>>>(sax_a, en_a, seg, nbits, N, cbits, zf);
+        }
+        exclusive_scan(zf, Z, N, zsums, st);
+        const int64_t nodes2 = nodes + S;
+        uint32_t* nstart2 = tmp.get<uint32_t>(nodes2);
+        uint32_t* ncnt2 = tmp.get<uint32_t>(nodes2);
+        unsigned long long* nbits2 = tmp.get<unsigned long long>(nodes2);
+        uint32_t* ngid2 = tmp.get<uint32_t>(nodes2);
+        {
+        ISAX_LAUNCH("bl_split", st);
+        bl_nodes_kernel<<<grid_for(nodes, 256, num_sms), 256, 0, st>>>(
+            nodes, nstart, ncnt, nbits, ngid, seg, spos, Z, ztot, N, (uint32_t)next_gid, nstart2, ncnt2,
+            nbits2, ngid2, ix->tree);
+        bl_scatter_kernel<<<g_n, 256, 0, st>>>(N, sax_a, vA, en_a, seg, nstart, ncnt, spos, zf, Z, ztot,
+                                               sax_b, vB, en_b);
+        }
+        ISAX_CUDA_TRY(cudaGetLastError());
+        std::swap(sax_a, sax_b);
+        std::swap(vA, vB);
+        std::swap(en_a, en_b);
+        for (void* p : {(void*)seg, (void*)split, (void*)spos, (void*)ssums, (void*)nstart, (void*)ncnt,
+                        (void*)nbits, (void*)ngid})
+            tmp.release(p);
+        nstart = nstart2;
+        ncnt = ncnt2;
+        nbits = nbits2;
+        ngid = ngid2;
+        nodes = nodes2;
+        next_gid += 2 * S;
+    }
+
+    // (the tree may hold more nodes than series: empty leaves)
+    uint32_t* nonempty = tmp.get<uint32_t>(nodes);
+    uint32_t* li = tmp.get<uint32_t>(nodes);
+    uint32_t* lsums = tmp.get<uint32_t>(scan_sums_len(nodes));
+    {
+    ISAX_LAUNCH("bl_leaves", st);
+    bl_leaf_flags_kernel<<<grid_for(nodes, 256, num_sms), 256, 0, st>>>(ncnt, nodes, nonempty);
+    }
+    exclusive_scan(nonempty, li, nodes, lsums, st);
+    const uint32_t L = read_u32(lsums + (scan_sums_len(nodes) - 1), st);
+    ix->leaf_begin = static_cast<uint32_t*>(dev_alloc(((size_t)L + 1) * sizeof(uint32_t), st));
+    {
+    ISAX_LAUNCH("bl_leaves", st);
+    bl_leaves_kernel<<<grid_for(nodes, 256, num_sms), 256, 0, st>>>(nodes, nstart, ncnt, ngid, li, L, N,
+                                                                     ix->leaf_begin, ix->tree);
+    }
+    ISAX_CUDA_TRY(cudaGetLastError());
+    ix->tree_nodes = next_gid;
+    for (void* p : {(void*)zf, (void*)Z, (void*)zsums, (void*)sax_a, (void*)sax_b, (void*)en_a, (void*)en_b,
+                    (void*)nstart, (void*)ncnt, (void*)nbits, (void*)ngid, (void*)nonempty, (void*)li,
+                    (void*)lsums})
+        tmp.release(p);
+    return L;
 }
 
 }  // namespace
@@ -962,88 +1398,15 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
                              st);
         }
 
-        // radix sort of (key, row): LSD over the key's meaningful bits
-        {
-            const int64_t tiles = (N + RS_TILE - 1) / RS_TILE;
-            uint32_t* hist = tmp.get<uint32_t>((size_t)256 * tiles);
-            uint32_t* sums = tmp.get<uint32_t>(scan_sums_len(256 * tiles));
-            for (int pass = 0; pass < keybits / 8; ++pass) {
-                const int shift = 64 - keybits + 8 * pass;
-                {
-                ISAX_LAUNCH("rs_hist", st);
-                rs_hist_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(kA, N, shift, hist, tiles);
-                }
-                exclusive_scan(hist, hist, 256 * tiles, sums, st);
-                {
-                ISAX_LAUNCH("rs_scatter", st);
-                rs_scatter_kernel<<<(unsigned)tiles, RS_THREADS, 0, st>>>(kA, vA, kB, vB, N, shift,
-                                                                          hist, tiles);
-                }
-                ISAX_CUDA_TRY(cudaGetLastError());
-                std::swap(kA, kB);
-                std::swap(vA, vB);
-            }
-            tmp.release(hist);
-            tmp.release(sums);
-        }
-
-        // leaves
-        const int64_t Lc = leaf_size;
-        const int64_t NA = N > Lc ? N - Lc : 0;
-        uint8_t* c = tmp.get<uint8_t>(N);
-        uint8_t* a = tmp.get<uint8_t>(NA);
-        uint8_t* P = tmp.get<uint8_t>(NA);
-        uint8_t* S = tmp.get<uint8_t>(NA);
-        uint32_t* flags = tmp.get<uint32_t>(N);
-        uint32_t* pos = tmp.get<uint32_t>(N);
-        uint32_t* sums = tmp.get<uint32_t>(scan_sums_len(N));
-        {
-        ISAX_LAUNCH("lf_lcp", st);
-        lf_lcp_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(kA, N, Lc, keybits, c, a);
-        }
-        if (NA > 0) {
-            ISAX_LAUNCH("lf_blockmax", st);
-            int64_t nblk = (NA + Lc - 1) / Lc;
-            lf_blockmax_kernel<<<(unsigned)std::min<int64_t>(nblk, (int64_t)num_sms * 16), LF_THREADS,
-                                 0, st>>>(a, NA, Lc, P, S);
-        }
-        {
-        ISAX_LAUNCH("lf_flags", st);
-        lf_flags_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(c, P, S, N, Lc, keybits, flags);
-        }
-        exclusive_scan(flags, pos, N, sums, st);
-        ISAX_CUDA_TRY(cudaGetLastError());
-        uint32_t L0 = 0;
-        ISAX_CUDA_TRY(cudaMemcpyAsync(&L0, sums + (scan_sums_len(N) - 1), sizeof(uint32_t),
-                                      cudaMemcpyDeviceToHost, st));
-        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
-        uint32_t* starts = tmp.get<uint32_t>((size_t)L0 + 1);
-        {
-        ISAX_LAUNCH("lf_compact", st);
-        lf_compact_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(flags, pos, N, starts, L0);
-        }
-        uint32_t* pieces = tmp.get<uint32_t>(L0);
-        uint32_t* poff = tmp.get<uint32_t>(L0);
-        uint32_t* psums = tmp.get<uint32_t>(scan_sums_len(L0));
-        {
-        ISAX_LAUNCH("lf_pieces", st);
-        lf_pieces_kernel<<<grid_for(L0, 256, num_sms), 256, 0, st>>>(starts, L0, Lc, pieces);
-        }
-        exclusive_scan(pieces, poff, L0, psums, st);
+        // leaves: the round-robin split of the sorted keys, or ADS+ node splitting
+        const bool balanced = (mem_flags & ISAX_BUILD_SPLIT_BALANCED) != 0;
         uint32_t L = 0;
-        ISAX_CUDA_TRY(cudaMemcpyAsync(&L, psums + (scan_sums_len(L0) - 1), sizeof(uint32_t),
-                                      cudaMemcpyDeviceToHost, st));
-        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
-        ix->leaf_begin = static_cast<uint32_t*>(dev_alloc(((size_t)L + 1) * sizeof(uint32_t), st));
-        {
-        ISAX_LAUNCH("lf_expand", st);
-        lf_expand_kernel<<<grid_for(L0, 256, num_sms), 256, 0, st>>>(starts, poff, L0, Lc, N,
-                                                                      ix->leaf_begin, L);
+        if (balanced) {
+            L = balanced_leaves(ix, tmp, sax_tmp, kA, kB, vA, vB, N, cbits, leaf_size, num_sms, st);
+        } else {
+            radix_sort(kA, vA, kB, vB, N, 64 - keybits, keybits / 8, tmp, st);
+            L = round_robin_leaves(ix, tmp, kA, N, leaf_size, keybits, num_sms, st);
         }
-        ISAX_CUDA_TRY(cudaGetLastError());
-        for (void* p : {(void*)c, (void*)a, (void*)P, (void*)S, (void*)flags, (void*)pos,
-                        (void*)sums, (void*)starts, (void*)pieces, (void*)poff, (void*)psums})
-            tmp.release(p);
 
         // permute rows and SAX words into leaf order
         ix->sax = static_cast<uint4*>(dev_alloc((size_t)N * sizeof(uint4), st));
@@ -1089,8 +1452,9 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
             dev_alloc((size_t)L * sizeof(unsigned long long), st));
         {
         ISAX_LAUNCH("envelope", st);
-        envelope_kernel<<<grid_for(L, 8, num_sms, 8), 256, 0, st>>>(ix->sax, ix->leaf_begin, L, kA,
-                                                                     ix->env, ix->leaf_key, misc + 2);
+        envelope_kernel<<<grid_for(L, 8, num_sms, 8), 256, 0, st>>>(
+            ix->sax, ix->leaf_begin, L, kA, ix->env, ix->leaf_key,
+            balanced ? 0xFFFF000000000000ull : ~0ull, misc + 2);
         ISAX_CUDA_TRY(cudaGetLastError());
         }
 
@@ -1119,10 +1483,13 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         d.bp = ix->bp;
         d.maxabs = maxabs;
         d.rows_in_place = ix->rows_in_place ? 1 : 0;
+        d.tree = ix->tree;
+        d.tree_root = ix->tree_root;
         ix->max_leaf = (int32_t)hm[2];
         ix->bytes = (int64_t)N * n * 4 + N * 16 + N * 4 + ((int64_t)L + 1) * 4 + (int64_t)L * 40 +
                     (card + 1) * 4;
         if (rows_host || in_place) ix->bytes -= (int64_t)N * n * 4;
+        if (balanced) ix->bytes += ix->tree_nodes * 8 + ((int64_t)1 << 16) * 4;
         alloc_query_scratch(ix, (uint32_t)std::min<int64_t>(N, 1 << 20), default_surv_cap(N), st);
     } catch (...) {
         free_index_arrays(ix, st);

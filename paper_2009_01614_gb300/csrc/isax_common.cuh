@@ -74,6 +74,12 @@ struct DevIndex {
     const float* bp;              // [card+1] breakpoints: -inf, beta_1 .. beta_{card-1}, +inf
     float maxabs;                 // max |x| over the collection
     int32_t rows_in_place;        // x is the caller's array, indexed by original id
+    // balanced-split tree (ISAX_BUILD_SPLIT_BALANCED only, else null): node g is
+    // {first child, split segment} when internal (children g' and g'+1), {-1 - leaf, -1}
+    // when a leaf; tree_root[key] is the node of the root child with that 16-bit key, -1
+    // if none
+    const int2* tree;
+    const int32_t* tree_root;
 };
 
 // row of x that holds the series at leaf-order position pos
@@ -215,6 +221,9 @@ struct isax_index {
     uint4* env;
     unsigned long long* leaf_key;
     float* bp;
+    int2* tree;          // balanced-split tree nodes (null for the round-robin split)
+    int32_t* tree_root;  // [2^16]
+    int64_t tree_nodes;
     // query scratch (one in-flight query)
     isax::QueryScratch qs;
     void* mu;      // std::mutex*

@@ -215,6 +215,28 @@ __device__ __forceinline__ void put_pieces(const DevIndex& ix, const QueryScratc
 
 // ---------------------------------------------------------------- q_prep
 constexpr int PREP_THREADS = 256;
+
+// Balanced-split index: the leaf a word descends to (root child of its 16-bit
+// key, then at each node the child of the word's next bit on the node's split
+// segment), or -1 when no series has that root key.
+__device__ int32_t tree_leaf(const DevIndex& ix, const int* qsym) {
+    unsigned root = 0;
+    for (int i = 0; i < W; ++i) root = (root << 1) | ((unsigned)(qsym[i] >> (ix.cbits - 1)) & 1u);
+    int32_t g = ix.tree_root[root];
+    if (g < 0) return -1;
+    int bits[W];
+    for (int i = 0; i < W; ++i) bits[i] = 1;
+    for (int depth = 0; depth <= W * 8; ++depth) {
+        const int2 t = ix.tree[g];
+        if (t.x < 0) return -1 - t.x;
+        const int sg = t.y;
+        if (sg < 0 || sg >= W || bits[sg] >= ix.cbits) return -1;
+        const int b = (qsym[sg] >> (ix.cbits - 1 - bits[sg])) & 1;
+        ++bits[sg];
+        g = t.x + b;
+    }
+    return -1;
+}
 constexpr int APPROX_NEIGHBORS = 2;
 
 // One query's preparation by one CTA of PREP_THREADS threads; `neighbors`
@@ -281,8 +303,11 @@ __device__ __forceinline__ void q_prep_body(const DevIndex& ix, const QueryScrat
     __syncthreads();
     // descent: the last leaf whose first key <= the query key.  Keys are
     // sorted: count the samples at stride `step` that are <= key, then count
-    // inside the one stride that holds the boundary.
-    const unsigned long long key = key_s;
+    // inside the one stride that holds the boundary.  A balanced-split index
+    // keeps only the root key (the top 16 bits) in leaf_key: the search finds
+    // the last leaf of the query's root child, and the tree descent below
+    // refines it.
+    const unsigned long long key = ix.tree ? (key_s & 0xFFFF000000000000ull) : key_s;
     const int64_t L = ix.L;
     const int64_t step = (L + PREP_THREADS - 1) / PREP_THREADS;
     const int64_t si = (int64_t)tid * step;
@@ -299,7 +324,11 @@ __device__ __forceinline__ void q_prep_body(const DevIndex& ix, const QueryScrat
         QCtl* c = s.ctl;
         c->qkey = key;
         const int64_t ub = lo + cnt_s;
-        const int64_t dl = ub > 0 ? ub - 1 : 0;
+        int64_t dl = ub > 0 ? ub - 1 : 0;
+        if (ix.tree) {
+            const int32_t t = tree_leaf(ix, qsym);
+            if (t >= 0 && t < L) dl = t;
+        }
         // approximate-answer range: that leaf and its APPROX_NEIGHBORS neighbours on
         // each side in key order (the nearest iSAX words), widened until it holds
         // >= k series
@@ -1483,7 +1512,8 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
         cudaFreeHost(ix->h_ctl);
         ix->h_ctl = nullptr;
     }
-    void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp};
+    void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp,
+                    ix->tree, ix->tree_root};
     for (void* p : ptrs)
         if (p) dev_free(p, st);
     ix->x = nullptr;
@@ -1493,6 +1523,8 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
     ix->env = nullptr;
     ix->leaf_key = nullptr;
     ix->bp = nullptr;
+    ix->tree = nullptr;
+    ix->tree_root = nullptr;
 }
 
 namespace {

@@ -67,7 +67,7 @@ def test_build_rejects_bad_arguments(lib):
     _expect(lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out)), 1, "w must be 16")
     q = pkg.BuildParams(16, 256, 0, 0)
     _expect(lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out)), 1, "leaf_size")
-    q = pkg.BuildParams(16, 256, 10, 16)
+    q = pkg.BuildParams(16, 256, 10, 32)
     _expect(lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out)), 1, "mem_flags")
     # rows read in place need device-resident series, and exclude rows in host memory
     q = pkg.BuildParams(16, 256, 10, pkg.BUILD_ROWS_IN_PLACE)

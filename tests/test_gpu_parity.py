@@ -436,3 +436,92 @@ def test_trim_memory_between_builds():
     b.close()
     with pytest.raises(pkg.ISAXError):
         pkg.isax_trim_memory(4096)
+
+
+# ---------------------------------------------------------------- balanced split (ADS+)
+def _far_from_breakpoints(X, card):
+    """The rows whose FP64 segment means all lie farther than four times the
+    fp32 PAA error bound from every breakpoint: on them the GPU's fp32 symbols
+    and the oracle's FP64 symbols agree, so both sides build the same tree."""
+    P64, _ = oracle.summarize(X, card=card)
+    m = X.shape[1] // 16
+    eps = 1.01 * (m + 1) * 2.0**-24 * np.abs(X).max()
+    beta = np.sort(oracle.breakpoints(card))
+    j = np.clip(np.searchsorted(beta, P64), 1, len(beta) - 1)
+    near = np.minimum(np.abs(P64 - beta[j - 1]), np.abs(P64 - beta[j])) if len(beta) > 1 else np.abs(P64 - beta[0])
+    return np.ascontiguousarray(X[(near > 4 * eps + 1e-7).all(axis=1)])
+
+
+@pytest.mark.parametrize("kind,N,n,card,cap,dup", [
+    ("walk", 3000, 64, 256, 20, False), ("walk", 2000, 64, 16, 7, True), ("sine", 3000, 128, 256, 50, False),
+    ("walk", 600, 32, 4, 1, True), ("walk", 4000, 256, 256, 100, True), ("walk", 40000, 256, 256, 300, False)])
+def test_balanced_split_tree_equals_oracle(kind, N, n, card, cap, dup):
+    """ADS+ node splitting on the GPU (level by level over the whole collection)
+    forms exactly the oracle's leaves (series inserted one by one, a leaf split
+    when it overflows): the same members in the same depth-first order, empty
+    leaves dropped; a run of identical words beyond capacity stays one leaf.
+    Answers equal brute force on every query path, and a query equal to a
+    collection row descends to that row's leaf."""
+    X = _far_from_breakpoints(datagen.rows(kind, 11, 0, N, n), card)
+    if dup:
+        X[len(X) // 3: len(X) // 3 + 2 * cap + 3] = X[0]
+    N = len(X)
+    Xd = torch.from_numpy(X).cuda()
+    ix = pkg.Index(Xd, cardinality=card, leaf_size=cap, split="balanced")
+    ex = ix.export()
+    orig = ex["orig"].astype(np.int64)
+    _, S64 = oracle.summarize(X, card=card)
+    np.testing.assert_array_equal(ex["sax"], S64[orig])  # precondition: the same symbols
+    ox = oracle.ISAXIndex(X, card=card, leaf_size=cap)
+    np.testing.assert_array_equal(orig, ox.leaf_ids())
+    sizes = ox.leaf_sizes()
+    lb = ex["leaf_begin"].astype(np.int64)
+    np.testing.assert_array_equal(np.diff(lb), sizes[sizes > 0])
+    info = ix.info()
+    assert info["leaves"] == (sizes > 0).sum() and info["max_leaf"] == sizes.max()
+    for l in range(0, len(lb) - 1, max(1, (len(lb) - 1) // 50)):
+        s = ex["sax"][lb[l]:lb[l + 1]]
+        np.testing.assert_array_equal(ex["env"][l, :16], s.min(axis=0))
+        np.testing.assert_array_equal(ex["env"][l, 16:], s.max(axis=0))
+
+    Q, _ = datagen.queries(kind, 11, N, n, 12, 10, 6, 0.05)
+    for k in (1, 5):
+        i, d = ix.query_batch(torch.from_numpy(Q).cuda(), k)
+        check_knn(i.cpu().numpy(), d.cpu().numpy(), X, Q, k)
+        for qi in (0, len(Q) - 1):
+            i2, d2 = ix.query(Q[qi], k)
+            np.testing.assert_array_equal(i2, i.cpu().numpy()[qi])
+            i3, d3 = ix.query_flat(Q[qi], k)
+            np.testing.assert_array_equal(i3, i.cpu().numpy()[qi])
+    pos = np.empty(N, np.int64)
+    pos[orig] = np.arange(N)
+    for r in np.linspace(0, N - 1, 12).astype(np.int64):
+        _, _, st = ix.query(X[r], 1, stats=True)
+        leaf_r = int(np.searchsorted(lb, pos[r], side="right")) - 1
+        assert st["approx_leaf"] <= leaf_r <= st["approx_leaf"] + 4, (r, leaf_r, st["approx_leaf"])
+    ix.close()
+
+
+def test_balanced_split_with_every_row_store():
+    """The balanced split combines with rows in place, rows in host memory and a
+    host input: the same leaves and the same answers."""
+    N, n = 30_000, 128
+    X = datagen.rows("walk", 43, 0, N, n)
+    Q, _ = datagen.queries("walk", 43, N, n, 44, 10, 6, 0.05)
+    Xd = torch.from_numpy(X).cuda()
+    a = pkg.Index(Xd, leaf_size=200, split="balanced")
+    ea = a.export()
+    others = [pkg.Index(Xd, leaf_size=200, split="balanced", rows_in_place=True),
+              pkg.Index(Xd, leaf_size=200, split="balanced", rows_on_host=True),
+              pkg.Index(X, leaf_size=200, split="balanced")]
+    i1, d1 = a.query_batch(Q, 3)
+    check_knn(i1, d1, X, Q, 3)
+    for b in others:
+        eb = b.export()
+        for key in ("orig", "leaf_begin", "sax", "env"):
+            np.testing.assert_array_equal(eb[key], ea[key])
+        i2, d2 = b.query_batch(Q, 3)
+        np.testing.assert_array_equal(i2, i1)
+        np.testing.assert_array_equal(d2, d1)
+        b.close()
+    a.close()

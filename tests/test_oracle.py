@@ -243,3 +243,52 @@ def test_index_leaves_respect_capacity():
     X = datagen.rows("walk", 58, 0, N, 128)
     ix = oracle.ISAXIndex(X, leaf_size=30)
     assert ix.leaf_sizes().max() <= 30
+
+
+def _words(rows):
+    """Series of length 16 (one point per segment, so PAA = the values): 0.1 has
+    symbol 2 (binary 10) and 1.0 symbol 3 (binary 11) at cardinality 4, whose
+    breakpoints are -0.674, 0, 0.674.  Every series has root key 1...1 and the
+    extra bit of a segment is 1 exactly where the value is 1.0."""
+    X = np.full((len(rows), 16), 0.1, dtype=np.float32)
+    for r, segs in enumerate(rows):
+        X[r, list(segs)] = 1.0
+    return X
+
+
+@pytest.mark.parametrize("rows,cap,sizes,ids", [
+    # capacity 2.  Insert 0,1,2: over capacity -> split {0,1,2}: segment 0 has
+    # ones {0,2}, segment 1 ones {1,2} (both |2*2-3| = 1), the rest none: the tie
+    # goes to segment 0 -> {1} | {0,2}.  3 joins {1}.  4 makes {0,2,4}: segment 0
+    # is at full cardinality; segments 1 and 2 tie (one 1 each) -> segment 1:
+    # {0,4} | {2}.  5 makes {0,4,5}: segments 0, 1 full; segment 2 -> {0,5} | {4}.
+    ([[0], [1], [0, 1], [], [0, 2], [0]], 2, [2, 2, 1, 1], [1, 3, 0, 5, 4, 2]),
+    # capacity 3: the split is decided on the first cap+1 members only.  {0..3}:
+    # segment 1 has ones {0,1} (|4-4| = 0), segment 0 ones {1} (2) -> segment 1:
+    # {2,3} | {0,1}.  4, 5 make {2,3,4,5}: segment 0 ones {4,5} -> {2,3} | {4,5};
+    # 6 joins {4,5}.  (All seven at once would have chosen segment 0 first.)
+    ([[1], [0, 1], [], [], [0], [0], [0]], 3, [2, 3, 2], [2, 3, 4, 5, 6, 0, 1]),
+    # capacity 1, two identical words: every split sends both to child 0 and
+    # leaves an empty child 1, segment after segment, until all 16 segments are
+    # at full cardinality; the leaf then stays over capacity.
+    ([[], []], 1, [2] + [0] * 16, [0, 1]),
+])
+def test_split_rule_worked_examples(rows, cap, sizes, ids):
+    """ADS+ leaf split (Section II): on overflow a leaf splits on the segment
+    whose extra bit divides its series most evenly (ties: lowest segment),
+    decided when the leaf first holds cap+1 series in insertion order."""
+    ix = oracle.ISAXIndex(_words(rows), card=4, leaf_size=cap)
+    np.testing.assert_array_equal(ix.leaf_sizes(), sizes)
+    assert ix.leaves == len(sizes)
+    np.testing.assert_array_equal(ix.leaf_ids(), ids)
+
+
+def test_leaf_ids_partition_the_collection():
+    N = 4000
+    X = datagen.rows("walk", 59, 0, N, 64)
+    ix = oracle.ISAXIndex(X, leaf_size=40)
+    ids, sizes = ix.leaf_ids(), ix.leaf_sizes()
+    assert np.array_equal(np.sort(ids), np.arange(N))
+    assert sizes.sum() == N
+    for a, b in zip(np.cumsum(sizes) - sizes, np.cumsum(sizes)):
+        assert (np.diff(ids[a:b]) > 0).all()  # insertion order inside a leaf
