@@ -146,8 +146,9 @@ isax_status isax_trim_memory(int32_t device);
  * Steps, all on the GPU: PAA of w segments and SAX symbols against N(0,1)
  * breakpoints; a stable radix sort of the bit-plane-interleaved iSAX keys
  * (first bit of every segment first: the root subtree of Section III); leaves
- * cut top-down from the sorted keys; rows and SAX words gathered into leaf
- * order; per-leaf min/max symbol envelopes.
+ * cut top-down from the sorted keys (with ISAX_BUILD_SPLIT_BALANCED: a sort by
+ * root key, then ADS+ node splitting one tree level at a time); rows and SAX
+ * words gathered into leaf order; per-leaf min/max symbol envelopes.
  * Errors: ISAX_ERR_INVALID_ARG (sizes, flags, null pointers, misaligned
  * pointer, a non-finite value anywhere in `series`), ISAX_ERR_OOM, ISAX_ERR_CUDA.
  */
