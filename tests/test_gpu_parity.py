@@ -516,6 +516,25 @@ def test_balanced_split_with_every_row_store():
               pkg.Index(X, leaf_size=200, split="balanced")]
     i1, d1 = a.query_batch(Q, 3)
     check_knn(i1, d1, X, Q, 3)
+    i0, d0 = a.query_batch_bf16(Q, 3)  # the tensor-core filtered batch on the same leaves
+    np.testing.assert_array_equal(i0, i1)
+    np.testing.assert_array_equal(d0, d1)
+    srv = pkg.Server(slots=4)  # the resident server on the same index
+    cid = srv.add(a)
+    for t, q in enumerate(Q):
+        srv.submit(cid, q, 3, t)
+    got = {}
+    for _ in range(400):
+        for r in srv.poll(64, wait_ms=50):
+            got[r["tag"]] = r
+        if len(got) == len(Q):
+            break
+    assert len(got) == len(Q)
+    for t in range(len(Q)):
+        assert got[t]["status"] == 0
+        np.testing.assert_array_equal(got[t]["idx"], i1[t])
+        np.testing.assert_array_equal(got[t]["dist"], d1[t])
+    srv.close()
     for b in others:
         eb = b.export()
         for key in ("orig", "leaf_begin", "sax", "env"):

@@ -49,12 +49,12 @@ def _call(fn, handle, q, k, on_device):
     return idx, dist
 
 
-@pytest.mark.parametrize("in_place", [False, True])
-def test_noalloc_query_matches_regular_query_twice_in_a_row(in_place):
+@pytest.mark.parametrize("in_place,split", [(False, "round-robin"), (True, "round-robin"), (False, "balanced")])
+def test_noalloc_query_matches_regular_query_twice_in_a_row(in_place, split):
     N, n = 50000, 256
     X = datagen.rows("walk", 21, 0, N, n)
     Q, _ = datagen.queries("walk", 21, N, n, 22, 3, 3, 0.05)
-    ix = pkg.Index(torch.from_numpy(X).cuda(), leaf_size=500, rows_in_place=in_place)
+    ix = pkg.Index(torch.from_numpy(X).cuda(), leaf_size=500, rows_in_place=in_place, split=split)
     lib = pkg.lib()
     for k in (1, 10):
         for b, q in enumerate(Q):
