@@ -47,6 +47,9 @@ UNIT = "queries/s"
 HBM_FALLBACK = 6800.0
 
 
+L2_BYTES = 129 * 1000 * 1000  # GB300 L2 (129 MB)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -92,8 +95,10 @@ def workload_config(a):
         "rows": ("read in place in the collection array by row id (leaves hold iSAX words and "
                  "row ids)" if a.rows == "in-place" else "copied into leaf order by every build"),
         "queries_per_step": a.queries,
-        "l2": "inputs larger than L2: the %.1f GB collection is streamed by every build"
-              % (a.N * a.n * 4 / 1e9),
+        "l2": ("inputs larger than L2: the %.1f GB collection is streamed by every build"
+               % (a.N * a.n * 4 / 1e9) if a.N * a.n * 4 > L2_BYTES else
+               "inputs NOT larger than L2 (%.3f GB collection): a small check, not a bench value"
+               % (a.N * a.n * 4 / 1e9)),
         "parallelism": "independent collection per GPU",
     }
 

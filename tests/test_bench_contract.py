@@ -1,0 +1,54 @@
+"""bench.py's output contract, checked on the CPU through its reference arm
+(the oracle timed on the host cores, on a small sample), and the refusal of its
+GPU arm to run without a GPU (no CPU fallback)."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench(args, env=None, timeout=300):
+    e = dict(os.environ)
+    e.update(env or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, env=e,
+                          capture_output=True, text=True, timeout=timeout)
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = _bench(["--impl", "reference", "--N", "20000", "--steps", "2", "--warmup", "1", "--queries", "10"])
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "queries/s"
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
+    assert d["data"] == "synthetic" and d["dtype"] == "f64"
+    assert "workload" in d["config"] and d["config"]["N"] == 20000
+    assert "NOT larger than L2" in d["config"]["l2"]  # a small check says so
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    # value = the step's queries / the step's time
+    q = d["config"]["queries_per_step"]
+    assert abs(q / (d["ms_per_step"] / 1e3) - d["value"]) <= 1e-6 * d["value"]
+
+
+def test_reference_arm_runs_on_rank_0_only():
+    r = _bench(["--impl", "reference", "--N", "20000", "--steps", "1", "--warmup", "0"], env={"RANK": "1"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_gpu_arm_refuses_to_run_without_a_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    r = _bench(["--steps", "1", "--warmup", "3", "--N", "20000", "--no-e2e", "--no-cpu-baseline",
+                "--no-serving", "--no-host-rows", "--batch", "0"], timeout=900)
+    assert r.returncode != 0
+    assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
