@@ -21,9 +21,12 @@ through the C ABI with host buffers (the 102.4 GB collection copied from pinned
 host memory by every build, queries and answers through host memory);
 `roofline` = the dominant kernel's algorithmic bytes per launch / its mean
 CUDA-event duration; `scan_roofline` = the same for the lower-bound scan
-(16 B per series bounded; MESSI queries here, the ParIS flat scan under
-`ablation_flat_scan`); `cpu_baseline` = the CPU oracle's FP64 brute force on a
-sample of the same workload.  `--impl reference` times that oracle alone.
+(16 B per series bounded; MESSI queries here, the ParIS flat scan and MESSI on
+an ADS+ balanced-split index under `ablation_flat_scan`); `query_roofline` = a
+whole query's algorithmic bytes (leaf envelopes, SAX words bounded, rows
+refined) over its mean latency; `cpu_baseline` = the CPU oracle's FP64 brute
+force on a sample of the same workload.  `--impl reference` times that oracle
+alone.
 
 With --gpus N > 1 (torchrun, one process per GPU) every rank runs the job on
 its own collection (seed = rank): independent problems, no collective on the
@@ -208,6 +211,19 @@ def kernel_bytes(name, a, launches, acc):
     if name == "q_approx":
         return row * acc["approx_series"]
     return None
+
+
+def query_roofline(acc, n_queries, leaves, n, q_time_ms, hbm):
+    """A whole query against HBM: algorithmic bytes per query = 32 per leaf
+    (every leaf's envelope is bounded) + 16 per SAX word bounded + one full row
+    (4n) per series refined (approximate-answer leaves included; early
+    abandoning would read less), over the mean CUDA-event latency of a query."""
+    if not n_queries or not q_time_ms:
+        return None
+    b = (32.0 * leaves + 16.0 * acc["series_lb"] / n_queries + 4.0 * n * acc["series_refined"] / n_queries)
+    t = q_time_ms / n_queries / 1e3
+    return {"bound": "hbm", "algorithmic_bytes_per_query": b, "mean_query_ms": t * 1e3,
+            "achieved": b / t / 1e9, "peak": hbm, "unit": "GB/s", "frac": b / t / 1e9 / hbm}
 
 
 def kernel_source_hash(kernel):
@@ -949,6 +965,7 @@ def main():
         "kernels": kernels,
         "scan_roofline": scan_roofline(qprof, stats_acc["series_lb"] / a.steps, hbm,
                                        "messi_%dMx%d" % (a.N // 1000000, a.n)),
+        "query_roofline": query_roofline(stats_acc, len(lat_ms), info["leaves"], n, q_time_ms, hbm),
         "gpu_launches": launches,
         "clocks": clock_info,
     }

@@ -52,3 +52,18 @@ def test_gpu_arm_refuses_to_run_without_a_gpu():
                 "--no-serving", "--no-host-rows", "--batch", "0"], timeout=900)
     assert r.returncode != 0
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_query_roofline_arithmetic():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    acc = {"series_lb": 814_000_000, "series_refined": 7_650_000}
+    r = bench.query_roofline(acc, 100, 151_497, 256, 13.1, 6701.5)
+    b = 32 * 151_497 + 16 * 8_140_000 + 4 * 256 * 76_500
+    assert r["algorithmic_bytes_per_query"] == pytest.approx(b)
+    assert r["mean_query_ms"] == pytest.approx(0.131)
+    assert r["achieved"] == pytest.approx(b / 0.131e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6701.5)
+    assert bench.query_roofline(acc, 0, 1, 256, 0.0, 6701.5) is None
