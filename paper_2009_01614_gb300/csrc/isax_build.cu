@@ -14,6 +14,9 @@
 //                node splits on the next key bit (round-robin over segments),
 //                decided for every adjacent pair from its common-prefix length
 //                and a sliding-window maximum (no pointer tree is built);
+//                or, with ISAX_BUILD_SPLIT_BALANCED, the ADS+ split itself: a
+//                sort by root key, then one pass per tree level that splits
+//                every overflowing node on its most balanced segment;
 //   permute    - rows and SAX words gathered into leaf order;
 //   envelopes  - per-leaf min/max symbol of every segment.
 #include <algorithm>
