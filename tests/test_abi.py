@@ -69,6 +69,13 @@ def test_build_rejects_bad_arguments(lib):
     _expect(lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out)), 1, "leaf_size")
     q = pkg.BuildParams(16, 256, 10, 32)
     _expect(lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out)), 1, "mem_flags")
+    # the balanced split is a known flag, alone and with the row stores: argument checks pass it
+    for fl in (pkg.BUILD_SPLIT_BALANCED, pkg.BUILD_SPLIT_BALANCED | pkg.BUILD_ROWS_HOST):
+        q = pkg.BuildParams(16, 256, 10, fl)
+        st = lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out))
+        assert st != 1 or "mem_flags" not in pkg.isax_last_error(), pkg.isax_last_error()
+        if st == 0:
+            pkg.isax_free_index(out.value)
     # rows read in place need device-resident series, and exclude rows in host memory
     q = pkg.BuildParams(16, 256, 10, pkg.BUILD_ROWS_IN_PLACE)
     _expect(lib.isax_build_index(ptr, 4, 32, ctypes.byref(q), None, ctypes.byref(out)), 1,
