@@ -67,3 +67,23 @@ def test_query_roofline_arithmetic():
     assert r["achieved"] == pytest.approx(b / 0.131e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6701.5)
     assert bench.query_roofline(acc, 0, 1, 256, 0.0, 6701.5) is None
+
+
+def test_traffic_entries_resolve_to_kernel_sources():
+    """Every measured-traffic entry names a kernel whose source the bench can
+    hash, and an entry is returned only under the hash it was taken on."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod2", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    entries = [l.split() for l in open(os.path.join(ROOT, "profiles", "traffic.txt"))
+               if l.strip() and not l.startswith("#")]
+    assert entries
+    for label, digest, nbytes, source in (e[:4] for e in entries):
+        kernel = label.split(":")[0]
+        h = bench.kernel_source_hash(kernel)
+        assert len(h) == 16 and float(nbytes) > 0 and source.startswith("ncu:")
+        got = bench.traffic_from_profile(kernel, label)
+        assert (got is not None) == (h == digest)
+        if got is not None:
+            assert got == (float(nbytes), source)
