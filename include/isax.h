@@ -233,10 +233,9 @@ isax_status isax_summarize(const float* series, int64_t N, int32_t n, int32_t ca
 /*
  * isax_query_knn_noalloc - the same exact k-NN query as isax_query_knn (same
  * arguments, same answers) for callers that must not allocate device memory
- * while they query: a runtime that owns all GPU memory through its own pool, a
- * latency-critical serving thread for which an allocation can stall on the
- * driver, or code being recorded into a CUDA graph, where allocation calls are
- * not allowed.  The paper has no counterpart; it is a deployment feature.
+ * while they query: a runtime that owns all GPU memory through its own pool, or
+ * a latency-critical serving thread for which an allocation can stall on the
+ * driver.  The paper has no counterpart; it is a deployment feature.
  *
  * Its scratch is one device array built into the library, of
  * ISAX_NOALLOC_SCRATCH_BYTES, held by every GPU that loads the library until

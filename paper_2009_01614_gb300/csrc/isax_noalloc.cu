@@ -2,10 +2,9 @@
 //
 // Some callers cannot allocate device memory while they answer a query: a
 // host runtime that owns every byte of the GPU through its own pool and treats
-// any allocation behind its back as a bug, a latency-critical serving thread
+// any allocation behind its back as a bug, or a latency-critical serving thread
 // for which cudaMalloc / cudaMallocAsync can block on the driver or on other
-// streams, or code that records its launches into a CUDA graph, where an
-// allocation call is not allowed.  For them, isax_query_knn_noalloc runs the
+// streams.  For them, isax_query_knn_noalloc runs the
 // same query kernels as isax_query_knn on scratch that lives in one
 // file-scope device array, fixed in size when the library is loaded and kept by
 // every GPU that loads it until the process exits.
