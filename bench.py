@@ -28,9 +28,15 @@ refined) over its mean latency; `cpu_baseline` = the CPU oracle's FP64 brute
 force on a sample of the same workload.  `--impl reference` times that oracle
 alone.
 
-With --gpus N > 1 (torchrun, one process per GPU) every rank runs the job on
-its own collection (seed = rank): independent problems, no collective on the
-data path; the barrier and the max over ranks only frame the timing.
+With --gpus N > 1 (torchrun, one process per GPU) the collection is N times
+larger and sharded by rows: rank r holds rows [r N, (r + 1) N) of the one
+seeded collection (N = --N per rank) and builds its own index over them; every
+query is answered on every shard, each rank attaches the FP64 squared distance
+of its k answers (isax_exact_d2), one NCCL all-gather per step carries every
+query's k (row, distance, squared distance) triples of all ranks, and each rank
+merges them by (FP64 squared distance, global row): the exact answer over the
+whole collection.  Per-GPU work is fixed as N grows ("scaling": "weak"); `value`
+counts each query once.
 """
 import argparse
 import hashlib
@@ -74,6 +80,10 @@ def parse():
                          "80M x 128, 10M x 1024)")
     ap.add_argument("--serve-requests", type=int, default=3000,
                     help="serving workload: requests per arrival rate")
+    ap.add_argument("--no-hardness", action="store_true",
+                    help="skip the query-hardness leg (50M sinusoid series, member queries by noise level)")
+    ap.add_argument("--no-floor", action="store_true",
+                    help="skip the measured GPU brute-force floor and the host round-trip latency")
     ap.add_argument("--no-host-rows", action="store_true",
                     help="skip the leg with the index's rows in host memory")
     ap.add_argument("--workload", choices=["walk", "hardness", "serving"], default="walk",
@@ -87,7 +97,7 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(a):
+def workload_config(a, world=1):
     return {
         "workload": "random-walk collection %d x %d fp32 z-normalised (seed = rank), iSAX w=16 "
                     "card=256 leaf=%d; per step: full index build + %d exact %d-NN queries "
@@ -98,11 +108,15 @@ def workload_config(a):
         "rows": ("read in place in the collection array by row id (leaves hold iSAX words and "
                  "row ids)" if a.rows == "in-place" else "copied into leaf order by every build"),
         "queries_per_step": a.queries,
+        "gpus_sharing_the_collection": world,
+        "collection_rows": a.N * world,
         "l2": ("inputs larger than L2: the %.1f GB collection is streamed by every build"
                % (a.N * a.n * 4 / 1e9) if a.N * a.n * 4 > L2_BYTES else
                "inputs NOT larger than L2 (%.3f GB collection): a small check, not a bench value"
                % (a.N * a.n * 4 / 1e9)),
-        "parallelism": "independent collection per GPU",
+        "parallelism": ("row shards of one %d x %d collection, one per GPU; one all-gather of every "
+                        "query's k (row, distance, FP64 squared distance) per step, exact merge" % (a.N * world, a.n)
+                        if world > 1 else "one GPU"),
     }
 
 
@@ -116,11 +130,12 @@ def peaks():
         return HBM_FALLBACK, "fallback"
 
 
-def make_queries(a, rank):
+def make_queries(a, world):
+    """The step's queries over the whole (world x N row) collection: fresh walks
+    of seed 1, then members of the collection with sigma 0.01 noise."""
     import datagen
     nq_member = a.queries // 10
-    Q, src = datagen.queries("walk", rank, a.N, a.n, 1 + 1000 * rank, a.queries - nq_member,
-                             nq_member, 0.01)
+    Q, src = datagen.queries("walk", 0, a.N * world, a.n, 1, a.queries - nq_member, nq_member, 0.01)
     return Q, src
 
 
@@ -207,7 +222,12 @@ def kernel_bytes(name, a, launches, acc):
     if name == "q_series_lb":
         return 16 * acc["series_lb"]
     if name == "q_refine":
-        return row * (acc["series_refined"] - acc["approx_series"])
+        # the row floats actually read outside the approximate answer (early
+        # abandoning stops a row before its end)
+        return 4 * (acc["ed_floats"] - n * acc["approx_series"])
+    if name == "q_front":
+        # every leaf's envelope and the approximate answer's rows
+        return 32 * acc["leaves_total"] + row * acc["approx_series"]
     if name == "q_approx":
         return row * acc["approx_series"]
     return None
@@ -215,12 +235,13 @@ def kernel_bytes(name, a, launches, acc):
 
 def query_roofline(acc, n_queries, leaves, n, q_time_ms, hbm):
     """A whole query against HBM: algorithmic bytes per query = 32 per leaf
-    (every leaf's envelope is bounded) + 16 per SAX word bounded + one full row
-    (4n) per series refined (approximate-answer leaves included; early
-    abandoning would read less), over the mean CUDA-event latency of a query."""
+    (every leaf's envelope is bounded) + 16 per SAX word bounded + 4 per row
+    value read by the refinement (approximate-answer rows included; an
+    abandoned row counts the part read), over the mean CUDA-event latency of a
+    query."""
     if not n_queries or not q_time_ms:
         return None
-    b = (32.0 * leaves + 16.0 * acc["series_lb"] / n_queries + 4.0 * n * acc["series_refined"] / n_queries)
+    b = (32.0 * leaves + 16.0 * acc["series_lb"] / n_queries + 4.0 * acc["ed_floats"] / n_queries)
     t = q_time_ms / n_queries / 1e3
     return {"bound": "hbm", "algorithmic_bytes_per_query": b, "mean_query_ms": t * 1e3,
             "achieved": b / t / 1e9, "peak": hbm, "unit": "GB/s", "frac": b / t / 1e9 / hbm}
@@ -712,20 +733,15 @@ def reference_arm(a):
 
 
 # ------------------------------------------------------------------ query hardness
-def hardness(a):
-    """Sum-of-3-sinusoids collection (default 50M x 256): 50 member queries per
-    noise level sigma in {0.01, 0.1, 0.5, 1.0}, each answered for k in {1, 10,
-    100}; per (sigma, k): leaf and series pruning, series refined, floats read
-    by refinement, latency.  One JSON line."""
+def hardness_leg(a, pkg, torch, datagen, queries_per_level=50):
+    """Query hardness (the sum-of-3-sinusoids collection, 50M x 256 unless --N
+    says otherwise): member queries with noise sigma in {0.01, 0.1, 0.5, 1.0},
+    each answered for k in {1, 10, 100}; per (sigma, k): leaf and series
+    pruning, series refined, row floats actually read by the refinement (early
+    abandoning stops a row early), latency."""
     import numpy as np
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    import datagen
-    import paper_2009_01614_gb300 as pkg
     N = a.N if a.N != 100_000_000 else 50_000_000
     n = a.n
-    torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     X = torch.empty((N, n), dtype=torch.float32, device="cuda")
     datagen.rows_device("sine", 0, 0, N, n, X.data_ptr(), stream.cuda_stream)
@@ -739,9 +755,10 @@ def hardness(a):
     info = ix.info()
     rows = []
     for si, sigma in enumerate([0.01, 0.1, 0.5, 1.0]):
-        Q, _ = datagen.queries("sine", 0, N, n, 3 + si, 0, 50, sigma)
+        Q, _ = datagen.queries("sine", 0, N, n, 3 + si, 0, queries_per_level, sigma)
         Qd = torch.from_numpy(Q).cuda()
         for k in [1, 10, 100]:
+            ix.query(Qd[0], k)  # its query graph
             lat, st_all = [], []
             for b in range(len(Q)):
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -760,15 +777,96 @@ def hardness(a):
                 "series_pruning_by_lb": 1.0 - (mean("series_refined") - mean("approx_series"))
                 / max(1.0, mean("series_lb")),
                 "series_refined_per_query": mean("series_refined"),
-                "ed_floats_read_per_query": mean("series_refined") * n,
+                "ed_floats_read_per_query": mean("ed_floats"),
+                "ed_floats_if_rows_read_whole": mean("series_refined") * n,
                 "latency_ms_p50": float(np.percentile(lat, 50)),
                 "latency_ms_p99": float(np.percentile(lat, 99)),
             })
     ix.close()
-    print(json.dumps({"workload": "query hardness: %d sum-of-3-sinusoid series x %d fp32, leaf %d; "
-                                  "50 member queries per noise level" % (N, n, a.leaf),
-                      "build_s": build_s, "leaves": info["leaves"], "rows": rows}), flush=True)
+    torch.cuda.synchronize()
+    return {"workload": "query hardness: %d sum-of-3-sinusoid series x %d fp32, leaf %d; %d member "
+                        "queries per noise level" % (N, n, a.leaf, queries_per_level),
+            "build_s": build_s, "leaves": info["leaves"], "rows": rows}
+
+
+def hardness(a):
+    """The hardness leg alone, as one JSON line (--workload hardness)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import datagen
+    import paper_2009_01614_gb300 as pkg
+    torch.cuda.set_device(0)
+    print(json.dumps(hardness_leg(a, pkg, torch, datagen)), flush=True)
     return 0
+
+
+# ------------------------------------------------------------------ host round trip, floors
+def host_latency_leg(a, X, Qh, pkg, torch, stream):
+    """Single queries through the C ABI with HOST buffers: every call copies its
+    1 KB query to the device and its k results back, and returns when they are
+    in host memory; per-query wall-clock latency (the caller's view)."""
+    import numpy as np
+    sp = stream.cuda_stream
+    ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp, rows_in_place=a.rows == "in-place")
+    Qp = torch.from_numpy(Qh).pin_memory().numpy()
+    for b in range(3):
+        ix.query(Qp[b], a.k, stream=sp)
+    lat = []
+    for b in range(len(Qp)):
+        t0 = time.perf_counter()
+        ix.query(Qp[b], a.k, stream=sp)
+        lat.append((time.perf_counter() - t0) * 1e3)
+    ix.close()
+    return {"latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(np.mean(lat))},
+            "queries_per_s": len(lat) / (sum(lat) / 1e3),
+            "h2d_bytes_per_query": a.n * 4, "d2h_bytes_per_query": a.k * (8 + 4),
+            "how": "wall clock around isax_query_knn with pinned host query and host outputs"}
+
+
+def bruteforce_floor(a, X, Qd, torch, stream, queries=5):
+    """The GPU brute-force floor, measured: every query reads the whole
+    collection once (cuBLAS GEMV X q, then the smallest ||x||^2 - 2 x.q): the
+    bytes a scan without an index must move.  A floor, not an exact answer."""
+    norms = (X * X).sum(dim=1)
+    torch.cuda.synchronize()
+    times = []
+    for b in range(queries + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d = norms - 2.0 * torch.mv(X, Qd[b])
+        torch.argmin(d)
+        e1.record(stream)
+        e1.synchronize()
+        if b > 0:
+            times.append(e0.elapsed_time(e1))
+    del norms, d
+    ms = sum(times) / len(times)
+    return {"ms_per_query": ms, "queries_per_s": 1e3 / ms, "bytes_per_query": a.N * a.n * 4,
+            "GB_per_s": a.N * a.n * 4 / (ms / 1e3) / 1e9, "queries": queries,
+            "how": "torch.mv (cuBLAS) over the resident collection + argmin, CUDA events"}
+
+
+def isax_oracle_baseline(a, sample_rows=1_000_000, n_queries=10):
+    """The CPU oracle's single-threaded iSAX index (ADS+ tree, MESSI-style exact
+    search, FP64) on a bounded sample of the collection: seconds per exact query."""
+    import datagen
+    import oracle
+    X = datagen.rows("walk", 0, 0, sample_rows, a.n)
+    Q, _ = datagen.queries("walk", 0, sample_rows, a.n, 1, n_queries - n_queries // 10, n_queries // 10, 0.01)
+    t0 = time.perf_counter()
+    ix = oracle.ISAXIndex(X, 16, 256, a.leaf)
+    build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for q in Q:
+        ix.query(q, a.k)
+    per_q = (time.perf_counter() - t0) / len(Q)
+    return {"value": 1.0 / per_q, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "seconds_per_query": per_q, "build_s": build_s,
+            "sample": "single-threaded FP64 iSAX index (oracle) over the first %d rows of the collection, %d "
+                      "queries (not scaled: its query time grows with N)" % (sample_rows, len(Q))}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -816,8 +914,9 @@ def main():
 
     # inputs: collection generated on the device (bit-identical to the host generator)
     X = torch.empty((N, n), dtype=torch.float32, device="cuda")
-    datagen.rows_device("walk", rank, 0, N, n, X.data_ptr(), sp)
-    Qh, src = make_queries(a, rank)
+    # this rank's rows of the collection (all of it on one GPU)
+    datagen.rows_device("walk", 0, rank * N, N, n, X.data_ptr(), sp)
+    Qh, src = make_queries(a, world)
     Qd = torch.from_numpy(Qh).cuda()
     torch.cuda.synchronize()
     # the end-to-end leg's page-locked host copy of the collection, taken now while
@@ -846,10 +945,13 @@ def main():
 
     lat_ms = []
     stats_acc = {"series_lb": 0, "series_refined": 0, "approx_series": 0, "leaves_queued": 0,
-                 "leaves_scanned": 0, "candidates": 0, "window": 0}
+                 "leaves_scanned": 0, "candidates": 0, "window": 0, "ed_floats": 0, "leaves_total": 0}
+
+    from paper_2009_01614_gb300 import shard
 
     def step(record, rows=a.rows):
         ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp, rows_in_place=rows == "in-place")
+        res_i, res_d = [], []
         for b in range(a.queries):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -861,7 +963,17 @@ def main():
                 lat_ms.append(e0.elapsed_time(e1))
                 for key in stats_acc:
                     stats_acc[key] += st[key]
-            last = (i, d)
+            res_i.append(i)
+            res_d.append(d)
+        last = (res_i[-1], res_d[-1])
+        if dist is not None:
+            # row shards: the FP64 squared distances of this shard's answers, one
+            # all-gather of every query's k triples, the exact merge
+            I, D = torch.stack(res_i), torch.stack(res_d)
+            D2 = ix.exact_d2(Qd, I, stream=sp)
+            gi, gd, _ = shard.gather_merge(I.cpu().numpy(), D.cpu().numpy(), D2.cpu().numpy(), k, rank * N,
+                                           world, device=torch.device("cuda", local))
+            last = (gi[-1], gd[-1])
         info = ix.info()
         ix.close()
         return info, last
@@ -894,7 +1006,9 @@ def main():
     pkg.isax_profile(0)
     qprof = {nm: v for nm, v in pkg.isax_profile_report().items() if nm.startswith("q_")}
 
-    total_queries = a.queries * a.steps * world
+    # each query is answered once over the whole collection (its shards
+    # together on N > 1 GPUs)
+    total_queries = a.queries * a.steps
     value = total_queries / (elapsed_ms / 1e3)
     q_time_ms = sum(lat_ms)
     build_ms = (elapsed_ms - q_time_ms) / a.steps
@@ -939,6 +1053,13 @@ def main():
     # batched queries: the plain FP32 path against the tensor-core (BF16) filter
     batch_info = batch_leg(a, X, pkg, torch, stream, rank) if a.batch > 0 else None
 
+    # the caller's view of a single query (host buffers: 1 KB in, k results out)
+    # and the brute-force floor, measured on the resident collection
+    host_rt = floor = None
+    if not a.no_floor:
+        host_rt = host_latency_leg(a, X, Qh, pkg, torch, stream)
+        floor = bruteforce_floor(a, X, Qd, torch, stream)
+
     lat_sorted = sorted(lat_ms)
 
     def pct(p):
@@ -951,10 +1072,12 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": elapsed_ms / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(a),
+        "config": workload_config(a, world),
         "roofline": roof,
         "latency_ms": {"p50": pct(50), "p99": pct(99), "mean": statistics.mean(lat_ms)},
         "query_qps": len(lat_ms) / (q_time_ms / 1e3) if q_time_ms else None,
+        "latency_host_round_trip": host_rt,
+        "bruteforce_floor": floor,
         "build_ms": build_ms, "build_input_GB_per_s": N * n * 4 / 1e9 / (build_ms / 1e3),
         "index": {"leaves": info["leaves"], "max_leaf": info["max_leaf"]},
         "pruning": {key + "_per_query": stats_acc[key] / max(1, len(lat_ms)) for key in stats_acc},
@@ -1030,7 +1153,7 @@ def main():
     elif not a.no_host_rows and (a.no_e2e or e2e_skip is not None or empty_host is not None):
         torch.cuda.synchronize()
         X = torch.empty((N, n), dtype=torch.float32, device="cuda")
-        datagen.rows_device("walk", rank, 0, N, n, X.data_ptr(), sp)
+        datagen.rows_device("walk", 0, rank * N, N, n, X.data_ptr(), sp)
         Qd = torch.from_numpy(Qh).cuda()
         out["rows_in_host_memory"] = host_rows_leg(a, X, Qd, pkg, torch, stream)
         del X, Qd
@@ -1045,8 +1168,14 @@ def main():
         torch.cuda.empty_cache()
         out["serving"] = serving_leg(a, pkg, torch)
 
+    if rank == 0 and not a.no_hardness and world == 1:
+        # query hardness (config 2): its own 50M-row collection, after the others are freed
+        torch.cuda.empty_cache()
+        out["hardness"] = hardness_leg(a, pkg, torch, datagen)
+
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, min(a.cpu_sample_rows, N))
+        out["cpu_baseline_isax_index"] = isax_oracle_baseline(a)
 
     if rank == 0:
         print(json.dumps(out), flush=True)

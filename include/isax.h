@@ -92,6 +92,8 @@ typedef struct isax_query_stats {
     int64_t window;           /* candidates re-ranked in FP64 */
     int32_t approx_leaf;      /* leaf used for the approximate answer */
     int32_t reruns;           /* reruns after a candidate-buffer overflow */
+    int64_t ed_floats;        /* row values read for exact distances (early abandoning stops a
+                                 row before its end; on the BF16 path, the fp32 re-checks) */
 } isax_query_stats;
 
 typedef struct isax_index_info {
@@ -222,6 +224,27 @@ isax_status isax_index_export(const isax_index* ix, uint8_t* sax, uint32_t* orig
  */
 isax_status isax_summarize(const float* series, int64_t N, int32_t n, int32_t cardinality,
                            uint32_t mem_flags, uint8_t* out_sax, float* out_paa, void* cuda_stream);
+
+/*
+ * isax_exact_d2 - FP64 squared Euclidean distances of given series of the
+ * collection to given queries, each summed with the definition's order
+ * (Section II, Similarity Search: the distance of the NN problem; elements in
+ * ascending order, every difference, square and sum rounded to FP64 on its
+ * own, no fused multiply-add).  out_d2[b][j] = d^2(Q[b], series idx[b][j]).
+ * These are the values the brute-force definition orders by, so the answers
+ * of row shards of one collection (each an exact k-NN of its own rows) merge
+ * exactly when ordered by (out_d2, global row): two rows of different shards
+ * whose fp32 distances tie are still put in their exact order.
+ *   Q      [B][n] fp32, idx [B][k] int64 original rows (host or device per
+ *          ISAX_MEM_INPUT_DEVICE); out_d2 [B][k] (host or device per
+ *          ISAX_MEM_OUTPUT_DEVICE).  A row outside [0, N) gives NaN.
+ * The first call on an index whose rows are in leaf order builds the map from
+ * original row to leaf position (4 N bytes, kept until isax_free_index).
+ * Synchronises cuda_stream.  Errors: ISAX_ERR_INVALID_ARG, ISAX_ERR_OOM,
+ * ISAX_ERR_CUDA.
+ */
+isax_status isax_exact_d2(const isax_index* ix, const float* Q, int32_t B, int32_t k, uint32_t mem_flags,
+                          const int64_t* idx, double* out_d2, void* cuda_stream);
 
 /* ------------------------------------------------------------ allocation-free query */
 

@@ -20,7 +20,7 @@ __all__ = [
     "isax_last_error", "isax_get_index_info", "isax_index_export", "isax_summarize",
     "isax_set_allocator", "isax_trim_memory", "isax_profile", "isax_profile_report", "isax_launch_count",
     "isax_query_knn_noalloc", "isax_tc_selftest", "isax_query_knn_batch_bf16",
-    "isax_prepare_bf16", "isax_query_knn_flat", "Server", "ServerParams", "ServerResult", "ServerInfo",
+    "isax_prepare_bf16", "isax_query_knn_flat", "isax_exact_d2", "Server", "ServerParams", "ServerResult", "ServerInfo",
     "isax_server_create", "isax_server_add_collection", "isax_server_submit", "isax_server_poll",
     "isax_server_get_info", "isax_server_clock", "isax_server_destroy",
 ]
@@ -56,7 +56,7 @@ class QueryStats(ctypes.Structure):
                 ("series_refined", ctypes.c_int64), ("approx_series", ctypes.c_int64),
                 ("candidates", ctypes.c_int64),
                 ("window", ctypes.c_int64), ("approx_leaf", ctypes.c_int32),
-                ("reruns", ctypes.c_int32)]
+                ("reruns", ctypes.c_int32), ("ed_floats", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -173,6 +173,8 @@ def lib():
         L.isax_server_get_info.restype = st
         L.isax_server_clock.argtypes = []
         L.isax_server_clock.restype = ctypes.c_double
+        L.isax_exact_d2.argtypes = [vp, vp, i32, i32, u32, vp, vp, vp]
+        L.isax_exact_d2.restype = st
         L.isax_server_destroy.argtypes = [vp]
         L.isax_server_destroy.restype = None
         _lib = L
@@ -225,6 +227,11 @@ def isax_query_knn_batch(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_pt
 def isax_query_knn_flat(index, q_ptr, k, mem_flags, out_idx_ptr, out_dist_ptr, stats=None, stream=0):
     _check(lib().isax_query_knn_flat(index, q_ptr, k, mem_flags, out_idx_ptr, out_dist_ptr, stats,
                                      stream))
+
+
+def isax_exact_d2(index, Q_ptr, B, k, mem_flags, idx_ptr, out_d2_ptr, stream=0):
+    """FP64 squared distances of rows idx[b][j] to queries Q[b], definition order."""
+    _check(lib().isax_exact_d2(index, Q_ptr, B, k, mem_flags, idx_ptr, out_d2_ptr, stream))
 
 
 def isax_query_knn_batch_bf16(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_ptr, stats=None,
@@ -426,6 +433,39 @@ class Index:
     def query_batch_bf16(self, Q, k=1, stats=False, stream=None):
         """Same answers as query_batch, through the tensor-core (BF16) filter."""
         return self._run(Q, k, stats, stream, batch="bf16")
+
+    def exact_d2(self, Q, idx, stream=None):
+        """FP64 squared distances [B, k] of the original rows idx [B, k] to the
+        queries Q [B, n], summed in the definition's order (isax_exact_d2):
+        the values by which row shards' answers merge exactly.  CUDA tensors
+        in give a CUDA float64 tensor out; otherwise a numpy array."""
+        import numpy as np
+        if _is_torch(Q) and Q.is_cuda and _is_torch(idx) and idx.is_cuda:
+            import torch
+            Qc = Q.contiguous()
+            Ic = idx.to(torch.int64).contiguous()
+            if Qc.dim() != 2 or Qc.shape[1] != self.n or Ic.dim() != 2 or Ic.shape[0] != Qc.shape[0]:
+                raise ValueError("queries must be [B, %d] and idx [B, k]" % self.n)
+            out = torch.empty(Ic.shape, dtype=torch.float64, device=Qc.device)
+            isax_exact_d2(self._h, Qc.data_ptr(), Ic.shape[0], Ic.shape[1],
+                          MEM_INPUT_DEVICE | MEM_OUTPUT_DEVICE, Ic.data_ptr(), out.data_ptr(),
+                          _stream_of(Qc, stream))
+            return out
+        ptr, on_dev, keep, shape = _buffer(Q)
+        if len(shape) != 2 or shape[1] != self.n:
+            raise ValueError("queries must be [B, %d]" % self.n)
+        if _is_torch(idx):
+            idx = idx.detach().cpu().numpy()
+        I = np.ascontiguousarray(idx, dtype=np.int64)
+        if I.ndim != 2 or I.shape[0] != shape[0]:
+            raise ValueError("idx must be [B, k]")
+        B, k = I.shape
+        out = np.empty((B, k), np.float64)
+        if on_dev:
+            keep = keep.detach().cpu().numpy()
+            ptr = keep.ctypes.data
+        isax_exact_d2(self._h, ptr, B, k, 0, I.ctypes.data, out.ctypes.data, _stream_of(None, stream))
+        return out
 
     def prepare_bf16(self, stream=None):
         """Build the BF16 copy of the collection used by query_batch_bf16."""

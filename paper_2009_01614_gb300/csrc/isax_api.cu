@@ -128,12 +128,13 @@ static void fill_stats(isax_query_stats* st, const isax_index* ix, const QCtl& c
     st->leaves_queued = (int64_t)c.leaves_queued;
     st->leaves_scanned = (int64_t)c.leaves_scanned;
     st->series_lb = (int64_t)c.series_lb;
-    st->series_refined = (int64_t)c.series_refined;
+    st->series_refined = (int64_t)c.refined_total;
     st->approx_series = (int64_t)c.approx_series;
-    st->candidates = (int64_t)c.cand_count;
+    st->candidates = (int64_t)c.cand_total;
     st->window = (int64_t)c.window;
     st->approx_leaf = c.approx_leaf;
     st->reruns = reruns;
+    st->ed_floats = (int64_t)c.ed_floats;
 }
 
 // one query whose input already sits in ix->qs.q; copies the results out
@@ -366,6 +367,49 @@ isax_status isax_query_knn_batch_bf16(const isax_index* cix, const float* Q, int
             if (cx->stats) fill_stats(cx->stats + b, cx->ix, c, reruns);
         };
         query_batch_tc(ix, Q, B, k, mem_flags, out_idx, out_dist, fill, &ctx, st);
+        ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    });
+}
+
+isax_status isax_exact_d2(const isax_index* cix, const float* Q, int32_t B, int32_t k, uint32_t mem_flags,
+                          const int64_t* idx, double* out_d2, void* cuda_stream) {
+    return guarded([&] {
+        check(cix != nullptr, "index is NULL");
+        check(B >= 0 && k >= 1 && k <= ISAX_MAX_K, "B must be >= 0 and k in [1, 1024]");
+        check(B == 0 || (Q != nullptr && idx != nullptr && out_d2 != nullptr), "NULL queries, rows or output");
+        check((mem_flags & ~(uint32_t)(ISAX_MEM_INPUT_DEVICE | ISAX_MEM_OUTPUT_DEVICE)) == 0,
+              "unknown mem_flags bits");
+        if (B == 0) return;
+        isax_index* ix = const_cast<isax_index*>(cix);
+        DeviceGuard dg(ix->device);
+        std::lock_guard<std::mutex> lk(*static_cast<std::mutex*>(ix->mu));
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        const size_t qb = sizeof(float) * (size_t)B * ix->d.n, ib = sizeof(int64_t) * (size_t)B * k,
+                     ob = sizeof(double) * (size_t)B * k;
+        const bool in_dev = (mem_flags & ISAX_MEM_INPUT_DEVICE) != 0, out_dev = (mem_flags & ISAX_MEM_OUTPUT_DEVICE) != 0;
+        // host inputs and outputs go through device staging
+        struct Tmp {
+            void* p = nullptr;
+            cudaStream_t st;
+            ~Tmp() { if (p) dev_free(p, st); }
+        } tq{nullptr, st}, ti{nullptr, st}, to{nullptr, st};
+        const float* dq = Q;
+        const int64_t* di = idx;
+        double* dout = out_d2;
+        if (!in_dev) {
+            tq.p = dev_alloc(qb, st);
+            ti.p = dev_alloc(ib, st);
+            ISAX_CUDA_TRY(cudaMemcpyAsync(tq.p, Q, qb, cudaMemcpyHostToDevice, st));
+            ISAX_CUDA_TRY(cudaMemcpyAsync(ti.p, idx, ib, cudaMemcpyHostToDevice, st));
+            dq = static_cast<const float*>(tq.p);
+            di = static_cast<const int64_t*>(ti.p);
+        }
+        if (!out_dev) {
+            to.p = dev_alloc(ob, st);
+            dout = static_cast<double*>(to.p);
+        }
+        exact_d2_device(ix, dq, B, k, di, dout, st);
+        if (!out_dev) ISAX_CUDA_TRY(cudaMemcpyAsync(out_d2, dout, ob, cudaMemcpyDeviceToHost, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
     });
 }

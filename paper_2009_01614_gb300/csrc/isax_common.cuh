@@ -17,6 +17,12 @@ constexpr int MAX_LEN = ISAX_MAX_LEN;
 constexpr int ROOT_BITS = W;       // root key: first bit of each of the 16 segments
 
 constexpr int NBINS = 256;         // leaf ordering bins (lower bound / threshold)
+constexpr int APPROX_NEIGHBORS = 2; // leaves on each side of the descent leaf in the approximate answer
+// rows of the approximate answer at most (its leaves, widened until they hold k
+// rows): a query's first candidate slots
+inline uint32_t approx_rows_max(int leaf_size, int k) {
+    return (uint32_t)((2 * APPROX_NEIGHBORS + 1) * leaf_size + k);
+}
 constexpr uint64_t EMPTY_SLOT = ~0ull;
 
 // ---------------------------------------------------------------- errors
@@ -100,14 +106,20 @@ struct QCtl {
     uint8_t qsym[16];      // query symbols
     uint32_t work_count;   // scan work items (pieces of the queued leaves)
     uint32_t cand_count;   // candidate appends attempted (may exceed capacity)
+    uint32_t cand_base;    // candidate slots [0, cand_base) hold the approximate answer's rows
     uint32_t surv_count;   // series whose bound passed (appended; may exceed capacity)
     uint32_t window;       // candidates re-ranked in FP64
     uint32_t flags;        // QF_* bits
     float thr_lb0;         // bound threshold the work list was binned with
+    float thr_scan;        // squared-bound threshold of the series scan (from the approximate answer)
+    uint32_t grid_sync;    // arrivals at the binning step's grid barrier
+    uint32_t cand_total, pad0;  // candidate appends and
+    unsigned long long refined_total;  // series refined, saved by q_finalize (which clears the live counts)
     float qpaa[16];        // query PAA (fp32, as used by the bound table)
     double E;              // sqrt(n) * (eps_x + eps_q): PAA rounding slack
     double delta;          // relative error bound of an fp32 squared distance
     unsigned long long series_lb, series_refined, leaves_scanned, leaves_queued, approx_series;
+    unsigned long long ed_floats;  // row floats read by the refinement (abandoned rows: the chunks read)
 };
 
 enum : uint32_t {
@@ -182,6 +194,9 @@ void launch_bq_fill(isax_index* ix, int B, const uint32_t* mask, const uint32_t*
 void launch_bq_recheck(isax_index* ix, const QueryScratch* ss, int k, const uint4* cand,
                        const uint32_t* cand_count, uint32_t cap, cudaStream_t st);
 void launch_bq_finalize(isax_index* ix, const QueryScratch* ss, int B, int k, cudaStream_t st);
+// FP64 squared distances, definition order, of rows idx[b][j] to queries Q[b] (device arrays)
+void exact_d2_device(isax_index* ix, const float* Q, int B, int k, const int64_t* idx, double* out,
+                     cudaStream_t st);
 // scratch and captured graphs for the resident query server (isax_serve.cu)
 int64_t work_items_cap(int64_t L, int64_t N);
 void alloc_query_scratch_for(int64_t L, int64_t N, int n, int card, uint32_t cand_cap, uint32_t surv_cap,
@@ -223,6 +238,7 @@ struct isax_index {
     float* bp;
     int2* tree;          // balanced-split tree nodes (null for the round-robin split)
     int32_t* tree_root;  // [2^16]
+    uint32_t* inv;       // row of x of each original row (built on first use; leaf-order rows only)
     int64_t tree_nodes;
     // query scratch (one in-flight query)
     isax::QueryScratch qs;

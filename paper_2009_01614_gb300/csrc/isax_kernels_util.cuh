@@ -98,6 +98,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// arrive once (no transaction bytes)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 // bounded wait for phase `parity` of a barrier; false if it gave up
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t max_tries) {
     for (uint32_t i = 0; i < max_tries; ++i)
@@ -126,6 +130,36 @@ __device__ __forceinline__ void bulk_wait_read_all() {
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident): every CTA
+// arrives once on *count, which the caller has cleared before the launch, and
+// then waits until `expected` arrivals are seen, polling at most max_polls
+// times.  Returns false (in every thread of the CTA) when the wait gave up.
+// Called by every thread of every CTA; writes before it are visible after it.
+__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t expected, uint32_t max_polls, int* ok_smem) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        bool ok = false;
+        for (uint32_t i = 0; i < max_polls; ++i) {
+            if (ld_acquire_u32(count) >= expected) {
+                ok = true;
+                break;
+            }
+            __nanosleep(64);
+        }
+        *ok_smem = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return *ok_smem != 0;
 }
 
 template <typename T>

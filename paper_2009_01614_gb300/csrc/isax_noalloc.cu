@@ -14,8 +14,8 @@
 // call looks the real address up with cudaGetSymbolAddress and caches it; make
 // that first call before any stream capture begins.  All calls share the one
 // array and it keeps the previous call's contents, so each call resets what
-// must start at zero (the control block is cleared and the prep kernel resets
-// the counters, bins and top-k slots).  Two calls whose kernels overlap on the
+// must start cleared (the control block and the top-k slots, before the
+// kernels; the first kernel clears the bins).  Two calls whose kernels overlap on the
 // GPU would race on the array; calls are serialised by a process-wide lock and
 // each returns only after its results are copied out, so calls through this
 // entry point never overlap.
@@ -135,6 +135,7 @@ extern "C" isax_status isax_query_knn_noalloc(const isax_index* cix, const float
         const QueryScratch s = scratch_view(scratch_on(ix->device));
         const int n = ix->d.n;
         ISAX_CUDA_TRY(cudaMemsetAsync(s.ctl, 0, sizeof(QCtl), st));
+        ISAX_CUDA_TRY(cudaMemsetAsync(s.topk, 0xFF, sizeof(unsigned long long) * MAX_K, st));
         const cudaMemcpyKind kin = (mem_flags & ISAX_MEM_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice
                                                                        : cudaMemcpyHostToDevice;
         ISAX_CUDA_TRY(cudaMemcpyAsync(s.q, q, sizeof(float) * n, kin, st));
@@ -162,12 +163,13 @@ extern "C" isax_status isax_query_knn_noalloc(const isax_index* cix, const float
             stats->leaves_queued = (int64_t)c.leaves_queued;
             stats->leaves_scanned = (int64_t)c.leaves_scanned;
             stats->series_lb = (int64_t)c.series_lb;
-            stats->series_refined = (int64_t)c.series_refined;
+            stats->series_refined = (int64_t)c.refined_total;
             stats->approx_series = (int64_t)c.approx_series;
-            stats->candidates = (int64_t)c.cand_count;
+            stats->candidates = (int64_t)c.cand_total;
             stats->window = (int64_t)c.window;
             stats->approx_leaf = c.approx_leaf;
             stats->reruns = 0;
+            stats->ed_floats = (int64_t)c.ed_floats;
         }
         if (switched) cudaSetDevice(prev);
         return ISAX_OK;

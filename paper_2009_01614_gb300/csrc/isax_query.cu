@@ -78,7 +78,8 @@ __device__ void consider(const QueryScratch& s, int k, unsigned long long key, u
     bool keep = kth == EMPTY_SLOT ||
                 (double)key_d2(key) <= (double)key_d2(kth) * (1.0 + 3.0 * delta);
     if (keep) {
-        uint32_t i = atomicAdd(&s.ctl->cand_count, 1u);
+        // slots [0, cand_base) hold the approximate answer's rows (written in place)
+        uint32_t i = s.ctl->cand_base + atomicAdd(&s.ctl->cand_count, 1u);
         if (i < s.cand_cap) {
             s.cand_key[i] = key;
             s.cand_pos[i] = pos;
@@ -98,10 +99,11 @@ __device__ __forceinline__ float abandon_limit(unsigned long long kth, double de
 // n = 128 * NV: lane holds float4 p*32+lane.  Early abandon every 256 floats.
 template <int NV>
 __device__ __forceinline__ float warp_d2_vec(const float4* __restrict__ xr, const float4 (&qv)[NV],
-                                             float abandon, bool& abandoned) {
+                                             float abandon, bool& abandoned, int& nread) {
     const int lane = threadIdx.x & 31;
     float acc = 0.0f;
     abandoned = false;
+    nread = NV * 128;
     if constexpr (NV <= 2) {
         float4 v[NV];
 #pragma unroll
@@ -133,6 +135,7 @@ __device__ __forceinline__ float warp_d2_vec(const float4* __restrict__ xr, cons
             float part = warp_sum_f(acc);
             if (part > abandon) {
                 abandoned = true;
+                nread = (p + 2) * 128;
                 return part;
             }
         }
@@ -143,10 +146,11 @@ __device__ __forceinline__ float warp_d2_vec(const float4* __restrict__ xr, cons
 
 // any n: lane sums elements lane, lane+32, ...; abandon check every 8 full rounds
 __device__ __forceinline__ float warp_d2_gen(const float* __restrict__ xr, const float* __restrict__ q,
-                                             int n, float abandon, bool& abandoned) {
+                                             int n, float abandon, bool& abandoned, int& nread) {
     const int lane = threadIdx.x & 31;
     float acc = 0.0f;
     abandoned = false;
+    nread = n;
     for (int t = 0; 32 * t < n; ++t) {
         int j = 32 * t + lane;
         if (j < n) {
@@ -157,6 +161,7 @@ __device__ __forceinline__ float warp_d2_gen(const float* __restrict__ xr, const
             float part = warp_sum_f(acc);
             if (part > abandon) {
                 abandoned = true;
+                nread = 32 * (t + 1);
                 return part;
             }
         }
@@ -164,14 +169,15 @@ __device__ __forceinline__ float warp_d2_gen(const float* __restrict__ xr, const
     return warp_sum_f(acc);
 }
 
+// nread: the row's floats read (fewer than n when abandoned)
 template <int NV>
 __device__ __forceinline__ float warp_d2(const DevIndex& ix, int64_t r, const float4 (&qv)[NV ? NV : 1],
-                                         const float* q, float abandon, bool& abandoned) {
+                                         const float* q, float abandon, bool& abandoned, int& nread) {
     if constexpr (NV > 0) {
         return warp_d2_vec<NV>(reinterpret_cast<const float4*>(ix.x + r * ix.n), qv, abandon,
-                               abandoned);
+                               abandoned, nread);
     } else {
-        return warp_d2_gen(ix.x + r * ix.n, q, ix.n, abandon, abandoned);
+        return warp_d2_gen(ix.x + r * ix.n, q, ix.n, abandon, abandoned, nread);
     }
 }
 
@@ -198,10 +204,19 @@ __device__ __forceinline__ float series_lb(uint4 w, const float* __restrict__ ta
 
 // work items of the scan: a queued leaf is cut into pieces of at most LB_PIECE
 // rows, item = {first row, rows | 1 << 31 on the leaf's first piece}
-constexpr int LB_PIECE = 256;
+constexpr int LB_PIECE = 128;
 __device__ __forceinline__ uint32_t leaf_pieces(const DevIndex& ix, int64_t l) {
     const uint32_t size = ix.leaf_begin[l + 1] - ix.leaf_begin[l];
     return (size + LB_PIECE - 1) / LB_PIECE;
+}
+// the pieces of the leaf holding positions [b, e)
+__device__ __forceinline__ void put_pieces_of(const QueryScratch& s, uint32_t b, uint32_t e, uint32_t at,
+                                              uint32_t n_pieces, uint32_t cap) {
+    for (uint32_t ch = 0; ch < n_pieces && at + ch < cap; ++ch) {
+        const uint32_t r = b + ch * LB_PIECE;
+        const uint32_t rows = e - r < (uint32_t)LB_PIECE ? e - r : (uint32_t)LB_PIECE;
+        s.work[at + ch] = make_uint2(r, rows | (ch == 0 ? 0x80000000u : 0u));
+    }
 }
 __device__ __forceinline__ void put_pieces(const DevIndex& ix, const QueryScratch& s, int64_t l, uint32_t at,
                                            uint32_t n_pieces, uint32_t cap) {
@@ -237,7 +252,6 @@ __device__ int32_t tree_leaf(const DevIndex& ix, const int* qsym) {
     }
     return -1;
 }
-constexpr int APPROX_NEIGHBORS = 2;
 
 // One query's preparation by one CTA of PREP_THREADS threads; `neighbors`
 // leaves on each side of the descent leaf join the approximate answer.
@@ -352,6 +366,7 @@ __device__ __forceinline__ void q_prep_body(const DevIndex& ix, const QueryScrat
         c->approx_end = (int32_t)a1;
         c->work_count = 0;
         c->cand_count = 0;
+        c->cand_base = 0;
         c->surv_count = 0;
         c->window = 0;
         c->flags = bad ? QF_NONFINITE : 0u;
@@ -363,6 +378,7 @@ __device__ __forceinline__ void q_prep_body(const DevIndex& ix, const QueryScrat
         c->delta = (double)((n + 31) / 32 + 16) * u;
         c->series_lb = 0;
         c->series_refined = 0;
+        c->ed_floats = 0;
         c->leaves_scanned = 0;
         c->leaves_queued = 0;
         for (int i = 0; i < W; ++i) {
@@ -397,8 +413,9 @@ __device__ __forceinline__ void q_approx_body(const DevIndex& ix, const QueryScr
     unsigned long long refined = 0;
     for (int64_t p = b + gw; p < e; p += nw) {
         bool ab;
+        int nread;
         const uint32_t r = row_at(ix, p);
-        const float d2 = warp_d2<NV>(ix, r, qv, s.q, INFINITY, ab);
+        const float d2 = warp_d2<NV>(ix, r, qv, s.q, INFINITY, ab, nread);
         if (lane == 0) {
             const unsigned long long kth = ld_volatile_u64(&s.topk[k - 1]);
             if (kth == EMPTY_SLOT || (double)d2 <= (double)key_d2(kth) * (1.0 + 3.0 * delta))
@@ -406,7 +423,10 @@ __device__ __forceinline__ void q_approx_body(const DevIndex& ix, const QueryScr
         }
         ++refined;
     }
-    if (lane == 0 && refined) atomicAdd(&s.ctl->series_refined, refined);
+    if (lane == 0 && refined) {
+        atomicAdd(&s.ctl->series_refined, refined);
+        atomicAdd(&s.ctl->ed_floats, refined * (unsigned long long)ix.n);
+    }
 }
 template <int NV>
 __global__ void __launch_bounds__(256) q_approx_kernel(DevIndex ix, QueryScratch s, int k) {
@@ -507,6 +527,7 @@ __device__ __forceinline__ void q_leaf_scatter_body(const DevIndex& ix, const Qu
         c->work_count = tot < s.work_cap ? tot : s.work_cap;
         if (tot > s.work_cap) atomicOr(&c->flags, QF_OVERFLOW);
         c->thr_lb0 = thr;
+        c->thr_scan = thr;
     }
 }
 __global__ void __launch_bounds__(NBINS) q_leaf_scatter_kernel(DevIndex ix, QueryScratch s, int k) {
@@ -522,7 +543,7 @@ __global__ void __launch_bounds__(NBINS) bq_leaf_scatter_kernel(DevIndex ix, con
 // does not prune): every leaf goes on the work list, in storage order, with
 // bound 0 and all in the first bin, so the scan bounds every series and never
 // stops early nor skips a leaf.  The approximate-answer leaves stay out.
-__global__ void __launch_bounds__(256) q_flat_list_kernel(DevIndex ix, QueryScratch s) {
+__global__ void __launch_bounds__(256) q_flat_list_kernel(DevIndex ix, QueryScratch s, int k) {
     QCtl* c = s.ctl;
     if (c->flags & QF_NONFINITE) return;
     const int lane = threadIdx.x & 31;
@@ -549,7 +570,10 @@ __global__ void __launch_bounds__(256) q_flat_list_kernel(DevIndex ix, QueryScra
         base = __shfl_sync(FULL, base, 0);
         if (nch) put_pieces(ix, s, l, base + incl - nch, nch, 0xFFFFFFFFu);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) c->thr_lb0 = 0.0f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->thr_lb0 = 0.0f;
+        c->thr_scan = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), c->delta, c->E);
+    }
 }
 
 // ---------------------------------------------------------------- refinement helpers
@@ -617,6 +641,430 @@ __device__ __forceinline__ void warp_d2_four(const DevIndex& ix, const uint2 (&e
     }
 }
 
+// ---------------------------------------------------------------- q_front
+// The query's preparation, approximate answer and leaf bounds in one launch
+// (MESSI query answering, Section III: the approximate answer from the query's
+// own leaf seeds the BSF; every leaf's envelope bound then decides whether the
+// leaf is visited).  Every CTA computes the query's PAA, symbols and key and
+// searches the descent leaf itself, with q_prep's expressions and search, so all
+// CTAs find the same approximate-answer leaves; the grid's threads bound every
+// leaf's envelope into leaf_lb (q_leaf_lb's expression) while its warps refine
+// the approximate-answer rows, FR_ROWS rows per warp with one k-best update per
+// warp.  CTA 0 writes the control block and the lower-bound table.  The k best,
+// the candidate count and the refined count start each query cleared: the
+// previous query's q_finalize leaves them so, and a new scratch is allocated so.
+constexpr int FR_THREADS = 256, FR_WARPS = FR_THREADS / 32, FR_ROWS = 4, FR_LEAVES = 4, FR_KEYS = 4;
+
+template <int NV>
+__global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryScratch s, int k, int neighbors) {
+    __shared__ float bp[MAX_CARD + 1];
+    __shared__ __align__(16) float qv[MAX_LEN];  // read as float4 below
+    __shared__ float qpaa[W];
+    __shared__ int qsym[W];
+    __shared__ float red[FR_WARPS];
+    __shared__ unsigned bad, cnt_s;
+    __shared__ unsigned long long key_s;
+    __shared__ int64_t range_s[2], spec_s[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = ix.n, m = n / W, card = ix.card;
+    const bool lead = blockIdx.x == 0;
+    for (int i = tid; i <= card; i += FR_THREADS) bp[i] = ix.bp[i];
+    for (int j = tid; j < n; j += FR_THREADS) qv[j] = s.q[j];
+    if (tid == 0) {
+        bad = 0;
+        cnt_s = 0;
+    }
+    if (lead) {
+        // the binning step's counters and grid barrier start at zero
+        for (int i = tid; i < NBINS; i += FR_THREADS) {
+            s.bin_count[i] = 0;
+            s.bin_cursor[i] = 0;
+        }
+        if (tid == 0) s.ctl->grid_sync = 0;
+    }
+    __syncthreads();
+    float amax = 0.0f;
+    for (int j = tid; j < n; j += FR_THREADS) amax = fmaxf(amax, fabsf(qv[j]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, off));
+    if (lane == 0) red[warp] = amax;
+    if (tid < W) {
+        float sum = 0.0f;
+        for (int j = 0; j < m; ++j) sum += qv[tid * m + j];
+        const float p = sum / (float)m;
+        qpaa[tid] = p;
+        qsym[tid] = symbol_of(p, bp, card);
+        if (!isfinite(p)) atomicOr(&bad, 1u);
+    }
+    __syncthreads();
+    const float mf = (float)m;
+    if (lead) {
+        // lower-bound table T[i][s] = m * dist(qpaa_i, [bp[s], bp[s+1]))^2
+        for (int e = tid; e < W * card; e += FR_THREADS) {
+            const int i = e / card, sym = e - i * card;
+            const float lo = bp[sym], hi = bp[sym + 1], v = qpaa[i];
+            const float d = v < lo ? lo - v : (v >= hi ? v - hi : 0.0f);
+            s.table[e] = (d * d) * mf;
+        }
+    }
+    if (tid == 0) {
+        unsigned long long key = 0;
+        for (int pl = 0; pl < 4; ++pl) {
+            const int b = ix.cbits - 1 - pl;
+            unsigned plane = 0;
+            for (int i = 0; i < W; ++i)
+                plane = (plane << 1) | (b >= 0 ? ((unsigned)(qsym[i] >> b) & 1u) : 0u);
+            key = (key << 16) | plane;
+        }
+        key_s = key;
+    }
+    __syncthreads();
+    const unsigned long long key = ix.tree ? (key_s & 0xFFFF000000000000ull) : key_s;
+    const int64_t L = ix.L;
+    const int64_t step = (L + FR_THREADS - 1) / FR_THREADS;
+    const int64_t si = (int64_t)tid * step;
+    const unsigned long long sample = si < L ? ix.leaf_key[si] : ~0ull;
+    {
+        // envelope bound of this thread's leaves (q_leaf_lb's expression)
+        float qp[W];
+        int qs[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            qp[i] = qpaa[i];
+            qs[i] = qsym[i];
+        }
+        // FR_LEAVES leaves at a time, their envelopes all loaded before any bound
+        const int64_t stride = (int64_t)gridDim.x * FR_THREADS;
+        for (int64_t l0 = (int64_t)blockIdx.x * FR_THREADS + tid; l0 < L; l0 += FR_LEAVES * stride) {
+            uint4 mn[FR_LEAVES], mx[FR_LEAVES];
+#pragma unroll
+            for (int u = 0; u < FR_LEAVES; ++u) {
+                const int64_t l = l0 + u * stride;
+                if (l < L) {
+                    mn[u] = ix.env[2 * l];
+                    mx[u] = ix.env[2 * l + 1];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < FR_LEAVES; ++u) {
+                const int64_t l = l0 + u * stride;
+                if (l >= L) break;
+                const uint32_t wn[4] = {mn[u].x, mn[u].y, mn[u].z, mn[u].w};
+                const uint32_t wx[4] = {mx[u].x, mx[u].y, mx[u].z, mx[u].w};
+                float lb = 0.0f;
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    const int lo = (wn[i >> 2] >> (8 * (i & 3))) & 255, hi = (wx[i >> 2] >> (8 * (i & 3))) & 255;
+                    if (qs[i] < lo) {
+                        const float d = bp[lo] - qp[i];
+                        lb += (d * d) * mf;
+                    } else if (qs[i] > hi) {
+                        const float d = qp[i] - bp[hi + 1];
+                        lb += (d * d) * mf;
+                    }
+                }
+                s.leaf_lb[l] = lb;
+            }
+        }
+    }
+    // descent: the last leaf whose first key <= the query key (q_prep's search).
+    // The keys of the boundary's stride are read all at once, and with each key
+    // the first positions of the leaves `neighbors` before and `neighbors` + 1
+    // after it: the thread holding the descent leaf then knows the approximate
+    // range's extent without another read.
+    const int c1 = __syncthreads_count(si < L && sample <= key);
+    const int64_t lo = c1 > 0 ? (int64_t)(c1 - 1) * step : 0;
+    const int64_t hi = lo + step < L ? lo + step : L;
+    if (tid == 0) spec_s[0] = spec_s[1] = -1;
+    unsigned cnt = 0;
+    int64_t mj[FR_KEYS];
+    uint32_t mb0[FR_KEYS], mb1[FR_KEYS];
+#pragma unroll
+    for (int u = 0; u < FR_KEYS; ++u) mj[u] = -1;  // a thread past the stride holds no key
+    for (int64_t j0 = lo + tid; j0 < hi; j0 += FR_KEYS * FR_THREADS) {
+        unsigned long long kv[FR_KEYS];
+#pragma unroll
+        for (int u = 0; u < FR_KEYS; ++u) {
+            const int64_t j = j0 + u * FR_THREADS;
+            mj[u] = j;
+            if (j < hi) {
+                kv[u] = ix.leaf_key[j];
+                const int64_t x0 = j - neighbors > 0 ? j - neighbors : 0;
+                const int64_t x1 = j + 1 + neighbors < L ? j + 1 + neighbors : L;
+                mb0[u] = ix.leaf_begin[x0];
+                mb1[u] = ix.leaf_begin[x1];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < FR_KEYS; ++u) cnt += (mj[u] < hi && kv[u] <= key) ? 1u : 0u;
+    }
+    if (cnt) atomicAdd(&cnt_s, cnt);
+    __syncthreads();
+    {
+        // the holder of the descent leaf publishes its range's extent
+        const int64_t ub = lo + cnt_s;
+        const int64_t dl = ub > 0 ? ub - 1 : 0;
+        if (hi - lo <= (int64_t)FR_KEYS * FR_THREADS) {
+#pragma unroll
+            for (int u = 0; u < FR_KEYS; ++u)
+                if (mj[u] == dl && dl >= lo && dl < hi) {
+                    spec_s[0] = mb0[u];
+                    spec_s[1] = mb1[u];
+                }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int64_t ub = lo + cnt_s;
+        int64_t dl = ub > 0 ? ub - 1 : 0;
+        bool known = spec_s[0] >= 0;  // the range's extent was read with the keys
+        if (ix.tree) {
+            const int32_t t = tree_leaf(ix, qsym);
+            if (t >= 0 && t < L && t != dl) {
+                dl = t;
+                known = false;
+            }
+        }
+        int64_t a0 = dl - neighbors > 0 ? dl - neighbors : 0;
+        int64_t a1 = dl + 1 + neighbors < L ? dl + 1 + neighbors : L;
+        int64_t b0 = known ? spec_s[0] : (int64_t)ix.leaf_begin[a0];
+        int64_t b1 = known ? spec_s[1] : (int64_t)ix.leaf_begin[a1];
+        int64_t tot = b1 - b0;
+        while (tot < k) {
+            if (a1 < L) {
+                ++a1;
+                b1 = ix.leaf_begin[a1];
+            } else if (a0 > 0) {
+                --a0;
+                b0 = ix.leaf_begin[a0];
+            } else {
+                break;
+            }
+            tot = b1 - b0;
+        }
+        range_s[0] = b0;
+        range_s[1] = b1;
+        if (lead) {
+            float qmax = 0.0f;
+            for (int i = 0; i < FR_WARPS; ++i) qmax = fmaxf(qmax, red[i]);
+            QCtl* c = s.ctl;
+            c->qkey = key;
+            c->approx_series = (unsigned long long)tot;
+            c->cand_base = (uint32_t)tot;  // candidate slots of the approximate rows, by position
+            c->descent_leaf = (int32_t)dl;
+            c->approx_leaf = (int32_t)a0;
+            c->approx_end = (int32_t)a1;
+            c->work_count = 0;
+            c->surv_count = 0;
+            c->window = 0;
+            c->flags = bad ? QF_NONFINITE : 0u;
+            c->thr_lb0 = INFINITY;
+            c->thr_scan = INFINITY;
+            const double u = 0x1p-24;
+            const double eps_x = 1.01 * (m + 1) * u * (double)ix.maxabs;
+            const double eps_q = 1.01 * (m + 1) * u * (double)qmax;
+            c->E = sqrt((double)n) * (eps_x + eps_q) * (1.0 + 1e-9);
+            c->delta = (double)((n + 31) / 32 + 16) * u;
+            c->series_lb = 0;
+            c->ed_floats = (unsigned long long)tot * (unsigned long long)n;  // the approximate rows, read whole
+            c->leaves_scanned = 0;
+            c->leaves_queued = 0;
+            for (int i = 0; i < W; ++i) {
+                c->qsym[i] = (uint8_t)qsym[i];
+                c->qpaa[i] = qpaa[i];
+            }
+        }
+    }
+    __syncthreads();
+    if (bad) return;  // a non-finite query: CTA 0 has flagged it
+    // approximate answer: the rows of the approximate-answer leaves, FR_ROWS
+    // consecutive positions per warp at a time
+    const int64_t b = range_s[0], e = range_s[1];
+    constexpr int NQ = NV ? NV : 1;
+    float4 qr[NQ];
+#pragma unroll
+    for (int p = 0; p < NQ; ++p)
+        qr[p] = NV ? reinterpret_cast<const float4*>(qv)[p * 32 + lane] : make_float4(0, 0, 0, 0);
+    const double delta = (double)((n + 31) / 32 + 16) * 0x1p-24;
+    const int64_t gw = (int64_t)blockIdx.x * FR_WARPS + warp, nw = (int64_t)gridDim.x * FR_WARPS;
+    unsigned long long refined = 0;
+    for (int64_t p0 = b + gw * FR_ROWS; p0 < e; p0 += nw * FR_ROWS) {
+        const int R = e - p0 < FR_ROWS ? (int)(e - p0) : FR_ROWS;
+        uint2 rw[4];
+        uint32_t my_id = 0, my_row = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int64_t p = p0 + (t < R ? t : 0);
+            rw[t] = make_uint2(row_at(ix, p), 0u);
+        }
+        if (lane < R) {
+            my_id = ix.orig[p0 + lane];
+            my_row = rw[0].x;
+#pragma unroll
+            for (int t = 1; t < 4; ++t)
+                if (lane == t) my_row = rw[t].x;
+        }
+        float d[4];
+        if constexpr (NV > 0 && NV <= 2) {
+            warp_d2_four<NQ>(ix, rw, (1u << R) - 1u, qr, d);
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                bool ab;
+                int nread;
+                d[t] = t < R ? warp_d2<NV>(ix, (int64_t)rw[t].x, qr, s.q, INFINITY, ab, nread) : 0.0f;
+            }
+        }
+        float my_d2 = d[0];
+#pragma unroll
+        for (int t = 1; t < 4; ++t)
+            if (lane == t) my_d2 = d[t];
+        // the k best: for k = 1 one atomicMin per row (its result is not needed);
+        // for larger k the rows under the current k-th best go through the
+        // insertion cascade.  Every approximate row is a candidate for the final
+        // ordering, in the slot of its position (q_finalize keeps those within
+        // the final window).
+        const unsigned long long my_key = pack_key(my_d2, my_id);
+        if (k == 1) {
+            if (lane < R) atomicMin(&s.topk[0], my_key);
+        } else {
+            unsigned long long kth = 0;
+            if (lane == 0) kth = ld_volatile_u64(&s.topk[k - 1]);
+            kth = __shfl_sync(FULL, kth, 0);
+            if (lane < R && my_key < kth) topk_insert(s.topk, k, my_key);
+        }
+        if (lane < R) {
+            const int64_t slot = p0 + lane - b;
+            if (slot < (int64_t)s.cand_cap) {
+                s.cand_key[slot] = my_key;
+                s.cand_pos[slot] = my_row;
+            }
+        }
+        refined += (unsigned long long)R;
+    }
+    if (lane == 0 && refined) atomicAdd(&s.ctl->series_refined, refined);
+}
+
+// ---------------------------------------------------------------- q_leaf_bin
+// The leaves the approximate answer does not prune, listed bin by bin of
+// bound / BSF (MESSI's priority queues): a cooperative launch of G CTAs.  Each
+// CTA counts its leaves' pieces into the bins, the counts are summed over the
+// grid, and after a grid barrier every CTA places its leaves' pieces at their
+// bin's offset (the work list of q_leaf_lb + q_leaf_scatter, in one launch).
+// The barrier waits at most GRID_WAIT polls; a barrier that gives up flags the
+// query QF_STALLED and the list is left empty.
+constexpr int BIN_THREADS = 512, BIN_LEAVES = 4;
+constexpr uint32_t GRID_WAIT = 1u << 22;
+
+__global__ void __launch_bounds__(BIN_THREADS) q_leaf_bin_kernel(DevIndex ix, QueryScratch s, int k) {
+    __shared__ uint32_t hist[NBINS];
+    __shared__ uint32_t off[NBINS];
+    __shared__ uint32_t scratch[32];
+    __shared__ float thr_s;
+    __shared__ int ok_s;
+    QCtl* c = s.ctl;
+    const int tid = threadIdx.x;
+    const uint32_t flags = c->flags;
+    const int64_t a0 = c->approx_leaf, a1 = c->approx_end;
+    for (int i = tid; i < NBINS; i += BIN_THREADS) hist[i] = 0;
+    if (tid == 0) thr_s = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), c->delta, c->E);
+    __syncthreads();
+    const float thr = thr_s;
+    const bool skip = (flags & QF_NONFINITE) != 0;
+    const int64_t L = ix.L, stride = (int64_t)gridDim.x * BIN_THREADS;
+    const int64_t first = (int64_t)blockIdx.x * BIN_THREADS + tid;
+    // BIN_LEAVES leaves at a time, all loads issued first: bound (bin, or -1 when
+    // the leaf is not queued) and pieces; the first group stays in registers for
+    // the placement after the barrier
+    int bin0[BIN_LEAVES];
+    uint32_t nch0[BIN_LEAVES], b0[BIN_LEAVES], e0[BIN_LEAVES];
+    auto load_group = [&](int64_t l0, int (&bn)[BIN_LEAVES], uint32_t (&nc)[BIN_LEAVES], uint32_t (&b)[BIN_LEAVES],
+                          uint32_t (&e)[BIN_LEAVES]) {
+        float lb[BIN_LEAVES];
+#pragma unroll
+        for (int u = 0; u < BIN_LEAVES; ++u) {
+            const int64_t l = l0 + u * stride;
+            if (l < L) {
+                lb[u] = s.leaf_lb[l];
+                b[u] = ix.leaf_begin[l];
+                e[u] = ix.leaf_begin[l + 1];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < BIN_LEAVES; ++u) {
+            const int64_t l = l0 + u * stride;
+            const bool q = l < L && !(l >= a0 && l < a1) && lb[u] <= thr;
+            bn[u] = q ? bin_of(lb[u], thr) : -1;
+            nc[u] = q ? (e[u] - b[u] + LB_PIECE - 1) / LB_PIECE : 0u;
+        }
+    };
+    if (!skip) {
+        for (int64_t l0 = first; l0 < L; l0 += BIN_LEAVES * stride) {
+            int bn[BIN_LEAVES];
+            uint32_t nc[BIN_LEAVES], b[BIN_LEAVES], e[BIN_LEAVES];
+            load_group(l0, bn, nc, b, e);
+#pragma unroll
+            for (int u = 0; u < BIN_LEAVES; ++u) {
+                if (bn[u] >= 0) atomicAdd(&hist[bn[u]], nc[u]);
+                if (l0 == first) {
+                    bin0[u] = bn[u];
+                    nch0[u] = nc[u];
+                    b0[u] = b[u];
+                    e0[u] = e[u];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < NBINS; i += BIN_THREADS)
+        if (hist[i]) atomicAdd(&s.bin_count[i], hist[i]);
+    // grid barrier: every CTA's counts are in bin_count
+    const bool met = grid_barrier(&c->grid_sync, gridDim.x, GRID_WAIT, &ok_s);
+    if (!met && tid == 0) atomicOr(&c->flags, QF_STALLED);
+    if (!met || skip) {
+        if (blockIdx.x == 0 && tid == 0) c->work_count = 0;
+        return;
+    }
+    uint32_t tot;
+    const uint32_t cnt = tid < NBINS ? ld_volatile_u32(&s.bin_count[tid]) : 0u;
+    const uint32_t o = block_excl_scan<uint32_t>(cnt, 0u, OpAdd<uint32_t>(), scratch, &tot);
+    if (tid < NBINS) off[tid] = o;
+    __syncthreads();
+    const uint32_t cap = tot < s.work_cap ? tot : s.work_cap;
+    uint32_t mine = 0;
+    for (int64_t l0 = first; l0 < L; l0 += BIN_LEAVES * stride) {
+        int bn[BIN_LEAVES];
+        uint32_t nc[BIN_LEAVES], b[BIN_LEAVES], e[BIN_LEAVES];
+        if (l0 == first) {
+#pragma unroll
+            for (int u = 0; u < BIN_LEAVES; ++u) {
+                bn[u] = bin0[u];
+                nc[u] = nch0[u];
+                b[u] = b0[u];
+                e[u] = e0[u];
+            }
+        } else {
+            load_group(l0, bn, nc, b, e);
+        }
+#pragma unroll
+        for (int u = 0; u < BIN_LEAVES; ++u) {
+            if (bn[u] < 0) continue;
+            const uint32_t p = off[bn[u]] + atomicAdd(&s.bin_cursor[bn[u]], nc[u]);
+            put_pieces_of(s, b[u], e[u], p, nc[u], cap);
+            ++mine;
+        }
+    }
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) mine += __shfl_xor_sync(FULL, mine, o2);
+    if ((tid & 31) == 0 && mine) atomicAdd(&c->leaves_queued, (unsigned long long)mine);
+    if (blockIdx.x == 0 && tid == 0) {
+        c->work_count = cap;
+        if (tot > s.work_cap) atomicOr(&c->flags, QF_OVERFLOW);
+        c->thr_lb0 = thr;
+        c->thr_scan = thr;
+    }
+}
+
 // ---------------------------------------------------------------- q_series_lb
 // The lower-bound scan (MESSI's lower-bound calculations).  Work item i of the
 // list (a piece of at most LB_PIECE rows of a queued leaf, in ascending leaf
@@ -633,16 +1081,17 @@ __device__ __forceinline__ void warp_d2_four(const DevIndex& ix, const uint2 (&e
 // warp is still under the threshold (the sum runs in segment order either way,
 // so the bound is the same).  Survivors {row of x, bound} are buffered per warp
 // and appended with one atomic per batch.
-constexpr int LB_THREADS = 512;
+constexpr int LB_THREADS = 1024;
 constexpr int LB_WARPS = LB_THREADS / 32;
 constexpr int LB_STAGES = 3;
 constexpr int LB_PER_LANE = LB_PIECE / 32;
-constexpr int LB_BUF = 64;     // survivors buffered per warp before one global append
+constexpr int LB_BUF = 48;     // survivors buffered per warp before one global append
 constexpr uint32_t LB_WAIT = 1u << 22;  // bounded wait on a stage's copy
 constexpr size_t LB_TAB_BYTES = sizeof(float) * W * MAX_CARD;
 constexpr size_t LB_RING_BYTES = (size_t)LB_WARPS * LB_STAGES * LB_PIECE * sizeof(uint4);
 constexpr size_t LB_SMEM = 1024 + LB_TAB_BYTES + LB_RING_BYTES + sizeof(uint64_t) * LB_WARPS * LB_STAGES +
-                           sizeof(uint2) * LB_WARPS * (LB_STAGES + LB_BUF) + 16;
+                           sizeof(uint2) * LB_WARPS * (LB_STAGES + LB_BUF) + sizeof(uint32_t) * (LB_WARPS + 2);
+static_assert(LB_SMEM <= 227 * 1024, "the scan's shared memory exceeds a CTA's limit");
 
 template <int OFF>
 __device__ __forceinline__ float lds_f32(uint32_t addr) {
@@ -675,8 +1124,8 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + LB_TAB_BYTES + LB_RING_BYTES);
     uint2* metas = reinterpret_cast<uint2*>(bars + LB_WARPS * LB_STAGES);
     uint2* bufs = metas + LB_WARPS * LB_STAGES;
-    float* thr_p = reinterpret_cast<float*>(bufs + LB_WARPS * LB_BUF);
-    uint32_t* next_p = reinterpret_cast<uint32_t*>(thr_p + 1);
+    uint32_t* next_p = reinterpret_cast<uint32_t*>(bufs + LB_WARPS * LB_BUF);
+    uint32_t* wcnt = next_p + 1;  // [LB_WARPS + 1]: each warp's last survivors, then the CTA's base
     const int card = ix.card;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint4* wring = ring + (size_t)warp * LB_STAGES * LB_PIECE;
@@ -688,6 +1137,7 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
     // threshold and the table
     const uint32_t flags = c->flags;
     const uint32_t count = c->work_count;
+    const float thr = c->thr_scan;  // set with the work list, from the approximate answer
     uint2 e[LB_STAGES];
 #pragma unroll
     for (int t = 0; t < LB_STAGES; ++t) {
@@ -734,12 +1184,8 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         const int i = threadIdx.x + t * LB_THREADS;
         if (i < nv) tdst[i] = tv[t];
     }
-    if (threadIdx.x == 0) {
-        *next_p = LB_WARPS * LB_STAGES;  // the items after the warps' first ones go by claim
-        *thr_p = lb_threshold(ld_volatile_u64(&s.topk[k - 1]), c->delta, c->E);
-    }
+    if (threadIdx.x == 0) *next_p = LB_WARPS * LB_STAGES;  // the items after the warps' first ones go by claim
     __syncthreads();
-    const float thr = *thr_p;
     const uint32_t tab_sa = smem_u32(tab);
     uint2* buf = bufs + warp * LB_BUF;
     int nbuf = 0;  // warp-uniform
@@ -832,7 +1278,23 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         }
         __syncwarp();
     }
-    drain();
+    // the warps' last survivors go to the list in one append for the whole CTA
+    // (thousands of warps finish at about the same time: one counter update per
+    // CTA instead of one per warp)
+    if (lane == 0) wcnt[warp] = (uint32_t)nbuf;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        for (int i = 0; i < LB_WARPS; ++i) tot += wcnt[i];
+        wcnt[LB_WARPS] = tot ? atomicAdd(&c->surv_count, tot) : 0u;
+    }
+    __syncthreads();
+    {
+        uint32_t base = wcnt[LB_WARPS];
+        for (int i = 0; i < warp; ++i) base += wcnt[i];
+        for (int t = lane; t < nbuf; t += 32)
+            if (base + t < s.surv_cap) s.surv[base + t] = make_uint2(row_at(ix, buf[t].x), buf[t].y);
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) n_lb += __shfl_xor_sync(FULL, n_lb, off);
     if (lane == 0) {
@@ -895,16 +1357,15 @@ __device__ __forceinline__ void q_refine_body(const DevIndex& ix, const QueryScr
     const double delta = c->delta, E = c->E;
     unsigned long long kth = 0ull;  // cached k-th best and the limits derived from it
     float thr = INFINITY, lim = INFINITY;
-    unsigned long long n_ref = 0;
+    unsigned long long n_ref = 0, n_floats = 0;
     float my_d2 = INFINITY;
     uint32_t my_pos = 0;
     int nb = 0;
+    // the window filter uses the cached k-th best (never below the current one);
+    // consider() decides with a fresh value
     auto flush = [&]() {
         if (nb == 0) return;
-        unsigned long long kt = 0;
-        if (lane == 0) kt = ld_volatile_u64(&s.topk[k - 1]);
-        kt = __shfl_sync(FULL, kt, 0);
-        const double lim_w = kt == EMPTY_SLOT ? INFINITY : (double)key_d2(kt) * (1.0 + 3.0 * delta);
+        const double lim_w = kth == 0ull || kth == EMPTY_SLOT ? INFINITY : (double)key_d2(kth) * (1.0 + 3.0 * delta);
         if (lane < nb && (double)my_d2 <= lim_w)
             consider(s, k, pack_key(my_d2, id_of_row(ix, my_pos)), my_pos, delta);
         __syncwarp();
@@ -952,6 +1413,7 @@ __device__ __forceinline__ void q_refine_body(const DevIndex& ix, const QueryScr
             for (int t = 0; t < 4; ++t)
                 if (keep & (1u << t)) {
                     ++n_ref;
+                    n_floats += (unsigned long long)ix.n;
                     push(d[t], e[t].x);
                 }
         } else {
@@ -959,14 +1421,19 @@ __device__ __forceinline__ void q_refine_body(const DevIndex& ix, const QueryScr
             for (int t = 0; t < 4; ++t)
                 if (keep & (1u << t)) {
                     bool ab;
-                    const float d0 = warp_d2<NV>(ix, (int64_t)e[t].x, qv, s.q, lim, ab);
+                    int nread;
+                    const float d0 = warp_d2<NV>(ix, (int64_t)e[t].x, qv, s.q, lim, ab, nread);
                     ++n_ref;
+                    n_floats += (unsigned long long)nread;
                     if (!ab) push(d0, e[t].x);
                 }
         }
     }
     flush();
-    if (lane == 0 && n_ref) atomicAdd(&c->series_refined, n_ref);
+    if (lane == 0 && n_ref) {
+        atomicAdd(&c->series_refined, n_ref);
+        atomicAdd(&c->ed_floats, n_floats);
+    }
 }
 template <int NV>
 __global__ void __launch_bounds__(RF_THREADS, 3) q_refine_kernel(DevIndex ix, QueryScratch s, int k) {
@@ -982,8 +1449,151 @@ __global__ void __launch_bounds__(RF_THREADS, 3) bq_refine_kernel(DevIndex ix, c
     q_refine_body<NV>(ix, ss[t.x], k, (t.y & 0xFFFFu) * WPB + (threadIdx.x >> 5), (t.y >> 16) * WPB);
 }
 
+// n = 256 (two float4 per lane): every row in two halves of 128 floats.  The
+// first halves of a quad of survivors are read one round ahead; their partial
+// distances then decide each row (a partial above (1 + 8 delta) times the k-th
+// best puts the full fp32 distance outside the candidate window: the row is
+// abandoned and its second half never read), and the second halves of the kept
+// rows are read together with the next quad's first halves, so a round still
+// costs one memory latency.  A row's distance is its lanes' sums over both
+// halves, then the butterfly: warp_d2_vec<2>'s value.
+__device__ __forceinline__ void q_refine_half_body(const DevIndex& ix, const QueryScratch& s, int k, uint32_t gw,
+                                                   uint32_t nw) {
+    QCtl* c = s.ctl;
+    if (c->flags & QF_NONFINITE) return;
+    const int lane = threadIdx.x & 31;
+    float4 qv[2];
+    load_q<2>(s.q, qv);
+    const uint32_t found = c->surv_count;
+    const uint32_t total = found < s.surv_cap ? found : s.surv_cap;
+    const double delta = c->delta, E = c->E;
+    unsigned long long kth = 0ull;
+    float thr = INFINITY, lim = INFINITY;
+    unsigned long long n_ref = 0, n_floats = 0;
+    float my_d2 = INFINITY;
+    uint32_t my_pos = 0;
+    int nb = 0;
+    auto flush = [&]() {
+        if (nb == 0) return;
+        const double lim_w = kth == 0ull || kth == EMPTY_SLOT ? INFINITY : (double)key_d2(kth) * (1.0 + 3.0 * delta);
+        if (lane < nb && (double)my_d2 <= lim_w)
+            consider(s, k, pack_key(my_d2, id_of_row(ix, my_pos)), my_pos, delta);
+        __syncwarp();
+        nb = 0;
+    };
+    auto push = [&](float d2, uint32_t r) {
+        if (lane == nb) {
+            my_d2 = d2;
+            my_pos = r;
+        }
+        ++nb;
+        if (nb == SR_BATCH) flush();
+    };
+    unsigned long long kt_next = 0;
+    if (lane == 0) kt_next = ld_volatile_u64(&s.topk[k - 1]);
+    auto refresh = [&]() {
+        const unsigned long long kt = __shfl_sync(FULL, kt_next, 0);
+        if (lane == 0) kt_next = ld_volatile_u64(&s.topk[k - 1]);
+        if (kt != kth || kth == 0ull) {
+            kth = kt;
+            thr = lb_threshold(kt, delta, E);
+            lim = abandon_limit(kt, delta);
+        }
+    };
+    const float4* x4 = reinterpret_cast<const float4*>(ix.x);
+    uint2 nx[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) nx[t] = 4 * gw + t < total ? s.surv[4 * gw + t] : make_uint2(0u, 0x7f800000u);
+    // the quad at index i: its rows and the ones the bound does not skip; the
+    // next quad's survivors are read meanwhile
+    auto take = [&](uint32_t i, uint2 (&e)[4], unsigned& keep) {
+        keep = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            e[t] = nx[t];
+            if (i + t < total && __uint_as_float(e[t].y) <= thr) keep |= 1u << t;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) nx[t] = i + 4 * nw + t < total ? s.surv[i + 4 * nw + t] : make_uint2(0u, 0x7f800000u);
+    };
+    uint32_t i = 4 * gw;
+    uint2 eA[4];
+    unsigned keepA = 0;
+    float4 hA[4];
+    refresh();
+    take(i, eA, keepA);
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        if (keepA & (1u << t)) hA[t] = ld_stream(x4 + (int64_t)eA[t].x * 64 + lane);
+    while (i < total) {
+        // partial distances of the quad's first halves
+        float a[4];
+        unsigned keep2 = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            a[t] = 0.0f;
+            if (keepA & (1u << t)) {
+                float d;
+                d = hA[t].x - qv[0].x; a[t] = fmaf(d, d, a[t]);
+                d = hA[t].y - qv[0].y; a[t] = fmaf(d, d, a[t]);
+                d = hA[t].z - qv[0].z; a[t] = fmaf(d, d, a[t]);
+                d = hA[t].w - qv[0].w; a[t] = fmaf(d, d, a[t]);
+                ++n_ref;
+                n_floats += 128;
+                if (warp_sum_f(a[t]) <= lim) keep2 |= 1u << t;
+            }
+        }
+        // the next quad, then one round of reads: the kept rows' second halves
+        // and the next quad's first halves
+        const uint32_t iB = i + 4 * nw;
+        uint2 eB[4];
+        unsigned keepB = 0;
+        refresh();
+        if (iB < total) take(iB, eB, keepB);
+        float4 sA[4], hB[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (keep2 & (1u << t)) sA[t] = ld_stream(x4 + (int64_t)eA[t].x * 64 + 32 + lane);
+            if (keepB & (1u << t)) hB[t] = ld_stream(x4 + (int64_t)eB[t].x * 64 + lane);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (keep2 & (1u << t)) {
+                float d;
+                d = sA[t].x - qv[1].x; a[t] = fmaf(d, d, a[t]);
+                d = sA[t].y - qv[1].y; a[t] = fmaf(d, d, a[t]);
+                d = sA[t].z - qv[1].z; a[t] = fmaf(d, d, a[t]);
+                d = sA[t].w - qv[1].w; a[t] = fmaf(d, d, a[t]);
+                n_floats += 128;
+                push(warp_sum_f(a[t]), eA[t].x);
+            }
+        }
+        i = iB;
+        keepA = keepB;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            eA[t] = eB[t];
+            hA[t] = hB[t];
+        }
+    }
+    flush();
+    if (lane == 0 && n_ref) {
+        atomicAdd(&c->series_refined, n_ref);
+        atomicAdd(&c->ed_floats, n_floats);
+    }
+}
+__global__ void __launch_bounds__(RF_THREADS, 2) q_refine_half_kernel(DevIndex ix, QueryScratch s, int k) {
+    q_refine_half_body(ix, s, k, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+}
+__global__ void __launch_bounds__(RF_THREADS, 2) bq_refine_half_kernel(DevIndex ix, const QueryScratch* ss,
+                                                                       const uint2* __restrict__ tasks, int k) {
+    const uint2 t = tasks[blockIdx.x];
+    constexpr uint32_t WPB = RF_THREADS / 32;
+    q_refine_half_body(ix, ss[t.x], k, (t.y & 0xFFFFu) * WPB + (threadIdx.x >> 5), (t.y >> 16) * WPB);
+}
+
 // ---------------------------------------------------------------- q_finalize
-constexpr int FIN_THREADS = 1024, FIN_WARPS = FIN_THREADS / 32, FIN_CAP = 2 * FIN_THREADS;
+constexpr int FIN_THREADS = 1024, FIN_WARPS = FIN_THREADS / 32, FIN_CAP = 2 * FIN_THREADS, FIN_UNROLL = 4;
 
 __device__ __forceinline__ bool key_greater(unsigned long long a, uint32_t ia, unsigned long long b,
                                             uint32_t ib) {
@@ -1076,19 +1686,29 @@ __device__ __forceinline__ void q_finalize_body(const DevIndex& ix, const QueryS
     }
     const double delta = c->delta;
     const double bound = (double)key_d2(kth) * (1.0 + 3.0 * delta);
-    const uint32_t attempted = c->cand_count;
+    const uint32_t attempted = c->cand_base + c->cand_count;
     const uint32_t M = attempted < s.cand_cap ? attempted : s.cand_cap;
     const int n = ix.n;
     if (tid == 0) nst = 0;
     __syncthreads();
-    // one pass over all candidates: count the window, stage it if it fits
-    for (uint32_t i = tid; i < M; i += FIN_THREADS) {
-        const unsigned long long key = s.cand_key[i];
-        if ((double)key_d2(key) <= bound) {
-            const int p = atomicAdd(&nst, 1);
-            if (p < FIN_THREADS) {
-                stage[p] = s.cand_pos[i];
-                stage_key[p] = key;
+    // one pass over all candidates (FIN_UNROLL per thread at a time, all read
+    // first): count the window, stage it if it fits
+    for (uint32_t i0 = tid; i0 < M; i0 += FIN_UNROLL * FIN_THREADS) {
+        unsigned long long key[FIN_UNROLL];
+#pragma unroll
+        for (int u = 0; u < FIN_UNROLL; ++u) {
+            const uint32_t i = i0 + u * FIN_THREADS;
+            key[u] = i < M ? s.cand_key[i] : EMPTY_SLOT;
+        }
+#pragma unroll
+        for (int u = 0; u < FIN_UNROLL; ++u) {
+            const uint32_t i = i0 + u * FIN_THREADS;
+            if (i < M && (double)key_d2(key[u]) <= bound) {
+                const int p = atomicAdd(&nst, 1);
+                if (p < FIN_THREADS) {
+                    stage[p] = s.cand_pos[i];
+                    stage_key[p] = key[u];
+                }
             }
         }
     }
@@ -1192,12 +1812,62 @@ __device__ __forceinline__ void q_finalize_body(const DevIndex& ix, const QueryS
         if (attempted > s.cand_cap || c->surv_count > s.surv_cap) c->flags |= QF_OVERFLOW;
     }
 }
+// After the answer: the totals the host reads are saved and the state the next
+// query's q_front accumulates into is cleared (the k best, the candidate and
+// refined counts), so a query's first kernel needs no clearing step of its own.
+__device__ __forceinline__ void q_finalize_epilogue(const QueryScratch& s, int k) {
+    __syncthreads();  // every thread is done reading the k best
+    QCtl* c = s.ctl;
+    if (threadIdx.x == 0) {
+        c->cand_total = c->cand_base + c->cand_count;
+        c->refined_total = c->series_refined;
+        c->cand_count = 0;
+        c->series_refined = 0;
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) s.topk[i] = EMPTY_SLOT;
+}
 __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, QueryScratch s, int k) {
     q_finalize_body(ix, s, k);
+    q_finalize_epilogue(s, k);
 }
 __global__ void __launch_bounds__(FIN_THREADS) bq_finalize_kernel(DevIndex ix, const QueryScratch* ss,
                                                                    int k) {
     q_finalize_body(ix, ss[blockIdx.y], k);
+    q_finalize_epilogue(ss[blockIdx.y], k);
+}
+
+// ---------------------------------------------------------------- exact FP64 distances
+// FP64 squared distance of given series to given queries with the definition's
+// order (elements ascending, each difference, square and sum rounded on its
+// own, no fused multiply-add), the value the brute-force definition computes.
+// Merging the answers of row shards by it orders them exactly as the whole
+// collection's brute force does.  One warp per (query, result); inv maps an
+// original row to its row of x (null when x is in the original order).
+constexpr int XD_WARPS = 8;
+__global__ void __launch_bounds__(XD_WARPS * 32) exact_d2_kernel(DevIndex ix, const uint32_t* __restrict__ inv,
+                                                                 const float* __restrict__ Q, int B, int k,
+                                                                 const int64_t* __restrict__ idx,
+                                                                 double* __restrict__ out) {
+    __shared__ double buf[XD_WARPS][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * XD_WARPS + warp;
+    if (t >= (int64_t)B * k) return;  // warp-uniform
+    const int64_t b = t / k;
+    const int64_t id = idx[t];
+    double d = __longlong_as_double(0x7ff8000000000000ll);  // NaN for a row outside [0, N)
+    if (id >= 0 && id < ix.N) {
+        const int64_t row = inv ? (int64_t)inv[id] : id;
+        d = warp_d2_fp64_seq(ix.x + row * ix.n, Q + b * ix.n, ix.n, buf[warp]);
+    }
+    if (lane == 0) out[t] = d;
+}
+
+// inv[orig[p]] = p: the row of x of every original row, for indexes that hold
+// their rows in leaf order
+__global__ void __launch_bounds__(256) inverse_perm_kernel(const uint32_t* __restrict__ orig, int64_t N,
+                                                           uint32_t* __restrict__ inv) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x)
+        inv[orig[p]] = (uint32_t)p;
 }
 
 // ================================================================ batched kernels
@@ -1345,10 +2015,12 @@ __global__ void __launch_bounds__(256) bq_recheck_kernel(DevIndex ix, const Quer
         float4 qv[NV ? NV : 1];
         load_q<NV>(s.q, qv);
         bool ab;
+        int nread;
         const uint32_t row = row_at(ix, r.x);
-        const float d2 = warp_d2<NV>(ix, (int64_t)row, qv, s.q, abandon_limit(kth, delta), ab);
+        const float d2 = warp_d2<NV>(ix, (int64_t)row, qv, s.q, abandon_limit(kth, delta), ab, nread);
         if (lane == 0) {
             atomicAdd(&s.ctl->series_refined, 1ull);
+            atomicAdd(&s.ctl->ed_floats, (unsigned long long)nread);
             if (!ab) {
                 const unsigned long long kk = ld_volatile_u64(&s.topk[k - 1]);
                 if (kk == EMPTY_SLOT || (double)d2 <= (double)key_d2(kk) * (1.0 + 3.0 * delta))
@@ -1393,7 +2065,10 @@ void alloc_query_scratch_for(int64_t L, int64_t N, int n, int card, uint32_t can
     q.out_dist = static_cast<float*>(dev_alloc(sizeof(float) * MAX_K, st));
     q.surv_cap = surv_cap;
     q.surv = static_cast<uint2*>(dev_alloc(sizeof(uint2) * surv_cap, st));
+    // a query starts with its k best empty and its counts at zero (each query's
+    // q_finalize leaves them so for the next one)
     ISAX_CUDA_TRY(cudaMemsetAsync(q.ctl, 0, sizeof(QCtl), st));
+    ISAX_CUDA_TRY(cudaMemsetAsync(q.topk, 0xFF, sizeof(unsigned long long) * MAX_K, st));
 }
 
 uint32_t default_surv_cap(int64_t N) { return (uint32_t)std::max<int64_t>(1, std::min<int64_t>(N, 1 << 21)); }
@@ -1513,7 +2188,7 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
         ix->h_ctl = nullptr;
     }
     void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp,
-                    ix->tree, ix->tree_root};
+                    ix->tree, ix->tree_root, ix->inv};
     for (void* p : ptrs)
         if (p) dev_free(p, st);
     ix->x = nullptr;
@@ -1525,6 +2200,7 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
     ix->bp = nullptr;
     ix->tree = nullptr;
     ix->tree_root = nullptr;
+    ix->inv = nullptr;
 }
 
 namespace {
@@ -1541,40 +2217,47 @@ template <int NV>
 void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st, int mode,
                           int scan_share) {
     const DevIndex& d = ix->d;
+    // the query's share of the SMs (all of them, or a part when queries run side by side)
+    const unsigned grid = (unsigned)std::max(1, ix->num_sms / std::max(1, scan_share));
     {
-        ISAX_LAUNCH("q_prep", st);
-        q_prep_kernel<<<1, PREP_THREADS, 0, st>>>(d, s, k);
-    }
-    const int approx_blocks = std::max(1, std::min(ix->num_sms, (d.leaf_size + 7) / 8));
-    {
-        ISAX_LAUNCH("q_approx", st);
-        q_approx_kernel<NV><<<approx_blocks, 256, 0, st>>>(d, s, k);
+        ISAX_LAUNCH("q_front", st);
+        q_front_kernel<NV><<<grid, FR_THREADS, 0, st>>>(d, s, k, APPROX_NEIGHBORS);
     }
     const unsigned lb_blocks = (unsigned)std::min<int64_t>((d.L + 255) / 256, (int64_t)ix->num_sms * 8);
     if (mode == QUERY_FLAT) {
         ISAX_LAUNCH("q_flat_list", st);
-        q_flat_list_kernel<<<lb_blocks, 256, 0, st>>>(d, s);
+        q_flat_list_kernel<<<lb_blocks, 256, 0, st>>>(d, s, k);
     } else {
-        {
-            ISAX_LAUNCH("q_leaf_lb", st);
-            q_leaf_lb_kernel<<<lb_blocks, 256, 0, st>>>(d, s, k);
-        }
-        {
-            ISAX_LAUNCH("q_leaf_scatter", st);
-            q_leaf_scatter_kernel<<<lb_blocks, NBINS, 0, st>>>(d, s, k);
-        }
+        // cooperative: its CTAs meet at a grid barrier, so all of them must be resident
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(BIN_THREADS);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        ISAX_LAUNCH("q_leaf_bin", st);
+        ISAX_CUDA_TRY(cudaLaunchKernelEx(&cfg, q_leaf_bin_kernel, d, s, k));
     }
     {
         // one CTA per SM: its warps' copy rings take most of the SM's shared memory
         prepare_scan_kernel(ix->device);
-        const unsigned grid = (unsigned)std::max(1, ix->num_sms / std::max(1, scan_share));
         ISAX_LAUNCH("q_series_lb", st);
         if (d.card == 256)
             q_series_lb_kernel<256><<<grid, LB_THREADS, LB_SMEM, st>>>(d, s, k);
         else
             q_series_lb_kernel<0><<<grid, LB_THREADS, LB_SMEM, st>>>(d, s, k);
     }
-    {
+    if (NV == 2) {
+        // n = 256: rows in two halves, the second read only while the row may be in the answer
+        static int grid_rh = 0;
+        if (!grid_rh) grid_rh = occupancy_grid((const void*)q_refine_half_kernel, RF_THREADS, 0, ix->num_sms);
+        ISAX_LAUNCH("q_refine", st);
+        q_refine_half_kernel<<<grid_rh, RF_THREADS, 0, st>>>(d, s, k);
+    } else {
         static int grid_rf = 0;
         if (!grid_rf) grid_rf = occupancy_grid((const void*)q_refine_kernel<NV>, RF_THREADS, 0, ix->num_sms);
         ISAX_LAUNCH("q_refine", st);
@@ -1678,8 +2361,8 @@ void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_
             if (attempt >= 3) throw Error{ISAX_ERR_INTERNAL, "candidate buffer kept overflowing"};
             const uint64_t N = (uint64_t)ix->d.N;
             uint64_t want_c = ix->qs.cand_cap, want_s = ix->qs.surv_cap;
-            if (ctl_out->cand_count > ix->qs.cand_cap)
-                want_c = std::min<uint64_t>(std::max<uint64_t>((uint64_t)ctl_out->cand_count * 2,
+            if (ctl_out->cand_total > ix->qs.cand_cap)
+                want_c = std::min<uint64_t>(std::max<uint64_t>((uint64_t)ctl_out->cand_total * 2,
                                                                (uint64_t)ix->qs.cand_cap * 4), N);
             if (ctl_out->surv_count > ix->qs.surv_cap)
                 want_s = std::min<uint64_t>(std::max<uint64_t>((uint64_t)ctl_out->surv_count * 2,
@@ -1984,7 +2667,10 @@ static void launch_plain_chunk(isax_index* ix, PlainBatch* pb, int C, int k, cud
         ISAX_CUDA_TRY(cudaMemcpyAsync(pb->tasks_refine, pb->h_tasks_refine, sizeof(uint2) * Tr,
                                       cudaMemcpyHostToDevice, st));
         ISAX_LAUNCH("bq_refine", st);
-        bq_refine_kernel<NV><<<Tr, RF_THREADS, 0, st>>>(d, ss, pb->tasks_refine, k);
+        if (NV == 2)
+            bq_refine_half_kernel<<<Tr, RF_THREADS, 0, st>>>(d, ss, pb->tasks_refine, k);
+        else
+            bq_refine_kernel<NV><<<Tr, RF_THREADS, 0, st>>>(d, ss, pb->tasks_refine, k);
     }
     launch_bq_finalize(ix, ss, C, k, st);
     ISAX_CUDA_TRY(cudaGetLastError());
@@ -2073,6 +2759,29 @@ void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t m
         next.clear();
     }
     if (nonfinite) throw Error{ISAX_ERR_INVALID_ARG, "a query contains a non-finite value"};
+}
+
+// ---------------------------------------------------------------- exact FP64 distances (host)
+void exact_d2_device(isax_index* ix, const float* Q, int B, int k, const int64_t* idx, double* out,
+                     cudaStream_t st) {
+    if (!ix->rows_in_place && !ix->inv) {
+        uint32_t* inv = static_cast<uint32_t*>(dev_alloc(sizeof(uint32_t) * (size_t)ix->d.N, st));
+        ISAX_LAUNCH("inverse_perm", st);
+        inverse_perm_kernel<<<ix->num_sms * 8, 256, 0, st>>>(ix->d.orig, ix->d.N, inv);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            dev_free(inv, st);
+            ISAX_CUDA_TRY(e);
+        }
+        ix->inv = inv;
+        ix->bytes += (int64_t)sizeof(uint32_t) * ix->d.N;
+    }
+    const int64_t T = (int64_t)B * k;
+    if (T == 0) return;
+    ISAX_LAUNCH("exact_d2", st);
+    exact_d2_kernel<<<(unsigned)((T + XD_WARPS - 1) / XD_WARPS), XD_WARPS * 32, 0, st>>>(
+        ix->d, ix->rows_in_place ? nullptr : ix->inv, Q, B, k, idx, out);
+    ISAX_CUDA_TRY(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------- batched launchers

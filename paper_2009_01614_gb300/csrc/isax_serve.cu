@@ -32,8 +32,11 @@ static double now_s() {
 }
 
 // candidate entries reserved for a k-NN request (12 bytes each; a query that
-// keeps more reruns with four times the room)
-static uint32_t serve_cand_cap(int k) { return 4096u + 256u * (uint32_t)k; }
+// keeps more reruns with four times the room): the approximate answer's rows,
+// which all take a slot, and room for the refined rows near the k-th best
+static uint32_t serve_cand_cap(int k, int leaf_size) {
+    return approx_rows_max(leaf_size, k) + 4096u + 256u * (uint32_t)k;
+}
 
 struct ServeRequest {
     uint64_t tag = 0;
@@ -111,9 +114,10 @@ static void slot_free(ServeSlot* sl) {
 
 static void server_setup(isax_server* s) {
     int64_t L = 1, Nmax = 1;
-    int n = 16, card = 2;
+    int n = 16, card = 2, leaf = 1;
     for (isax_index* ix : s->colls) {
         L = std::max<int64_t>(L, ix->d.L);
+        leaf = std::max(leaf, (int)ix->d.leaf_size);
         Nmax = std::max<int64_t>(Nmax, ix->d.N);
         n = std::max(n, (int)ix->d.n);
         card = std::max(card, (int)ix->d.card);
@@ -123,7 +127,7 @@ static void server_setup(isax_server* s) {
         s->slots.push_back(sl);
         ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking));
         ISAX_CUDA_TRY(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
-        alloc_query_scratch_for(L, Nmax, n, card, serve_cand_cap(1), default_surv_cap(Nmax), sl->qs, sl->st);
+        alloc_query_scratch_for(L, Nmax, n, card, serve_cand_cap(1, leaf), default_surv_cap(Nmax), sl->qs, sl->st);
         ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_q, sizeof(float) * n));
         ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_ctl, sizeof(QCtl)));
         ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_idx, sizeof(int64_t) * MAX_K));
@@ -159,7 +163,7 @@ static void slot_launch(isax_server* s, ServeSlot* sl) {
 static void slot_start(isax_server* s, ServeSlot* sl, ServeRequest&& r, size_t bytes) {
     sl->req = std::move(r);
     sl->reserved = bytes;
-    sl->need_cap = serve_cand_cap(sl->req.k);
+    sl->need_cap = serve_cand_cap(sl->req.k, s->colls[sl->req.coll]->d.leaf_size);
     sl->need_surv = 0;
     sl->reruns = 0;
     sl->wants_room = false;
@@ -250,8 +254,8 @@ static void server_loop(isax_server* s) {
                 publish(s, sl, ISAX_ERR_TIMEOUT);
             } else if ((c.flags & QF_OVERFLOW) && sl->reruns < 4) {
                 const uint64_t N = (uint64_t)s->colls[sl->req.coll]->d.N;
-                if (c.cand_count > sl->qs.cand_cap) {
-                    const uint64_t want = std::max<uint64_t>((uint64_t)c.cand_count * 2, (uint64_t)sl->need_cap * 4);
+                if (c.cand_total > sl->qs.cand_cap) {
+                    const uint64_t want = std::max<uint64_t>((uint64_t)c.cand_total * 2, (uint64_t)sl->need_cap * 4);
                     sl->need_cap = (uint32_t)std::min<uint64_t>(want, N + 16);
                 }
                 if (c.surv_count > sl->qs.surv_cap)
@@ -278,7 +282,8 @@ static void server_loop(isax_server* s) {
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 if (s->pending.empty()) break;
-                bytes = (size_t)serve_cand_cap(s->pending.front().k) * 12;
+                bytes = (size_t)serve_cand_cap(s->pending.front().k,
+                                               s->colls[s->pending.front().coll]->d.leaf_size) * 12;
                 if (s->reserved + bytes > s->budget && s->in_flight > 0) break;
                 r = std::move(s->pending.front());
                 s->pending.pop_front();
@@ -408,12 +413,13 @@ int32_t isax_server_poll(isax_server* s, isax_server_result* out, int64_t* idx, 
         o.stats.leaves_queued = (int64_t)r.ctl.leaves_queued;
         o.stats.leaves_scanned = (int64_t)r.ctl.leaves_scanned;
         o.stats.series_lb = (int64_t)r.ctl.series_lb;
-        o.stats.series_refined = (int64_t)r.ctl.series_refined;
+        o.stats.series_refined = (int64_t)r.ctl.refined_total;
         o.stats.approx_series = (int64_t)r.ctl.approx_series;
-        o.stats.candidates = (int64_t)r.ctl.cand_count;
+        o.stats.candidates = (int64_t)r.ctl.cand_total;
         o.stats.window = (int64_t)r.ctl.window;
         o.stats.approx_leaf = r.ctl.approx_leaf;
         o.stats.reruns = r.reruns;
+        o.stats.ed_floats = (int64_t)r.ctl.ed_floats;
         if (idx && r.status == ISAX_OK) memcpy(idx + (size_t)m * stride, r.idx.data(), sizeof(int64_t) * r.k);
         if (dist && r.status == ISAX_OK) memcpy(dist + (size_t)m * stride, r.dist.data(), sizeof(float) * r.k);
         s->done.pop_front();

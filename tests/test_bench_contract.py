@@ -59,9 +59,10 @@ def test_query_roofline_arithmetic():
     spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
-    acc = {"series_lb": 814_000_000, "series_refined": 7_650_000}
+    # the row values the refinement read (an abandoned row counts what it read)
+    acc = {"series_lb": 814_000_000, "series_refined": 7_650_000, "ed_floats": 1_200_000_000}
     r = bench.query_roofline(acc, 100, 151_497, 256, 13.1, 6701.5)
-    b = 32 * 151_497 + 16 * 8_140_000 + 4 * 256 * 76_500
+    b = 32 * 151_497 + 16 * 8_140_000 + 4 * 12_000_000
     assert r["algorithmic_bytes_per_query"] == pytest.approx(b)
     assert r["mean_query_ms"] == pytest.approx(0.131)
     assert r["achieved"] == pytest.approx(b / 0.131e-3 / 1e9)
