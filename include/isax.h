@@ -414,6 +414,30 @@ void isax_server_destroy(isax_server* s);
 isax_status isax_tc_selftest(const uint16_t* a, const uint16_t* b, int32_t n_cols, float* d,
                              void* cuda_stream);
 
+/* ------------------------------------------------------------ failure checks */
+
+/*
+ * isax_selftest_wait - make one of the library's bounded device waits run out
+ * on purpose, to check its failure path without a GPU fault (the paper has no
+ * counterpart).  kind 0: a one-warp kernel waits on its own mbarrier, which
+ * completes only if satisfied != 0 (the kernel then arrives on it first); no
+ * copy is in flight.  kind 1: a cooperative grid of 4 CTAs meets at the
+ * binning step's grid barrier, expecting 4 arrivals if satisfied != 0 and 5
+ * (never reached) otherwise.  Each wait polls at most max_polls times (1 ..
+ * 2^24).  Returns ISAX_OK when the wait completed, ISAX_ERR_TIMEOUT when it gave
+ * up; the device stays usable either way.  Synchronises cuda_stream.
+ */
+isax_status isax_selftest_wait(int32_t kind, int32_t satisfied, int32_t max_polls, void* cuda_stream);
+
+/*
+ * isax_debug_inject_timeout - test hook: the next `queries` query control
+ * blocks that the host reads back (single, batch, BF16 batch, allocation-free
+ * and served queries alike) report a bounded device wait that gave up, so each
+ * entry point's handling of it (ISAX_ERR_TIMEOUT) can be checked without a wait
+ * running out.  0 cancels.  The paper has no counterpart.
+ */
+isax_status isax_debug_inject_timeout(int32_t queries);
+
 /* ------------------------------------------------------------ tracing */
 
 typedef struct isax_kernel_time {

@@ -20,7 +20,8 @@ __all__ = [
     "isax_last_error", "isax_get_index_info", "isax_index_export", "isax_summarize",
     "isax_set_allocator", "isax_trim_memory", "isax_profile", "isax_profile_report", "isax_launch_count",
     "isax_query_knn_noalloc", "isax_tc_selftest", "isax_query_knn_batch_bf16",
-    "isax_prepare_bf16", "isax_query_knn_flat", "isax_exact_d2", "Server", "ServerParams", "ServerResult", "ServerInfo",
+    "isax_prepare_bf16", "isax_query_knn_flat", "isax_exact_d2", "isax_selftest_wait",
+    "isax_debug_inject_timeout", "Server", "ServerParams", "ServerResult", "ServerInfo",
     "isax_server_create", "isax_server_add_collection", "isax_server_submit", "isax_server_poll",
     "isax_server_get_info", "isax_server_clock", "isax_server_destroy",
 ]
@@ -175,6 +176,10 @@ def lib():
         L.isax_server_clock.restype = ctypes.c_double
         L.isax_exact_d2.argtypes = [vp, vp, i32, i32, u32, vp, vp, vp]
         L.isax_exact_d2.restype = st
+        L.isax_selftest_wait.argtypes = [i32, i32, i32, vp]
+        L.isax_selftest_wait.restype = st
+        L.isax_debug_inject_timeout.argtypes = [i32]
+        L.isax_debug_inject_timeout.restype = st
         L.isax_server_destroy.argtypes = [vp]
         L.isax_server_destroy.restype = None
         _lib = L
@@ -232,6 +237,15 @@ def isax_query_knn_flat(index, q_ptr, k, mem_flags, out_idx_ptr, out_dist_ptr, s
 def isax_exact_d2(index, Q_ptr, B, k, mem_flags, idx_ptr, out_d2_ptr, stream=0):
     """FP64 squared distances of rows idx[b][j] to queries Q[b], definition order."""
     _check(lib().isax_exact_d2(index, Q_ptr, B, k, mem_flags, idx_ptr, out_d2_ptr, stream))
+
+
+def isax_selftest_wait(kind, satisfied, max_polls, stream=0):
+    """Make a bounded device wait run out (or not); returns the status code."""
+    return lib().isax_selftest_wait(kind, satisfied, max_polls, stream)
+
+
+def isax_debug_inject_timeout(queries):
+    _check(lib().isax_debug_inject_timeout(queries))
 
 
 def isax_query_knn_batch_bf16(index, Q_ptr, B, k, mem_flags, out_idx_ptr, out_dist_ptr, stats=None,

@@ -10,7 +10,7 @@ LIB = os.path.join(OUT, "libisaxgpu.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["isax_api.cu", "isax_build.cu", "isax_query.cu", "isax_profile.cu", "isax_noalloc.cu",
-           "isax_tc.cu", "isax_serve.cu"]
+           "isax_tc.cu", "isax_serve.cu", "isax_selftest.cu"]
 HEADERS = ["isax_common.cuh", "isax_kernels_util.cuh", "isax_tc.cuh"]
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = [GENCODE, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -1317,7 +1317,7 @@ uint32_t balanced_leaves(isax_index* ix, TempPool& tmp, const uint4* sax_tmp, un
 }  // namespace
 
 void free_index_arrays(isax_index* ix, cudaStream_t st);
-void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, uint32_t surv_cap, cudaStream_t st);
+
 
 isax_index* build_index_impl(const float* series, int64_t N, int n, int card, int leaf_size,
                              uint32_t mem_flags, cudaStream_t st) {

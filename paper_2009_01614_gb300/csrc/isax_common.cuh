@@ -179,9 +179,12 @@ void free_index_arrays(isax_index* ix, cudaStream_t st);
 // more leaves room for the scans of concurrent queries)
 void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st,
                              int mode = QUERY_MESSI, int scan_share = 1);
-void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, uint32_t surv_cap, cudaStream_t st);
+void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, uint32_t surv_cap, cudaStream_t st,
+                         bool keep_query = false);
 uint32_t default_surv_cap(int64_t N);  // survivor entries of a fresh query scratch
 void launch_breakpoints(int card, float* bp, cudaStream_t st);
+// test hook: QF_STALLED for the next queries whose control block the host reads (isax_selftest.cu)
+uint32_t injected_query_flags();
 // batched query kernels (query b of the batch owns scratch ss[b])
 void launch_bq_prep(isax_index* ix, const QueryScratch* ss, int B, int k, int neighbors,
                     cudaStream_t st);

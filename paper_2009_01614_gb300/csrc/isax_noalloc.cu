@@ -143,6 +143,7 @@ extern "C" isax_status isax_query_knn_noalloc(const isax_index* cix, const float
         QCtl c;
         ISAX_CUDA_TRY(cudaMemcpyAsync(&c, s.ctl, sizeof(QCtl), cudaMemcpyDeviceToHost, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+        c.flags |= injected_query_flags();
         if (c.flags & QF_NONFINITE) fail(ISAX_ERR_INVALID_ARG, "query contains a non-finite value");
         if (c.flags & QF_STALLED) fail(ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed");
         if (c.flags & QF_OVERFLOW)

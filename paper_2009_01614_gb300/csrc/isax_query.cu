@@ -1087,11 +1087,19 @@ constexpr int LB_STAGES = 3;
 constexpr int LB_PER_LANE = LB_PIECE / 32;
 constexpr int LB_BUF = 48;     // survivors buffered per warp before one global append
 constexpr uint32_t LB_WAIT = 1u << 22;  // bounded wait on a stage's copy
-constexpr size_t LB_TAB_BYTES = sizeof(float) * W * MAX_CARD;
+// The first LB_TAB_BYTES of the scan's shared memory: for 8-bit symbols the byte
+// table [16][256] (4 KB), then the breakpoints and the query PAA; for smaller
+// cardinalities the fp32 table [16][card] (at most 8 KB)
+constexpr size_t LB_TAB_BYTES = 8192;
+constexpr size_t LB_BP_OFF = 4096, LB_QPAA_OFF = LB_BP_OFF + sizeof(float) * (MAX_CARD + 4);
+static_assert(LB_QPAA_OFF + sizeof(float) * W <= LB_TAB_BYTES, "byte table, breakpoints and PAA fit the region");
+static_assert(sizeof(float) * W * (MAX_CARD / 2) <= LB_TAB_BYTES, "the fp32 table of cardinality <= 128 fits");
 constexpr size_t LB_RING_BYTES = (size_t)LB_WARPS * LB_STAGES * LB_PIECE * sizeof(uint4);
 constexpr size_t LB_SMEM = 1024 + LB_TAB_BYTES + LB_RING_BYTES + sizeof(uint64_t) * LB_WARPS * LB_STAGES +
-                           sizeof(uint2) * LB_WARPS * (LB_STAGES + LB_BUF) + sizeof(uint32_t) * (LB_WARPS + 2);
+                           sizeof(uint2) * LB_WARPS * (LB_STAGES + LB_BUF) + (size_t)LB_WARPS * LB_PIECE +
+                           sizeof(uint32_t) * (LB_WARPS + 2);
 static_assert(LB_SMEM <= 227 * 1024, "the scan's shared memory exceeds a CTA's limit");
+constexpr uint32_t LB_QMAX = 255;  // byte-table units of the threshold
 
 template <int OFF>
 __device__ __forceinline__ float lds_f32(uint32_t addr) {
@@ -1099,15 +1107,36 @@ __device__ __forceinline__ float lds_f32(uint32_t addr) {
     asm("ld.shared.f32 %0, [%1+%2];" : "=f"(x) : "r"(addr), "n"(OFF));
     return x;
 }
-// 4 segments (word Q of the SAX word, 8-bit symbols) added to lb in segment
-// order; tab_sa is the table's shared address, 1024-aligned, so the symbol's
-// byte offset ORs into it and the row offset is the load's immediate
+template <int OFF>
+__device__ __forceinline__ uint32_t lds_u8(uint32_t addr) {
+    uint32_t x;
+    asm("ld.shared.u8 %0, [%1+%2];" : "=r"(x) : "r"(addr), "n"(OFF));
+    return x;
+}
+// byte-table units of the 4 segments held by word Q of the SAX word, summed:
+// the byte table's rows are 256 bytes and its base is 256-aligned, so one byte
+// permute puts a symbol in the low byte of the table's address and the row
+// offset is the load's immediate
 template <int Q>
-__device__ __forceinline__ float lb_word256(float lb, uint32_t v, uint32_t tab_sa) {
-    lb += lds_f32<(4 * Q + 0) * 1024>(((v << 2) & 0x3FCu) | tab_sa);
-    lb += lds_f32<(4 * Q + 1) * 1024>(((v >> 6) & 0x3FCu) | tab_sa);
-    lb += lds_f32<(4 * Q + 2) * 1024>(((v >> 14) & 0x3FCu) | tab_sa);
-    lb += lds_f32<(4 * Q + 3) * 1024>(((v >> 22) & 0x3FCu) | tab_sa);
+__device__ __forceinline__ uint32_t lb8_word(uint32_t v, uint32_t tab8_sa) {
+    return lds_u8<(4 * Q + 0) * 256>(__byte_perm(v, tab8_sa, 0x7650u)) +
+           lds_u8<(4 * Q + 1) * 256>(__byte_perm(v, tab8_sa, 0x7651u)) +
+           lds_u8<(4 * Q + 2) * 256>(__byte_perm(v, tab8_sa, 0x7652u)) +
+           lds_u8<(4 * Q + 3) * 256>(__byte_perm(v, tab8_sa, 0x7653u));
+}
+// the fp32 lower bound of an 8-bit SAX word, every table entry formed as the
+// query's table is: T[i][s] = m * dist(qpaa_i, [bp[s], bp[s+1]))^2, summed in
+// segment order
+__device__ __forceinline__ float lb_exact256(uint4 w, const float* bp, const float* qpaa, float mf) {
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+    float lb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const uint32_t sym = (words[i >> 2] >> (8 * (i & 3))) & 255u;
+        const float lo = bp[sym], hi = bp[sym + 1], v = qpaa[i];
+        const float d = v < lo ? lo - v : (v >= hi ? v - hi : 0.0f);
+        lb += (d * d) * mf;
+    }
     return lb;
 }
 
@@ -1119,12 +1148,16 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
     extern __shared__ unsigned char lb_smem_raw[];
     QCtl* c = s.ctl;
     unsigned char* sm = lb_smem_raw + ((1024u - (smem_u32(lb_smem_raw) & 1023u)) & 1023u);
-    float* tab = reinterpret_cast<float*>(sm);
+    float* tab = reinterpret_cast<float*>(sm);                      // fp32 table (cardinality < 256)
+    unsigned char* tab8 = sm;                                       // byte table (8-bit symbols)
+    float* bp_s = reinterpret_cast<float*>(sm + LB_BP_OFF);         // breakpoints (8-bit symbols)
+    float* qpaa_s = reinterpret_cast<float*>(sm + LB_QPAA_OFF);     // query PAA (8-bit symbols)
     uint4* ring = reinterpret_cast<uint4*>(sm + LB_TAB_BYTES);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + LB_TAB_BYTES + LB_RING_BYTES);
     uint2* metas = reinterpret_cast<uint2*>(bars + LB_WARPS * LB_STAGES);
     uint2* bufs = metas + LB_WARPS * LB_STAGES;
-    uint32_t* next_p = reinterpret_cast<uint32_t*>(bufs + LB_WARPS * LB_BUF);
+    uint8_t* cand1 = reinterpret_cast<uint8_t*>(bufs + LB_WARPS * LB_BUF);  // [LB_WARPS][LB_PIECE]
+    uint32_t* next_p = reinterpret_cast<uint32_t*>(cand1 + LB_WARPS * LB_PIECE);
     uint32_t* wcnt = next_p + 1;  // [LB_WARPS + 1]: each warp's last survivors, then the CTA's base
     const int card = ix.card;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1144,14 +1177,22 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         const size_t i = cta + (size_t)(warp * LB_STAGES + t) * G;
         e[t] = lane == 0 && i < s.work_cap ? s.work[i] : make_uint2(0u, 0u);
     }
-    const float4* tsrc = reinterpret_cast<const float4*>(s.table);
-    const int nv = W * card / 4;
-    constexpr int TV = (W * MAX_CARD / 4 + LB_THREADS - 1) / LB_THREADS;
+    // the table's inputs: the breakpoints and the query PAA (8-bit symbols), or
+    // the query's fp32 table (smaller cardinalities)
+    constexpr int TV = (W * MAX_CARD / 2 / 4 + LB_THREADS - 1) / LB_THREADS;
     float4 tv[TV];
+    float bpv = 0.0f, qpv = 0.0f;
+    if constexpr (CARD == 256) {
+        if (threadIdx.x <= MAX_CARD) bpv = ix.bp[threadIdx.x];
+        if (threadIdx.x < W) qpv = c->qpaa[threadIdx.x];
+    } else {
+        const float4* tsrc = reinterpret_cast<const float4*>(s.table);
+        const int nv = W * card / 4;
 #pragma unroll
-    for (int t = 0; t < TV; ++t) {
-        const int i = threadIdx.x + t * LB_THREADS;
-        if (i < nv) tv[t] = tsrc[i];
+        for (int t = 0; t < TV; ++t) {
+            const int i = threadIdx.x + t * LB_THREADS;
+            if (i < nv) tv[t] = tsrc[i];
+        }
     }
     if (flags & QF_NONFINITE) return;
     const uint32_t mine = count > cta ? (count - cta + G - 1) / G : 0u;  // this CTA's items
@@ -1178,15 +1219,46 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
     for (int t = 0; t + 1 < LB_STAGES; ++t) issued += j0 + t < mine ? 1u : 0u;
     uint2 pend = e[LB_STAGES - 1];
     bool pend_ok = j0 + LB_STAGES - 1 < mine;
-    float4* tdst = reinterpret_cast<float4*>(tab);
+    const float mf = (float)(ix.n / W);
+    if constexpr (CARD == 256) {
+        if (threadIdx.x <= MAX_CARD) bp_s[threadIdx.x] = bpv;
+        if (threadIdx.x < W) qpaa_s[threadIdx.x] = qpv;
+        __syncthreads();
+        // the byte table: q[i][s] = floor(T[i][s] * 255 / thr), at most 255, with T
+        // the query table's fp32 entry; computed in FP64 with a relative margin
+        // below the exact quotient, so q * thr / 255 <= T.  A row whose units sum
+        // to more than 255 has a true bound >= 256 thr / 255, whose fp32 sum of 16
+        // entries exceeds thr: it would be pruned.  A threshold that is not a
+        // positive finite number gives zeros: every row goes on to the fp32 bound.
+        const bool scaled = thr > 0.0f && thr < INFINITY;
+        const double inv = scaled ? 255.0 / (double)thr * (1.0 - 1e-9) : 0.0;
+        uint32_t packed = 0;
 #pragma unroll
-    for (int t = 0; t < TV; ++t) {
-        const int i = threadIdx.x + t * LB_THREADS;
-        if (i < nv) tdst[i] = tv[t];
+        for (int b = 0; b < 4; ++b) {
+            const int e = threadIdx.x * 4 + b;
+            const int i = e >> 8, sym = e & 255;
+            const float lo = bp_s[sym], hi = bp_s[sym + 1], v = qpaa_s[i];
+            const float d = v < lo ? lo - v : (v >= hi ? v - hi : 0.0f);
+            const float T = (d * d) * mf;
+            const double qd = (double)T * inv;
+            const uint32_t q = qd >= (double)LB_QMAX ? LB_QMAX : (uint32_t)qd;
+            packed |= q << (8 * b);
+        }
+        reinterpret_cast<uint32_t*>(tab8)[threadIdx.x] = packed;
+        static_assert(LB_THREADS * 4 == W * MAX_CARD, "one 4-entry word of the byte table per thread");
+    } else {
+        float4* tdst = reinterpret_cast<float4*>(tab);
+        const int nv = W * card / 4;
+#pragma unroll
+        for (int t = 0; t < TV; ++t) {
+            const int i = threadIdx.x + t * LB_THREADS;
+            if (i < nv) tdst[i] = tv[t];
+        }
     }
     if (threadIdx.x == 0) *next_p = LB_WARPS * LB_STAGES;  // the items after the warps' first ones go by claim
     __syncthreads();
-    const uint32_t tab_sa = smem_u32(tab);
+    const uint32_t tab8_sa = smem_u32(tab8);
+    uint8_t* wcand = cand1 + warp * LB_PIECE;
     uint2* buf = bufs + warp * LB_BUF;
     int nbuf = 0;  // warp-uniform
     // the buffered survivors go to the global list in one append, each as
@@ -1235,34 +1307,53 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
             const uint32_t r = j * 32 + lane;
             w[j] = r < rows ? src[r] : make_uint4(0u, 0u, 0u, 0u);
         }
-        // the first 8 segments of every row of the lane at once (independent
-        // chains), then per row the rest, 4 segments at a time, while some lane
-        // of the warp is still under the threshold
-        float part[LB_PER_LANE];
-#pragma unroll
-        for (int j = 0; j < LB_PER_LANE; ++j)
-            part[j] = CARD == 256 ? lb_word256<1>(lb_word256<0>(0.0f, w[j].x, tab_sa), w[j].y, tab_sa) : 0.0f;
-#pragma unroll
-        for (int j = 0; j < LB_PER_LANE; ++j) {
-            const uint32_t r = j * 32 + lane;
-            const bool ok = r < rows;
-            float lb;
-            if constexpr (CARD == 256) {
-                lb = part[j];
-                if (!__any_sync(FULL, ok && lb <= thr)) continue;
-                lb = lb_word256<2>(lb, w[j].z, tab_sa);
-                if (!__any_sync(FULL, ok && lb <= thr)) continue;
-                lb = lb_word256<3>(lb, w[j].w, tab_sa);
-            } else {
-                lb = series_lb(w[j], tab, card);
-            }
-            const bool keep = ok && lb <= thr;
+        // a kept row: appended to the warp's buffer as {position, bound}
+        auto keep_rows = [&](bool keep, uint32_t r, float lb) {
             const unsigned m = __ballot_sync(FULL, keep);
             if (m) {
                 if (nbuf + 32 > LB_BUF) drain();
                 if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = make_uint2(pos0 + r, __float_as_uint(lb));
                 nbuf += __popc(m);
                 __syncwarp();
+            }
+        };
+        if constexpr (CARD == 256) {
+            // pass 1, byte units: the first 8 segments of every row of the lane at
+            // once, then per row the rest, 4 segments at a time, while some lane
+            // of the warp is still at or under 255 units; rows still there after
+            // all 16 segments are listed for pass 2
+            uint32_t part[LB_PER_LANE];
+#pragma unroll
+            for (int j = 0; j < LB_PER_LANE; ++j) part[j] = lb8_word<0>(w[j].x, tab8_sa) + lb8_word<1>(w[j].y, tab8_sa);
+            uint32_t ncand = 0;  // warp-uniform
+#pragma unroll
+            for (int j = 0; j < LB_PER_LANE; ++j) {
+                const uint32_t r = j * 32 + lane;
+                const bool ok = r < rows;
+                uint32_t u = part[j];
+                if (!__any_sync(FULL, ok && u <= LB_QMAX)) continue;
+                u += lb8_word<2>(w[j].z, tab8_sa);
+                if (!__any_sync(FULL, ok && u <= LB_QMAX)) continue;
+                u += lb8_word<3>(w[j].w, tab8_sa);
+                const bool cand = ok && u <= LB_QMAX;
+                const unsigned m = __ballot_sync(FULL, cand);
+                if (cand) wcand[ncand + __popc(m & ((1u << lane) - 1u))] = (uint8_t)r;
+                ncand += __popc(m);
+            }
+            // pass 2: the fp32 bound of the listed rows, one per lane
+            __syncwarp();
+            for (uint32_t c0 = 0; c0 < ncand; c0 += 32) {
+                const bool mine_c = c0 + lane < ncand;
+                const uint32_t r = mine_c ? wcand[c0 + lane] : 0u;
+                const float lb = mine_c ? lb_exact256(src[r], bp_s, qpaa_s, mf) : INFINITY;
+                keep_rows(mine_c && lb <= thr, r, lb);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < LB_PER_LANE; ++j) {
+                const uint32_t r = j * 32 + lane;
+                const float lb = series_lb(w[j], tab, card);
+                keep_rows(r < rows && lb <= thr, r, lb);
             }
         }
         ++done;
@@ -2163,10 +2254,23 @@ static void drop_query_graphs(isax_index* ix) {
     if (ix->graphs) static_cast<QueryGraphs*>(ix->graphs)->clear();
 }
 
-void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, uint32_t surv_cap, cudaStream_t st) {
+// A new scratch for the index's own queries; the old one (if any) is freed only
+// once the new one is allocated, so a failed allocation leaves the index as it
+// was.  keep_query: the query already in the old scratch moves to the new one.
+void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, uint32_t surv_cap, cudaStream_t st,
+                         bool keep_query) {
+    QueryScratch fresh{};
+    try {
+        alloc_scratch(ix->d, cand_cap, surv_cap, fresh, st);
+        if (keep_query && ix->qs.q)
+            ISAX_CUDA_TRY(cudaMemcpyAsync(fresh.q, ix->qs.q, sizeof(float) * ix->d.n, cudaMemcpyDeviceToDevice, st));
+    } catch (...) {
+        free_scratch(fresh, st);
+        throw;
+    }
     drop_query_graphs(ix);
     free_query_scratch(ix, st);
-    alloc_scratch(ix->d, cand_cap, surv_cap, ix->qs, st);
+    ix->qs = fresh;
 }
 
 void free_index_arrays(isax_index* ix, cudaStream_t st) {
@@ -2355,6 +2459,7 @@ void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_
         if (out_dist) ISAX_CUDA_TRY(cudaMemcpyAsync(out_dist, ix->qs.out_dist, sizeof(float) * k, kout, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         *ctl_out = *ix->h_ctl;
+        ctl_out->flags |= injected_query_flags();
         if (ctl_out->flags & QF_NONFINITE) throw Error{ISAX_ERR_INVALID_ARG, "query contains a non-finite value"};
         if (ctl_out->flags & QF_STALLED) throw Error{ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed"};
         if (ctl_out->flags & QF_OVERFLOW) {
@@ -2367,12 +2472,7 @@ void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_
             if (ctl_out->surv_count > ix->qs.surv_cap)
                 want_s = std::min<uint64_t>(std::max<uint64_t>((uint64_t)ctl_out->surv_count * 2,
                                                                (uint64_t)ix->qs.surv_cap * 4), N);
-            // keep q across the reallocation
-            float* qsave = static_cast<float*>(dev_alloc(sizeof(float) * ix->d.n, st));
-            ISAX_CUDA_TRY(cudaMemcpyAsync(qsave, ix->qs.q, sizeof(float) * ix->d.n, cudaMemcpyDeviceToDevice, st));
-            alloc_query_scratch(ix, (uint32_t)want_c, (uint32_t)want_s, st);
-            ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, qsave, sizeof(float) * ix->d.n, cudaMemcpyDeviceToDevice, st));
-            dev_free(qsave, st);
+            alloc_query_scratch(ix, (uint32_t)want_c, (uint32_t)want_s, st, true);  // q moves along
             ++*reruns;
             continue;
         }
@@ -2392,11 +2492,20 @@ static void query_batch_slots(isax_index* ix, const float* Q, int B, int k, uint
     if (!ix->pool) ix->pool = new SlotPool();
     SlotPool* pool = static_cast<SlotPool*>(ix->pool);
     while ((int)pool->slots.size() < S) {
+        // a slot joins the pool only once all of it is allocated
         QuerySlot* sl = new QuerySlot();
+        try {
+            ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking));
+            ISAX_CUDA_TRY(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
+            alloc_scratch(ix->d, ix->qs.cand_cap, ix->qs.surv_cap, sl->qs, st);
+        } catch (...) {
+            free_scratch(sl->qs, st);
+            if (sl->done) cudaEventDestroy(sl->done);
+            if (sl->stream) cudaStreamDestroy(sl->stream);
+            delete sl;
+            throw;
+        }
         pool->slots.push_back(sl);
-        ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking));
-        ISAX_CUDA_TRY(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
-        alloc_scratch(ix->d, ix->qs.cand_cap, ix->qs.surv_cap, sl->qs, st);
     }
     if (pool->host_cap < (size_t)B) {
         if (pool->host_ctl) cudaFreeHost(pool->host_ctl);
@@ -2452,6 +2561,7 @@ static void query_batch_slots(isax_index* ix, const float* Q, int B, int k, uint
     bool nonfinite = false;
     for (int b = 0; b < B; ++b) {
         QCtl c = pool->host_ctl[b];
+        c.flags |= injected_query_flags();
         int reruns = 0;
         if (c.flags & QF_NONFINITE) {
             nonfinite = true;
@@ -2731,6 +2841,7 @@ void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t m
             for (int i = 0; i < C; ++i) {
                 const int b = todo[c0 + i];
                 QCtl c = pb->h_ctl[i];
+                c.flags |= injected_query_flags();
                 int reruns = tier;
                 if (c.flags & QF_NONFINITE) {
                     nonfinite = true;

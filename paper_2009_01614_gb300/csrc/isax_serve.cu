@@ -122,17 +122,25 @@ static void server_setup(isax_server* s) {
         n = std::max(n, (int)ix->d.n);
         card = std::max(card, (int)ix->d.card);
     }
-    for (int i = 0; i < s->nslots; ++i) {
-        ServeSlot* sl = new ServeSlot();
-        s->slots.push_back(sl);
-        ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking));
-        ISAX_CUDA_TRY(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
-        alloc_query_scratch_for(L, Nmax, n, card, serve_cand_cap(1, leaf), default_surv_cap(Nmax), sl->qs, sl->st);
-        ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_q, sizeof(float) * n));
-        ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_ctl, sizeof(QCtl)));
-        ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_idx, sizeof(int64_t) * MAX_K));
-        ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_dist, sizeof(float) * MAX_K));
-        ISAX_CUDA_TRY(cudaStreamSynchronize(sl->st));
+    // all slots or none: a failure frees the slots made so far
+    try {
+        for (int i = 0; i < s->nslots; ++i) {
+            ServeSlot* sl = new ServeSlot();
+            s->slots.push_back(sl);
+            ISAX_CUDA_TRY(cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking));
+            ISAX_CUDA_TRY(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
+            alloc_query_scratch_for(L, Nmax, n, card, serve_cand_cap(1, leaf), default_surv_cap(Nmax), sl->qs,
+                                    sl->st);
+            ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_q, sizeof(float) * n));
+            ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_ctl, sizeof(QCtl)));
+            ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_idx, sizeof(int64_t) * MAX_K));
+            ISAX_CUDA_TRY(cudaMallocHost((void**)&sl->h_dist, sizeof(float) * MAX_K));
+            ISAX_CUDA_TRY(cudaStreamSynchronize(sl->st));
+        }
+    } catch (...) {
+        for (ServeSlot* sl : s->slots) slot_free(sl);
+        s->slots.clear();
+        throw;
     }
 }
 
@@ -247,7 +255,8 @@ static void server_loop(isax_server* s) {
                 publish(s, sl, ISAX_ERR_CUDA);
                 continue;
             }
-            const QCtl& c = *sl->h_ctl;
+            QCtl& c = *sl->h_ctl;
+            c.flags |= injected_query_flags();
             if (c.flags & QF_NONFINITE) {
                 publish(s, sl, ISAX_ERR_INVALID_ARG);
             } else if (c.flags & QF_STALLED) {

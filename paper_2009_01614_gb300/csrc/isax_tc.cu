@@ -881,9 +881,19 @@ static TcState* ensure_tc(isax_index* ix, cudaStream_t st) {
     return t;
 }
 
+static void ensure_batch_alloc(TcState* t, const isax_index* ix, int B, cudaStream_t st);
+// batch scratch for B queries: all of it, or (on a failed allocation) none
 static void ensure_batch(TcState* t, const isax_index* ix, int B, cudaStream_t st) {
     if (t->Bcap >= B) return;
     free_batch(t, st);
+    try {
+        ensure_batch_alloc(t, ix, B, st);
+    } catch (...) {
+        free_batch(t, st);
+        throw;
+    }
+}
+static void ensure_batch_alloc(TcState* t, const isax_index* ix, int B, cudaStream_t st) {
     const DevIndex& d = ix->d;
     const size_t Bs = (size_t)B;
     t->q = dalloc<float>(Bs * d.n, st);
@@ -1055,11 +1065,13 @@ void query_batch_tc(isax_index* ix, const float* Q, int B, int k, uint32_t mem_f
         const cudaMemcpyKind kout = dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         for (int b = 0; b < Bp; ++b) {
             QCtl c = t->host_ctl[b];
+            c.flags |= injected_query_flags();
             int reruns = 0;
             if (c.flags & QF_NONFINITE) {
                 nonfinite = true;
                 continue;
             }
+            if (c.flags & QF_STALLED) throw Error{ISAX_ERR_TIMEOUT, "a bounded wait of the query gave up"};
             c.leaves_scanned = c.leaves_queued;
             if (c.flags & (QF_OVERFLOW | QF_SHORT)) {
                 // this query's candidate window overflowed: answer it alone

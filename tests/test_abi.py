@@ -138,3 +138,19 @@ def test_server_argument_validation(lib):
     assert lib.isax_server_get_info(None, None) == 1
     lib.isax_server_destroy(None)  # no-op
     assert lib.isax_server_clock() > 0
+
+
+def test_failure_check_entry_points_validate_arguments(lib):
+    # rejected before any device work
+    _expect(lib.isax_selftest_wait(2, 0, 10, None), 1, "kind must be")
+    _expect(lib.isax_selftest_wait(0, 0, 0, None), 1, "max_polls")
+    _expect(lib.isax_debug_inject_timeout(-1), 1, "queries must be")
+    assert lib.isax_debug_inject_timeout(0) == 0
+
+
+def test_exact_d2_validates_arguments(lib):
+    q = np.zeros(32, np.float32)
+    i = np.zeros(4, np.int64)
+    d = np.zeros(4, np.float64)
+    _expect(lib.isax_exact_d2(None, q.ctypes.data, 1, 1, 0, i.ctypes.data, d.ctypes.data, None), 1,
+            "index is NULL")
