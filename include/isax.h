@@ -269,7 +269,7 @@ isax_status isax_exact_d2(const isax_index* ix, const float* Q, int32_t B, int32
  * their results are copied out, because two queries running at once on the GPU
  * would race on the shared array.
  * Limits and errors: ISAX_ERR_INVALID_ARG for an index with more than
- * ISAX_NOALLOC_MAX_LEAVES leaves or with leaves + N / 256 above twice that
+ * ISAX_NOALLOC_MAX_LEAVES leaves or with leaves + N / 128 above twice that
  * (and as isax_query_knn); ISAX_ERR_OOM when
  * more than ISAX_NOALLOC_MAX_SURVIVORS series pass the lower bound of the
  * approximate answer, or the query keeps more than ISAX_NOALLOC_MAX_CANDIDATES
@@ -415,6 +415,20 @@ isax_status isax_tc_selftest(const uint16_t* a, const uint16_t* b, int32_t n_col
                              void* cuda_stream);
 
 /* ------------------------------------------------------------ failure checks */
+
+/* 1 if the library was compiled with -DISAX_CHECKS (bounds-checked kernels),
+ * else 0.  The paper has no counterpart. */
+int32_t isax_checks_enabled(void);
+
+/*
+ * isax_check_word - in a bounds-checked build: the invariants that kernels
+ * found violated since the last call, one bit each (row or position outside
+ * the collection, a scan work item longer than a piece or past the end, a
+ * survivor's or candidate's row outside the collection, a leaf range out of
+ * order, ...), then cleared.  0 means every checked access stayed in range.
+ * Always 0 in the normal build.  Call it with no query or build in flight.
+ */
+isax_status isax_check_word(uint32_t* out);
 
 /*
  * isax_selftest_wait - make one of the library's bounded device waits run out

@@ -22,21 +22,31 @@ def _deps():
             [os.path.join(INCLUDE, "isax.h")])
 
 
-def stale():
-    if not os.path.exists(LIB):
+# the bounds-checked variant (-DISAX_CHECKS), built on demand by the tests that use it
+OUT_CHECKS = os.path.join(HERE, "_build_checks")
+LIB_CHECKS = os.path.join(OUT_CHECKS, "libisaxgpu.so")
+
+
+def stale(lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(verbose=False, extra_flags=()):
-    if not stale() and not extra_flags:
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build_checked(verbose=False):
+    """The library with bounds-checked kernels (isax_check_word reports)."""
+    return build(verbose, ("-DISAX_CHECKS",), out=OUT_CHECKS, lib=LIB_CHECKS)
+
+
+def build(verbose=False, extra_flags=(), out=OUT, lib=LIB):
+    if not stale(lib) and (not extra_flags or lib != LIB):
+        return lib
+    os.makedirs(out, exist_ok=True)
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(OUT, src.replace(".cu", ".o"))
+        obj = os.path.join(out, src.replace(".cu", ".o"))
         objs.append(obj)
         cmd = ["nvcc"] + NVCC_FLAGS + list(extra_flags) + ["-I", INCLUDE, "-c",
                                                             os.path.join(CSRC, src), "-o", obj]
@@ -47,13 +57,13 @@ def build(verbose=False, extra_flags=()):
         logs.append(out.decode())
         if p.returncode != 0:
             raise RuntimeError("nvcc failed: %s\n%s" % (" ".join(cmd), out.decode()))
-    link = ["nvcc", GENCODE, "-shared", "-o", LIB] + objs + ["-lcudart"]
+    link = ["nvcc", GENCODE, "-shared", "-o", lib] + objs + ["-lcudart"]
     p = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if p.returncode != 0:
         raise RuntimeError("link failed:\n" + p.stdout.decode())
     if verbose:
         print("".join(logs))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -371,6 +371,21 @@ isax_status isax_query_knn_batch_bf16(const isax_index* cix, const float* Q, int
     });
 }
 
+int32_t isax_checks_enabled(void) {
+#ifdef ISAX_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+isax_status isax_check_word(uint32_t* out) {
+    return guarded([&] {
+        check(out != nullptr, "out is NULL");
+        *out = take_check_word_build() | take_check_word_query();
+    });
+}
+
 isax_status isax_exact_d2(const isax_index* cix, const float* Q, int32_t B, int32_t k, uint32_t mem_flags,
                           const int64_t* idx, double* out_d2, void* cuda_stream) {
     return guarded([&] {

@@ -742,6 +742,7 @@ __global__ void __launch_bounds__(256) permute_sax_kernel(const uint32_t* __rest
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N;
          r += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t src = ids[r];
+        ISAX_CHECK(src < (uint64_t)N, CHK_BUILD_ID);
         sax_out[r] = sax_in[src];
         orig[r] = src;
     }
@@ -798,6 +799,7 @@ __global__ void __launch_bounds__(256) envelope_kernel(const uint4* __restrict__
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t l = gw; l < L; l += nw) {
         const uint32_t b = leaf_begin[l], e = leaf_begin[l + 1];
+        ISAX_CHECK(b < e, CHK_LEAF_RANGE);
         uint4 mn = make_uint4(FULL, FULL, FULL, FULL), mx = make_uint4(0, 0, 0, 0);
         for (uint32_t r = b + lane; r < e; r += 32) {
             uint4 s = sax[r];
@@ -1538,5 +1540,7 @@ void summarize_impl(const float* series, int64_t N, int n, int card, uint32_t me
     ISAX_CUDA_TRY(cudaStreamSynchronize(st));
     if (hm[1]) throw Error{ISAX_ERR_INVALID_ARG, "series contains a non-finite value"};
 }
+
+uint32_t take_check_word_build() { return take_check_word_here(); }
 
 }  // namespace isax

@@ -41,6 +41,45 @@ void set_error(isax_status st, const std::string& msg);
                                                    cudaGetErrorString(e_)};          \
     } while (0)
 
+// ---------------------------------------------------------------- checked build
+// Compiled with -DISAX_CHECKS, kernels verify the invariants their memory
+// accesses rely on (positions and rows inside the collection, list entries
+// inside their capacity, leaf ranges in order) and record a failed one as a bit
+// of a device word (one per translation unit), which isax_check_word() reads
+// and clears.  The access itself goes ahead as in the normal build, where the
+// checks compile to nothing.
+enum : uint32_t {
+    CHK_SCAN_ITEM = 0,     // a scan work item outside the collection or longer than a piece
+    CHK_SCAN_CAND = 1,     // a pass-2 row outside its piece
+    CHK_REFINE_ROW = 2,    // a survivor's row outside the collection
+    CHK_APPROX_RANGE = 3,  // the approximate answer's positions outside the collection
+    CHK_FINAL_ROW = 4,     // a final-ordering candidate's row outside the collection
+    CHK_LEAF_RANGE = 5,    // a leaf whose first position is after its end
+    CHK_BUILD_ID = 6,      // a leaf-order position holding an original row >= N
+    CHK_WORK_COUNT = 7,    // a work list longer than its capacity without the overflow flag
+};
+#ifdef ISAX_CHECKS
+static __device__ unsigned int g_check_word = 0;
+#define ISAX_CHECK(cond, bit)                                              \
+    do {                                                                   \
+        if (!(cond)) atomicOr(&::isax::g_check_word, 1u << (unsigned)(bit)); \
+    } while (0)
+// this translation unit's word, read and cleared
+static inline uint32_t take_check_word_here() {
+    uint32_t v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_check_word, sizeof(v)) != cudaSuccess) return 0xFFFFFFFFu;
+    cudaMemcpyToSymbol(g_check_word, &z, sizeof(z));
+    return v;
+}
+#else
+#define ISAX_CHECK(cond, bit) \
+    do {                      \
+    } while (0)
+static inline uint32_t take_check_word_here() { return 0; }
+#endif
+uint32_t take_check_word_query();  // isax_query.cu
+uint32_t take_check_word_build();  // isax_build.cu
+
 // ---------------------------------------------------------------- tracing
 // Counts a launch; with profiling on, brackets it with CUDA events on `st`.
 class KernelScope {

@@ -34,6 +34,11 @@ __device__ __forceinline__ void st_stream(float4* p, float4 v) {
                  : "memory");
 }
 
+// bring the line holding p into L2 ahead of a later read
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
     return *(volatile const unsigned long long*)p;
 }

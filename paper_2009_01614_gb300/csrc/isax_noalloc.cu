@@ -34,7 +34,7 @@ namespace {
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr uint32_t MAX_LEAVES = ISAX_NOALLOC_MAX_LEAVES;
-constexpr uint32_t MAX_WORK = 2 * MAX_LEAVES;  // scan items: leaves + series / 256
+constexpr uint32_t MAX_WORK = 2 * MAX_LEAVES;  // scan items: leaves + series / 128 (the scan's piece)
 constexpr uint32_t MAX_CAND = ISAX_NOALLOC_MAX_CANDIDATES;
 constexpr uint32_t MAX_SURV = ISAX_NOALLOC_MAX_SURVIVORS;
 
@@ -122,7 +122,7 @@ extern "C" isax_status isax_query_knn_noalloc(const isax_index* cix, const float
             fail(ISAX_ERR_INVALID_ARG,
                  "index has " + std::to_string(cix->d.L) + " leaves and " + std::to_string(cix->d.N) +
                  " series; the allocation-free query supports at most " + std::to_string(MAX_LEAVES) +
-                 " leaves and leaves + series / 256 <= " + std::to_string(MAX_WORK) +
+                 " leaves and leaves + series / 128 <= " + std::to_string(MAX_WORK) +
                  " (use isax_query_knn)");
         isax_index* ix = const_cast<isax_index*>(cix);
         std::lock_guard<std::mutex> lk(g_mu);

@@ -880,6 +880,7 @@ __global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryS
     // approximate answer: the rows of the approximate-answer leaves, FR_ROWS
     // consecutive positions per warp at a time
     const int64_t b = range_s[0], e = range_s[1];
+    ISAX_CHECK(0 <= b && b <= e && e <= ix.N, CHK_APPROX_RANGE);
     constexpr int NQ = NV ? NV : 1;
     float4 qr[NQ];
 #pragma unroll
@@ -993,6 +994,7 @@ __global__ void __launch_bounds__(BIN_THREADS) q_leaf_bin_kernel(DevIndex ix, Qu
 #pragma unroll
         for (int u = 0; u < BIN_LEAVES; ++u) {
             const int64_t l = l0 + u * stride;
+            ISAX_CHECK(l >= L || b[u] < e[u], CHK_LEAF_RANGE);
             const bool q = l < L && !(l >= a0 && l < a1) && lb[u] <= thr;
             bn[u] = q ? bin_of(lb[u], thr) : -1;
             nc[u] = q ? (e[u] - b[u] + LB_PIECE - 1) / LB_PIECE : 0u;
@@ -1225,13 +1227,14 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         if (threadIdx.x < W) qpaa_s[threadIdx.x] = qpv;
         __syncthreads();
         // the byte table: q[i][s] = floor(T[i][s] * 255 / thr), at most 255, with T
-        // the query table's fp32 entry; computed in FP64 with a relative margin
-        // below the exact quotient, so q * thr / 255 <= T.  A row whose units sum
-        // to more than 255 has a true bound >= 256 thr / 255, whose fp32 sum of 16
-        // entries exceeds thr: it would be pruned.  A threshold that is not a
-        // positive finite number gives zeros: every row goes on to the fp32 bound.
+        // the query table's fp32 entry; the scale and the product are rounded
+        // down (and the scale shrunk by 2^-20), so q * thr / 255 <= T.  A row
+        // whose units sum to more than 255 has a true bound >= 256 thr / 255,
+        // whose fp32 sum of 16 entries exceeds thr: it would be pruned.  A
+        // threshold that is not a positive finite number gives zeros: every row
+        // goes on to the fp32 bound.
         const bool scaled = thr > 0.0f && thr < INFINITY;
-        const double inv = scaled ? 255.0 / (double)thr * (1.0 - 1e-9) : 0.0;
+        const float inv = scaled ? __fmul_rd(__fdiv_rd((float)LB_QMAX, thr), 1.0f - 0x1p-20f) : 0.0f;
         uint32_t packed = 0;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
@@ -1240,8 +1243,8 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
             const float lo = bp_s[sym], hi = bp_s[sym + 1], v = qpaa_s[i];
             const float d = v < lo ? lo - v : (v >= hi ? v - hi : 0.0f);
             const float T = (d * d) * mf;
-            const double qd = (double)T * inv;
-            const uint32_t q = qd >= (double)LB_QMAX ? LB_QMAX : (uint32_t)qd;
+            const float qf = __fmul_rd(T, inv);
+            const uint32_t q = qf >= (float)LB_QMAX ? LB_QMAX : (uint32_t)qf;
             packed |= q << (8 * b);
         }
         reinterpret_cast<uint32_t*>(tab8)[threadIdx.x] = packed;
@@ -1257,6 +1260,14 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
     }
     if (threadIdx.x == 0) *next_p = LB_WARPS * LB_STAGES;  // the items after the warps' first ones go by claim
     __syncthreads();
+    // the warp's next item of the CTA into `pend` (claimed in list order)
+    auto claim = [&]() -> bool {
+        uint32_t j = 0;
+        if (lane == 0) j = atomicAdd(next_p, 1u);
+        j = __shfl_sync(FULL, j, 0);
+        if (lane == 0 && j < mine) pend = s.work[cta + (size_t)j * G];
+        return j < mine;
+    };
     const uint32_t tab8_sa = smem_u32(tab8);
     uint8_t* wcand = cand1 + warp * LB_PIECE;
     uint2* buf = bufs + warp * LB_BUF;
@@ -1274,6 +1285,18 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         __syncwarp();
         nbuf = 0;
     };
+    // a kept row: appended to the warp's buffer as {position, bound}
+    auto keep_rows = [&](bool keep, uint32_t pos, float lb) {
+        const unsigned m = __ballot_sync(FULL, keep);
+        // the row id is read when the buffer is appended: start bringing it in
+        if (keep && ix.rows_in_place) prefetch_l2(ix.orig + pos);
+        if (m) {
+            if (nbuf + 32 > LB_BUF) drain();
+            if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = make_uint2(pos, __float_as_uint(lb));
+            nbuf += __popc(m);
+            __syncwarp();
+        }
+    };
     unsigned long long n_lb = 0, n_leaves = 0;
     bool stalled = false;
     uint32_t done = 0;  // warp-uniform, like issued and pend_ok
@@ -1282,11 +1305,7 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
             // the stage of piece `issued` held piece issued - LB_STAGES, already bounded
             if (lane == 0) issue(issued % LB_STAGES, pend);
             ++issued;
-            uint32_t j = 0;
-            if (lane == 0) j = atomicAdd(next_p, 1u);
-            j = __shfl_sync(FULL, j, 0);
-            pend_ok = j < mine;
-            if (lane == 0 && pend_ok) pend = s.work[cta + (size_t)j * G];
+            pend_ok = claim();
         }
         if (done == issued) break;
         const uint32_t st = done % LB_STAGES;
@@ -1296,6 +1315,7 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         }
         const uint2 p = wmeta[st];
         const uint32_t rows = p.y & 0x7FFFFFFFu, pos0 = p.x;
+        ISAX_CHECK(rows <= (uint32_t)LB_PIECE && (uint64_t)pos0 + rows <= (uint64_t)ix.N, CHK_SCAN_ITEM);
         if (lane == 0) {
             n_lb += rows;
             n_leaves += p.y >> 31;
@@ -1307,16 +1327,6 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
             const uint32_t r = j * 32 + lane;
             w[j] = r < rows ? src[r] : make_uint4(0u, 0u, 0u, 0u);
         }
-        // a kept row: appended to the warp's buffer as {position, bound}
-        auto keep_rows = [&](bool keep, uint32_t r, float lb) {
-            const unsigned m = __ballot_sync(FULL, keep);
-            if (m) {
-                if (nbuf + 32 > LB_BUF) drain();
-                if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = make_uint2(pos0 + r, __float_as_uint(lb));
-                nbuf += __popc(m);
-                __syncwarp();
-            }
-        };
         if constexpr (CARD == 256) {
             // pass 1, byte units: the first 8 segments of every row of the lane at
             // once, then per row the rest, 4 segments at a time, while some lane
@@ -1340,20 +1350,22 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
                 if (cand) wcand[ncand + __popc(m & ((1u << lane) - 1u))] = (uint8_t)r;
                 ncand += __popc(m);
             }
-            // pass 2: the fp32 bound of the listed rows, one per lane
+            // pass 2: the fp32 bound of the listed rows (their words are still
+            // in the stage), one per lane
             __syncwarp();
             for (uint32_t c0 = 0; c0 < ncand; c0 += 32) {
                 const bool mine_c = c0 + lane < ncand;
                 const uint32_t r = mine_c ? wcand[c0 + lane] : 0u;
+                ISAX_CHECK(!mine_c || r < rows, CHK_SCAN_CAND);
                 const float lb = mine_c ? lb_exact256(src[r], bp_s, qpaa_s, mf) : INFINITY;
-                keep_rows(mine_c && lb <= thr, r, lb);
+                keep_rows(mine_c && lb <= thr, pos0 + r, lb);
             }
         } else {
 #pragma unroll
             for (int j = 0; j < LB_PER_LANE; ++j) {
                 const uint32_t r = j * 32 + lane;
                 const float lb = series_lb(w[j], tab, card);
-                keep_rows(r < rows && lb <= thr, r, lb);
+                keep_rows(r < rows && lb <= thr, pos0 + r, lb);
             }
         }
         ++done;
@@ -1492,6 +1504,7 @@ __device__ __forceinline__ void q_refine_body(const DevIndex& ix, const QueryScr
         for (int t = 0; t < 4; ++t) {
             e[t] = nx[t];
             if (i + t < total && __uint_as_float(e[t].y) <= thr) keep |= 1u << t;
+            ISAX_CHECK(!(keep & (1u << t)) || e[t].x < (uint64_t)ix.N, CHK_REFINE_ROW);
         }
         const uint32_t in = i + 4 * nw;
 #pragma unroll
@@ -1614,8 +1627,10 @@ __device__ __forceinline__ void q_refine_half_body(const DevIndex& ix, const Que
     refresh();
     take(i, eA, keepA);
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
+    for (int t = 0; t < 4; ++t) {
+        ISAX_CHECK(!(keepA & (1u << t)) || eA[t].x < (uint64_t)ix.N, CHK_REFINE_ROW);
         if (keepA & (1u << t)) hA[t] = ld_stream(x4 + (int64_t)eA[t].x * 64 + lane);
+    }
     while (i < total) {
         // partial distances of the quad's first halves
         float a[4];
@@ -1644,6 +1659,7 @@ __device__ __forceinline__ void q_refine_half_body(const DevIndex& ix, const Que
         float4 sA[4], hB[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
+            ISAX_CHECK(!(keepB & (1u << t)) || eB[t].x < (uint64_t)ix.N, CHK_REFINE_ROW);
             if (keep2 & (1u << t)) sA[t] = ld_stream(x4 + (int64_t)eA[t].x * 64 + 32 + lane);
             if (keepB & (1u << t)) hB[t] = ld_stream(x4 + (int64_t)eB[t].x * 64 + lane);
         }
@@ -1799,6 +1815,7 @@ __device__ __forceinline__ void q_finalize_body(const DevIndex& ix, const QueryS
                 if (p < FIN_THREADS) {
                     stage[p] = s.cand_pos[i];
                     stage_key[p] = key[u];
+                    ISAX_CHECK(stage[p] < (uint64_t)ix.N, CHK_FINAL_ROW);
                 }
             }
         }
@@ -2956,5 +2973,7 @@ void launch_bq_finalize(isax_index* ix, const QueryScratch* ss, int B, int k, cu
     bq_finalize_kernel<<<dim3(1, B), FIN_THREADS, 0, st>>>(ix->d, ss, k);
     ISAX_CUDA_TRY(cudaGetLastError());
 }
+
+uint32_t take_check_word_query() { return take_check_word_here(); }
 
 }  // namespace isax
