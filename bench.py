@@ -949,27 +949,38 @@ def main():
 
     from paper_2009_01614_gb300 import shard
 
+    # every query goes through the C entry point with device buffers made once
+    # (the per-call tensor allocations of the Python wrapper are not the query's cost)
+    out_i = torch.empty((a.queries, k), dtype=torch.int64, device="cuda")
+    out_d = torch.empty((a.queries, k), dtype=torch.float32, device="cuda")
+    qstats = (pkg.QueryStats * a.queries)()
+    dev_flags = pkg.MEM_INPUT_DEVICE | pkg.MEM_OUTPUT_DEVICE
+    q_ptr = [Qd[b].data_ptr() for b in range(a.queries)]
+    i_ptr = [out_i[b].data_ptr() for b in range(a.queries)]
+    d_ptr = [out_d[b].data_ptr() for b in range(a.queries)]
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(a.queries)]
+
     def step(record, rows=a.rows):
         ix = pkg.Index(X, cardinality=256, leaf_size=a.leaf, stream=sp, rows_in_place=rows == "in-place")
-        res_i, res_d = [], []
+        h = ix.handle
         for b in range(a.queries):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
+            e0, e1 = events[b]
             e0.record(stream)
-            i, d, st = ix.query(Qd[b], k, stats=True, stream=sp)
+            pkg.isax_query_knn(h, q_ptr[b], k, dev_flags, i_ptr[b], d_ptr[b], qstats[b], sp)
             e1.record(stream)
-            if record:
-                e1.synchronize()
-                lat_ms.append(e0.elapsed_time(e1))
+        if record:
+            torch.cuda.synchronize()
+            for b in range(a.queries):
+                lat_ms.append(events[b][0].elapsed_time(events[b][1]))
+                st = qstats[b].as_dict()
                 for key in stats_acc:
                     stats_acc[key] += st[key]
-            res_i.append(i)
-            res_d.append(d)
-        last = (res_i[-1], res_d[-1])
+        last = (out_i[-1], out_d[-1])
         if dist is not None:
             # row shards: the FP64 squared distances of this shard's answers, one
             # all-gather of every query's k triples, the exact merge
-            I, D = torch.stack(res_i), torch.stack(res_d)
+            I, D = out_i, out_d
             D2 = ix.exact_d2(Qd, I, stream=sp)
             gi, gd, _ = shard.gather_merge(I.cpu().numpy(), D.cpu().numpy(), D2.cpu().numpy(), k, rank * N,
                                            world, device=torch.device("cuda", local))
@@ -1116,6 +1127,21 @@ def main():
 
         for _ in range(max(1, min(a.warmup, 2))):
             step_e2e()
+        # the CPU-GPU link's copy rate from this page-locked buffer (a slice of
+        # up to 4 GiB, three copies timed with CUDA events), untimed, to read the
+        # step time against
+        rows_probe = min(N, (1 << 30) // n)
+        dst = torch.empty((rows_probe, n), dtype=torch.float32, device="cuda")
+        dst.copy_(Xh[:rows_probe], non_blocking=True)
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record()
+        for _ in range(3):
+            dst.copy_(Xh[:rows_probe], non_blocking=True)
+        h1.record()
+        torch.cuda.synchronize()
+        h2d_gbs = 3 * rows_probe * n * 4 / (h0.elapsed_time(h1) * 1e-3) / 1e9
+        del dst
+        torch.cuda.empty_cache()
         barrier()
         t0 = time.perf_counter()
         marks = []
@@ -1128,7 +1154,9 @@ def main():
         out["e2e"] = {"value": total_queries / e2e_s, "unit": UNIT,
                       "h2d_bytes_per_step": N * n * 4 + a.queries * n * 4,
                       "d2h_bytes_per_step": a.queries * k * (8 + 4),
-                      "ms_per_step": e2e_s / a.steps * 1e3, "step_ms": step_ms}
+                      "ms_per_step": e2e_s / a.steps * 1e3, "step_ms": step_ms,
+                      "h2d_GB_per_s": round(h2d_gbs, 1),
+                      "h2d_ms_per_step_at_that_rate": round((N * n * 4 + a.queries * n * 4) / h2d_gbs / 1e6, 1)}
         del Xh, Qp, Qp_np, Xh_np
     else:
         del X, Qd
