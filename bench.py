@@ -20,9 +20,10 @@ queries / wall time of the timed steps, builds included); `e2e` = the same job
 through the C ABI with host buffers (the 102.4 GB collection copied from pinned
 host memory by every build, queries and answers through host memory);
 `roofline` = the dominant kernel's algorithmic bytes per launch / its mean
-CUDA-event duration; `scan_roofline` = the same for the lower-bound scan
-(16 B per series bounded; MESSI queries here, the ParIS flat scan and MESSI on
-an ADS+ balanced-split index under `ablation_flat_scan`); `query_roofline` = a
+CUDA-event duration; `scan_roofline` = the same for a single query's
+lower-bound scan and refinement, one launch (16 B per series bounded + 4 B
+per row value refined; MESSI queries here, the ParIS flat scan under
+`ablation_flat_scan`); `query_roofline` = a
 whole query's algorithmic bytes (leaf envelopes, SAX words bounded, rows
 refined) over its mean latency; `cpu_baseline` = the CPU oracle's FP64 brute
 force on a sample of the same workload.  `--impl reference` times that oracle
@@ -205,9 +206,10 @@ def kernel_bytes(name, a, launches, acc):
     """Algorithmic bytes of all timed launches of a kernel (None if not modelled).
     Build kernels run once per step (rs_* once per radix pass); the query
     kernels' bytes come from the per-query counters: 16 B per SAX word bounded
-    (q_series_lb), one full row per series refined outside the approximate leaf
-    (q_refine; an upper bound: early abandoning reads less), one row per series
-    of the approximate leaf (q_approx)."""
+    plus 4 B per row value the refinement read outside the approximate answer
+    (q_scan_refine: the scan and the refinement in one launch; an abandoned row
+    counts the part read), the leaf envelopes and the approximate answer's rows
+    (q_front)."""
     N, n = a.N, a.n
     row = 4 * n
     per_launch = {
@@ -219,17 +221,13 @@ def kernel_bytes(name, a, launches, acc):
     }
     if name in per_launch:
         return per_launch[name] * launches
-    if name == "q_series_lb":
-        return 16 * acc["series_lb"]
-    if name == "q_refine":
-        # the row floats actually read outside the approximate answer (early
-        # abandoning stops a row before its end)
-        return 4 * (acc["ed_floats"] - n * acc["approx_series"])
+    if name == "q_scan_refine":
+        # SAX words bounded, and the row floats actually read outside the
+        # approximate answer (early abandoning stops a row before its end)
+        return 16 * acc["series_lb"] + 4 * (acc["ed_floats"] - n * acc["approx_series"])
     if name == "q_front":
         # every leaf's envelope and the approximate answer's rows
         return 32 * acc["leaves_total"] + row * acc["approx_series"]
-    if name == "q_approx":
-        return row * acc["approx_series"]
     return None
 
 
@@ -255,6 +253,9 @@ def kernel_source_hash(kernel):
     header."""
     import re
     kernel = {"summarize": "summarize_vec"}.get(kernel, kernel)  # launch name -> kernel name
+    # a kernel whose device body carries another name (the scan's body, whose
+    # refinement step it calls, is hashed with that step below)
+    body_name = {"q_scan_refine": "q_series_lb"}.get(kernel, kernel)
     src = os.path.join(ROOT, "paper_2009_01614_gb300", "csrc")
     own = ("isax_query.cu" if kernel.startswith(("q_", "bq_")) else
            "isax_tc.cu" if kernel.startswith("tc_") else "isax_build.cu")
@@ -275,7 +276,9 @@ def kernel_source_hash(kernel):
     if body is None:
         raise KeyError("no __global__ definition of %s_kernel in %s" % (kernel, own))
     # a kernel that wraps a device body (shared with its batched form) is hashed with it
-    inner = definition(r"__device__[^;{]*?\b%s_body\s*\(" % re.escape(kernel))
+    inner = definition(r"__device__[^;{]*?\b%s_body\s*\(" % re.escape(body_name))
+    if kernel == "q_scan_refine":
+        inner = (inner or "") + (definition(r"__device__[^;{]*?\bq_refine_claimed\s*\(") or "")
     h = hashlib.sha256(body.encode() + (inner or "").encode())
     h.update(open(os.path.join(src, "isax_kernels_util.cuh"), "rb").read())
     return h.hexdigest()[:16]
@@ -300,18 +303,23 @@ def traffic_from_profile(kernel, label=None):
     return None
 
 
-def scan_roofline(prof, series_lb_total, hbm, workload):
-    """The lower-bound scan's HBM fraction: 16 B per series bounded over the
-    traced launches / their summed CUDA-event time (events around each launch:
-    a little above the kernel's own duration)."""
-    if "q_series_lb" not in prof:
+def scan_roofline(prof, series_lb_total, refined_floats_total, hbm, workload):
+    """The HBM fraction of a single query's lower-bound scan and refinement
+    (one launch, q_scan_refine): 16 B per series bounded + 4 B per row value
+    the refinement read outside the approximate answer, over the traced
+    launches / their summed CUDA-event time (events around each launch: a
+    little above the kernel's own duration)."""
+    if "q_scan_refine" not in prof:
         return None
-    cnt, ms = prof["q_series_lb"]
-    per_launch = 16 * series_lb_total / cnt
+    cnt, ms = prof["q_scan_refine"]
+    sax = 16 * series_lb_total / cnt
+    rows = 4 * refined_floats_total / cnt
+    per_launch = sax + rows
     achieved = per_launch / (ms / cnt / 1e3) / 1e9
-    tr = traffic_from_profile("q_series_lb", "q_series_lb:" + workload)
-    return {"kernel": "q_series_lb", "bound": "hbm", "launches": cnt, "avg_launch_ms": ms / cnt,
-            "algorithmic_bytes_per_launch": per_launch, "achieved": achieved, "peak": hbm,
+    tr = traffic_from_profile("q_scan_refine", "q_scan_refine:" + workload)
+    return {"kernel": "q_scan_refine", "bound": "hbm", "launches": cnt, "avg_launch_ms": ms / cnt,
+            "algorithmic_bytes_per_launch": per_launch, "sax_bytes_per_launch": sax,
+            "row_bytes_per_launch": rows, "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm,
             "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None}
 
@@ -364,7 +372,8 @@ def ablation_leg(a, X, Qd, pkg, torch, stream):
         torch.cuda.synchronize()
         pkg.isax_profile(0)
         out[mode]["scan_roofline"] = scan_roofline(
-            pkg.isax_profile_report(), sum(s["series_lb"] for s in st_all), peaks()[0],
+            pkg.isax_profile_report(), sum(s["series_lb"] for s in st_all),
+            sum(s["ed_floats"] - a.n * s["approx_series"] for s in st_all), peaks()[0],
             "%s_%dMx%d" % (mode, a.N // 1000000, a.n))
     out["same_answers"] = all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
                               for x, y in zip(answers["messi"], answers["flat"]))
@@ -1097,7 +1106,8 @@ def main():
         "ablation_flat_scan": ablation,
         "rows_in_host_memory": None,
         "kernels": kernels,
-        "scan_roofline": scan_roofline(qprof, stats_acc["series_lb"] / a.steps, hbm,
+        "scan_roofline": scan_roofline(qprof, stats_acc["series_lb"] / a.steps,
+                                       (stats_acc["ed_floats"] - n * stats_acc["approx_series"]) / a.steps, hbm,
                                        "messi_%dMx%d" % (a.N // 1000000, a.n)),
         "query_roofline": query_roofline(stats_acc, len(lat_ms), info["leaves"], n, q_time_ms, hbm),
         "gpu_launches": launches,

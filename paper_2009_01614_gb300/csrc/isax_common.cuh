@@ -159,6 +159,11 @@ struct QCtl {
     double delta;          // relative error bound of an fp32 squared distance
     unsigned long long series_lb, series_refined, leaves_scanned, leaves_queued, approx_series;
     unsigned long long ed_floats;  // row floats read by the refinement (abandoned rows: the chunks read)
+    uint32_t scan_done;    // scan CTAs whose survivors are all in the list
+    uint32_t pad1;
+    // fp32 factors of the pruning limits, each rounded up from its FP64 value:
+    // 1 + 5 delta, 1 + 8 delta, 1 + 3 delta, E, (1 + 24 u)(1 + 1e-12)
+    float f_lb, f_ab, f_win, f_E, f_sq, pad2[3];
 };
 
 enum : uint32_t {
@@ -182,7 +187,9 @@ struct QueryScratch {
     unsigned long long* cand_key;  // [cap]
     uint32_t* cand_pos;            // [cap]
     uint32_t cand_cap;
-    uint2* surv;                   // [surv_cap] series that passed the bound: {row of x, bound bits}
+    uint2* surv;                   // [surv_cap] series that passed the bound: {row of x + 1, bound
+                                   // bits}; a slot with .x == 0 is empty (slots start empty, and
+                                   // the refinement of a single query empties each one it takes)
     uint32_t surv_cap;
     QCtl* ctl;
     int64_t* out_idx;              // [MAX_K]
@@ -245,6 +252,7 @@ void alloc_query_scratch_for(int64_t L, int64_t N, int n, int card, uint32_t can
                              QueryScratch& q, cudaStream_t st);
 void grow_query_candidates(QueryScratch& q, uint32_t cand_cap, cudaStream_t st);
 void grow_query_survivors(QueryScratch& q, uint32_t surv_cap, cudaStream_t st);
+void empty_survivors(const QueryScratch& q, cudaStream_t st);
 void free_query_scratch_struct(QueryScratch& q, cudaStream_t st);
 void* query_graphs_new();
 void query_graphs_delete(void* g);

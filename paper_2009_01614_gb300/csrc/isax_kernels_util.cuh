@@ -45,6 +45,11 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
     return *(volatile const uint32_t*)p;
 }
+__device__ __forceinline__ uint2 ld_volatile_u2(const uint2* p) {
+    uint2 v;
+    asm volatile("ld.volatile.global.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
 
 // packed (fp32 value bits << 32 | id): for non-negative values the integer
 // order is the (value, id) order

@@ -145,7 +145,11 @@ extern "C" isax_status isax_query_knn_noalloc(const isax_index* cix, const float
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         c.flags |= injected_query_flags();
         if (c.flags & QF_NONFINITE) fail(ISAX_ERR_INVALID_ARG, "query contains a non-finite value");
-        if (c.flags & QF_STALLED) fail(ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed");
+        if (c.flags & QF_STALLED) {
+            empty_survivors(s, st);
+            ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+            fail(ISAX_ERR_TIMEOUT, "a bounded wait of the query gave up");
+        }
         if (c.flags & QF_OVERFLOW)
             fail(ISAX_ERR_OOM, c.surv_count > MAX_SURV
                  ? "more than " + std::to_string(MAX_SURV) + " series passed the lower bound: the "

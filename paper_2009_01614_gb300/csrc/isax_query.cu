@@ -1,27 +1,28 @@
 // isax_query.cu - exact k-NN query answering on the GPU, following MESSI's
 // query strategy (Section III, MESSI Approach; lower-bound and real-distance
-// calculations are its two hot loops):
+// calculations are its two hot loops).  A single query is four launches:
 //
-//   q_prep        query PAA, SAX symbols and key; the lower-bound table
+//   q_front       query PAA, SAX symbols and key; the lower-bound table
 //                 T[i][s] = (n/w) dist(qpaa_i, region s)^2 in fp32; the leaf the
-//                 query's key descends to (the approximate-answer leaf).
-//   q_approx      real distances to every series of that leaf -> first BSF.
-//   q_leaf_lb     envelope lower bound of every leaf; leaves that the BSF does
-//                 not prune are counted into bins of bound / BSF.
-//   q_leaf_scatter  the unpruned leaves listed bin by bin: a work list in
-//                 ascending lower-bound order (MESSI's priority queues).
-//   q_series_lb   the queued leaves' pieces (at most 256 rows) dealt to the
-//                 warps in that order; each warp streams its pieces' 16-byte
-//                 SAX words through a ring of shared-memory stages filled by
-//                 bulk copies and bounds them against the table in shared
-//                 memory; survivors {row of x, bound} are appended with warp
-//                 ballots.
-//   q_refine      warps take the survivors in that order, skip those whose
-//                 bound now exceeds the k-th best, and compute real distances
-//                 (early abandoning for long series); the k best so far live in
-//                 a sorted array updated by an atomicMin cascade.
+//                 query's key descends to and the real distances of its rows
+//                 (the approximate answer: the first BSF); the envelope lower
+//                 bound of every leaf.
+//   q_leaf_bin    the leaves the BSF does not prune, counted into bins of
+//                 bound / BSF and listed bin by bin: a work list of leaf pieces
+//                 in ascending lower-bound order (MESSI's priority queues).
+//   q_scan_refine the pieces dealt to the warps in that order; each warp streams
+//                 its pieces' 16-byte SAX words through a ring of shared-memory
+//                 stages filled by bulk copies and bounds them against the table
+//                 in shared memory; survivors {row of x, bound} go to a list.
+//                 Warps with no piece left take survivors from the list, skip
+//                 those whose bound now exceeds the k-th best and compute real
+//                 distances; the k best so far live in a sorted array updated
+//                 by an atomicMin cascade.
 //   q_finalize    candidates within fp32 error of the k-th best re-ranked in
 //                 FP64 (ties by lower row), distances rounded to fp32.
+//
+// Batches of queries (bq_*) run the same steps with the scan and the
+// refinement as separate launches over all queries of a chunk.
 //
 // Rows.  The rows are either copied into leaf order by the build (row of x =
 // leaf-order position) or read in the caller's array, where each leaf refers
@@ -92,6 +93,36 @@ __device__ void consider(const QueryScratch& s, int k, unsigned long long key, u
 __device__ __forceinline__ float abandon_limit(unsigned long long kth, double delta) {
     if (kth == EMPTY_SLOT) return INFINITY;
     return __double2float_ru((double)key_d2(kth) * (1.0 + 8.0 * delta));
+}
+
+// The fp32 factors of the limits below, each rounded up from its FP64 value
+// (written once per query with the control block).
+__device__ __forceinline__ void set_limit_factors(QCtl* c, double delta, double E) {
+    c->f_lb = __double2float_ru(1.0 + 5.0 * delta);
+    c->f_ab = __double2float_ru(1.0 + 8.0 * delta);
+    c->f_win = __double2float_ru(1.0 + 3.0 * delta);
+    c->f_E = __double2float_ru(E);
+    c->f_sq = __double2float_ru((1.0 + 24.0 * 0x1p-24) * (1.0 + 1e-12));
+}
+
+// A k-th best's three limits in fp32, every operation rounded up from values
+// that are themselves upper bounds, so each is at least the FP64 expression it
+// stands for: thr >= lb_threshold (a bound above it is pruned), lim >=
+// abandon_limit (a partial distance above it is abandoned), win >= the
+// candidate window (1 + 3 delta) k-th best.  Larger limits prune, abandon and
+// drop less, so the answer stays exact; FP64 arithmetic in every refining warp
+// would load the GPU's few FP64 units.
+__device__ __forceinline__ void limits_f32(const QCtl* c, unsigned long long kth, float& thr, float& lim,
+                                           float& win) {
+    if (kth == EMPTY_SLOT) {
+        thr = lim = win = INFINITY;
+        return;
+    }
+    const float t = key_d2(kth);
+    const float r = __fadd_ru(__fsqrt_ru(__fmul_ru(t, c->f_lb)), c->f_E);
+    thr = __fmul_ru(__fmul_ru(r, r), c->f_sq);
+    lim = __fmul_ru(t, c->f_ab);
+    win = __fmul_ru(t, c->f_win);
 }
 
 // squared distance of a row to the query, one warp, fixed order: every lane
@@ -368,6 +399,7 @@ __device__ __forceinline__ void q_prep_body(const DevIndex& ix, const QueryScrat
         c->cand_count = 0;
         c->cand_base = 0;
         c->surv_count = 0;
+        c->scan_done = 0;
         c->window = 0;
         c->flags = bad ? QF_NONFINITE : 0u;
         c->thr_lb0 = INFINITY;
@@ -376,6 +408,7 @@ __device__ __forceinline__ void q_prep_body(const DevIndex& ix, const QueryScrat
         const double eps_q = 1.01 * (m + 1) * u * (double)qmax;
         c->E = sqrt((double)n) * (eps_x + eps_q) * (1.0 + 1e-9);
         c->delta = (double)((n + 31) / 32 + 16) * u;
+        set_limit_factors(c, c->delta, c->E);
         c->series_lb = 0;
         c->series_refined = 0;
         c->ed_floats = 0;
@@ -856,6 +889,7 @@ __global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryS
             c->approx_end = (int32_t)a1;
             c->work_count = 0;
             c->surv_count = 0;
+            c->scan_done = 0;
             c->window = 0;
             c->flags = bad ? QF_NONFINITE : 0u;
             c->thr_lb0 = INFINITY;
@@ -865,6 +899,7 @@ __global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryS
             const double eps_q = 1.01 * (m + 1) * u * (double)qmax;
             c->E = sqrt((double)n) * (eps_x + eps_q) * (1.0 + 1e-9);
             c->delta = (double)((n + 31) / 32 + 16) * u;
+            set_limit_factors(c, c->delta, c->E);
             c->series_lb = 0;
             c->ed_floats = (unsigned long long)tot * (unsigned long long)n;  // the approximate rows, read whole
             c->leaves_scanned = 0;
@@ -886,7 +921,6 @@ __global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryS
 #pragma unroll
     for (int p = 0; p < NQ; ++p)
         qr[p] = NV ? reinterpret_cast<const float4*>(qv)[p * 32 + lane] : make_float4(0, 0, 0, 0);
-    const double delta = (double)((n + 31) / 32 + 16) * 0x1p-24;
     const int64_t gw = (int64_t)blockIdx.x * FR_WARPS + warp, nw = (int64_t)gridDim.x * FR_WARPS;
     unsigned long long refined = 0;
     for (int64_t p0 = b + gw * FR_ROWS; p0 < e; p0 += nw * FR_ROWS) {
@@ -1067,6 +1101,256 @@ __global__ void __launch_bounds__(BIN_THREADS) q_leaf_bin_kernel(DevIndex ix, Qu
     }
 }
 
+// ---------------------------------------------------------------- refinement inside the scan
+// MESSI's workers compute a series' real distance as soon as its lower bound
+// falls below the BSF, in the same pass over the queued leaves (Section III).
+// Here the scan warps publish their survivors into the list as the separate
+// refinement would read them, and a warp with no piece left turns to refining.
+// The list is cut into chunks of RQ_CHUNK slots dealt to the CTAs in turn
+// (chunk j to CTA j mod G); a CTA's warps take its slots RQ_UNIT at a time from
+// a shared-memory counter, and wait (bounded) until each slot is filled, or the
+// scan is over in every CTA and the slot lies past the last survivor.  Each
+// slot taken goes back empty, so the list starts the next query empty.  A
+// survivor whose bound exceeds the threshold of the current k-th best is
+// skipped without reading its row; the others get the fp32 distance of the
+// separate refinement (the same order of sums).
+constexpr uint32_t RQ_WAIT = 1u << 21;      // polls of one slot before the wait gives up
+constexpr uint32_t RQ_CHUNK = 64;           // list slots per chunk
+constexpr uint32_t RQ_UNIT = 8;             // slots a warp takes at once
+constexpr uint32_t RQ_ROW = 1024;           // bytes of a row of n = 256
+constexpr uint32_t RQ_BAR_WAIT = 1u << 22;  // bounded wait on a staged row copy
+constexpr int RQ_DEPTH = 3;                 // pairs of rows in flight per warp (n = 256)
+
+// squared distance of a row to the query (n = 128 * nv, query read through
+// the read-only cache): warp_d2_vec's order and early abandon
+__device__ __forceinline__ float warp_d2_v4q(const float4* __restrict__ xr, const float4* __restrict__ q, int nv,
+                                             float abandon, bool& abandoned, int& nread) {
+    const int lane = threadIdx.x & 31;
+    float acc = 0.0f;
+    abandoned = false;
+    nread = nv * 128;
+    for (int p = 0; p < nv; p += 2) {
+        const bool two = p + 1 < nv;
+        const float4 v0 = ld_stream(xr + p * 32 + lane);
+        const float4 v1 = two ? ld_stream(xr + (p + 1) * 32 + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 q0 = __ldg(q + p * 32 + lane);
+        float d;
+        d = v0.x - q0.x; acc = fmaf(d, d, acc);
+        d = v0.y - q0.y; acc = fmaf(d, d, acc);
+        d = v0.z - q0.z; acc = fmaf(d, d, acc);
+        d = v0.w - q0.w; acc = fmaf(d, d, acc);
+        if (two) {
+            const float4 q1 = __ldg(q + (p + 1) * 32 + lane);
+            d = v1.x - q1.x; acc = fmaf(d, d, acc);
+            d = v1.y - q1.y; acc = fmaf(d, d, acc);
+            d = v1.z - q1.z; acc = fmaf(d, d, acc);
+            d = v1.w - q1.w; acc = fmaf(d, d, acc);
+        }
+        if (p + 2 < nv) {
+            const float part = warp_sum_f(acc);
+            if (part > abandon) {
+                abandoned = true;
+                nread = (p + 2) * 128;
+                return part;
+            }
+        }
+    }
+    return warp_sum_f(acc);
+}
+
+// The refining phase of one warp of CTA `cta` of G.  fz: the CTA's shared
+// words [the scan is over everywhere, polling token, units taken].  A warp
+// takes RQ_UNIT slots at a time (one lane each); their kept rows queue in the
+// lanes and are refined in turn.  HALF (n = 256, rows in device memory): each
+// pair of rows is staged whole in the warp's own copy ring (free once its scan
+// is done: wbuf, 6 KB = RQ_DEPTH buffers of two rows, with its barriers wbar,
+// whose next waits have the parities in the bits of `par`) by bulk copies,
+// RQ_DEPTH pairs in flight.
+template <bool HALF>
+__device__ __forceinline__ void q_refine_claimed(const DevIndex& ix, const QueryScratch& s, int k, uint32_t cta,
+                                                 uint32_t G, uint32_t* fz, unsigned char* wbuf, uint64_t* wbar,
+                                                 uint32_t par) {
+    QCtl* c = s.ctl;
+    const int lane = threadIdx.x & 31;
+    const uint64_t cap = s.surv_cap;
+    const float4* q4 = reinterpret_cast<const float4*>(s.q);  // read through the read-only cache
+    unsigned long long kth = 0ull;
+    float thr = INFINITY, lim = INFINITY, win = INFINITY;
+    unsigned long long n_ref = 0, n_floats = 0;
+    float my_d2 = INFINITY;
+    uint32_t my_pos = 0;
+    int nb = 0;
+    auto flush = [&]() {
+        if (nb == 0) return;
+        if (lane < nb && my_d2 <= win) consider(s, k, pack_key(my_d2, id_of_row(ix, my_pos)), my_pos, c->delta);
+        __syncwarp();
+        nb = 0;
+    };
+    auto push = [&](float d2, uint32_t r) {
+        if (lane == nb) {
+            my_d2 = d2;
+            my_pos = r;
+        }
+        ++nb;
+        if (nb == SR_BATCH) flush();
+    };
+    bool stalled = false;
+    bool end = false;    // no later slot of this CTA can be filled
+    uint32_t qrow = 0;   // lane t < RQ_UNIT: the row of the unit's slot t
+    unsigned qm = 0;     // the unit's slots still to refine (warp-uniform)
+    // the CTA's next unit of slots: lane t < RQ_UNIT waits for its slot (none:
+    // past the list's end), empties it, and keeps its row unless the bound of
+    // the current k-th best skips it
+    auto take = [&]() {
+        uint32_t p = 0;
+        if (lane == 0) p = atomicAdd(&fz[2], 1u);
+        p = __shfl_sync(FULL, p, 0);
+        const uint64_t i0 = ((uint64_t)(p / (RQ_CHUNK / RQ_UNIT)) * G + cta) * RQ_CHUNK +
+                            (uint64_t)RQ_UNIT * (p % (RQ_CHUNK / RQ_UNIT));
+        unsigned long long kt = 0;
+        if (lane == RQ_UNIT) kt = ld_volatile_u64(&s.topk[k - 1]);  // read alongside the slots
+        uint2 e = make_uint2(0u, 0u);
+        bool none = true;
+        if (lane < RQ_UNIT) {
+            const uint64_t i = i0 + (uint64_t)lane;
+            none = i >= cap;  // past the list's room: never filled (the overflow rerun answers)
+            uint32_t nap = 64;
+            for (uint32_t poll = 0; !none; ++poll) {
+                e = ld_volatile_u2(&s.surv[i]);
+                if (e.x) break;
+                if (*(volatile uint32_t*)&fz[0]) {
+                    // the scan is over everywhere: every survivor is in the list
+                    __threadfence();
+                    e = ld_volatile_u2(&s.surv[i]);
+                    if (e.x) break;
+                    none = true;
+                    if (i < (uint64_t)ld_volatile_u32(&c->surv_count)) stalled = true;  // a counted slot left empty
+                    break;
+                }
+                if (poll >= RQ_WAIT) {
+                    stalled = true;
+                    none = true;
+                    break;
+                }
+                // one thread of the CTA at a time looks at the scan's end
+                if (atomicCAS(&fz[1], 0u, 1u) == 0u) {
+                    if (ld_acquire_u32(&c->scan_done) >= G) {
+                        __threadfence_block();
+                        *(volatile uint32_t*)&fz[0] = 1u;
+                    }
+                    atomicExch(&fz[1], 0u);
+                }
+                __nanosleep(nap);
+                if (nap < 1024u) nap <<= 1;
+            }
+            if (!none) s.surv[i] = make_uint2(0u, 0u);  // back empty for the next query
+        }
+        end = __any_sync(FULL, (lane < RQ_UNIT && none) || stalled);
+        kt = __shfl_sync(FULL, kt, RQ_UNIT);
+        if (kt != kth || kth == 0ull) {
+            kth = kt;
+            limits_f32(c, kt, thr, lim, win);
+        }
+        qrow = e.x - 1u;
+        qm = __ballot_sync(FULL, lane < RQ_UNIT && !none && __uint_as_float(e.y) <= thr);
+    };
+    // the next row to refine (mask bit t of the unit, row in lane t), taking
+    // units until one has a kept row or the list ends; false when none is left
+    auto next_row = [&](uint32_t& r) -> bool {
+        while (qm == 0u && !end) take();
+        if (qm == 0u) return false;
+        const int t = __ffs(qm) - 1;
+        qm &= qm - 1u;
+        r = __shfl_sync(FULL, qrow, t);
+        ISAX_CHECK(r < (uint64_t)ix.N, CHK_REFINE_ROW);
+        return true;
+    };
+    if constexpr (HALF) {
+        const unsigned char* xb = reinterpret_cast<const unsigned char*>(ix.x);
+        uint32_t pr0[RQ_DEPTH], pr1[RQ_DEPTH];  // each buffer's rows
+        unsigned pm[RQ_DEPTH];                   // and which of the two it holds
+        uint32_t pending = 0;                    // buffers whose copies are not yet waited for
+        // the next (up to) two rows into buffer b, copied whole
+        auto fill = [&](int b) {
+            pm[b] = 0u;
+            if (next_row(pr0[b])) pm[b] |= 1u;
+            if (next_row(pr1[b])) pm[b] |= 2u;
+            if (!pm[b]) return;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&wbar[b], (uint32_t)__popc(pm[b]) * RQ_ROW);
+                if (pm[b] & 1u) bulk_load(wbuf + b * 2 * RQ_ROW, xb + (int64_t)pr0[b] * RQ_ROW, RQ_ROW, &wbar[b]);
+                if (pm[b] & 2u)
+                    bulk_load(wbuf + b * 2 * RQ_ROW + RQ_ROW, xb + (int64_t)pr1[b] * RQ_ROW, RQ_ROW, &wbar[b]);
+            }
+            pending |= 1u << b;
+        };
+#pragma unroll
+        for (int b = 0; b < RQ_DEPTH; ++b) fill(b);
+        // buffers in turn (the order they were filled in), each refilled once done
+        while (pending && !stalled) {
+#pragma unroll
+            for (int b = 0; b < RQ_DEPTH; ++b) {
+                if (!(pending & (1u << b)) || stalled) continue;
+                if (!__all_sync(FULL, mbar_wait_bounded(&wbar[b], (par >> b) & 1u, RQ_BAR_WAIT))) {
+                    stalled = true;
+                    continue;
+                }
+                par ^= 1u << b;
+                pending &= ~(1u << b);
+                // the distances of the buffer's rows: every lane its two float4
+                // of each row (the first half's, then the second half's), then
+                // the butterfly, as warp_d2_vec<2>
+                const float4 q0 = __ldg(q4 + lane), q1 = __ldg(q4 + 32 + lane);
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    if (!(pm[b] & (1u << t))) continue;
+                    const float4* row = reinterpret_cast<const float4*>(wbuf + b * 2 * RQ_ROW + t * RQ_ROW);
+                    const float4 v0 = row[lane], v1 = row[32 + lane];
+                    float a = 0.0f, d;
+                    d = v0.x - q0.x; a = fmaf(d, d, a);
+                    d = v0.y - q0.y; a = fmaf(d, d, a);
+                    d = v0.z - q0.z; a = fmaf(d, d, a);
+                    d = v0.w - q0.w; a = fmaf(d, d, a);
+                    d = v1.x - q1.x; a = fmaf(d, d, a);
+                    d = v1.y - q1.y; a = fmaf(d, d, a);
+                    d = v1.z - q1.z; a = fmaf(d, d, a);
+                    d = v1.w - q1.w; a = fmaf(d, d, a);
+                    ++n_ref;
+                    n_floats += 256;
+                    push(warp_sum_f(a), t ? pr1[b] : pr0[b]);
+                }
+                __syncwarp();  // every lane is done with the buffer before it is refilled
+                fill(b);
+            }
+        }
+        // after a wait that gave up: the copies still in flight land before the
+        // ring is left (bounded)
+        if (lane == 0)
+            for (int t = 0; t < RQ_DEPTH; ++t)
+                if (pending & (1u << t)) mbar_wait_bounded(&wbar[t], (par >> t) & 1u, RQ_BAR_WAIT);
+        __syncwarp();
+    } else {
+        const float4* x4 = reinterpret_cast<const float4*>(ix.x);
+        const bool vec = ix.n % 128 == 0;
+        uint32_t r;
+        while (!stalled && next_row(r)) {
+            bool ab;
+            int nread;
+            const float d2 = vec ? warp_d2_v4q(x4 + (int64_t)r * (ix.n / 4), q4, ix.n / 128, lim, ab, nread)
+                                 : warp_d2_gen(ix.x + (int64_t)r * ix.n, s.q, ix.n, lim, ab, nread);
+            ++n_ref;
+            n_floats += (unsigned long long)nread;
+            if (!ab) push(d2, r);
+        }
+    }
+    flush();
+    if (lane == 0 && n_ref) {
+        atomicAdd(&c->series_refined, n_ref);
+        atomicAdd(&c->ed_floats, n_floats);
+    }
+    if (stalled) atomicOr(&c->flags, QF_STALLED);
+}
+
 // ---------------------------------------------------------------- q_series_lb
 // The lower-bound scan (MESSI's lower-bound calculations).  Work item i of the
 // list (a piece of at most LB_PIECE rows of a queued leaf, in ascending leaf
@@ -1099,8 +1383,10 @@ static_assert(sizeof(float) * W * (MAX_CARD / 2) <= LB_TAB_BYTES, "the fp32 tabl
 constexpr size_t LB_RING_BYTES = (size_t)LB_WARPS * LB_STAGES * LB_PIECE * sizeof(uint4);
 constexpr size_t LB_SMEM = 1024 + LB_TAB_BYTES + LB_RING_BYTES + sizeof(uint64_t) * LB_WARPS * LB_STAGES +
                            sizeof(uint2) * LB_WARPS * (LB_STAGES + LB_BUF) + (size_t)LB_WARPS * LB_PIECE +
-                           sizeof(uint32_t) * (LB_WARPS + 2);
+                           sizeof(uint32_t) * (LB_WARPS + 6);
 static_assert(LB_SMEM <= 227 * 1024, "the scan's shared memory exceeds a CTA's limit");
+static_assert(LB_STAGES >= RQ_DEPTH && LB_STAGES * LB_PIECE * sizeof(uint4) >= RQ_DEPTH * 2 * RQ_ROW,
+              "a warp's ring and barriers hold the refinement's pairs of rows in flight");
 constexpr uint32_t LB_QMAX = 255;  // byte-table units of the threshold
 
 template <int OFF>
@@ -1143,8 +1429,12 @@ __device__ __forceinline__ float lb_exact256(uint4 w, const float* bp, const flo
 }
 
 // One query's scan by G CTAs, this one being number cta (item i belongs to CTA
-// i mod G).
-template <int CARD>
+// i mod G).  REFINE > 0: every warp appends its own last survivors, the CTA
+// then counts itself done in the control block (scan_done), and the warps go
+// on to refine survivors (q_refine_claimed; REFINE == 2: rows of n = 256 staged
+// by bulk copies); REFINE == 0: the CTA appends its warps' last survivors at
+// once.
+template <int CARD, int REFINE>
 __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const QueryScratch& s, int k, uint32_t cta,
                                                  uint32_t G) {
     extern __shared__ unsigned char lb_smem_raw[];
@@ -1161,6 +1451,8 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
     uint8_t* cand1 = reinterpret_cast<uint8_t*>(bufs + LB_WARPS * LB_BUF);  // [LB_WARPS][LB_PIECE]
     uint32_t* next_p = reinterpret_cast<uint32_t*>(cand1 + LB_WARPS * LB_PIECE);
     uint32_t* wcnt = next_p + 1;  // [LB_WARPS + 1]: each warp's last survivors, then the CTA's base
+    // REFINE: warps done scanning, the scan over everywhere, polling token, slot units taken
+    uint32_t* fz = wcnt + LB_WARPS + 1;
     const int card = ix.card;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint4* wring = ring + (size_t)warp * LB_STAGES * LB_PIECE;
@@ -1258,7 +1550,10 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
             if (i < nv) tdst[i] = tv[t];
         }
     }
-    if (threadIdx.x == 0) *next_p = LB_WARPS * LB_STAGES;  // the items after the warps' first ones go by claim
+    if (threadIdx.x == 0) {
+        *next_p = LB_WARPS * LB_STAGES;  // the items after the warps' first ones go by claim
+        fz[0] = fz[1] = fz[2] = fz[3] = 0u;
+    }
     __syncthreads();
     // the warp's next item of the CTA into `pend` (claimed in list order)
     auto claim = [&]() -> bool {
@@ -1273,7 +1568,8 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
     uint2* buf = bufs + warp * LB_BUF;
     int nbuf = 0;  // warp-uniform
     // the buffered survivors go to the global list in one append, each as
-    // {row of x, bound} (the position is translated here, once per batch)
+    // {row of x + 1, bound} in one 8-byte store (the position is translated
+    // here, once per batch)
     auto drain = [&]() {
         if (nbuf == 0) return;
         uint32_t base = 0;
@@ -1281,7 +1577,7 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         base = __shfl_sync(FULL, base, 0);
         __syncwarp();
         for (int t = lane; t < nbuf; t += 32)
-            if (base + t < s.surv_cap) s.surv[base + t] = make_uint2(row_at(ix, buf[t].x), buf[t].y);
+            if (base + t < s.surv_cap) s.surv[base + t] = make_uint2(row_at(ix, buf[t].x) + 1u, buf[t].y);
         __syncwarp();
         nbuf = 0;
     };
@@ -1381,22 +1677,35 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         }
         __syncwarp();
     }
-    // the warps' last survivors go to the list in one append for the whole CTA
-    // (thousands of warps finish at about the same time: one counter update per
-    // CTA instead of one per warp)
-    if (lane == 0) wcnt[warp] = (uint32_t)nbuf;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t tot = 0;
-        for (int i = 0; i < LB_WARPS; ++i) tot += wcnt[i];
-        wcnt[LB_WARPS] = tot ? atomicAdd(&c->surv_count, tot) : 0u;
-    }
-    __syncthreads();
-    {
+    if constexpr (REFINE > 0) {
+        // the warp's last survivors, then the warp counts itself done; the CTA's
+        // last warp counts the CTA done once every warp's survivors are visible
+        // (each warp's fence before its count, the last one's fence after it)
+        drain();
+        if (lane == 0) {
+            __threadfence();
+            if (atomicAdd(&fz[0], 1u) == (uint32_t)LB_WARPS - 1u) {
+                __threadfence();
+                atomicAdd(&c->scan_done, 1u);
+            }
+        }
+        __syncwarp();
+    } else {
+        // the warps' last survivors go to the list in one append for the whole CTA
+        // (thousands of warps finish at about the same time: one counter update per
+        // CTA instead of one per warp)
+        if (lane == 0) wcnt[warp] = (uint32_t)nbuf;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int i = 0; i < LB_WARPS; ++i) tot += wcnt[i];
+            wcnt[LB_WARPS] = tot ? atomicAdd(&c->surv_count, tot) : 0u;
+        }
+        __syncthreads();
         uint32_t base = wcnt[LB_WARPS];
         for (int i = 0; i < warp; ++i) base += wcnt[i];
         for (int t = lane; t < nbuf; t += 32)
-            if (base + t < s.surv_cap) s.surv[base + t] = make_uint2(row_at(ix, buf[t].x), buf[t].y);
+            if (base + t < s.surv_cap) s.surv[base + t] = make_uint2(row_at(ix, buf[t].x) + 1u, buf[t].y);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) n_lb += __shfl_xor_sync(FULL, n_lb, off);
@@ -1404,10 +1713,23 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         if (n_lb) atomicAdd(&c->series_lb, n_lb);
         if (n_leaves) atomicAdd(&c->leaves_scanned, n_leaves);
     }
+    if constexpr (REFINE > 0) {
+        // the warp's ring and barriers go on staging rows: stage t's next wait
+        // has the parity of the copies it has completed
+        uint32_t par = 0;
+#pragma unroll
+        for (int t = 0; t < LB_STAGES; ++t)
+            par |= ((issued > (uint32_t)t ? (issued - 1u - t) / LB_STAGES + 1u : 0u) & 1u) << t;
+        if (!stalled)
+            q_refine_claimed<REFINE == 2>(ix, s, k, cta, G, fz + 1, reinterpret_cast<unsigned char*>(wring), wbar,
+                                          par);
+    }
 }
-template <int CARD>
-__global__ void __launch_bounds__(LB_THREADS, 1) q_series_lb_kernel(DevIndex ix, QueryScratch s, int k) {
-    q_series_lb_body<CARD>(ix, s, k, blockIdx.x, gridDim.x);
+// a single query's scan and refinement (one CTA per SM, cooperative launch:
+// a refining warp may wait on any CTA's survivors)
+template <int CARD, int REFINE>
+__global__ void __launch_bounds__(LB_THREADS, 1) q_scan_refine_kernel(DevIndex ix, QueryScratch s, int k) {
+    q_series_lb_body<CARD, REFINE>(ix, s, k, blockIdx.x, gridDim.x);
 }
 // a batch of queries: CTA j runs task j = {query, part | parts << 16}, the
 // parts of a query sized to its number of work items
@@ -1415,7 +1737,7 @@ template <int CARD>
 __global__ void __launch_bounds__(LB_THREADS, 1) bq_series_lb_kernel(DevIndex ix, const QueryScratch* ss,
                                                                      const uint2* __restrict__ tasks, int k) {
     const uint2 t = tasks[blockIdx.x];
-    q_series_lb_body<CARD>(ix, ss[t.x], k, t.y & 0xFFFFu, t.y >> 16);
+    q_series_lb_body<CARD, 0>(ix, ss[t.x], k, t.y & 0xFFFFu, t.y >> 16);
 }
 
 // the scan kernels' shared-memory limit, raised once per device (before any
@@ -1424,9 +1746,13 @@ void prepare_scan_kernel(int device) {
     if (device < 0 && cudaGetDevice(&device) != cudaSuccess) device = -1;
     static bool done[64] = {};
     if (device >= 0 && device < 64 && done[device]) return;
-    ISAX_CUDA_TRY(cudaFuncSetAttribute(q_series_lb_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ISAX_CUDA_TRY(cudaFuncSetAttribute(q_scan_refine_kernel<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)LB_SMEM));
-    ISAX_CUDA_TRY(cudaFuncSetAttribute(q_series_lb_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ISAX_CUDA_TRY(cudaFuncSetAttribute(q_scan_refine_kernel<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)LB_SMEM));
+    ISAX_CUDA_TRY(cudaFuncSetAttribute(q_scan_refine_kernel<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)LB_SMEM));
+    ISAX_CUDA_TRY(cudaFuncSetAttribute(q_scan_refine_kernel<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)LB_SMEM));
     ISAX_CUDA_TRY(cudaFuncSetAttribute(bq_series_lb_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)LB_SMEM));
@@ -1436,6 +1762,12 @@ void prepare_scan_kernel(int device) {
 }
 
 // ---------------------------------------------------------------- q_refine
+// survivor slot i as {row of x, bound} (a slot holds row + 1)
+__device__ __forceinline__ uint2 surv_get(const QueryScratch& s, uint32_t i) {
+    uint2 e = s.surv[i];
+    e.x -= 1u;
+    return e;
+}
 // Real distances of the survivors (MESSI's real distance calculations), in the
 // order the scan found them: warp w takes survivor quads w, w + W, ... (W
 // warps in the grid).  Before each quad the warp reads the current k-th best
@@ -1457,9 +1789,8 @@ __device__ __forceinline__ void q_refine_body(const DevIndex& ix, const QueryScr
     load_q<NV>(s.q, qv);
     const uint32_t found = c->surv_count;
     const uint32_t total = found < s.surv_cap ? found : s.surv_cap;
-    const double delta = c->delta, E = c->E;
     unsigned long long kth = 0ull;  // cached k-th best and the limits derived from it
-    float thr = INFINITY, lim = INFINITY;
+    float thr = INFINITY, lim = INFINITY, win = INFINITY;
     unsigned long long n_ref = 0, n_floats = 0;
     float my_d2 = INFINITY;
     uint32_t my_pos = 0;
@@ -1468,9 +1799,7 @@ __device__ __forceinline__ void q_refine_body(const DevIndex& ix, const QueryScr
     // consider() decides with a fresh value
     auto flush = [&]() {
         if (nb == 0) return;
-        const double lim_w = kth == 0ull || kth == EMPTY_SLOT ? INFINITY : (double)key_d2(kth) * (1.0 + 3.0 * delta);
-        if (lane < nb && (double)my_d2 <= lim_w)
-            consider(s, k, pack_key(my_d2, id_of_row(ix, my_pos)), my_pos, delta);
+        if (lane < nb && my_d2 <= win) consider(s, k, pack_key(my_d2, id_of_row(ix, my_pos)), my_pos, c->delta);
         __syncwarp();
         nb = 0;
     };
@@ -1488,15 +1817,14 @@ __device__ __forceinline__ void q_refine_body(const DevIndex& ix, const QueryScr
     if (lane == 0) kt_next = ld_volatile_u64(&s.topk[k - 1]);
     uint2 nx[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) nx[t] = 4 * gw + t < total ? s.surv[4 * gw + t] : make_uint2(0u, 0x7f800000u);
+    for (int t = 0; t < 4; ++t) nx[t] = 4 * gw + t < total ? surv_get(s, 4 * gw + t) : make_uint2(0u, 0x7f800000u);
     for (uint32_t i = 4 * gw; i < total; i += 4 * nw) {
         __syncwarp();
         const unsigned long long kt = __shfl_sync(FULL, kt_next, 0);
         if (lane == 0) kt_next = ld_volatile_u64(&s.topk[k - 1]);
         if (kt != kth || kth == 0ull) {
             kth = kt;
-            thr = lb_threshold(kt, delta, E);
-            lim = abandon_limit(kt, delta);
+            limits_f32(c, kt, thr, lim, win);
         }
         uint2 e[4];
         unsigned keep = 0;
@@ -1508,7 +1836,7 @@ __device__ __forceinline__ void q_refine_body(const DevIndex& ix, const QueryScr
         }
         const uint32_t in = i + 4 * nw;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) nx[t] = in + t < total ? s.surv[in + t] : make_uint2(0u, 0x7f800000u);
+        for (int t = 0; t < 4; ++t) nx[t] = in + t < total ? surv_get(s, in + t) : make_uint2(0u, 0x7f800000u);
         if (!keep) continue;
         if constexpr (NV > 0 && NV <= 2) {
             float d[4];
@@ -1539,10 +1867,6 @@ __device__ __forceinline__ void q_refine_body(const DevIndex& ix, const QueryScr
         atomicAdd(&c->ed_floats, n_floats);
     }
 }
-template <int NV>
-__global__ void __launch_bounds__(RF_THREADS, 3) q_refine_kernel(DevIndex ix, QueryScratch s, int k) {
-    q_refine_body<NV>(ix, s, k, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
-}
 // a batch of queries: CTA j runs task j = {query, part | parts << 16}, the
 // parts of a query sharing its survivors
 template <int NV>
@@ -1570,18 +1894,15 @@ __device__ __forceinline__ void q_refine_half_body(const DevIndex& ix, const Que
     load_q<2>(s.q, qv);
     const uint32_t found = c->surv_count;
     const uint32_t total = found < s.surv_cap ? found : s.surv_cap;
-    const double delta = c->delta, E = c->E;
     unsigned long long kth = 0ull;
-    float thr = INFINITY, lim = INFINITY;
+    float thr = INFINITY, lim = INFINITY, win = INFINITY;
     unsigned long long n_ref = 0, n_floats = 0;
     float my_d2 = INFINITY;
     uint32_t my_pos = 0;
     int nb = 0;
     auto flush = [&]() {
         if (nb == 0) return;
-        const double lim_w = kth == 0ull || kth == EMPTY_SLOT ? INFINITY : (double)key_d2(kth) * (1.0 + 3.0 * delta);
-        if (lane < nb && (double)my_d2 <= lim_w)
-            consider(s, k, pack_key(my_d2, id_of_row(ix, my_pos)), my_pos, delta);
+        if (lane < nb && my_d2 <= win) consider(s, k, pack_key(my_d2, id_of_row(ix, my_pos)), my_pos, c->delta);
         __syncwarp();
         nb = 0;
     };
@@ -1600,14 +1921,13 @@ __device__ __forceinline__ void q_refine_half_body(const DevIndex& ix, const Que
         if (lane == 0) kt_next = ld_volatile_u64(&s.topk[k - 1]);
         if (kt != kth || kth == 0ull) {
             kth = kt;
-            thr = lb_threshold(kt, delta, E);
-            lim = abandon_limit(kt, delta);
+            limits_f32(c, kt, thr, lim, win);
         }
     };
     const float4* x4 = reinterpret_cast<const float4*>(ix.x);
     uint2 nx[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) nx[t] = 4 * gw + t < total ? s.surv[4 * gw + t] : make_uint2(0u, 0x7f800000u);
+    for (int t = 0; t < 4; ++t) nx[t] = 4 * gw + t < total ? surv_get(s, 4 * gw + t) : make_uint2(0u, 0x7f800000u);
     // the quad at index i: its rows and the ones the bound does not skip; the
     // next quad's survivors are read meanwhile
     auto take = [&](uint32_t i, uint2 (&e)[4], unsigned& keep) {
@@ -1618,7 +1938,7 @@ __device__ __forceinline__ void q_refine_half_body(const DevIndex& ix, const Que
             if (i + t < total && __uint_as_float(e[t].y) <= thr) keep |= 1u << t;
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) nx[t] = i + 4 * nw + t < total ? s.surv[i + 4 * nw + t] : make_uint2(0u, 0x7f800000u);
+        for (int t = 0; t < 4; ++t) nx[t] = i + 4 * nw + t < total ? surv_get(s, i + 4 * nw + t) : make_uint2(0u, 0x7f800000u);
     };
     uint32_t i = 4 * gw;
     uint2 eA[4];
@@ -1688,9 +2008,6 @@ __device__ __forceinline__ void q_refine_half_body(const DevIndex& ix, const Que
         atomicAdd(&c->series_refined, n_ref);
         atomicAdd(&c->ed_floats, n_floats);
     }
-}
-__global__ void __launch_bounds__(RF_THREADS, 2) q_refine_half_kernel(DevIndex ix, QueryScratch s, int k) {
-    q_refine_half_body(ix, s, k, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
 }
 __global__ void __launch_bounds__(RF_THREADS, 2) bq_refine_half_kernel(DevIndex ix, const QueryScratch* ss,
                                                                        const uint2* __restrict__ tasks, int k) {
@@ -2173,8 +2490,9 @@ void alloc_query_scratch_for(int64_t L, int64_t N, int n, int card, uint32_t can
     q.out_dist = static_cast<float*>(dev_alloc(sizeof(float) * MAX_K, st));
     q.surv_cap = surv_cap;
     q.surv = static_cast<uint2*>(dev_alloc(sizeof(uint2) * surv_cap, st));
-    // a query starts with its k best empty and its counts at zero (each query's
-    // q_finalize leaves them so for the next one)
+    // a query starts with its k best empty, its counts at zero and its survivor
+    // slots empty (each query's kernels leave them so for the next one)
+    ISAX_CUDA_TRY(cudaMemsetAsync(q.surv, 0, sizeof(uint2) * surv_cap, st));
     ISAX_CUDA_TRY(cudaMemsetAsync(q.ctl, 0, sizeof(QCtl), st));
     ISAX_CUDA_TRY(cudaMemsetAsync(q.topk, 0xFF, sizeof(unsigned long long) * MAX_K, st));
 }
@@ -2193,6 +2511,13 @@ void grow_query_survivors(QueryScratch& q, uint32_t surv_cap, cudaStream_t st) {
     q.surv_cap = 0;
     q.surv = static_cast<uint2*>(dev_alloc(sizeof(uint2) * surv_cap, st));
     q.surv_cap = surv_cap;
+    ISAX_CUDA_TRY(cudaMemsetAsync(q.surv, 0, sizeof(uint2) * surv_cap, st));
+}
+
+// every survivor slot empty again: after a query whose refinement gave up a
+// wait, slots it never took may still be filled
+void empty_survivors(const QueryScratch& q, cudaStream_t st) {
+    if (q.surv && q.surv_cap) ISAX_CUDA_TRY(cudaMemsetAsync(q.surv, 0, sizeof(uint2) * q.surv_cap, st));
 }
 
 // a larger candidate buffer (the old contents are dropped)
@@ -2326,14 +2651,6 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
 
 namespace {
 
-int occupancy_grid(const void* fn, int threads, size_t smem, int num_sms) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    return per_sm * num_sms;
-}
-
 template <int NV>
 void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st, int mode,
                           int scan_share) {
@@ -2364,25 +2681,30 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
         ISAX_CUDA_TRY(cudaLaunchKernelEx(&cfg, q_leaf_bin_kernel, d, s, k));
     }
     {
-        // one CTA per SM: its warps' copy rings take most of the SM's shared memory
+        // one CTA per SM (its warps' copy rings take most of the SM's shared
+        // memory); cooperative: a refining warp waits on other CTAs' survivors
         prepare_scan_kernel(ix->device);
-        ISAX_LAUNCH("q_series_lb", st);
-        if (d.card == 256)
-            q_series_lb_kernel<256><<<grid, LB_THREADS, LB_SMEM, st>>>(d, s, k);
-        else
-            q_series_lb_kernel<0><<<grid, LB_THREADS, LB_SMEM, st>>>(d, s, k);
-    }
-    if (NV == 2) {
-        // n = 256: rows in two halves, the second read only while the row may be in the answer
-        static int grid_rh = 0;
-        if (!grid_rh) grid_rh = occupancy_grid((const void*)q_refine_half_kernel, RF_THREADS, 0, ix->num_sms);
-        ISAX_LAUNCH("q_refine", st);
-        q_refine_half_kernel<<<grid_rh, RF_THREADS, 0, st>>>(d, s, k);
-    } else {
-        static int grid_rf = 0;
-        if (!grid_rf) grid_rf = occupancy_grid((const void*)q_refine_kernel<NV>, RF_THREADS, 0, ix->num_sms);
-        ISAX_LAUNCH("q_refine", st);
-        q_refine_kernel<NV><<<grid_rf, RF_THREADS, 0, st>>>(d, s, k);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(LB_THREADS);
+        cfg.dynamicSmemBytes = LB_SMEM;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        // n = 256 with the rows in device memory: rows staged by bulk copies;
+        // otherwise read by the warps' own loads
+        const bool half = NV == 2 && !ix->rows_host;
+        ISAX_LAUNCH("q_scan_refine", st);
+        if (d.card == 256) {
+            if (half) ISAX_CUDA_TRY(cudaLaunchKernelEx(&cfg, q_scan_refine_kernel<256, 2>, d, s, k));
+            else ISAX_CUDA_TRY(cudaLaunchKernelEx(&cfg, q_scan_refine_kernel<256, 1>, d, s, k));
+        } else {
+            if (half) ISAX_CUDA_TRY(cudaLaunchKernelEx(&cfg, q_scan_refine_kernel<0, 2>, d, s, k));
+            else ISAX_CUDA_TRY(cudaLaunchKernelEx(&cfg, q_scan_refine_kernel<0, 1>, d, s, k));
+        }
     }
     {
         ISAX_LAUNCH("q_finalize", st);
@@ -2478,7 +2800,11 @@ void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_
         *ctl_out = *ix->h_ctl;
         ctl_out->flags |= injected_query_flags();
         if (ctl_out->flags & QF_NONFINITE) throw Error{ISAX_ERR_INVALID_ARG, "query contains a non-finite value"};
-        if (ctl_out->flags & QF_STALLED) throw Error{ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed"};
+        if (ctl_out->flags & QF_STALLED) {
+            empty_survivors(ix->qs, st);
+            ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+            throw Error{ISAX_ERR_TIMEOUT, "a bounded wait of the query gave up"};
+        }
         if (ctl_out->flags & QF_OVERFLOW) {
             if (attempt >= 3) throw Error{ISAX_ERR_INTERNAL, "candidate buffer kept overflowing"};
             const uint64_t N = (uint64_t)ix->d.N;
@@ -2584,7 +2910,11 @@ static void query_batch_slots(isax_index* ix, const float* Q, int B, int k, uint
             nonfinite = true;
             continue;
         }
-        if (c.flags & QF_STALLED) throw Error{ISAX_ERR_TIMEOUT, "a bulk copy of the lower-bound scan never completed"};
+        if (c.flags & QF_STALLED) {
+            for (int i = 0; i < S; ++i) empty_survivors(pool->slots[i]->qs, st);
+            ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+            throw Error{ISAX_ERR_TIMEOUT, "a bounded wait of the query gave up"};
+        }
         if (c.flags & (QF_OVERFLOW | QF_SHORT)) {
             ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, Q + (size_t)b * n, sizeof(float) * n, kin, st));
             query_device(ix, k, &c, &reruns, st);

@@ -260,6 +260,7 @@ static void server_loop(isax_server* s) {
             if (c.flags & QF_NONFINITE) {
                 publish(s, sl, ISAX_ERR_INVALID_ARG);
             } else if (c.flags & QF_STALLED) {
+                empty_survivors(sl->qs, sl->st);
                 publish(s, sl, ISAX_ERR_TIMEOUT);
             } else if ((c.flags & QF_OVERFLOW) && sl->reruns < 4) {
                 const uint64_t N = (uint64_t)s->colls[sl->req.coll]->d.N;
