@@ -137,13 +137,14 @@ static void fill_stats(isax_query_stats* st, const isax_index* ix, const QCtl& c
     st->ed_floats = (int64_t)c.ed_floats;
 }
 
-// one query whose input already sits in ix->qs.q; copies the results out
-static void run_one(isax_index* ix, int32_t k, uint32_t mem_flags, int64_t* out_idx,
+// one query read from q_src (a device address); the results go to the caller's
+// outputs
+static void run_one(isax_index* ix, const float* q_src, int32_t k, uint32_t mem_flags, int64_t* out_idx,
                     float* out_dist, isax_query_stats* stats, cudaStream_t st, int mode = QUERY_MESSI) {
     QCtl c;
     int reruns = 0;
-    // the answer is copied out with the control block, under the same wait
-    query_device(ix, k, &c, &reruns, st, mode, out_idx, out_dist, (mem_flags & ISAX_MEM_OUTPUT_DEVICE) != 0);
+    query_device(ix, k, &c, &reruns, st, mode, out_idx, out_dist, (mem_flags & ISAX_MEM_OUTPUT_DEVICE) != 0,
+                 q_src);
     fill_stats(stats, ix, c, reruns);
 }
 
@@ -164,10 +165,15 @@ static isax_status query_knn_mode(const isax_index* cix, const float* q, int32_t
         DeviceGuard dg(ix->device);
         std::lock_guard<std::mutex> lk(*static_cast<std::mutex*>(ix->mu));
         cudaStream_t st = (cudaStream_t)cuda_stream;
-        const cudaMemcpyKind kin = (mem_flags & ISAX_MEM_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice
-                                                                       : cudaMemcpyHostToDevice;
-        ISAX_CUDA_TRY(cudaMemcpyAsync(ix->qs.q, q, sizeof(float) * ix->d.n, kin, st));
-        run_one(ix, k, mem_flags, out_idx, out_dist, stats, st, mode);
+        // the query's first kernel reads a device query where it is; a host
+        // query is first placed in the index's mapped block
+        const float* q_src = q;
+        if (!(mem_flags & ISAX_MEM_INPUT_DEVICE)) {
+            ensure_query_mail(ix);
+            memcpy(ix->mail->q, q, sizeof(float) * ix->d.n);
+            q_src = ix->mail_dev->q;
+        }
+        run_one(ix, q_src, k, mem_flags, out_idx, out_dist, stats, st, mode);
     });
 }
 

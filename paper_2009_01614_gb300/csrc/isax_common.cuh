@@ -196,6 +196,23 @@ struct QueryScratch {
     float* out_dist;               // [MAX_K]
 };
 
+// A mapped page-locked block per index for its single queries: before a launch
+// the host writes the query's source and output pointers (and, for a query in
+// host memory, its values); the query's first kernel reads the query from
+// there, and its last writes the answer to the caller's device outputs and
+// leaves the control block (and the answer for host outputs) here, so a query
+// needs no copies of its own around its kernels.
+struct QMail {
+    const float* q_src;   // device address of the query: the caller's array, or q below
+    int64_t* out_idx;     // the caller's device outputs, or null (answer only below)
+    float* out_dist;
+    uint64_t pad;
+    QCtl ctl;             // the control block as the query ended
+    int64_t idx[MAX_K];
+    float dist[MAX_K];
+    float q[MAX_LEN];
+};
+
 }  // namespace isax
 
 struct isax_index;
@@ -210,12 +227,15 @@ void summarize_impl(const float* series, int64_t N, int n, int card, uint32_t me
 // query strategies: MESSI (leaf pruning, leaves in bound order) and the ParIS
 // flat scan (every series of the SAX array bounded, storage order)
 enum : int { QUERY_MESSI = 0, QUERY_FLAT = 1 };
-// One query on the index's own scratch (q already there); the control block is
-// copied to *ctl_out and, when given, the answer to out_idx / out_dist (device
-// pointers if out_device), all under one wait.
+// One query on the index's own scratch, its n values read from q_src (a device
+// address; null: already in the scratch); the control block is copied to
+// *ctl_out and, when given, the answer to out_idx / out_dist (device pointers
+// if out_device).
 void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st,
                   int mode = QUERY_MESSI, int64_t* out_idx = nullptr, float* out_dist = nullptr,
-                  bool out_device = false);
+                  bool out_device = false, const float* q_src = nullptr);
+// the index's mapped block, allocated on first use
+void ensure_query_mail(isax_index* ix);
 typedef void (*isax_query_stats_fill)(void* ctx, int b, const QCtl& c, int reruns);
 void query_batch_device(isax_index* ix, const float* Q, int B, int k, uint32_t mem_flags,
                         int64_t* out_idx, float* out_dist, isax_query_stats_fill fill,
@@ -224,7 +244,7 @@ void free_index_arrays(isax_index* ix, cudaStream_t st);
 // scan_share: the query's scan runs on num_sms / scan_share CTAs (1: every SM;
 // more leaves room for the scans of concurrent queries)
 void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st,
-                             int mode = QUERY_MESSI, int scan_share = 1);
+                             int mode = QUERY_MESSI, int scan_share = 1, QMail* mail = nullptr);
 void alloc_query_scratch(isax_index* ix, uint32_t cand_cap, uint32_t surv_cap, cudaStream_t st,
                          bool keep_query = false);
 uint32_t default_surv_cap(int64_t N);  // survivor entries of a fresh query scratch
@@ -299,5 +319,6 @@ struct isax_index {
     bool rows_host;  // x is pinned host memory (ISAX_BUILD_ROWS_HOST)
     bool rows_in_place;  // x holds the rows in the input's order, read by original row
     bool rows_borrowed;  // ... and is the caller's device array (ISAX_BUILD_ROWS_IN_PLACE), not owned
-    isax::QCtl* h_ctl;   // page-locked copy of the single query's control block
+    isax::QMail* mail;      // the single queries' mapped block (host address), or null
+    isax::QMail* mail_dev;  // its device address
 };

@@ -41,6 +41,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -689,7 +690,8 @@ __device__ __forceinline__ void warp_d2_four(const DevIndex& ix, const uint2 (&e
 constexpr int FR_THREADS = 256, FR_WARPS = FR_THREADS / 32, FR_ROWS = 4, FR_LEAVES = 4, FR_KEYS = 4;
 
 template <int NV>
-__global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryScratch s, int k, int neighbors) {
+__global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryScratch s, int k, int neighbors,
+                                                              const QMail* mail) {
     __shared__ float bp[MAX_CARD + 1];
     __shared__ __align__(16) float qv[MAX_LEN];  // read as float4 below
     __shared__ float qpaa[W];
@@ -701,11 +703,20 @@ __global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryS
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = ix.n, m = n / W, card = ix.card;
     const bool lead = blockIdx.x == 0;
-    for (int i = tid; i <= card; i += FR_THREADS) bp[i] = ix.bp[i];
-    for (int j = tid; j < n; j += FR_THREADS) qv[j] = s.q[j];
+    __shared__ const float* qsrc;
     if (tid == 0) {
         bad = 0;
         cnt_s = 0;
+        // the query: where the index's mapped block says (CTA 0 also leaves it in
+        // the scratch for the later kernels), else already in the scratch
+        qsrc = mail ? mail->q_src : s.q;
+    }
+    for (int i = tid; i <= card; i += FR_THREADS) bp[i] = ix.bp[i];
+    __syncthreads();
+    for (int j = tid; j < n; j += FR_THREADS) {
+        const float v = qsrc[j];
+        qv[j] = v;
+        if (lead && mail) s.q[j] = v;
     }
     if (lead) {
         // the binning step's counters and grid barrier start at zero
@@ -1117,6 +1128,8 @@ __global__ void __launch_bounds__(BIN_THREADS) q_leaf_bin_kernel(DevIndex ix, Qu
 constexpr uint32_t RQ_WAIT = 1u << 21;      // polls of one slot before the wait gives up
 constexpr uint32_t RQ_CHUNK = 64;           // list slots per chunk
 constexpr uint32_t RQ_UNIT = 8;             // slots a warp takes at once
+constexpr int RQ_KT_LANE = RQ_UNIT < 32 ? (int)RQ_UNIT : 0;  // the lane that reads the k-th best
+static_assert(RQ_UNIT <= 32 && RQ_CHUNK % RQ_UNIT == 0, "a unit is at most a warp's lanes and divides a chunk");
 constexpr uint32_t RQ_ROW = 1024;           // bytes of a row of n = 256
 constexpr uint32_t RQ_BAR_WAIT = 1u << 22;  // bounded wait on a staged row copy
 constexpr int RQ_DEPTH = 3;                 // pairs of rows in flight per warp (n = 256)
@@ -1164,12 +1177,13 @@ __device__ __forceinline__ float warp_d2_v4q(const float4* __restrict__ xr, cons
 // lanes and are refined in turn.  HALF (n = 256, rows in device memory): each
 // pair of rows is staged whole in the warp's own copy ring (free once its scan
 // is done: wbuf, 6 KB = RQ_DEPTH buffers of two rows, with its barriers wbar,
-// whose next waits have the parities in the bits of `par`) by bulk copies,
-// RQ_DEPTH pairs in flight.
+// whose next waits have the parities in the bits of `par`) by asynchronous
+// copies, RQ_DEPTH pairs in flight, and the query is read from its copy q_sm
+// in shared memory.
 template <bool HALF>
 __device__ __forceinline__ void q_refine_claimed(const DevIndex& ix, const QueryScratch& s, int k, uint32_t cta,
                                                  uint32_t G, uint32_t* fz, unsigned char* wbuf, uint64_t* wbar,
-                                                 uint32_t par) {
+                                                 uint32_t par, const float* q_sm) {
     QCtl* c = s.ctl;
     const int lane = threadIdx.x & 31;
     const uint64_t cap = s.surv_cap;
@@ -1198,26 +1212,35 @@ __device__ __forceinline__ void q_refine_claimed(const DevIndex& ix, const Query
     bool end = false;    // no later slot of this CTA can be filled
     uint32_t qrow = 0;   // lane t < RQ_UNIT: the row of the unit's slot t
     unsigned qm = 0;     // the unit's slots still to refine (warp-uniform)
-    // the CTA's next unit of slots: lane t < RQ_UNIT waits for its slot (none:
-    // past the list's end), empties it, and keeps its row unless the bound of
-    // the current k-th best skips it
-    auto take = [&]() {
+    // The next unit of slots is claimed and its slots' first reads issued one
+    // unit ahead (claim), so their latency passes while the rows before them
+    // are refined; take() then waits for what is still missing.
+    uint32_t nx_p = 0;              // the claimed unit (warp-uniform)
+    uint2 nx_e = make_uint2(0u, 0u);  // lane t < RQ_UNIT: its slot's first read
+    unsigned long long nx_kt = 0;   // lane RQ_KT_LANE: the k-th best, read with them
+    auto slot_of = [&](uint32_t p) {
+        return ((uint64_t)(p / (RQ_CHUNK / RQ_UNIT)) * G + cta) * RQ_CHUNK +
+               (uint64_t)RQ_UNIT * (p % (RQ_CHUNK / RQ_UNIT)) + (uint64_t)lane;
+    };
+    auto claim = [&]() {
         uint32_t p = 0;
         if (lane == 0) p = atomicAdd(&fz[2], 1u);
-        p = __shfl_sync(FULL, p, 0);
-        const uint64_t i0 = ((uint64_t)(p / (RQ_CHUNK / RQ_UNIT)) * G + cta) * RQ_CHUNK +
-                            (uint64_t)RQ_UNIT * (p % (RQ_CHUNK / RQ_UNIT));
-        unsigned long long kt = 0;
-        if (lane == RQ_UNIT) kt = ld_volatile_u64(&s.topk[k - 1]);  // read alongside the slots
-        uint2 e = make_uint2(0u, 0u);
+        nx_p = __shfl_sync(FULL, p, 0);
+        const uint64_t i = slot_of(nx_p);
+        nx_e = lane < RQ_UNIT && i < cap ? ld_volatile_u2(&s.surv[i]) : make_uint2(0u, 0u);
+        if (lane == RQ_KT_LANE) nx_kt = ld_volatile_u64(&s.topk[k - 1]);
+    };
+    // the claimed unit: lane t < RQ_UNIT waits for its slot (none: past the
+    // list's end), empties it, and keeps its row unless the bound of the
+    // current k-th best skips it; then the unit after it is claimed
+    auto take = [&]() {
+        uint2 e = nx_e;
         bool none = true;
         if (lane < RQ_UNIT) {
-            const uint64_t i = i0 + (uint64_t)lane;
+            const uint64_t i = slot_of(nx_p);
             none = i >= cap;  // past the list's room: never filled (the overflow rerun answers)
             uint32_t nap = 64;
-            for (uint32_t poll = 0; !none; ++poll) {
-                e = ld_volatile_u2(&s.surv[i]);
-                if (e.x) break;
+            for (uint32_t poll = 0; !none && !e.x; ++poll) {
                 if (*(volatile uint32_t*)&fz[0]) {
                     // the scan is over everywhere: every survivor is in the list
                     __threadfence();
@@ -1242,17 +1265,19 @@ __device__ __forceinline__ void q_refine_claimed(const DevIndex& ix, const Query
                 }
                 __nanosleep(nap);
                 if (nap < 1024u) nap <<= 1;
+                e = ld_volatile_u2(&s.surv[i]);
             }
             if (!none) s.surv[i] = make_uint2(0u, 0u);  // back empty for the next query
         }
         end = __any_sync(FULL, (lane < RQ_UNIT && none) || stalled);
-        kt = __shfl_sync(FULL, kt, RQ_UNIT);
+        const unsigned long long kt = __shfl_sync(FULL, nx_kt, RQ_KT_LANE);
         if (kt != kth || kth == 0ull) {
             kth = kt;
             limits_f32(c, kt, thr, lim, win);
         }
         qrow = e.x - 1u;
         qm = __ballot_sync(FULL, lane < RQ_UNIT && !none && __uint_as_float(e.y) <= thr);
+        if (!end) claim();
     };
     // the next row to refine (mask bit t of the unit, row in lane t), taking
     // units until one has a kept row or the list ends; false when none is left
@@ -1265,23 +1290,43 @@ __device__ __forceinline__ void q_refine_claimed(const DevIndex& ix, const Query
         ISAX_CHECK(r < (uint64_t)ix.N, CHK_REFINE_ROW);
         return true;
     };
+    claim();
     if constexpr (HALF) {
         const unsigned char* xb = reinterpret_cast<const unsigned char*>(ix.x);
         uint32_t pr0[RQ_DEPTH], pr1[RQ_DEPTH];  // each buffer's rows
         unsigned pm[RQ_DEPTH];                   // and which of the two it holds
         uint32_t pending = 0;                    // buffers whose copies are not yet waited for
+        // The rows come in through the load path, 16 bytes per lane (a single
+        // engine per SM issuing 1 KB bulk copies for every warp moves rows at
+        // about half the rate of the warps' own loads); each barrier then counts
+        // the 32 lanes' arrivals once their copies have landed.
+        if (lane == 0) {
+            for (int t = 0; t < RQ_DEPTH; ++t) {
+                mbar_inval(&wbar[t]);
+                mbar_init(&wbar[t], 32);
+            }
+            mbar_fence_init();
+        }
+        __syncwarp();
+        par = 0u;
         // the next (up to) two rows into buffer b, copied whole
         auto fill = [&](int b) {
             pm[b] = 0u;
             if (next_row(pr0[b])) pm[b] |= 1u;
             if (next_row(pr1[b])) pm[b] |= 2u;
             if (!pm[b]) return;
-            if (lane == 0) {
-                mbar_arrive_expect_tx(&wbar[b], (uint32_t)__popc(pm[b]) * RQ_ROW);
-                if (pm[b] & 1u) bulk_load(wbuf + b * 2 * RQ_ROW, xb + (int64_t)pr0[b] * RQ_ROW, RQ_ROW, &wbar[b]);
-                if (pm[b] & 2u)
-                    bulk_load(wbuf + b * 2 * RQ_ROW + RQ_ROW, xb + (int64_t)pr1[b] * RQ_ROW, RQ_ROW, &wbar[b]);
+            unsigned char* dst = wbuf + b * 2 * RQ_ROW + lane * 16;
+            if (pm[b] & 1u) {
+                const unsigned char* src = xb + (int64_t)pr0[b] * RQ_ROW + lane * 16;
+                cp_async16(dst, src);
+                cp_async16(dst + RQ_ROW / 2, src + RQ_ROW / 2);
             }
+            if (pm[b] & 2u) {
+                const unsigned char* src = xb + (int64_t)pr1[b] * RQ_ROW + lane * 16;
+                cp_async16(dst + RQ_ROW, src);
+                cp_async16(dst + RQ_ROW + RQ_ROW / 2, src + RQ_ROW / 2);
+            }
+            cp_async_arrive(&wbar[b]);
             pending |= 1u << b;
         };
 #pragma unroll
@@ -1300,7 +1345,8 @@ __device__ __forceinline__ void q_refine_claimed(const DevIndex& ix, const Query
                 // the distances of the buffer's rows: every lane its two float4
                 // of each row (the first half's, then the second half's), then
                 // the butterfly, as warp_d2_vec<2>
-                const float4 q0 = __ldg(q4 + lane), q1 = __ldg(q4 + 32 + lane);
+                const float4 q0 = reinterpret_cast<const float4*>(q_sm)[lane];
+                const float4 q1 = reinterpret_cast<const float4*>(q_sm)[32 + lane];
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     if (!(pm[b] & (1u << t))) continue;
@@ -1381,13 +1427,25 @@ constexpr size_t LB_BP_OFF = 4096, LB_QPAA_OFF = LB_BP_OFF + sizeof(float) * (MA
 static_assert(LB_QPAA_OFF + sizeof(float) * W <= LB_TAB_BYTES, "byte table, breakpoints and PAA fit the region");
 static_assert(sizeof(float) * W * (MAX_CARD / 2) <= LB_TAB_BYTES, "the fp32 table of cardinality <= 128 fits");
 constexpr size_t LB_RING_BYTES = (size_t)LB_WARPS * LB_STAGES * LB_PIECE * sizeof(uint4);
+// the scan's counters and flags (next item, each warp's last survivors and the
+// CTA's base, the refinement's words), then the query for the n = 256
+// refinement (16-byte aligned)
+constexpr int LB_WORDS = LB_WARPS + 8;
+constexpr size_t LB_Q_BYTES = 256 * sizeof(float);
 constexpr size_t LB_SMEM = 1024 + LB_TAB_BYTES + LB_RING_BYTES + sizeof(uint64_t) * LB_WARPS * LB_STAGES +
                            sizeof(uint2) * LB_WARPS * (LB_STAGES + LB_BUF) + (size_t)LB_WARPS * LB_PIECE +
-                           sizeof(uint32_t) * (LB_WARPS + 6);
+                           sizeof(uint32_t) * LB_WORDS + LB_Q_BYTES;
+static_assert((LB_TAB_BYTES + LB_RING_BYTES + sizeof(uint64_t) * LB_WARPS * LB_STAGES +
+               sizeof(uint2) * LB_WARPS * (LB_STAGES + LB_BUF) + (size_t)LB_WARPS * LB_PIECE +
+               sizeof(uint32_t) * LB_WORDS) % 16 == 0 && LB_WORDS >= LB_WARPS + 6,
+              "the query's copy in shared memory is 16-byte aligned after the scan's words");
 static_assert(LB_SMEM <= 227 * 1024, "the scan's shared memory exceeds a CTA's limit");
 static_assert(LB_STAGES >= RQ_DEPTH && LB_STAGES * LB_PIECE * sizeof(uint4) >= RQ_DEPTH * 2 * RQ_ROW,
               "a warp's ring and barriers hold the refinement's pairs of rows in flight");
 constexpr uint32_t LB_QMAX = 255;  // byte-table units of the threshold
+constexpr int LB_REFINERS = 4;  // warps per CTA that refine from the start of a fused launch
+constexpr int LB_EAGER = 8;     // survivors a scanning warp buffers before it publishes them (fused)
+static_assert(LB_REFINERS >= 0 && LB_REFINERS < LB_WARPS, "at least one warp scans");
 
 template <int OFF>
 __device__ __forceinline__ float lds_f32(uint32_t addr) {
@@ -1453,8 +1511,12 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
     uint32_t* wcnt = next_p + 1;  // [LB_WARPS + 1]: each warp's last survivors, then the CTA's base
     // REFINE: warps done scanning, the scan over everywhere, polling token, slot units taken
     uint32_t* fz = wcnt + LB_WARPS + 1;
+    float* q_sm = reinterpret_cast<float*>(next_p + LB_WORDS);  // REFINE == 2: the query (n = 256)
     const int card = ix.card;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // REFINE: the last LB_REFINERS warps refine from the start instead of scanning
+    constexpr int SW = REFINE > 0 ? LB_WARPS - LB_REFINERS : LB_WARPS;
+    const bool scans = warp < SW;
     uint4* wring = ring + (size_t)warp * LB_STAGES * LB_PIECE;
     uint64_t* wbar = bars + warp * LB_STAGES;
     uint2* wmeta = metas + warp * LB_STAGES;
@@ -1469,7 +1531,7 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
 #pragma unroll
     for (int t = 0; t < LB_STAGES; ++t) {
         const size_t i = cta + (size_t)(warp * LB_STAGES + t) * G;
-        e[t] = lane == 0 && i < s.work_cap ? s.work[i] : make_uint2(0u, 0u);
+        e[t] = lane == 0 && scans && i < s.work_cap ? s.work[i] : make_uint2(0u, 0u);
     }
     // the table's inputs: the breakpoints and the query PAA (8-bit symbols), or
     // the query's fp32 table (smaller cardinalities)
@@ -1495,7 +1557,11 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         const uint32_t rows = p.y & 0x7FFFFFFFu;
         wmeta[st] = p;
         mbar_arrive_expect_tx(&wbar[st], rows * (uint32_t)sizeof(uint4));
-        if (rows) bulk_load(wring + st * LB_PIECE, ix.sax + p.x, rows * (uint32_t)sizeof(uint4), &wbar[st]);
+        // the SAX words are read once: first out of L2, so they pass by the
+        // lines the survivors' refinement reads (its list, rows and query)
+        if (rows)
+            bulk_load_hint(wring + st * LB_PIECE, ix.sax + p.x, rows * (uint32_t)sizeof(uint4), &wbar[st],
+                           l2_evict_first());
     };
     // the warp's own stage barriers, then its first LB_STAGES - 1 pieces; the
     // last of its first LB_STAGES is held until a stage frees up
@@ -1507,12 +1573,12 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         mbar_fence_init();
 #pragma unroll
         for (int t = 0; t + 1 < LB_STAGES; ++t)
-            if (j0 + t < mine) issue(t, e[t]);
+            if (scans && j0 + t < mine) issue(t, e[t]);
     }
 #pragma unroll
-    for (int t = 0; t + 1 < LB_STAGES; ++t) issued += j0 + t < mine ? 1u : 0u;
+    for (int t = 0; t + 1 < LB_STAGES; ++t) issued += scans && j0 + t < mine ? 1u : 0u;
     uint2 pend = e[LB_STAGES - 1];
-    bool pend_ok = j0 + LB_STAGES - 1 < mine;
+    bool pend_ok = scans && j0 + LB_STAGES - 1 < mine;
     const float mf = (float)(ix.n / W);
     if constexpr (CARD == 256) {
         if (threadIdx.x <= MAX_CARD) bp_s[threadIdx.x] = bpv;
@@ -1551,9 +1617,11 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         }
     }
     if (threadIdx.x == 0) {
-        *next_p = LB_WARPS * LB_STAGES;  // the items after the warps' first ones go by claim
+        *next_p = SW * LB_STAGES;  // the items after the scanning warps' first ones go by claim
         fz[0] = fz[1] = fz[2] = fz[3] = 0u;
     }
+    if (REFINE == 2 && threadIdx.x < 64)
+        reinterpret_cast<float4*>(q_sm)[threadIdx.x] = reinterpret_cast<const float4*>(s.q)[threadIdx.x];
     __syncthreads();
     // the warp's next item of the CTA into `pend` (claimed in list order)
     auto claim = [&]() -> bool {
@@ -1666,6 +1734,9 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
         }
         ++done;
         __syncwarp();  // every lane is done with the stage before it is refilled
+        // REFINE: survivors go to the list soon after they are found, for the
+        // warps refining meanwhile
+        if (REFINE > 0 && nbuf >= LB_EAGER) drain();
     }
     if (stalled) {
         // a copy never completed: flag the query and wait (bounded) for the
@@ -1722,7 +1793,7 @@ __device__ __forceinline__ void q_series_lb_body(const DevIndex& ix, const Query
             par |= ((issued > (uint32_t)t ? (issued - 1u - t) / LB_STAGES + 1u : 0u) & 1u) << t;
         if (!stalled)
             q_refine_claimed<REFINE == 2>(ix, s, k, cta, G, fz + 1, reinterpret_cast<unsigned char*>(wring), wbar,
-                                          par);
+                                          par, q_sm);
     }
 }
 // a single query's scan and refinement (one CTA per SM, cooperative launch:
@@ -2251,9 +2322,29 @@ __device__ __forceinline__ void q_finalize_epilogue(const QueryScratch& s, int k
     }
     for (int i = threadIdx.x; i < k; i += blockDim.x) s.topk[i] = EMPTY_SLOT;
 }
-__global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, QueryScratch s, int k) {
+// the index's mapped block: the control block as the query ended, the answer,
+// and the answer again in the caller's device outputs if it named them
+__device__ __forceinline__ void q_finalize_mail(const QueryScratch& s, int k, QMail* mail) {
+    __syncthreads();  // the answer and the saved totals are written
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        const int64_t i = s.out_idx[t];
+        const float d = s.out_dist[t];
+        mail->idx[t] = i;
+        mail->dist[t] = d;
+        int64_t* oi = mail->out_idx;
+        float* od = mail->out_dist;
+        if (oi) oi[t] = i;
+        if (od) od[t] = d;
+    }
+    static_assert(sizeof(QCtl) % sizeof(unsigned long long) == 0, "the control block is copied in 8-byte words");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(s.ctl);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&mail->ctl);
+    for (int t = threadIdx.x; t < (int)(sizeof(QCtl) / sizeof(unsigned long long)); t += blockDim.x) dst[t] = src[t];
+}
+__global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, QueryScratch s, int k, QMail* mail) {
     q_finalize_body(ix, s, k);
     q_finalize_epilogue(s, k);
+    if (mail) q_finalize_mail(s, k, mail);
 }
 __global__ void __launch_bounds__(FIN_THREADS) bq_finalize_kernel(DevIndex ix, const QueryScratch* ss,
                                                                    int k) {
@@ -2629,9 +2720,10 @@ void free_index_arrays(isax_index* ix, cudaStream_t st) {
         ix->x = nullptr;
     }
     if (ix->rows_borrowed) ix->x = nullptr;  // the caller's array
-    if (ix->h_ctl) {
-        cudaFreeHost(ix->h_ctl);
-        ix->h_ctl = nullptr;
+    if (ix->mail) {
+        cudaFreeHost(ix->mail);
+        ix->mail = nullptr;
+        ix->mail_dev = nullptr;
     }
     void* ptrs[] = {ix->x, ix->sax, ix->orig, ix->leaf_begin, ix->env, ix->leaf_key, ix->bp,
                     ix->tree, ix->tree_root, ix->inv};
@@ -2653,13 +2745,13 @@ namespace {
 
 template <int NV>
 void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st, int mode,
-                          int scan_share) {
+                          int scan_share, QMail* mail) {
     const DevIndex& d = ix->d;
     // the query's share of the SMs (all of them, or a part when queries run side by side)
     const unsigned grid = (unsigned)std::max(1, ix->num_sms / std::max(1, scan_share));
     {
         ISAX_LAUNCH("q_front", st);
-        q_front_kernel<NV><<<grid, FR_THREADS, 0, st>>>(d, s, k, APPROX_NEIGHBORS);
+        q_front_kernel<NV><<<grid, FR_THREADS, 0, st>>>(d, s, k, APPROX_NEIGHBORS, mail);
     }
     const unsigned lb_blocks = (unsigned)std::min<int64_t>((d.L + 255) / 256, (int64_t)ix->num_sms * 8);
     if (mode == QUERY_FLAT) {
@@ -2708,7 +2800,7 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
     }
     {
         ISAX_LAUNCH("q_finalize", st);
-        q_finalize_kernel<<<1, FIN_THREADS, 0, st>>>(d, s, k);
+        q_finalize_kernel<<<1, FIN_THREADS, 0, st>>>(d, s, k, mail);
     }
     ISAX_CUDA_TRY(cudaGetLastError());
 }
@@ -2718,18 +2810,18 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
 // The query's kernels on the given scratch (the index's own, or the
 // allocation-free entry point's built-in array).
 void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaStream_t st, int mode,
-                             int scan_share) {
+                             int scan_share, QMail* mail) {
     const int n = ix->d.n;
     if (n % 128 == 0) {
         switch (n / 128) {
-            case 1: return launch_query_kernels<1>(ix, s, k, st, mode, scan_share);
-            case 2: return launch_query_kernels<2>(ix, s, k, st, mode, scan_share);
-            case 4: return launch_query_kernels<4>(ix, s, k, st, mode, scan_share);
-            case 8: return launch_query_kernels<8>(ix, s, k, st, mode, scan_share);
+            case 1: return launch_query_kernels<1>(ix, s, k, st, mode, scan_share, mail);
+            case 2: return launch_query_kernels<2>(ix, s, k, st, mode, scan_share, mail);
+            case 4: return launch_query_kernels<4>(ix, s, k, st, mode, scan_share, mail);
+            case 8: return launch_query_kernels<8>(ix, s, k, st, mode, scan_share, mail);
             default: break;
         }
     }
-    launch_query_kernels<0>(ix, s, k, st, mode, scan_share);
+    launch_query_kernels<0>(ix, s, k, st, mode, scan_share, mail);
 }
 
 // One exact k-NN query; q is already in ix->qs.q.  Results land in
@@ -2737,9 +2829,10 @@ void launch_query_on_scratch(isax_index* ix, const QueryScratch& s, int k, cudaS
 // launch the query's kernels on st: replay of a captured graph, or direct
 // launches while per-kernel tracing is on
 static void launch_query_graph(isax_index* ix, const QueryScratch& qs, QueryGraphs* g, int k,
-                               cudaStream_t st, int mode = QUERY_MESSI, int scan_share = 1) {
+                               cudaStream_t st, int mode = QUERY_MESSI, int scan_share = 1,
+                               QMail* mail = nullptr) {
     if (profiling_on()) {
-        launch_query_on_scratch(ix, qs, k, st, mode, scan_share);
+        launch_query_on_scratch(ix, qs, k, st, mode, scan_share, mail);
         return;
     }
     const int key = k | (mode << 16) | (scan_share << 20);
@@ -2749,7 +2842,7 @@ static void launch_query_graph(isax_index* ix, const QueryScratch& qs, QueryGrap
         ISAX_CUDA_TRY(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
         cudaGraph_t graph = nullptr;
         try {
-            launch_query_on_scratch(ix, qs, k, g->capture, mode, scan_share);
+            launch_query_on_scratch(ix, qs, k, g->capture, mode, scan_share, mail);
         } catch (...) {
             cudaStreamEndCapture(g->capture, &graph);
             if (graph) cudaGraphDestroy(graph);
@@ -2781,23 +2874,39 @@ void launch_query_graph_ext(isax_index* ix, const QueryScratch& qs, void* g, int
 
 static void launch_query_index(isax_index* ix, int k, cudaStream_t st, int mode) {
     if (!ix->graphs) ix->graphs = new QueryGraphs();
-    launch_query_graph(ix, ix->qs, static_cast<QueryGraphs*>(ix->graphs), k, st, mode);
+    launch_query_graph(ix, ix->qs, static_cast<QueryGraphs*>(ix->graphs), k, st, mode, 1, ix->mail_dev);
+}
+
+void ensure_query_mail(isax_index* ix) {
+    if (ix->mail) return;
+    QMail* h = nullptr;
+    ISAX_CUDA_TRY(cudaHostAlloc((void**)&h, sizeof(QMail), cudaHostAllocMapped));
+    void* dv = nullptr;
+    const cudaError_t e = cudaHostGetDevicePointer(&dv, h, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(h);
+        ISAX_CUDA_TRY(e);
+    }
+    memset(h, 0, sizeof(QMail));
+    ix->mail = h;
+    ix->mail_dev = static_cast<QMail*>(dv);
 }
 
 void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_t st, int mode,
-                  int64_t* out_idx, float* out_dist, bool out_device) {
+                  int64_t* out_idx, float* out_dist, bool out_device, const float* q_src) {
     *reruns = 0;
-    if (!ix->h_ctl) ISAX_CUDA_TRY(cudaMallocHost((void**)&ix->h_ctl, sizeof(QCtl)));
-    const cudaMemcpyKind kout = out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    ensure_query_mail(ix);
+    // the mapped block names where the query is read and the answer written;
+    // the query's kernels leave the control block there
+    QMail* m = ix->mail;
+    m->q_src = q_src ? q_src : ix->qs.q;
+    m->out_idx = out_device ? out_idx : nullptr;
+    m->out_dist = out_device ? out_dist : nullptr;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
     for (int attempt = 0;; ++attempt) {
         launch_query_index(ix, k, st, mode);
-        // the control block into page-locked memory and, if asked, the answer too:
-        // one wait covers both (an overflow below answers again and copies again)
-        ISAX_CUDA_TRY(cudaMemcpyAsync(ix->h_ctl, ix->qs.ctl, sizeof(QCtl), cudaMemcpyDeviceToHost, st));
-        if (out_idx) ISAX_CUDA_TRY(cudaMemcpyAsync(out_idx, ix->qs.out_idx, sizeof(int64_t) * k, kout, st));
-        if (out_dist) ISAX_CUDA_TRY(cudaMemcpyAsync(out_dist, ix->qs.out_dist, sizeof(float) * k, kout, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
-        *ctl_out = *ix->h_ctl;
+        *ctl_out = m->ctl;
         ctl_out->flags |= injected_query_flags();
         if (ctl_out->flags & QF_NONFINITE) throw Error{ISAX_ERR_INVALID_ARG, "query contains a non-finite value"};
         if (ctl_out->flags & QF_STALLED) {
@@ -2816,10 +2925,15 @@ void query_device(isax_index* ix, int k, QCtl* ctl_out, int* reruns, cudaStream_
                 want_s = std::min<uint64_t>(std::max<uint64_t>((uint64_t)ctl_out->surv_count * 2,
                                                                (uint64_t)ix->qs.surv_cap * 4), N);
             alloc_query_scratch(ix, (uint32_t)want_c, (uint32_t)want_s, st, true);  // q moves along
+            if (!q_src) m->q_src = ix->qs.q;  // the query now sits in the new scratch
             ++*reruns;
             continue;
         }
         if (ctl_out->flags & QF_SHORT) throw Error{ISAX_ERR_INTERNAL, "fewer than k candidates survived"};
+        if (!out_device) {
+            if (out_idx) memcpy(out_idx, m->idx, sizeof(int64_t) * k);
+            if (out_dist) memcpy(out_dist, m->dist, sizeof(float) * k);
+        }
         return;
     }
 }

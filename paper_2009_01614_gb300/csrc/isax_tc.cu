@@ -304,10 +304,6 @@ __device__ __forceinline__ void tf_fail(volatile int* abort_flag, uint32_t* err,
     atomicOr(err, code);
 }
 
-// 16-byte global -> shared copy that completes asynchronously (cp.async)
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
-}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // warp-uniform bounded wait
