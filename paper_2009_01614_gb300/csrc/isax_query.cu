@@ -687,10 +687,10 @@ __device__ __forceinline__ void warp_d2_four(const DevIndex& ix, const uint2 (&e
 // warp.  CTA 0 writes the control block and the lower-bound table.  The k best,
 // the candidate count and the refined count start each query cleared: the
 // previous query's q_finalize leaves them so, and a new scratch is allocated so.
-constexpr int FR_THREADS = 256, FR_WARPS = FR_THREADS / 32, FR_ROWS = 4, FR_LEAVES = 4, FR_KEYS = 4;
+constexpr int FR_THREADS = 512, FR_WARPS = FR_THREADS / 32, FR_ROWS = 4, FR_LEAVES = 4, FR_KEYS = 4;
 
 template <int NV>
-__global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryScratch s, int k, int neighbors,
+__global__ void __launch_bounds__(FR_THREADS, 1) q_front_kernel(DevIndex ix, QueryScratch s, int k, int neighbors,
                                                               const QMail* mail) {
     __shared__ float bp[MAX_CARD + 1];
     __shared__ __align__(16) float qv[MAX_LEN];  // read as float4 below
@@ -703,6 +703,20 @@ __global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryS
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = ix.n, m = n / W, card = ix.card;
     const bool lead = blockIdx.x == 0;
+    // the envelopes of this thread's first FR_LEAVES leaves and the descent's
+    // sample key do not depend on the query: they are brought into L2 (and the
+    // sample read) first, while the query is read and summarised
+    const int64_t L = ix.L;
+    const int64_t stride = (int64_t)gridDim.x * FR_THREADS;
+    const int64_t lfirst = (int64_t)blockIdx.x * FR_THREADS + tid;
+#pragma unroll
+    for (int u = 0; u < FR_LEAVES; ++u) {
+        const int64_t l = lfirst + u * stride;
+        if (l < L && (l & 3) == 0) prefetch_l2(ix.env + 2 * l);  // one 128-byte line per four leaves
+    }
+    const int64_t step = (L + FR_THREADS - 1) / FR_THREADS;
+    const int64_t si = (int64_t)tid * step;
+    const unsigned long long sample = si < L ? ix.leaf_key[si] : ~0ull;
     __shared__ const float* qsrc;
     if (tid == 0) {
         bad = 0;
@@ -764,22 +778,11 @@ __global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryS
     }
     __syncthreads();
     const unsigned long long key = ix.tree ? (key_s & 0xFFFF000000000000ull) : key_s;
-    const int64_t L = ix.L;
-    const int64_t step = (L + FR_THREADS - 1) / FR_THREADS;
-    const int64_t si = (int64_t)tid * step;
-    const unsigned long long sample = si < L ? ix.leaf_key[si] : ~0ull;
     {
-        // envelope bound of this thread's leaves (q_leaf_lb's expression)
-        float qp[W];
-        int qs[W];
-#pragma unroll
-        for (int i = 0; i < W; ++i) {
-            qp[i] = qpaa[i];
-            qs[i] = qsym[i];
-        }
+        // envelope bound of this thread's leaves (q_leaf_lb's expression); the
+        // query's PAA and symbols are read from shared memory
         // FR_LEAVES leaves at a time, their envelopes all loaded before any bound
-        const int64_t stride = (int64_t)gridDim.x * FR_THREADS;
-        for (int64_t l0 = (int64_t)blockIdx.x * FR_THREADS + tid; l0 < L; l0 += FR_LEAVES * stride) {
+        for (int64_t l0 = lfirst; l0 < L; l0 += FR_LEAVES * stride) {
             uint4 mn[FR_LEAVES], mx[FR_LEAVES];
 #pragma unroll
             for (int u = 0; u < FR_LEAVES; ++u) {
@@ -789,21 +792,33 @@ __global__ void __launch_bounds__(FR_THREADS) q_front_kernel(DevIndex ix, QueryS
                     mx[u] = ix.env[2 * l + 1];
                 }
             }
-#pragma unroll
+            // one leaf at a time through a short loop body (its code is fetched
+            // once per query: a long unrolled body costs more in instruction
+            // fetch than it saves); a segment inside the envelope adds +0, so
+            // the sum is the per-segment expression's in segment order
+#pragma unroll 1
             for (int u = 0; u < FR_LEAVES; ++u) {
                 const int64_t l = l0 + u * stride;
                 if (l >= L) break;
-                const uint32_t wn[4] = {mn[u].x, mn[u].y, mn[u].z, mn[u].w};
-                const uint32_t wx[4] = {mx[u].x, mx[u].y, mx[u].z, mx[u].w};
-                float lb = 0.0f;
+                uint4 a = mn[0], z = mx[0];
 #pragma unroll
-                for (int i = 0; i < W; ++i) {
-                    const int lo = (wn[i >> 2] >> (8 * (i & 3))) & 255, hi = (wx[i >> 2] >> (8 * (i & 3))) & 255;
-                    if (qs[i] < lo) {
-                        const float d = bp[lo] - qp[i];
-                        lb += (d * d) * mf;
-                    } else if (qs[i] > hi) {
-                        const float d = qp[i] - bp[hi + 1];
+                for (int v = 1; v < FR_LEAVES; ++v)
+                    if (u == v) {
+                        a = mn[v];
+                        z = mx[v];
+                    }
+                float lb = 0.0f;
+#pragma unroll 1
+                for (int g = 0; g < 4; ++g) {
+                    const uint32_t wn = g == 0 ? a.x : g == 1 ? a.y : g == 2 ? a.z : a.w;
+                    const uint32_t wx = g == 0 ? z.x : g == 1 ? z.y : g == 2 ? z.z : z.w;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int i = 4 * g + b;
+                        const int lo = (wn >> (8 * b)) & 255, hi = (wx >> (8 * b)) & 255;
+                        const int qsi = qsym[i];
+                        const float qp = qpaa[i];
+                        const float d = qsi < lo ? bp[lo] - qp : (qsi > hi ? qp - bp[hi + 1] : 0.0f);
                         lb += (d * d) * mf;
                     }
                 }
@@ -2323,16 +2338,18 @@ __device__ __forceinline__ void q_finalize_epilogue(const QueryScratch& s, int k
     for (int i = threadIdx.x; i < k; i += blockDim.x) s.topk[i] = EMPTY_SLOT;
 }
 // the index's mapped block: the control block as the query ended, the answer,
-// and the answer again in the caller's device outputs if it named them
-__device__ __forceinline__ void q_finalize_mail(const QueryScratch& s, int k, QMail* mail) {
+// and the answer again in the caller's device outputs (oi, od: read from the
+// block when the kernel started) if it named them
+__device__ __forceinline__ void q_finalize_mail(const QueryScratch& s, int k, QMail* mail, int64_t* oi,
+                                                float* od) {
     __syncthreads();  // the answer and the saved totals are written
-    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+    static_assert(FIN_THREADS >= MAX_K, "one thread per answer");
+    if ((int)threadIdx.x < k) {
+        const int t = threadIdx.x;
         const int64_t i = s.out_idx[t];
         const float d = s.out_dist[t];
         mail->idx[t] = i;
         mail->dist[t] = d;
-        int64_t* oi = mail->out_idx;
-        float* od = mail->out_dist;
         if (oi) oi[t] = i;
         if (od) od[t] = d;
     }
@@ -2342,9 +2359,17 @@ __device__ __forceinline__ void q_finalize_mail(const QueryScratch& s, int k, QM
     for (int t = threadIdx.x; t < (int)(sizeof(QCtl) / sizeof(unsigned long long)); t += blockDim.x) dst[t] = src[t];
 }
 __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, QueryScratch s, int k, QMail* mail) {
+    // the caller's output pointers are read from host memory now, so the read
+    // has landed when the answer is ready
+    int64_t* oi = nullptr;
+    float* od = nullptr;
+    if (mail && (int)threadIdx.x < k) {
+        oi = mail->out_idx;
+        od = mail->out_dist;
+    }
     q_finalize_body(ix, s, k);
     q_finalize_epilogue(s, k);
-    if (mail) q_finalize_mail(s, k, mail);
+    if (mail) q_finalize_mail(s, k, mail, oi, od);
 }
 __global__ void __launch_bounds__(FIN_THREADS) bq_finalize_kernel(DevIndex ix, const QueryScratch* ss,
                                                                    int k) {
