@@ -2103,7 +2103,7 @@ __global__ void __launch_bounds__(RF_THREADS, 2) bq_refine_half_kernel(DevIndex 
 }
 
 // ---------------------------------------------------------------- q_finalize
-constexpr int FIN_THREADS = 1024, FIN_WARPS = FIN_THREADS / 32, FIN_CAP = 2 * FIN_THREADS, FIN_UNROLL = 4;
+constexpr int FIN_THREADS = 1024, FIN_WARPS = FIN_THREADS / 32, FIN_CAP = 2 * FIN_THREADS, FIN_UNROLL = 8;
 
 __device__ __forceinline__ bool key_greater(unsigned long long a, uint32_t ia, unsigned long long b,
                                             uint32_t ib) {
@@ -2187,16 +2187,19 @@ __device__ __forceinline__ void q_finalize_body(const DevIndex& ix, const QueryS
     __shared__ double sqbuf[FIN_WARPS][32];
     __shared__ int nst, ambiguous;
     QCtl* c = s.ctl;
-    if (c->flags & QF_NONFINITE) return;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the control block's words and the k-th best are read together
+    const uint32_t flags = c->flags;
     const unsigned long long kth = s.topk[k - 1];
+    const double delta = c->delta;
+    const uint32_t cand_base = c->cand_base, cand_count = c->cand_count;
+    if (flags & QF_NONFINITE) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (kth == EMPTY_SLOT) {
         if (tid == 0) c->flags |= QF_SHORT;
         return;
     }
-    const double delta = c->delta;
     const double bound = (double)key_d2(kth) * (1.0 + 3.0 * delta);
-    const uint32_t attempted = c->cand_base + c->cand_count;
+    const uint32_t attempted = cand_base + cand_count;
     const uint32_t M = attempted < s.cand_cap ? attempted : s.cand_cap;
     const int n = ix.n;
     if (tid == 0) nst = 0;
@@ -2358,7 +2361,7 @@ __device__ __forceinline__ void q_finalize_mail(const QueryScratch& s, int k, QM
     unsigned long long* dst = reinterpret_cast<unsigned long long*>(&mail->ctl);
     for (int t = threadIdx.x; t < (int)(sizeof(QCtl) / sizeof(unsigned long long)); t += blockDim.x) dst[t] = src[t];
 }
-__global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, QueryScratch s, int k, QMail* mail) {
+__global__ void __launch_bounds__(FIN_THREADS, 1) q_finalize_kernel(DevIndex ix, QueryScratch s, int k, QMail* mail) {
     // the caller's output pointers are read from host memory now, so the read
     // has landed when the answer is ready
     int64_t* oi = nullptr;
@@ -2371,7 +2374,7 @@ __global__ void __launch_bounds__(FIN_THREADS) q_finalize_kernel(DevIndex ix, Qu
     q_finalize_epilogue(s, k);
     if (mail) q_finalize_mail(s, k, mail, oi, od);
 }
-__global__ void __launch_bounds__(FIN_THREADS) bq_finalize_kernel(DevIndex ix, const QueryScratch* ss,
+__global__ void __launch_bounds__(FIN_THREADS, 1) bq_finalize_kernel(DevIndex ix, const QueryScratch* ss,
                                                                    int k) {
     q_finalize_body(ix, ss[blockIdx.y], k);
     q_finalize_epilogue(ss[blockIdx.y], k);
@@ -2811,8 +2814,9 @@ void launch_query_kernels(isax_index* ix, const QueryScratch& s, int k, cudaStre
         at[0].val.cooperative = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        // n = 256 with the rows in device memory: rows staged by bulk copies;
-        // otherwise read by the warps' own loads
+        // n = 256 with the rows in device memory: rows staged in shared memory
+        // by the warps' asynchronous copies; otherwise (rows in host memory too)
+        // read by the warps' own loads
         const bool half = NV == 2 && !ix->rows_host;
         ISAX_LAUNCH("q_scan_refine", st);
         if (d.card == 256) {
