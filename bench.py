@@ -204,7 +204,7 @@ def host_available_bytes():
 # ------------------------------------------------------------------ roofline
 def kernel_bytes(name, a, launches, acc):
     """Algorithmic bytes of all timed launches of a kernel (None if not modelled).
-    Build kernels run once per step (rs_* once per radix pass); the query
+    Build kernels run once per step (rs_* and os_scatter once per radix pass); the query
     kernels' bytes come from the per-query counters: 16 B per SAX word bounded
     plus 4 B per row value the refinement read outside the approximate answer
     (q_scan_refine: the scan and the refinement in one launch; an abandoned row
@@ -217,6 +217,8 @@ def kernel_bytes(name, a, launches, acc):
         "summarize": N * (row + 16 + 8 + 4),         # rows read; SAX, key, id written
         "rs_scatter": N * (8 + 4) * 2,               # keys and ids read and written
         "rs_hist": N * 8,
+        "os_scatter": N * (8 + 4) * 2,               # one-sweep pass: keys and ids read and written
+        "os_hist": N * 8,                            # every pass's digit histogram in one read of the keys
         "permute_sax": N * (4 + 2 * 16 + 4),         # ids read, SAX words gathered, ids written
     }
     if name in per_launch:

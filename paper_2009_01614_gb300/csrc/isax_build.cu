@@ -514,6 +514,223 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(
     }
 }
 
+// ---------------------------------------------------------- one-sweep passes
+// The same stable LSD sort with a single launch per digit, after the
+// decoupled look-back of Merrill and Garland's single-pass prefix scan as
+// Adinets and Merrill's Onesweep applies it to radix sorting: the digit
+// histograms of all passes come from one read of the keys, and in a pass each
+// CTA takes the next tile by ticket, ranks it, publishes its per-digit counts,
+// then adds up its predecessors' counts walking back until a tile whose
+// inclusive prefix is already published, and publishes its own.  A (tile,
+// digit) status word holds a 2-bit state over a 30-bit count (N < 2^30).
+constexpr int OS_THREADS = 512, OS_ITEMS = 8, OS_TILE = OS_THREADS * OS_ITEMS;
+constexpr int OS_CTAS = 2;  // resident per SM
+constexpr int OS_WARPS = OS_THREADS / 32;
+constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_COUNT = OS_AGG - 1u;
+constexpr uint32_t OS_WAIT = 1u << 20;  // polls of one predecessor's status before the wait gives up
+constexpr int OS_LOOK = 16;             // predecessors' status words read at once in the look-back
+// keys, rows in tile order, rows as loaded (the ranking's digit masks use the keys' room first)
+constexpr size_t OS_SMEM = (size_t)OS_TILE * (sizeof(unsigned long long) + 2 * sizeof(uint32_t));
+static_assert(OS_WARPS * 256 * sizeof(uint32_t) <= OS_TILE * sizeof(unsigned long long), "masks fit the keys' room");
+constexpr int OS_HIST_THREADS = 256, OS_HIST_UNROLL = 4;
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// hist[p][d] += the keys whose digit p (bits shift0 + 8p ..) is d
+__global__ void __launch_bounds__(OS_HIST_THREADS) os_hist_kernel(const unsigned long long* __restrict__ keys,
+                                                                  int64_t N, int shift0, int passes,
+                                                                  uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[8 * 256];
+    for (int i = threadIdx.x; i < 8 * 256; i += OS_HIST_THREADS) h[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * OS_HIST_THREADS;
+    for (int64_t i0 = (int64_t)blockIdx.x * OS_HIST_THREADS + threadIdx.x; i0 < N; i0 += stride * OS_HIST_UNROLL) {
+        unsigned long long k[OS_HIST_UNROLL];
+#pragma unroll
+        for (int u = 0; u < OS_HIST_UNROLL; ++u) {
+            const int64_t i = i0 + u * stride;
+            k[u] = i < N ? keys[i] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < OS_HIST_UNROLL; ++u) {
+            if (i0 + u * stride >= N) break;
+            for (int p = 0; p < passes; ++p)
+                atomicAdd(&h[p * 256 + ((unsigned)(k[u] >> (shift0 + 8 * p)) & 255u)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += OS_HIST_THREADS)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// One digit pass.  ghist: this pass's digit histogram over all keys; status:
+// tiles x 256 words, zero before the pass; ticket: zero before the pass;
+// err: set when a look-back wait gave up (the output is then not sorted).
+// The tile's digit counts are taken and published as soon as its keys are in,
+// and the first 256 threads (one digit each) walk back while any further warps
+// rank their keys; the walk reads OS_LOOK predecessors' words at a time, so that a run of
+// tiles that have published only their own counts costs one round trip per
+// OS_LOOK of them.
+__global__ void __launch_bounds__(OS_THREADS, OS_CTAS) os_scatter_kernel(
+    const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
+    unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, int64_t N, int shift,
+    const uint32_t* __restrict__ ghist, uint32_t* status, uint32_t* ticket, unsigned* err) {
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    unsigned long long* skey = reinterpret_cast<unsigned long long*>(os_smem);
+    uint32_t* sval = reinterpret_cast<uint32_t*>(skey + OS_TILE);
+    uint32_t* sval_in = sval + OS_TILE;
+    uint32_t* masks = reinterpret_cast<uint32_t*>(os_smem);  // [warp][digit] lanes, while ranking
+    __shared__ uint32_t cnt[OS_WARPS][256];  // warp's count, then its digit's tile-local start
+    __shared__ uint32_t hist[256];           // the tile's digit counts
+    __shared__ uint32_t dpos[256];           // output position of the tile's element i of digit d: dpos[d] + i
+    __shared__ unsigned long long scratch[32];
+    __shared__ uint32_t s_tile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    for (int i = threadIdx.x; i < OS_WARPS * 256; i += OS_THREADS) {
+        (&cnt[0][0])[i] = 0;
+        masks[i] = 0;
+    }
+    if (threadIdx.x < 256) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t t = s_tile;
+    const int64_t tbase = (int64_t)t * OS_TILE;
+    const int valid = (int)(N - tbase < OS_TILE ? N - tbase : OS_TILE);
+    // the tile's rows come into shared memory meanwhile (16-byte pieces, the
+    // ragged end one by one)
+    {
+        const int whole = valid / 4;
+        for (int c = threadIdx.x; c < whole; c += OS_THREADS) cp_async16(sval_in + 4 * c, vin + tbase + 4 * c);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        for (int i = whole * 4 + threadIdx.x; i < valid; i += OS_THREADS) sval_in[i] = vin[tbase + i];
+    }
+    const int wbase = warp * (OS_ITEMS * 32);
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long k[OS_ITEMS];
+#pragma unroll
+    for (int it = 0; it < OS_ITEMS; ++it) {
+        const int i = wbase + it * 32 + lane;
+        k[it] = i < valid ? kin[tbase + i] : 0ull;
+    }
+#pragma unroll
+    for (int it = 0; it < OS_ITEMS; ++it)
+        if (wbase + it * 32 + lane < valid) atomicAdd(&hist[(unsigned)(k[it] >> shift) & 255u], 1u);
+    __syncthreads();
+    // ranks inside the warp: the lanes of an item with the same digit find one
+    // another through the warp's digit mask (tile order is warp, item, lane:
+    // stable)
+    uint32_t local[OS_ITEMS];
+    auto rank = [&]() {
+        uint32_t* wm = masks + warp * 256;
+#pragma unroll
+        for (int it = 0; it < OS_ITEMS; ++it) {
+            const bool ok = wbase + it * 32 + lane < valid;
+            const unsigned d = (unsigned)(k[it] >> shift) & 255u;
+            if (ok) atomicOr(&wm[d], 1u << lane);
+            __syncwarp();
+            const unsigned peers = ok ? wm[d] : 0u;
+            __syncwarp();
+            const int leader = ok ? __ffs(peers) - 1 : lane;
+            uint32_t old = 0;
+            if (ok && lane == leader) {
+                old = cnt[warp][d];
+                cnt[warp][d] = old + __popc(peers);
+                wm[d] = 0u;
+            }
+            old = __shfl_sync(FULL, old, leader);
+            local[it] = old + __popc(peers & lt);
+            __syncwarp();
+        }
+    };
+    uint32_t tot = 0, gh = 0, before = 0;
+    if (threadIdx.x < 256) {
+        // the tile's count of digit d published at once, then the digit's
+        // elements in the tiles before this one
+        const int d = threadIdx.x;
+        tot = hist[d];
+        uint32_t* mine = status + (size_t)t * 256 + d;
+        st_relaxed_u32(mine, (t == 0 ? OS_INC : OS_AGG) | tot);
+        gh = ghist[d];
+        int64_t j = (int64_t)t - 1;
+        uint32_t polls = 0;
+        while (j >= 0) {
+            uint32_t w[OS_LOOK];
+#pragma unroll
+            for (int u = 0; u < OS_LOOK; ++u)
+                w[u] = j - u >= 0 ? ld_relaxed_u32(status + (size_t)(j - u) * 256 + d) : OS_INC;
+            bool done = false;
+            int used = 0;  // words taken, in order, up to the first not yet published
+#pragma unroll
+            for (int u = 0; u < OS_LOOK; ++u) {
+                if (done || used < u) continue;
+                if (!(w[u] & (OS_AGG | OS_INC))) continue;
+                before += w[u] & OS_COUNT;
+                used = u + 1;
+                if (w[u] & OS_INC) done = true;
+            }
+            if (done) break;
+            j -= used;
+            if (used == 0) {
+                if (++polls >= OS_WAIT) {
+                    atomicOr(err, 1u);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        if (t > 0) st_relaxed_u32(mine, OS_INC | (before + tot));
+        rank();
+    } else {
+        rank();
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    // the digits' starts: in the whole pass (from the histogram) and in the tile
+    // (one scan of both, packed: a tile's counts sum to at most OS_TILE)
+    unsigned long long all;
+    const unsigned long long ex = block_excl_scan<unsigned long long>(
+        threadIdx.x < 256 ? ((unsigned long long)gh << 32) | tot : 0ull, 0ull, OpAdd<unsigned long long>(), scratch,
+        &all);
+    if (threadIdx.x < 256) {
+        const int d = threadIdx.x;
+        uint32_t run = (uint32_t)ex;  // each warp's first position of digit d in the tile
+#pragma unroll
+        for (int w = 0; w < OS_WARPS; ++w) {
+            const uint32_t c = cnt[w][d];
+            cnt[w][d] = run;
+            run += c;
+        }
+        dpos[d] = (uint32_t)(ex >> 32) + before - (uint32_t)ex;
+    }
+    __syncthreads();
+    // the tile reordered by digit in shared memory
+#pragma unroll
+    for (int it = 0; it < OS_ITEMS; ++it) {
+        const int i = wbase + it * 32 + lane;
+        if (i < valid) {
+            const uint32_t lp = cnt[warp][(unsigned)(k[it] >> shift) & 255u] + local[it];
+            skey[lp] = k[it];
+            sval[lp] = sval_in[i];
+        }
+    }
+    __syncthreads();
+    // written out so that consecutive threads write consecutive positions of
+    // each digit's run
+    for (int i = threadIdx.x; i < valid; i += OS_THREADS) {
+        const unsigned long long key = skey[i];
+        const uint32_t gpos = dpos[(unsigned)(key >> shift) & 255u] + (uint32_t)i;
+        kout[gpos] = key;
+        vout[gpos] = sval[i];
+    }
+}
+
 // ============================================================== leaf formation
 __device__ __forceinline__ int lcp_bits(unsigned long long a, unsigned long long b, int keybits) {
     int l = (a == b) ? 64 : __clzll((long long)(a ^ b));
@@ -1094,10 +1311,51 @@ inline unsigned grid_for(int64_t work, int per_block, int num_sms, int max_per_s
     return (unsigned)std::max<int64_t>(1, std::min(b, cap));
 }
 
+uint32_t read_u32(const uint32_t* p, cudaStream_t st) {
+    uint32_t v = 0;
+    ISAX_CUDA_TRY(cudaMemcpyAsync(&v, p, sizeof v, cudaMemcpyDeviceToHost, st));
+    ISAX_CUDA_TRY(cudaStreamSynchronize(st));
+    return v;
+}
+
 // Stable LSD radix sort of (key, row) pairs on `passes` 8-bit digits, the
-// lowest at bit `shift0`; the sorted pairs end in kA / vA.
+// lowest at bit `shift0`; the sorted pairs end in kA / vA.  One-sweep passes
+// for N < 2^30, else three-phase ones.  A look-back wait that gave up sets
+// *err and ends the build here, before anything reads the unsorted rows.
 void radix_sort(unsigned long long*& kA, uint32_t*& vA, unsigned long long*& kB, uint32_t*& vB, int64_t N,
-                int shift0, int passes, TempPool& tmp, cudaStream_t st) {
+                int shift0, int passes, TempPool& tmp, cudaStream_t st, unsigned* err, int num_sms) {
+    if (N <= 0 || passes <= 0) return;
+    if (N < ((int64_t)1 << 30) && passes <= 8) {
+        const int64_t tiles = (N + OS_TILE - 1) / OS_TILE;
+        const size_t words = (size_t)passes * 256 + (size_t)passes + (size_t)passes * tiles * 256;
+        uint32_t* ws = tmp.get<uint32_t>(words);
+        uint32_t* hist = ws;
+        uint32_t* tickets = ws + (size_t)passes * 256;
+        uint32_t* status = tickets + passes;
+        ISAX_CUDA_TRY(cudaMemsetAsync(ws, 0, words * sizeof(uint32_t), st));
+        {
+            ISAX_LAUNCH("os_hist", st);
+            os_hist_kernel<<<grid_for(N, OS_HIST_THREADS * OS_HIST_UNROLL, num_sms, 8), OS_HIST_THREADS, 0, st>>>(
+                kA, N, shift0, passes, hist);
+        }
+        static std::once_flag attr_once;
+        std::call_once(attr_once, [] {
+            ISAX_CUDA_TRY(cudaFuncSetAttribute(os_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)OS_SMEM));
+        });
+        for (int pass = 0; pass < passes; ++pass) {
+            ISAX_LAUNCH("os_scatter", st);
+            os_scatter_kernel<<<(unsigned)tiles, OS_THREADS, OS_SMEM, st>>>(
+                kA, vA, kB, vB, N, shift0 + 8 * pass, hist + (size_t)pass * 256, status + (size_t)pass * tiles * 256,
+                tickets + pass, err);
+            ISAX_CUDA_TRY(cudaGetLastError());
+            std::swap(kA, kB);
+            std::swap(vA, vB);
+        }
+        tmp.release(ws);
+        if (read_u32(err, st)) throw Error{ISAX_ERR_TIMEOUT, "a look-back wait of the radix sort gave up"};
+        return;
+    }
     const int64_t tiles = (N + RS_TILE - 1) / RS_TILE;
     uint32_t* hist = tmp.get<uint32_t>((size_t)256 * tiles);
     uint32_t* sums = tmp.get<uint32_t>(scan_sums_len(256 * tiles));
@@ -1118,13 +1376,6 @@ void radix_sort(unsigned long long*& kA, uint32_t*& vA, unsigned long long*& kB,
     }
     tmp.release(hist);
     tmp.release(sums);
-}
-
-uint32_t read_u32(const uint32_t* p, cudaStream_t st) {
-    uint32_t v = 0;
-    ISAX_CUDA_TRY(cudaMemcpyAsync(&v, p, sizeof v, cudaMemcpyDeviceToHost, st));
-    ISAX_CUDA_TRY(cudaStreamSynchronize(st));
-    return v;
 }
 
 // Leaves of the round-robin split, cut top-down from the sorted keys kA; fills
@@ -1195,8 +1446,8 @@ uint32_t round_robin_leaves(isax_index* ix, TempPool& tmp, const unsigned long l
 // ix->tree, ix->tree_root, ix->tree_nodes and returns the number of leaves.
 uint32_t balanced_leaves(isax_index* ix, TempPool& tmp, const uint4* sax_tmp, unsigned long long*& kA,
                          unsigned long long*& kB, uint32_t*& vA, uint32_t*& vB, int64_t N, int cbits,
-                         int leaf_size, int num_sms, cudaStream_t st) {
-    radix_sort(kA, vA, kB, vB, N, 48, 2, tmp, st);  // the root key: top 16 bits
+                         int leaf_size, int num_sms, cudaStream_t st, unsigned* sort_err) {
+    radix_sort(kA, vA, kB, vB, N, 48, 2, tmp, st, sort_err, num_sms);  // the root key: top 16 bits
 
     const unsigned g_n = grid_for(N, 256, num_sms);
     uint32_t* zf = tmp.get<uint32_t>(N);
@@ -1386,8 +1637,9 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         unsigned long long* kB = tmp.get<unsigned long long>(N);
         uint32_t* vA = tmp.get<uint32_t>(N);
         uint32_t* vB = tmp.get<uint32_t>(N);
-        unsigned* misc = tmp.get<unsigned>(4);  // maxabs bits, nonfinite, max_leaf
-        ISAX_CUDA_TRY(cudaMemsetAsync(misc, 0, 4 * sizeof(unsigned), st));
+        // maxabs bits, nonfinite, max_leaf, permutation wait gave up, sort wait gave up
+        unsigned* misc = tmp.get<unsigned>(5);
+        ISAX_CUDA_TRY(cudaMemsetAsync(misc, 0, 5 * sizeof(unsigned), st));
         if (chunked_host) {
             ChunkCopier cp(st);
             float* xd = ix->x;
@@ -1407,9 +1659,9 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         const bool balanced = (mem_flags & ISAX_BUILD_SPLIT_BALANCED) != 0;
         uint32_t L = 0;
         if (balanced) {
-            L = balanced_leaves(ix, tmp, sax_tmp, kA, kB, vA, vB, N, cbits, leaf_size, num_sms, st);
+            L = balanced_leaves(ix, tmp, sax_tmp, kA, kB, vA, vB, N, cbits, leaf_size, num_sms, st, misc + 4);
         } else {
-            radix_sort(kA, vA, kB, vB, N, 64 - keybits, keybits / 8, tmp, st);
+            radix_sort(kA, vA, kB, vB, N, 64 - keybits, keybits / 8, tmp, st, misc + 4, num_sms);
             L = round_robin_leaves(ix, tmp, kA, N, leaf_size, keybits, num_sms, st);
         }
 
@@ -1463,11 +1715,12 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         ISAX_CUDA_TRY(cudaGetLastError());
         }
 
-        unsigned hm[4];
+        unsigned hm[5];
         ISAX_CUDA_TRY(cudaMemcpyAsync(hm, misc, sizeof hm, cudaMemcpyDeviceToHost, st));
         ISAX_CUDA_TRY(cudaStreamSynchronize(st));
         if (hm[1]) throw Error{ISAX_ERR_INVALID_ARG, "series contains a non-finite value"};
         if (hm[3]) throw Error{ISAX_ERR_TIMEOUT, "a bulk-copy wait of the permutation gave up"};
+        if (hm[4]) throw Error{ISAX_ERR_TIMEOUT, "a look-back wait of the radix sort gave up"};
         float maxabs;
         memcpy(&maxabs, &hm[0], sizeof maxabs);
 
