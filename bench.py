@@ -930,10 +930,10 @@ def main():
     Qh, src = make_queries(a, world)
     Qd = torch.from_numpy(Qh).cuda()
     torch.cuda.synchronize()
-    # the end-to-end leg's page-locked host copy of the collection, taken now while
-    # host memory is fresh (page-locked later, after other large host allocations,
-    # it copied to the device measurably slower).  Every rank on this host holds one:
-    # the leg runs only if they all fit, decided alike on every rank.
+    # the end-to-end leg's page-locked host copy of the collection (made after the
+    # timed steps, before the host-rows leg page-locks 102 GB of its own: made after
+    # that, it copied to the device measurably slower).  Every rank on this host
+    # holds one: the leg runs only if they all fit, decided alike on every rank.
     Xh = None
     e2e_skip = None
     if not a.no_e2e:
@@ -947,12 +947,6 @@ def main():
         if not fits:
             e2e_skip = ("host memory available %.0f GB < %d ranks x %.0f GB of page-locked collection"
                         % ((avail or 0) / 1e9, local_world, N * n * 4 * 1.15 / 1e9))
-    if not a.no_e2e and e2e_skip is None:
-        Xh = torch.empty((N, n), dtype=torch.float32, pin_memory=True)
-        for r0 in range(0, N, 1 << 22):
-            c = min(1 << 22, N - r0)
-            Xh[r0:r0 + c].copy_(X[r0:r0 + c])
-        torch.cuda.synchronize()
 
     lat_ms = []
     stats_acc = {"series_lb": 0, "series_refined": 0, "approx_series": 0, "leaves_queued": 0,
@@ -1120,6 +1114,14 @@ def main():
     if e2e_skip is not None:
         out["e2e"] = {"skipped": e2e_skip}
     if not a.no_e2e and e2e_skip is None:
+        # the page-locked host copy of the collection is made only now: made
+        # before the timed steps, a build right after its fill once took 95 ms
+        # instead of 31
+        Xh = torch.empty((N, n), dtype=torch.float32, pin_memory=True)
+        for r0 in range(0, N, 1 << 22):
+            c = min(1 << 22, N - r0)
+            Xh[r0:r0 + c].copy_(X[r0:r0 + c])
+        torch.cuda.synchronize()
         del Qd
         del X
         torch.cuda.synchronize()
