@@ -491,27 +491,28 @@ class Index:
         if (batch and (len(shape) != 2 or shape[1] != self.n)) or (not batch and shape[-1] != self.n):
             raise ValueError("query length must be %d" % self.n)
         st = _stream_of(keep, stream)
+        oshape = (B, k) if batch else (k,)
         if on_dev:
             import torch
-            idx = torch.empty((B, k), dtype=torch.int64, device=keep.device)
-            dist = torch.empty((B, k), dtype=torch.float32, device=keep.device)
+            idx = torch.empty(oshape, dtype=torch.int64, device=keep.device)
+            dist = torch.empty(oshape, dtype=torch.float32, device=keep.device)
             ip, dp, flags = idx.data_ptr(), dist.data_ptr(), MEM_INPUT_DEVICE | MEM_OUTPUT_DEVICE
         else:
             import numpy as np
-            idx = np.empty((B, k), np.int64)
-            dist = np.empty((B, k), np.float32)
+            idx = np.empty(oshape, np.int64)
+            dist = np.empty(oshape, np.float32)
             ip, dp, flags = idx.ctypes.data, dist.ctypes.data, 0
-        stats = (QueryStats * B)()
+        # the counters only when asked for (NULL otherwise)
+        stats = (QueryStats * B)() if want_stats else None
+        one = stats[0] if want_stats else None
         if flat:
-            isax_query_knn_flat(self._h, ptr, k, flags, ip, dp, stats[0], st)
+            isax_query_knn_flat(self._h, ptr, k, flags, ip, dp, one, st)
         elif batch == "bf16":
             isax_query_knn_batch_bf16(self._h, ptr, B, k, flags, ip, dp, stats, st)
         elif batch:
             isax_query_knn_batch(self._h, ptr, B, k, flags, ip, dp, stats, st)
         else:
-            isax_query_knn(self._h, ptr, k, flags, ip, dp, stats[0], st)
-        if not batch:
-            idx, dist = idx[0], dist[0]
+            isax_query_knn(self._h, ptr, k, flags, ip, dp, one, st)
         if want_stats:
             s = [x.as_dict() for x in stats]
             return idx, dist, (s if batch else s[0])
