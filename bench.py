@@ -217,7 +217,10 @@ def kernel_bytes(name, a, launches, acc):
         "summarize": N * (row + 16 + 8 + 4),         # rows read; SAX, key, id written
         "rs_scatter": N * (8 + 4) * 2,               # keys and ids read and written
         "rs_hist": N * 8,
-        "os_scatter": N * (8 + 4) * 2,               # one-sweep pass: keys and ids read and written
+        # one-sweep pass: keys and ids read and written; the last of the 8 passes
+        # of a build with the rows in place also gathers the SAX words and writes
+        # them and the ids in leaf order (averaged over the 8 launches)
+        "os_scatter": N * (8 + 4) * 2 + N * (16 + 16 + 4) // 8,
         "os_hist": N * 8,                            # every pass's digit histogram in one read of the keys
         "permute_sax": N * (4 + 2 * 16 + 4),         # ids read, SAX words gathered, ids written
     }

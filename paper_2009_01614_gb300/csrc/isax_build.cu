@@ -573,6 +573,10 @@ __global__ void __launch_bounds__(OS_HIST_THREADS) os_hist_kernel(const unsigned
 // One digit pass.  ghist: this pass's digit histogram over all keys; status:
 // tiles x 256 words, zero before the pass; ticket: zero before the pass;
 // err: set when a look-back wait gave up (the output is then not sorted).
+// sax_dst (the last pass of a build whose rows stay in input order, else
+// null): each pair's SAX word sax_src[row] and its row id also go to the
+// pair's final position in sax_dst / orig_dst, the random 16-byte gathers
+// overlapping the pass instead of running as a launch of their own.
 // The tile's digit counts are taken and published as soon as its keys are in,
 // and the first 256 threads (one digit each) walk back while any further warps
 // rank their keys; the walk reads OS_LOOK predecessors' words at a time, so that a run of
@@ -581,7 +585,8 @@ __global__ void __launch_bounds__(OS_HIST_THREADS) os_hist_kernel(const unsigned
 __global__ void __launch_bounds__(OS_THREADS, OS_CTAS) os_scatter_kernel(
     const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
     unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, int64_t N, int shift,
-    const uint32_t* __restrict__ ghist, uint32_t* status, uint32_t* ticket, unsigned* err) {
+    const uint32_t* __restrict__ ghist, uint32_t* status, uint32_t* ticket, unsigned* err,
+    const uint4* __restrict__ sax_src, uint4* __restrict__ sax_dst, uint32_t* __restrict__ orig_dst) {
     extern __shared__ __align__(16) unsigned char os_smem[];
     unsigned long long* skey = reinterpret_cast<unsigned long long*>(os_smem);
     uint32_t* sval = reinterpret_cast<uint32_t*>(skey + OS_TILE);
@@ -692,6 +697,14 @@ __global__ void __launch_bounds__(OS_THREADS, OS_CTAS) os_scatter_kernel(
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
+    // the last pass's SAX words requested into L2 now, read at write-out
+    if (sax_dst) {
+#pragma unroll
+        for (int u = 0; u < OS_ITEMS; ++u) {
+            const int i = threadIdx.x + u * OS_THREADS;
+            if (i < valid) prefetch_l2(sax_src + sval_in[i]);
+        }
+    }
     // the digits' starts: in the whole pass (from the histogram) and in the tile
     // (one scan of both, packed: a tile's counts sum to at most OS_TILE)
     unsigned long long all;
@@ -723,6 +736,28 @@ __global__ void __launch_bounds__(OS_THREADS, OS_CTAS) os_scatter_kernel(
     __syncthreads();
     // written out so that consecutive threads write consecutive positions of
     // each digit's run
+    if (sax_dst) {
+        // (the gathers of all the thread's pairs issued before any store)
+        uint4 w[OS_ITEMS];
+#pragma unroll
+        for (int u = 0; u < OS_ITEMS; ++u) {
+            const int i = threadIdx.x + u * OS_THREADS;
+            if (i < valid) w[u] = sax_src[sval[i]];
+        }
+#pragma unroll
+        for (int u = 0; u < OS_ITEMS; ++u) {
+            const int i = threadIdx.x + u * OS_THREADS;
+            if (i < valid) {
+                const unsigned long long key = skey[i];
+                const uint32_t gpos = dpos[(unsigned)(key >> shift) & 255u] + (uint32_t)i, row = sval[i];
+                kout[gpos] = key;
+                vout[gpos] = row;
+                sax_dst[gpos] = w[u];
+                orig_dst[gpos] = row;
+            }
+        }
+        return;
+    }
     for (int i = threadIdx.x; i < valid; i += OS_THREADS) {
         const unsigned long long key = skey[i];
         const uint32_t gpos = dpos[(unsigned)(key >> shift) & 255u] + (uint32_t)i;
@@ -1322,9 +1357,12 @@ uint32_t read_u32(const uint32_t* p, cudaStream_t st) {
 // lowest at bit `shift0`; the sorted pairs end in kA / vA.  One-sweep passes
 // for N < 2^30, else three-phase ones.  A look-back wait that gave up sets
 // *err and ends the build here, before anything reads the unsorted rows.
-void radix_sort(unsigned long long*& kA, uint32_t*& vA, unsigned long long*& kB, uint32_t*& vB, int64_t N,
-                int shift0, int passes, TempPool& tmp, cudaStream_t st, unsigned* err, int num_sms) {
-    if (N <= 0 || passes <= 0) return;
+// With sax_dst, a one-sweep sort's last pass also writes sax_dst[i] =
+// sax_src[vA[i]] and orig_dst[i] = vA[i]; returns whether it did.
+bool radix_sort(unsigned long long*& kA, uint32_t*& vA, unsigned long long*& kB, uint32_t*& vB, int64_t N,
+                int shift0, int passes, TempPool& tmp, cudaStream_t st, unsigned* err, int num_sms,
+                const uint4* sax_src = nullptr, uint4* sax_dst = nullptr, uint32_t* orig_dst = nullptr) {
+    if (N <= 0 || passes <= 0) return false;
     if (N < ((int64_t)1 << 30) && passes <= 8) {
         const int64_t tiles = (N + OS_TILE - 1) / OS_TILE;
         const size_t words = (size_t)passes * 256 + (size_t)passes + (size_t)passes * tiles * 256;
@@ -1345,16 +1383,17 @@ void radix_sort(unsigned long long*& kA, uint32_t*& vA, unsigned long long*& kB,
         });
         for (int pass = 0; pass < passes; ++pass) {
             ISAX_LAUNCH("os_scatter", st);
+            const bool last = pass + 1 == passes;
             os_scatter_kernel<<<(unsigned)tiles, OS_THREADS, OS_SMEM, st>>>(
                 kA, vA, kB, vB, N, shift0 + 8 * pass, hist + (size_t)pass * 256, status + (size_t)pass * tiles * 256,
-                tickets + pass, err);
+                tickets + pass, err, sax_src, last ? sax_dst : nullptr, orig_dst);
             ISAX_CUDA_TRY(cudaGetLastError());
             std::swap(kA, kB);
             std::swap(vA, vB);
         }
         tmp.release(ws);
         if (read_u32(err, st)) throw Error{ISAX_ERR_TIMEOUT, "a look-back wait of the radix sort gave up"};
-        return;
+        return sax_dst != nullptr;
     }
     const int64_t tiles = (N + RS_TILE - 1) / RS_TILE;
     uint32_t* hist = tmp.get<uint32_t>((size_t)256 * tiles);
@@ -1376,6 +1415,7 @@ void radix_sort(unsigned long long*& kA, uint32_t*& vA, unsigned long long*& kB,
     }
     tmp.release(hist);
     tmp.release(sums);
+    return false;
 }
 
 // Leaves of the round-robin split, cut top-down from the sorted keys kA; fills
@@ -1656,18 +1696,24 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
         }
 
         // leaves: the round-robin split of the sorted keys, or ADS+ node splitting
+        // (the index's SAX words and row ids: when the rows stay in input order,
+        // the sort's last pass puts them in leaf order itself)
         const bool balanced = (mem_flags & ISAX_BUILD_SPLIT_BALANCED) != 0;
+        ix->sax = static_cast<uint4*>(dev_alloc((size_t)N * sizeof(uint4), st));
+        ix->orig = static_cast<uint32_t*>(dev_alloc((size_t)N * sizeof(uint32_t), st));
         uint32_t L = 0;
+        bool sax_placed = false;
         if (balanced) {
             L = balanced_leaves(ix, tmp, sax_tmp, kA, kB, vA, vB, N, cbits, leaf_size, num_sms, st, misc + 4);
         } else {
-            radix_sort(kA, vA, kB, vB, N, 64 - keybits, keybits / 8, tmp, st, misc + 4, num_sms);
+            const bool gather = in_place || chunked_host;
+            sax_placed = radix_sort(kA, vA, kB, vB, N, 64 - keybits, keybits / 8, tmp, st, misc + 4, num_sms,
+                                    gather ? sax_tmp : nullptr, gather ? ix->sax : nullptr,
+                                    gather ? ix->orig : nullptr);
             L = round_robin_leaves(ix, tmp, kA, N, leaf_size, keybits, num_sms, st);
         }
 
         // permute rows and SAX words into leaf order
-        ix->sax = static_cast<uint4*>(dev_alloc((size_t)N * sizeof(uint4), st));
-        ix->orig = static_cast<uint32_t*>(dev_alloc((size_t)N * sizeof(uint32_t), st));
         if (in_place || chunked_host) {
             // the rows stay in the input's order (the caller's array, or the device copy
             // of a host input), read by original id
@@ -1676,8 +1722,10 @@ isax_index* build_index_impl(const float* series, int64_t N, int n, int card, in
                 ix->rows_in_place = true;
                 ix->rows_borrowed = true;
             }
-            ISAX_LAUNCH("permute_sax", st);
-            permute_sax_kernel<<<num_sms * 8, 256, 0, st>>>(vA, N, sax_tmp, ix->sax, ix->orig);
+            if (!sax_placed) {
+                ISAX_LAUNCH("permute_sax", st);
+                permute_sax_kernel<<<num_sms * 8, 256, 0, st>>>(vA, N, sax_tmp, ix->sax, ix->orig);
+            }
         } else if (rows_host) {
             // leaf-ordered rows in pinned host memory (unified addressing: the host
             // pointer is valid on the device)

@@ -138,13 +138,16 @@ def keys_of(sax, cbits):
     return key
 
 
+@pytest.mark.parametrize("in_place", [False, True])
 @pytest.mark.parametrize("N,leaf,card", [(30000, 100, 256), (5000, 7, 256), (20000, 500, 16),
                                          (4001, 2000, 256), (1, 5, 256), (3000, 1, 4)])
-def test_build_invariants(N, leaf, card):
+def test_build_invariants(N, leaf, card, in_place):
+    """Leaf order, envelopes and leaf boundaries; with the rows read in place the
+    SAX words and row ids are put in leaf order by the radix sort's last pass."""
     n = 128
     X = datagen.rows("walk", 4, 0, N, n)
     X[N // 3: N // 3 + min(N // 4, 2 * leaf + 3)] = X[0]  # a long run of identical words
-    ix = pkg.Index(torch.from_numpy(X).cuda(), cardinality=card, leaf_size=leaf)
+    ix = pkg.Index(torch.from_numpy(X).cuda(), cardinality=card, leaf_size=leaf, rows_in_place=in_place)
     ex = ix.export()
     orig = ex["orig"].astype(np.int64)
     assert np.array_equal(np.sort(orig), np.arange(N))
