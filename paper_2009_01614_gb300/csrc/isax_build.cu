@@ -697,14 +697,6 @@ __global__ void __launch_bounds__(OS_THREADS, OS_CTAS) os_scatter_kernel(
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    // the last pass's SAX words requested into L2 now, read at write-out
-    if (sax_dst) {
-#pragma unroll
-        for (int u = 0; u < OS_ITEMS; ++u) {
-            const int i = threadIdx.x + u * OS_THREADS;
-            if (i < valid) prefetch_l2(sax_src + sval_in[i]);
-        }
-    }
     // the digits' starts: in the whole pass (from the histogram) and in the tile
     // (one scan of both, packed: a tile's counts sum to at most OS_TILE)
     unsigned long long all;
