@@ -833,43 +833,82 @@ __global__ void __launch_bounds__(LF_THREADS) lf_blockmax_kernel(const uint8_t* 
 // root when that node, the run of keys sharing c[i] bits around i, holds more
 // than L series, i.e. some window of L+1 consecutive keys containing i-1 and
 // i shares c[i] bits: max(a[i-L .. i-1]) >= c[i].
-__global__ void lf_flags_kernel(const uint8_t* __restrict__ c, const uint8_t* __restrict__ P,
-                                const uint8_t* __restrict__ S, int64_t N, int64_t L, int keybits,
-                                uint32_t* __restrict__ flags) {
-    const int64_t NA = N > L ? N - L : 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t f;
-        if (i == 0) {
-            f = 1;
-        } else {
-            int ci = c[i];
-            if (ci < ROOT_BITS) {
-                f = 1;
-            } else if (ci >= keybits) {
-                f = 0;
-            } else {
-                int64_t lo = i - L > 0 ? i - L : 0;
-                int64_t hi = std::min(i - 1, NA - 1);
-                int M = 0;
-                if (NA > 0 && lo <= hi) {
-                    if (lo / L == hi / L)
-                        M = (lo % L == 0) ? P[hi] : S[lo];
-                    else
-                        M = max(S[lo], P[hi]);
-                }
-                f = M >= ci ? 1u : 0u;
-            }
-        }
-        flags[i] = f;
-    }
+// 1 if series i starts a leaf: the first series, a new root key, or a split
+// at depth ci (the common prefix with the previous series) that the window of
+// L series ending at i - 1 does not cover (its common prefix M is >= ci).
+// P / S: prefix / suffix maxima of a inside blocks of L (N < 2^32: 32-bit
+// index arithmetic, one division).
+__device__ __forceinline__ uint32_t leaf_start_flag(const uint8_t* __restrict__ c, const uint8_t* __restrict__ P,
+                                                    const uint8_t* __restrict__ S, uint32_t i, uint32_t N,
+                                                    uint32_t L, int keybits) {
+    if (i == 0) return 1u;
+    const int ci = c[i];
+    if (ci < ROOT_BITS) return 1u;
+    if (ci >= keybits) return 0u;
+    const uint32_t NA = N > L ? N - L : 0u;
+    if (NA == 0) return 0u;  // M = 0 < ci
+    const uint32_t lo = i > L ? i - L : 0u;
+    const uint32_t hi = i - 1 < NA - 1 ? i - 1 : NA - 1;
+    if (lo > hi) return 0u;
+    const uint32_t q = lo / L, r = lo - q * L;
+    int M;
+    if (hi < (q + 1) * L)  // lo and hi in one block
+        M = r == 0 ? P[hi] : S[lo];
+    else
+        M = max(S[lo], P[hi]);
+    return M >= ci ? 1u : 0u;
 }
 
-__global__ void lf_compact_kernel(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
-                                  int64_t N, uint32_t* __restrict__ starts, uint32_t count) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x)
-        if (flags[i]) starts[pos[i]] = (uint32_t)i;
+// Leaf starts in two passes over tiles of LF_TILE series, series i0 + 256 j + t
+// to thread t (coalesced byte loads): the number of starts of each tile, then
+// (after a scan of those counts) the starts themselves, written in order.
+constexpr int LF_PER = 16, LF_TILE = 256 * LF_PER;
+__global__ void __launch_bounds__(256) lf_count_kernel(const uint8_t* __restrict__ c, const uint8_t* __restrict__ P,
+                                                       const uint8_t* __restrict__ S, int64_t N, int64_t L,
+                                                       int keybits, uint32_t* __restrict__ tile_count) {
+    __shared__ uint32_t scratch[32];
+    const int64_t i0 = (int64_t)blockIdx.x * LF_TILE + threadIdx.x;
+    uint32_t n = 0;
+#pragma unroll
+    for (int j = 0; j < LF_PER; ++j)
+        if (i0 + 256 * j < N) n += leaf_start_flag(c, P, S, (uint32_t)(i0 + 256 * j), (uint32_t)N, (uint32_t)L, keybits);
+    uint32_t tot;
+    block_excl_scan<uint32_t>(n, 0u, OpAdd<uint32_t>(), scratch, &tot);
+    if (threadIdx.x == 0) tile_count[blockIdx.x] = tot;
+}
+__global__ void __launch_bounds__(256) lf_emit_kernel(const uint8_t* __restrict__ c, const uint8_t* __restrict__ P,
+                                                      const uint8_t* __restrict__ S, int64_t N, int64_t L,
+                                                      int keybits, const uint32_t* __restrict__ tile_off,
+                                                      uint32_t* __restrict__ starts, uint32_t count) {
+    __shared__ uint32_t wc[LF_PER * 8 + 1];  // starts per (j, warp), then their exclusive prefix
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i0 = (int64_t)blockIdx.x * LF_TILE + threadIdx.x;
+    uint32_t f = 0;  // bit j: series i0 + 256 j starts a leaf
+#pragma unroll
+    for (int j = 0; j < LF_PER; ++j) {
+        const bool s = i0 + 256 * j < N &&
+                       leaf_start_flag(c, P, S, (uint32_t)(i0 + 256 * j), (uint32_t)N, (uint32_t)L, keybits);
+        if (s) f |= 1u << j;
+        const unsigned m = __ballot_sync(FULL, s);
+        if (lane == 0) wc[j * 8 + warp] = __popc(m);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;  // series order is j major, then warp, then lane
+        for (int q = 0; q < LF_PER * 8; ++q) {
+            const uint32_t v = wc[q];
+            wc[q] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    const uint32_t base = tile_off[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < LF_PER; ++j) {
+        const unsigned m = __ballot_sync(FULL, (f >> j) & 1u);
+        if ((f >> j) & 1u)
+            starts[base + wc[j * 8 + warp] + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(i0 + 256 * j);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) starts[count] = (uint32_t)N;
 }
 
@@ -1038,15 +1077,24 @@ __global__ void __launch_bounds__(256) envelope_kernel(const uint4* __restrict__
                                                        unsigned long long* __restrict__ leaf_key,
                                                        unsigned long long key_mask,
                                                        uint32_t* __restrict__ max_leaf) {
+    __shared__ uint32_t big[8];
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t biggest = 0;  // the largest leaf this warp saw (one atomic per block at the end)
     for (int64_t l = gw; l < L; l += nw) {
         const uint32_t b = leaf_begin[l], e = leaf_begin[l + 1];
         ISAX_CHECK(b < e, CHK_LEAF_RANGE);
         uint4 mn = make_uint4(FULL, FULL, FULL, FULL), mx = make_uint4(0, 0, 0, 0);
-        for (uint32_t r = b + lane; r < e; r += 32) {
-            uint4 s = sax[r];
+        // four words per lane in flight
+        uint32_t r = b + lane;
+        for (; r + 96 < e; r += 128) {
+            const uint4 s0 = sax[r], s1 = sax[r + 32], s2 = sax[r + 64], s3 = sax[r + 96];
+            mn = vmin4(vmin4(mn, s0), vmin4(s1, vmin4(s2, s3)));
+            mx = vmax4(vmax4(mx, s0), vmax4(s1, vmax4(s2, s3)));
+        }
+        for (; r < e; r += 32) {
+            const uint4 s = sax[r];
             mn = vmin4(mn, s);
             mx = vmax4(mx, s);
         }
@@ -1059,8 +1107,15 @@ __global__ void __launch_bounds__(256) envelope_kernel(const uint4* __restrict__
             env[2 * l] = mn;
             env[2 * l + 1] = mx;
             leaf_key[l] = keys[b] & key_mask;
-            atomicMax(max_leaf, e - b);
         }
+        biggest = max(biggest, e - b);
+    }
+    if (lane == 0) big[threadIdx.x >> 5] = biggest;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t m = 0;
+        for (int w = 0; w < 8; ++w) m = max(m, big[w]);
+        if (m) atomicMax(max_leaf, m);
     }
 }
 
@@ -1420,9 +1475,10 @@ uint32_t round_robin_leaves(isax_index* ix, TempPool& tmp, const unsigned long l
     uint8_t* a = tmp.get<uint8_t>(NA);
     uint8_t* P = tmp.get<uint8_t>(NA);
     uint8_t* S = tmp.get<uint8_t>(NA);
-    uint32_t* flags = tmp.get<uint32_t>(N);
-    uint32_t* pos = tmp.get<uint32_t>(N);
-    uint32_t* sums = tmp.get<uint32_t>(scan_sums_len(N));
+    const int64_t tiles = (N + LF_TILE - 1) / LF_TILE;
+    uint32_t* tcount = tmp.get<uint32_t>(tiles);
+    uint32_t* toff = tmp.get<uint32_t>(tiles);
+    uint32_t* sums = tmp.get<uint32_t>(scan_sums_len(tiles));
     {
     ISAX_LAUNCH("lf_lcp", st);
     lf_lcp_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(kA, N, Lc, keybits, c, a);
@@ -1434,19 +1490,19 @@ uint32_t round_robin_leaves(isax_index* ix, TempPool& tmp, const unsigned long l
                              0, st>>>(a, NA, Lc, P, S);
     }
     {
-    ISAX_LAUNCH("lf_flags", st);
-    lf_flags_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(c, P, S, N, Lc, keybits, flags);
+    ISAX_LAUNCH("lf_count", st);
+    lf_count_kernel<<<(unsigned)tiles, 256, 0, st>>>(c, P, S, N, Lc, keybits, tcount);
     }
-    exclusive_scan(flags, pos, N, sums, st);
+    exclusive_scan(tcount, toff, tiles, sums, st);
     ISAX_CUDA_TRY(cudaGetLastError());
     uint32_t L0 = 0;
-    ISAX_CUDA_TRY(cudaMemcpyAsync(&L0, sums + (scan_sums_len(N) - 1), sizeof(uint32_t),
+    ISAX_CUDA_TRY(cudaMemcpyAsync(&L0, sums + (scan_sums_len(tiles) - 1), sizeof(uint32_t),
                                   cudaMemcpyDeviceToHost, st));
     ISAX_CUDA_TRY(cudaStreamSynchronize(st));
     uint32_t* starts = tmp.get<uint32_t>((size_t)L0 + 1);
     {
-    ISAX_LAUNCH("lf_compact", st);
-    lf_compact_kernel<<<grid_for(N, 256, num_sms), 256, 0, st>>>(flags, pos, N, starts, L0);
+    ISAX_LAUNCH("lf_emit", st);
+    lf_emit_kernel<<<(unsigned)tiles, 256, 0, st>>>(c, P, S, N, Lc, keybits, toff, starts, L0);
     }
     uint32_t* pieces = tmp.get<uint32_t>(L0);
     uint32_t* poff = tmp.get<uint32_t>(L0);
@@ -1467,7 +1523,7 @@ uint32_t round_robin_leaves(isax_index* ix, TempPool& tmp, const unsigned long l
                                                                   ix->leaf_begin, L);
     }
     ISAX_CUDA_TRY(cudaGetLastError());
-    for (void* p : {(void*)c, (void*)a, (void*)P, (void*)S, (void*)flags, (void*)pos,
+    for (void* p : {(void*)c, (void*)a, (void*)P, (void*)S, (void*)tcount, (void*)toff,
                     (void*)sums, (void*)starts, (void*)pieces, (void*)poff, (void*)psums})
         tmp.release(p);
     return L;
