@@ -859,19 +859,19 @@ __device__ __forceinline__ uint32_t leaf_start_flag(const uint8_t* __restrict__ 
     return M >= ci ? 1u : 0u;
 }
 
-// Leaf starts in two passes over tiles of LF_TILE series, series i0 + 256 j + t
-// to thread t (coalesced byte loads): the number of starts of each tile, then
-// (after a scan of those counts) the starts themselves, written in order.
+// Leaf starts in two passes over tiles of LF_TILE series (LF_PER consecutive
+// series per thread): the number of starts of each tile, then (after a scan of
+// those counts) the starts themselves, written in order.
 constexpr int LF_PER = 16, LF_TILE = 256 * LF_PER;
 __global__ void __launch_bounds__(256) lf_count_kernel(const uint8_t* __restrict__ c, const uint8_t* __restrict__ P,
                                                        const uint8_t* __restrict__ S, int64_t N, int64_t L,
                                                        int keybits, uint32_t* __restrict__ tile_count) {
     __shared__ uint32_t scratch[32];
-    const int64_t i0 = (int64_t)blockIdx.x * LF_TILE + threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * LF_TILE + (int64_t)threadIdx.x * LF_PER;
     uint32_t n = 0;
 #pragma unroll
     for (int j = 0; j < LF_PER; ++j)
-        if (i0 + 256 * j < N) n += leaf_start_flag(c, P, S, (uint32_t)(i0 + 256 * j), (uint32_t)N, (uint32_t)L, keybits);
+        if (i0 + j < N) n += leaf_start_flag(c, P, S, (uint32_t)(i0 + j), (uint32_t)N, (uint32_t)L, keybits);
     uint32_t tot;
     block_excl_scan<uint32_t>(n, 0u, OpAdd<uint32_t>(), scratch, &tot);
     if (threadIdx.x == 0) tile_count[blockIdx.x] = tot;
@@ -880,35 +880,16 @@ __global__ void __launch_bounds__(256) lf_emit_kernel(const uint8_t* __restrict_
                                                       const uint8_t* __restrict__ S, int64_t N, int64_t L,
                                                       int keybits, const uint32_t* __restrict__ tile_off,
                                                       uint32_t* __restrict__ starts, uint32_t count) {
-    __shared__ uint32_t wc[LF_PER * 8 + 1];  // starts per (j, warp), then their exclusive prefix
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t i0 = (int64_t)blockIdx.x * LF_TILE + threadIdx.x;
-    uint32_t f = 0;  // bit j: series i0 + 256 j starts a leaf
+    __shared__ uint32_t scratch[32];
+    const int64_t i0 = (int64_t)blockIdx.x * LF_TILE + (int64_t)threadIdx.x * LF_PER;
+    uint32_t f = 0;  // bit j: series i0 + j starts a leaf
 #pragma unroll
-    for (int j = 0; j < LF_PER; ++j) {
-        const bool s = i0 + 256 * j < N &&
-                       leaf_start_flag(c, P, S, (uint32_t)(i0 + 256 * j), (uint32_t)N, (uint32_t)L, keybits);
-        if (s) f |= 1u << j;
-        const unsigned m = __ballot_sync(FULL, s);
-        if (lane == 0) wc[j * 8 + warp] = __popc(m);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;  // series order is j major, then warp, then lane
-        for (int q = 0; q < LF_PER * 8; ++q) {
-            const uint32_t v = wc[q];
-            wc[q] = run;
-            run += v;
-        }
-    }
-    __syncthreads();
-    const uint32_t base = tile_off[blockIdx.x];
-#pragma unroll
-    for (int j = 0; j < LF_PER; ++j) {
-        const unsigned m = __ballot_sync(FULL, (f >> j) & 1u);
-        if ((f >> j) & 1u)
-            starts[base + wc[j * 8 + warp] + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(i0 + 256 * j);
-    }
+    for (int j = 0; j < LF_PER; ++j)
+        if (i0 + j < N && leaf_start_flag(c, P, S, (uint32_t)(i0 + j), (uint32_t)N, (uint32_t)L, keybits))
+            f |= 1u << j;
+    uint32_t tot;
+    uint32_t o = tile_off[blockIdx.x] + block_excl_scan<uint32_t>(__popc(f), 0u, OpAdd<uint32_t>(), scratch, &tot);
+    for (; f; f &= f - 1u) starts[o++] = (uint32_t)(i0 + __ffs(f) - 1);
     if (blockIdx.x == 0 && threadIdx.x == 0) starts[count] = (uint32_t)N;
 }
 
