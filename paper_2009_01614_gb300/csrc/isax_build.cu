@@ -778,18 +778,24 @@ __global__ void lf_lcp_kernel(const unsigned long long* __restrict__ keys, int64
 
 // prefix max P and suffix max S of a[] inside consecutive blocks of L entries
 // (van Herk / Gil-Werman sliding-window maximum)
-constexpr int LF_THREADS = 256, LF_ITEMS = 8, LF_CHUNK = LF_THREADS * LF_ITEMS;
+constexpr int LF_THREADS = 256, LF_ITEMS = 8;
 
+// P[e] = max a[b0 .. e] and S[e] = max a[e .. b1 - 1] inside each block [b0, b1)
+// of L positions: a warp per block, LF_ITEMS consecutive positions per lane and
+// a warp max-scan per chunk of 32 x LF_ITEMS (no block barrier).
 __global__ void __launch_bounds__(LF_THREADS) lf_blockmax_kernel(const uint8_t* __restrict__ a,
                                                                   int64_t NA, int64_t L,
                                                                   uint8_t* __restrict__ P,
                                                                   uint8_t* __restrict__ S) {
-    __shared__ uint32_t scratch[32];
-    for (int64_t blk = blockIdx.x; blk * L < NA; blk += gridDim.x) {
+    constexpr int CH = 32 * LF_ITEMS;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t blk = gw; blk * L < NA; blk += nw) {
         const int64_t b0 = blk * L, b1 = std::min(b0 + L, NA);
         uint32_t carry = 0;
-        for (int64_t c0 = b0; c0 < b1; c0 += LF_CHUNK) {
-            const int64_t t0 = c0 + (int64_t)threadIdx.x * LF_ITEMS;
+        for (int64_t c0 = b0; c0 < b1; c0 += CH) {
+            const int64_t t0 = c0 + (int64_t)lane * LF_ITEMS;
             uint32_t run[LF_ITEMS];
             uint32_t m = 0;
 #pragma unroll
@@ -797,31 +803,35 @@ __global__ void __launch_bounds__(LF_THREADS) lf_blockmax_kernel(const uint8_t* 
                 if (t0 + j < b1) m = max(m, (uint32_t)a[t0 + j]);
                 run[j] = m;
             }
-            uint32_t tot;
-            uint32_t before = block_excl_scan<uint32_t>(m, 0u, OpMax<uint32_t>(), scratch, &tot);
+            const uint32_t inc = warp_incl_scan<uint32_t>(m, OpMax<uint32_t>());
+            uint32_t before = __shfl_up_sync(FULL, inc, 1);
+            if (lane == 0) before = 0;
+            const uint32_t tot = __shfl_sync(FULL, inc, 31);
 #pragma unroll
             for (int j = 0; j < LF_ITEMS; ++j)
                 if (t0 + j < b1) P[t0 + j] = (uint8_t)max(carry, max(before, run[j]));
             carry = max(carry, tot);
         }
         carry = 0;
-        for (int64_t c1 = b1; c1 > b0; c1 -= LF_CHUNK) {
-            // element e = c1 - 1 - (thread * ITEMS + j), walking right to left
-            const int64_t t1 = c1 - 1 - (int64_t)threadIdx.x * LF_ITEMS;
+        for (int64_t c1 = b1; c1 > b0; c1 -= CH) {
+            // position e = c1 - 1 - (lane * ITEMS + j), walking right to left
+            const int64_t t1 = c1 - 1 - (int64_t)lane * LF_ITEMS;
             uint32_t run[LF_ITEMS];
             uint32_t m = 0;
 #pragma unroll
             for (int j = 0; j < LF_ITEMS; ++j) {
-                int64_t e = t1 - j;
-                if (e >= b0 && e >= c1 - LF_CHUNK) m = max(m, (uint32_t)a[e]);
+                const int64_t e = t1 - j;
+                if (e >= b0 && e >= c1 - CH) m = max(m, (uint32_t)a[e]);
                 run[j] = m;
             }
-            uint32_t tot;
-            uint32_t before = block_excl_scan<uint32_t>(m, 0u, OpMax<uint32_t>(), scratch, &tot);
+            const uint32_t inc = warp_incl_scan<uint32_t>(m, OpMax<uint32_t>());
+            uint32_t before = __shfl_up_sync(FULL, inc, 1);
+            if (lane == 0) before = 0;
+            const uint32_t tot = __shfl_sync(FULL, inc, 31);
 #pragma unroll
             for (int j = 0; j < LF_ITEMS; ++j) {
-                int64_t e = t1 - j;
-                if (e >= b0 && e >= c1 - LF_CHUNK) S[e] = (uint8_t)max(carry, max(before, run[j]));
+                const int64_t e = t1 - j;
+                if (e >= b0 && e >= c1 - CH) S[e] = (uint8_t)max(carry, max(before, run[j]));
             }
             carry = max(carry, tot);
         }
@@ -1467,8 +1477,9 @@ uint32_t round_robin_leaves(isax_index* ix, TempPool& tmp, const unsigned long l
     if (NA > 0) {
         ISAX_LAUNCH("lf_blockmax", st);
         int64_t nblk = (NA + Lc - 1) / Lc;
-        lf_blockmax_kernel<<<(unsigned)std::min<int64_t>(nblk, (int64_t)num_sms * 16), LF_THREADS,
-                             0, st>>>(a, NA, Lc, P, S);
+        lf_blockmax_kernel<<<(unsigned)std::min<int64_t>((nblk + LF_THREADS / 32 - 1) / (LF_THREADS / 32),
+                                                         (int64_t)num_sms * 8),
+                             LF_THREADS, 0, st>>>(a, NA, Lc, P, S);
     }
     {
     ISAX_LAUNCH("lf_count", st);
