@@ -735,8 +735,12 @@ def reference_arm(a):
     sample = ("CPU oracle (FP64 brute-force exact %d-NN, %d host cores) of the step's %d queries "
               "over a %d-row sample of the collection, %.3f s per sample step, scaled to N=%d by rows"
               % (a.k, cores, a.queries, S, t / a.steps, a.N))
+    # a step is the bounded sample actually timed (so steps x ms_per_step is the
+    # timed region); the value is the metric at the full N (the sample's time
+    # scaled by rows)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_full * 1e3,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t / a.steps * 1e3,
+            "sample_rows": S, "ms_per_step_scaled_to_N": step_full * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(a),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",

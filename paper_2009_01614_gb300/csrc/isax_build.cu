@@ -1414,11 +1414,18 @@ bool radix_sort(unsigned long long*& kA, uint32_t*& vA, unsigned long long*& kB,
             os_hist_kernel<<<grid_for(N, OS_HIST_THREADS * OS_HIST_UNROLL, num_sms, 8), OS_HIST_THREADS, 0, st>>>(
                 kA, N, shift0, passes, hist);
         }
-        static std::once_flag attr_once;
-        std::call_once(attr_once, [] {
-            ISAX_CUDA_TRY(cudaFuncSetAttribute(os_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)OS_SMEM));
-        });
+        {
+            // the pass's shared memory (above the default limit), once per device
+            // (setting it again is harmless)
+            static bool attr_done[64] = {};
+            int dev = -1;
+            if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+            if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+                ISAX_CUDA_TRY(cudaFuncSetAttribute(os_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)OS_SMEM));
+                if (dev >= 0 && dev < 64) attr_done[dev] = true;
+            }
+        }
         for (int pass = 0; pass < passes; ++pass) {
             ISAX_LAUNCH("os_scatter", st);
             const bool last = pass + 1 == passes;

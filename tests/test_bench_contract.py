@@ -34,9 +34,12 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
-    # value = the step's queries / the step's time
+    # a step is the timed sample; value = the step's queries / the sample's time
+    # scaled to N by rows
     q = d["config"]["queries_per_step"]
-    assert abs(q / (d["ms_per_step"] / 1e3) - d["value"]) <= 1e-6 * d["value"]
+    scaled = d["ms_per_step"] * d["config"]["N"] / d["sample_rows"]
+    assert abs(d["ms_per_step_scaled_to_N"] - scaled) <= 1e-6 * scaled
+    assert abs(q / (scaled / 1e3) - d["value"]) <= 1e-6 * d["value"]
 
 
 def test_reference_arm_runs_on_rank_0_only():
