@@ -523,8 +523,8 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(
 // then adds up its predecessors' counts walking back until a tile whose
 // inclusive prefix is already published, and publishes its own.  A (tile,
 // digit) status word holds a 2-bit state over a 30-bit count (N < 2^30).
-constexpr int OS_THREADS = 512, OS_ITEMS = 8, OS_TILE = OS_THREADS * OS_ITEMS;
-constexpr int OS_CTAS = 2;  // resident per SM
+constexpr int OS_THREADS = 1024, OS_ITEMS = 8, OS_TILE = OS_THREADS * OS_ITEMS;
+constexpr int OS_CTAS = 1;  // resident per SM
 constexpr int OS_WARPS = OS_THREADS / 32;
 constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_COUNT = OS_AGG - 1u;
 constexpr uint32_t OS_WAIT = 1u << 20;  // polls of one predecessor's status before the wait gives up
