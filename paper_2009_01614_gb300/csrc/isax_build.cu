@@ -7,9 +7,10 @@
 //   summarize  - one warp per series: PAA of 16 segments, SAX symbols, and a
 //                bit-plane-interleaved key whose top 16 bits are the root key
 //                (first bit of every segment);
-//   radix sort - a stable LSD sort of (key, row) pairs: the per-root buffers
-//                become contiguous runs, and inside a run series are ordered
-//                by their next bits, so every iSAX node is a contiguous range;
+//   radix sort - a stable LSD sort of (key, row) pairs (one launch per 8-bit
+//                digit, decoupled look-back): the per-root buffers become
+//                contiguous runs, and inside a run series are ordered by
+//                their next bits, so every iSAX node is a contiguous range;
 //   leaves     - a node becomes a leaf once it holds <= leaf_size series; a
 //                node splits on the next key bit (round-robin over segments),
 //                decided for every adjacent pair from its common-prefix length
@@ -17,7 +18,9 @@
 //                or, with ISAX_BUILD_SPLIT_BALANCED, the ADS+ split itself: a
 //                sort by root key, then one pass per tree level that splits
 //                every overflowing node on its most balanced segment;
-//   permute    - rows and SAX words gathered into leaf order;
+//   permute    - rows and SAX words gathered into leaf order (with the rows
+//                kept in input order, the sort's last pass places the SAX
+//                words and row ids itself);
 //   envelopes  - per-leaf min/max symbol of every segment.
 #include <algorithm>
 #include <mutex>
@@ -578,10 +581,10 @@ __global__ void __launch_bounds__(OS_HIST_THREADS) os_hist_kernel(const unsigned
 // pair's final position in sax_dst / orig_dst, the random 16-byte gathers
 // overlapping the pass instead of running as a launch of their own.
 // The tile's digit counts are taken and published as soon as its keys are in,
-// and the first 256 threads (one digit each) walk back while any further warps
-// rank their keys; the walk reads OS_LOOK predecessors' words at a time, so that a run of
-// tiles that have published only their own counts costs one round trip per
-// OS_LOOK of them.
+// and the first 256 threads (one digit each) walk back while the other warps
+// rank their keys; the walk reads OS_LOOK predecessors' words at a time, so
+// that a run of tiles that have published only their own counts costs one
+// round trip per OS_LOOK of them.
 __global__ void __launch_bounds__(OS_THREADS, OS_CTAS) os_scatter_kernel(
     const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
     unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, int64_t N, int shift,
